@@ -1,0 +1,378 @@
+"""FP64 CPU oracle for the Tactile Genesis contact query and noise model.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / reference legs of ``bench.py`` may import this package.  It
+shares no code with the CUDA path and takes no input from it.
+
+The arithmetic lives in ``tg_oracle.c`` (plain C, double precision, one
+function per passage of the paper); this module only compiles it and
+marshals numpy arrays through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tg_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_tg_oracle.so")
+_lib = None
+_lock = threading.Lock()
+
+OR_SPHERE, OR_BOX, OR_PLANE, OR_MESH, OR_GRID = 0, 1, 2, 3, 4
+NCH = 8
+LINK_REC = 18
+
+
+def build(force: bool = False) -> str:
+    """Compile tg_oracle.c into _tg_oracle.so (OpenMP when the compiler has it)."""
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= max(
+        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "tg_oracle.h"))
+    ):
+        return _LIB_PATH
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC", _SRC, "-o", _LIB_PATH + ".tmp"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:] + ["-lm"], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base + ["-lm"], check=True, capture_output=True)
+    os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
+    return _LIB_PATH
+
+
+class ORObject(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int32), ("radius", C.c_double), ("half", C.c_double * 3),
+        ("n_verts", C.c_int32), ("n_faces", C.c_int32),
+        ("verts", C.c_void_p), ("faces", C.c_void_p),
+        ("dims", C.c_int32 * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+        ("fp16", C.c_int32), ("values", C.c_void_p),
+    ]
+
+
+class ORNoiseGroup(C.Structure):
+    _fields_ = [(n, C.c_double) for n in (
+        "gain_lo", "gain_hi", "beta", "tau", "bias", "sigma_white", "sigma_rw", "quant", "stuck_lo", "stuck_hi")]
+
+
+class ORParams(C.Structure):
+    _fields_ = [
+        ("k", C.c_double), ("c", C.c_double), ("alpha", C.c_double), ("k_t", C.c_double),
+        ("k_omega", C.c_double), ("mu", C.c_double), ("eta_on", C.c_double), ("eta_off", C.c_double),
+        ("dt", C.c_double), ("seed", C.c_uint64), ("p_dead", C.c_double),
+        ("depth", ORNoiseGroup), ("ft", ORNoiseGroup), ("prox", ORNoiseGroup),
+        ("chi", C.c_double), ("xt_sigma", C.c_double),
+    ]
+
+
+class ORScene(C.Structure):
+    _fields_ = [
+        ("n_envs", C.c_int32), ("max_links", C.c_int32),
+        ("taxel_offsets", C.c_void_p), ("taxel_gid0", C.c_void_p), ("env_gid", C.c_void_p),
+        ("link_rows", C.c_void_p), ("link_cols", C.c_void_p), ("link_wrap", C.c_void_p),
+        ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
+        ("nx", C.c_void_p), ("ny", C.c_void_p), ("nz", C.c_void_p), ("R", C.c_void_p),
+        ("objects", C.c_void_p), ("n_objects", C.c_int32), ("params", ORParams),
+    ]
+
+
+class ORInputs(C.Structure):
+    _fields_ = [
+        ("link_pose", C.c_void_p), ("link_vel", C.c_void_p), ("obj_pose", C.c_void_p),
+        ("obj_vel", C.c_void_p), ("obj_id", C.c_void_p), ("env_params", C.c_void_p),
+        ("pose_dt", C.c_double), ("step", C.c_uint32),
+    ]
+
+
+class ORState(C.Structure):
+    _fields_ = [("flags", C.c_void_p), ("hyst_prev", C.c_void_p), ("hyst_xi", C.c_void_p),
+                ("drift", C.c_void_p), ("episode", C.c_void_p)]
+
+
+class OROutputs(C.Structure):
+    _fields_ = [("contact_clean", C.c_void_p), ("contact_noisy", C.c_void_p),
+                ("depth_clean", C.c_void_p), ("depth_noisy", C.c_void_p), ("dist", C.c_void_p),
+                ("ft_clean", C.c_void_p), ("ft_noisy", C.c_void_p),
+                ("link_sums", C.c_void_p), ("link_counts", C.c_void_p)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            dp = C.POINTER(C.c_double)
+            L.or_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+            L.or_uniform.argtypes = [C.c_uint32]; L.or_uniform.restype = C.c_double
+            L.or_box_muller.argtypes = [C.c_uint32, C.c_uint32, dp, dp]
+            L.or_double_to_half.argtypes = [C.c_double]; L.or_double_to_half.restype = C.c_uint16
+            L.or_half_to_double.argtypes = [C.c_uint16]; L.or_half_to_double.restype = C.c_double
+            L.or_quat_to_mat.argtypes = [C.c_void_p, C.c_void_p]
+            L.or_advance_pose.argtypes = [C.c_void_p] * 4 + [C.c_double, C.c_void_p, C.c_void_p]
+            L.or_closest_point_triangle.argtypes = [C.c_void_p] * 5 + [C.POINTER(C.c_int)]
+            L.or_closest_point_triangle.restype = C.c_double
+            L.or_winding_number.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
+            L.or_winding_number.restype = C.c_double
+            L.or_sdf_object_batch.argtypes = [C.POINTER(ORObject), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+            L.or_schmitt.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double]; L.or_schmitt.restype = C.c_int
+            L.or_taxel_force.argtypes = [C.POINTER(ORParams), C.c_double, C.c_double, C.c_double,
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]
+            L.or_crosstalk_weights.argtypes = [C.c_double, C.c_void_p]
+            L.or_bake_grid.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_int32, C.c_void_p, C.c_int32]
+            L.or_reset.argtypes = [C.POINTER(ORScene), C.c_void_p, C.c_uint32, C.POINTER(ORState)]
+            L.or_step.argtypes = [C.POINTER(ORScene), C.POINTER(ORInputs), C.POINTER(ORState),
+                                  C.POINTER(OROutputs), C.c_int32]
+            L.or_step.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data if a is not None else None
+
+
+# --------------------------------------------------------------------------
+# primitives
+# --------------------------------------------------------------------------
+def philox(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    o = np.zeros(4, np.uint32)
+    lib().or_philox4x32_10(_p(c), _p(k), _p(o))
+    return o
+
+
+def uniform(x):
+    return lib().or_uniform(int(x))
+
+
+def box_muller(x0, x1):
+    z0, z1 = C.c_double(), C.c_double()
+    lib().or_box_muller(int(x0), int(x1), C.byref(z0), C.byref(z1))
+    return z0.value, z1.value
+
+
+def double_to_half(x):
+    return lib().or_double_to_half(float(x))
+
+
+def half_to_double(h):
+    return lib().or_half_to_double(int(h))
+
+
+def quat_to_mat(q):
+    q = np.ascontiguousarray(q, np.float64)
+    R = np.zeros(9)
+    lib().or_quat_to_mat(_p(q), _p(R))
+    return R.reshape(3, 3)
+
+
+def advance_pose(p0, q0, v, w, tau):
+    a = [np.ascontiguousarray(t, np.float64) for t in (p0, q0, v, w)]
+    p = np.zeros(3); R = np.zeros(9)
+    lib().or_advance_pose(*[_p(t) for t in a], float(tau), _p(p), _p(R))
+    return p, R.reshape(3, 3)
+
+
+def closest_point_triangle(p, a, b, c):
+    arr = [np.ascontiguousarray(t, np.float64) for t in (p, a, b, c)]
+    cp = np.zeros(3)
+    reg = C.c_int()
+    d = lib().or_closest_point_triangle(*[_p(t) for t in arr], _p(cp), C.byref(reg))
+    return d, cp, reg.value
+
+
+def winding_number(verts, faces, p):
+    V = np.ascontiguousarray(verts, np.float32); F = np.ascontiguousarray(faces, np.int32)
+    p = np.ascontiguousarray(p, np.float64)
+    return lib().or_winding_number(_p(V), _p(F), len(F), _p(p))
+
+
+class Obj:
+    """An oracle object; keeps the arrays its ctypes struct points at alive."""
+
+    def __init__(self, kind, radius=0.0, half=(0, 0, 0), verts=None, faces=None,
+                 dims=(0, 0, 0), lo=(0, 0, 0), hi=(0, 0, 0), values=None, fp16=False):
+        self.keep = []
+        s = ORObject()
+        s.kind = kind
+        s.radius = float(radius)
+        s.half[:] = [float(h) for h in half]
+        if verts is not None:
+            V = np.ascontiguousarray(verts, np.float32); F = np.ascontiguousarray(faces, np.int32)
+            self.keep += [V, F]
+            s.n_verts, s.n_faces = len(V), len(F)
+            s.verts, s.faces = _p(V), _p(F)
+        if values is not None:
+            vals = np.ascontiguousarray(values, np.uint16 if fp16 else np.float32)
+            self.keep.append(vals)
+            s.values = _p(vals)
+            s.fp16 = 1 if fp16 else 0
+        s.dims[:] = [int(d) for d in dims]
+        s.lo[:] = [float(v) for v in lo]
+        s.hi[:] = [float(v) for v in hi]
+        self.s = s
+
+    @staticmethod
+    def sphere(r):
+        return Obj(OR_SPHERE, radius=r)
+
+    @staticmethod
+    def box(half):
+        return Obj(OR_BOX, half=half)
+
+    @staticmethod
+    def plane():
+        return Obj(OR_PLANE)
+
+    @staticmethod
+    def mesh(verts, faces):
+        return Obj(OR_MESH, verts=verts, faces=faces)
+
+    @staticmethod
+    def grid(values, lo, hi, fp16=False):
+        values = np.asarray(values)
+        nz, ny, nx = values.shape
+        return Obj(OR_GRID, dims=(nx, ny, nz), lo=lo, hi=hi, values=values, fp16=fp16)
+
+    def sdf(self, q):
+        q = np.ascontiguousarray(np.atleast_2d(q), np.float64)
+        n = len(q)
+        phi = np.zeros(n); g = np.zeros((n, 3))
+        lib().or_sdf_object_batch(C.byref(self.s), _p(q), n, _p(phi), _p(g))
+        return phi, g
+
+
+def schmitt(prev, d, eta_on, eta_off):
+    return lib().or_schmitt(int(prev), float(d), float(eta_on), float(eta_off))
+
+
+def crosstalk_weights(sigma):
+    w = np.zeros(9)
+    lib().or_crosstalk_weights(float(sigma), _p(w))
+    return w.reshape(3, 3)
+
+
+def bake_grid(verts, faces, dims, lo, hi, fp16=False, threads=0):
+    """Exact mesh SDF at the grid nodes, rounded to float32 or binary16 bits; [z][y][x]."""
+    V = np.ascontiguousarray(verts, np.float32); F = np.ascontiguousarray(faces, np.int32)
+    d = np.ascontiguousarray(dims, np.int32)
+    lo = np.ascontiguousarray(lo, np.float64); hi = np.ascontiguousarray(hi, np.float64)
+    out = np.zeros((d[2], d[1], d[0]), np.uint16 if fp16 else np.float32)
+    lib().or_bake_grid(_p(V), _p(F), len(F), _p(d), _p(lo), _p(hi), 1 if fp16 else 0, _p(out), int(threads))
+    return out
+
+
+# --------------------------------------------------------------------------
+# parameters
+# --------------------------------------------------------------------------
+_GROUP_KEYS = ("gain_lo", "gain_hi", "beta", "tau", "bias", "sigma_white", "sigma_rw", "quant", "stuck_lo", "stuck_hi")
+
+
+def make_params(p: dict) -> ORParams:
+    """Fill the C parameter struct from the plain dict used by the workloads."""
+    P = ORParams()
+    for k in ("k", "c", "alpha", "k_t", "k_omega", "eta_on", "eta_off", "dt", "p_dead", "chi", "xt_sigma"):
+        setattr(P, k, float(p[k]))
+    P.mu = -1.0 if p["mu"] is None or np.isinf(p["mu"]) else float(p["mu"])
+    P.seed = int(p["seed"])
+    for gname in ("depth", "ft", "prox"):
+        g = getattr(P, gname)
+        for k in _GROUP_KEYS:
+            setattr(g, k, float(p["noise"][gname][k]))
+    return P
+
+
+def taxel_force(params: dict, k, mu, d, x, mbar, vrel, dw_dot_m):
+    P = make_params(params)
+    arr = [np.ascontiguousarray(t, np.float64) for t in (x, mbar, vrel)]
+    f = np.zeros(3); tau = np.zeros(3)
+    mu_c = -1.0 if mu is None or np.isinf(mu) else float(mu)
+    lib().or_taxel_force(C.byref(P), float(k), mu_c, float(d), *[_p(t) for t in arr], float(dw_dot_m), _p(f), _p(tau))
+    return f, tau
+
+
+# --------------------------------------------------------------------------
+# whole-scene oracle
+# --------------------------------------------------------------------------
+class OracleScene:
+    """A (sub)scene in oracle form.
+
+    ``geom`` is a dict with the workload's static arrays (taxel_offsets,
+    taxel_gid0, env_gid, link_rows, link_cols, link_wrap, x..R) and ``objects``
+    a list of :class:`Obj`.
+    """
+
+    def __init__(self, geom: dict, objects: list, params: dict):
+        self.keep = {}
+        g = {}
+        for k, dt in (("taxel_offsets", np.int64), ("taxel_gid0", np.int64), ("env_gid", np.int32),
+                      ("link_rows", np.int32), ("link_cols", np.int32), ("link_wrap", np.uint8),
+                      ("x", np.float32), ("y", np.float32), ("z", np.float32),
+                      ("nx", np.float32), ("ny", np.float32), ("nz", np.float32), ("R", np.float32)):
+            g[k] = np.ascontiguousarray(geom[k], dt)
+        self.keep.update(g)
+        self.n_envs = len(g["taxel_offsets"]) - 1
+        self.max_links = len(g["link_rows"]) // self.n_envs
+        self.T = int(g["taxel_offsets"][-1])
+        self.objects = objects
+        arr = (ORObject * len(objects))(*[o.s for o in objects])
+        self.keep["objarr"] = arr
+        S = ORScene()
+        S.n_envs, S.max_links = self.n_envs, self.max_links
+        for k in g:
+            setattr(S, k, _p(g[k]))
+        S.objects = C.cast(arr, C.c_void_p)
+        S.n_objects = len(objects)
+        S.params = make_params(params)
+        self.S = S
+        self.params = params
+
+    def new_state(self):
+        T, E = self.T, self.n_envs
+        return {
+            "flags": np.zeros(T, np.uint8),
+            "hyst_prev": np.zeros((NCH, T)), "hyst_xi": np.zeros((NCH, T)), "drift": np.zeros((NCH, T)),
+            "episode": np.zeros(E, np.uint32),
+        }
+
+    def _state(self, st):
+        s = ORState()
+        for k in ("flags", "hyst_prev", "hyst_xi", "drift", "episode"):
+            setattr(s, k, _p(st[k]))
+        return s
+
+    def reset(self, st, episode, env_mask=None):
+        m = None if env_mask is None else np.ascontiguousarray(env_mask, np.uint8)
+        s = self._state(st)
+        lib().or_reset(C.byref(self.S), _p(m), int(episode), C.byref(s))
+
+    def step(self, st, inputs: dict, threads: int = 0):
+        T, E, L = self.T, self.n_envs, self.max_links
+        keep = {}
+        I = ORInputs()
+        for k, dt in (("link_pose", np.float32), ("link_vel", np.float32), ("obj_pose", np.float32),
+                      ("obj_vel", np.float32), ("obj_id", np.int32)):
+            keep[k] = np.ascontiguousarray(inputs[k], dt)
+            setattr(I, k, _p(keep[k]))
+        if inputs.get("env_params") is not None:
+            keep["env_params"] = np.ascontiguousarray(inputs["env_params"], np.float32)
+            I.env_params = _p(keep["env_params"])
+        I.pose_dt = float(inputs.get("pose_dt", 0.0))
+        I.step = int(inputs.get("step", 0))
+        out = {
+            "contact_clean": np.zeros(T, np.uint8), "contact_noisy": np.zeros(T, np.uint8),
+            "depth_clean": np.zeros(T), "depth_noisy": np.zeros(T), "dist": np.zeros(T),
+            "ft_clean": np.zeros((6, T)), "ft_noisy": np.zeros((6, T)),
+            "link_sums": np.zeros((E * L, LINK_REC)), "link_counts": np.zeros((E * L, 2), np.int32),
+        }
+        O = OROutputs()
+        for k in out:
+            setattr(O, k, _p(out[k]))
+        s = self._state(st)
+        lib().or_step(C.byref(self.S), C.byref(I), C.byref(s), C.byref(O), int(threads))
+        return out

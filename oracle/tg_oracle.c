@@ -1,0 +1,728 @@
+/*
+ * tg_oracle.c -- FP64 CPU oracle for the Tactile Genesis contact query and
+ * noise model.  TEST INFRASTRUCTURE ONLY (see tg_oracle.h): used by tests/,
+ * __graft_entry__.smoke() and bench.py's cpu_baseline / reference legs, never
+ * by the product path.
+ *
+ * Each function follows one passage of the paper (arxiv 2606.22332):
+ *   Appendix A "Probe geometry and contact-depth query"  Eqs. 1-2
+ *   Appendix A "ContactProbe"                          Eq. 3
+ *   Appendix A "KinematicTaxel"                        Eqs. 4-9, 11
+ *   Appendix A "Sensor Noise Model"                    Eqs. 25-31
+ *   Appendix B "Tactile Observation Types"             Eq. 32 (agg_force)
+ * plus the published methods the paper relies on without printing them:
+ *   Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11),
+ *   Box-Muller (1958),
+ *   closest point on a triangle by Voronoi regions (Ericson, RTCD 5.1.5),
+ *   generalised winding number (Jacobson et al. 2013) with the
+ *   Van Oosterom-Strackee (1983) solid angle.
+ * The readings where the paper is silent are listed in the design doc.
+ */
+#include "tg_oracle.h"
+
+#include <math.h>
+#include <stddef.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define PI 3.14159265358979323846
+
+/* ======================================================================== */
+/* Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32->64 bit     */
+/* multiplications with the published multipliers and Weyl key increments. */
+/* ======================================================================== */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* uniform in (0,1): the top 24 bits plus one half, scaled by 2^-24 */
+double or_uniform(uint32_t x) { return ((double)(x >> 8) + 0.5) * 0x1p-24; }
+
+/* Box-Muller: two independent standard normals from two uniforms */
+void or_box_muller(uint32_t x0, uint32_t x1, double* z0, double* z1) {
+    double u0 = or_uniform(x0), u1 = or_uniform(x1);
+    double r = sqrt(-2.0 * log(u0));
+    *z0 = r * cos(2.0 * PI * u1);
+    *z1 = r * sin(2.0 * PI * u1);
+}
+
+/* Philox stream tags: which draw a counter belongs to */
+enum {
+    TAG_EPISODE = 1,  /* w0 dead Bernoulli, w1..w3 gain (depth, ft, prox) */
+    TAG_STUCK = 2,    /* w0..w2 stuck readout uniforms (depth, ft, prox) */
+    TAG_FT_A = 16,    /* normals: drift fx fy fz tx */
+    TAG_FT_B = 17,    /* normals: drift ty tz, white fx fy */
+    TAG_FT_C = 18,    /* normals: white fz tx ty tz */
+    TAG_SCALAR = 19,  /* normals: drift depth, white depth, drift prox, white prox */
+    TAG_DR = 32       /* per-env domain randomisation */
+};
+
+static void philox_draw(uint64_t seed, uint64_t gid, uint32_t word1, uint32_t tag, uint32_t out[4]) {
+    uint32_t ctr[4] = {(uint32_t)gid, word1, tag, (uint32_t)(gid >> 32)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    or_philox4x32_10(ctr, key, out);
+}
+
+static void philox_normals(uint64_t seed, uint64_t gid, uint32_t step, uint32_t tag, double z[4]) {
+    uint32_t w[4];
+    philox_draw(seed, gid, step, tag, w);
+    or_box_muller(w[0], w[1], &z[0], &z[1]);
+    or_box_muller(w[2], w[3], &z[2], &z[3]);
+}
+
+/* Bernoulli(p) decided on integers: the top 24 bits below round(p 2^24) */
+static int bernoulli(uint32_t x, double p) {
+    double thr = nearbyint(p * 16777216.0);
+    return (double)(x >> 8) < thr;
+}
+
+/* ======================================================================== */
+/* IEEE 754 binary16 <-> double, written from the format definition.        */
+/* ======================================================================== */
+uint16_t or_double_to_half(double x) {
+    uint16_t sign = signbit(x) ? 0x8000u : 0u;
+    double a = fabs(x);
+    if (isnan(x)) return 0x7e00u;
+    if (a >= 65520.0) return (uint16_t)(sign | 0x7c00u);
+    if (a < 0x1p-14) {            /* subnormal: a multiple of 2^-24 */
+        double m = nearbyint(a * 0x1p24);
+        return (uint16_t)(sign | (uint16_t)m);
+    }
+    int e;
+    double fr = frexp(a, &e);     /* a = fr 2^e, fr in [0.5, 1) */
+    int E = e - 1;                /* a = (1 + f) 2^E */
+    double m = nearbyint((fr * 2.0 - 1.0) * 1024.0);
+    if (m == 1024.0) { m = 0.0; E += 1; }
+    if (E > 15) return (uint16_t)(sign | 0x7c00u);
+    return (uint16_t)(sign | (uint16_t)((E + 15) << 10) | (uint16_t)m);
+}
+
+double or_half_to_double(uint16_t h) {
+    int s = h >> 15, E = (h >> 10) & 31, m = h & 1023;
+    double v;
+    if (E == 0) v = ldexp((double)m, -24);
+    else if (E == 31) v = m ? NAN : INFINITY;
+    else v = ldexp((double)(m + 1024), E - 25);
+    return s ? -v : v;
+}
+
+/* ======================================================================== */
+/* small vector helpers                                                      */
+/* ======================================================================== */
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void cross3(const double a[3], const double b[3], double o[3]) {
+    double t0 = a[1] * b[2] - a[2] * b[1];
+    double t1 = a[2] * b[0] - a[0] * b[2];
+    double t2 = a[0] * b[1] - a[1] * b[0];
+    o[0] = t0; o[1] = t1; o[2] = t2;
+}
+static double norm3(const double a[3]) { return sqrt(dot3(a, a)); }
+static void sub3(const double a[3], const double b[3], double o[3]) { o[0] = a[0] - b[0]; o[1] = a[1] - b[1]; o[2] = a[2] - b[2]; }
+static void matvec(const double R[9], const double v[3], double o[3]) {
+    double t0 = R[0] * v[0] + R[1] * v[1] + R[2] * v[2];
+    double t1 = R[3] * v[0] + R[4] * v[1] + R[5] * v[2];
+    double t2 = R[6] * v[0] + R[7] * v[1] + R[8] * v[2];
+    o[0] = t0; o[1] = t1; o[2] = t2;
+}
+static void matTvec(const double R[9], const double v[3], double o[3]) {
+    double t0 = R[0] * v[0] + R[3] * v[1] + R[6] * v[2];
+    double t1 = R[1] * v[0] + R[4] * v[1] + R[7] * v[2];
+    double t2 = R[2] * v[0] + R[5] * v[1] + R[8] * v[2];
+    o[0] = t0; o[1] = t1; o[2] = t2;
+}
+static void matmul(const double A[9], const double B[9], double C[9]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            C[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
+}
+
+/* ======================================================================== */
+/* Poses (Appendix A, Eq. 1 and the constant-velocity advance of the        */
+/* synthetic workload): rotation of a quaternion of any norm, Rodrigues.    */
+/* ======================================================================== */
+void or_quat_to_mat(const double q[4], double R[9]) {
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    double s = 2.0 / (w * w + x * x + y * y + z * z);
+    R[0] = 1.0 - s * (y * y + z * z); R[1] = s * (x * y - w * z);       R[2] = s * (x * z + w * y);
+    R[3] = s * (x * y + w * z);       R[4] = 1.0 - s * (x * x + z * z); R[5] = s * (y * z - w * x);
+    R[6] = s * (x * z - w * y);       R[7] = s * (y * z + w * x);       R[8] = 1.0 - s * (x * x + y * y);
+}
+
+/* p = p0 + v tau ;  R = exp([w] tau) R(q0)  with exp by Rodrigues' formula */
+void or_advance_pose(const double p0[3], const double q0[4], const double v[3],
+                     const double w[3], double tau, double p[3], double R[9]) {
+    double R0[9];
+    or_quat_to_mat(q0, R0);
+    for (int a = 0; a < 3; ++a) p[a] = p0[a] + v[a] * tau;
+    double th = norm3(w) * tau;
+    if (th == 0.0) { memcpy(R, R0, sizeof(R0)); return; }
+    double k[3] = {w[0] / norm3(w), w[1] / norm3(w), w[2] / norm3(w)};
+    double K[9] = {0, -k[2], k[1], k[2], 0, -k[0], -k[1], k[0], 0};
+    double K2[9];
+    matmul(K, K, K2);
+    double s = sin(th), c1 = 1.0 - cos(th);
+    double E[9];
+    for (int i = 0; i < 9; ++i) E[i] = (i % 4 == 0 ? 1.0 : 0.0) + s * K[i] + c1 * K2[i];
+    matmul(E, R0, R);
+}
+
+/* ======================================================================== */
+/* Signed distance fields (Appendix A, Eq. 2: depth uses phi_g, normal is   */
+/* grad phi).  Every function returns phi and writes the unit gradient g.   */
+/* ======================================================================== */
+double or_sdf_sphere(double r, const double q[3], double g[3]) {
+    double n = norm3(q);
+    if (n > 0.0) { g[0] = q[0] / n; g[1] = q[1] / n; g[2] = q[2] / n; }
+    else { g[0] = 0.0; g[1] = 0.0; g[2] = 1.0; }
+    return n - r;
+}
+
+/* axis-aligned box of half extents h centred at the origin */
+double or_sdf_box(const double h[3], const double q[3], double g[3]) {
+    double d[3], o[3];
+    for (int a = 0; a < 3; ++a) { d[a] = fabs(q[a]) - h[a]; o[a] = d[a] > 0.0 ? d[a] : 0.0; }
+    double outside = norm3(o);
+    int amax = 0;
+    if (d[1] > d[amax]) amax = 1;
+    if (d[2] > d[amax]) amax = 2;
+    if (outside > 0.0) {
+        for (int a = 0; a < 3; ++a) g[a] = (q[a] < 0.0 ? -o[a] : o[a]) / outside;
+        return outside;
+    }
+    g[0] = g[1] = g[2] = 0.0;
+    g[amax] = q[amax] < 0.0 ? -1.0 : 1.0;
+    return d[amax];
+}
+
+/* half-space z <= 0 (the surface is the plane z = 0, outward normal +z) */
+double or_sdf_plane(const double q[3], double g[3]) {
+    g[0] = 0.0; g[1] = 0.0; g[2] = 1.0;
+    return q[2];
+}
+
+/* Closest point on triangle abc to p by Voronoi-region classification.
+   region: 0 face, 1 a, 2 b, 3 c, 4 edge ab, 5 edge ac, 6 edge bc.
+   Returns the Euclidean distance |p - cp|. */
+double or_closest_point_triangle(const double p[3], const double a[3], const double b[3],
+                                 const double c[3], double cp[3], int* region) {
+    double ab[3], ac[3], ap[3], bp[3], cpv[3];
+    sub3(b, a, ab); sub3(c, a, ac); sub3(p, a, ap);
+    double d1 = dot3(ab, ap), d2 = dot3(ac, ap);
+    if (d1 <= 0.0 && d2 <= 0.0) {
+        memcpy(cp, a, 3 * sizeof(double)); *region = 1;
+        goto done;
+    }
+    sub3(p, b, bp);
+    double d3 = dot3(ab, bp), d4 = dot3(ac, bp);
+    if (d3 >= 0.0 && d4 <= d3) {
+        memcpy(cp, b, 3 * sizeof(double)); *region = 2;
+        goto done;
+    }
+    double vc = d1 * d4 - d3 * d2;
+    if (vc <= 0.0 && d1 >= 0.0 && d3 <= 0.0) {
+        double v = d1 / (d1 - d3);
+        for (int i = 0; i < 3; ++i) cp[i] = a[i] + v * ab[i];
+        *region = 4;
+        goto done;
+    }
+    sub3(p, c, cpv);
+    double d5 = dot3(ab, cpv), d6 = dot3(ac, cpv);
+    if (d6 >= 0.0 && d5 <= d6) {
+        memcpy(cp, c, 3 * sizeof(double)); *region = 3;
+        goto done;
+    }
+    double vb = d5 * d2 - d1 * d6;
+    if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) {
+        double w = d2 / (d2 - d6);
+        for (int i = 0; i < 3; ++i) cp[i] = a[i] + w * ac[i];
+        *region = 5;
+        goto done;
+    }
+    double va = d3 * d6 - d5 * d4;
+    if (va <= 0.0 && (d4 - d3) >= 0.0 && (d5 - d6) >= 0.0) {
+        double w = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+        for (int i = 0; i < 3; ++i) cp[i] = b[i] + w * (c[i] - b[i]);
+        *region = 6;
+        goto done;
+    }
+    {
+        double den = 1.0 / (va + vb + vc);
+        double v = vb * den, w = vc * den;
+        for (int i = 0; i < 3; ++i) cp[i] = a[i] + ab[i] * v + ac[i] * w;
+        *region = 0;
+    }
+done:;
+    double dd[3];
+    sub3(p, cp, dd);
+    return norm3(dd);
+}
+
+static void vert(const float* V, int32_t i, double o[3]) {
+    o[0] = (double)V[3 * i]; o[1] = (double)V[3 * i + 1]; o[2] = (double)V[3 * i + 2];
+}
+
+/* generalised winding number: sum of signed solid angles / (4 pi) */
+double or_winding_number(const float* V, const int32_t* F, int32_t nf, const double p[3]) {
+    double total = 0.0;
+    for (int32_t f = 0; f < nf; ++f) {
+        double a[3], b[3], c[3], A[3], B[3], C[3], BxC[3];
+        vert(V, F[3 * f], a); vert(V, F[3 * f + 1], b); vert(V, F[3 * f + 2], c);
+        sub3(a, p, A); sub3(b, p, B); sub3(c, p, C);
+        double la = norm3(A), lb = norm3(B), lc = norm3(C);
+        cross3(B, C, BxC);
+        double num = dot3(A, BxC);
+        double den = la * lb * lc + dot3(A, B) * lc + dot3(B, C) * la + dot3(C, A) * lb;
+        total += 2.0 * atan2(num, den);
+    }
+    return total / (4.0 * PI);
+}
+
+/* exact mesh SDF: unsigned distance = min over faces; negative where the
+   winding number exceeds 1/2; gradient sign (q - c*)/|q - c*|, or the face
+   normal of the nearest face when the point lies on the surface. */
+double or_sdf_mesh(const float* V, const int32_t* F, int32_t nf, const double p[3], double g[3]) {
+    double best = INFINITY, bcp[3] = {0, 0, 0};
+    int32_t bface = 0;
+    for (int32_t f = 0; f < nf; ++f) {
+        double a[3], b[3], c[3], cp[3];
+        int reg;
+        vert(V, F[3 * f], a); vert(V, F[3 * f + 1], b); vert(V, F[3 * f + 2], c);
+        double d = or_closest_point_triangle(p, a, b, c, cp, &reg);
+        if (d < best) { best = d; bface = f; memcpy(bcp, cp, sizeof(bcp)); }
+    }
+    double w = or_winding_number(V, F, nf, p);
+    double sign = w > 0.5 ? -1.0 : 1.0;
+    if (best >= 1e-12) {
+        for (int i = 0; i < 3; ++i) g[i] = sign * (p[i] - bcp[i]) / best;
+    } else {
+        double a[3], b[3], c[3], ab[3], ac[3], n[3];
+        vert(V, F[3 * bface], a); vert(V, F[3 * bface + 1], b); vert(V, F[3 * bface + 2], c);
+        sub3(b, a, ab); sub3(c, a, ac); cross3(ab, ac, n);
+        double nn = norm3(n);
+        for (int i = 0; i < 3; ++i) g[i] = n[i] / nn;
+    }
+    return sign * best;
+}
+
+/* Sampled grid: node (i,j,k) at lo + (i,j,k) h, h = (hi - lo)/(dims - 1);
+   trilinear interpolation of the stored values at the point clamped into the
+   box, plus the distance from the point to the box; the gradient is the
+   analytic gradient of the trilinear interpolant at the clamped point. */
+static double grid_node(const or_object* o, int i, int j, int k) {
+    size_t idx = ((size_t)k * (size_t)o->dims[1] + (size_t)j) * (size_t)o->dims[0] + (size_t)i;
+    if (o->fp16) return or_half_to_double(((const uint16_t*)o->values)[idx]);
+    return (double)((const float*)o->values)[idx];
+}
+
+double or_sdf_grid(const or_object* o, const double q[3], double g[3]) {
+    double c[3], f[3], h[3];
+    int i0[3];
+    for (int a = 0; a < 3; ++a) {
+        c[a] = q[a] < o->lo[a] ? o->lo[a] : (q[a] > o->hi[a] ? o->hi[a] : q[a]);
+        h[a] = (o->hi[a] - o->lo[a]) / (double)(o->dims[a] - 1);
+        double u = (c[a] - o->lo[a]) / h[a];
+        int i = (int)floor(u);
+        if (i > o->dims[a] - 2) i = o->dims[a] - 2;
+        if (i < 0) i = 0;
+        i0[a] = i;
+        f[a] = u - (double)i;
+    }
+    double v[2][2][2];
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) v[dz][dy][dx] = grid_node(o, i0[0] + dx, i0[1] + dy, i0[2] + dz);
+    double fx = f[0], fy = f[1], fz = f[2];
+    double phi = 0.0;
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx)
+                phi += v[dz][dy][dx] * (dx ? fx : 1.0 - fx) * (dy ? fy : 1.0 - fy) * (dz ? fz : 1.0 - fz);
+    double gx = 0.0, gy = 0.0, gz = 0.0;
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy) gx += (v[dz][dy][1] - v[dz][dy][0]) * (dy ? fy : 1.0 - fy) * (dz ? fz : 1.0 - fz);
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dx = 0; dx < 2; ++dx) gy += (v[dz][1][dx] - v[dz][0][dx]) * (dx ? fx : 1.0 - fx) * (dz ? fz : 1.0 - fz);
+    for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) gz += (v[1][dy][dx] - v[0][dy][dx]) * (dx ? fx : 1.0 - fx) * (dy ? fy : 1.0 - fy);
+    double gr[3] = {gx / h[0], gy / h[1], gz / h[2]};
+    double gn = norm3(gr);
+    if (gn > 0.0) { g[0] = gr[0] / gn; g[1] = gr[1] / gn; g[2] = gr[2] / gn; }
+    else {
+        double qn = norm3(q);
+        if (qn > 0.0) { g[0] = q[0] / qn; g[1] = q[1] / qn; g[2] = q[2] / qn; }
+        else { g[0] = 0.0; g[1] = 0.0; g[2] = 1.0; }
+    }
+    double out[3];
+    sub3(q, c, out);
+    return phi + norm3(out);
+}
+
+double or_sdf_object(const or_object* o, const double q[3], double g[3]) {
+    switch (o->kind) {
+    case OR_SPHERE: return or_sdf_sphere(o->radius, q, g);
+    case OR_BOX: return or_sdf_box(o->half, q, g);
+    case OR_PLANE: return or_sdf_plane(q, g);
+    case OR_MESH: return or_sdf_mesh(o->verts, o->faces, o->n_faces, q, g);
+    case OR_GRID: return or_sdf_grid(o, q, g);
+    default: g[0] = g[1] = g[2] = NAN; return NAN;
+    }
+}
+
+void or_sdf_object_batch(const or_object* o, const double* q, int64_t n, double* phi, double* g) {
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) phi[i] = or_sdf_object(o, q + 3 * i, g + 3 * i);
+}
+
+/* exact mesh SDF sampled at the grid nodes, rounded to float or binary16 */
+void or_bake_grid(const float* V, const int32_t* F, int32_t nf, const int32_t dims[3],
+                  const double lo[3], const double hi[3], int32_t fp16, void* out, int32_t threads) {
+    int64_t n = (int64_t)dims[0] * dims[1] * dims[2];
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#else
+    (void)threads;
+#endif
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t idx = 0; idx < n; ++idx) {
+        int i = (int)(idx % dims[0]);
+        int j = (int)((idx / dims[0]) % dims[1]);
+        int k = (int)(idx / ((int64_t)dims[0] * dims[1]));
+        double p[3], g[3];
+        p[0] = lo[0] + i * ((hi[0] - lo[0]) / (double)(dims[0] - 1));
+        p[1] = lo[1] + j * ((hi[1] - lo[1]) / (double)(dims[1] - 1));
+        p[2] = lo[2] + k * ((hi[2] - lo[2]) / (double)(dims[2] - 1));
+        double phi = or_sdf_mesh(V, F, nf, p, g);
+        if (fp16) ((uint16_t*)out)[idx] = or_double_to_half(phi);
+        else ((float*)out)[idx] = (float)phi;
+    }
+}
+
+/* ======================================================================== */
+/* Sensor formulas                                                           */
+/* ======================================================================== */
+
+/* ContactProbe, Eq. 3: on above eta_on, stays on above eta_off */
+int or_schmitt(int prev, double d, double eta_on, double eta_off) {
+    return (d > eta_on) || (prev && d > eta_off);
+}
+
+/* KinematicTaxel, Eqs. 7-9 in the sensor-link frame, with the Coulomb clamp
+   on the tangential term: f_t = -k_t v_t min(1, mu |f_n| / (k_t |v_t|)).
+   dw_dot_m is (omega_C - omega_L) . m.  d > 0 is required. */
+void or_taxel_force(const or_params* P, double k, double mu, double d, const double x[3],
+                    const double mbar[3], const double vrel[3], const double dw_dot_m,
+                    double f[3], double tau[3]) {
+    double s = pow(d, P->alpha);
+    double vn_s = dot3(vrel, mbar);
+    double vn[3], vt[3], fn[3], ft[3];
+    for (int a = 0; a < 3; ++a) { vn[a] = vn_s * mbar[a]; vt[a] = vrel[a] - vn[a]; }
+    for (int a = 0; a < 3; ++a) fn[a] = k * s * mbar[a] + P->c * s * vn[a];
+    double vt_n = norm3(vt);
+    double scale = 1.0;
+    if (mu >= 0.0 && P->k_t * vt_n > 0.0) {
+        double lim = mu * norm3(fn) / (P->k_t * vt_n);
+        if (lim < 1.0) scale = lim;
+    }
+    for (int a = 0; a < 3; ++a) { ft[a] = -P->k_t * vt[a] * scale; f[a] = fn[a] + ft[a]; }
+    double xf[3];
+    cross3(x, f, xf);
+    for (int a = 0; a < 3; ++a) tau[a] = xf[a] - P->k_omega * dw_dot_m * mbar[a];
+}
+
+/* L1-normalised 3x3 Gaussian of standard deviation sigma (lattice steps),
+   w[(di+1)*3 + (dj+1)] for row offset di and column offset dj */
+void or_crosstalk_weights(double sigma, double w[9]) {
+    double s = 0.0;
+    for (int di = -1; di <= 1; ++di)
+        for (int dj = -1; dj <= 1; ++dj) {
+            double e = exp(-(double)(di * di + dj * dj) / (2.0 * sigma * sigma));
+            w[(di + 1) * 3 + (dj + 1)] = e;
+            s += e;
+        }
+    for (int i = 0; i < 9; ++i) w[i] /= s;
+}
+
+static int group_gain_on(const or_noise_group* g) { return !(g->gain_lo == 1.0 && g->gain_hi == 1.0); }
+
+/* ======================================================================== */
+/* Reset: dead mask from the episode draw; state cleared (x_{-1}=0, xi=0,   */
+/* drift 0, Schmitt off).                                                    */
+/* ======================================================================== */
+void or_reset(const or_scene* S, const uint8_t* env_mask, uint32_t episode, or_state* st) {
+    int64_t T = S->taxel_offsets[S->n_envs];
+    for (int32_t e = 0; e < S->n_envs; ++e) {
+        if (env_mask && !env_mask[e]) continue;
+        st->episode[e] = episode;
+        for (int64_t i = S->taxel_offsets[e]; i < S->taxel_offsets[e + 1]; ++i) {
+            uint64_t gid = (uint64_t)(S->taxel_gid0[e] + (i - S->taxel_offsets[e]));
+            uint32_t w[4];
+            philox_draw(S->params.seed, gid, episode, TAG_EPISODE, w);
+            int dead = S->R[i] > 0.0f && bernoulli(w[0], S->params.p_dead);
+            st->flags[i] = (uint8_t)(dead ? 2 : 0);
+            for (int ch = 0; ch < OR_NCH; ++ch) {
+                st->hyst_prev[(size_t)ch * T + i] = 0.0;
+                st->hyst_xi[(size_t)ch * T + i] = 0.0;
+                st->drift[(size_t)ch * T + i] = 0.0;
+            }
+        }
+    }
+}
+
+/* one noise group applied to one channel value after the clean reading:
+   gain and hysteresis (Eqs. 27, 29-30).  Updates the hysteresis state. */
+static double gain_hysteresis(const or_noise_group* g, double dt, double gain, double clean,
+                              double* prev, double* xi) {
+    double x = gain * clean;
+    if (g->beta == 0.0) return x;
+    double a = exp(-dt / g->tau);
+    double xi_t = a * (*xi) + (x - *prev);
+    *xi = xi_t;
+    *prev = x;
+    return x + g->beta * xi_t;
+}
+
+/* base noise (Eq. 25) then dead override (Eq. 28): + b + n_t + d_t,
+   quantise, stuck value when dead */
+static double base_noise(const or_noise_group* g, double z, double white_n, double drift_n,
+                         double* drift, int dead, double stuck_u) {
+    if (g->sigma_rw != 0.0) *drift += g->sigma_rw * drift_n;
+    double y = z + g->bias + g->sigma_white * white_n + (g->sigma_rw != 0.0 ? *drift : 0.0);
+    if (g->quant > 0.0) y = g->quant * nearbyint(y / g->quant);
+    if (dead) y = g->stuck_lo + (g->stuck_hi - g->stuck_lo) * stuck_u;
+    return y;
+}
+
+/* ======================================================================== */
+/* One step of the whole sensor pipeline for every env of the (sub)scene.   */
+/* ======================================================================== */
+static void env_step(const or_scene* S, const or_inputs* in, or_state* st, or_outputs* out, int32_t e) {
+    const or_params* P = &S->params;
+    const int32_t L = S->max_links;
+    const int64_t T = S->taxel_offsets[S->n_envs];
+    const int64_t t0 = S->taxel_offsets[e], t1 = S->taxel_offsets[e + 1];
+    const int64_t n = t1 - t0;
+
+    double k = P->k, mu = P->mu, scale = 1.0;
+    if (in->env_params) {
+        mu = in->env_params[3 * e]; k = in->env_params[3 * e + 1]; scale = in->env_params[3 * e + 2];
+    }
+    const or_object* obj = &S->objects[in->obj_id[e]];
+
+    /* object pose and velocity */
+    double pC0[3], qC0[4], vC[3], wC[3], pC[3], RC[9];
+    for (int a = 0; a < 3; ++a) pC0[a] = in->obj_pose[7 * e + a];
+    for (int a = 0; a < 4; ++a) qC0[a] = in->obj_pose[7 * e + 3 + a];
+    for (int a = 0; a < 3; ++a) { vC[a] = in->obj_vel[6 * e + a]; wC[a] = in->obj_vel[6 * e + 3 + a]; }
+    or_advance_pose(pC0, qC0, vC, wC, in->pose_dt, pC, RC);
+
+    /* per-taxel scratch in clean order */
+    double* hx = (double*)calloc((size_t)n * 6, sizeof(double)); /* x~ of force/torque after hysteresis */
+    double* fclean = (double*)calloc((size_t)n * 6, sizeof(double));
+    int* active = (int*)calloc((size_t)n, sizeof(int));
+
+    uint32_t episode = st->episode[e];
+    int64_t j = t0;
+    for (int32_t l = 0; l < L; ++l) {
+        int32_t nl = S->link_rows[e * L + l] * S->link_cols[e * L + l];
+        if (nl == 0) continue;
+        const float* lp = in->link_pose + ((size_t)e * L + l) * 7;
+        const float* lv = in->link_vel + ((size_t)e * L + l) * 6;
+        double pL0[3], qL0[4], vL[3], wL[3], pL[3], RL[9];
+        for (int a = 0; a < 3; ++a) pL0[a] = lp[a];
+        for (int a = 0; a < 4; ++a) qL0[a] = lp[3 + a];
+        for (int a = 0; a < 3; ++a) { vL[a] = lv[a]; wL[a] = lv[3 + a]; }
+        or_advance_pose(pL0, qL0, vL, wL, in->pose_dt, pL, RL);
+
+        for (int32_t m_ = 0; m_ < nl; ++m_, ++j) {
+            int64_t jl = j - t0;
+            double R = S->R[j];
+            if (!(R > 0.0)) continue; /* inactive filler: every output is zero */
+            active[jl] = 1;
+            uint64_t gid = (uint64_t)(S->taxel_gid0[e] + jl);
+            double x[3] = {S->x[j], S->y[j], S->z[j]};
+            /* Eq. 1: world position of the probe */
+            double q[3];
+            matvec(RL, x, q);
+            for (int a = 0; a < 3; ++a) q[a] += pL[a];
+            /* object frame, scaled: q^ = R_C^T (q - p_C) / s */
+            double dq[3], qh[3], go[3], m[3], mbar[3];
+            sub3(q, pC, dq);
+            matTvec(RC, dq, qh);
+            for (int a = 0; a < 3; ++a) qh[a] /= scale;
+            double phi = scale * or_sdf_object(obj, qh, go);
+            matvec(RC, go, m);          /* world normal */
+            matTvec(RL, m, mbar);       /* link-frame normal */
+            /* Eq. 2 */
+            double d = R - phi;
+            if (d < 0.0) d = 0.0;
+            out->dist[j] = phi - R;
+            /* Eq. 3 */
+            int prev = st->flags[j] & 1;
+            int y = or_schmitt(prev, d, P->eta_on, P->eta_off);
+            st->flags[j] = (uint8_t)((st->flags[j] & ~1u) | (unsigned)y);
+            int dead = (st->flags[j] >> 1) & 1;
+            out->contact_clean[j] = (uint8_t)y;
+            out->contact_noisy[j] = (uint8_t)(y && !dead);
+            out->depth_clean[j] = d;
+
+            double f[3] = {0, 0, 0}, tau[3] = {0, 0, 0};
+            if (d > 0.0) {
+                /* Eqs. 4-6: point velocities and link-frame relative velocity */
+                double rC[3], rL[3], vCq[3], vLq[3], tmp[3], vrel[3];
+                sub3(q, pC, rC); sub3(q, pL, rL);
+                cross3(wC, rC, tmp);
+                for (int a = 0; a < 3; ++a) vCq[a] = vC[a] + tmp[a];
+                cross3(wL, rL, tmp);
+                for (int a = 0; a < 3; ++a) vLq[a] = vL[a] + tmp[a];
+                sub3(vCq, vLq, tmp);
+                matTvec(RL, tmp, vrel);
+                double dw[3];
+                sub3(wC, wL, dw);
+                or_taxel_force(P, k, mu, d, x, mbar, vrel, dot3(dw, m), f, tau);
+            }
+            for (int a = 0; a < 3; ++a) { fclean[jl * 6 + a] = f[a]; fclean[jl * 6 + 3 + a] = tau[a]; }
+            for (int a = 0; a < 3; ++a) { out->ft_clean[(size_t)a * T + j] = f[a]; out->ft_clean[(size_t)(3 + a) * T + j] = tau[a]; }
+
+            /* noise: per-probe gains for this episode */
+            uint32_t we[4];
+            philox_draw(P->seed, gid, episode, TAG_EPISODE, we);
+            double gain_d = group_gain_on(&P->depth) ? P->depth.gain_lo + (P->depth.gain_hi - P->depth.gain_lo) * or_uniform(we[1]) : 1.0;
+            double gain_f = group_gain_on(&P->ft) ? P->ft.gain_lo + (P->ft.gain_hi - P->ft.gain_lo) * or_uniform(we[2]) : 1.0;
+            /* depth: gain, hysteresis, base noise, dead */
+            double hd = gain_hysteresis(&P->depth, P->dt, gain_d, d, &st->hyst_prev[j], &st->hyst_xi[j]);
+            double zs[4];
+            philox_normals(P->seed, gid, in->step, TAG_SCALAR, zs);
+            uint32_t wst[4];
+            philox_draw(P->seed, gid, episode, TAG_STUCK, wst);
+            out->depth_noisy[j] = base_noise(&P->depth, hd, zs[1], zs[0], &st->drift[j], dead, or_uniform(wst[0]));
+            /* force/torque: gain and hysteresis now, crosstalk after the link */
+            for (int c = 0; c < 6; ++c) {
+                size_t si = (size_t)(1 + c) * T + j;
+                hx[jl * 6 + c] = gain_hysteresis(&P->ft, P->dt, gain_f, fclean[jl * 6 + c], &st->hyst_prev[si], &st->hyst_xi[si]);
+            }
+        }
+    }
+
+    /* Eq. 31: 3x3 crosstalk on each link lattice, then base noise and dead */
+    double W[9];
+    or_crosstalk_weights(P->xt_sigma, W);
+    int64_t lbase = 0;
+    for (int32_t l = 0; l < L; ++l) {
+        int32_t rows = S->link_rows[e * L + l], cols = S->link_cols[e * L + l];
+        int wrap = S->link_wrap[e * L + l];
+        int32_t nl = rows * cols;
+        if (nl == 0) continue;
+        double Fc[3] = {0, 0, 0}, Tc[3] = {0, 0, 0}, Fn[3] = {0, 0, 0}, Tn[3] = {0, 0, 0};
+        double Ac[3] = {0, 0, 0}, An[3] = {0, 0, 0};
+        int32_t cnt_c = 0, cnt_n = 0;
+        for (int32_t r = 0; r < rows; ++r) {
+            for (int32_t cc = 0; cc < cols; ++cc) {
+                int64_t jl = lbase + (int64_t)r * cols + cc;
+                int64_t jg = t0 + jl;
+                if (!active[jl]) {
+                    out->depth_noisy[jg] = 0.0; out->dist[jg] = 0.0;
+                    out->depth_clean[jg] = 0.0;
+                    out->contact_clean[jg] = 0; out->contact_noisy[jg] = 0;
+                    for (int c = 0; c < 6; ++c) { out->ft_clean[(size_t)c * T + jg] = 0.0; out->ft_noisy[(size_t)c * T + jg] = 0.0; }
+                    continue;
+                }
+                uint64_t gid = (uint64_t)(S->taxel_gid0[e] + jl);
+                double z[6];
+                for (int c = 0; c < 6; ++c) {
+                    double v = hx[jl * 6 + c];
+                    if (P->chi != 0.0) {
+                        double conv = 0.0;
+                        for (int di = -1; di <= 1; ++di) {
+                            int32_t rr = r + di;
+                            if (rr < 0 || rr >= rows) continue;
+                            for (int dj = -1; dj <= 1; ++dj) {
+                                int32_t c2 = cc + dj;
+                                if (wrap) c2 = (c2 + cols) % cols;
+                                else if (c2 < 0 || c2 >= cols) continue;
+                                conv += W[(di + 1) * 3 + (dj + 1)] * hx[(lbase + (int64_t)rr * cols + c2) * 6 + c];
+                            }
+                        }
+                        v = (1.0 - P->chi) * v + P->chi * conv;
+                    }
+                    z[c] = v;
+                }
+                double nA[4], nB[4], nC[4];
+                philox_normals(P->seed, gid, in->step, TAG_FT_A, nA);
+                philox_normals(P->seed, gid, in->step, TAG_FT_B, nB);
+                philox_normals(P->seed, gid, in->step, TAG_FT_C, nC);
+                double drift_n[6] = {nA[0], nA[1], nA[2], nA[3], nB[0], nB[1]};
+                double white_n[6] = {nB[2], nB[3], nC[0], nC[1], nC[2], nC[3]};
+                uint32_t wst[4];
+                philox_draw(P->seed, gid, st->episode[e], TAG_STUCK, wst);
+                int dead = (st->flags[jg] >> 1) & 1;
+                for (int c = 0; c < 6; ++c) {
+                    size_t si = (size_t)(1 + c) * T + jg;
+                    out->ft_noisy[(size_t)c * T + jg] = base_noise(&P->ft, z[c], white_n[c], drift_n[c], &st->drift[si], dead, or_uniform(wst[1]));
+                }
+                /* per-link sums (clean and noisy) and agg_force (Eq. 32) */
+                for (int a = 0; a < 3; ++a) {
+                    Fc[a] += out->ft_clean[(size_t)a * T + jg];
+                    Tc[a] += out->ft_clean[(size_t)(3 + a) * T + jg];
+                    Fn[a] += out->ft_noisy[(size_t)a * T + jg];
+                    Tn[a] += out->ft_noisy[(size_t)(3 + a) * T + jg];
+                }
+                double nrm[3] = {S->nx[jg], S->ny[jg], S->nz[jg]};
+                for (int a = 0; a < 3; ++a) {
+                    Ac[a] += out->depth_clean[jg] * nrm[a];
+                    An[a] += out->depth_noisy[jg] * nrm[a];
+                }
+                cnt_c += out->contact_clean[jg];
+                cnt_n += out->contact_noisy[jg];
+            }
+        }
+        double* rec = out->link_sums + ((size_t)e * L + l) * OR_LINK_REC;
+        for (int a = 0; a < 3; ++a) {
+            rec[a] = Fc[a]; rec[3 + a] = Tc[a]; rec[6 + a] = Fn[a]; rec[9 + a] = Tn[a];
+            /* 1e4 * P_ZYX: reversed axis order */
+            rec[12 + a] = 1e4 * Ac[2 - a];
+            rec[15 + a] = 1e4 * An[2 - a];
+        }
+        out->link_counts[((size_t)e * L + l) * 2] = cnt_c;
+        out->link_counts[((size_t)e * L + l) * 2 + 1] = cnt_n;
+        lbase += nl;
+    }
+    /* absent links: zero records */
+    for (int32_t l = 0; l < L; ++l) {
+        if (S->link_rows[e * L + l] * S->link_cols[e * L + l] != 0) continue;
+        double* rec = out->link_sums + ((size_t)e * L + l) * OR_LINK_REC;
+        for (int a = 0; a < OR_LINK_REC; ++a) rec[a] = 0.0;
+        out->link_counts[((size_t)e * L + l) * 2] = 0;
+        out->link_counts[((size_t)e * L + l) * 2 + 1] = 0;
+    }
+    free(hx); free(fclean); free(active);
+}
+
+int or_step(const or_scene* S, const or_inputs* in, or_state* st, or_outputs* out, int32_t threads) {
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#else
+    (void)threads;
+#endif
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t e = 0; e < S->n_envs; ++e) env_step(S, in, st, out, e);
+    return 0;
+}

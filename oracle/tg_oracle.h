@@ -1,0 +1,150 @@
+/*
+ * tg_oracle.h -- plain, slow FP64 CPU oracle for the tactile contact query
+ * and noise model of "Tactile Genesis" (arxiv 2606.22332), Appendix A.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library.  It shares
+ * no code with the CUDA path (no headers, helpers, tables or constants) and
+ * never reads anything the CUDA path produced.
+ *
+ * Everything is double precision.  Inputs that the product takes as FP32
+ * (poses, taxel geometry, grid values, mesh vertices) are read as float and
+ * widened exactly; FP16 grid values are widened exactly from their bits.
+ *
+ * Conventions: SI units; quaternions (w, x, y, z); rotation matrices are
+ * row-major 3x3; per-taxel multi-channel arrays are channel-major
+ * (array[c * T + i]).
+ */
+#ifndef TG_ORACLE_H
+#define TG_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- object kinds -------------------------------------------------------- */
+enum { OR_SPHERE = 0, OR_BOX = 1, OR_PLANE = 2, OR_MESH = 3, OR_GRID = 4 };
+
+typedef struct {
+    int32_t kind;
+    double radius;            /* OR_SPHERE */
+    double half[3];           /* OR_BOX half extents */
+    int32_t n_verts, n_faces; /* OR_MESH */
+    const float* verts;       /* [n_verts][3] object frame */
+    const int32_t* faces;     /* [n_faces][3], outward (counter-clockwise) */
+    int32_t dims[3];          /* OR_GRID nodes per axis (x, y, z) */
+    double lo[3], hi[3];      /* OR_GRID box corners, object frame */
+    int32_t fp16;             /* OR_GRID: 1 = values are binary16 bits */
+    const void* values;       /* OR_GRID values [z][y][x] */
+} or_object;
+
+/* ---- noise knobs of one sensor group (Appendix A, "Sensor Noise Model") -- */
+typedef struct {
+    double gain_lo, gain_hi;  /* per-probe gain range drawn at reset (1,1 = off) */
+    double beta, tau;         /* viscoelastic hysteresis (beta = 0: off) */
+    double bias;              /* constant bias b */
+    double sigma_white;       /* white noise sigma */
+    double sigma_rw;          /* random-walk drift sigma per step */
+    double quant;             /* quantisation step q (0 = off) */
+    double stuck_lo, stuck_hi;/* dead-taxel stuck readout range */
+} or_noise_group;
+
+typedef struct {
+    /* contact model (KinematicTaxel, Eqs. 4-9, plus the Coulomb clamp) */
+    double k, c, alpha, k_t, k_omega;
+    double mu;                /* friction coefficient; mu < 0 means no clamp */
+    double eta_on, eta_off;   /* ContactProbe thresholds (Eq. 3) */
+    double dt;                /* simulation step (s) */
+    uint64_t seed;            /* Philox key */
+    double p_dead;            /* dead-taxel probability */
+    or_noise_group depth, ft, prox;
+    double chi, xt_sigma;     /* spatial crosstalk strength and Gaussian sigma (lattice steps) */
+} or_params;
+
+typedef struct {
+    int32_t n_envs, max_links;
+    const int64_t* taxel_offsets; /* [n_envs+1] CSR of this (sub)scene */
+    const int64_t* taxel_gid0;    /* [n_envs] global id of each env's first taxel */
+    const int32_t* env_gid;       /* [n_envs] global env index */
+    const int32_t* link_rows;     /* [n_envs*max_links] lattice rows (axial) */
+    const int32_t* link_cols;     /* [n_envs*max_links] lattice cols (around) */
+    const uint8_t* link_wrap;     /* [n_envs*max_links] 1: cols wrap around */
+    const float *x, *y, *z, *nx, *ny, *nz, *R; /* [T] link-frame probe geometry */
+    const or_object* objects;
+    int32_t n_objects;
+    or_params params;
+} or_scene;
+
+typedef struct {
+    const float* link_pose;  /* [E][L][7] p, q(w,x,y,z) at time 0 */
+    const float* link_vel;   /* [E][L][6] v, omega (world) */
+    const float* obj_pose;   /* [E][7] */
+    const float* obj_vel;    /* [E][6] */
+    const int32_t* obj_id;   /* [E] */
+    const float* env_params; /* [E][3] {mu, k, scale} or NULL */
+    double pose_dt;          /* seconds to advance every pose by its velocity */
+    uint32_t step;           /* RNG step counter */
+} or_inputs;
+
+/* channel index for per-taxel state: 0 depth, 1..6 force/torque, 7 proximity */
+#define OR_NCH 8
+
+typedef struct {
+    uint8_t* flags;     /* [T] bit0 Schmitt state, bit1 dead */
+    double* hyst_prev;  /* [OR_NCH][T] x_{t-1} */
+    double* hyst_xi;    /* [OR_NCH][T] xi_{t-1} */
+    double* drift;      /* [OR_NCH][T] d_{t-1} */
+    uint32_t* episode;  /* [E] */
+} or_state;
+
+/* per-link record: F_clean(3) T_clean(3) F_noisy(3) T_noisy(3)
+   agg_force_clean(3) agg_force_noisy(3) */
+#define OR_LINK_REC 18
+
+typedef struct {
+    uint8_t* contact_clean; uint8_t* contact_noisy;   /* [T] */
+    double* depth_clean; double* depth_noisy;         /* [T] */
+    double* dist;                                     /* [T] phi - R */
+    double* ft_clean; double* ft_noisy;               /* [6][T] */
+    double* link_sums;                                /* [E*L][OR_LINK_REC] */
+    int32_t* link_counts;                             /* [E*L][2] clean, noisy */
+} or_outputs;
+
+/* ---- primitives (exported for the pins) ------------------------------------ */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double or_uniform(uint32_t x);
+void or_box_muller(uint32_t x0, uint32_t x1, double* z0, double* z1);
+uint16_t or_double_to_half(double x);
+double or_half_to_double(uint16_t h);
+void or_quat_to_mat(const double q[4], double R[9]);
+void or_advance_pose(const double p0[3], const double q0[4], const double v[3],
+                     const double w[3], double tau, double p[3], double R[9]);
+double or_sdf_sphere(double r, const double q[3], double g[3]);
+double or_sdf_box(const double h[3], const double q[3], double g[3]);
+double or_sdf_plane(const double q[3], double g[3]);
+double or_closest_point_triangle(const double p[3], const double a[3], const double b[3],
+                                 const double c[3], double cp[3], int* region);
+double or_winding_number(const float* V, const int32_t* F, int32_t nf, const double p[3]);
+double or_sdf_mesh(const float* V, const int32_t* F, int32_t nf, const double p[3], double g[3]);
+double or_sdf_grid(const or_object* o, const double q[3], double g[3]);
+double or_sdf_object(const or_object* o, const double q[3], double g[3]);
+int or_schmitt(int prev, double d, double eta_on, double eta_off);
+void or_taxel_force(const or_params* P, double k, double mu, double d, const double x[3],
+                    const double mbar[3], const double vrel[3], const double dw_dot_m,
+                    double f[3], double tau[3]);
+void or_crosstalk_weights(double sigma, double w[9]);
+
+/* batched helpers for the pins */
+void or_sdf_object_batch(const or_object* o, const double* q, int64_t n, double* phi, double* g);
+void or_bake_grid(const float* V, const int32_t* F, int32_t nf, const int32_t dims[3],
+                  const double lo[3], const double hi[3], int32_t fp16, void* out, int32_t threads);
+
+/* ---- whole-scene operations ------------------------------------------------- */
+void or_reset(const or_scene* S, const uint8_t* env_mask, uint32_t episode, or_state* st);
+int or_step(const or_scene* S, const or_inputs* in, or_state* st, or_outputs* out, int32_t threads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

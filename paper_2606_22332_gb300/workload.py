@@ -1,0 +1,466 @@
+"""Seeded synthetic workloads for the tactile contact query.
+
+This module creates INPUT DATA only: capsule links carrying taxel lattices,
+procedural objects (spheres, convex hulls, superquadrics), poses and
+velocities, and the parameter sets.  It contains no step of the sensing
+method (no signed distance, no depth, force or noise arithmetic); both the
+CUDA path and the CPU oracle consume what it returns.
+
+The paper's own workloads (robot hands, task objects, a 10-cube scene) are
+not available, so these seeded procedural stand-ins follow the sizes the
+paper quotes (tens to thousands of taxels per hand, >16k environments).
+
+Geometry conventions: SI units, quaternions (w, x, y, z).  A link is a
+capsule centred at its frame origin with its axis along link +z; its taxels
+sit on the cylinder as a rows x cols lattice (rows along the axis, cols around
+the circumference, row-major), which is the regular lattice the spatial
+crosstalk uses.  Taxel radius R = 1 mm; R = 0 marks an inactive filler.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+DT = 1.0 / 200.0          # simulation step (200 Hz)
+TAXEL_RADIUS = 1e-3       # probe radius of an active taxel
+PAD_ARC = np.pi           # lattice arc of the batched configs: the pad half of each link
+
+
+def f32(x):
+    """Round to the nearest float32 (the precision both sides read)."""
+    return np.asarray(x, dtype=np.float32)
+
+
+# ---------------------------------------------------------------------------
+# parameters
+# ---------------------------------------------------------------------------
+def noise_group(**kw):
+    g = dict(gain_lo=1.0, gain_hi=1.0, beta=0.0, tau=0.05, bias=0.0, sigma_white=0.0,
+             sigma_rw=0.0, quant=0.0, stuck_lo=0.0, stuck_hi=0.0)
+    g.update(kw)
+    return g
+
+
+def default_params(seed: int) -> dict:
+    """Contact and noise parameters of the synthetic workloads: k = 1e4 N/m,
+    damping 5, mu = 0.8, dead rate 2 %, drift 1e-3 per step on force/torque,
+    hysteresis 0.1 (tau 0.05 s), 3x3 crosstalk 0.05."""
+    return dict(
+        k=1e4, c=5.0, alpha=1.0, k_t=2.0, k_omega=2.0, mu=0.8,
+        eta_on=5e-4, eta_off=2e-4, dt=DT, seed=int(seed), p_dead=0.02,
+        chi=0.05, xt_sigma=1.0,
+        noise=dict(
+            depth=noise_group(beta=0.1, tau=0.05),
+            ft=noise_group(beta=0.1, tau=0.05, sigma_rw=1e-3),
+            prox=noise_group(beta=0.1, tau=0.05),
+        ),
+    )
+
+
+# ---------------------------------------------------------------------------
+# rotations (random orientation generation only)
+# ---------------------------------------------------------------------------
+def random_rotation(rng) -> np.ndarray:
+    """Haar-uniform rotation matrix from the QR factorisation of a Gaussian matrix."""
+    A = rng.standard_normal((3, 3))
+    Q, Rr = np.linalg.qr(A)
+    Q = Q * np.sign(np.diag(Rr))
+    if np.linalg.det(Q) < 0:
+        Q[:, 0] = -Q[:, 0]
+    return Q
+
+
+def mat_to_quat(M: np.ndarray) -> np.ndarray:
+    """Unit quaternion (w, x, y, z) of a rotation matrix (Shepperd's branch choice)."""
+    t = np.trace(M)
+    if t > 0:
+        s = np.sqrt(t + 1.0) * 2
+        q = [0.25 * s, (M[2, 1] - M[1, 2]) / s, (M[0, 2] - M[2, 0]) / s, (M[1, 0] - M[0, 1]) / s]
+    elif M[0, 0] > M[1, 1] and M[0, 0] > M[2, 2]:
+        s = np.sqrt(1.0 + M[0, 0] - M[1, 1] - M[2, 2]) * 2
+        q = [(M[2, 1] - M[1, 2]) / s, 0.25 * s, (M[0, 1] + M[1, 0]) / s, (M[0, 2] + M[2, 0]) / s]
+    elif M[1, 1] > M[2, 2]:
+        s = np.sqrt(1.0 + M[1, 1] - M[0, 0] - M[2, 2]) * 2
+        q = [(M[0, 2] - M[2, 0]) / s, (M[0, 1] + M[1, 0]) / s, 0.25 * s, (M[1, 2] + M[2, 1]) / s]
+    else:
+        s = np.sqrt(1.0 + M[2, 2] - M[0, 0] - M[1, 1]) * 2
+        q = [(M[1, 0] - M[0, 1]) / s, (M[0, 2] + M[2, 0]) / s, (M[1, 2] + M[2, 1]) / s, 0.25 * s]
+    q = np.asarray(q)
+    return q / np.linalg.norm(q)
+
+
+def unit(v):
+    return v / np.linalg.norm(v)
+
+
+# ---------------------------------------------------------------------------
+# procedural meshes
+# ---------------------------------------------------------------------------
+def orient_outward(verts: np.ndarray, faces: np.ndarray) -> np.ndarray:
+    """Flip every face whose winding disagrees with a positive enclosed volume
+    (for convex hull faces: whose normal points towards the interior point)."""
+    c = verts.mean(axis=0)
+    a, b, cc = verts[faces[:, 0]], verts[faces[:, 1]], verts[faces[:, 2]]
+    n = np.cross(b - a, cc - a)
+    flip = np.einsum("ij,ij->i", n, a - c) < 0
+    faces = faces.copy()
+    faces[flip] = faces[flip][:, [0, 2, 1]]
+    return faces
+
+
+def subdivide(verts: np.ndarray, faces: np.ndarray):
+    """Planar 1->4 midpoint subdivision (leaves the surface unchanged)."""
+    verts = [tuple(v) for v in verts]
+    index = {}
+
+    def mid(i, j):
+        key = (min(i, j), max(i, j))
+        if key not in index:
+            index[key] = len(verts)
+            verts.append(tuple((np.asarray(verts[i]) + np.asarray(verts[j])) / 2.0))
+        return index[key]
+
+    out = []
+    for a, b, c in faces:
+        ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+        out += [(a, ab, ca), (ab, b, bc), (ca, bc, c), (ab, bc, ca)]
+    return np.asarray(verts), np.asarray(out, dtype=np.int64)
+
+
+def hull_mesh(rng, n_points: int, extent: float = 0.04, min_faces: int = 0):
+    """Convex hull of Gaussian points, scaled to `extent` along its longest
+    axis, centred on its vertex mean, subdivided until it has >= min_faces."""
+    from scipy.spatial import ConvexHull
+
+    P = rng.standard_normal((n_points, 3))
+    hull = ConvexHull(P)
+    used = np.unique(hull.simplices)
+    remap = -np.ones(n_points, np.int64)
+    remap[used] = np.arange(len(used))
+    V = P[used]
+    F = remap[hull.simplices]
+    V = V - V.mean(axis=0)
+    V = V * (extent / (V.max(axis=0) - V.min(axis=0)).max())
+    F = orient_outward(V, F)
+    while len(F) < min_faces:
+        V, F = subdivide(V, F)
+    return f32(V), F.astype(np.int32)
+
+
+def superquadric_mesh(rng, eps1: float, eps2: float, axes, n_eta: int, n_omega: int = 64):
+    """UV tessellation of a superellipsoid with exponents eps1 (latitude) and
+    eps2 (longitude) and semi-axes `axes`; 2 n_omega (n_eta - 1) faces."""
+    def spow(w, e):
+        return np.sign(w) * np.abs(w) ** e
+
+    a1, a2, a3 = axes
+    verts = [(0.0, 0.0, -a3)]
+    for i in range(1, n_eta):
+        eta = -np.pi / 2 + i * np.pi / n_eta
+        for j in range(n_omega):
+            om = -np.pi + 2 * np.pi * j / n_omega
+            ce, se = spow(np.cos(eta), eps1), spow(np.sin(eta), eps1)
+            verts.append((a1 * ce * spow(np.cos(om), eps2), a2 * ce * spow(np.sin(om), eps2), a3 * se))
+    verts.append((0.0, 0.0, a3))
+    V = np.asarray(verts)
+    north = len(V) - 1
+
+    def vid(i, j):  # ring i in 1..n_eta-1
+        return 1 + (i - 1) * n_omega + (j % n_omega)
+
+    F = []
+    for j in range(n_omega):
+        F.append((0, vid(1, j + 1), vid(1, j)))
+    for i in range(1, n_eta - 1):
+        for j in range(n_omega):
+            F.append((vid(i, j), vid(i, j + 1), vid(i + 1, j + 1)))
+            F.append((vid(i, j), vid(i + 1, j + 1), vid(i + 1, j)))
+    for j in range(n_omega):
+        F.append((north, vid(n_eta - 1, j), vid(n_eta - 1, j + 1)))
+    F = np.asarray(F, dtype=np.int64)
+    a, b, c = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    vol = np.einsum("ij,ij->i", a, np.cross(b, c)).sum() / 6.0
+    if vol < 0:
+        F = F[:, [0, 2, 1]]
+    return f32(V), F.astype(np.int32)
+
+
+# ---------------------------------------------------------------------------
+# objects
+# ---------------------------------------------------------------------------
+@dataclass
+class ObjectSpec:
+    kind: str                     # 'sphere' | 'box' | 'plane' | 'mesh' | 'grid'
+    radius: float = 0.0
+    half: tuple = (0.0, 0.0, 0.0)
+    verts: np.ndarray | None = None
+    faces: np.ndarray | None = None
+    dims: tuple | None = None     # grid nodes per axis (x, y, z)
+    lo: np.ndarray | None = None  # float32 box corners
+    hi: np.ndarray | None = None
+    fp16: bool = False
+    values: np.ndarray | None = None  # [z][y][x] float32 or binary16 bits (uint16), set by a bake
+    name: str = ""
+
+
+def grid_box(verts: np.ndarray):
+    """Per-axis box = bounding-box centre +- 0.6 x extent (a 1.2x padded box)."""
+    lo, hi = verts.min(axis=0).astype(np.float64), verts.max(axis=0).astype(np.float64)
+    c, ext = (lo + hi) / 2, hi - lo
+    return f32(c - 0.6 * ext), f32(c + 0.6 * ext)
+
+
+def make_grid_object(verts, faces, n: int, fp16: bool, name="") -> ObjectSpec:
+    lo, hi = grid_box(verts)
+    return ObjectSpec(kind="grid", verts=verts, faces=faces, dims=(n, n, n), lo=lo, hi=hi, fp16=fp16, name=name)
+
+
+def support(obj: ObjectSpec, R: np.ndarray, u: np.ndarray) -> float:
+    """Extent of the object along world direction u (the support function),
+    used only to place links near the surface."""
+    if obj.kind == "sphere":
+        return float(obj.radius)
+    if obj.kind == "box":
+        return float(np.abs(R.T @ u) @ np.asarray(obj.half))
+    return float((obj.verts.astype(np.float64) @ (R.T @ u)).max())
+
+
+# ---------------------------------------------------------------------------
+# scenes
+# ---------------------------------------------------------------------------
+@dataclass
+class Workload:
+    name: str
+    n_envs: int
+    max_links: int
+    taxel_offsets: np.ndarray       # int64 [E+1]
+    taxel_gid0: np.ndarray          # int64 [E] global id of each env's first taxel
+    env_gid: np.ndarray             # int32 [E]
+    link_rows: np.ndarray           # int32 [E*L]
+    link_cols: np.ndarray           # int32 [E*L]
+    link_wrap: np.ndarray           # uint8 [E*L]
+    x: np.ndarray; y: np.ndarray; z: np.ndarray      # float32 [T]
+    nx: np.ndarray; ny: np.ndarray; nz: np.ndarray   # float32 [T]
+    R: np.ndarray                   # float32 [T]
+    objects: list
+    obj_id: np.ndarray              # int32 [E]
+    link_pose: np.ndarray           # float32 [E, L, 7]
+    link_vel: np.ndarray            # float32 [E, L, 6]
+    obj_pose: np.ndarray            # float32 [E, 7]
+    obj_vel: np.ndarray             # float32 [E, 6]
+    params: dict
+    steps: int = 1
+    env_params: np.ndarray | None = None
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_taxels(self) -> int:
+        return int(self.taxel_offsets[-1])
+
+    @property
+    def n_active(self) -> int:
+        return int((self.R > 0).sum())
+
+    def geom(self) -> dict:
+        return {k: getattr(self, k) for k in ("taxel_offsets", "taxel_gid0", "env_gid", "link_rows", "link_cols",
+                                              "link_wrap", "x", "y", "z", "nx", "ny", "nz", "R")}
+
+    def inputs(self, step: int) -> dict:
+        """Per-step inputs: time-0 poses advanced by step * dt, RNG step counter."""
+        return dict(link_pose=self.link_pose, link_vel=self.link_vel, obj_pose=self.obj_pose,
+                    obj_vel=self.obj_vel, obj_id=self.obj_id, env_params=self.env_params,
+                    pose_dt=float(step) * self.params["dt"], step=int(step))
+
+    def subset(self, envs) -> "Workload":
+        """The same envs as a smaller scene that keeps global taxel and env ids."""
+        envs = np.asarray(envs, dtype=np.int64)
+        L = self.max_links
+        off = self.taxel_offsets
+        counts = off[envs + 1] - off[envs]
+        new_off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+        idx = np.concatenate([np.arange(off[e], off[e + 1]) for e in envs]) if len(envs) else np.zeros(0, np.int64)
+        lidx = (envs[:, None] * L + np.arange(L)[None, :]).reshape(-1)
+        sub = Workload(
+            name=self.name + "[subset]", n_envs=len(envs), max_links=L, taxel_offsets=new_off,
+            taxel_gid0=self.taxel_gid0[envs].copy(), env_gid=self.env_gid[envs].copy(),
+            link_rows=self.link_rows[lidx].copy(), link_cols=self.link_cols[lidx].copy(),
+            link_wrap=self.link_wrap[lidx].copy(),
+            x=self.x[idx], y=self.y[idx], z=self.z[idx], nx=self.nx[idx], ny=self.ny[idx], nz=self.nz[idx],
+            R=self.R[idx], objects=self.objects, obj_id=self.obj_id[envs].copy(),
+            link_pose=self.link_pose[envs].copy(), link_vel=self.link_vel[envs].copy(),
+            obj_pose=self.obj_pose[envs].copy(), obj_vel=self.obj_vel[envs].copy(), params=self.params,
+            steps=self.steps, env_params=None if self.env_params is None else self.env_params[envs].copy(),
+            meta=dict(self.meta),
+        )
+        return sub
+
+
+def capsule_lattice(rows: int, cols: int, radius: float, length: float, n_active: int, arc: float = 2 * np.pi):
+    """Taxels on the cylinder of a capsule (axis link +z), rows along the
+    axis and cols around an arc centred on link +x (the full circumference
+    when arc = 2 pi); the slots past n_active are R = 0 fillers."""
+    r = np.arange(rows)[:, None] * np.ones((1, cols))
+    c = np.ones((rows, 1)) * np.arange(cols)[None, :]
+    if arc >= 2 * np.pi:
+        th = 2 * np.pi * c / cols
+    else:
+        th = -arc / 2 + arc * (c + 0.5) / cols
+    zz = -length / 2 + (r + 0.5) * length / rows
+    x = radius * np.cos(th); y = radius * np.sin(th)
+    nx = np.cos(th); ny = np.sin(th); nz = np.zeros_like(th)
+    Rr = np.full(rows * cols, TAXEL_RADIUS)
+    Rr[n_active:] = 0.0
+    return [a.reshape(-1) for a in (x, y, zz, nx, ny, nz)] + [Rr]
+
+
+def _assemble(name, rng, objects, env_obj, env_lattices, params, steps, press_frac=(0.5, 1.0),
+              press_depth=(0.0, 2e-3), gap=(2e-3, 2e-2), max_links=None, arc=2 * np.pi):
+    """Place every env's links around its object and stack the arrays.
+
+    env_lattices[e] is a list of (rows, cols, n_active) per link.  Each link is
+    a capsule (radius 8-12 mm, cylinder 20-45 mm) whose lattice arc faces the
+    object and whose side is pressed into the object's support plane by
+    U(press_depth) with probability U(press_frac) per env, otherwise held off
+    by U(gap)."""
+    E = len(env_lattices)
+    L = max_links or max(len(lat) for lat in env_lattices)
+    xs, ys, zs, nxs, nys, nzs, Rs = ([] for _ in range(7))
+    rows = np.zeros(E * L, np.int32); cols = np.zeros(E * L, np.int32); wrap = np.zeros(E * L, np.uint8)
+    link_pose = np.zeros((E, L, 7), np.float32); link_pose[:, :, 3] = 1.0
+    link_vel = np.zeros((E, L, 6), np.float32)
+    obj_pose = np.zeros((E, 7), np.float32); obj_vel = np.zeros((E, 6), np.float32)
+    offsets = [0]
+    for e in range(E):
+        obj = objects[env_obj[e]]
+        RC = random_rotation(rng)
+        pC = rng.normal(0.0, 0.005, 3)
+        obj_pose[e, :3] = pC
+        obj_pose[e, 3:] = mat_to_quat(RC)
+        obj_vel[e, :3] = rng.normal(0.0, 0.1, 3)
+        obj_vel[e, 3:] = rng.normal(0.0, 1.0, 3)
+        pf = rng.uniform(*press_frac)
+        n_e = 0
+        for l, (rr, cc, na) in enumerate(env_lattices[e]):
+            rc = rng.uniform(8e-3, 12e-3)
+            ln = rng.uniform(20e-3, 45e-3)
+            lat = capsule_lattice(rr, cc, rc, ln, na, arc)
+            for lst, arr in zip((xs, ys, zs, nxs, nys, nzs, Rs), lat):
+                lst.append(arr)
+            rows[e * L + l], cols[e * L + l] = rr, cc
+            wrap[e * L + l] = 1 if arc >= 2 * np.pi else 0
+            n_e += rr * cc
+            u = unit(rng.standard_normal(3))
+            h = float(pC @ u) + support(obj, RC, u)
+            delta = rng.uniform(*press_depth) if rng.uniform() < pf else -rng.uniform(*gap)
+            centre = (h + rc - delta) * u
+            axis = unit(np.cross(u, rng.standard_normal(3)))
+            e1 = -u                      # lattice column 0 faces the object
+            e2 = np.cross(axis, e1)
+            RL = np.stack([e1, e2, axis], axis=1)
+            link_pose[e, l, :3] = centre
+            link_pose[e, l, 3:] = mat_to_quat(RL)
+            link_vel[e, l, :3] = rng.normal(0.0, 0.1, 3)
+            link_vel[e, l, 3:] = rng.normal(0.0, 1.0, 3)
+        offsets.append(offsets[-1] + n_e)
+    cat = lambda lst: f32(np.concatenate(lst)) if lst else np.zeros(0, np.float32)
+    off = np.asarray(offsets, np.int64)
+    return Workload(
+        name=name, n_envs=E, max_links=L, taxel_offsets=off, taxel_gid0=off[:-1].copy(),
+        env_gid=np.arange(E, dtype=np.int32), link_rows=rows, link_cols=cols, link_wrap=wrap,
+        x=cat(xs), y=cat(ys), z=cat(zs), nx=cat(nxs), ny=cat(nys), nz=cat(nzs), R=cat(Rs),
+        objects=objects, obj_id=np.asarray(env_obj, np.int32), link_pose=link_pose, link_vel=link_vel,
+        obj_pose=obj_pose, obj_vel=obj_vel, params=params, steps=steps,
+    )
+
+
+def config0(seed: int = 20260001, n_envs: int = 64, n_meshes: int = 8) -> Workload:
+    """Plain method: 16 capsule links with 200 taxels; per env a sphere
+    (r = 30 mm, analytic) or a ~2,000-face mesh (hull of 64 Gaussian points,
+    40 mm extent, subdivided twice); one step."""
+    rng = np.random.default_rng(seed)
+    objects = [ObjectSpec(kind="sphere", radius=float(f32(0.03)), name="sphere30")]
+    for i in range(n_meshes):
+        V, F = hull_mesh(rng, 64, 0.04, min_faces=1500)
+        objects.append(ObjectSpec(kind="mesh", verts=V, faces=F, name=f"hull{i}"))
+    env_obj = [0 if rng.uniform() < 0.5 else 1 + int(rng.integers(n_meshes)) for _ in range(n_envs)]
+    lat = [(3, 4, 12)] * 12 + [(2, 7, 14)] * 4
+    lattices = []
+    for _ in range(n_envs):
+        order = rng.permutation(16)
+        lattices.append([lat[i] for i in order])
+    return _assemble("config0", rng, objects, env_obj, lattices, default_params(seed), steps=1,
+                     press_frac=(0.8, 1.0), press_depth=(0.5e-3, 2e-3))
+
+
+def config1_objects(rng, n_objects: int = 8, n_grid: int = 64, fp16: bool = False, faces=(3000, 6000)):
+    """Half superquadrics (exponents U(0.3, 2)), half convex hulls of 64-256
+    points, each with a grid spec over its 1.2x padded bounding box."""
+    objs = []
+    for i in range(n_objects):
+        if i % 2 == 0:
+            e1, e2 = rng.uniform(0.3, 2.0, 2)
+            axes = rng.uniform(0.012, 0.020, 3)
+            target = rng.integers(faces[0], faces[1] + 1)
+            n_eta = max(3, int(round(target / 128.0)) + 1)
+            V, F = superquadric_mesh(rng, e1, e2, axes, n_eta=n_eta, n_omega=64)
+            name = f"superquadric{i}"
+        else:
+            V, F = hull_mesh(rng, int(rng.integers(64, 257)), 0.04, min_faces=faces[0])
+            name = f"hull{i}"
+        objs.append(make_grid_object(V, F, n_grid, fp16, name=name))
+    return objs
+
+
+def config1(seed: int = 20260002, n_envs: int = 4096, n_links: int = 20, rows: int = 5, cols: int = 10,
+            n_objects: int = 8, n_grid: int = 64, steps: int = 100) -> Workload:
+    """Batched grid path: n_envs x 20 links x 50 taxels (5 x 10), 8 objects
+    as 64^3 FP32 grids, 100 steps of constant-velocity motion."""
+    rng = np.random.default_rng(seed)
+    objects = config1_objects(rng, n_objects, n_grid, fp16=False)
+    env_obj = rng.integers(0, n_objects, n_envs)
+    lattices = [[(rows, cols, rows * cols)] * n_links for _ in range(n_envs)]
+    return _assemble("config1", rng, objects, env_obj, lattices, default_params(seed), steps=steps,
+                     arc=PAD_ARC, press_frac=(1.0, 1.0), press_depth=(0.5e-3, 2.5e-3))
+
+
+def uneven_lattices(rng, n_envs, taxels=(200, 1000), links=(10, 20), cols=10):
+    """T_e ~ U{taxels}, L_e ~ U{links}; each link's share as a lattice of
+    `cols` columns whose last row is padded with R = 0 fillers."""
+    out = []
+    for _ in range(n_envs):
+        T = int(rng.integers(taxels[0], taxels[1] + 1))
+        L = int(rng.integers(links[0], links[1] + 1))
+        base, rem = divmod(T, L)
+        lat = []
+        for l in range(L):
+            n = base + (1 if l < rem else 0)
+            c = min(cols, n)
+            r = -(-n // c)
+            lat.append((r, c, n))
+        out.append(lat)
+    return out
+
+
+def metric_run(seed: int = 20260003, n_envs: int = 20480, n_objects: int = 64, n_grid: int = 96,
+               steps: int = 200, faces=(3000, 6000)) -> Workload:
+    """Headline workload: n_envs x 20 links x 50 taxels (1,000 per env),
+    64 objects as 96^3 FP16 grids, full noise model."""
+    rng = np.random.default_rng(seed)
+    objects = config1_objects(rng, n_objects, n_grid, fp16=True, faces=faces)
+    env_obj = rng.integers(0, n_objects, n_envs)
+    lattices = [[(5, 10, 50)] * 20 for _ in range(n_envs)]
+    return _assemble("metric_run", rng, objects, env_obj, lattices, default_params(seed), steps=steps,
+                     arc=PAD_ARC, press_frac=(1.0, 1.0), press_depth=(0.5e-3, 2.5e-3))
+
+
+def config2(seed: int = 20260003, n_envs: int = 20480, n_objects: int = 64, n_grid: int = 96,
+            steps: int = 200, faces=(3000, 6000)) -> Workload:
+    """Full sensor set at scale: uneven T_e ~ U{200..1000}, L_e ~ U{10..20},
+    64 objects as 96^3 FP16 grids."""
+    rng = np.random.default_rng(seed)
+    objects = config1_objects(rng, n_objects, n_grid, fp16=True, faces=faces)
+    env_obj = rng.integers(0, n_objects, n_envs)
+    lattices = uneven_lattices(rng, n_envs)
+    return _assemble("config2", rng, objects, env_obj, lattices, default_params(seed), steps=steps, max_links=20,
+                     arc=PAD_ARC, press_frac=(1.0, 1.0), press_depth=(0.5e-3, 2.5e-3))

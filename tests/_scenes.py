@@ -1,0 +1,76 @@
+"""Small hand-built scenes and conversions shared by the tests."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+from paper_2606_22332_gb300 import workload as W
+
+
+def oracle_objects(objects):
+    out = []
+    for o in objects:
+        if o.kind == "sphere":
+            out.append(oracle.Obj.sphere(o.radius))
+        elif o.kind == "box":
+            out.append(oracle.Obj.box(o.half))
+        elif o.kind == "plane":
+            out.append(oracle.Obj.plane())
+        elif o.kind == "mesh":
+            out.append(oracle.Obj.mesh(o.verts, o.faces))
+        elif o.kind == "grid":
+            assert o.values is not None, "grid object has no baked values"
+            out.append(oracle.Obj.grid(o.values, o.lo, o.hi, fp16=o.fp16))
+        else:
+            raise ValueError(o.kind)
+    return out
+
+
+def oracle_scene(wl: W.Workload):
+    return oracle.OracleScene(wl.geom(), oracle_objects(wl.objects), wl.params)
+
+
+def pad_workload(depths, rows, cols, params=None, wrap=0, pitch=1e-3, obj=None,
+                 link_vel=(0, 0, 0, 0, 0, 0), obj_vel=(0, 0, 0, 0, 0, 0), R=1e-3, link_quat=(1, 0, 0, 0)):
+    """One env, one flat pad link over the half-space z <= 0.
+
+    The pad is a rows x cols lattice in the link's z = 0 plane with pitch
+    `pitch`, probe normals -z (facing the plane).  The link origin sits at
+    height h above the plane, so a probe at link position x is at world
+    height h + x_z; `depths` (rows x cols, or a scalar) sets each probe's
+    link-frame z so that its penetration R - phi equals the given depth.
+    """
+    depths = np.broadcast_to(np.asarray(depths, dtype=np.float64), (rows, cols))
+    h = 0.01
+    rr, cc = np.meshgrid(np.arange(rows), np.arange(cols), indexing="ij")
+    x = (cc - (cols - 1) / 2.0) * pitch
+    y = (rr - (rows - 1) / 2.0) * pitch
+    z = -(h - (R - depths))          # world height of the probe = R - depth
+    T = rows * cols
+    params = params or W.default_params(1234)
+    objs = [obj or W.ObjectSpec(kind="plane")]
+    lp = np.zeros((1, 1, 7), np.float32); lp[0, 0, 2] = h; lp[0, 0, 3:] = link_quat
+    lv = np.asarray(link_vel, np.float32).reshape(1, 1, 6)
+    op = np.zeros((1, 7), np.float32); op[0, 3] = 1.0
+    ov = np.asarray(obj_vel, np.float32).reshape(1, 6)
+    f = lambda a: W.f32(np.asarray(a).reshape(-1))
+    return W.Workload(
+        name="pad", n_envs=1, max_links=1, taxel_offsets=np.array([0, T], np.int64),
+        taxel_gid0=np.array([0], np.int64), env_gid=np.array([0], np.int32),
+        link_rows=np.array([rows], np.int32), link_cols=np.array([cols], np.int32),
+        link_wrap=np.array([wrap], np.uint8),
+        x=f(x), y=f(y), z=f(z), nx=f(np.zeros(T)), ny=f(np.zeros(T)), nz=f(-np.ones(T)),
+        R=f(np.full(T, R)), objects=objs, obj_id=np.array([0], np.int32),
+        link_pose=lp, link_vel=lv, obj_pose=op, obj_vel=ov, params=params, steps=1,
+    )
+
+
+def quiet_params(seed=1234, **over):
+    """Default parameters with every noise knob off."""
+    p = W.default_params(seed)
+    p["p_dead"] = 0.0
+    p["chi"] = 0.0
+    for g in ("depth", "ft", "prox"):
+        p["noise"][g] = W.noise_group()
+    p.update(over)
+    return p
