@@ -1,0 +1,221 @@
+/*
+ * tg.h -- C-ABI of the GB300-native tactile contact-query library.
+ *
+ * What it computes: the per-(environment, taxel) sensor read of Tactile
+ * Genesis (arxiv 2606.22332), Appendix A:
+ *   probe transform            q_j = p_L + R_L x_j, a_j = R_L n_j      (Eq. 1)
+ *   contact depth (sdf)        d_j = [R_j - phi(q_j)]_+, m_j = grad phi (Eq. 2)
+ *   contact bit (Schmitt)      on above eta_on, held above eta_off      (Eq. 3)
+ *   kinematic force/torque     f = k_n s m + c_n s v_n - k_t v_t,
+ *                              tau = x cross f - k_w ((w_C - w_L).m) m  (Eqs. 4-9)
+ *                              with the tangential part clamped to the
+ *                              Coulomb cone |f_t| <= mu |f_n|
+ *   noise model                gain, viscoelastic hysteresis, 3x3 spatial
+ *                              crosstalk, bias + white + random-walk drift,
+ *                              quantisation, dead taxels         (Eqs. 25-31)
+ *   per-link sums              sum f, sum tau (clean and noisy), contact
+ *                              counts (agg_bool), agg_force      (Eq. 32)
+ *
+ * Conventions.
+ *   - SI units.  Quaternions are (w, x, y, z); any non-zero norm is accepted
+ *     and the rotation of the normalised quaternion is used.
+ *   - Every call returns tg_status; no C++ exception crosses this boundary.
+ *     tg_last_error() holds a message for the last failing call on a scene.
+ *   - Pointers documented as "host or device" may be either; the library
+ *     tells them apart with cudaPointerGetAttributes and copies host data on
+ *     the call's stream.  Caller-owned inputs must stay valid until the
+ *     stream work they feed has completed.
+ *   - The library owns the scene's device state and outputs (cudaMalloc at
+ *     tg_create_scene, cudaFree at tg_destroy_scene).  Views returned by
+ *     tg_get_buffer stay valid until tg_destroy_scene; their contents are
+ *     those of the last completed step.
+ *   - Asynchronous device faults and the device error word (non-finite
+ *     inputs) surface at the next tg_sync().
+ *   - A scene is not thread-safe: one host thread at a time per scene.
+ *   - Per-taxel arrays are in CSR order: env e owns taxels
+ *     [taxel_offsets[e], taxel_offsets[e+1]); within an env, the taxels of
+ *     link 0 come first, each link's rows x cols lattice in row-major order.
+ *     Multi-channel per-taxel arrays are channel-major ([channel][T]).
+ */
+#ifndef TG_H
+#define TG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tg_scene tg_scene;          /* opaque, owned by the library */
+typedef void* tg_stream;                   /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    TG_OK = 0,
+    TG_ERR_INVALID_ARG = 1,   /* bad pointer, size, layout or parameter */
+    TG_ERR_OOM = 2,           /* device allocation failed */
+    TG_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+    TG_ERR_STATE = 4,         /* call out of order (e.g. step before objects) */
+    TG_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
+    TG_ERR_NUMERIC = 6,       /* non-finite values were seen in a step */
+    TG_ERR_UNSUPPORTED = 7    /* valid request this build does not implement */
+} tg_status;
+
+/* Noise knobs of one sensor group ("Sensor Noise Model", Eqs. 25-30). */
+typedef struct {
+    double gain_lo, gain_hi;   /* per-probe gain U[lo, hi] drawn at reset; (1, 1) = off */
+    double beta, tau;          /* hysteresis strength and time constant (s); beta = 0 = off */
+    double bias;               /* constant bias b */
+    double sigma_white;        /* white noise sigma */
+    double sigma_rw;           /* random-walk drift sigma per step */
+    double quant;              /* quantisation step q; 0 = off (ties to even) */
+    double stuck_lo, stuck_hi; /* dead-taxel readout U[lo, hi] drawn per episode */
+} tg_noise_group;
+
+/* Contact and noise parameters.  Doubles on the host; the kernels use FP32
+   (and compensated FP32 for the geometry of near-contact taxels). */
+typedef struct {
+    double k, c, alpha, k_t, k_omega; /* KinematicTaxel (Eqs. 8-9): k_n, c_n, alpha, k_t, k_omega */
+    double mu;                        /* Coulomb clamp coefficient; < 0 = no clamp */
+    double eta_on, eta_off;           /* ContactProbe thresholds (Eq. 3), eta_off <= eta_on */
+    double dt;                        /* simulation step in seconds (hysteresis decay) */
+    double p_dead;                    /* dead-taxel probability per episode */
+    double chi, xt_sigma;             /* crosstalk strength, Gaussian sigma in lattice steps */
+    uint64_t seed;                    /* Philox4x32-10 key */
+    tg_noise_group depth, ft, prox;   /* per sensor group */
+} tg_params;
+
+/* sensor mask bits (depth, contact and force/torque are always computed) */
+#define TG_SENSOR_DIST 0x1u           /* SurfaceDistanceProbe output phi - R */
+
+typedef struct {
+    int32_t n_envs;                   /* E >= 1 */
+    int32_t max_links;                /* L, 1..255: poses are [E][L] */
+    const int64_t* taxel_offsets;     /* host [E+1], non-decreasing, [0] = 0 */
+    const int32_t* link_rows;         /* host [E*L]; rows x cols taxels per link (0 x 0 = absent) */
+    const int32_t* link_cols;         /* host [E*L] */
+    const uint8_t* link_wrap;         /* host [E*L] or NULL: 1 = lattice columns wrap around */
+    const float *x, *y, *z;           /* host or device [T]: link-frame probe position x_j */
+    const float *nx, *ny, *nz;        /* host or device [T]: link-frame unit normal n_j */
+    const float* R;                   /* host or device [T]: probe radius; 0 = inactive filler */
+    tg_params params;
+    uint32_t sensors;                 /* TG_SENSOR_* mask */
+    int64_t taxel_gid0;               /* global id of taxel 0 in the RNG counters (sharding) */
+    int32_t env_gid0;                 /* global id of env 0 */
+} tg_scene_desc;
+
+/* Create a scene: validates the layout, copies the taxel geometry to the
+   device, allocates state and outputs, sets every env to episode 0 (dead
+   masks drawn, state zeroed).  T = taxel_offsets[E]; a link lattice may hold
+   at most tg_max_link_taxels() taxels.  Errors: TG_ERR_INVALID_ARG,
+   TG_ERR_OOM, TG_ERR_CUDA.  *out is NULL on failure. */
+tg_status tg_create_scene(const tg_scene_desc* desc, tg_scene** out);
+void tg_destroy_scene(tg_scene* scene);
+int32_t tg_max_link_taxels(void);
+
+/* Object geometry in its own frame (Appendix A, "two contact-depth
+   backends", the sdf form). */
+typedef enum {
+    TG_OBJ_SPHERE = 0,   /* radius */
+    TG_OBJ_BOX = 1,      /* half[3], centred at the origin */
+    TG_OBJ_PLANE = 2,    /* half-space z <= 0 */
+    TG_OBJ_MESH = 3,     /* closed, outward-oriented triangle mesh: exact distance, winding-number sign */
+    TG_OBJ_GRID = 4      /* sampled SDF: trilinear, node (i,j,k) at lo + (i,j,k)(hi-lo)/(dims-1) */
+} tg_object_kind;
+
+typedef struct {
+    int32_t kind;
+    float radius;                     /* SPHERE */
+    float half[3];                    /* BOX */
+    int32_t n_verts, n_faces;         /* MESH */
+    const float* verts;               /* host or device [n_verts][3] */
+    const int32_t* faces;             /* host or device [n_faces][3], indices < n_verts */
+    int32_t dims[3];                  /* GRID nodes per axis (x, y, z), each >= 2 */
+    float lo[3], hi[3];               /* GRID box, lo < hi */
+    int32_t fp16;                     /* GRID: 1 = values are IEEE binary16 */
+    const void* values;               /* GRID: host or device [dims z][dims y][dims x] */
+} tg_object_desc;
+
+/* Upload (replace) the scene's object table.  Per env, tg_step_inputs.obj_id
+   picks one object.  The library copies everything.  A query outside a grid's
+   box reads phi(clamp(q)) + |q - clamp(q)|.  Errors: TG_ERR_INVALID_ARG,
+   TG_ERR_OOM, TG_ERR_CUDA. */
+tg_status tg_upload_objects(tg_scene* scene, const tg_object_desc* objs, int32_t n);
+
+/* Start a new episode for the envs whose env_mask byte is non-zero (host or
+   device [E]; NULL = all): dead masks are redrawn from (seed, taxel id,
+   episode), hysteresis, drift and Schmitt state are zeroed.  Ordered on
+   `stream`. */
+tg_status tg_reset_envs(tg_scene* scene, const uint8_t* env_mask, uint32_t episode, tg_stream stream);
+
+/* Per-step inputs (host or device pointers, caller-owned). */
+typedef struct {
+    const float* link_pose;   /* [E][L][7] p(3), q(4) of every link at time 0 of the advance */
+    const float* link_vel;    /* [E][L][6] v(3), omega(3), world frame */
+    const float* obj_pose;    /* [E][7] */
+    const float* obj_vel;     /* [E][6] */
+    const int32_t* obj_id;    /* [E], index into the object table */
+    const float* env_params;  /* [E][3] {mu, k, scale} per env, or NULL = params.mu, params.k, 1 */
+    double pose_dt;           /* advance: p += v pose_dt, R = exp([omega] pose_dt) R */
+    uint32_t step;            /* RNG counter of this step */
+} tg_step_inputs;
+
+/* One sensor step for every env: enqueued on `stream`, asynchronous.
+   Errors: TG_ERR_STATE (no objects), TG_ERR_INVALID_ARG (NULL input),
+   TG_ERR_CUDA (launch failure). */
+tg_status tg_step_sensors(tg_scene* scene, const tg_step_inputs* in, tg_stream stream);
+
+typedef enum {
+    TG_CH_CONTACT = 0,        /* uint8 [T]: 0/1 */
+    TG_CH_DEPTH = 1,          /* float [T] */
+    TG_CH_DIST = 2,           /* float [T] (needs TG_SENSOR_DIST); clean only */
+    TG_CH_FORCE_TORQUE = 3,   /* float [6][T]: fx fy fz tx ty tz, link frame */
+    TG_CH_LINK_WRENCH = 4,    /* float [E*L][18]: F_clean T_clean F_noisy T_noisy agg_clean agg_noisy */
+    TG_CH_LINK_COUNT = 5,     /* int32 [E*L][2]: contact count clean, noisy (agg_bool = count > 2) */
+    TG_CH_STATE_FLAGS = 6     /* uint8 [T]: bit0 clean contact, bit1 dead, bit2 noisy contact */
+} tg_channel;
+
+/* Copy one output channel (clean or noisy) into dst (host or device),
+   ordered on `stream` after the last step.  dst_bytes must equal the
+   channel's size (tg_channel_bytes).  Errors: TG_ERR_INVALID_ARG. */
+tg_status tg_read_taxels(tg_scene* scene, int32_t channel, int32_t noisy, void* dst, size_t dst_bytes,
+                         tg_stream stream);
+size_t tg_channel_bytes(const tg_scene* scene, int32_t channel);
+
+/* Device view of a library-owned output buffer (no copy).  CONTACT has no
+   view: read it, or decode TG_CH_STATE_FLAGS.  Errors: TG_ERR_INVALID_ARG. */
+tg_status tg_get_buffer(tg_scene* scene, int32_t channel, int32_t noisy, void** dev_ptr, size_t* bytes);
+
+/* Wait for the scene's work on `stream` and report device-side errors
+   (TG_ERR_NUMERIC when non-finite values were seen since the last sync,
+   TG_ERR_CUDA on an asynchronous fault). */
+tg_status tg_sync(tg_scene* scene, tg_stream stream);
+const char* tg_last_error(const tg_scene* scene);
+
+/* Checkpoint: the per-taxel state (flags, hysteresis, drift) and per-env
+   episode numbers.  With buf == NULL, *size receives the needed size.
+   Philox draws are counter-based, so a restored scene replays bit-exactly.
+   Synchronous.  Errors: TG_ERR_INVALID_ARG (size mismatch). */
+tg_status tg_save_state(tg_scene* scene, void* buf, size_t* size);
+tg_status tg_load_state(tg_scene* scene, const void* buf, size_t size);
+
+/* Exact signed distance to a closed, outward-oriented triangle mesh sampled
+   at the nodes of a grid (the grid bake that turns a mesh into a
+   TG_OBJ_GRID): unsigned distance by closest point over every face, negative
+   where the generalised winding number exceeds 1/2.  Computed in FP32 with a
+   compensated re-evaluation of the nearest faces, then rounded once to float
+   or binary16.  out: device [dims z][dims y][dims x].  Stateless,
+   asynchronous on `stream`.  Errors: TG_ERR_INVALID_ARG, TG_ERR_CUDA. */
+tg_status tg_bake_grid(const float* verts, int32_t n_verts, const int32_t* faces, int32_t n_faces,
+                       const int32_t dims[3], const float lo[3], const float hi[3], int32_t fp16,
+                       void* out, tg_stream stream);
+
+/* The same exact mesh SDF at n arbitrary points (device [n][3]); phi device
+   [n]; grad device [n][3] (unit gradient) or NULL. */
+tg_status tg_mesh_sdf(const float* verts, int32_t n_verts, const int32_t* faces, int32_t n_faces,
+                      const float* points, int64_t n, float* phi, float* grad, tg_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TG_H */

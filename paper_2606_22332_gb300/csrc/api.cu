@@ -1,0 +1,698 @@
+// api.cu -- host side of the C-ABI declared in include/tg.h: argument
+// validation, scene layout (CSR work items, link lattices), device
+// allocation, staging of host inputs, launches, reads and checkpoints.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace tg;
+
+struct tg_scene {
+    int E = 0, L = 0;
+    int64_t T = 0;
+    uint32_t sensors = 0;
+    int64_t gid0 = 0;
+    int env_gid0 = 0;
+    tg_params params{};
+    ParamsDev P{};
+    std::vector<Item> items_h;
+    int n_items = 0;
+    // device: geometry and layout
+    float *x = nullptr, *y = nullptr, *z = nullptr, *nx = nullptr, *ny = nullptr, *nz = nullptr, *R = nullptr;
+    Item* items = nullptr;
+    LinkLattice* lattice = nullptr;
+    // objects
+    ObjDev* objects = nullptr;
+    int n_objects = 0;
+    std::vector<void*> obj_bufs;
+    // state
+    uint8_t* flags = nullptr;
+    float *hyst_prev = nullptr, *hyst_xi = nullptr, *drift = nullptr;
+    uint32_t* episode = nullptr;
+    // outputs
+    float *depth_clean = nullptr, *depth_noisy = nullptr, *dist = nullptr;
+    float *ft_clean = nullptr, *ft_noisy = nullptr, *link_out = nullptr;
+    int32_t* link_count = nullptr;
+    unsigned* err = nullptr;
+    float* link_rec = nullptr;
+    // staging of host inputs
+    float *s_link_pose = nullptr, *s_link_vel = nullptr, *s_obj_pose = nullptr, *s_obj_vel = nullptr;
+    float* s_env_params = nullptr;
+    int32_t* s_obj_id = nullptr;
+    uint8_t* s_mask = nullptr;
+    uint8_t* s_contact = nullptr;
+    std::string last_error;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+tg_status fail(tg_scene* s, tg_status st, const std::string& msg) {
+    if (s) s->last_error = msg;
+    else g_create_error = msg;
+    return st;
+}
+
+tg_status cuda_fail(tg_scene* s, cudaError_t e, const char* what) {
+    return fail(s, e == cudaErrorMemoryAllocation ? TG_ERR_OOM : TG_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(scene, call)                                                 \
+    do {                                                                \
+        cudaError_t _e = (call);                                        \
+        if (_e != cudaSuccess) return cuda_fail((scene), _e, #call);    \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+void dfree(void* p) {
+    if (p) cudaFree(p);
+}
+
+bool finite(double v) { return std::isfinite(v); }
+
+NoiseDev make_group(const tg_noise_group& g, double dt) {
+    NoiseDev n{};
+    n.gain_lo = (float)g.gain_lo;
+    n.gain_span = (float)(g.gain_hi - g.gain_lo);
+    n.gain_on = !(g.gain_lo == 1.0 && g.gain_hi == 1.0);
+    n.beta = (float)g.beta;
+    n.decay = g.tau > 0.0 ? (float)std::exp(-dt / g.tau) : 0.0f;
+    n.bias = (float)g.bias;
+    n.sigma_white = (float)g.sigma_white;
+    n.sigma_rw = (float)g.sigma_rw;
+    n.quant = (float)g.quant;
+    n.stuck_lo = (float)g.stuck_lo;
+    n.stuck_span = (float)(g.stuck_hi - g.stuck_lo);
+    return n;
+}
+
+const char* check_group(const tg_noise_group& g) {
+    const double v[] = {g.gain_lo, g.gain_hi, g.beta, g.tau, g.bias, g.sigma_white, g.sigma_rw, g.quant,
+                        g.stuck_lo, g.stuck_hi};
+    for (double x : v)
+        if (!finite(x)) return "non-finite noise parameter";
+    if (g.gain_hi < g.gain_lo || g.stuck_hi < g.stuck_lo) return "noise range with hi < lo";
+    if (g.beta != 0.0 && !(g.tau > 0.0)) return "hysteresis needs tau > 0";
+    if (g.sigma_white < 0 || g.sigma_rw < 0 || g.quant < 0) return "negative noise sigma or quantisation step";
+    return nullptr;
+}
+
+const char* make_params(const tg_params& p, ParamsDev* out) {
+    const double v[] = {p.k, p.c, p.alpha, p.k_t, p.k_omega, p.mu, p.eta_on, p.eta_off, p.dt, p.p_dead, p.chi, p.xt_sigma};
+    for (double x : v)
+        if (!finite(x)) return "non-finite parameter";
+    if (p.eta_off > p.eta_on) return "eta_off must not exceed eta_on";
+    if (!(p.dt > 0.0)) return "dt must be positive";
+    if (p.p_dead < 0.0 || p.p_dead > 1.0) return "p_dead outside [0, 1]";
+    if (!(p.alpha > 0.0)) return "alpha must be positive";
+    if (p.chi != 0.0 && !(p.xt_sigma > 0.0)) return "crosstalk needs xt_sigma > 0";
+    for (const tg_noise_group* g : {&p.depth, &p.ft, &p.prox})
+        if (const char* m = check_group(*g)) return m;
+    ParamsDev d{};
+    d.k = (float)p.k;
+    d.c = (float)p.c;
+    d.alpha = (float)p.alpha;
+    d.k_t = (float)p.k_t;
+    d.k_omega = (float)p.k_omega;
+    d.mu = (float)p.mu;
+    d.eta_on_hi = (float)p.eta_on;
+    d.eta_on_lo = (float)(p.eta_on - (double)d.eta_on_hi);
+    d.eta_off_hi = (float)p.eta_off;
+    d.eta_off_lo = (float)(p.eta_off - (double)d.eta_off_hi);
+    d.dead_threshold24 = (uint32_t)std::nearbyint(p.p_dead * 16777216.0);
+    d.chi = (float)p.chi;
+    double w[9], sum = 0.0;
+    for (int di = -1; di <= 1; ++di)
+        for (int dj = -1; dj <= 1; ++dj) {
+            double s = p.xt_sigma > 0.0 ? p.xt_sigma : 1.0;
+            w[(di + 1) * 3 + dj + 1] = std::exp(-(double)(di * di + dj * dj) / (2.0 * s * s));
+            sum += w[(di + 1) * 3 + dj + 1];
+        }
+    for (int i = 0; i < 9; ++i) d.xt_w[i] = (float)(w[i] / sum);
+    d.seed = p.seed;
+    d.depth = make_group(p.depth, p.dt);
+    d.ft = make_group(p.ft, p.dt);
+    d.prox = make_group(p.prox, p.dt);
+    *out = d;
+    return nullptr;
+}
+
+StepArgs step_args(tg_scene* s) {
+    StepArgs a{};
+    a.x = s->x; a.y = s->y; a.z = s->z; a.nx = s->nx; a.ny = s->ny; a.nz = s->nz; a.R = s->R;
+    a.items = s->items;
+    a.lattice = s->lattice;
+    a.objects = s->objects;
+    a.n_objects = s->n_objects;
+    a.n_envs = s->E;
+    a.max_links = s->L;
+    a.n_taxels = s->T;
+    a.gid0 = s->gid0;
+    a.sensors = s->sensors;
+    a.P = s->P;
+    a.link_rec = s->link_rec;
+    a.flags = s->flags;
+    a.hyst_prev = s->hyst_prev;
+    a.hyst_xi = s->hyst_xi;
+    a.drift = s->drift;
+    a.episode = s->episode;
+    a.depth_clean = s->depth_clean;
+    a.depth_noisy = s->depth_noisy;
+    a.dist = s->dist;
+    a.ft_clean = s->ft_clean;
+    a.ft_noisy = s->ft_noisy;
+    a.link_out = s->link_out;
+    a.link_count = s->link_count;
+    a.err = s->err;
+    return a;
+}
+
+// device copy of a host-or-device input: returns the pointer the kernels read
+template <class T>
+cudaError_t stage(const T* src, T* staging, size_t count, cudaStream_t st, const T** out) {
+    if (is_device_ptr(src)) {
+        *out = src;
+        return cudaSuccess;
+    }
+    *out = staging;
+    return cudaMemcpyAsync(staging, src, count * sizeof(T), cudaMemcpyHostToDevice, st);
+}
+
+void free_objects(tg_scene* s) {
+    for (void* p : s->obj_bufs) dfree(p);
+    s->obj_bufs.clear();
+    dfree(s->objects);
+    s->objects = nullptr;
+    s->n_objects = 0;
+}
+
+// host copy of a host-or-device array
+template <class T>
+bool host_copy(const T* src, size_t count, std::vector<T>* out) {
+    out->resize(count);
+    if (count == 0) return true;
+    return cudaMemcpy(out->data(), src, count * sizeof(T), cudaMemcpyDefault) == cudaSuccess;
+}
+
+// triangles [nf][9] and unit outward normals [nf][3] from an indexed mesh
+const char* build_triangles(const float* verts, int nv, const int32_t* faces, int nf, std::vector<float>* tri,
+                            std::vector<float>* tri_n) {
+    if (nv < 3 || nf < 1 || !verts || !faces) return "mesh needs >= 3 vertices and >= 1 face";
+    std::vector<float> V;
+    std::vector<int32_t> F;
+    if (!host_copy(verts, (size_t)nv * 3, &V) || !host_copy(faces, (size_t)nf * 3, &F)) return "mesh copy failed";
+    tri->resize((size_t)nf * 9);
+    tri_n->resize((size_t)nf * 3);
+    for (int f = 0; f < nf; ++f) {
+        double p[3][3];
+        for (int k = 0; k < 3; ++k) {
+            int vi = F[3 * f + k];
+            if (vi < 0 || vi >= nv) return "face index out of range";
+            for (int a = 0; a < 3; ++a) {
+                p[k][a] = V[3 * vi + a];
+                (*tri)[(size_t)f * 9 + 3 * k + a] = V[3 * vi + a];
+            }
+        }
+        double u[3], w[3], n[3];
+        for (int a = 0; a < 3; ++a) { u[a] = p[1][a] - p[0][a]; w[a] = p[2][a] - p[0][a]; }
+        n[0] = u[1] * w[2] - u[2] * w[1];
+        n[1] = u[2] * w[0] - u[0] * w[2];
+        n[2] = u[0] * w[1] - u[1] * w[0];
+        double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (!(nn > 0.0)) return "degenerate (zero-area) face";
+        for (int a = 0; a < 3; ++a) (*tri_n)[(size_t)f * 3 + a] = (float)(n[a] / nn);
+    }
+    return nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t tg_max_link_taxels(void) { return kItemCap; }
+
+tg_status tg_create_scene(const tg_scene_desc* d, tg_scene** out) {
+    if (!out) return fail(nullptr, TG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!d) return fail(nullptr, TG_ERR_INVALID_ARG, "desc is NULL");
+    if (d->n_envs < 1 || d->max_links < 1 || d->max_links > kMaxLinks)
+        return fail(nullptr, TG_ERR_INVALID_ARG, "n_envs must be >= 1 and max_links in 1..255");
+    if (!d->taxel_offsets || !d->link_rows || !d->link_cols)
+        return fail(nullptr, TG_ERR_INVALID_ARG, "taxel_offsets, link_rows and link_cols are required");
+    const int E = d->n_envs, L = d->max_links;
+    if (d->taxel_offsets[0] != 0) return fail(nullptr, TG_ERR_INVALID_ARG, "taxel_offsets[0] must be 0");
+    for (int e = 0; e < E; ++e)
+        if (d->taxel_offsets[e + 1] < d->taxel_offsets[e])
+            return fail(nullptr, TG_ERR_INVALID_ARG, "taxel_offsets must be non-decreasing");
+    const int64_t T = d->taxel_offsets[E];
+    if (T > 0 && (!d->x || !d->y || !d->z || !d->nx || !d->ny || !d->nz || !d->R))
+        return fail(nullptr, TG_ERR_INVALID_ARG, "taxel geometry pointers are required");
+    ParamsDev P;
+    if (const char* m = make_params(d->params, &P)) return fail(nullptr, TG_ERR_INVALID_ARG, m);
+
+    // lattice table and work items
+    std::vector<LinkLattice> lat((size_t)E * L);
+    std::vector<Item> items;
+    for (int e = 0; e < E; ++e) {
+        int64_t acc = 0;
+        for (int l = 0; l < L; ++l) {
+            const int r = d->link_rows[e * L + l], c = d->link_cols[e * L + l];
+            if (r < 0 || c < 0 || (r == 0) != (c == 0) || r > 65535 || c > 65535)
+                return fail(nullptr, TG_ERR_INVALID_ARG, "link rows/cols must be both zero or both positive");
+            const int64_t nl = (int64_t)r * c;
+            if (nl > kItemCap)
+                return fail(nullptr, TG_ERR_INVALID_ARG,
+                            "a link lattice holds more taxels than tg_max_link_taxels()");
+            LinkLattice& t = lat[(size_t)e * L + l];
+            t.env_offset = (int32_t)acc;
+            t.rows = (uint16_t)r;
+            t.cols = (uint16_t)c;
+            t.wrap = d->link_wrap ? (d->link_wrap[e * L + l] ? 1 : 0) : 0;
+            t.present = nl > 0;
+            acc += nl;
+        }
+        if (acc != d->taxel_offsets[e + 1] - d->taxel_offsets[e])
+            return fail(nullptr, TG_ERR_INVALID_ARG, "sum of rows*cols over an env's links must equal its taxel count");
+        // pack consecutive link slots into items of <= kItemCap taxels and <= 32 links
+        int l = 0;
+        while (l < L) {
+            Item it{};
+            it.env = e;
+            it.link_begin = (int16_t)l;
+            it.taxel_begin = d->taxel_offsets[e] + lat[(size_t)e * L + l].env_offset;
+            int n = 0, k = 0;
+            while (l < L && k < kItemMaxLinksHost) {
+                const int nl = lat[(size_t)e * L + l].rows * lat[(size_t)e * L + l].cols;
+                if (n + nl > kItemCap) break;
+                n += nl;
+                ++l;
+                ++k;
+            }
+            it.link_end = (int16_t)l;
+            it.n_taxels = n;
+            if (n > 0) items.push_back(it);
+        }
+    }
+
+    tg_scene* s = new tg_scene();
+    s->E = E;
+    s->L = L;
+    s->T = T;
+    s->sensors = d->sensors;
+    s->gid0 = d->taxel_gid0;
+    s->env_gid0 = d->env_gid0;
+    s->params = d->params;
+    s->P = P;
+    s->items_h = items;
+    s->n_items = (int)items.size();
+
+    auto bail = [&](cudaError_t e, const char* what) {
+        tg_status st = cuda_fail(nullptr, e, what);
+        tg_destroy_scene(s);
+        return st;
+    };
+#define CKC(call)                                   \
+    do {                                            \
+        cudaError_t _e = (call);                    \
+        if (_e != cudaSuccess) return bail(_e, #call); \
+    } while (0)
+
+    const size_t EL = (size_t)E * L;
+    CKC(dalloc(&s->x, T)); CKC(dalloc(&s->y, T)); CKC(dalloc(&s->z, T));
+    CKC(dalloc(&s->nx, T)); CKC(dalloc(&s->ny, T)); CKC(dalloc(&s->nz, T)); CKC(dalloc(&s->R, T));
+    const float* src[7] = {d->x, d->y, d->z, d->nx, d->ny, d->nz, d->R};
+    float* dst[7] = {s->x, s->y, s->z, s->nx, s->ny, s->nz, s->R};
+    for (int i = 0; i < 7; ++i)
+        if (T > 0) CKC(cudaMemcpy(dst[i], src[i], (size_t)T * sizeof(float), cudaMemcpyDefault));
+    CKC(dalloc(&s->items, items.size()));
+    if (!items.empty()) CKC(cudaMemcpy(s->items, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice));
+    CKC(dalloc(&s->lattice, EL));
+    CKC(cudaMemcpy(s->lattice, lat.data(), EL * sizeof(LinkLattice), cudaMemcpyHostToDevice));
+    CKC(dalloc(&s->flags, T));
+    CKC(dalloc(&s->hyst_prev, (size_t)8 * T));
+    CKC(dalloc(&s->hyst_xi, (size_t)8 * T));
+    CKC(dalloc(&s->drift, (size_t)8 * T));
+    CKC(dalloc(&s->episode, E));
+    CKC(dalloc(&s->depth_clean, T));
+    CKC(dalloc(&s->depth_noisy, T));
+    CKC(dalloc(&s->dist, (d->sensors & TG_SENSOR_DIST) ? T : 1));
+    CKC(dalloc(&s->ft_clean, (size_t)6 * T));
+    CKC(dalloc(&s->ft_noisy, (size_t)6 * T));
+    CKC(dalloc(&s->link_out, EL * kLinkOut));
+    CKC(dalloc(&s->link_count, EL * 2));
+    CKC(dalloc(&s->err, 4));
+    CKC(dalloc(&s->link_rec, EL * kLinkRec));
+    CKC(dalloc(&s->s_link_pose, EL * 7));
+    CKC(dalloc(&s->s_link_vel, EL * 6));
+    CKC(dalloc(&s->s_obj_pose, (size_t)E * 7));
+    CKC(dalloc(&s->s_obj_vel, (size_t)E * 6));
+    CKC(dalloc(&s->s_env_params, (size_t)E * 3));
+    CKC(dalloc(&s->s_obj_id, E));
+    CKC(dalloc(&s->s_mask, E));
+    CKC(dalloc(&s->s_contact, T));
+    CKC(cudaMemset(s->link_out, 0, EL * kLinkOut * sizeof(float)));
+    CKC(cudaMemset(s->link_count, 0, EL * 2 * sizeof(int32_t)));
+    CKC(cudaMemset(s->err, 0, 4 * sizeof(unsigned)));
+    CKC(cudaMemset(s->link_rec, 0, EL * kLinkRec * sizeof(float)));
+    CKC(cudaMemset(s->hyst_prev, 0, (size_t)8 * T * sizeof(float)));
+    CKC(cudaMemset(s->hyst_xi, 0, (size_t)8 * T * sizeof(float)));
+    CKC(cudaMemset(s->drift, 0, (size_t)8 * T * sizeof(float)));
+    CKC(cudaMemset(s->episode, 0, (size_t)E * sizeof(uint32_t)));
+    CKC(cudaMemset(s->depth_clean, 0, (size_t)T * sizeof(float)));
+    CKC(cudaMemset(s->depth_noisy, 0, (size_t)T * sizeof(float)));
+    CKC(cudaMemset(s->ft_clean, 0, (size_t)6 * T * sizeof(float)));
+    CKC(cudaMemset(s->ft_noisy, 0, (size_t)6 * T * sizeof(float)));
+    CKC(launch_reset(step_args(s), s->n_items, nullptr, 0u, s->episode, 0));
+    CKC(cudaDeviceSynchronize());
+#undef CKC
+    *out = s;
+    return TG_OK;
+}
+
+void tg_destroy_scene(tg_scene* s) {
+    if (!s) return;
+    cudaDeviceSynchronize();
+    free_objects(s);
+    void* ptrs[] = {s->x, s->y, s->z, s->nx, s->ny, s->nz, s->R, s->items, s->lattice, s->flags, s->hyst_prev,
+                    s->hyst_xi, s->drift, s->episode, s->depth_clean, s->depth_noisy, s->dist, s->ft_clean,
+                    s->ft_noisy, s->link_out, s->link_count, s->err, s->link_rec, s->s_link_pose, s->s_link_vel,
+                    s->s_obj_pose, s->s_obj_vel, s->s_env_params, s->s_obj_id, s->s_mask, s->s_contact};
+    for (void* p : ptrs) dfree(p);
+    delete s;
+}
+
+tg_status tg_upload_objects(tg_scene* s, const tg_object_desc* objs, int32_t n) {
+    if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
+    if (!objs || n < 1) return fail(s, TG_ERR_INVALID_ARG, "need at least one object");
+    std::vector<ObjDev> table(n);
+    std::vector<void*> bufs;
+    auto cleanup = [&]() {
+        for (void* p : bufs) dfree(p);
+    };
+    for (int i = 0; i < n; ++i) {
+        const tg_object_desc& o = objs[i];
+        ObjDev& t = table[i];
+        t = ObjDev{};
+        t.kind = o.kind;
+        switch (o.kind) {
+        case TG_OBJ_SPHERE:
+            if (!(o.radius >= 0.0f) || !std::isfinite(o.radius)) { cleanup(); return fail(s, TG_ERR_INVALID_ARG, "sphere radius must be >= 0"); }
+            t.radius = o.radius;
+            break;
+        case TG_OBJ_BOX:
+            for (int a = 0; a < 3; ++a) {
+                if (!(o.half[a] >= 0.0f) || !std::isfinite(o.half[a])) { cleanup(); return fail(s, TG_ERR_INVALID_ARG, "box half extents must be >= 0"); }
+                t.half[a] = o.half[a];
+            }
+            break;
+        case TG_OBJ_PLANE: break;
+        case TG_OBJ_MESH: {
+            std::vector<float> tri, trin;
+            if (const char* m = build_triangles(o.verts, o.n_verts, o.faces, o.n_faces, &tri, &trin)) {
+                cleanup();
+                return fail(s, TG_ERR_INVALID_ARG, m);
+            }
+            float *dt = nullptr, *dn = nullptr;
+            cudaError_t e1 = dalloc(&dt, tri.size()), e2 = dalloc(&dn, trin.size());
+            if (dt) bufs.push_back(dt);
+            if (dn) bufs.push_back(dn);
+            if (e1 != cudaSuccess || e2 != cudaSuccess) { cleanup(); return cuda_fail(s, e1 != cudaSuccess ? e1 : e2, "mesh alloc"); }
+            cudaMemcpy(dt, tri.data(), tri.size() * sizeof(float), cudaMemcpyHostToDevice);
+            cudaMemcpy(dn, trin.data(), trin.size() * sizeof(float), cudaMemcpyHostToDevice);
+            t.n_verts = o.n_verts;
+            t.n_faces = o.n_faces;
+            t.tri = dt;
+            t.tri_n = dn;
+            break;
+        }
+        case TG_OBJ_GRID: {
+            size_t cnt = 1;
+            for (int a = 0; a < 3; ++a) {
+                if (o.dims[a] < 2 || !(o.hi[a] > o.lo[a]) || !std::isfinite(o.lo[a]) || !std::isfinite(o.hi[a])) {
+                    cleanup();
+                    return fail(s, TG_ERR_INVALID_ARG, "grid needs dims >= 2 and lo < hi on every axis");
+                }
+                cnt *= (size_t)o.dims[a];
+                t.dims[a] = o.dims[a];
+                t.lo[a] = o.lo[a];
+                t.hi[a] = o.hi[a];
+                const double h = ((double)o.hi[a] - (double)o.lo[a]) / (double)(o.dims[a] - 1);
+                const double ih = 1.0 / h;
+                t.h[a] = (float)h;
+                t.inv_h_hi[a] = (float)ih;
+                t.inv_h_lo[a] = (float)(ih - (double)t.inv_h_hi[a]);
+            }
+            if (!o.values) { cleanup(); return fail(s, TG_ERR_INVALID_ARG, "grid values are NULL"); }
+            const size_t bytes = cnt * (o.fp16 ? 2 : 4);
+            void* dv = nullptr;
+            cudaError_t e = cudaMalloc(&dv, bytes);
+            if (e != cudaSuccess) { cleanup(); return cuda_fail(s, e, "grid alloc"); }
+            bufs.push_back(dv);
+            e = cudaMemcpy(dv, o.values, bytes, cudaMemcpyDefault);
+            if (e != cudaSuccess) { cleanup(); return cuda_fail(s, e, "grid copy"); }
+            t.fp16 = o.fp16 ? 1 : 0;
+            t.values = dv;
+            break;
+        }
+        default:
+            cleanup();
+            return fail(s, TG_ERR_INVALID_ARG, "unknown object kind");
+        }
+    }
+    ObjDev* dtab = nullptr;
+    cudaError_t e = dalloc(&dtab, (size_t)n);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(s, e, "object table alloc"); }
+    cudaMemcpy(dtab, table.data(), sizeof(ObjDev) * n, cudaMemcpyHostToDevice);
+    CK(s, cudaDeviceSynchronize());  // old objects may still be read by queued steps
+    free_objects(s);
+    s->objects = dtab;
+    s->n_objects = n;
+    s->obj_bufs = bufs;
+    return TG_OK;
+}
+
+tg_status tg_reset_envs(tg_scene* s, const uint8_t* env_mask, uint32_t episode, tg_stream stream) {
+    if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint8_t* m = nullptr;
+    if (env_mask) CK(s, stage(env_mask, s->s_mask, (size_t)s->E, st, &m));
+    CK(s, launch_reset(step_args(s), s->n_items, m, episode, s->episode, st));
+    return TG_OK;
+}
+
+tg_status tg_step_sensors(tg_scene* s, const tg_step_inputs* in, tg_stream stream) {
+    if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
+    if (!in || !in->link_pose || !in->link_vel || !in->obj_pose || !in->obj_vel || !in->obj_id)
+        return fail(s, TG_ERR_INVALID_ARG, "step inputs: link_pose, link_vel, obj_pose, obj_vel, obj_id are required");
+    if (s->n_objects < 1) return fail(s, TG_ERR_STATE, "tg_upload_objects must come before tg_step_sensors");
+    if (!std::isfinite(in->pose_dt)) return fail(s, TG_ERR_INVALID_ARG, "pose_dt must be finite");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t EL = (size_t)s->E * s->L;
+    PoseArgs pa{};
+    CK(s, stage(in->link_pose, s->s_link_pose, EL * 7, st, &pa.link_pose));
+    CK(s, stage(in->link_vel, s->s_link_vel, EL * 6, st, &pa.link_vel));
+    CK(s, stage(in->obj_pose, s->s_obj_pose, (size_t)s->E * 7, st, &pa.obj_pose));
+    CK(s, stage(in->obj_vel, s->s_obj_vel, (size_t)s->E * 6, st, &pa.obj_vel));
+    pa.env_params = nullptr;
+    if (in->env_params) CK(s, stage(in->env_params, s->s_env_params, (size_t)s->E * 3, st, &pa.env_params));
+    const int32_t* oid = nullptr;
+    CK(s, stage(in->obj_id, s->s_obj_id, (size_t)s->E, st, &oid));
+    pa.n_envs = s->E;
+    pa.max_links = s->L;
+    pa.lattice = s->lattice;
+    pa.def_mu = (float)s->params.mu;
+    pa.def_k = (float)s->params.k;
+    pa.tau_hi = (float)in->pose_dt;
+    pa.tau_lo = (float)(in->pose_dt - (double)pa.tau_hi);
+    pa.link_rec = s->link_rec;
+    CK(s, launch_pose(pa, st));
+    StepArgs a = step_args(s);
+    a.obj_id = oid;
+    a.step = in->step;
+    CK(s, launch_step(a, s->n_items, st));
+    return TG_OK;
+}
+
+size_t tg_channel_bytes(const tg_scene* s, int32_t ch) {
+    if (!s) return 0;
+    const size_t T = (size_t)s->T, EL = (size_t)s->E * s->L;
+    switch (ch) {
+    case TG_CH_CONTACT: return T;
+    case TG_CH_DEPTH: return T * 4;
+    case TG_CH_DIST: return (s->sensors & TG_SENSOR_DIST) ? T * 4 : 0;
+    case TG_CH_FORCE_TORQUE: return T * 24;
+    case TG_CH_LINK_WRENCH: return EL * kLinkOut * 4;
+    case TG_CH_LINK_COUNT: return EL * 8;
+    case TG_CH_STATE_FLAGS: return T;
+    default: return 0;
+    }
+}
+
+tg_status tg_get_buffer(tg_scene* s, int32_t ch, int32_t noisy, void** ptr, size_t* bytes) {
+    if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
+    if (!ptr) return fail(s, TG_ERR_INVALID_ARG, "ptr is NULL");
+    void* p = nullptr;
+    switch (ch) {
+    case TG_CH_DEPTH: p = noisy ? s->depth_noisy : s->depth_clean; break;
+    case TG_CH_DIST: p = (s->sensors & TG_SENSOR_DIST) ? s->dist : nullptr; break;
+    case TG_CH_FORCE_TORQUE: p = noisy ? s->ft_noisy : s->ft_clean; break;
+    case TG_CH_LINK_WRENCH: p = s->link_out; break;
+    case TG_CH_LINK_COUNT: p = s->link_count; break;
+    case TG_CH_STATE_FLAGS: p = s->flags; break;
+    default: break;
+    }
+    if (!p) return fail(s, TG_ERR_INVALID_ARG, "channel has no device view (or its sensor is off)");
+    *ptr = p;
+    if (bytes) *bytes = tg_channel_bytes(s, ch);
+    return TG_OK;
+}
+
+tg_status tg_read_taxels(tg_scene* s, int32_t ch, int32_t noisy, void* dst, size_t dst_bytes, tg_stream stream) {
+    if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
+    const size_t need = tg_channel_bytes(s, ch);
+    if (need == 0) return fail(s, TG_ERR_INVALID_ARG, "unknown channel or sensor not enabled");
+    if (!dst || dst_bytes != need) return fail(s, TG_ERR_INVALID_ARG, "dst is NULL or dst_bytes != tg_channel_bytes");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (ch == TG_CH_CONTACT) {
+        if (is_device_ptr(dst)) {
+            CK(s, launch_unpack_contact(s->flags, s->T, noisy, (uint8_t*)dst, st));
+        } else {
+            CK(s, launch_unpack_contact(s->flags, s->T, noisy, s->s_contact, st));
+            CK(s, cudaMemcpyAsync(dst, s->s_contact, need, cudaMemcpyDeviceToHost, st));
+        }
+        return TG_OK;
+    }
+    void* p = nullptr;
+    tg_status r = tg_get_buffer(s, ch, noisy, &p, nullptr);
+    if (r != TG_OK) return r;
+    CK(s, cudaMemcpyAsync(dst, p, need, cudaMemcpyDefault, st));
+    return TG_OK;
+}
+
+tg_status tg_sync(tg_scene* s, tg_stream stream) {
+    if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
+    CK(s, cudaStreamSynchronize((cudaStream_t)stream));
+    CK(s, cudaGetLastError());
+    unsigned h[4] = {0, 0, 0, 0};
+    CK(s, cudaMemcpy(h, s->err, sizeof(h), cudaMemcpyDeviceToHost));
+    if (h[0]) {
+        CK(s, cudaMemset(s->err, 0, sizeof(h)));
+        return fail(s, TG_ERR_NUMERIC, "non-finite signed distances were seen (" + std::to_string(h[0]) + " taxel queries)");
+    }
+    return TG_OK;
+}
+
+const char* tg_last_error(const tg_scene* s) { return s ? s->last_error.c_str() : g_create_error.c_str(); }
+
+static const uint64_t kStateMagic = 0x3130455441545354ull;  // "TSTATE01"
+
+tg_status tg_save_state(tg_scene* s, void* buf, size_t* size) {
+    if (!s || !size) return fail(s, TG_ERR_INVALID_ARG, "scene or size is NULL");
+    const size_t T = (size_t)s->T, E = (size_t)s->E;
+    const size_t need = 32 + T + 3 * 8 * T * 4 + E * 4;
+    if (!buf) { *size = need; return TG_OK; }
+    if (*size != need) return fail(s, TG_ERR_INVALID_ARG, "state buffer size mismatch");
+    CK(s, cudaDeviceSynchronize());
+    unsigned char* p = (unsigned char*)buf;
+    uint64_t hdr[4] = {kStateMagic, (uint64_t)T, (uint64_t)E, 0};
+    memcpy(p, hdr, 32);
+    p += 32;
+    CK(s, cudaMemcpy(p, s->flags, T, cudaMemcpyDeviceToHost)); p += T;
+    CK(s, cudaMemcpy(p, s->hyst_prev, 8 * T * 4, cudaMemcpyDeviceToHost)); p += 8 * T * 4;
+    CK(s, cudaMemcpy(p, s->hyst_xi, 8 * T * 4, cudaMemcpyDeviceToHost)); p += 8 * T * 4;
+    CK(s, cudaMemcpy(p, s->drift, 8 * T * 4, cudaMemcpyDeviceToHost)); p += 8 * T * 4;
+    CK(s, cudaMemcpy(p, s->episode, E * 4, cudaMemcpyDeviceToHost));
+    return TG_OK;
+}
+
+tg_status tg_load_state(tg_scene* s, const void* buf, size_t size) {
+    if (!s || !buf) return fail(s, TG_ERR_INVALID_ARG, "scene or buf is NULL");
+    const size_t T = (size_t)s->T, E = (size_t)s->E;
+    const size_t need = 32 + T + 3 * 8 * T * 4 + E * 4;
+    if (size != need) return fail(s, TG_ERR_INVALID_ARG, "state buffer size mismatch");
+    const unsigned char* p = (const unsigned char*)buf;
+    uint64_t hdr[4];
+    memcpy(hdr, p, 32);
+    if (hdr[0] != kStateMagic || hdr[1] != T || hdr[2] != E) return fail(s, TG_ERR_INVALID_ARG, "state buffer is not from a scene of this shape");
+    p += 32;
+    CK(s, cudaDeviceSynchronize());
+    CK(s, cudaMemcpy(s->flags, p, T, cudaMemcpyHostToDevice)); p += T;
+    CK(s, cudaMemcpy(s->hyst_prev, p, 8 * T * 4, cudaMemcpyHostToDevice)); p += 8 * T * 4;
+    CK(s, cudaMemcpy(s->hyst_xi, p, 8 * T * 4, cudaMemcpyHostToDevice)); p += 8 * T * 4;
+    CK(s, cudaMemcpy(s->drift, p, 8 * T * 4, cudaMemcpyHostToDevice)); p += 8 * T * 4;
+    CK(s, cudaMemcpy(s->episode, p, E * 4, cudaMemcpyHostToDevice));
+    return TG_OK;
+}
+
+static tg_status mesh_common(const float* verts, int32_t nv, const int32_t* faces, int32_t nf, cudaStream_t st,
+                             float** tri, float** trin) {
+    std::vector<float> t, tn;
+    if (const char* m = build_triangles(verts, nv, faces, nf, &t, &tn)) return fail(nullptr, TG_ERR_INVALID_ARG, m);
+    cudaError_t e = cudaMallocAsync((void**)tri, t.size() * sizeof(float), st);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "mesh alloc");
+    e = cudaMallocAsync((void**)trin, tn.size() * sizeof(float), st);
+    if (e != cudaSuccess) { cudaFreeAsync(*tri, st); return cuda_fail(nullptr, e, "mesh alloc"); }
+    cudaMemcpyAsync(*tri, t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(*trin, tn.data(), tn.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+    e = cudaStreamSynchronize(st);  // the host vectors die at return
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "mesh upload");
+    return TG_OK;
+}
+
+tg_status tg_bake_grid(const float* verts, int32_t nv, const int32_t* faces, int32_t nf, const int32_t dims[3],
+                       const float lo[3], const float hi[3], int32_t fp16, void* out, tg_stream stream) {
+    if (!dims || !lo || !hi || !out) return fail(nullptr, TG_ERR_INVALID_ARG, "dims, lo, hi and out are required");
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] < 2 || !(hi[a] > lo[a])) return fail(nullptr, TG_ERR_INVALID_ARG, "grid needs dims >= 2 and lo < hi");
+    if (!is_device_ptr(out)) return fail(nullptr, TG_ERR_INVALID_ARG, "out must be device memory");
+    cudaStream_t st = (cudaStream_t)stream;
+    float *tri = nullptr, *trin = nullptr;
+    tg_status r = mesh_common(verts, nv, faces, nf, st, &tri, &trin);
+    if (r != TG_OK) return r;
+    int d3[3] = {dims[0], dims[1], dims[2]};
+    cudaError_t e = launch_mesh_bake(tri, trin, nf, d3, lo, hi, fp16, out, st);
+    cudaFreeAsync(tri, st);
+    cudaFreeAsync(trin, st);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "bake launch");
+    return TG_OK;
+}
+
+tg_status tg_mesh_sdf(const float* verts, int32_t nv, const int32_t* faces, int32_t nf, const float* points, int64_t n,
+                      float* phi, float* grad, tg_stream stream) {
+    if (n < 0 || (n > 0 && (!points || !phi))) return fail(nullptr, TG_ERR_INVALID_ARG, "points and phi are required");
+    if (n > 0 && (!is_device_ptr(points) || !is_device_ptr(phi) || (grad && !is_device_ptr(grad))))
+        return fail(nullptr, TG_ERR_INVALID_ARG, "points, phi and grad must be device memory");
+    cudaStream_t st = (cudaStream_t)stream;
+    float *tri = nullptr, *trin = nullptr;
+    tg_status r = mesh_common(verts, nv, faces, nf, st, &tri, &trin);
+    if (r != TG_OK) return r;
+    cudaError_t e = launch_mesh_sdf_points(tri, trin, nf, points, n, phi, grad, st);
+    cudaFreeAsync(tri, st);
+    cudaFreeAsync(trin, st);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "mesh sdf launch");
+    return TG_OK;
+}
+
+}  // extern "C"

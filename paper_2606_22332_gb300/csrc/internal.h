@@ -1,0 +1,129 @@
+// internal.h -- device-side data layout of a scene and the launch wrappers
+// shared by the translation units of libtg.so.  Not part of the C-ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "../../include/tg.h"
+
+namespace tg {
+
+constexpr int kMaxLinks = 255;       // u8 link ids
+constexpr int kItemCap = 1024;       // max taxels per work item (one CTA)
+constexpr int kStepThreads = 256;    // CTA size of the step kernel
+constexpr int kLinkRec = 40;         // floats per (env, link) pose record
+constexpr int kLinkOut = 18;         // floats per (env, link) output record
+
+// A noise group with the host-derived constants the kernel uses.
+struct NoiseDev {
+    float gain_lo, gain_span;    // gain = lo + span * u
+    float beta, decay;           // decay = exp(-dt / tau)
+    float bias, sigma_white, sigma_rw, quant;
+    float stuck_lo, stuck_span;
+    int gain_on;
+};
+
+struct ParamsDev {
+    float k, c, alpha, k_t, k_omega, mu;  // mu < 0: no clamp
+    float eta_on_hi, eta_on_lo, eta_off_hi, eta_off_lo;  // thresholds as float pairs
+    uint32_t dead_threshold24;            // rint(p_dead * 2^24)
+    float chi;
+    float xt_w[9];                        // L1-normalised 3x3 Gaussian, row-major
+    uint64_t seed;
+    NoiseDev depth, ft, prox;
+};
+
+// Object table entry (object frame).
+struct ObjDev {
+    int kind;
+    float radius;
+    float half[3];
+    // grid
+    int dims[3];
+    float lo[3];
+    float hi[3];
+    float inv_h_hi[3], inv_h_lo[3];   // (dims-1)/(hi-lo) as a float pair
+    float h[3];
+    int fp16;
+    const void* values;
+    // mesh
+    int n_verts, n_faces;
+    const float* tri;                 // [n_faces][9]: a, b, c vertices
+    const float* tri_n;               // [n_faces][3]: unit outward normals
+};
+
+// One CTA of the step kernel: a run of whole links of one env.
+struct Item {
+    int32_t env;
+    int16_t link_begin, link_end;     // [begin, end) over the env's link slots
+    int64_t taxel_begin;              // global index of the first taxel
+    int32_t n_taxels;
+    int32_t pad;
+};
+
+// Per (env, link) lattice: where its taxels start within the item's env.
+struct LinkLattice {
+    int32_t env_offset;               // first taxel of the link, relative to the env
+    uint16_t rows, cols;
+    uint8_t wrap, present, pad0, pad1;
+};
+
+struct StepArgs {
+    // static geometry
+    const float *x, *y, *z, *nx, *ny, *nz, *R;
+    const Item* items;
+    const LinkLattice* lattice;       // [E*L]
+    const ObjDev* objects;
+    int n_objects;
+    int n_envs, max_links;
+    int64_t n_taxels;
+    int64_t gid0;
+    uint32_t sensors;
+    ParamsDev P;
+    // per-step inputs (device)
+    const int32_t* obj_id;
+    const float* link_rec;            // [E*L][kLinkRec] from the pose kernel
+    uint32_t step;
+    // state
+    uint8_t* flags;
+    float* hyst_prev;                 // [8][T]
+    float* hyst_xi;                   // [8][T]
+    float* drift;                     // [8][T]
+    const uint32_t* episode;          // [E]
+    // outputs
+    float* depth_clean;
+    float* depth_noisy;
+    float* dist;
+    float* ft_clean;                  // [6][T]
+    float* ft_noisy;                  // [6][T]
+    float* link_out;                  // [E*L][kLinkOut]
+    int32_t* link_count;              // [E*L][2]
+    unsigned int* err;                // [0] non-finite count
+};
+
+struct PoseArgs {
+    int n_envs, max_links;
+    const float* link_pose;
+    const float* link_vel;
+    const float* obj_pose;
+    const float* obj_vel;
+    const float* env_params;          // may be null
+    const LinkLattice* lattice;
+    float def_mu, def_k;
+    float tau_hi, tau_lo;             // pose_dt as a float pair
+    float* link_rec;
+};
+
+cudaError_t launch_pose(const PoseArgs& a, cudaStream_t s);
+cudaError_t launch_step(const StepArgs& a, int n_items, cudaStream_t s);
+cudaError_t launch_reset(const StepArgs& a, int n_items, const uint8_t* env_mask, uint32_t episode,
+                         uint32_t* episode_arr, cudaStream_t s);
+constexpr int kItemMaxLinksHost = 32;   // links per work item (matches the step kernel)
+cudaError_t launch_mesh_sdf_points(const float* tri, const float* tri_n, int n_faces, const float* points,
+                                   int64_t n, float* phi, float* grad, cudaStream_t s);
+cudaError_t launch_mesh_bake(const float* tri, const float* tri_n, int n_faces, const int dims[3],
+                             const float lo[3], const float hi[3], int fp16, void* out, cudaStream_t s);
+cudaError_t launch_unpack_contact(const uint8_t* flags, int64_t n, int noisy, uint8_t* out, cudaStream_t s);
+
+}  // namespace tg

@@ -1,0 +1,325 @@
+"""Thin Python binding of the C-ABI in include/tg.h (argument marshalling only).
+
+Every step of the sensor pipeline runs in libtg.so's CUDA kernels; this
+module builds the C structs, passes raw pointers (numpy arrays for host
+memory, torch tensors for device memory) and the current torch stream, and
+turns status codes into exceptions.  There is no fallback: if libtg.so is
+missing the import of this module fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "csrc", "libtg.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
+        "(the CUDA library is the only compute path)")
+
+_lib = C.CDLL(LIB_PATH)
+
+# status codes, object kinds, channels, sensors (include/tg.h)
+TG_OK = 0
+STATUS = {0: "TG_OK", 1: "TG_ERR_INVALID_ARG", 2: "TG_ERR_OOM", 3: "TG_ERR_CUDA", 4: "TG_ERR_STATE",
+          5: "TG_ERR_TIMEOUT", 6: "TG_ERR_NUMERIC", 7: "TG_ERR_UNSUPPORTED"}
+TG_OBJ_SPHERE, TG_OBJ_BOX, TG_OBJ_PLANE, TG_OBJ_MESH, TG_OBJ_GRID = 0, 1, 2, 3, 4
+CH_CONTACT, CH_DEPTH, CH_DIST, CH_FORCE_TORQUE, CH_LINK_WRENCH, CH_LINK_COUNT, CH_STATE_FLAGS = range(7)
+TG_SENSOR_DIST = 0x1
+LINK_REC = 18
+
+
+class TGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class NoiseGroup(C.Structure):
+    _fields_ = [(n, C.c_double) for n in (
+        "gain_lo", "gain_hi", "beta", "tau", "bias", "sigma_white", "sigma_rw", "quant", "stuck_lo", "stuck_hi")]
+
+
+class Params(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("k", "c", "alpha", "k_t", "k_omega", "mu", "eta_on", "eta_off", "dt",
+                                          "p_dead", "chi", "xt_sigma")] + [
+        ("seed", C.c_uint64), ("depth", NoiseGroup), ("ft", NoiseGroup), ("prox", NoiseGroup)]
+
+
+class SceneDesc(C.Structure):
+    _fields_ = [("n_envs", C.c_int32), ("max_links", C.c_int32), ("taxel_offsets", C.c_void_p),
+                ("link_rows", C.c_void_p), ("link_cols", C.c_void_p), ("link_wrap", C.c_void_p),
+                ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
+                ("nx", C.c_void_p), ("ny", C.c_void_p), ("nz", C.c_void_p), ("R", C.c_void_p),
+                ("params", Params), ("sensors", C.c_uint32), ("taxel_gid0", C.c_int64), ("env_gid0", C.c_int32)]
+
+
+class ObjectDesc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("radius", C.c_float), ("half", C.c_float * 3),
+                ("n_verts", C.c_int32), ("n_faces", C.c_int32), ("verts", C.c_void_p), ("faces", C.c_void_p),
+                ("dims", C.c_int32 * 3), ("lo", C.c_float * 3), ("hi", C.c_float * 3),
+                ("fp16", C.c_int32), ("values", C.c_void_p)]
+
+
+class StepInputs(C.Structure):
+    _fields_ = [("link_pose", C.c_void_p), ("link_vel", C.c_void_p), ("obj_pose", C.c_void_p),
+                ("obj_vel", C.c_void_p), ("obj_id", C.c_void_p), ("env_params", C.c_void_p),
+                ("pose_dt", C.c_double), ("step", C.c_uint32)]
+
+
+_vp, _i32, _sz = C.c_void_p, C.c_int32, C.c_size_t
+_lib.tg_create_scene.argtypes = [C.POINTER(SceneDesc), C.POINTER(_vp)]
+_lib.tg_destroy_scene.argtypes = [_vp]
+_lib.tg_destroy_scene.restype = None
+_lib.tg_max_link_taxels.restype = C.c_int32
+_lib.tg_upload_objects.argtypes = [_vp, C.POINTER(ObjectDesc), _i32]
+_lib.tg_reset_envs.argtypes = [_vp, _vp, C.c_uint32, _vp]
+_lib.tg_step_sensors.argtypes = [_vp, C.POINTER(StepInputs), _vp]
+_lib.tg_read_taxels.argtypes = [_vp, _i32, _i32, _vp, _sz, _vp]
+_lib.tg_channel_bytes.argtypes = [_vp, _i32]
+_lib.tg_channel_bytes.restype = _sz
+_lib.tg_get_buffer.argtypes = [_vp, _i32, _i32, C.POINTER(_vp), C.POINTER(_sz)]
+_lib.tg_sync.argtypes = [_vp, _vp]
+_lib.tg_last_error.argtypes = [_vp]
+_lib.tg_last_error.restype = C.c_char_p
+_lib.tg_save_state.argtypes = [_vp, _vp, C.POINTER(_sz)]
+_lib.tg_load_state.argtypes = [_vp, _vp, _sz]
+_lib.tg_bake_grid.argtypes = [_vp, _i32, _vp, _i32, _vp, _vp, _vp, _i32, _vp, _vp]
+_lib.tg_mesh_sdf.argtypes = [_vp, _i32, _vp, _i32, _vp, C.c_int64, _vp, _vp, _vp]
+for _f in ("tg_create_scene", "tg_upload_objects", "tg_reset_envs", "tg_step_sensors", "tg_read_taxels",
+           "tg_get_buffer", "tg_sync", "tg_save_state", "tg_load_state", "tg_bake_grid", "tg_mesh_sdf"):
+    getattr(_lib, _f).restype = C.c_int
+
+EXPORTED = ["tg_create_scene", "tg_destroy_scene", "tg_max_link_taxels", "tg_upload_objects", "tg_reset_envs",
+            "tg_step_sensors", "tg_read_taxels", "tg_channel_bytes", "tg_get_buffer", "tg_sync", "tg_last_error",
+            "tg_save_state", "tg_load_state", "tg_bake_grid", "tg_mesh_sdf"]
+
+
+def lib():
+    return _lib
+
+
+def _check(status, scene_handle=None):
+    if status != TG_OK:
+        msg = _lib.tg_last_error(scene_handle)
+        raise TGError(status, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array (host) or a torch tensor (host or device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"], "arrays must be C-contiguous"
+        return a.ctypes.data
+    assert a.is_contiguous(), "tensors must be contiguous"
+    return a.data_ptr()
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    import torch
+
+    if torch.cuda.is_available() and torch.cuda.is_initialized():
+        return torch.cuda.current_stream().cuda_stream
+    return None
+
+
+def _fill_params(params: dict) -> Params:
+    P = Params()
+    for k in ("k", "c", "alpha", "k_t", "k_omega", "eta_on", "eta_off", "dt", "p_dead", "chi", "xt_sigma"):
+        setattr(P, k, float(params[k]))
+    mu = params["mu"]
+    P.mu = -1.0 if mu is None or np.isinf(mu) else float(mu)
+    P.seed = int(params["seed"])
+    for g in ("depth", "ft", "prox"):
+        grp = getattr(P, g)
+        for k in NoiseGroup._fields_:
+            setattr(grp, k[0], float(params["noise"][g][k[0]]))
+    return P
+
+
+class _CudaView:
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+def object_desc(o, keep: list) -> ObjectDesc:
+    """tg_object_desc of a workload ObjectSpec (arrays kept alive in `keep`)."""
+    d = ObjectDesc()
+    kind = {"sphere": TG_OBJ_SPHERE, "box": TG_OBJ_BOX, "plane": TG_OBJ_PLANE, "mesh": TG_OBJ_MESH,
+            "grid": TG_OBJ_GRID}[o.kind]
+    d.kind = kind
+    d.radius = float(o.radius)
+    d.half[:] = [float(h) for h in o.half]
+    if kind == TG_OBJ_MESH:
+        V = np.ascontiguousarray(o.verts, np.float32); F = np.ascontiguousarray(o.faces, np.int32)
+        keep += [V, F]
+        d.n_verts, d.n_faces = len(V), len(F)
+        d.verts, d.faces = _ptr(V), _ptr(F)
+    if kind == TG_OBJ_GRID:
+        vals = o.values
+        if isinstance(vals, np.ndarray):
+            vals = np.ascontiguousarray(vals, np.uint16 if o.fp16 else np.float32)
+        keep.append(vals)
+        d.dims[:] = [int(v) for v in o.dims]
+        d.lo[:] = [float(v) for v in o.lo]
+        d.hi[:] = [float(v) for v in o.hi]
+        d.fp16 = 1 if o.fp16 else 0
+        d.values = _ptr(vals)
+    return d
+
+
+class Scene:
+    """A tg_scene: the taxel geometry, state and outputs of E envs."""
+
+    def __init__(self, geom: dict, params: dict, sensors: int = 0, taxel_gid0: int = 0, env_gid0: int = 0):
+        keep = {}
+        off = np.ascontiguousarray(geom["taxel_offsets"], np.int64)
+        E = len(off) - 1
+        rows = np.ascontiguousarray(geom["link_rows"], np.int32)
+        L = len(rows) // E
+        keep["off"] = off
+        keep["rows"] = rows
+        keep["cols"] = np.ascontiguousarray(geom["link_cols"], np.int32)
+        keep["wrap"] = np.ascontiguousarray(geom["link_wrap"], np.uint8)
+        d = SceneDesc()
+        d.n_envs, d.max_links = E, L
+        d.taxel_offsets, d.link_rows = _ptr(off), _ptr(rows)
+        d.link_cols, d.link_wrap = _ptr(keep["cols"]), _ptr(keep["wrap"])
+        for k in ("x", "y", "z", "nx", "ny", "nz", "R"):
+            a = geom[k]
+            if isinstance(a, np.ndarray):
+                a = np.ascontiguousarray(a, np.float32)
+            keep[k] = a
+            setattr(d, k, _ptr(a))
+        d.params = _fill_params(params)
+        d.sensors = sensors
+        d.taxel_gid0 = int(taxel_gid0)
+        d.env_gid0 = int(env_gid0)
+        h = C.c_void_p()
+        _check(_lib.tg_create_scene(C.byref(d), C.byref(h)), None)
+        self.h = h
+        self.n_envs, self.max_links, self.n_taxels = E, L, int(off[-1])
+        self.sensors = sensors
+        self._keep_inputs = None
+
+    @classmethod
+    def from_workload(cls, wl, sensors: int = 0):
+        return cls(wl.geom(), wl.params, sensors=sensors)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.tg_destroy_scene(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def upload_objects(self, objects):
+        keep = []
+        arr = (ObjectDesc * len(objects))(*[object_desc(o, keep) for o in objects])
+        _check(_lib.tg_upload_objects(self.h, arr, len(objects)), self.h)
+
+    def reset(self, episode: int, env_mask=None, stream=None):
+        _check(_lib.tg_reset_envs(self.h, _ptr(env_mask), int(episode), _stream(stream)), self.h)
+
+    def step(self, inputs: dict, stream=None):
+        """inputs: link_pose, link_vel, obj_pose, obj_vel, obj_id, optional env_params (numpy = host,
+        torch = host or device), pose_dt (s), step (RNG counter)."""
+        I = StepInputs()
+        keep = {}
+        for k, dt in (("link_pose", np.float32), ("link_vel", np.float32), ("obj_pose", np.float32),
+                      ("obj_vel", np.float32), ("obj_id", np.int32), ("env_params", np.float32)):
+            a = inputs.get(k)
+            if a is None:
+                continue
+            if isinstance(a, np.ndarray):
+                a = np.ascontiguousarray(a, dt)
+            keep[k] = a
+            setattr(I, k, _ptr(a))
+        I.pose_dt = float(inputs.get("pose_dt", 0.0))
+        I.step = int(inputs.get("step", 0))
+        self._keep_inputs = keep  # host sources must outlive the async copies
+        _check(_lib.tg_step_sensors(self.h, C.byref(I), _stream(stream)), self.h)
+
+    def channel_bytes(self, ch: int) -> int:
+        return int(_lib.tg_channel_bytes(self.h, ch))
+
+    def _shape_dtype(self, ch):
+        T, EL = self.n_taxels, self.n_envs * self.max_links
+        return {CH_CONTACT: ((T,), np.uint8), CH_DEPTH: ((T,), np.float32), CH_DIST: ((T,), np.float32),
+                CH_FORCE_TORQUE: ((6, T), np.float32), CH_LINK_WRENCH: ((EL, LINK_REC), np.float32),
+                CH_LINK_COUNT: ((EL, 2), np.int32), CH_STATE_FLAGS: ((T,), np.uint8)}[ch]
+
+    def read(self, ch: int, noisy: bool = False, out=None, stream=None):
+        """Copy a channel into `out` (numpy = host, torch tensor = host or device); returns it."""
+        shape, dt = self._shape_dtype(ch)
+        if out is None:
+            out = np.empty(shape, dt)
+        _check(_lib.tg_read_taxels(self.h, ch, int(noisy), _ptr(out), self.channel_bytes(ch), _stream(stream)),
+               self.h)
+        if isinstance(out, np.ndarray):
+            self.sync(stream)
+        return out
+
+    def buffer(self, ch: int, noisy: bool = False):
+        """Zero-copy torch view of a library-owned device buffer."""
+        import torch
+
+        p, n = C.c_void_p(), C.c_size_t()
+        _check(_lib.tg_get_buffer(self.h, ch, int(noisy), C.byref(p), C.byref(n)), self.h)
+        shape, dt = self._shape_dtype(ch)
+        typestr = {np.float32: "<f4", np.int32: "<i4", np.uint8: "|u1"}[dt]
+        return torch.as_tensor(_CudaView(p.value, shape, typestr), device="cuda")
+
+    def sync(self, stream=None):
+        _check(_lib.tg_sync(self.h, _stream(stream)), self.h)
+
+    def save_state(self) -> bytes:
+        n = C.c_size_t()
+        _check(_lib.tg_save_state(self.h, None, C.byref(n)), self.h)
+        buf = C.create_string_buffer(n.value)
+        _check(_lib.tg_save_state(self.h, buf, C.byref(n)), self.h)
+        return buf.raw
+
+    def load_state(self, data: bytes):
+        buf = C.create_string_buffer(data, len(data))
+        _check(_lib.tg_load_state(self.h, buf, len(data)), self.h)
+
+
+def bake_grid(verts, faces, dims, lo, hi, fp16=False, stream=None):
+    """Exact mesh SDF at the grid nodes on the GPU; returns a torch tensor [z][y][x]
+    (float32, or int16 holding binary16 bits when fp16)."""
+    import torch
+
+    V = np.ascontiguousarray(verts, np.float32); F = np.ascontiguousarray(faces, np.int32)
+    d = np.ascontiguousarray(dims, np.int32)
+    lo = np.ascontiguousarray(lo, np.float32); hi = np.ascontiguousarray(hi, np.float32)
+    out = torch.empty((int(d[2]), int(d[1]), int(d[0])), dtype=torch.float16 if fp16 else torch.float32, device="cuda")
+    _check(_lib.tg_bake_grid(_ptr(V), len(V), _ptr(F), len(F), _ptr(d), _ptr(lo), _ptr(hi), int(fp16),
+                             out.data_ptr(), _stream(stream)), None)
+    return out
+
+
+def mesh_sdf(verts, faces, points, with_grad=True, stream=None):
+    """Exact mesh SDF (and unit gradient) at device points [n][3]."""
+    import torch
+
+    V = np.ascontiguousarray(verts, np.float32); F = np.ascontiguousarray(faces, np.int32)
+    pts = points.contiguous()
+    n = pts.shape[0]
+    phi = torch.empty(n, dtype=torch.float32, device=pts.device)
+    grad = torch.empty((n, 3), dtype=torch.float32, device=pts.device) if with_grad else None
+    _check(_lib.tg_mesh_sdf(_ptr(V), len(V), _ptr(F), len(F), pts.data_ptr(), n, phi.data_ptr(),
+                            grad.data_ptr() if grad is not None else None, _stream(stream)), None)
+    return phi, grad

@@ -1,0 +1,106 @@
+"""Element-by-element comparison of the CUDA path with the FP64 oracle.
+
+Tolerances (stated for the hot path):
+  contact flags, dead masks, RNG-driven bits   bit-exact
+  depth, noisy depth, surface distance         |d_gpu - d_ora| <= 1e-5 m
+  force/torque (clean and noisy)               |f_gpu - f_ora| <= 1e-4 |f_ora| + 1e-6
+  per-link sums                                the per-taxel bound summed over the
+                                               link: 1e-4 sum|f_j| + 1e-6 n_link
+Contact bits are decided by the depth against eta_on / eta_off; a taxel
+whose oracle depth lies within BAND of a threshold may legitimately differ
+(the two sides round differently) and is counted instead of failed; the
+count must stay below 1e-4 of the active taxels.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+F_REL, F_ABS, D_ABS = 1e-4, 1e-6, 1e-5
+BAND = 1e-9
+
+
+def gpu_outputs(scene):
+    import paper_2606_22332_gb300.tg as tg
+
+    return {
+        "flags": scene.read(tg.CH_STATE_FLAGS),
+        "contact_clean": scene.read(tg.CH_CONTACT, False),
+        "contact_noisy": scene.read(tg.CH_CONTACT, True),
+        "depth_clean": scene.read(tg.CH_DEPTH, False),
+        "depth_noisy": scene.read(tg.CH_DEPTH, True),
+        "ft_clean": scene.read(tg.CH_FORCE_TORQUE, False),
+        "ft_noisy": scene.read(tg.CH_FORCE_TORQUE, True),
+        "link_sums": scene.read(tg.CH_LINK_WRENCH),
+        "link_counts": scene.read(tg.CH_LINK_COUNT),
+        "dist": scene.read(tg.CH_DIST) if scene.sensors & tg.TG_SENSOR_DIST else None,
+    }
+
+
+def compare_step(gpu, ora, ostate, params, wl, active=None, where=""):
+    """Assert the CUDA step matches the oracle step; returns error statistics."""
+    R = wl.R
+    act = R > 0 if active is None else active
+    n_act = int(act.sum())
+    stats = {}
+    # dead masks: bit-exact
+    assert np.array_equal((gpu["flags"] >> 1) & 1, (ostate["flags"] >> 1) & 1), f"{where}: dead masks differ"
+    # contact bits, with the threshold band
+    d_or = ora["depth_clean"]
+    band = (np.abs(d_or - params["eta_on"]) < BAND) | (np.abs(d_or - params["eta_off"]) < BAND)
+    for k in ("contact_clean", "contact_noisy"):
+        bad = (gpu[k] != ora[k]) & ~band
+        assert not bad.any(), f"{where}: {k} differs at {np.flatnonzero(bad)[:10]}"
+    nb = int(((gpu["contact_clean"] != ora["contact_clean"]) & band).sum())
+    assert nb <= max(1, 1e-4 * n_act), f"{where}: {nb} banded contact mismatches"
+    stats["banded"] = nb
+    # depth
+    for k in ("depth_clean", "depth_noisy"):
+        err = np.abs(gpu[k].astype(np.float64) - ora[k])
+        stats[k] = float(err.max()) if err.size else 0.0
+        assert stats[k] <= D_ABS, f"{where}: {k} max err {stats[k]:.3e} at {np.argmax(err)}"
+    if gpu.get("dist") is not None:
+        err = np.abs(gpu["dist"].astype(np.float64) - ora["dist"])
+        stats["dist"] = float(err.max()) if err.size else 0.0
+        assert stats["dist"] <= D_ABS, f"{where}: dist max err {stats['dist']:.3e}"
+    # force/torque
+    for k in ("ft_clean", "ft_noisy"):
+        g, o = gpu[k].astype(np.float64), ora[k]
+        err = np.abs(g - o)
+        tol = F_REL * np.abs(o) + F_ABS
+        ratio = err / tol
+        stats[k] = float(ratio.max()) if ratio.size else 0.0
+        stats[k + "_abs"] = float(err.max()) if err.size else 0.0
+        if stats[k] > 1.0:
+            idx = np.unravel_index(np.argmax(ratio), ratio.shape)
+            raise AssertionError(f"{where}: {k} err {err[idx]:.3e} > tol {tol[idx]:.3e} at {idx}: gpu {g[idx]} oracle {o[idx]}"
+                                 f" depth {d_or[idx[1]]:.3e}")
+    # per-link sums
+    L = wl.max_links
+    off = wl.taxel_offsets
+    absf = {"c": np.abs(ora["ft_clean"]), "n": np.abs(ora["ft_noisy"])}
+    ls_g, ls_o = gpu["link_sums"].astype(np.float64), ora["link_sums"]
+    worst = 0.0
+    for e in range(wl.n_envs):
+        t0 = int(off[e])
+        for l in range(L):
+            r, c = wl.link_rows[e * L + l], wl.link_cols[e * L + l]
+            nl = int(r * c)
+            if nl == 0:
+                continue
+            sl = slice(t0, t0 + nl)
+            t0 += nl
+            rec = e * L + l
+            for part, cols_, srcs in (("c", range(0, 6), absf["c"]), ("n", range(6, 12), absf["n"])):
+                for j, col in enumerate(cols_):
+                    tol = F_REL * srcs[j, sl].sum() + F_ABS * nl
+                    err = abs(ls_g[rec, col] - ls_o[rec, col])
+                    worst = max(worst, err / tol)
+                    assert err <= tol, f"{where}: link sum env {e} link {l} col {col}: {ls_g[rec, col]} vs {ls_o[rec, col]}"
+            for col, dsrc in ((12, "depth_clean"), (15, "depth_noisy")):
+                for j in range(3):
+                    tol = 1e4 * (D_ABS * 0 + 1e-4 * np.abs(ora[dsrc][sl]).sum()) + F_ABS * nl
+                    err = abs(ls_g[rec, col + j] - ls_o[rec, col + j])
+                    assert err <= tol, f"{where}: agg_force env {e} link {l}: {ls_g[rec, col + j]} vs {ls_o[rec, col + j]}"
+    stats["link_sums"] = worst
+    assert np.array_equal(gpu["link_counts"], ora["link_counts"]) or nb > 0, f"{where}: link contact counts differ"
+    return stats

@@ -74,3 +74,27 @@ def quiet_params(seed=1234, **over):
         p["noise"][g] = W.noise_group()
     p.update(over)
     return p
+
+
+def bake_objects_oracle(objects, dims=None):
+    """Fill every grid object's values with the oracle's exact-mesh bake
+    (optionally at other dims); returns the list of objects."""
+    out = []
+    for o in objects:
+        if o.kind == "grid":
+            d = tuple(dims) if dims is not None else tuple(o.dims)
+            vals = oracle.bake_grid(o.verts, o.faces, d, o.lo.astype(np.float64), o.hi.astype(np.float64), fp16=o.fp16)
+            o = W.ObjectSpec(kind="grid", verts=o.verts, faces=o.faces, dims=d, lo=o.lo, hi=o.hi, fp16=o.fp16,
+                             values=vals, name=o.name)
+        out.append(o)
+    return out
+
+
+def low_poly_grid_objects(rng, n_objects, n_grid, fp16, points=(12, 40)):
+    """Grid objects over low-face-count hulls (fast to bake exactly at full
+    grid resolution), for full-size runs the oracle can check."""
+    objs = []
+    for i in range(n_objects):
+        V, F = W.hull_mesh(rng, int(rng.integers(*points)), 0.04)
+        objs.append(W.make_grid_object(V, F, n_grid, fp16, name=f"lowpoly{i}"))
+    return bake_objects_oracle(objs)

@@ -1,0 +1,79 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry
+point include/tg.h declares; the binding's structs match the header."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2606_22332_gb300 import build
+
+    try:
+        return build.build()
+    except RuntimeError as e:  # no nvcc on this machine
+        pytest.skip(str(e))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "tg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tg_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("tg_create_scene", "tg_upload_objects", "tg_step_sensors", "tg_read_taxels"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_lists_every_symbol(libpath):
+    import paper_2606_22332_gb300.tg as tg
+
+    assert sorted(tg.EXPORTED) == declared_functions()
+
+
+def test_struct_sizes_match_header(libpath):
+    """Compile a tiny C program against tg.h and compare sizeof/offsetof with ctypes."""
+    import subprocess
+    import tempfile
+
+    import paper_2606_22332_gb300.tg as tg
+
+    prog = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "tg.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\n", sizeof(tg_params), sizeof(tg_scene_desc), sizeof(tg_object_desc),
+         sizeof(tg_step_inputs), sizeof(tg_noise_group));
+  printf("%zu %zu %zu\n", offsetof(tg_scene_desc, params), offsetof(tg_scene_desc, sensors),
+         offsetof(tg_object_desc, values));
+  return 0; }
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(prog)
+        exe = os.path.join(d, "t")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    sizes = [int(v) for v in out]
+    assert sizes[:5] == [ctypes.sizeof(tg.Params), ctypes.sizeof(tg.SceneDesc), ctypes.sizeof(tg.ObjectDesc),
+                         ctypes.sizeof(tg.StepInputs), ctypes.sizeof(tg.NoiseGroup)]
+    assert sizes[5:] == [tg.SceneDesc.params.offset, tg.SceneDesc.sensors.offset, tg.ObjectDesc.values.offset]
+
+
+def test_max_link_taxels(libpath):
+    import paper_2606_22332_gb300.tg as tg
+
+    assert tg.lib().tg_max_link_taxels() >= 1000
