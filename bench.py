@@ -1,0 +1,385 @@
+#!/usr/bin/env python3
+"""Throughput of the tactile sensor step on GB300: taxel-queries/s.
+
+Workload (default ``metric_run``): 20,480 envs x 20 capsule links x 50
+taxels (1,000 per env, 20.48M active taxel queries per step), 64 procedural
+objects (superquadrics and convex hulls, 3k-6k faces) as 96^3 FP16 SDF grids
+baked on the GPU from the exact meshes, the full noise model (dead taxels,
+hysteresis, 3x3 crosstalk, drift).  One step = the pose prologue kernel + the
+fused sensor kernel over every env; a taxel query is one active
+(env, taxel) pair of one step.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl tg|reference]
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the reference arm of this build).  Under torchrun
+(N > 1) every rank runs its own shard of envs with no collective on the data
+path (weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "taxel-queries/s at 20,480 envs×1,000 taxels; neural-SDF vs plain at ≤0.2 mm"
+UNIT = "taxel-queries/s"
+
+# Algorithmic HBM bytes per taxel query of the fused step kernel (itemised in
+# the design doc): taxel position + radius 16, flag byte r/w 2, hysteresis x_{t-1}
+# and xi for 7 channels r/w 112, drift for 6 channels r/w 48, outputs 58
+# (clean/noisy depth, clean/noisy force/torque), per-link pose records and
+# link outputs amortised over 50 taxels 4.8.  Contact taxels additionally read
+# their normal (12 B) for agg_force; counted with the measured contact share.
+BYTES_PER_QUERY_BASE = 16 + 2 + 112 + 48 + 58 + 4.8
+BYTES_NORMAL = 12.0
+SURVEY_BYTES_PER_QUERY = 251.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["tg", "reference"], default="tg")
+    ap.add_argument("--workload", choices=["metric_run", "config2"], default="metric_run")
+    ap.add_argument("--envs", type=int, default=20480)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--oracle-envs", type=int, default=400, help="env sample of the CPU oracle legs")
+    ap.add_argument("--oracle-steps", type=int, default=10)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(args, rank=0):
+    from paper_2606_22332_gb300 import workload as W
+
+    if args.workload == "metric_run":
+        return W.metric_run(n_envs=args.envs)
+    return W.config2(n_envs=args.envs)
+
+
+def workload_config(args, wl):
+    return {
+        "workload": (f"{args.workload}: {wl.n_envs} envs x {wl.max_links} links, "
+                     f"{wl.n_active // wl.n_envs} active taxels/env, 64 objects as 96^3 FP16 SDF grids "
+                     "(exact-mesh bake), full noise model (dead 2%, hysteresis 0.1, 3x3 crosstalk 0.05, drift 1e-3)"),
+        "envs_per_gpu": wl.n_envs,
+        "active_taxels_per_gpu": wl.n_active,
+        "grid": "96^3 fp16",
+        "objects": len(wl.objects),
+        "l2": "no flush: every step streams ~4.8 GB of taxel state/outputs, far above the 129 MB L2",
+    }
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle legs (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+class OracleSample:
+    """Bounded sample of the workload for the CPU oracle: the envs that use the
+    object with the fewest faces (at most `oracle_envs` of them), whose 96^3
+    grid the oracle bakes itself from the exact mesh (untimed)."""
+
+    def __init__(self, args, wl):
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+        from _scenes import bake_objects_oracle, oracle_scene
+
+        counts = np.bincount(wl.obj_id, minlength=len(wl.objects))
+        cand = [k for k in range(len(wl.objects)) if counts[k] > 0]
+        k = min(cand, key=lambda i: len(wl.objects[i].faces))
+        envs = np.flatnonzero(wl.obj_id == k)[: args.oracle_envs]
+        sub = wl.subset(envs)
+        t0 = time.time()
+        baked = bake_objects_oracle([wl.objects[k]])[0]
+        self.bake_s = time.time() - t0
+        sub.objects = [baked] * len(wl.objects)  # the subset references object k only
+        self.sub, self.k, self.n_envs = sub, k, len(envs)
+        self.faces = len(wl.objects[k].faces)
+        self.sc = oracle_scene(sub)
+        self.st = self.sc.new_state()
+        self.sc.reset(self.st, 0)
+        self.threads = os.cpu_count() or 1
+        self.t = 0
+
+    def step_seconds(self):
+        t0 = time.time()
+        self.sc.step(self.st, self.sub.inputs(self.t), threads=self.threads)
+        self.t += 1
+        return time.time() - t0
+
+    def describe(self, steps, secs):
+        q = self.sub.n_active * steps
+        return (f"{self.n_envs} envs x {self.sub.n_active // max(self.n_envs, 1)} taxels x {steps} steps of the same "
+                f"workload (the envs of object {self.k}, {self.faces} faces; its 96^3 grid baked exactly by the "
+                f"oracle in {self.bake_s:.1f} s, untimed); {q} queries in {secs:.2f} s")
+
+
+def oracle_baseline(args, wl):
+    o = OracleSample(args, wl)
+    secs = sum(o.step_seconds() for _ in range(args.oracle_steps))
+    q = o.sub.n_active * args.oracle_steps
+    return {"value": q / secs, "unit": UNIT, "cores": o.threads, "kind": "oracle",
+            "sample": o.describe(args.oracle_steps, secs)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    wl = make_workload(args)
+    o = OracleSample(args, wl)
+    for _ in range(args.warmup):
+        o.step_seconds()
+    secs = sum(o.step_seconds() for _ in range(args.steps))
+    value = o.sub.n_active * args.steps / secs
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args, wl), "impl": "reference",
+        "cpu_baseline": {"kind": "oracle", "cores": o.threads, "sample": o.describe(args.steps, secs),
+                         "value": value, "unit": UNIT},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    def __init__(self, path):
+        self.path = path
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0],
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            self.p.wait()
+            self.f.close()
+
+    def summary(self):
+        if self.p is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [t.strip() for t in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]) if parts[3] not in ("[N/A]", "N/A") else 0.0,
+                             parts[5], parts[6], parts[7], parts[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        pmax = max(r[2] for r in rows)
+        load = [r for r in rows if r[2] >= 0.5 * pmax] or rows
+        reasons = set()
+        for r in load:
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), r[3:]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median([r[0] for r in load])), "sm_max_mhz": float(max(r[1] for r in rows)),
+                "reasons": sorted(reasons), "samples": len(rows), "power_w_max": pmax}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_from_profile(kernel_source):
+    """dram bytes per launch of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    sha = hashlib.sha256(open(kernel_source, "rb").read()).hexdigest()[:16]
+    rec = d.get("step_kernel")
+    if not rec or rec.get("source_sha") != sha:
+        return None
+    return rec.get("dram_bytes_per_launch_full")
+
+
+def run_tg(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    import paper_2606_22332_gb300.tg as tg
+    from paper_2606_22332_gb300 import workload as W
+
+    t_setup = time.time()
+    wl = make_workload(args, rank)
+    E, T = wl.n_envs, wl.n_taxels
+    # objects: the exact-mesh bake of every grid on the GPU
+    objs = []
+    for o in wl.objects:
+        vals = tg.bake_grid(o.verts, o.faces, o.dims, o.lo, o.hi, fp16=o.fp16)
+        objs.append(W.ObjectSpec(kind="grid", dims=o.dims, lo=o.lo, hi=o.hi, fp16=o.fp16, values=vals, name=o.name))
+    torch.cuda.synchronize()
+    bake_s = time.time() - t_setup
+    scene = tg.Scene(wl.geom(), wl.params, taxel_gid0=rank * T, env_gid0=rank * E)
+    scene.upload_objects(objs)
+    del objs
+    d_in = {k: torch.as_tensor(getattr(wl, k)).to(dev) for k in ("link_pose", "link_vel", "obj_pose", "obj_vel", "obj_id")}
+    stream = torch.cuda.current_stream()
+    dt = wl.params["dt"]
+
+    def step_inputs(t, src):
+        return dict(src, pose_dt=t * dt, step=t)
+
+    scene.profile(True)
+    for t in range(args.warmup):
+        scene.step(step_inputs(t, d_in))
+    torch.cuda.synchronize()
+    scene.sync()
+    scene.profile_read()
+    contact_share = float((scene.read(tg.CH_STATE_FLAGS) & 1).sum()) / max(wl.n_active, 1)
+    depth = scene.buffer(tg.CH_DEPTH)
+    pen_share = float((depth > 0).sum().item()) / max(wl.n_active, 1)
+
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else f"/tmp/tg_clocks_{os.getpid()}.csv")
+    with clk:
+        ev0.record(stream)
+        for t in range(args.warmup, args.warmup + args.steps):
+            scene.step(step_inputs(t, d_in))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ms = ev0.elapsed_time(ev1)
+    pose_ms, step_ms, nsteps = scene.profile_read()
+    scene.sync()
+    t_max = ms
+    if pg:
+        tt = torch.tensor([ms], device=dev)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        t_max = float(tt.item())
+    n_q = wl.n_active * ws
+    value = n_q * args.steps / (t_max / 1e3)
+
+    # e2e: host inputs through the C-ABI (H2D inside), per-link results read back to host
+    e2e = None
+    if not args.no_e2e:
+        pinned = {k: torch.as_tensor(getattr(wl, k)).pin_memory() for k in d_in}
+        out_w = torch.empty((E * wl.max_links, tg.LINK_REC), dtype=torch.float32).pin_memory()
+        out_c = torch.empty((E * wl.max_links, 2), dtype=torch.int32).pin_memory()
+        h2d = sum(v.numel() * v.element_size() for v in pinned.values())
+        d2h = out_w.numel() * 4 + out_c.numel() * 4
+        k2 = args.steps
+        base = args.warmup
+        scene.step(step_inputs(base - 1, pinned))
+        scene.read(tg.CH_LINK_WRENCH, out=out_w)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for t in range(base, base + k2):  # the same step indices (same poses) as the device-timed region
+            scene.step(step_inputs(t, pinned))
+            scene.read(tg.CH_LINK_WRENCH, out=out_w)
+            scene.read(tg.CH_LINK_COUNT, out=out_c)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1)
+        if pg:
+            tt = torch.tensor([ems], device=dev)
+            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+            ems = float(tt.item())
+        e2e = {"value": n_q * k2 / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h),
+               "note": "time-0 poses/velocities copied from pinned host memory every step (the C-ABI stages them); "
+                       "per-link wrench sums and contact counts (agg_force / agg_bool observations) read back to "
+                       "pinned host memory every step; same step indices as the device-timed region"}
+
+    peak, peak_kind = peaks()
+    bpq = BYTES_PER_QUERY_BASE + BYTES_NORMAL * pen_share
+    step_avg_ms = step_ms / max(nsteps, 1)
+    achieved = bpq * wl.n_active / (step_avg_ms / 1e3) / 1e9
+    traffic = traffic_from_profile(os.path.join(ROOT, "paper_2606_22332_gb300", "csrc", "step.cu"))
+    roofline = {
+        "bound": "hbm", "kernel": "step_kernel", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+        "frac": round(achieved / peak, 4), "peak_kind": peak_kind, "traffic": traffic,
+        "algorithmic_bytes_per_query": round(bpq, 2), "survey_bytes_per_query": SURVEY_BYTES_PER_QUERY,
+        "step_kernel_ms": round(step_avg_ms, 4), "pose_kernel_ms": round(pose_ms / max(nsteps, 1), 4),
+        "step_kernel_share": round(step_ms / max(step_ms + pose_ms, 1e-9), 4),
+    }
+    clocks = clk.summary()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = oracle_baseline(args, wl)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic", "config": workload_config(args, wl), "clocks": clocks,
+            "e2e": e2e, "gpu_launches": 2 * args.steps, "roofline": roofline, "cpu_baseline": cpu,
+            "contact_share": round(contact_share, 4), "penetrating_share": round(pen_share, 4),
+            "setup_s": {"bake": round(bake_s, 2), "total": round(time.time() - t_setup, 1)},
+        }
+        print(json.dumps(out))
+    scene.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_tg(args)
+
+
+if __name__ == "__main__":
+    main()

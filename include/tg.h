@@ -199,6 +199,14 @@ const char* tg_last_error(const tg_scene* scene);
 tg_status tg_save_state(tg_scene* scene, void* buf, size_t* size);
 tg_status tg_load_state(tg_scene* scene, const void* buf, size_t size);
 
+/* Kernel timing for measurement.  While enabled, every tg_step_sensors
+   records CUDA events on its stream around its two kernels (the pose
+   prologue and the fused step).  tg_profile_read waits for the recorded
+   events and returns the summed device time in milliseconds of each kernel
+   and the number of steps since the previous read, then clears them. */
+tg_status tg_profile_enable(tg_scene* scene, int32_t on);
+tg_status tg_profile_read(tg_scene* scene, double* pose_ms, double* step_ms, int64_t* n_steps);
+
 /* Exact signed distance to a closed, outward-oriented triangle mesh sampled
    at the nodes of a grid (the grid bake that turns a mesh into a
    TG_OBJ_GRID): unsigned distance by closest point over every face, negative

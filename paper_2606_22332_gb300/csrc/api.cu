@@ -46,6 +46,10 @@ struct tg_scene {
     uint8_t* s_mask = nullptr;
     uint8_t* s_contact = nullptr;
     std::string last_error;
+    // kernel timing (tg_profile_*)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<cudaEvent_t> ev_pending;   // triples: before pose, after pose, after step
 };
 
 namespace {
@@ -395,6 +399,8 @@ void tg_destroy_scene(tg_scene* s) {
     if (!s) return;
     cudaDeviceSynchronize();
     free_objects(s);
+    for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : s->ev_pending) cudaEventDestroy(e);
     void* ptrs[] = {s->x, s->y, s->z, s->nx, s->ny, s->nz, s->R, s->items, s->lattice, s->flags, s->hyst_prev,
                     s->hyst_xi, s->drift, s->episode, s->depth_clean, s->depth_noisy, s->dist, s->ft_clean,
                     s->ft_noisy, s->link_out, s->link_count, s->err, s->link_rec, s->s_link_pose, s->s_link_vel,
@@ -527,11 +533,53 @@ tg_status tg_step_sensors(tg_scene* s, const tg_step_inputs* in, tg_stream strea
     pa.tau_hi = (float)in->pose_dt;
     pa.tau_lo = (float)(in->pose_dt - (double)pa.tau_hi);
     pa.link_rec = s->link_rec;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    if (s->profiling) {
+        for (int i = 0; i < 3; ++i) {
+            if (s->ev_pool.empty()) {
+                CK(s, cudaEventCreate(&ev[i]));
+            } else {
+                ev[i] = s->ev_pool.back();
+                s->ev_pool.pop_back();
+            }
+            s->ev_pending.push_back(ev[i]);
+        }
+        CK(s, cudaEventRecord(ev[0], st));
+    }
     CK(s, launch_pose(pa, st));
+    if (s->profiling) CK(s, cudaEventRecord(ev[1], st));
     StepArgs a = step_args(s);
     a.obj_id = oid;
     a.step = in->step;
     CK(s, launch_step(a, s->n_items, st));
+    if (s->profiling) CK(s, cudaEventRecord(ev[2], st));
+    return TG_OK;
+}
+
+tg_status tg_profile_enable(tg_scene* s, int32_t on) {
+    if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
+    s->profiling = on != 0;
+    return TG_OK;
+}
+
+tg_status tg_profile_read(tg_scene* s, double* pose_ms, double* step_ms, int64_t* n_steps) {
+    if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
+    double tp = 0.0, ts = 0.0;
+    const size_t n = s->ev_pending.size() / 3;
+    for (size_t i = 0; i < n; ++i) {
+        cudaEvent_t* e = &s->ev_pending[3 * i];
+        CK(s, cudaEventSynchronize(e[2]));
+        float a = 0.f, b = 0.f;
+        CK(s, cudaEventElapsedTime(&a, e[0], e[1]));
+        CK(s, cudaEventElapsedTime(&b, e[1], e[2]));
+        tp += a;
+        ts += b;
+    }
+    for (cudaEvent_t e : s->ev_pending) s->ev_pool.push_back(e);
+    s->ev_pending.clear();
+    if (pose_ms) *pose_ms = tp;
+    if (step_ms) *step_ms = ts;
+    if (n_steps) *n_steps = (int64_t)n;
     return TG_OK;
 }
 

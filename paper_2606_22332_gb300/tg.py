@@ -88,15 +88,18 @@ _lib.tg_last_error.argtypes = [_vp]
 _lib.tg_last_error.restype = C.c_char_p
 _lib.tg_save_state.argtypes = [_vp, _vp, C.POINTER(_sz)]
 _lib.tg_load_state.argtypes = [_vp, _vp, _sz]
+_lib.tg_profile_enable.argtypes = [_vp, _i32]
+_lib.tg_profile_read.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int64)]
 _lib.tg_bake_grid.argtypes = [_vp, _i32, _vp, _i32, _vp, _vp, _vp, _i32, _vp, _vp]
 _lib.tg_mesh_sdf.argtypes = [_vp, _i32, _vp, _i32, _vp, C.c_int64, _vp, _vp, _vp]
 for _f in ("tg_create_scene", "tg_upload_objects", "tg_reset_envs", "tg_step_sensors", "tg_read_taxels",
-           "tg_get_buffer", "tg_sync", "tg_save_state", "tg_load_state", "tg_bake_grid", "tg_mesh_sdf"):
+           "tg_get_buffer", "tg_sync", "tg_save_state", "tg_load_state", "tg_bake_grid", "tg_mesh_sdf",
+           "tg_profile_enable", "tg_profile_read"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ["tg_create_scene", "tg_destroy_scene", "tg_max_link_taxels", "tg_upload_objects", "tg_reset_envs",
             "tg_step_sensors", "tg_read_taxels", "tg_channel_bytes", "tg_get_buffer", "tg_sync", "tg_last_error",
-            "tg_save_state", "tg_load_state", "tg_bake_grid", "tg_mesh_sdf"]
+            "tg_save_state", "tg_load_state", "tg_bake_grid", "tg_mesh_sdf", "tg_profile_enable", "tg_profile_read"]
 
 
 def lib():
@@ -284,6 +287,15 @@ class Scene:
 
     def sync(self, stream=None):
         _check(_lib.tg_sync(self.h, _stream(stream)), self.h)
+
+    def profile(self, on: bool = True):
+        _check(_lib.tg_profile_enable(self.h, int(on)), self.h)
+
+    def profile_read(self):
+        """(pose kernel ms, step kernel ms, steps) summed since the last read."""
+        a, b, n = C.c_double(), C.c_double(), C.c_int64()
+        _check(_lib.tg_profile_read(self.h, C.byref(a), C.byref(b), C.byref(n)), self.h)
+        return a.value, b.value, n.value
 
     def save_state(self) -> bytes:
         n = C.c_size_t()

@@ -314,62 +314,135 @@ def capsule_lattice(rows: int, cols: int, radius: float, length: float, n_active
     return [a.reshape(-1) for a in (x, y, zz, nx, ny, nz)] + [Rr]
 
 
+def random_rotations(rng, n: int) -> np.ndarray:
+    """n Haar-uniform rotation matrices (batched QR of Gaussian matrices)."""
+    A = rng.standard_normal((n, 3, 3))
+    Q, Rr = np.linalg.qr(A)
+    Q = Q * np.sign(np.diagonal(Rr, axis1=1, axis2=2))[:, None, :]
+    neg = np.linalg.det(Q) < 0
+    Q[neg, :, 0] = -Q[neg, :, 0]
+    return Q
+
+
+def mats_to_quats(M: np.ndarray) -> np.ndarray:
+    """Batched mat_to_quat."""
+    out = np.empty(M.shape[:-2] + (4,))
+    flat = M.reshape(-1, 3, 3)
+    o = out.reshape(-1, 4)
+    t = np.trace(flat, axis1=1, axis2=2)
+    c0 = t > 0
+    c1 = ~c0 & (flat[:, 0, 0] > flat[:, 1, 1]) & (flat[:, 0, 0] > flat[:, 2, 2])
+    c2 = ~c0 & ~c1 & (flat[:, 1, 1] > flat[:, 2, 2])
+    c3 = ~c0 & ~c1 & ~c2
+    m = flat
+    with np.errstate(invalid="ignore", divide="ignore"):
+        s = np.sqrt(np.maximum(t + 1.0, 0)) * 2
+        q0 = np.stack([0.25 * s, (m[:, 2, 1] - m[:, 1, 2]) / s, (m[:, 0, 2] - m[:, 2, 0]) / s, (m[:, 1, 0] - m[:, 0, 1]) / s], 1)
+        s = np.sqrt(np.maximum(1.0 + m[:, 0, 0] - m[:, 1, 1] - m[:, 2, 2], 0)) * 2
+        q1 = np.stack([(m[:, 2, 1] - m[:, 1, 2]) / s, 0.25 * s, (m[:, 0, 1] + m[:, 1, 0]) / s, (m[:, 0, 2] + m[:, 2, 0]) / s], 1)
+        s = np.sqrt(np.maximum(1.0 + m[:, 1, 1] - m[:, 0, 0] - m[:, 2, 2], 0)) * 2
+        q2 = np.stack([(m[:, 0, 2] - m[:, 2, 0]) / s, (m[:, 0, 1] + m[:, 1, 0]) / s, 0.25 * s, (m[:, 1, 2] + m[:, 2, 1]) / s], 1)
+        s = np.sqrt(np.maximum(1.0 + m[:, 2, 2] - m[:, 0, 0] - m[:, 1, 1], 0)) * 2
+        q3 = np.stack([(m[:, 1, 0] - m[:, 0, 1]) / s, (m[:, 0, 2] + m[:, 2, 0]) / s, (m[:, 1, 2] + m[:, 2, 1]) / s, 0.25 * s], 1)
+    o[c0], o[c1], o[c2], o[c3] = q0[c0], q1[c1], q2[c2], q3[c3]
+    o /= np.linalg.norm(o, axis=1, keepdims=True)
+    return out
+
+
+def _unit(v):
+    return v / np.linalg.norm(v, axis=-1, keepdims=True)
+
+
 def _assemble(name, rng, objects, env_obj, env_lattices, params, steps, press_frac=(0.5, 1.0),
               press_depth=(0.0, 2e-3), gap=(2e-3, 2e-2), max_links=None, arc=2 * np.pi):
-    """Place every env's links around its object and stack the arrays.
+    """Place every env's links around its object and build the arrays.
 
     env_lattices[e] is a list of (rows, cols, n_active) per link.  Each link is
     a capsule (radius 8-12 mm, cylinder 20-45 mm) whose lattice arc faces the
     object and whose side is pressed into the object's support plane by
     U(press_depth) with probability U(press_frac) per env, otherwise held off
-    by U(gap)."""
+    by U(gap).  Vectorised over envs and links."""
     E = len(env_lattices)
     L = max_links or max(len(lat) for lat in env_lattices)
-    xs, ys, zs, nxs, nys, nzs, Rs = ([] for _ in range(7))
-    rows = np.zeros(E * L, np.int32); cols = np.zeros(E * L, np.int32); wrap = np.zeros(E * L, np.uint8)
-    link_pose = np.zeros((E, L, 7), np.float32); link_pose[:, :, 3] = 1.0
-    link_vel = np.zeros((E, L, 6), np.float32)
-    obj_pose = np.zeros((E, 7), np.float32); obj_vel = np.zeros((E, 6), np.float32)
-    offsets = [0]
-    for e in range(E):
-        obj = objects[env_obj[e]]
-        RC = random_rotation(rng)
-        pC = rng.normal(0.0, 0.005, 3)
-        obj_pose[e, :3] = pC
-        obj_pose[e, 3:] = mat_to_quat(RC)
-        obj_vel[e, :3] = rng.normal(0.0, 0.1, 3)
-        obj_vel[e, 3:] = rng.normal(0.0, 1.0, 3)
-        pf = rng.uniform(*press_frac)
-        n_e = 0
-        for l, (rr, cc, na) in enumerate(env_lattices[e]):
-            rc = rng.uniform(8e-3, 12e-3)
-            ln = rng.uniform(20e-3, 45e-3)
-            lat = capsule_lattice(rr, cc, rc, ln, na, arc)
-            for lst, arr in zip((xs, ys, zs, nxs, nys, nzs, Rs), lat):
-                lst.append(arr)
-            rows[e * L + l], cols[e * L + l] = rr, cc
-            wrap[e * L + l] = 1 if arc >= 2 * np.pi else 0
-            n_e += rr * cc
-            u = unit(rng.standard_normal(3))
-            h = float(pC @ u) + support(obj, RC, u)
-            delta = rng.uniform(*press_depth) if rng.uniform() < pf else -rng.uniform(*gap)
-            centre = (h + rc - delta) * u
-            axis = unit(np.cross(u, rng.standard_normal(3)))
-            e1 = -u                      # lattice column 0 faces the object
-            e2 = np.cross(axis, e1)
-            RL = np.stack([e1, e2, axis], axis=1)
-            link_pose[e, l, :3] = centre
-            link_pose[e, l, 3:] = mat_to_quat(RL)
-            link_vel[e, l, :3] = rng.normal(0.0, 0.1, 3)
-            link_vel[e, l, 3:] = rng.normal(0.0, 1.0, 3)
-        offsets.append(offsets[-1] + n_e)
-    cat = lambda lst: f32(np.concatenate(lst)) if lst else np.zeros(0, np.float32)
-    off = np.asarray(offsets, np.int64)
+    rows = np.zeros((E, L), np.int32); cols = np.zeros((E, L), np.int32); nact = np.zeros((E, L), np.int64)
+    uniform = all(lat == env_lattices[0] for lat in env_lattices[1:]) if E > 1 else True
+    if uniform and env_lattices[0]:
+        lat = np.asarray(env_lattices[0], np.int64)
+        rows[:, :len(lat)], cols[:, :len(lat)], nact[:, :len(lat)] = lat[:, 0], lat[:, 1], lat[:, 2]
+    else:
+        for e, lat in enumerate(env_lattices):
+            for l, (r, c, na) in enumerate(lat):
+                rows[e, l], cols[e, l], nact[e, l] = r, c, na
+    env_obj = np.asarray(env_obj, np.int64)
+    # object poses
+    RC = random_rotations(rng, E)
+    pC = rng.normal(0.0, 0.005, (E, 3))
+    obj_pose = np.zeros((E, 7), np.float32)
+    obj_pose[:, :3] = pC
+    obj_pose[:, 3:] = mats_to_quats(RC)
+    obj_vel = np.concatenate([rng.normal(0.0, 0.1, (E, 3)), rng.normal(0.0, 1.0, (E, 3))], 1).astype(np.float32)
+    # links
+    pf = rng.uniform(*press_frac, E)
+    rc = rng.uniform(8e-3, 12e-3, (E, L))
+    ln = rng.uniform(20e-3, 45e-3, (E, L))
+    u = _unit(rng.standard_normal((E, L, 3)))
+    pressed = rng.uniform(size=(E, L)) < pf[:, None]
+    delta = np.where(pressed, rng.uniform(*press_depth, (E, L)), -rng.uniform(*gap, (E, L)))
+    d_obj = np.einsum("eji,elj->eli", RC, u)          # directions in each object's frame
+    h = np.einsum("ei,eli->el", pC, u)
+    for k, obj in enumerate(objects):
+        sel = env_obj == k
+        if not sel.any():
+            continue
+        dk = d_obj[sel]
+        if obj.kind == "sphere":
+            h[sel] += float(obj.radius)
+        elif obj.kind == "box":
+            h[sel] += np.abs(dk) @ np.asarray(obj.half, np.float64)
+        elif obj.kind == "plane":
+            h[sel] += 0.0
+        else:
+            Vd = obj.verts.astype(np.float64)
+            h[sel] += (dk.reshape(-1, 3) @ Vd.T).max(axis=1).reshape(dk.shape[:2])
+    centre = (h + rc - delta)[..., None] * u
+    axis = _unit(np.cross(u, rng.standard_normal((E, L, 3))))
+    e1 = -u                                            # lattice column 0 faces the object
+    e2 = np.cross(axis, e1)
+    RL = np.stack([e1, e2, axis], axis=-1)
+    link_pose = np.zeros((E, L, 7), np.float32)
+    link_pose[..., 3] = 1.0
+    link_pose[..., :3] = centre
+    link_pose[..., 3:] = mats_to_quats(RL)
+    link_vel = np.concatenate([rng.normal(0.0, 0.1, (E, L, 3)), rng.normal(0.0, 1.0, (E, L, 3))], -1).astype(np.float32)
+    absent = rows * cols == 0
+    link_pose[absent] = (0, 0, 0, 1, 0, 0, 0)
+    link_vel[absent] = 0
+    # taxels of every link lattice, in CSR order
+    n_link = (rows.astype(np.int64) * cols).reshape(-1)
+    starts = np.concatenate([[0], np.cumsum(n_link)])
+    T = int(starts[-1])
+    link_of = np.repeat(np.arange(E * L), n_link)
+    j = np.arange(T) - starts[link_of]
+    cl = cols.reshape(-1)[link_of].astype(np.int64)
+    rl = rows.reshape(-1)[link_of].astype(np.int64)
+    rr, cc = j // cl, j % cl
+    if arc >= 2 * np.pi:
+        th = 2 * np.pi * cc / cl
+    else:
+        th = -arc / 2 + arc * (cc + 0.5) / cl
+    radius = rc.reshape(-1)[link_of]
+    length = ln.reshape(-1)[link_of]
+    x = radius * np.cos(th); y = radius * np.sin(th)
+    z = -length / 2 + (rr + 0.5) * length / rl
+    Rt = np.where(j < nact.reshape(-1)[link_of], TAXEL_RADIUS, 0.0)
+    off = np.concatenate([[0], np.cumsum(n_link.reshape(E, L).sum(1))]).astype(np.int64)
+    wrap = np.full(E * L, 1 if arc >= 2 * np.pi else 0, np.uint8)
+    wrap[absent.reshape(-1)] = 0
     return Workload(
         name=name, n_envs=E, max_links=L, taxel_offsets=off, taxel_gid0=off[:-1].copy(),
-        env_gid=np.arange(E, dtype=np.int32), link_rows=rows, link_cols=cols, link_wrap=wrap,
-        x=cat(xs), y=cat(ys), z=cat(zs), nx=cat(nxs), ny=cat(nys), nz=cat(nzs), R=cat(Rs),
-        objects=objects, obj_id=np.asarray(env_obj, np.int32), link_pose=link_pose, link_vel=link_vel,
+        env_gid=np.arange(E, dtype=np.int32), link_rows=rows.reshape(-1), link_cols=cols.reshape(-1), link_wrap=wrap,
+        x=f32(x), y=f32(y), z=f32(z), nx=f32(np.cos(th)), ny=f32(np.sin(th)), nz=f32(np.zeros(T)), R=f32(Rt),
+        objects=objects, obj_id=env_obj.astype(np.int32), link_pose=link_pose, link_vel=link_vel,
         obj_pose=obj_pose, obj_vel=obj_vel, params=params, steps=steps,
     )
 

@@ -3,7 +3,11 @@
 Tolerances (stated for the hot path):
   contact flags, dead masks, RNG-driven bits   bit-exact
   depth, noisy depth, surface distance         |d_gpu - d_ora| <= 1e-5 m
-  force/torque (clean and noisy)               |f_gpu - f_ora| <= 1e-4 |f_ora| + 1e-6
+  force/torque (clean and noisy)               per 3-vector (force, torque):
+                                               |f_gpu - f_ora| <= 1e-4 |f_ora| + 1e-6
+                                               (Euclidean norms; a float32 component of
+                                               a 20 N vector is itself only resolved to
+                                               ~2e-6 N, so the bound is on the vector)
   per-link sums                                the per-taxel bound summed over the
                                                link: 1e-4 sum|f_j| + 1e-6 n_link
 Contact bits are decided by the depth against eta_on / eta_off; a taxel
@@ -62,22 +66,30 @@ def compare_step(gpu, ora, ostate, params, wl, active=None, where=""):
         err = np.abs(gpu["dist"].astype(np.float64) - ora["dist"])
         stats["dist"] = float(err.max()) if err.size else 0.0
         assert stats["dist"] <= D_ABS, f"{where}: dist max err {stats['dist']:.3e}"
-    # force/torque
+    # force/torque, per 3-vector
     for k in ("ft_clean", "ft_noisy"):
         g, o = gpu[k].astype(np.float64), ora[k]
-        err = np.abs(g - o)
-        tol = F_REL * np.abs(o) + F_ABS
-        ratio = err / tol
-        stats[k] = float(ratio.max()) if ratio.size else 0.0
-        stats[k + "_abs"] = float(err.max()) if err.size else 0.0
-        if stats[k] > 1.0:
-            idx = np.unravel_index(np.argmax(ratio), ratio.shape)
-            raise AssertionError(f"{where}: {k} err {err[idx]:.3e} > tol {tol[idx]:.3e} at {idx}: gpu {g[idx]} oracle {o[idx]}"
-                                 f" depth {d_or[idx[1]]:.3e}")
+        for part, rows in (("force", slice(0, 3)), ("torque", slice(3, 6))):
+            err = np.linalg.norm(g[rows] - o[rows], axis=0)
+            tol = F_REL * np.linalg.norm(o[rows], axis=0) + F_ABS
+            ratio = err / tol
+            key = f"{k}_{part}"
+            stats[key] = float(ratio.max()) if ratio.size else 0.0
+            stats[key + "_abs"] = float(err.max()) if err.size else 0.0
+            if stats[key] > 1.0:
+                i = int(np.argmax(ratio))
+                raise AssertionError(f"{where}: {key} err {err[i]:.3e} > tol {tol[i]:.3e} at taxel {i}: "
+                                     f"gpu {g[rows, i]} oracle {o[rows, i]} depth {d_or[i]:.3e}")
     # per-link sums
     L = wl.max_links
     off = wl.taxel_offsets
-    absf = {"c": np.abs(ora["ft_clean"]), "n": np.abs(ora["ft_noisy"])}
+    # per-taxel vector magnitudes (force rows 0-2, torque rows 3-5)
+    def mags(a):
+        m = np.empty_like(a)
+        m[0:3] = np.linalg.norm(a[0:3], axis=0)
+        m[3:6] = np.linalg.norm(a[3:6], axis=0)
+        return m
+    absf = {"c": mags(ora["ft_clean"]), "n": mags(ora["ft_noisy"])}
     ls_g, ls_o = gpu["link_sums"].astype(np.float64), ora["link_sums"]
     worst = 0.0
     for e in range(wl.n_envs):
