@@ -201,9 +201,11 @@ tg_status tg_load_state(tg_scene* scene, const void* buf, size_t size);
 
 /* Kernel timing for measurement.  While enabled, every tg_step_sensors
    records CUDA events on its stream around its two kernels (the pose
-   prologue and the fused step).  tg_profile_read waits for the recorded
-   events and returns the summed device time in milliseconds of each kernel
-   and the number of steps since the previous read, then clears them. */
+   prologue: pose advance and the object-sorted work order; and the fused
+   step).  tg_profile_read waits for the recorded events and returns the
+   summed device time in milliseconds of the prologue kernels and of the
+   step kernel, and the number of steps since the previous read, then clears
+   them. */
 tg_status tg_profile_enable(tg_scene* scene, int32_t on);
 tg_status tg_profile_read(tg_scene* scene, double* pose_ms, double* step_ms, int64_t* n_steps);
 

@@ -45,6 +45,7 @@ struct tg_scene {
     int32_t* s_obj_id = nullptr;
     uint8_t* s_mask = nullptr;
     uint8_t* s_contact = nullptr;
+    int32_t* item_order = nullptr;    // per-step object-sorted item order
     std::string last_error;
     // kernel timing (tg_profile_*)
     bool profiling = false;
@@ -376,6 +377,7 @@ tg_status tg_create_scene(const tg_scene_desc* d, tg_scene** out) {
     CKC(dalloc(&s->s_obj_id, E));
     CKC(dalloc(&s->s_mask, E));
     CKC(dalloc(&s->s_contact, T));
+    CKC(dalloc(&s->item_order, items.size()));
     CKC(cudaMemset(s->link_out, 0, EL * kLinkOut * sizeof(float)));
     CKC(cudaMemset(s->link_count, 0, EL * 2 * sizeof(int32_t)));
     CKC(cudaMemset(s->err, 0, 4 * sizeof(unsigned)));
@@ -404,7 +406,8 @@ void tg_destroy_scene(tg_scene* s) {
     void* ptrs[] = {s->x, s->y, s->z, s->nx, s->ny, s->nz, s->R, s->items, s->lattice, s->flags, s->hyst_prev,
                     s->hyst_xi, s->drift, s->episode, s->depth_clean, s->depth_noisy, s->dist, s->ft_clean,
                     s->ft_noisy, s->link_out, s->link_count, s->err, s->link_rec, s->s_link_pose, s->s_link_vel,
-                    s->s_obj_pose, s->s_obj_vel, s->s_env_params, s->s_obj_id, s->s_mask, s->s_contact};
+                    s->s_obj_pose, s->s_obj_vel, s->s_env_params, s->s_obj_id, s->s_mask, s->s_contact,
+                    s->item_order};
     for (void* p : ptrs) dfree(p);
     delete s;
 }
@@ -547,10 +550,15 @@ tg_status tg_step_sensors(tg_scene* s, const tg_step_inputs* in, tg_stream strea
         CK(s, cudaEventRecord(ev[0], st));
     }
     CK(s, launch_pose(pa, st));
-    if (s->profiling) CK(s, cudaEventRecord(ev[1], st));
     StepArgs a = step_args(s);
     a.obj_id = oid;
     a.step = in->step;
+    a.item_order = nullptr;
+    if (s->n_objects > 1 && s->n_objects <= 12288) {
+        CK(s, launch_order_items(s->items, s->n_items, oid, s->n_objects, s->item_order, st));
+        a.item_order = s->item_order;
+    }
+    if (s->profiling) CK(s, cudaEventRecord(ev[1], st));
     CK(s, launch_step(a, s->n_items, st));
     if (s->profiling) CK(s, cudaEventRecord(ev[2], st));
     return TG_OK;

@@ -35,10 +35,32 @@ __device__ __forceinline__ float3 normalize_or(float3 v, float3 fallback) {
 }
 
 // ------------------------------------------------------------------ grids
+// Grid values are re-read by every env that holds the object, while the
+// per-taxel state streams through L2 once per step: grid loads carry an
+// evict-last L2 policy so the grids stay resident under the stream.
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ float ld_grid_f32(const float* p, uint64_t pol) {
+    float v;
+    asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ float ld_grid_f16(const __half* p, uint64_t pol) {
+    unsigned short v;
+    asm("ld.global.nc.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
+    return __half2float(__ushort_as_half(v));
+}
+
 __device__ __forceinline__ float grid_value(const ObjDev& o, int i, int j, int k) {
     size_t idx = ((size_t)k * o.dims[1] + j) * o.dims[0] + i;
-    if (o.fp16) return __half2float(__ldg(reinterpret_cast<const __half*>(o.values) + idx));
-    return __ldg(reinterpret_cast<const float*>(o.values) + idx);
+    const uint64_t pol = l2_evict_last_policy();
+    if (o.fp16) return ld_grid_f16(reinterpret_cast<const __half*>(o.values) + idx, pol);
+    return ld_grid_f32(reinterpret_cast<const float*>(o.values) + idx, pol);
 }
 
 struct Corners {
@@ -130,7 +152,7 @@ __device__ __forceinline__ df grid_refine(const ObjDev& o, df3 q, float3* g) {
 }
 
 // ------------------------------------------------------------------ analytic
-__device__ __forceinline__ float box_fast(const ObjDev& o, float3 q, float3* g) {
+static __device__ __noinline__ float box_fast(const ObjDev& o, float3 q, float3* g) {
     float d[3] = {fabsf(q.x) - o.half[0], fabsf(q.y) - o.half[1], fabsf(q.z) - o.half[2]};
     float qa[3] = {q.x, q.y, q.z};
     float oo[3] = {fmaxf(d[0], 0.f), fmaxf(d[1], 0.f), fmaxf(d[2], 0.f)};
@@ -150,7 +172,7 @@ __device__ __forceinline__ float box_fast(const ObjDev& o, float3 q, float3* g) 
 
 __device__ __forceinline__ df df_abs(df a) { return a.hi < 0.f ? df_neg(a) : a; }
 
-__device__ __forceinline__ df box_refine(const ObjDev& o, df3 q, float3* g) {
+static __device__ __noinline__ df box_refine(const ObjDev& o, df3 q, float3* g) {
     df qa[3] = {q.x, q.y, q.z};
     df d[3];
     df o2 = df_from(0.f);
@@ -262,7 +284,7 @@ __device__ __forceinline__ float solid_angle(V3<float> A, V3<float> B, V3<float>
 }
 
 // FP32 pass over all faces: min squared distance, nearest face, winding number
-__device__ __forceinline__ void mesh_scan(const ObjDev& o, float3 qf, float* dmin2, int* best, float* wind) {
+static __device__ __noinline__ void mesh_scan(const ObjDev& o, float3 qf, float* dmin2, int* best, float* wind) {
     V3<float> p{qf.x, qf.y, qf.z};
     float bd = INFINITY, w = 0.f;
     int bf = 0;
@@ -279,7 +301,7 @@ __device__ __forceinline__ void mesh_scan(const ObjDev& o, float3 qf, float* dmi
     *wind = w * 0.079577471545947668f;  // 1 / (4 pi)
 }
 
-__device__ __forceinline__ float mesh_fast(const ObjDev& o, float3 q, float3* g) {
+static __device__ __noinline__ float mesh_fast(const ObjDev& o, float3 q, float3* g) {
     float d2, w;
     int bf;
     mesh_scan(o, q, &d2, &bf, &w);
@@ -299,7 +321,7 @@ __device__ __forceinline__ float mesh_fast(const ObjDev& o, float3 q, float3* g)
 
 // FP32 scan, then every face within a guard of the FP32 minimum re-evaluated
 // with the compensated closest point; the smallest compensated distance wins.
-__device__ __forceinline__ df mesh_refine(const ObjDev& o, df3 q, float3* g) {
+static __device__ __noinline__ df mesh_refine(const ObjDev& o, df3 q, float3* g) {
     float3 qf = f3(q.x.hi, q.y.hi, q.z.hi);
     float d2, w;
     int bf;

@@ -11,7 +11,8 @@ namespace tg {
 
 constexpr int kMaxLinks = 255;       // u8 link ids
 constexpr int kItemCap = 1024;       // max taxels per work item (one CTA)
-constexpr int kStepThreads = 256;    // CTA size of the step kernel
+constexpr int kStepThreads = 512;    // CTA size of the step kernel
+constexpr int kStepMinBlocks = 2;    // resident CTAs per SM the register budget is set for
 constexpr int kLinkRec = 40;         // floats per (env, link) pose record
 constexpr int kLinkOut = 18;         // floats per (env, link) output record
 
@@ -83,6 +84,8 @@ struct StepArgs {
     ParamsDev P;
     // per-step inputs (device)
     const int32_t* obj_id;
+    const int32_t* item_order;        // item of each CTA (object-sorted), or null
+
     const float* link_rec;            // [E*L][kLinkRec] from the pose kernel
     uint32_t step;
     // state
@@ -117,6 +120,8 @@ struct PoseArgs {
 
 cudaError_t launch_pose(const PoseArgs& a, cudaStream_t s);
 cudaError_t launch_step(const StepArgs& a, int n_items, cudaStream_t s);
+cudaError_t launch_order_items(const Item* items, int n_items, const int32_t* obj_id, int n_objects,
+                               int32_t* order, cudaStream_t s);
 cudaError_t launch_reset(const StepArgs& a, int n_items, const uint8_t* env_mask, uint32_t episode,
                          uint32_t* episode_arr, cudaStream_t s);
 constexpr int kItemMaxLinksHost = 32;   // links per work item (matches the step kernel)

@@ -90,15 +90,42 @@ __device__ dmat advance_rotation(const float* q0, const float* w, df tau) {
     return dmatmul(E, R0);
 }
 
-__global__ void pose_kernel(const PoseArgs a) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+constexpr int kPoseThreads = 128;
+
+// One thread per (env, link); the object pose of each env the block touches
+// is advanced once, by one thread, into shared memory.
+__global__ void __launch_bounds__(kPoseThreads) pose_kernel(const PoseArgs a) {
+    __shared__ float s_obj[kPoseThreads][24];  // R_C as 9 float pairs, p_C as 3 float pairs
     const int L = a.max_links;
-    if (idx >= a.n_envs * L) return;
+    const int n = a.n_envs * L;
+    const int base = blockIdx.x * kPoseThreads;
+    const int idx = base + threadIdx.x;
+    const int e0 = base / L;
+    const int e_last = min(base + kPoseThreads, n) - 1;
+    const int n_env = e_last / L - e0 + 1;
+    const df tau{a.tau_hi, a.tau_lo};
+    if ((int)threadIdx.x < n_env) {
+        const int e = e0 + threadIdx.x;
+        const float* op = a.obj_pose + (size_t)e * 7;
+        const float* ov = a.obj_vel + (size_t)e * 6;
+        float oq[4] = {op[3], op[4], op[5], op[6]}, ow[3] = {ov[3], ov[4], ov[5]};
+        dmat RC = advance_rotation(oq, ow, tau);
+        float* o = s_obj[threadIdx.x];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) { o[2 * i] = RC.m[i].hi; o[2 * i + 1] = RC.m[i].lo; }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            df p = df_add(df_from(op[i]), df_mul_f(tau, ov[i]));
+            o[18 + 2 * i] = p.hi;
+            o[19 + 2 * i] = p.lo;
+        }
+    }
+    __syncthreads();
+    if (idx >= n) return;
     const int e = idx / L;
     if (!a.lattice[idx].present) return;
     const float* lp = a.link_pose + (size_t)idx * 7;
     const float* lv = a.link_vel + (size_t)idx * 6;
-    const float* op = a.obj_pose + (size_t)e * 7;
     const float* ov = a.obj_vel + (size_t)e * 6;
     float mu = a.def_mu, k = a.def_k, scale = 1.0f;
     if (a.env_params) {
@@ -106,17 +133,18 @@ __global__ void pose_kernel(const PoseArgs a) {
         k = a.env_params[3 * e + 1];
         scale = a.env_params[3 * e + 2];
     }
-    const df tau{a.tau_hi, a.tau_lo};
-    float lq[4] = {lp[3], lp[4], lp[5], lp[6]}, oq[4] = {op[3], op[4], op[5], op[6]};
+    const float* o = s_obj[e - e0];
+    dmat RC;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) RC.m[i] = df{o[2 * i], o[2 * i + 1]};
+    float lq[4] = {lp[3], lp[4], lp[5], lp[6]};
     float lw[3] = {lv[3], lv[4], lv[5]}, ow[3] = {ov[3], ov[4], ov[5]};
     dmat RL = advance_rotation(lq, lw, tau);
-    dmat RC = advance_rotation(oq, ow, tau);
-    df pL[3], pC[3], dp[3];
+    df dp[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        pL[i] = df_add(df_from(lp[i]), df_mul_f(tau, lv[i]));
-        pC[i] = df_add(df_from(op[i]), df_mul_f(tau, ov[i]));
-        dp[i] = df_sub(pL[i], pC[i]);  // p_L - p_C
+        const df pL = df_add(df_from(lp[i]), df_mul_f(tau, lv[i]));
+        dp[i] = df_sub(pL, df{o[18 + 2 * i], o[19 + 2 * i]});  // p_L - p_C
     }
     dmat M = dmatTmul(RC, RL);
     float* rec = a.link_rec + (size_t)idx * kLinkRec;
@@ -153,8 +181,7 @@ __global__ void pose_kernel(const PoseArgs a) {
 cudaError_t launch_pose(const PoseArgs& a, cudaStream_t s) {
     const int n = a.n_envs * a.max_links;
     if (n == 0) return cudaSuccess;
-    const int nt = 128;
-    pose_kernel<<<(n + nt - 1) / nt, nt, 0, s>>>(a);
+    pose_kernel<<<(n + kPoseThreads - 1) / kPoseThreads, kPoseThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -43,12 +43,15 @@ __device__ __forceinline__ uint4 draw(uint64_t seed, uint64_t gid, uint32_t word
 // (top 24 bits + 1/2) * 2^-24: exact in float, strictly inside (0, 1)
 __device__ __forceinline__ float u24(uint32_t x) { return ((float)(x >> 8) + 0.5f) * 5.9604644775390625e-08f; }
 
-// two standard normals from two words
+// two standard normals from two words: r = sqrt(-2 ln u1), angle 2 pi u2.
+// The angle is evaluated as pi (2 u2 - 1) + pi, inside [-pi, pi) where the
+// hardware sine/cosine is accurate to ~4e-7 absolute; cos and sin of the
+// shifted angle change sign.
 __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
-    float r = sqrtf(-2.0f * logf(u24(a)));
+    const float r = sqrtf(-2.0f * logf(u24(a)));
     float s, c;
-    sincospif(2.0f * u24(b), &s, &c);
-    return make_float2(r * c, r * s);
+    __sincosf(3.14159265358979323846f * (2.0f * u24(b) - 1.0f), &s, &c);
+    return make_float2(-r * c, -r * s);
 }
 
 __device__ __forceinline__ bool bernoulli24(uint32_t x, uint32_t threshold24) { return (x >> 8) < threshold24; }
