@@ -46,6 +46,7 @@ struct tg_scene {
     uint8_t* s_mask = nullptr;
     uint8_t* s_contact = nullptr;
     int32_t* item_order = nullptr;    // per-step object-sorted item order
+
     std::string last_error;
     // kernel timing (tg_profile_*)
     bool profiling = false;
@@ -378,6 +379,7 @@ tg_status tg_create_scene(const tg_scene_desc* d, tg_scene** out) {
     CKC(dalloc(&s->s_mask, E));
     CKC(dalloc(&s->s_contact, T));
     CKC(dalloc(&s->item_order, items.size()));
+
     CKC(cudaMemset(s->link_out, 0, EL * kLinkOut * sizeof(float)));
     CKC(cudaMemset(s->link_count, 0, EL * 2 * sizeof(int32_t)));
     CKC(cudaMemset(s->err, 0, 4 * sizeof(unsigned)));

@@ -1,0 +1,323 @@
+// step_common.cuh -- per-taxel pieces of the fused sensor step (step.cu).
+// Each routine follows one passage of the paper:
+//   fast_query      FP32 object-frame query point and SDF (Eqs. 1-2)
+//   clear_taxel     outputs of a taxel clear of the surface: depth 0, no
+//                   contact, no force (Eqs. 2-3, 8-9 with d = 0)
+//   refine_taxel    near-contact taxel: compensated query point and SDF,
+//                   depth, Schmitt bit (Eq. 3), force/torque with the Coulomb
+//                   clamp (Eqs. 4-9)
+//   noise_state     gain, hysteresis (Eqs. 27, 29-30), depth base noise and
+//                   dead override (Eqs. 25, 28), agg_force terms (Eq. 32)
+//   noisy_ft        3x3 crosstalk (Eq. 31), drift / white noise,
+//                   quantisation, dead override of the force/torque channels
+// Smem is any shared-memory layout with the per-taxel arrays fc, hx, ag
+// ([6][capacity] floats) and bits.
+#pragma once
+#include <cstdint>
+
+#include "df.cuh"
+#include "geom.cuh"
+#include "internal.h"
+#include "rng.cuh"
+
+namespace tg {
+
+// per-taxel bits in shared memory
+enum : uint8_t { BIT_CLEAN = 1, BIT_NOISY = 2, BIT_DEAD = 4, BIT_ACTIVE = 8, BIT_NEAR = 16 };
+
+__device__ __forceinline__ float hyst_update(const NoiseDev& g, float x, float* prev_p, float* xi_p) {
+    float xi = g.decay * __ldcs(xi_p) + (x - __ldcs(prev_p));
+    __stcs(xi_p, xi);
+    __stcs(prev_p, x);
+    return x + g.beta * xi;
+}
+
+__device__ __forceinline__ float quantise(const NoiseDev& g, float y) {
+    return g.quant > 0.0f ? g.quant * rintf(y / g.quant) : y;
+}
+
+// compensated accumulation (Neumaier)
+struct Acc {
+    float s, c;
+};
+__device__ __forceinline__ void acc_add(Acc& a, float x) {
+    float t = a.s + x;
+    if (fabsf(a.s) >= fabsf(x)) a.c += (a.s - t) + x;
+    else a.c += (x - t) + a.s;
+    a.s = t;
+}
+
+// FP32 object-frame query point q^ = M x + t and scaled SDF s phi(q^)
+__device__ __forceinline__ float fast_query(const float* rec, const ObjDev& obj, float x0, float x1, float x2) {
+    const float3 q = f3(fmaf(rec[0], x0, fmaf(rec[1], x1, fmaf(rec[2], x2, rec[18]))),
+                        fmaf(rec[3], x0, fmaf(rec[4], x1, fmaf(rec[5], x2, rec[19]))),
+                        fmaf(rec[6], x0, fmaf(rec[7], x1, fmaf(rec[8], x2, rec[20]))));
+    float3 go;
+    return rec[38] * sdf_fast(obj, q, &go);
+}
+
+// A taxel clear of the surface (or an inactive filler, R = 0): depth 0,
+// contact off, zero force.  Returns its shared-memory bits.
+__device__ __forceinline__ uint8_t clear_taxel(const StepArgs& a, int64_t g, float R, uint8_t flags, float phi) {
+    const int64_t T = a.n_taxels;
+    __stcs(a.flags + g, (uint8_t)(flags & 2u));
+    __stcs(a.depth_clean + g, 0.f);
+    if (a.sensors & TG_SENSOR_DIST) __stcs(a.dist + g, R > 0.0f ? phi - R : 0.0f);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) __stcs(a.ft_clean + c * T + g, 0.f);
+    return (uint8_t)(((flags & 2u) ? BIT_DEAD : 0u) | (R > 0.0f ? BIT_ACTIVE : 0u));
+}
+
+struct CleanReading {
+    float d;
+    float f[3], tq[3];
+    uint8_t bits;
+};
+
+// A near-contact taxel: compensated query point and SDF (near-contact depths
+// carry ~1e-14 relative error), depth, Schmitt decision on the compensated
+// depth, force/torque; writes the clean outputs and the new flag byte.
+__device__ __forceinline__ CleanReading refine_taxel(const StepArgs& a, const float* rec, const ObjDev& obj,
+                                                     int64_t g) {
+    const ParamsDev& P = a.P;
+    const int64_t T = a.n_taxels;
+    const float R = a.R[g];
+    const uint8_t flags = a.flags[g];
+    const float x0 = a.x[g], x1 = a.y[g], x2 = a.z[g];
+    df qd[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        df acc = df{rec[18 + r], rec[21 + r]};
+        acc = df_add(acc, df_mul_f(df{rec[3 * r], rec[9 + 3 * r]}, x0));
+        acc = df_add(acc, df_mul_f(df{rec[3 * r + 1], rec[9 + 3 * r + 1]}, x1));
+        acc = df_add(acc, df_mul_f(df{rec[3 * r + 2], rec[9 + 3 * r + 2]}, x2));
+        qd[r] = acc;
+    }
+    float3 go;
+    const float scale = rec[38];
+    const df phid = df_mul_f(sdf_refine(obj, df3{qd[0], qd[1], qd[2]}, &go), scale);
+    const df dd = df_add_f(df_neg(phid), R);  // R - phi
+    CleanReading out;
+    out.d = dd.hi > 0.0f ? dd.hi : 0.0f;
+    const bool prev = flags & 1u;
+    const bool y = df_gt(dd, df{P.eta_on_hi, P.eta_on_lo}) || (prev && df_gt(dd, df{P.eta_off_hi, P.eta_off_lo}));
+    const bool dead = flags & 2u;
+    const bool yn = y && !dead;
+    __stcs(a.flags + g, (uint8_t)((y ? 1u : 0u) | (flags & 2u) | (yn ? 4u : 0u)));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { out.f[c] = 0.f; out.tq[c] = 0.f; }
+    const float d = out.d;
+    if (d > 0.0f) {
+        const float3 mb = normalize_or(f3(rec[0] * go.x + rec[3] * go.y + rec[6] * go.z,
+                                          rec[1] * go.x + rec[4] * go.y + rec[7] * go.z,
+                                          rec[2] * go.x + rec[5] * go.y + rec[8] * go.z),
+                                       f3(0.f, 0.f, 1.f));
+        const float3 xv = f3(x0, x1, x2);
+        const float3 V = f3(rec[24], rec[25], rec[26]), Wc = f3(rec[27], rec[28], rec[29]);
+        const float3 Wl = f3(rec[30], rec[31], rec[32]), pLC = f3(rec[33], rec[34], rec[35]);
+        const float3 vrel = V + cross(Wc, xv - pLC) - cross(Wl, xv);
+        const float s = (P.alpha == 1.0f) ? d : powf(d, P.alpha);
+        const float kk = rec[36], mu = rec[37];
+        const float vns = dot(vrel, mb);
+        const float3 vn = mb * vns;
+        const float3 vt = vrel - vn;
+        const float3 fn = mb * (kk * s) + vn * (P.c * s);
+        const float vtn = sqrtf(dot(vt, vt));
+        float sc = 1.0f;
+        if (mu >= 0.0f && P.k_t * vtn > 0.0f) sc = fminf(1.0f, mu * sqrtf(dot(fn, fn)) / (P.k_t * vtn));
+        const float3 ff = fn - vt * (P.k_t * sc);
+        const float3 tt = cross(xv, ff) - mb * (P.k_omega * dot(Wc - Wl, mb));
+        out.f[0] = ff.x; out.f[1] = ff.y; out.f[2] = ff.z;
+        out.tq[0] = tt.x; out.tq[1] = tt.y; out.tq[2] = tt.z;
+    }
+    __stcs(a.depth_clean + g, d);
+    if (a.sensors & TG_SENSOR_DIST) __stcs(a.dist + g, -dd.hi);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        __stcs(a.ft_clean + c * T + g, out.f[c]);
+        __stcs(a.ft_clean + (3 + c) * T + g, out.tq[c]);
+    }
+    out.bits = (uint8_t)((y ? BIT_CLEAN : 0u) | (yn ? BIT_NOISY : 0u) | (dead ? BIT_DEAD : 0u) | BIT_ACTIVE);
+    return out;
+}
+
+// Noise state of one active taxel after its clean reading (fc[.][i] and the
+// clean depth in ag[0][i]); the state loads do not depend on the geometry.
+template <class Smem>
+__device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, int64_t g, uint32_t ep, uint8_t bits) {
+    const ParamsDev& P = a.P;
+    const int64_t T = a.n_taxels;
+    const float n0 = __ldcs(a.nx + g), n1 = __ldcs(a.ny + g), n2 = __ldcs(a.nz + g);
+    const uint64_t gid = (uint64_t)(a.gid0 + g);
+    const bool dead = bits & BIT_DEAD;
+    const float d = S.ag[0][i];
+    uint4 wep = make_uint4(0, 0, 0, 0);
+    if (P.depth.gain_on | P.ft.gain_on) wep = draw(P.seed, gid, ep, TAG_EPISODE);
+    const float gain_d = P.depth.gain_on ? P.depth.gain_lo + P.depth.gain_span * u24(wep.y) : 1.0f;
+    const float gain_f = P.ft.gain_on ? P.ft.gain_lo + P.ft.gain_span * u24(wep.z) : 1.0f;
+    float xd = gain_d * d;
+    if (P.depth.beta != 0.0f) xd = hyst_update(P.depth, xd, a.hyst_prev + g, a.hyst_xi + g);
+    if (P.ft.beta != 0.0f) {
+        float pv[6], xv[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            pv[c] = __ldcs(a.hyst_prev + (1 + c) * T + g);
+            xv[c] = __ldcs(a.hyst_xi + (1 + c) * T + g);
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const float x = gain_f * S.fc[c][i];
+            const float xi = P.ft.decay * xv[c] + (x - pv[c]);
+            __stcs(a.hyst_xi + (1 + c) * T + g, xi);
+            __stcs(a.hyst_prev + (1 + c) * T + g, x);
+            S.hx[c][i] = x + P.ft.beta * xi;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) S.hx[c][i] = gain_f * S.fc[c][i];
+    }
+    if (P.depth.sigma_rw != 0.0f || P.depth.sigma_white != 0.0f) {
+        uint4 w = draw(P.seed, gid, a.step, TAG_SCALAR);
+        float2 z = box_muller(w.x, w.y);
+        float dr = 0.0f;
+        if (P.depth.sigma_rw != 0.0f) {
+            dr = __ldcs(a.drift + g) + P.depth.sigma_rw * z.x;
+            __stcs(a.drift + g, dr);
+        }
+        xd = xd + P.depth.bias + P.depth.sigma_white * z.y + dr;
+    } else {
+        xd += P.depth.bias;
+    }
+    xd = quantise(P.depth, xd);
+    if (dead) xd = P.depth.stuck_lo + P.depth.stuck_span * u24(draw(P.seed, gid, ep, TAG_STUCK).x);
+    __stcs(a.depth_noisy + g, xd);
+    S.ag[0][i] = d * n0; S.ag[1][i] = d * n1; S.ag[2][i] = d * n2;
+    S.ag[3][i] = xd * n0; S.ag[4][i] = xd * n1; S.ag[5][i] = xd * n2;
+}
+
+// Inactive filler: zero noisy depth and staged values.
+template <class Smem>
+__device__ __forceinline__ void noise_state_filler(const StepArgs& a, Smem& S, int i, int64_t g) {
+    __stcs(a.depth_noisy + g, 0.f);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        S.hx[c][i] = 0.f;
+        S.ag[c][i] = 0.f;
+    }
+}
+
+// Noisy force/torque of taxel i at lattice (r, cc) of a rows x cols lattice
+// whose first taxel is `base` in the hx arrays; writes ft_noisy and out[.][i].
+template <class Smem, class Out>
+__device__ __forceinline__ void noisy_ft(const StepArgs& a, const Smem& S, Out out, int i, int64_t g, uint32_t ep,
+                                         uint8_t bits, int base, int r, int cc, int rows, int cols, bool wrap) {
+    const ParamsDev& P = a.P;
+    const int64_t T = a.n_taxels;
+    if (!(bits & BIT_ACTIVE)) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            __stcs(a.ft_noisy + c * T + g, 0.f);
+            out[c][i] = 0.f;
+        }
+        return;
+    }
+    const uint64_t gid = (uint64_t)(a.gid0 + g);
+    const NoiseDev& G = P.ft;
+    float dr_prev[6];
+    if (G.sigma_rw != 0.0f) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) dr_prev[c] = __ldcs(a.drift + (1 + c) * T + g);
+    }
+    float z[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) z[c] = S.hx[c][i];
+    if (P.chi != 0.0f) {
+        float conv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int di = -1; di <= 1; ++di) {
+            const int rr = r + di;
+            if (rr < 0 || rr >= rows) continue;
+#pragma unroll
+            for (int dj = -1; dj <= 1; ++dj) {
+                int c2 = cc + dj;
+                if (c2 < 0 || c2 >= cols) {
+                    if (!wrap) continue;
+                    c2 += c2 < 0 ? cols : -cols;
+                }
+                const int nb = base + rr * cols + c2;
+                const float w = P.xt_w[(di + 1) * 3 + (dj + 1)];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) conv[c] = fmaf(w, S.hx[c][nb], conv[c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) z[c] = (1.0f - P.chi) * z[c] + P.chi * conv[c];
+    }
+    if (G.sigma_rw != 0.0f || G.sigma_white != 0.0f) {
+        float nrm[12];
+        uint4 wa = draw(P.seed, gid, a.step, TAG_FT_A);
+        uint4 wb = draw(P.seed, gid, a.step, TAG_FT_B);
+        float2 p0 = box_muller(wa.x, wa.y), p1 = box_muller(wa.z, wa.w);
+        float2 p2 = box_muller(wb.x, wb.y);
+        nrm[0] = p0.x; nrm[1] = p0.y; nrm[2] = p1.x; nrm[3] = p1.y; nrm[4] = p2.x; nrm[5] = p2.y;
+        if (G.sigma_white != 0.0f) {
+            uint4 wc = draw(P.seed, gid, a.step, TAG_FT_C);
+            float2 p3 = box_muller(wb.z, wb.w), p4 = box_muller(wc.x, wc.y), p5 = box_muller(wc.z, wc.w);
+            nrm[6] = p3.x; nrm[7] = p3.y; nrm[8] = p4.x; nrm[9] = p4.y; nrm[10] = p5.x; nrm[11] = p5.y;
+        } else {
+#pragma unroll
+            for (int c = 6; c < 12; ++c) nrm[c] = 0.0f;
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            float dr = 0.0f;
+            if (G.sigma_rw != 0.0f) {
+                dr = dr_prev[c] + G.sigma_rw * nrm[c];
+                __stcs(a.drift + (1 + c) * T + g, dr);
+            }
+            z[c] = z[c] + G.bias + G.sigma_white * nrm[6 + c] + dr;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) z[c] += G.bias;
+    }
+    const bool dead = bits & BIT_DEAD;
+    float stuck = 0.0f;
+    if (dead) stuck = G.stuck_lo + G.stuck_span * u24(draw(P.seed, gid, ep, TAG_STUCK).y);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        float v = quantise(G, z[c]);
+        if (dead) v = stuck;
+        __stcs(a.ft_noisy + c * T + g, v);
+        out[c][i] = v;
+    }
+}
+
+// One per-link quantity, summed over taxels [s0, s1) in lattice order with
+// compensated accumulation (deterministic).  Quantities: 0-5 clean
+// force/torque (out cols 0-5), 6-8 clean agg_force in ZYX order (cols 12-14,
+// scaled 1e4), 9-11 noisy agg_force (cols 15-17), 12 clean count, 13 noisy
+// count, 14-19 noisy force/torque (cols 6-11, read from `noisy`).
+template <class Smem, class Noisy>
+__device__ __forceinline__ void link_quantity(const StepArgs& a, const Smem& S, Noisy noisy, size_t rec, int s0, int s1,
+                                              int qn) {
+    if (qn == 12 || qn == 13) {
+        const int bit = qn == 12 ? 0 : 1;
+        int cnt = 0;
+        for (int i = s0; i < s1; ++i) cnt += (S.bits[i] >> bit) & 1;
+        a.link_count[rec * 2 + bit] = cnt;
+        return;
+    }
+    const float* src;
+    int col;
+    float scale = 1.0f;
+    if (qn < 6) { src = S.fc[qn]; col = qn; }
+    else if (qn < 9) { src = S.ag[2 - (qn - 6)]; col = 12 + (qn - 6); scale = 1e4f; }
+    else if (qn < 12) { src = S.ag[5 - (qn - 9)]; col = 15 + (qn - 9); scale = 1e4f; }
+    else { src = noisy[qn - 14]; col = 6 + (qn - 14); }
+    Acc acc{0.f, 0.f};
+    for (int i = s0; i < s1; ++i) acc_add(acc, src[i]);
+    a.link_out[rec * kLinkOut + col] = scale * (acc.s + acc.c);
+}
+
+}  // namespace tg
