@@ -225,6 +225,29 @@ tg_status tg_bake_grid(const float* verts, int32_t n_verts, const int32_t* faces
 tg_status tg_mesh_sdf(const float* verts, int32_t n_verts, const int32_t* faces, int32_t n_faces,
                       const float* points, int64_t n, float* phi, float* grad, tg_stream stream);
 
+/* Largest mesh tg_mesh_sdf_noalloc accepts. */
+#define TG_NOALLOC_MAX_FACES 65536
+
+/* tg_mesh_sdf without any device allocation.  The paper has no counterpart:
+   this entry point exists for callers that cannot call cudaMalloc, such as
+   code being captured into a CUDA graph that must not allocate, or a host
+   application whose allocator owns all device memory.  tg_mesh_sdf copies the
+   mesh into a triangle list it allocates for each call; this variant builds
+   that list on the GPU in a device array inside the library, sized for
+   TG_NOALLOC_MAX_FACES faces (3 MiB, held by every GPU that loads the library
+   until the process exits).
+   verts [n_verts][3], faces [n_faces][3], points [n][3], phi [n] and grad
+   [n][3] (or NULL) must all be device memory; the results are those of
+   tg_mesh_sdf.  Meshes over TG_NOALLOC_MAX_FACES faces, host pointers or bad
+   sizes return TG_ERR_INVALID_ARG and run nothing.  A face index outside
+   [0, n_verts) gives NaN distances instead of an out-of-bounds read.
+   The first call on each device looks up the array's device address once;
+   make that first call before any stream capture.  Every call shares the
+   array: calls whose GPU work overlaps (different streams or host threads)
+   race on it, so the caller must order them.  Asynchronous on `stream`. */
+tg_status tg_mesh_sdf_noalloc(const float* verts, int32_t n_verts, const int32_t* faces, int32_t n_faces,
+                              const float* points, int64_t n, float* phi, float* grad, tg_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -92,14 +92,17 @@ _lib.tg_profile_enable.argtypes = [_vp, _i32]
 _lib.tg_profile_read.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int64)]
 _lib.tg_bake_grid.argtypes = [_vp, _i32, _vp, _i32, _vp, _vp, _vp, _i32, _vp, _vp]
 _lib.tg_mesh_sdf.argtypes = [_vp, _i32, _vp, _i32, _vp, C.c_int64, _vp, _vp, _vp]
+_lib.tg_mesh_sdf_noalloc.argtypes = [_vp, _i32, _vp, _i32, _vp, C.c_int64, _vp, _vp, _vp]
 for _f in ("tg_create_scene", "tg_upload_objects", "tg_reset_envs", "tg_step_sensors", "tg_read_taxels",
            "tg_get_buffer", "tg_sync", "tg_save_state", "tg_load_state", "tg_bake_grid", "tg_mesh_sdf",
-           "tg_profile_enable", "tg_profile_read"):
+           "tg_profile_enable", "tg_profile_read", "tg_mesh_sdf_noalloc"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ["tg_create_scene", "tg_destroy_scene", "tg_max_link_taxels", "tg_upload_objects", "tg_reset_envs",
             "tg_step_sensors", "tg_read_taxels", "tg_channel_bytes", "tg_get_buffer", "tg_sync", "tg_last_error",
-            "tg_save_state", "tg_load_state", "tg_bake_grid", "tg_mesh_sdf", "tg_profile_enable", "tg_profile_read"]
+            "tg_save_state", "tg_load_state", "tg_bake_grid", "tg_mesh_sdf", "tg_profile_enable", "tg_profile_read",
+            "tg_mesh_sdf_noalloc"]
+NOALLOC_MAX_FACES = 65536
 
 
 def lib():
@@ -335,3 +338,13 @@ def mesh_sdf(verts, faces, points, with_grad=True, stream=None):
     _check(_lib.tg_mesh_sdf(_ptr(V), len(V), _ptr(F), len(F), pts.data_ptr(), n, phi.data_ptr(),
                             grad.data_ptr() if grad is not None else None, _stream(stream)), None)
     return phi, grad
+
+
+def mesh_sdf_noalloc(verts, faces, points, phi, grad=None, stream=None):
+    """tg_mesh_sdf_noalloc: exact mesh SDF at device points into caller-owned
+    device tensors, with no device allocation inside the library (for callers
+    that cannot allocate).  verts (float32 [nv][3]), faces (int32 [nf][3]),
+    points, phi and grad must be contiguous CUDA tensors."""
+    _check(_lib.tg_mesh_sdf_noalloc(verts.data_ptr(), verts.shape[0], faces.data_ptr(), faces.shape[0],
+                                    points.data_ptr(), points.shape[0], phi.data_ptr(),
+                                    grad.data_ptr() if grad is not None else None, _stream(stream)), None)
