@@ -476,15 +476,22 @@ tg_status tg_upload_objects(tg_scene* s, const tg_object_desc* objs, int32_t n) 
                 t.inv_h_lo[a] = (float)(ih - (double)t.inv_h_hi[a]);
             }
             if (!o.values) { cleanup(); return fail(s, TG_ERR_INVALID_ARG, "grid values are NULL"); }
-            const size_t bytes = cnt * (o.fp16 ? 2 : 4);
-            void* dv = nullptr;
+            const size_t esz = o.fp16 ? 2 : 4;
+            const size_t bytes = cnt * esz;
+            const size_t ncell = (size_t)(o.dims[0] - 1) * (o.dims[1] - 1) * (o.dims[2] - 1);
+            void *dv = nullptr, *dc = nullptr;
             cudaError_t e = cudaMalloc(&dv, bytes);
             if (e != cudaSuccess) { cleanup(); return cuda_fail(s, e, "grid alloc"); }
-            bufs.push_back(dv);
+            e = cudaMalloc(&dc, ncell * 8 * esz);
+            if (e != cudaSuccess) { cudaFree(dv); cleanup(); return cuda_fail(s, e, "grid cell alloc"); }
+            bufs.push_back(dc);
             e = cudaMemcpy(dv, o.values, bytes, cudaMemcpyDefault);
+            if (e == cudaSuccess) e = launch_build_cells(dv, o.dims, o.fp16 ? 1 : 0, dc, 0);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            cudaFree(dv);  // queries read the cell-major copy only
             if (e != cudaSuccess) { cleanup(); return cuda_fail(s, e, "grid copy"); }
             t.fp16 = o.fp16 ? 1 : 0;
-            t.values = dv;
+            t.cells = dc;
             break;
         }
         default:

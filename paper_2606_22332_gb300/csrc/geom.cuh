@@ -44,23 +44,18 @@ __device__ __forceinline__ uint64_t l2_evict_last_policy() {
     return p;
 }
 
-__device__ __forceinline__ float ld_grid_f32(const float* p, uint64_t pol) {
-    float v;
-    asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+// The 8 corner values of cell (i, j, k), read from the cell-major copy of
+// the grid (one 16-byte record per cell for binary16, two for float): one
+// vector load per query instead of eight scattered ones.
+__device__ __forceinline__ uint4 ld_cell16(const uint4* p, uint64_t pol) {
+    uint4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p), "l"(pol));
     return v;
 }
 
-__device__ __forceinline__ float ld_grid_f16(const __half* p, uint64_t pol) {
-    unsigned short v;
-    asm("ld.global.nc.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
-    return __half2float(__ushort_as_half(v));
-}
-
-__device__ __forceinline__ float grid_value(const ObjDev& o, int i, int j, int k) {
-    size_t idx = ((size_t)k * o.dims[1] + j) * o.dims[0] + i;
-    const uint64_t pol = l2_evict_last_policy();
-    if (o.fp16) return ld_grid_f16(reinterpret_cast<const __half*>(o.values) + idx, pol);
-    return ld_grid_f32(reinterpret_cast<const float*>(o.values) + idx, pol);
+__device__ __forceinline__ float2 h2f2(uint32_t w) {
+    return __half22float2(*reinterpret_cast<const __half2*>(&w));
 }
 
 struct Corners {
@@ -68,15 +63,22 @@ struct Corners {
 };
 
 __device__ __forceinline__ Corners grid_corners(const ObjDev& o, int i, int j, int k) {
+    const size_t cell = ((size_t)k * (o.dims[1] - 1) + j) * (o.dims[0] - 1) + i;
+    const uint64_t pol = l2_evict_last_policy();
     Corners c;
-    c.v000 = grid_value(o, i, j, k);
-    c.v100 = grid_value(o, i + 1, j, k);
-    c.v010 = grid_value(o, i, j + 1, k);
-    c.v110 = grid_value(o, i + 1, j + 1, k);
-    c.v001 = grid_value(o, i, j, k + 1);
-    c.v101 = grid_value(o, i + 1, j, k + 1);
-    c.v011 = grid_value(o, i, j + 1, k + 1);
-    c.v111 = grid_value(o, i + 1, j + 1, k + 1);
+    if (o.fp16) {
+        const uint4 v = ld_cell16(reinterpret_cast<const uint4*>(o.cells) + cell, pol);
+        float2 a = h2f2(v.x), b = h2f2(v.y), d = h2f2(v.z), e = h2f2(v.w);
+        c.v000 = a.x; c.v100 = a.y; c.v010 = b.x; c.v110 = b.y;
+        c.v001 = d.x; c.v101 = d.y; c.v011 = e.x; c.v111 = e.y;
+    } else {
+        const uint4* p = reinterpret_cast<const uint4*>(o.cells) + 2 * cell;
+        const uint4 v = ld_cell16(p, pol), w = ld_cell16(p + 1, pol);
+        c.v000 = __uint_as_float(v.x); c.v100 = __uint_as_float(v.y);
+        c.v010 = __uint_as_float(v.z); c.v110 = __uint_as_float(v.w);
+        c.v001 = __uint_as_float(w.x); c.v101 = __uint_as_float(w.y);
+        c.v011 = __uint_as_float(w.z); c.v111 = __uint_as_float(w.w);
+    }
     return c;
 }
 

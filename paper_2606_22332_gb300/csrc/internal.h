@@ -47,7 +47,7 @@ struct ObjDev {
     float inv_h_hi[3], inv_h_lo[3];   // (dims-1)/(hi-lo) as a float pair
     float h[3];
     int fp16;
-    const void* values;
+    const void* cells;                // cell-major corners: [cell][8] binary16 or float
     // mesh
     int n_verts, n_faces;
     const float* tri;                 // [n_faces][9]: a, b, c vertices
@@ -129,6 +129,7 @@ cudaError_t launch_mesh_sdf_points(const float* tri, const float* tri_n, int n_f
                                    int64_t n, float* phi, float* grad, cudaStream_t s);
 cudaError_t launch_mesh_bake(const float* tri, const float* tri_n, int n_faces, const int dims[3],
                              const float lo[3], const float hi[3], int fp16, void* out, cudaStream_t s);
+cudaError_t launch_build_cells(const void* values, const int dims[3], int fp16, void* cells, cudaStream_t s);
 cudaError_t launch_unpack_contact(const uint8_t* flags, int64_t n, int noisy, uint8_t* out, cudaStream_t s);
 
 }  // namespace tg

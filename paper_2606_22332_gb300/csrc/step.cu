@@ -81,29 +81,43 @@ __global__ void __launch_bounds__(NT, kStepMinBlocks) step_kernel(const StepArgs
     const ObjDev& obj = S.obj;
 
     // ---- phase A1 (geometry): FP32 query of every taxel; those clear of the
-    //      surface finish here, those within 1 um of contact are queued
+    //      surface finish here, those within 1 um of contact are queued.  A
+    //      thread takes its taxels in pairs so both load chains (taxel, then
+    //      grid cell) are in flight together.
     int l = 0;
-    for (int i = tid; i < n; i += NT) {
-        while (i >= S.start[l + 1]) ++l;
-        const int64_t g = it.taxel_begin + i;
-        const float R = __ldcs(a.R + g);
-        const float x0 = __ldcs(a.x + g), x1 = __ldcs(a.y + g), x2 = __ldcs(a.z + g);
-        const uint8_t flags = __ldcs(a.flags + g);
-        float phi = 0.0f;
-        bool near = false;
-        if (R > 0.0f) {
-            phi = fast_query(S.rec[l], obj, x0, x1, x2);
-            if (!isfinite(phi)) atomicAdd(a.err, 1u);
-            near = phi < R + 1e-6f;
-        }
-        if (near) {
-            S.queue[atomicAdd(&S.nq, 1)] = (int16_t)i;
-            continue;
-        }
-        S.bits[i] = clear_taxel(a, g, R, flags, phi);
+    for (int i0 = tid; i0 < n; i0 += 2 * NT) {
+        const int i1 = i0 + NT;
+        const bool has1 = i1 < n;
+        const int64_t g0 = it.taxel_begin + i0, g1 = it.taxel_begin + (has1 ? i1 : i0);
+        const float R0 = __ldcs(a.R + g0), R1 = has1 ? __ldcs(a.R + g1) : 0.0f;
+        const float x00 = __ldcs(a.x + g0), x01 = __ldcs(a.y + g0), x02 = __ldcs(a.z + g0);
+        const float x10 = __ldcs(a.x + g1), x11 = __ldcs(a.y + g1), x12 = __ldcs(a.z + g1);
+        const uint8_t fl0 = __ldcs(a.flags + g0), fl1 = __ldcs(a.flags + g1);
+        while (i0 >= S.start[l + 1]) ++l;
+        const int l0 = l;
+        int l1 = l;
+        if (has1)
+            while (i1 >= S.start[l1 + 1]) ++l1;
+        float phi0 = 0.0f, phi1 = 0.0f;
+        if (R0 > 0.0f) phi0 = fast_query(S.rec[l0], obj, x00, x01, x02);
+        if (R1 > 0.0f) phi1 = fast_query(S.rec[l1], obj, x10, x11, x12);
 #pragma unroll
-        for (int c = 0; c < 6; ++c) S.fc[c][i] = 0.f;
-        S.ag[0][i] = 0.f;
+        for (int u = 0; u < 2; ++u) {
+            if (u == 1 && !has1) break;
+            const int i = u ? i1 : i0;
+            const int64_t g = u ? g1 : g0;
+            const float R = u ? R1 : R0, phi = u ? phi1 : phi0;
+            if (R > 0.0f && !isfinite(phi)) atomicAdd(a.err, 1u);
+            if (R > 0.0f && phi < R + 1e-6f) {
+                S.queue[atomicAdd(&S.nq, 1)] = (int16_t)i;
+                continue;
+            }
+            S.bits[i] = clear_taxel(a, g, R, u ? fl1 : fl0, phi);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) S.fc[c][i] = 0.f;
+            S.ag[0][i] = 0.f;
+        }
+        l = l1;
     }
     __syncthreads();
 
@@ -245,6 +259,39 @@ cudaError_t launch_reset(const StepArgs& a, int n_items, const uint8_t* env_mask
                          uint32_t* episode_arr, cudaStream_t s) {
     if (n_items == 0) return cudaSuccess;
     reset_kernel<<<n_items, 256, 0, s>>>(a, env_mask, episode, episode_arr);
+    return cudaGetLastError();
+}
+
+// Cell-major copy of a grid: the 8 corner values of every cell in one record
+// (v000 v100 v010 v110 v001 v101 v011 v111), so a query reads one record.
+template <class V>
+__global__ void build_cells_kernel(const V* values, int nx, int ny, int nz, V* cells) {
+    const int64_t ncx = nx - 1, ncy = ny - 1, ncz = nz - 1;
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncx * ncy * ncz) return;
+    const int i = (int)(c % ncx), j = (int)((c / ncx) % ncy), k = (int)(c / (ncx * ncy));
+    const int64_t sx = 1, sy = nx, sz = (int64_t)nx * ny;
+    const int64_t b = k * sz + j * sy + i;
+    V* o = cells + 8 * c;
+    o[0] = values[b];
+    o[1] = values[b + sx];
+    o[2] = values[b + sy];
+    o[3] = values[b + sy + sx];
+    o[4] = values[b + sz];
+    o[5] = values[b + sz + sx];
+    o[6] = values[b + sz + sy];
+    o[7] = values[b + sz + sy + sx];
+}
+
+cudaError_t launch_build_cells(const void* values, const int dims[3], int fp16, void* cells, cudaStream_t s) {
+    const int64_t n = (int64_t)(dims[0] - 1) * (dims[1] - 1) * (dims[2] - 1);
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    if (fp16)
+        build_cells_kernel<<<blocks, 256, 0, s>>>(static_cast<const uint16_t*>(values), dims[0], dims[1], dims[2],
+                                                  static_cast<uint16_t*>(cells));
+    else
+        build_cells_kernel<<<blocks, 256, 0, s>>>(static_cast<const float*>(values), dims[0], dims[1], dims[2],
+                                                  static_cast<float*>(cells));
     return cudaGetLastError();
 }
 
