@@ -116,27 +116,50 @@ __device__ __forceinline__ df3 df3_cross(df3 a, df3 b) {
 __device__ __forceinline__ df3 df3_from(float x, float y, float z) { return df3{df_from(x), df_from(y), df_from(z)}; }
 
 // sin and cos of a compensated angle: reduction by multiples of pi/2 (pi/2
-// held as a float pair), then the Taylor series on |r| <= pi/4 summed to the
-// r^17 / r^18 terms (the first omitted term is below 2^-50).
+// held as a float pair), then the Taylor series on |r| <= pi/4 by Horner's
+// rule in r^2 up to the r^17 / r^18 terms (the first omitted term is below
+// 2^-50).  inv_fact(n) is 1/n! as a float pair, folded from the
+// definition at compile time.
+struct DfConst {
+    float hi, lo;
+};
+constexpr double kFactD[19] = {1.0, 1.0, 2.0, 6.0, 24.0, 120.0, 720.0, 5040.0, 40320.0, 362880.0, 3628800.0,
+                               39916800.0, 479001600.0, 6227020800.0, 87178291200.0, 1307674368000.0,
+                               20922789888000.0, 355687428096000.0, 6402373705728000.0};
+__host__ __device__ constexpr DfConst inv_fact(int n) {
+    return DfConst{(float)(1.0 / kFactD[n]), (float)(1.0 / kFactD[n] - (double)(float)(1.0 / kFactD[n]))};
+}
+
 __device__ inline void df_sincos(df x, df* s_out, df* c_out) {
     const df PIO2 = df{1.57079637050628662109375f, -4.37113882867379213008e-08f};
     float kf = rintf(x.hi / PIO2.hi);
     df r = df_sub(x, df_mul_f(PIO2, kf));
     df r2 = df_mul(r, r);
-    // sin: r - r^3/3! + ...
-    df term = r, s = r;
-    for (int n = 3; n <= 17; n += 2) {
-        term = df_div_f(df_mul(term, r2), (float)((n - 1) * n));
-        term = df_neg(term);
-        s = df_add(s, term);
-    }
-    // cos: 1 - r^2/2! + ...
-    df cterm = df_from(1.0f), c = df_from(1.0f);
-    for (int n = 2; n <= 18; n += 2) {
-        cterm = df_div_f(df_mul(cterm, r2), (float)((n - 1) * n));
-        cterm = df_neg(cterm);
-        c = df_add(c, cterm);
-    }
+    // sin r = r (1 - r^2/3! + r^4/5! - ...), cos r = 1 - r^2/2! + r^4/4! - ...
+    constexpr DfConst s17 = inv_fact(17), s15 = inv_fact(15), s13 = inv_fact(13), s11 = inv_fact(11), s9 = inv_fact(9),
+                      s7 = inv_fact(7), s5 = inv_fact(5), s3 = inv_fact(3);
+    constexpr DfConst c18 = inv_fact(18), c16 = inv_fact(16), c14 = inv_fact(14), c12 = inv_fact(12), c10 = inv_fact(10),
+                      c8 = inv_fact(8), c6 = inv_fact(6), c4 = inv_fact(4), c2 = inv_fact(2);
+    df ps = df{s17.hi, s17.lo};
+    ps = df_sub(df{s15.hi, s15.lo}, df_mul(r2, ps));
+    ps = df_sub(df{s13.hi, s13.lo}, df_mul(r2, ps));
+    ps = df_sub(df{s11.hi, s11.lo}, df_mul(r2, ps));
+    ps = df_sub(df{s9.hi, s9.lo}, df_mul(r2, ps));
+    ps = df_sub(df{s7.hi, s7.lo}, df_mul(r2, ps));
+    ps = df_sub(df{s5.hi, s5.lo}, df_mul(r2, ps));
+    ps = df_sub(df{s3.hi, s3.lo}, df_mul(r2, ps));
+    ps = df_sub(df_from(1.0f), df_mul(r2, ps));
+    const df s = df_mul(r, ps);
+    df pc = df{c18.hi, c18.lo};
+    pc = df_sub(df{c16.hi, c16.lo}, df_mul(r2, pc));
+    pc = df_sub(df{c14.hi, c14.lo}, df_mul(r2, pc));
+    pc = df_sub(df{c12.hi, c12.lo}, df_mul(r2, pc));
+    pc = df_sub(df{c10.hi, c10.lo}, df_mul(r2, pc));
+    pc = df_sub(df{c8.hi, c8.lo}, df_mul(r2, pc));
+    pc = df_sub(df{c6.hi, c6.lo}, df_mul(r2, pc));
+    pc = df_sub(df{c4.hi, c4.lo}, df_mul(r2, pc));
+    pc = df_sub(df{c2.hi, c2.lo}, df_mul(r2, pc));
+    const df c = df_sub(df_from(1.0f), df_mul(r2, pc));
     int k = ((int)kf) & 3;
     if (k == 0) { *s_out = s; *c_out = c; }
     else if (k == 1) { *s_out = c; *c_out = df_neg(s); }
