@@ -65,7 +65,15 @@ class ORParams(C.Structure):
         ("dt", C.c_double), ("seed", C.c_uint64), ("p_dead", C.c_double),
         ("depth", ORNoiseGroup), ("ft", ORNoiseGroup), ("prox", ORNoiseGroup),
         ("chi", C.c_double), ("xt_sigma", C.c_double),
+        ("prox_rays", C.c_int32), ("prox_range", C.c_double), ("prox_cone", C.c_double),
     ]
+
+
+class ORPads(C.Structure):
+    _fields_ = [("pads_per_env", C.c_int32), ("rows", C.c_int32), ("cols", C.c_int32), ("pitch", C.c_double),
+                ("pad_link", C.c_void_p), ("pad_frame", C.c_void_p),
+                ("s_d", C.c_double), ("alpha", C.c_double), ("lambda_d", C.c_double), ("c", C.c_double),
+                ("eps", C.c_double), ("radius", C.c_int32)]
 
 
 class ORScene(C.Structure):
@@ -94,6 +102,7 @@ class ORState(C.Structure):
 
 class OROutputs(C.Structure):
     _fields_ = [("contact_clean", C.c_void_p), ("contact_noisy", C.c_void_p),
+                ("prox_clean", C.c_void_p), ("prox_noisy", C.c_void_p), ("prox_grazing", C.c_void_p),
                 ("depth_clean", C.c_void_p), ("depth_noisy", C.c_void_p), ("dist", C.c_void_p),
                 ("ft_clean", C.c_void_p), ("ft_noisy", C.c_void_p),
                 ("link_sums", C.c_void_p), ("link_counts", C.c_void_p)]
@@ -127,6 +136,14 @@ def lib():
             L.or_step.argtypes = [C.POINTER(ORScene), C.POINTER(ORInputs), C.POINTER(ORState),
                                   C.POINTER(OROutputs), C.c_int32]
             L.or_step.restype = C.c_int
+            L.or_ray_first_root.argtypes = [C.POINTER(ORObject), C.c_double, C.c_void_p, C.c_void_p, C.c_double,
+                                            C.POINTER(C.c_int)]
+            L.or_ray_first_root.restype = C.c_double
+            L.or_prox_ray_dirs.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_void_p]
+            L.or_marker_kernel_g.argtypes = [C.c_double, C.c_double]
+            L.or_marker_kernel_g.restype = C.c_double
+            L.or_markers.argtypes = [C.POINTER(ORScene), C.POINTER(ORPads), C.POINTER(ORInputs), C.c_void_p,
+                                     C.c_void_p, C.c_int32]
             _lib = L
     return _lib
 
@@ -247,6 +264,25 @@ class Obj:
         return phi, g
 
 
+def ray_first_root(obj: "Obj", q0, d, tmax, scale=1.0):
+    """(t or nan, grazing) of the first root of the object's SDF along q0 + t d."""
+    q0 = np.ascontiguousarray(q0, np.float64); d = np.ascontiguousarray(d, np.float64)
+    g = C.c_int(0)
+    t = lib().or_ray_first_root(C.byref(obj.s), float(scale), _p(q0), _p(d), float(tmax), C.byref(g))
+    return t, bool(g.value)
+
+
+def prox_ray_dirs(n, n_rays, cone):
+    n = np.ascontiguousarray(n, np.float64)
+    out = np.zeros((n_rays, 3))
+    lib().or_prox_ray_dirs(_p(n), int(n_rays), float(cone), _p(out))
+    return out
+
+
+def marker_kernel_g(lambda_d, r2):
+    return lib().or_marker_kernel_g(float(lambda_d), float(r2))
+
+
 def schmitt(prev, d, eta_on, eta_off):
     return lib().or_schmitt(int(prev), float(d), float(eta_on), float(eta_off))
 
@@ -280,6 +316,9 @@ def make_params(p: dict) -> ORParams:
         setattr(P, k, float(p[k]))
     P.mu = -1.0 if p["mu"] is None or np.isinf(p["mu"]) else float(p["mu"])
     P.seed = int(p["seed"])
+    P.prox_rays = int(p.get("prox_rays", 0))
+    P.prox_range = float(p.get("prox_range", 0.05))
+    P.prox_cone = float(p.get("prox_cone", np.radians(30.0)))
     for gname in ("depth", "ft", "prox"):
         g = getattr(P, gname)
         for k in _GROUP_KEYS:
@@ -366,6 +405,7 @@ class OracleScene:
         I.step = int(inputs.get("step", 0))
         out = {
             "contact_clean": np.zeros(T, np.uint8), "contact_noisy": np.zeros(T, np.uint8),
+            "prox_clean": np.zeros(T), "prox_noisy": np.zeros(T), "prox_grazing": np.zeros(T, np.uint8),
             "depth_clean": np.zeros(T), "depth_noisy": np.zeros(T), "dist": np.zeros(T),
             "ft_clean": np.zeros((6, T)), "ft_noisy": np.zeros((6, T)),
             "link_sums": np.zeros((E * L, LINK_REC)), "link_counts": np.zeros((E * L, 2), np.int32),
@@ -376,3 +416,33 @@ class OracleScene:
         s = self._state(st)
         lib().or_step(C.byref(self.S), C.byref(I), C.byref(s), C.byref(O), int(threads))
         return out
+
+    def markers(self, pads: dict, inputs: dict, threads: int = 0):
+        """Marker displacements u [E][P][rows*cols][3] (pad frame: normal, tangent, bitangent)
+        and marker depths h [E][P][rows*cols].  pads: pads_per_env, rows, cols, pitch, pad_link
+        [E][P], pad_frame [E][P][9], s_d, alpha, lambda_d, c, eps, radius."""
+        E = self.n_envs
+        keep = {"link": np.ascontiguousarray(pads["pad_link"], np.int32),
+                "frame": np.ascontiguousarray(pads["pad_frame"], np.float32)}
+        Pd = ORPads()
+        Pd.pads_per_env, Pd.rows, Pd.cols = int(pads["pads_per_env"]), int(pads["rows"]), int(pads["cols"])
+        Pd.pitch = float(pads["pitch"])
+        Pd.pad_link, Pd.pad_frame = _p(keep["link"]), _p(keep["frame"])
+        for k in ("s_d", "alpha", "lambda_d", "c", "eps"):
+            setattr(Pd, k, float(pads[k]))
+        Pd.radius = int(pads["radius"])
+        I = ORInputs()
+        for k, dt in (("link_pose", np.float32), ("link_vel", np.float32), ("obj_pose", np.float32),
+                      ("obj_vel", np.float32), ("obj_id", np.int32)):
+            keep[k] = np.ascontiguousarray(inputs[k], dt)
+            setattr(I, k, _p(keep[k]))
+        if inputs.get("env_params") is not None:
+            keep["env_params"] = np.ascontiguousarray(inputs["env_params"], np.float32)
+            I.env_params = _p(keep["env_params"])
+        I.pose_dt = float(inputs.get("pose_dt", 0.0))
+        I.step = int(inputs.get("step", 0))
+        M = Pd.rows * Pd.cols
+        u = np.zeros((E, Pd.pads_per_env, M, 3))
+        h = np.zeros((E, Pd.pads_per_env, M))
+        lib().or_markers(C.byref(self.S), C.byref(Pd), C.byref(I), _p(u), _p(h), int(threads))
+        return u, h

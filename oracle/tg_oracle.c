@@ -417,6 +417,266 @@ void or_bake_grid(const float* V, const int32_t* F, int32_t nf, const int32_t di
 }
 
 /* ======================================================================== */
+/* Proximity by rays: the first root of the signed distance along a ray.    */
+/* The object frame may be scaled: phi_world(t) = s phi(q0 + t d) with d    */
+/* the world-unit ray direction mapped into the object frame (|d| = 1/s).   */
+/* grazing is set when the root is ill-posed: a crossing at a shallow      */
+/* angle (|d phi_world / dt| < 0.05) or a near miss (min phi_world < 2e-5). */
+/* ======================================================================== */
+#define OR_GRAZE_SLOPE 0.05
+#define OR_GRAZE_GAP 2e-5
+
+static double poly_eval(const double c[4], double t) { return ((c[3] * t + c[2]) * t + c[1]) * t + c[0]; }
+static double poly_deriv(const double c[4], double t) { return (3.0 * c[3] * t + 2.0 * c[2]) * t + c[1]; }
+
+/* first root of the cubic on [a, b] (NAN if none); tracks the minimum value */
+static double cubic_first_root(const double c[4], double a, double b, double* vmin) {
+    double pts[4];
+    int np = 0;
+    pts[np++] = a;
+    /* critical points inside (a, b) */
+    double A = 3.0 * c[3], B = 2.0 * c[2], Cc = c[1];
+    double crit[2];
+    int nc = 0;
+    if (A != 0.0) {
+        double disc = B * B - 4.0 * A * Cc;
+        if (disc >= 0.0) {
+            double sq = sqrt(disc);
+            double r1 = (-B - sq) / (2.0 * A), r2 = (-B + sq) / (2.0 * A);
+            if (r1 > r2) { double t = r1; r1 = r2; r2 = t; }
+            crit[nc++] = r1;
+            crit[nc++] = r2;
+        }
+    } else if (B != 0.0) {
+        crit[nc++] = -Cc / B;
+    }
+    for (int i = 0; i < nc; ++i)
+        if (crit[i] > a && crit[i] < b) pts[np++] = crit[i];
+    pts[np++] = b;
+    for (int i = 0; i < np; ++i) {
+        double v = poly_eval(c, pts[i]);
+        if (v < *vmin) *vmin = v;
+    }
+    for (int i = 0; i + 1 < np; ++i) {
+        double lo = pts[i], hi = pts[i + 1];
+        double flo = poly_eval(c, lo), fhi = poly_eval(c, hi);
+        if (flo == 0.0) return lo;
+        if (flo > 0.0 && fhi <= 0.0) {
+            if (fhi == 0.0 && hi == b) return hi;
+            for (int it = 0; it < 200 && hi - lo > 1e-18; ++it) {
+                double m = 0.5 * (lo + hi);
+                double fm = poly_eval(c, m);
+                if (fm > 0.0) lo = m; else hi = m;
+            }
+            return hi;
+        }
+        if (flo < 0.0) return lo; /* already inside (only at the first point) */
+    }
+    return NAN;
+}
+
+static void poly_mul_lin(const double p[4], double a0, double a1, double out[4]) {
+    /* (p0 + p1 t + p2 t^2 + p3 t^3) (a0 + a1 t), truncated at degree 3 */
+    double o[4];
+    o[0] = p[0] * a0;
+    o[1] = p[1] * a0 + p[0] * a1;
+    o[2] = p[2] * a0 + p[1] * a1;
+    o[3] = p[3] * a0 + p[2] * a1;
+    memcpy(out, o, sizeof(o));
+}
+
+static int cmp_double(const void* a, const void* b) {
+    double x = *(const double*)a, y = *(const double*)b;
+    return (x > y) - (x < y);
+}
+
+/* grid: trilinear field along the ray, cell by cell, as exact cubics */
+static double grid_first_root(const or_object* o, double scale, const double q0[3], const double d[3], double tmax,
+                              int* grazing) {
+    double h[3], ta = 0.0, tb = tmax;
+    for (int a = 0; a < 3; ++a) {
+        h[a] = (o->hi[a] - o->lo[a]) / (double)(o->dims[a] - 1);
+        if (d[a] == 0.0) {
+            if (q0[a] < o->lo[a] || q0[a] > o->hi[a]) return NAN;
+        } else {
+            double t1 = (o->lo[a] - q0[a]) / d[a], t2 = (o->hi[a] - q0[a]) / d[a];
+            if (t1 > t2) { double t = t1; t1 = t2; t2 = t; }
+            if (t1 > ta) ta = t1;
+            if (t2 < tb) tb = t2;
+        }
+    }
+    if (!(ta < tb)) return NAN;
+    /* parameters where the ray crosses a cell plane, plus the ends */
+    int cap = 2;
+    for (int a = 0; a < 3; ++a) cap += o->dims[a];
+    double* ts = (double*)malloc(sizeof(double) * (size_t)cap);
+    int nt = 0;
+    ts[nt++] = ta;
+    ts[nt++] = tb;
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0) continue;
+        for (int m = 0; m < o->dims[a]; ++m) {
+            double t = (o->lo[a] + m * h[a] - q0[a]) / d[a];
+            if (t > ta && t < tb) ts[nt++] = t;
+        }
+    }
+    qsort(ts, (size_t)nt, sizeof(double), cmp_double);
+    double vmin = INFINITY, root = NAN;
+    for (int k = 0; k + 1 < nt && isnan(root); ++k) {
+        double t0 = ts[k], t1 = ts[k + 1];
+        if (!(t1 > t0)) continue;
+        double tm = 0.5 * (t0 + t1);
+        int ci[3];
+        double x0[3], dx[3];
+        for (int a = 0; a < 3; ++a) {
+            double u = (q0[a] + tm * d[a] - o->lo[a]) / h[a];
+            int i = (int)floor(u);
+            if (i > o->dims[a] - 2) i = o->dims[a] - 2;
+            if (i < 0) i = 0;
+            ci[a] = i;
+            x0[a] = (q0[a] - (o->lo[a] + i * h[a])) / h[a];
+            dx[a] = d[a] / h[a];
+        }
+        double v[2][2][2];
+        for (int dz = 0; dz < 2; ++dz)
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dxx = 0; dxx < 2; ++dxx) v[dz][dy][dxx] = grid_node(o, ci[0] + dxx, ci[1] + dy, ci[2] + dz);
+        double a0 = v[0][0][0];
+        double ax = v[0][0][1] - v[0][0][0], ay = v[0][1][0] - v[0][0][0], az = v[1][0][0] - v[0][0][0];
+        double axy = v[0][1][1] - v[0][0][1] - v[0][1][0] + v[0][0][0];
+        double axz = v[1][0][1] - v[0][0][1] - v[1][0][0] + v[0][0][0];
+        double ayz = v[1][1][0] - v[0][1][0] - v[1][0][0] + v[0][0][0];
+        double axyz = v[1][1][1] - v[0][1][1] - v[1][0][1] - v[1][1][0] + v[0][0][1] + v[0][1][0] + v[1][0][0] - v[0][0][0];
+        double X[4] = {x0[0], dx[0], 0, 0}, Y[4] = {x0[1], dx[1], 0, 0}, Z[4] = {x0[2], dx[2], 0, 0};
+        double XY[4], XZ[4], YZ[4], XYZ[4];
+        poly_mul_lin(X, x0[1], dx[1], XY);
+        poly_mul_lin(X, x0[2], dx[2], XZ);
+        poly_mul_lin(Y, x0[2], dx[2], YZ);
+        poly_mul_lin(XY, x0[2], dx[2], XYZ);
+        double c[4];
+        for (int i = 0; i < 4; ++i)
+            c[i] = (i == 0 ? a0 : 0.0) + ax * X[i] + ay * Y[i] + az * Z[i] + axy * XY[i] + axz * XZ[i] + ayz * YZ[i] + axyz * XYZ[i];
+        root = cubic_first_root(c, t0, t1, &vmin);
+        if (!isnan(root)) {
+            double slope = scale * poly_deriv(c, root);
+            if (fabs(slope) < OR_GRAZE_SLOPE) *grazing = 1;
+        }
+    }
+    free(ts);
+    if (isnan(root) && scale * vmin < OR_GRAZE_GAP) *grazing = 1;
+    return root;
+}
+
+static double sphere_first_root(double r, double scale, const double q0[3], const double d[3], double tmax, int* grazing) {
+    double A = dot3(d, d), B = 2.0 * dot3(q0, d), Cc = dot3(q0, q0) - r * r;
+    double disc = B * B - 4.0 * A * Cc;
+    if (disc < 0.0) {
+        /* closest approach of the line */
+        double tc = -B / (2.0 * A);
+        if (tc > 0.0 && tc < tmax) {
+            double p[3] = {q0[0] + tc * d[0], q0[1] + tc * d[1], q0[2] + tc * d[2]};
+            if (scale * (norm3(p) - r) < OR_GRAZE_GAP) *grazing = 1;
+        }
+        return NAN;
+    }
+    double t = (-B - sqrt(disc)) / (2.0 * A);
+    if (t < 0.0 || t > tmax) return NAN;
+    double p[3] = {q0[0] + t * d[0], q0[1] + t * d[1], q0[2] + t * d[2]};
+    double slope = scale * dot3(p, d) / norm3(p);
+    if (fabs(slope) < OR_GRAZE_SLOPE) *grazing = 1;
+    return t;
+}
+
+static double box_first_root(const double hh[3], double scale, const double q0[3], const double d[3], double tmax,
+                             int* grazing) {
+    double ta = 0.0, tb = tmax;
+    int enter_axis = -1;
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0) {
+            if (q0[a] < -hh[a] || q0[a] > hh[a]) return NAN;
+        } else {
+            double t1 = (-hh[a] - q0[a]) / d[a], t2 = (hh[a] - q0[a]) / d[a];
+            if (t1 > t2) { double t = t1; t1 = t2; t2 = t; }
+            if (t1 > ta) { ta = t1; enter_axis = a; }
+            if (t2 < tb) tb = t2;
+        }
+    }
+    if (!(ta <= tb)) return NAN;
+    if (enter_axis >= 0 && fabs(scale * d[enter_axis]) < OR_GRAZE_SLOPE) *grazing = 1;
+    return ta;
+}
+
+static double mesh_first_root(const or_object* o, double scale, const double q0[3], const double d[3], double tmax,
+                              int* grazing) {
+    double best = NAN, best_slope = 0.0;
+    for (int32_t f = 0; f < o->n_faces; ++f) {
+        double a[3], b[3], c[3], e1[3], e2[3], pv[3], tv[3], qv[3];
+        vert(o->verts, o->faces[3 * f], a); vert(o->verts, o->faces[3 * f + 1], b); vert(o->verts, o->faces[3 * f + 2], c);
+        sub3(b, a, e1); sub3(c, a, e2);
+        cross3(d, e2, pv);
+        double det = dot3(e1, pv);
+        if (det == 0.0) continue;
+        double inv = 1.0 / det;
+        sub3(q0, a, tv);
+        double u = dot3(tv, pv) * inv;
+        if (u < 0.0 || u > 1.0) continue;
+        cross3(tv, e1, qv);
+        double v = dot3(d, qv) * inv;
+        if (v < 0.0 || u + v > 1.0) continue;
+        double t = dot3(e2, qv) * inv;
+        if (t < 0.0 || t > tmax) continue;
+        if (isnan(best) || t < best) {
+            double n[3];
+            cross3(e1, e2, n);
+            best = t;
+            best_slope = scale * dot3(d, n) / norm3(n);
+        }
+    }
+    if (!isnan(best) && fabs(best_slope) < OR_GRAZE_SLOPE) *grazing = 1;
+    return best;
+}
+
+double or_ray_first_root(const or_object* o, double scale, const double q0[3], const double d[3], double tmax,
+                         int* grazing) {
+    double g[3];
+    if (or_sdf_object(o, q0, g) <= 0.0) return 0.0;  /* the origin is inside: hit at once */
+    switch (o->kind) {
+    case OR_SPHERE: return sphere_first_root(o->radius, scale, q0, d, tmax, grazing);
+    case OR_BOX: return box_first_root(o->half, scale, q0, d, tmax, grazing);
+    case OR_PLANE: {
+        if (d[2] >= 0.0) return NAN;
+        double t = -q0[2] / d[2];
+        if (fabs(scale * d[2]) < OR_GRAZE_SLOPE) *grazing = 1;
+        return t <= tmax ? t : NAN;
+    }
+    case OR_MESH: return mesh_first_root(o, scale, q0, d, tmax, grazing);
+    case OR_GRID: return grid_first_root(o, scale, q0, d, tmax, grazing);
+    default: return NAN;
+    }
+}
+
+/* ray directions of one probe in the link frame: ray 0 along the normal n,
+   rays 1..n_rays-1 on a cone of half-angle `cone` around n at azimuths
+   2 pi (k-1)/(n_rays-1) from the tangent u = n x z (n x x if n is along z) */
+void or_prox_ray_dirs(const double n[3], int n_rays, double cone, double dirs[][3]) {
+    double ez[3] = {0, 0, 1}, ex[3] = {1, 0, 0}, u[3], v[3];
+    cross3(n, ez, u);
+    if (norm3(u) < 1e-6) cross3(n, ex, u);
+    double un = norm3(u);
+    for (int a = 0; a < 3; ++a) u[a] /= un;
+    cross3(n, u, v);
+    for (int a = 0; a < 3; ++a) dirs[0][a] = n[a];
+    for (int k = 1; k < n_rays; ++k) {
+        double az = 2.0 * PI * (double)(k - 1) / (double)(n_rays - 1);
+        for (int a = 0; a < 3; ++a)
+            dirs[k][a] = cos(cone) * n[a] + sin(cone) * (cos(az) * u[a] + sin(az) * v[a]);
+    }
+}
+
+/* Gaussian dilation kernel g(r) = exp(-lambda |r|^2) (Eq. 20) */
+double or_marker_kernel_g(double lambda_d, double r2) { return exp(-lambda_d * r2); }
+
+/* ======================================================================== */
 /* Sensor formulas                                                           */
 /* ======================================================================== */
 
@@ -619,6 +879,29 @@ static void env_step(const or_scene* S, const or_inputs* in, or_state* st, or_ou
                 size_t si = (size_t)(1 + c) * T + j;
                 hx[jl * 6 + c] = gain_hysteresis(&P->ft, P->dt, gain_f, fclean[jl * 6 + c], &st->hyst_prev[si], &st->hyst_xi[si]);
             }
+            /* proximity (rays from the probe centre, object frame, scaled) */
+            if (P->prox_rays > 0) {
+                double nl_[3] = {S->nx[j], S->ny[j], S->nz[j]};
+                double dirs[64][3];
+                or_prox_ray_dirs(nl_, P->prox_rays, P->prox_cone, dirs);
+                double reading = 0.0;
+                int grazing = 0;
+                for (int k = 0; k < P->prox_rays; ++k) {
+                    double dw[3], dobj[3];
+                    matvec(RL, dirs[k], dw);
+                    matTvec(RC, dw, dobj);
+                    for (int a = 0; a < 3; ++a) dobj[a] /= scale;
+                    double t = or_ray_first_root(obj, scale, qh, dobj, P->prox_range, &grazing);
+                    if (!isnan(t)) reading += 1.0 - t / P->prox_range;
+                }
+                reading /= (double)P->prox_rays;
+                out->prox_clean[j] = reading;
+                out->prox_grazing[j] = (uint8_t)grazing;
+                double gain_p = group_gain_on(&P->prox) ? P->prox.gain_lo + (P->prox.gain_hi - P->prox.gain_lo) * or_uniform(we[3]) : 1.0;
+                size_t sp = (size_t)7 * T + j;
+                double hp = gain_hysteresis(&P->prox, P->dt, gain_p, reading, &st->hyst_prev[sp], &st->hyst_xi[sp]);
+                out->prox_noisy[j] = base_noise(&P->prox, hp, zs[3], zs[2], &st->drift[sp], dead, or_uniform(wst[2]));
+            }
         }
     }
 
@@ -639,6 +922,7 @@ static void env_step(const or_scene* S, const or_inputs* in, or_state* st, or_ou
                 int64_t jl = lbase + (int64_t)r * cols + cc;
                 int64_t jg = t0 + jl;
                 if (!active[jl]) {
+                    if (P->prox_rays > 0) { out->prox_clean[jg] = 0.0; out->prox_noisy[jg] = 0.0; out->prox_grazing[jg] = 0; }
                     out->depth_noisy[jg] = 0.0; out->dist[jg] = 0.0;
                     out->depth_clean[jg] = 0.0;
                     out->contact_clean[jg] = 0; out->contact_noisy[jg] = 0;
@@ -725,4 +1009,91 @@ int or_step(const or_scene* S, const or_inputs* in, or_state* st, or_outputs* ou
 #pragma omp parallel for schedule(dynamic, 1)
     for (int32_t e = 0; e < S->n_envs; ++e) env_step(S, in, st, out, e);
     return 0;
+}
+
+/* ======================================================================== */
+/* ElastomerTaxel dilation (Eqs. 18-21) on planar marker pads: marker depth  */
+/* h_i = max(0, -phi(q_i)) (no radius), then for each marker j the sum over */
+/* sources i within `radius` markers of s_d (r_ij w_ij + n h_i^alpha g),   */
+/* w_ij = h_i (c g / g_bar + (1 - c) rho / rho_bar), r_ij = Pi_n(x_j - x_i). */
+/* ======================================================================== */
+static void env_markers(const or_scene* S, const or_pads* pads, const or_inputs* in, double* u, double* h_out, int32_t e) {
+    const int32_t L = S->max_links, P = pads->pads_per_env, M = pads->rows * pads->cols;
+    double scale = in->env_params ? in->env_params[3 * e + 2] : 1.0;
+    const or_object* obj = &S->objects[in->obj_id[e]];
+    double pC0[3], qC0[4], vC[3], wC[3], pC[3], RC[9];
+    for (int a = 0; a < 3; ++a) pC0[a] = in->obj_pose[7 * e + a];
+    for (int a = 0; a < 4; ++a) qC0[a] = in->obj_pose[7 * e + 3 + a];
+    for (int a = 0; a < 3; ++a) { vC[a] = in->obj_vel[6 * e + a]; wC[a] = in->obj_vel[6 * e + 3 + a]; }
+    or_advance_pose(pC0, qC0, vC, wC, in->pose_dt, pC, RC);
+    const double gbar = exp(-0.5) / sqrt(2.0 * pads->lambda_d);
+    const double rbar = 1.0 / (2.0 * pads->eps);
+    double* xs = (double*)malloc(sizeof(double) * 3 * (size_t)M);
+    double* hs = (double*)malloc(sizeof(double) * (size_t)M);
+    for (int32_t p = 0; p < P; ++p) {
+        int32_t l = pads->pad_link[e * P + p];
+        const float* fr = pads->pad_frame + ((size_t)e * P + p) * 9;
+        double o[3] = {fr[0], fr[1], fr[2]}, n[3] = {fr[3], fr[4], fr[5]}, tu[3] = {fr[6], fr[7], fr[8]}, tv[3];
+        cross3(n, tu, tv);
+        const float* lp = in->link_pose + ((size_t)e * L + l) * 7;
+        const float* lv = in->link_vel + ((size_t)e * L + l) * 6;
+        double pL0[3], qL0[4], vL[3], wL[3], pL[3], RL[9];
+        for (int a = 0; a < 3; ++a) pL0[a] = lp[a];
+        for (int a = 0; a < 4; ++a) qL0[a] = lp[3 + a];
+        for (int a = 0; a < 3; ++a) { vL[a] = lv[a]; wL[a] = lv[3 + a]; }
+        or_advance_pose(pL0, qL0, vL, wL, in->pose_dt, pL, RL);
+        for (int32_t m = 0; m < M; ++m) {
+            int32_t ra = m / pads->cols, cb = m % pads->cols;
+            double sa = (ra - 0.5 * (pads->rows - 1)) * pads->pitch, sb = (cb - 0.5 * (pads->cols - 1)) * pads->pitch;
+            double x[3], q[3], dq[3], qh[3], g[3];
+            for (int a = 0; a < 3; ++a) x[a] = o[a] + sa * tu[a] + sb * tv[a];
+            for (int a = 0; a < 3; ++a) xs[3 * m + a] = x[a];
+            matvec(RL, x, q);
+            for (int a = 0; a < 3; ++a) q[a] += pL[a];
+            sub3(q, pC, dq);
+            matTvec(RC, dq, qh);
+            for (int a = 0; a < 3; ++a) qh[a] /= scale;
+            double phi = scale * or_sdf_object(obj, qh, g);
+            hs[m] = phi < 0.0 ? -phi : 0.0;
+            if (h_out) h_out[((size_t)e * P + p) * M + m] = hs[m];
+        }
+        for (int32_t j = 0; j < M; ++j) {
+            int32_t rj = j / pads->cols, cj = j % pads->cols;
+            double acc[3] = {0, 0, 0};
+            for (int32_t di = -pads->radius; di <= pads->radius; ++di)
+                for (int32_t dj = -pads->radius; dj <= pads->radius; ++dj) {
+                    int32_t ri = rj + di, ci = cj + dj;
+                    if (ri < 0 || ri >= pads->rows || ci < 0 || ci >= pads->cols) continue;
+                    int32_t i = ri * pads->cols + ci;
+                    double h = hs[i];
+                    if (h == 0.0) continue;
+                    double dx[3], r[3];
+                    sub3(&xs[3 * j], &xs[3 * i], dx);
+                    double dn = dot3(dx, n);
+                    for (int a = 0; a < 3; ++a) r[a] = dx[a] - dn * n[a];
+                    double r2 = dot3(r, r);
+                    double gk = or_marker_kernel_g(pads->lambda_d, r2);
+                    double rho = 1.0 / (r2 + pads->eps * pads->eps);
+                    double w = h * (pads->c * gk / gbar + (1.0 - pads->c) * rho / rbar);
+                    double hn = pow(h, pads->alpha) * gk;
+                    for (int a = 0; a < 3; ++a) acc[a] += pads->s_d * (r[a] * w + n[a] * hn);
+                }
+            double* uo = u + (((size_t)e * P + p) * M + j) * 3;
+            uo[0] = dot3(acc, n);
+            uo[1] = dot3(acc, tu);
+            uo[2] = dot3(acc, tv);
+        }
+    }
+    free(xs);
+    free(hs);
+}
+
+void or_markers(const or_scene* S, const or_pads* pads, const or_inputs* in, double* u, double* h_out, int32_t threads) {
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#else
+    (void)threads;
+#endif
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t e = 0; e < S->n_envs; ++e) env_markers(S, pads, in, u, h_out, e);
 }

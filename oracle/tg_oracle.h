@@ -60,7 +60,22 @@ typedef struct {
     double p_dead;            /* dead-taxel probability */
     or_noise_group depth, ft, prox;
     double chi, xt_sigma;     /* spatial crosstalk strength and Gaussian sigma (lattice steps) */
+    /* proximity by rays: n_rays (0 = off) over range prox_range (m); ray 0
+       along the probe normal, the others on a cone of half-angle prox_cone */
+    int32_t prox_rays;
+    double prox_range, prox_cone;
 } or_params;
+
+/* elastomer marker pads (ElastomerTaxel dilation, Eqs. 18-21) */
+typedef struct {
+    int32_t pads_per_env;        /* P (0 = off) */
+    int32_t rows, cols;          /* markers per pad */
+    double pitch;                /* marker spacing (m) */
+    const int32_t* pad_link;     /* [E][P] link slot carrying the pad */
+    const float* pad_frame;      /* [E][P][9]: origin(3), normal(3), tangent(3), link frame */
+    double s_d, alpha, lambda_d, c, eps; /* dilation scale, depth power, Gaussian rate, compressibility, regularisation */
+    int32_t radius;              /* neighbourhood half-width in markers (2 = 5x5) */
+} or_pads;
 
 typedef struct {
     int32_t n_envs, max_links;
@@ -104,6 +119,8 @@ typedef struct {
 
 typedef struct {
     uint8_t* contact_clean; uint8_t* contact_noisy;   /* [T] */
+    double* prox_clean; double* prox_noisy;           /* [T] (proximity on) */
+    uint8_t* prox_grazing;                            /* [T] 1: a ray grazes the surface (root ill-posed) */
     double* depth_clean; double* depth_noisy;         /* [T] */
     double* dist;                                     /* [T] phi - R */
     double* ft_clean; double* ft_noisy;               /* [6][T] */
@@ -140,9 +157,16 @@ void or_sdf_object_batch(const or_object* o, const double* q, int64_t n, double*
 void or_bake_grid(const float* V, const int32_t* F, int32_t nf, const int32_t dims[3],
                   const double lo[3], const double hi[3], int32_t fp16, void* out, int32_t threads);
 
+double or_ray_first_root(const or_object* o, double scale, const double q0[3], const double d[3], double tmax,
+                         int* grazing);
+void or_prox_ray_dirs(const double n[3], int n_rays, double cone, double dirs[][3]);
+double or_marker_kernel_g(double lambda_d, double r2);
+
 /* ---- whole-scene operations ------------------------------------------------- */
 void or_reset(const or_scene* S, const uint8_t* env_mask, uint32_t episode, or_state* st);
 int or_step(const or_scene* S, const or_inputs* in, or_state* st, or_outputs* out, int32_t threads);
+/* marker displacements u [E][P][rows*cols][3] (pad frame: normal, tangent, normal x tangent) */
+void or_markers(const or_scene* S, const or_pads* pads, const or_inputs* in, double* u, double* h_out, int32_t threads);
 
 #ifdef __cplusplus
 }

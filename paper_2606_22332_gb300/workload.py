@@ -50,6 +50,7 @@ def default_params(seed: int) -> dict:
         k=1e4, c=5.0, alpha=1.0, k_t=2.0, k_omega=2.0, mu=0.8,
         eta_on=5e-4, eta_off=2e-4, dt=DT, seed=int(seed), p_dead=0.02,
         chi=0.05, xt_sigma=1.0,
+        prox_rays=0, prox_range=0.05, prox_cone=float(np.radians(30.0)),
         noise=dict(
             depth=noise_group(beta=0.1, tau=0.05),
             ft=noise_group(beta=0.1, tau=0.05, sigma_rw=1e-3),
