@@ -83,10 +83,38 @@ typedef struct {
     double chi, xt_sigma;             /* crosstalk strength, Gaussian sigma in lattice steps */
     uint64_t seed;                    /* Philox4x32-10 key */
     tg_noise_group depth, ft, prox;   /* per sensor group */
+    /* proximity rays (TG_SENSOR_PROX): n rays from the probe centre, ray 0
+       along the probe normal, the others on a cone of half-angle prox_cone
+       (rad) at equal azimuths from the tangent n x z (n x x when n is along z);
+       reading = mean over rays of hit (1 - t / prox_range), t the distance to
+       the first surface crossing along the ray */
+    int32_t prox_rays;                /* 1..16 */
+    double prox_range, prox_cone;
 } tg_params;
 
 /* sensor mask bits (depth, contact and force/torque are always computed) */
 #define TG_SENSOR_DIST 0x1u           /* SurfaceDistanceProbe output phi - R */
+#define TG_SENSOR_PROX 0x2u           /* proximity by rays (geometry-aware ProximityTaxel form) */
+#define TG_SENSOR_MARKERS 0x4u        /* ElastomerTaxel marker dilation on planar pads */
+
+/* Elastomer marker pads (ElastomerTaxel, Eqs. 18-21): every env carries
+   pads_per_env planar pads of rows x cols markers at `pitch`, each fixed in a
+   link frame.  Marker depth h = max(0, -phi) (no probe radius); the
+   displacement of marker j sums, over markers i within `radius` of j on the
+   pad, s_d (r_ij w_ij + n h_i^alpha g(r_ij)) with r_ij the in-plane offset
+   x_j - x_i, g(r) = exp(-lambda_d |r|^2), w_ij = h_i (c g / g_bar +
+   (1 - c) rho / rho_bar), rho = 1 / (|r|^2 + eps^2); g_bar and rho_bar are
+   the peaks of r g(r) and r rho(r).  Output per marker: (normal, tangent,
+   normal x tangent) components. */
+typedef struct {
+    int32_t pads_per_env;             /* P >= 0 */
+    int32_t rows, cols;               /* rows * cols <= 1024 */
+    double pitch;
+    const int32_t* pad_link;          /* host [E][P]: link slot carrying the pad (a present link) */
+    const float* pad_frame;           /* host [E][P][9]: origin, unit normal, unit tangent (link frame) */
+    double s_d, alpha, lambda_d, c, eps;
+    int32_t radius;                   /* neighbourhood half-width in markers, 0..4 */
+} tg_pad_desc;
 
 typedef struct {
     int32_t n_envs;                   /* E >= 1 */
@@ -102,6 +130,7 @@ typedef struct {
     uint32_t sensors;                 /* TG_SENSOR_* mask */
     int64_t taxel_gid0;               /* global id of taxel 0 in the RNG counters (sharding) */
     int32_t env_gid0;                 /* global id of env 0 */
+    tg_pad_desc pads;                 /* used when sensors has TG_SENSOR_MARKERS */
 } tg_scene_desc;
 
 /* Create a scene: validates the layout, copies the taxel geometry to the
@@ -172,7 +201,9 @@ typedef enum {
     TG_CH_FORCE_TORQUE = 3,   /* float [6][T]: fx fy fz tx ty tz, link frame */
     TG_CH_LINK_WRENCH = 4,    /* float [E*L][18]: F_clean T_clean F_noisy T_noisy agg_clean agg_noisy */
     TG_CH_LINK_COUNT = 5,     /* int32 [E*L][2]: contact count clean, noisy (agg_bool = count > 2) */
-    TG_CH_STATE_FLAGS = 6     /* uint8 [T]: bit0 clean contact, bit1 dead, bit2 noisy contact */
+    TG_CH_STATE_FLAGS = 6,    /* uint8 [T]: bit0 clean contact, bit1 dead, bit2 noisy contact */
+    TG_CH_PROX = 7,           /* float [T] (needs TG_SENSOR_PROX) */
+    TG_CH_MARKER = 8          /* float [E*P*rows*cols][3] (needs TG_SENSOR_MARKERS); clean only */
 } tg_channel;
 
 /* Copy one output channel (clean or noisy) into dst (host or device),

@@ -46,6 +46,12 @@ struct tg_scene {
     uint8_t* s_mask = nullptr;
     uint8_t* s_contact = nullptr;
     int32_t* item_order = nullptr;    // per-step object-sorted item order
+    // proximity and markers
+    float *prox_clean = nullptr, *prox_noisy = nullptr;
+    MarkerArgs markers{};
+    int32_t* pad_link = nullptr;
+    float* pad_frame = nullptr;
+    float* marker_u = nullptr;
 
     std::string last_error;
     // kernel timing (tg_profile_*)
@@ -134,6 +140,8 @@ const char* make_params(const tg_params& p, ParamsDev* out) {
     if (p.p_dead < 0.0 || p.p_dead > 1.0) return "p_dead outside [0, 1]";
     if (!(p.alpha > 0.0)) return "alpha must be positive";
     if (p.chi != 0.0 && !(p.xt_sigma > 0.0)) return "crosstalk needs xt_sigma > 0";
+    if (p.prox_rays < 0 || p.prox_rays > 16 || !finite(p.prox_range) || !finite(p.prox_cone))
+        return "prox_rays must be in 0..16 with finite range and cone";
     for (const tg_noise_group* g : {&p.depth, &p.ft, &p.prox})
         if (const char* m = check_group(*g)) return m;
     ParamsDev d{};
@@ -161,6 +169,15 @@ const char* make_params(const tg_params& p, ParamsDev* out) {
     d.depth = make_group(p.depth, p.dt);
     d.ft = make_group(p.ft, p.dt);
     d.prox = make_group(p.prox, p.dt);
+    d.prox_rays = p.prox_rays;
+    d.prox_range = (float)p.prox_range;
+    d.prox_cos = (float)std::cos(p.prox_cone);
+    d.prox_sin = (float)std::sin(p.prox_cone);
+    for (int k = 0; k < 16; ++k) {
+        const double az = (k >= 1 && p.prox_rays > 1) ? 2.0 * 3.14159265358979323846 * (k - 1) / (p.prox_rays - 1) : 0.0;
+        d.prox_az_cos[k] = (float)std::cos(az);
+        d.prox_az_sin[k] = (float)std::sin(az);
+    }
     *out = d;
     return nullptr;
 }
@@ -192,6 +209,8 @@ StepArgs step_args(tg_scene* s) {
     a.link_out = s->link_out;
     a.link_count = s->link_count;
     a.err = s->err;
+    a.prox_clean = s->prox_clean;
+    a.prox_noisy = s->prox_noisy;
     return a;
 }
 
@@ -277,6 +296,23 @@ tg_status tg_create_scene(const tg_scene_desc* d, tg_scene** out) {
         return fail(nullptr, TG_ERR_INVALID_ARG, "taxel geometry pointers are required");
     ParamsDev P;
     if (const char* m = make_params(d->params, &P)) return fail(nullptr, TG_ERR_INVALID_ARG, m);
+    if ((d->sensors & TG_SENSOR_PROX) && (d->params.prox_rays < 1 || !(d->params.prox_range > 0.0)))
+        return fail(nullptr, TG_ERR_INVALID_ARG, "TG_SENSOR_PROX needs prox_rays in 1..16 and prox_range > 0");
+    const tg_pad_desc& pd = d->pads;
+    if (d->sensors & TG_SENSOR_MARKERS) {
+        if (pd.pads_per_env < 1 || pd.rows < 1 || pd.cols < 1 || pd.rows * pd.cols > kMaxPadMarkers ||
+            pd.radius < 0 || pd.radius > kMaxPadRadius || !(pd.pitch > 0.0) || !pd.pad_link || !pd.pad_frame ||
+            !(pd.lambda_d > 0.0) || !(pd.eps > 0.0) || !std::isfinite(pd.s_d) || !std::isfinite(pd.alpha) || !std::isfinite(pd.c))
+            return fail(nullptr, TG_ERR_INVALID_ARG,
+                        "TG_SENSOR_MARKERS needs pads_per_env >= 1, rows*cols <= 1024, radius <= 4, pitch, "
+                        "lambda_d, eps > 0 and the pad_link / pad_frame arrays");
+        for (int i = 0; i < d->n_envs * pd.pads_per_env; ++i) {
+            const int l = pd.pad_link[i];
+            const int e = i / pd.pads_per_env;
+            if (l < 0 || l >= d->max_links || d->link_rows[e * d->max_links + l] == 0)
+                return fail(nullptr, TG_ERR_INVALID_ARG, "pad_link must name a present link of the env");
+        }
+    }
 
     // lattice table and work items
     std::vector<LinkLattice> lat((size_t)E * L);
@@ -379,6 +415,46 @@ tg_status tg_create_scene(const tg_scene_desc* d, tg_scene** out) {
     CKC(dalloc(&s->s_mask, E));
     CKC(dalloc(&s->s_contact, T));
     CKC(dalloc(&s->item_order, items.size()));
+    if (d->sensors & TG_SENSOR_PROX) {
+        CKC(dalloc(&s->prox_clean, T));
+        CKC(dalloc(&s->prox_noisy, T));
+        CKC(cudaMemset(s->prox_clean, 0, (size_t)T * sizeof(float)));
+        CKC(cudaMemset(s->prox_noisy, 0, (size_t)T * sizeof(float)));
+    }
+    if (d->sensors & TG_SENSOR_MARKERS) {
+        const size_t EP = (size_t)E * pd.pads_per_env, M = (size_t)pd.rows * pd.cols;
+        CKC(dalloc(&s->pad_link, EP));
+        CKC(dalloc(&s->pad_frame, EP * 9));
+        CKC(dalloc(&s->marker_u, EP * M * 3));
+        CKC(cudaMemcpy(s->pad_link, pd.pad_link, EP * sizeof(int32_t), cudaMemcpyHostToDevice));
+        CKC(cudaMemcpy(s->pad_frame, pd.pad_frame, EP * 9 * sizeof(float), cudaMemcpyHostToDevice));
+        CKC(cudaMemset(s->marker_u, 0, EP * M * 3 * sizeof(float)));
+        MarkerArgs& m = s->markers;
+        m.n_envs = E;
+        m.max_links = L;
+        m.pads_per_env = pd.pads_per_env;
+        m.rows = pd.rows;
+        m.cols = pd.cols;
+        m.radius = pd.radius;
+        m.pitch = (float)pd.pitch;
+        m.alpha = (float)pd.alpha;
+        m.pad_link = s->pad_link;
+        m.pad_frame = s->pad_frame;
+        m.link_rec = s->link_rec;
+        m.u = s->marker_u;
+        m.err = s->err;
+        // per-offset weights: w_norm = s_d g(r), w_tan = s_d (c g / g_bar + (1 - c) rho / rho_bar)
+        const double gbar = std::exp(-0.5) / std::sqrt(2.0 * pd.lambda_d), rbar = 1.0 / (2.0 * pd.eps);
+        const int W = 2 * pd.radius + 1;
+        for (int di = -pd.radius; di <= pd.radius; ++di)
+            for (int dj = -pd.radius; dj <= pd.radius; ++dj) {
+                const double r2 = (di * di + dj * dj) * pd.pitch * pd.pitch;
+                const double g = std::exp(-pd.lambda_d * r2), rho = 1.0 / (r2 + pd.eps * pd.eps);
+                const int w = (di + pd.radius) * W + (dj + pd.radius);
+                m.w_norm[w] = (float)(pd.s_d * g);
+                m.w_tan[w] = (float)(pd.s_d * (pd.c * g / gbar + (1.0 - pd.c) * rho / rbar));
+            }
+    }
 
     CKC(cudaMemset(s->link_out, 0, EL * kLinkOut * sizeof(float)));
     CKC(cudaMemset(s->link_count, 0, EL * 2 * sizeof(int32_t)));
@@ -409,7 +485,8 @@ void tg_destroy_scene(tg_scene* s) {
                     s->hyst_xi, s->drift, s->episode, s->depth_clean, s->depth_noisy, s->dist, s->ft_clean,
                     s->ft_noisy, s->link_out, s->link_count, s->err, s->link_rec, s->s_link_pose, s->s_link_vel,
                     s->s_obj_pose, s->s_obj_vel, s->s_env_params, s->s_obj_id, s->s_mask, s->s_contact,
-                    s->item_order};
+                    s->item_order, s->prox_clean, s->prox_noisy, s->pad_link, s->pad_frame,
+                    s->marker_u};
     for (void* p : ptrs) dfree(p);
     delete s;
 }
@@ -570,6 +647,14 @@ tg_status tg_step_sensors(tg_scene* s, const tg_step_inputs* in, tg_stream strea
     if (s->profiling) CK(s, cudaEventRecord(ev[1], st));
     CK(s, launch_step(a, s->n_items, st));
     if (s->profiling) CK(s, cudaEventRecord(ev[2], st));
+    if (s->sensors & TG_SENSOR_PROX) CK(s, launch_prox(a, s->n_items, st));
+    if (s->sensors & TG_SENSOR_MARKERS) {
+        MarkerArgs m = s->markers;
+        m.obj_id = oid;
+        m.objects = s->objects;
+        m.n_objects = s->n_objects;
+        CK(s, launch_markers(m, st));
+    }
     return TG_OK;
 }
 
@@ -611,6 +696,11 @@ size_t tg_channel_bytes(const tg_scene* s, int32_t ch) {
     case TG_CH_LINK_WRENCH: return EL * kLinkOut * 4;
     case TG_CH_LINK_COUNT: return EL * 8;
     case TG_CH_STATE_FLAGS: return T;
+    case TG_CH_PROX: return (s->sensors & TG_SENSOR_PROX) ? T * 4 : 0;
+    case TG_CH_MARKER:
+        return (s->sensors & TG_SENSOR_MARKERS)
+                   ? (size_t)s->E * s->markers.pads_per_env * s->markers.rows * s->markers.cols * 12
+                   : 0;
     default: return 0;
     }
 }
@@ -626,6 +716,8 @@ tg_status tg_get_buffer(tg_scene* s, int32_t ch, int32_t noisy, void** ptr, size
     case TG_CH_LINK_WRENCH: p = s->link_out; break;
     case TG_CH_LINK_COUNT: p = s->link_count; break;
     case TG_CH_STATE_FLAGS: p = s->flags; break;
+    case TG_CH_PROX: p = (s->sensors & TG_SENSOR_PROX) ? (noisy ? s->prox_noisy : s->prox_clean) : nullptr; break;
+    case TG_CH_MARKER: p = (s->sensors & TG_SENSOR_MARKERS) ? s->marker_u : nullptr; break;
     default: break;
     }
     if (!p) return fail(s, TG_ERR_INVALID_ARG, "channel has no device view (or its sensor is off)");

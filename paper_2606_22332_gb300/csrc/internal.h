@@ -33,6 +33,10 @@ struct ParamsDev {
     float xt_w[9];                        // L1-normalised 3x3 Gaussian, row-major
     uint64_t seed;
     NoiseDev depth, ft, prox;
+    // proximity rays
+    int prox_rays;
+    float prox_range, prox_cos, prox_sin;
+    float prox_az_cos[16], prox_az_sin[16];
 };
 
 // Object table entry (object frame).
@@ -103,6 +107,27 @@ struct StepArgs {
     float* link_out;                  // [E*L][kLinkOut]
     int32_t* link_count;              // [E*L][2]
     unsigned int* err;                // [0] non-finite count
+    float* prox_clean;                // [T] (proximity on)
+    float* prox_noisy;                // [T]
+};
+
+// Elastomer marker pads (one CTA per (env, pad)).
+constexpr int kMaxPadMarkers = 1024;
+constexpr int kMaxPadRadius = 4;
+struct MarkerArgs {
+    int n_envs, max_links, pads_per_env, rows, cols, radius;
+    float pitch, alpha;
+    const int32_t* pad_link;          // [E][P]
+    const float* pad_frame;           // [E][P][9]
+    const float* link_rec;            // pose records
+    const int32_t* obj_id;
+    const ObjDev* objects;
+    int n_objects;
+    // per-offset constants over the (2 radius + 1)^2 neighbourhood, offset o = source - target
+    float w_norm[(2 * kMaxPadRadius + 1) * (2 * kMaxPadRadius + 1)];  // s_d g(r)
+    float w_tan[(2 * kMaxPadRadius + 1) * (2 * kMaxPadRadius + 1)];   // s_d (c g / g_bar + (1 - c) rho / rho_bar)
+    float* u;                         // [E][P][rows*cols][3]
+    unsigned int* err;
 };
 
 struct PoseArgs {
@@ -130,6 +155,8 @@ cudaError_t launch_mesh_sdf_points(const float* tri, const float* tri_n, int n_f
 cudaError_t launch_mesh_bake(const float* tri, const float* tri_n, int n_faces, const int dims[3],
                              const float lo[3], const float hi[3], int fp16, void* out, cudaStream_t s);
 cudaError_t launch_build_cells(const void* values, const int dims[3], int fp16, void* cells, cudaStream_t s);
+cudaError_t launch_prox(const StepArgs& a, int n_items, cudaStream_t s);
+cudaError_t launch_markers(const MarkerArgs& m, cudaStream_t s);
 cudaError_t launch_unpack_contact(const uint8_t* flags, int64_t n, int noisy, uint8_t* out, cudaStream_t s);
 
 }  // namespace tg

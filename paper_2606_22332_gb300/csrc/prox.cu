@@ -1,0 +1,227 @@
+// prox.cu -- geometry-aware proximity by rays (the ProximityTaxel reading in
+// its ray form) and its noise chain.
+//
+// From each active probe centre, rays leave along the probe normal and on a
+// cone around it; each ray is sphere-traced through the object's signed
+// distance (step max(phi, 10 um), at most 192 steps).  When a sample falls
+// inside, the crossing is bracketed by it and the last outside sample and
+// refined by the Illinois variant of regula falsi, so the reported distance
+// is the first surface crossing along the ray.  The reading is the mean over
+// rays of hit (1 - t / range).  Noise (Eqs. 25-30): gain, hysteresis, bias,
+// white noise and drift, quantisation, dead override.
+// One CTA per work item, items in the object-sorted order of the step.
+#include "step_common.cuh"
+
+namespace tg {
+
+constexpr int kProxThreads = 256;
+constexpr int kProxItemLinks = 32;
+constexpr float kMinStep = 1e-5f;
+constexpr int kMaxMarch = 192;
+
+// signed distance in world units along the ray q0 + t d (object frame, d
+// already scaled by 1/s)
+__device__ __forceinline__ float ray_field(const ObjDev& obj, float3 q0, float3 d, float t, float scale) {
+    float3 go;
+    return scale * sdf_fast(obj, q0 + d * t, &go);
+}
+
+// first crossing on [ta, tb] with f(ta) > 0 >= f(tb), Illinois regula falsi
+__device__ __forceinline__ float refine_root(const ObjDev& obj, float3 q0, float3 d, float scale, float ta, float fa,
+                                             float tb, float fb) {
+    int side = 0;
+    for (int it = 0; it < 24 && tb - ta > 1e-7f; ++it) {
+        const float tc = (fa * tb - fb * ta) / (fa - fb);
+        const float fc = ray_field(obj, q0, d, tc, scale);
+        if (fc > 0.0f) {
+            ta = tc; fa = fc;
+            if (side == -1) fb *= 0.5f;
+            side = -1;
+        } else {
+            tb = tc; fb = fc;
+            if (side == 1) fa *= 0.5f;
+            side = 1;
+        }
+    }
+    return tb;
+}
+
+// distance to the first surface crossing along one ray, or -1 (no hit):
+// march by max(phi, 10 um) until a sample falls inside, then refine between
+// the last outside and the first inside sample.  192 steps reach the end of
+// the range even for rays meeting the surface at 3 degrees (the geometric
+// convergence of sphere tracing at incidence theta shrinks phi by
+// (1 - sin theta) per step).
+__device__ __forceinline__ float trace_ray(const ObjDev& obj, float3 q0, float3 d, float scale, float range) {
+    float t = 0.0f;
+    float f = ray_field(obj, q0, d, 0.0f, scale);
+    if (!(f > 0.0f)) return 0.0f;  // the probe centre is inside
+    for (int it = 0; it < kMaxMarch; ++it) {
+        const float tn = t + fmaxf(f, kMinStep);
+        if (tn > range) {
+            // the last stretch up to the range end
+            const float fe = ray_field(obj, q0, d, range, scale);
+            return fe > 0.0f ? -1.0f : refine_root(obj, q0, d, scale, t, f, range, fe);
+        }
+        const float fn = ray_field(obj, q0, d, tn, scale);
+        if (!(fn > 0.0f)) return refine_root(obj, q0, d, scale, t, f, tn, fn);
+        t = tn;
+        f = fn;
+    }
+    return -1.0f;
+}
+
+__global__ void __launch_bounds__(kProxThreads) prox_kernel(const StepArgs a) {
+    __shared__ float rec_s[kProxItemLinks][kLinkRec];
+    __shared__ int start_s[kProxItemLinks + 1];
+    __shared__ ObjDev obj_s;
+    const Item it = a.items[a.item_order ? a.item_order[blockIdx.x] : blockIdx.x];
+    const int e = it.env, L = a.max_links, lb = it.link_begin, nl = it.link_end - it.link_begin, n = it.n_taxels;
+    const ParamsDev& P = a.P;
+    for (int i = threadIdx.x; i < nl * kLinkRec; i += kProxThreads)
+        rec_s[i / kLinkRec][i % kLinkRec] = a.link_rec[(size_t)(e * L + lb + i / kLinkRec) * kLinkRec + i % kLinkRec];
+    if ((int)threadIdx.x <= nl) {
+        const int base = a.lattice[e * L + lb].env_offset;
+        start_s[threadIdx.x] = (int)threadIdx.x < nl ? a.lattice[e * L + lb + threadIdx.x].env_offset - base : n;
+    }
+    if (threadIdx.x == 0) {
+        int oid = min(max(a.obj_id[e], 0), a.n_objects - 1);
+        obj_s = a.objects[oid];
+    }
+    __syncthreads();
+    const uint32_t ep = a.episode[e];
+    const int64_t T = a.n_taxels;
+    int l = 0;
+    for (int i = threadIdx.x; i < n; i += kProxThreads) {
+        while (i >= start_s[l + 1]) ++l;
+        const int64_t g = it.taxel_begin + i;
+        const float R = a.R[g];
+        if (!(R > 0.0f)) {
+            a.prox_clean[g] = 0.0f;
+            a.prox_noisy[g] = 0.0f;
+            continue;
+        }
+        const float* rec = rec_s[l];
+        const float x0 = a.x[g], x1 = a.y[g], x2 = a.z[g];
+        const float3 nl_ = f3(a.nx[g], a.ny[g], a.nz[g]);
+        const float3 q0 = f3(fmaf(rec[0], x0, fmaf(rec[1], x1, fmaf(rec[2], x2, rec[18]))),
+                             fmaf(rec[3], x0, fmaf(rec[4], x1, fmaf(rec[5], x2, rec[19]))),
+                             fmaf(rec[6], x0, fmaf(rec[7], x1, fmaf(rec[8], x2, rec[20]))));
+        // ray fan in the link frame: n, then the cone around n
+        float3 u = cross(nl_, f3(0.f, 0.f, 1.f));
+        if (dot(u, u) < 1e-12f) u = cross(nl_, f3(1.f, 0.f, 0.f));
+        u = normalize_or(u, f3(1.f, 0.f, 0.f));
+        const float3 v = cross(nl_, u);
+        const float scale = rec[38];
+        float reading = 0.0f;
+        for (int k = 0; k < P.prox_rays; ++k) {
+            float3 dl = nl_;
+            if (k > 0) dl = nl_ * P.prox_cos + (u * P.prox_az_cos[k] + v * P.prox_az_sin[k]) * P.prox_sin;
+            const float3 dobj = f3(rec[0] * dl.x + rec[1] * dl.y + rec[2] * dl.z,
+                                   rec[3] * dl.x + rec[4] * dl.y + rec[5] * dl.z,
+                                   rec[6] * dl.x + rec[7] * dl.y + rec[8] * dl.z);
+            const float t = trace_ray(obj_s, q0, dobj, scale, P.prox_range);
+            if (t >= 0.0f) reading += 1.0f - t / P.prox_range;
+        }
+        reading /= (float)P.prox_rays;
+        a.prox_clean[g] = reading;
+        // noise chain of the proximity group
+        const NoiseDev& G = P.prox;
+        const uint64_t gid = (uint64_t)(a.gid0 + g);
+        const bool dead = a.flags[g] & 2u;
+        float x = reading;
+        if (G.gain_on) x *= G.gain_lo + G.gain_span * u24(draw(P.seed, gid, ep, TAG_EPISODE).w);
+        if (G.beta != 0.0f) x = hyst_update(G, x, a.hyst_prev + 7 * T + g, a.hyst_xi + 7 * T + g);
+        if (G.sigma_rw != 0.0f || G.sigma_white != 0.0f) {
+            const uint4 w = draw(P.seed, gid, a.step, TAG_SCALAR);
+            const float2 z = box_muller(w.z, w.w);
+            float dr = 0.0f;
+            if (G.sigma_rw != 0.0f) {
+                dr = a.drift[7 * T + g] + G.sigma_rw * z.x;
+                a.drift[7 * T + g] = dr;
+            }
+            x = x + G.bias + G.sigma_white * z.y + dr;
+        } else {
+            x += G.bias;
+        }
+        x = quantise(G, x);
+        if (dead) x = G.stuck_lo + G.stuck_span * u24(draw(P.seed, gid, ep, TAG_STUCK).z);
+        a.prox_noisy[g] = x;
+    }
+}
+
+cudaError_t launch_prox(const StepArgs& a, int n_items, cudaStream_t s) {
+    if (n_items == 0) return cudaSuccess;
+    prox_kernel<<<n_items, kProxThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Elastomer markers: h = max(0, -phi) at every marker of the pad, then the
+// dilation sum of Eqs. 20-21 over the neighbourhood, with the per-offset
+// weights computed on the host.
+// ---------------------------------------------------------------------------
+constexpr int kMarkerThreads = 256;
+
+__global__ void __launch_bounds__(kMarkerThreads) marker_kernel(const MarkerArgs m) {
+    __shared__ float h_s[kMaxPadMarkers];
+    __shared__ float ha_s[kMaxPadMarkers];
+    __shared__ float rec[kLinkRec];
+    __shared__ ObjDev obj_s;
+    const int pad = blockIdx.x;  // e * P + p
+    const int e = pad / m.pads_per_env;
+    const int l = m.pad_link[pad];
+    const int M = m.rows * m.cols;
+    if (threadIdx.x < kLinkRec) rec[threadIdx.x] = m.link_rec[(size_t)(e * m.max_links + l) * kLinkRec + threadIdx.x];
+    if (threadIdx.x == 0) obj_s = m.objects[min(max(m.obj_id[e], 0), m.n_objects - 1)];
+    __syncthreads();
+    const float* fr = m.pad_frame + (size_t)pad * 9;
+    const float3 o = f3(fr[0], fr[1], fr[2]), nrm = f3(fr[3], fr[4], fr[5]), tu = f3(fr[6], fr[7], fr[8]);
+    const float3 tv = cross(nrm, tu);
+    for (int j = threadIdx.x; j < M; j += kMarkerThreads) {
+        const int r = j / m.cols, c = j - r * m.cols;
+        const float sa = (r - 0.5f * (m.rows - 1)) * m.pitch, sb = (c - 0.5f * (m.cols - 1)) * m.pitch;
+        const float3 x = o + tu * sa + tv * sb;
+        const float phi = fast_query(rec, obj_s, x.x, x.y, x.z);
+        if (!isfinite(phi)) atomicAdd(m.err, 1u);
+        const float h = phi < 0.0f ? -phi : 0.0f;
+        h_s[j] = h;
+        ha_s[j] = h > 0.0f ? powf(h, m.alpha) : 0.0f;
+    }
+    __syncthreads();
+    const int W = 2 * m.radius + 1;
+    for (int j = threadIdx.x; j < M; j += kMarkerThreads) {
+        const int r = j / m.cols, c = j - r * m.cols;
+        float un = 0.f, ut = 0.f, uv = 0.f;
+        for (int di = -m.radius; di <= m.radius; ++di) {
+            const int ri = r + di;
+            if (ri < 0 || ri >= m.rows) continue;
+            for (int dj = -m.radius; dj <= m.radius; ++dj) {
+                const int ci = c + dj;
+                if (ci < 0 || ci >= m.cols) continue;
+                const int i = ri * m.cols + ci;
+                const float h = h_s[i];
+                if (h == 0.0f) continue;
+                const int w = (di + m.radius) * W + (dj + m.radius);
+                // r_ij = x_j - x_i = -(di, dj) pitch in (tangent, bitangent)
+                const float ht = h * m.w_tan[w];
+                ut = fmaf(-di * m.pitch, ht, ut);
+                uv = fmaf(-dj * m.pitch, ht, uv);
+                un = fmaf(ha_s[i], m.w_norm[w], un);
+            }
+        }
+        float* out = m.u + ((size_t)pad * M + j) * 3;
+        out[0] = un;
+        out[1] = ut;
+        out[2] = uv;
+    }
+}
+
+cudaError_t launch_markers(const MarkerArgs& m, cudaStream_t s) {
+    const int n = m.n_envs * m.pads_per_env;
+    if (n == 0) return cudaSuccess;
+    marker_kernel<<<n, kMarkerThreads, 0, s>>>(m);
+    return cudaGetLastError();
+}
+
+}  // namespace tg

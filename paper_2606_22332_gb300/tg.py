@@ -28,8 +28,8 @@ TG_OK = 0
 STATUS = {0: "TG_OK", 1: "TG_ERR_INVALID_ARG", 2: "TG_ERR_OOM", 3: "TG_ERR_CUDA", 4: "TG_ERR_STATE",
           5: "TG_ERR_TIMEOUT", 6: "TG_ERR_NUMERIC", 7: "TG_ERR_UNSUPPORTED"}
 TG_OBJ_SPHERE, TG_OBJ_BOX, TG_OBJ_PLANE, TG_OBJ_MESH, TG_OBJ_GRID = 0, 1, 2, 3, 4
-CH_CONTACT, CH_DEPTH, CH_DIST, CH_FORCE_TORQUE, CH_LINK_WRENCH, CH_LINK_COUNT, CH_STATE_FLAGS = range(7)
-TG_SENSOR_DIST = 0x1
+CH_CONTACT, CH_DEPTH, CH_DIST, CH_FORCE_TORQUE, CH_LINK_WRENCH, CH_LINK_COUNT, CH_STATE_FLAGS, CH_PROX, CH_MARKER = range(9)
+TG_SENSOR_DIST, TG_SENSOR_PROX, TG_SENSOR_MARKERS = 0x1, 0x2, 0x4
 LINK_REC = 18
 
 
@@ -47,7 +47,15 @@ class NoiseGroup(C.Structure):
 class Params(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("k", "c", "alpha", "k_t", "k_omega", "mu", "eta_on", "eta_off", "dt",
                                           "p_dead", "chi", "xt_sigma")] + [
-        ("seed", C.c_uint64), ("depth", NoiseGroup), ("ft", NoiseGroup), ("prox", NoiseGroup)]
+        ("seed", C.c_uint64), ("depth", NoiseGroup), ("ft", NoiseGroup), ("prox", NoiseGroup),
+        ("prox_rays", C.c_int32), ("prox_range", C.c_double), ("prox_cone", C.c_double)]
+
+
+class PadDesc(C.Structure):
+    _fields_ = [("pads_per_env", C.c_int32), ("rows", C.c_int32), ("cols", C.c_int32), ("pitch", C.c_double),
+                ("pad_link", C.c_void_p), ("pad_frame", C.c_void_p),
+                ("s_d", C.c_double), ("alpha", C.c_double), ("lambda_d", C.c_double), ("c", C.c_double),
+                ("eps", C.c_double), ("radius", C.c_int32)]
 
 
 class SceneDesc(C.Structure):
@@ -55,7 +63,8 @@ class SceneDesc(C.Structure):
                 ("link_rows", C.c_void_p), ("link_cols", C.c_void_p), ("link_wrap", C.c_void_p),
                 ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
                 ("nx", C.c_void_p), ("ny", C.c_void_p), ("nz", C.c_void_p), ("R", C.c_void_p),
-                ("params", Params), ("sensors", C.c_uint32), ("taxel_gid0", C.c_int64), ("env_gid0", C.c_int32)]
+                ("params", Params), ("sensors", C.c_uint32), ("taxel_gid0", C.c_int64), ("env_gid0", C.c_int32),
+                ("pads", PadDesc)]
 
 
 class ObjectDesc(C.Structure):
@@ -143,6 +152,9 @@ def _fill_params(params: dict) -> Params:
     mu = params["mu"]
     P.mu = -1.0 if mu is None or np.isinf(mu) else float(mu)
     P.seed = int(params["seed"])
+    P.prox_rays = int(params.get("prox_rays", 0))
+    P.prox_range = float(params.get("prox_range", 0.05))
+    P.prox_cone = float(params.get("prox_cone", np.radians(30.0)))
     for g in ("depth", "ft", "prox"):
         grp = getattr(P, g)
         for k in NoiseGroup._fields_:
@@ -185,7 +197,8 @@ def object_desc(o, keep: list) -> ObjectDesc:
 class Scene:
     """A tg_scene: the taxel geometry, state and outputs of E envs."""
 
-    def __init__(self, geom: dict, params: dict, sensors: int = 0, taxel_gid0: int = 0, env_gid0: int = 0):
+    def __init__(self, geom: dict, params: dict, sensors: int = 0, taxel_gid0: int = 0, env_gid0: int = 0,
+                 pads: dict | None = None):
         keep = {}
         off = np.ascontiguousarray(geom["taxel_offsets"], np.int64)
         E = len(off) - 1
@@ -209,6 +222,17 @@ class Scene:
         d.sensors = sensors
         d.taxel_gid0 = int(taxel_gid0)
         d.env_gid0 = int(env_gid0)
+        self.pads = pads
+        if pads is not None:
+            keep["pad_link"] = np.ascontiguousarray(pads["pad_link"], np.int32)
+            keep["pad_frame"] = np.ascontiguousarray(pads["pad_frame"], np.float32)
+            pd = d.pads
+            pd.pads_per_env, pd.rows, pd.cols = int(pads["pads_per_env"]), int(pads["rows"]), int(pads["cols"])
+            pd.pitch = float(pads["pitch"])
+            pd.pad_link, pd.pad_frame = _ptr(keep["pad_link"]), _ptr(keep["pad_frame"])
+            for k in ("s_d", "alpha", "lambda_d", "c", "eps"):
+                setattr(pd, k, float(pads[k]))
+            pd.radius = int(pads["radius"])
         h = C.c_void_p()
         _check(_lib.tg_create_scene(C.byref(d), C.byref(h)), None)
         self.h = h
@@ -218,7 +242,11 @@ class Scene:
 
     @classmethod
     def from_workload(cls, wl, sensors: int = 0):
-        return cls(wl.geom(), wl.params, sensors=sensors)
+        if wl.params.get("prox_rays", 0) > 0:
+            sensors |= TG_SENSOR_PROX
+        if wl.pads is not None:
+            sensors |= TG_SENSOR_MARKERS
+        return cls(wl.geom(), wl.params, sensors=sensors, pads=wl.pads)
 
     def close(self):
         if getattr(self, "h", None):
@@ -265,7 +293,13 @@ class Scene:
         T, EL = self.n_taxels, self.n_envs * self.max_links
         return {CH_CONTACT: ((T,), np.uint8), CH_DEPTH: ((T,), np.float32), CH_DIST: ((T,), np.float32),
                 CH_FORCE_TORQUE: ((6, T), np.float32), CH_LINK_WRENCH: ((EL, LINK_REC), np.float32),
-                CH_LINK_COUNT: ((EL, 2), np.int32), CH_STATE_FLAGS: ((T,), np.uint8)}[ch]
+                CH_LINK_COUNT: ((EL, 2), np.int32), CH_STATE_FLAGS: ((T,), np.uint8),
+                CH_PROX: ((T,), np.float32),
+                CH_MARKER: ((self._n_markers(), 3), np.float32)}[ch]
+
+    def _n_markers(self):
+        p = self.pads
+        return 0 if p is None else self.n_envs * int(p["pads_per_env"]) * int(p["rows"]) * int(p["cols"])
 
     def read(self, ch: int, noisy: bool = False, out=None, stream=None):
         """Copy a channel into `out` (numpy = host, torch tensor = host or device); returns it."""

@@ -253,6 +253,7 @@ class Workload:
     params: dict
     steps: int = 1
     env_params: np.ndarray | None = None
+    pads: dict | None = None          # elastomer marker pads (see add_pads)
     meta: dict = field(default_factory=dict)
 
     @property
@@ -294,6 +295,9 @@ class Workload:
             steps=self.steps, env_params=None if self.env_params is None else self.env_params[envs].copy(),
             meta=dict(self.meta),
         )
+        if self.pads is not None:
+            sub.pads = dict(self.pads, pad_link=self.pads["pad_link"][envs].copy(),
+                            pad_frame=self.pads["pad_frame"][envs].copy())
         return sub
 
 
@@ -448,6 +452,32 @@ def _assemble(name, rng, objects, env_obj, env_lattices, params, steps, press_fr
     )
 
 
+def add_pads(wl: Workload, pads_per_env: int = 5, rows: int = 16, cols: int = 16, pitch: float = 1e-3,
+             sigma: float = 1.5e-3) -> Workload:
+    """Planar 16 x 16 marker pads (1 mm pitch) on the first `pads_per_env`
+    links of every env (the fingertips), each tangent to its capsule on the
+    side facing the object: origin (r, 0, 0), normal +x, tangent +z (the
+    capsule radius r is read back from the link's taxel positions).
+    Dilation: s_d = 1, alpha = 1.2, c = 1, lambda_d = 1 / (2 sigma^2),
+    eps = pitch, 5 x 5 neighbourhood."""
+    E, L = wl.n_envs, wl.max_links
+    frame = np.zeros((E, pads_per_env, 9), np.float32)
+    link = np.zeros((E, pads_per_env), np.int32)
+    rows_ = wl.link_rows.reshape(E, L); cols_ = wl.link_cols.reshape(E, L)
+    starts = wl.taxel_offsets[:-1, None] + np.concatenate(
+        [np.zeros((E, 1), np.int64), np.cumsum((rows_ * cols_).astype(np.int64), 1)[:, :-1]], 1)
+    for p in range(pads_per_env):
+        link[:, p] = p
+        t0 = starts[:, p]
+        r = np.sqrt(wl.x[t0].astype(np.float64) ** 2 + wl.y[t0].astype(np.float64) ** 2)
+        frame[:, p, 0] = r
+        frame[:, p, 3] = 1.0
+        frame[:, p, 8] = 1.0
+    wl.pads = dict(pads_per_env=pads_per_env, rows=rows, cols=cols, pitch=pitch, pad_link=link, pad_frame=frame,
+                   s_d=1.0, alpha=1.2, lambda_d=1.0 / (2 * sigma * sigma), c=1.0, eps=pitch, radius=2)
+    return wl
+
+
 def config0(seed: int = 20260001, n_envs: int = 64, n_meshes: int = 8) -> Workload:
     """Plain method: 16 capsule links with 200 taxels; per env a sphere
     (r = 30 mm, analytic) or a ~2,000-face mesh (hull of 64 Gaussian points,
@@ -536,5 +566,8 @@ def config2(seed: int = 20260003, n_envs: int = 20480, n_objects: int = 64, n_gr
     objects = config1_objects(rng, n_objects, n_grid, fp16=True, faces=faces)
     env_obj = rng.integers(0, n_objects, n_envs)
     lattices = uneven_lattices(rng, n_envs)
-    return _assemble("config2", rng, objects, env_obj, lattices, default_params(seed), steps=steps, max_links=20,
-                     arc=PAD_ARC, press_frac=(1.0, 1.0), press_depth=(0.5e-3, 2.5e-3))
+    params = default_params(seed)
+    params["prox_rays"] = 8
+    wl = _assemble("config2", rng, objects, env_obj, lattices, params, steps=steps, max_links=20,
+                   arc=PAD_ARC, press_frac=(1.0, 1.0), press_depth=(0.5e-3, 2.5e-3))
+    return add_pads(wl)
