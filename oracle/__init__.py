@@ -66,6 +66,7 @@ class ORParams(C.Structure):
         ("depth", ORNoiseGroup), ("ft", ORNoiseGroup), ("prox", ORNoiseGroup),
         ("chi", C.c_double), ("xt_sigma", C.c_double),
         ("prox_rays", C.c_int32), ("prox_range", C.c_double), ("prox_cone", C.c_double),
+        ("dr_on", C.c_int32), ("dr_mu", C.c_double * 2), ("dr_k", C.c_double * 2), ("dr_scale", C.c_double * 2),
     ]
 
 
@@ -140,6 +141,7 @@ def lib():
                                             C.POINTER(C.c_int)]
             L.or_ray_first_root.restype = C.c_double
             L.or_prox_ray_dirs.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_void_p]
+            L.or_dr_draw.argtypes = [C.POINTER(ORParams), C.c_uint32, C.c_uint32, C.c_void_p]
             L.or_marker_kernel_g.argtypes = [C.c_double, C.c_double]
             L.or_marker_kernel_g.restype = C.c_double
             L.or_markers.argtypes = [C.POINTER(ORScene), C.POINTER(ORPads), C.POINTER(ORInputs), C.c_void_p,
@@ -283,6 +285,14 @@ def marker_kernel_g(lambda_d, r2):
     return lib().or_marker_kernel_g(float(lambda_d), float(r2))
 
 
+def dr_draw(params: dict, env_gid: int, step: int):
+    """(mu, k, scale) drawn for one env and step by per-step domain randomisation."""
+    P = make_params(params)
+    out = np.zeros(3, np.float64)
+    lib().or_dr_draw(C.byref(P), C.c_uint32(env_gid), C.c_uint32(step), _p(out))
+    return out
+
+
 def schmitt(prev, d, eta_on, eta_off):
     return lib().or_schmitt(int(prev), float(d), float(eta_on), float(eta_off))
 
@@ -319,6 +329,12 @@ def make_params(p: dict) -> ORParams:
     P.prox_rays = int(p.get("prox_rays", 0))
     P.prox_range = float(p.get("prox_range", 0.05))
     P.prox_cone = float(p.get("prox_cone", np.radians(30.0)))
+    dr = p.get("dr")
+    P.dr_on = 1 if dr else 0
+    if dr:
+        for k in ("mu", "k", "scale"):
+            getattr(P, "dr_" + k)[0] = float(dr[k][0])
+            getattr(P, "dr_" + k)[1] = float(dr[k][1])
     for gname in ("depth", "ft", "prox"):
         g = getattr(P, gname)
         for k in _GROUP_KEYS:

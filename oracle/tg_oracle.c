@@ -89,6 +89,21 @@ static void philox_normals(uint64_t seed, uint64_t gid, uint32_t step, uint32_t 
     or_box_muller(w[2], w[3], &z[2], &z[3]);
 }
 
+/* Per-step domain randomisation of one env (config 4 of the evaluation):
+   one Philox block at counter (env id, step, DR, 0) gives u0, u1, u2 and
+   mu = lo + (hi - lo) u0, k = ... u1, scale = ... u2.  The bounds and the
+   drawn values are binary32 numbers, the precision per-env parameters have
+   when a caller passes them in: the value is formed in FP64 and rounded. */
+void or_dr_draw(const or_params* P, uint32_t env_gid, uint32_t step, double out[3]) {
+    uint32_t w[4];
+    philox_draw(P->seed, env_gid, step, TAG_DR, w);
+    const double* b[3] = {P->dr_mu, P->dr_k, P->dr_scale};
+    for (int i = 0; i < 3; ++i) {
+        double lo = (double)(float)b[i][0], hi = (double)(float)b[i][1];
+        out[i] = (double)(float)(lo + (hi - lo) * or_uniform(w[i]));
+    }
+}
+
 /* Bernoulli(p) decided on integers: the top 24 bits below round(p 2^24) */
 static int bernoulli(uint32_t x, double p) {
     double thr = nearbyint(p * 16777216.0);
@@ -782,7 +797,11 @@ static void env_step(const or_scene* S, const or_inputs* in, or_state* st, or_ou
     const int64_t n = t1 - t0;
 
     double k = P->k, mu = P->mu, scale = 1.0;
-    if (in->env_params) {
+    if (P->dr_on) {
+        double v[3];
+        or_dr_draw(P, (uint32_t)S->env_gid[e], in->step, v);
+        mu = v[0]; k = v[1]; scale = v[2];
+    } else if (in->env_params) {
         mu = in->env_params[3 * e]; k = in->env_params[3 * e + 1]; scale = in->env_params[3 * e + 2];
     }
     const or_object* obj = &S->objects[in->obj_id[e]];
@@ -1020,6 +1039,11 @@ int or_step(const or_scene* S, const or_inputs* in, or_state* st, or_outputs* ou
 static void env_markers(const or_scene* S, const or_pads* pads, const or_inputs* in, double* u, double* h_out, int32_t e) {
     const int32_t L = S->max_links, P = pads->pads_per_env, M = pads->rows * pads->cols;
     double scale = in->env_params ? in->env_params[3 * e + 2] : 1.0;
+    if (S->params.dr_on) {
+        double v[3];
+        or_dr_draw(&S->params, (uint32_t)S->env_gid[e], in->step, v);
+        scale = v[2];
+    }
     const or_object* obj = &S->objects[in->obj_id[e]];
     double pC0[3], qC0[4], vC[3], wC[3], pC[3], RC[9];
     for (int a = 0; a < 3; ++a) pC0[a] = in->obj_pose[7 * e + a];

@@ -64,6 +64,10 @@ typedef struct {
        along the probe normal, the others on a cone of half-angle prox_cone */
     int32_t prox_rays;
     double prox_range, prox_cone;
+    /* per-step domain randomisation (dr_on = 0: off): for every env and step,
+       mu, k and the object scale uniform on [lo, hi] (index 0 lo, 1 hi) */
+    int32_t dr_on;
+    double dr_mu[2], dr_k[2], dr_scale[2];
 } or_params;
 
 /* elastomer marker pads (ElastomerTaxel dilation, Eqs. 18-21) */
@@ -159,6 +163,7 @@ void or_bake_grid(const float* V, const int32_t* F, int32_t nf, const int32_t di
 
 double or_ray_first_root(const or_object* o, double scale, const double q0[3], const double d[3], double tmax,
                          int* grazing);
+void or_dr_draw(const or_params* P, uint32_t env_gid, uint32_t step, double out[3]);
 void or_prox_ray_dirs(const double n[3], int n_rays, double cone, double dirs[][3]);
 double or_marker_kernel_g(double lambda_d, double r2);
 
