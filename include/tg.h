@@ -90,6 +90,15 @@ typedef struct {
        the first surface crossing along the ray */
     int32_t prox_rays;                /* 1..16 */
     double prox_range, prox_cone;
+    /* per-step domain randomisation (dr_on = 0: off).  For every env and
+       step, mu, k and the object scale are drawn uniformly on [lo, hi]
+       (index 0 = lo, 1 = hi) from Philox at counter (global env id, step,
+       tag 32, 0): mu from word 0, k from word 1, scale from word 2, each
+       formed as lo + (hi - lo) u and rounded to binary32 (bounds are taken
+       as binary32).  Replaces tg_step_inputs.env_params, which must then be
+       NULL. */
+    int32_t dr_on;
+    double dr_mu[2], dr_k[2], dr_scale[2];
 } tg_params;
 
 /* sensor mask bits (depth, contact and force/torque are always computed) */
@@ -193,6 +202,48 @@ typedef struct {
    Errors: TG_ERR_STATE (no objects), TG_ERR_INVALID_ARG (NULL input),
    TG_ERR_CUDA (launch failure). */
 tg_status tg_step_sensors(tg_scene* scene, const tg_step_inputs* in, tg_stream stream);
+
+/* Step replay through a CUDA graph (one vectorised launch sequence per step,
+   "Batched Simulation" of the paper's system section).
+   tg_graph_capture records the launches of one step, exactly as
+   tg_step_sensors(scene, in) enqueues them, into a graph owned by the scene.
+   The graph reads in's buffers in place on every replay, so they must be
+   device pointers that stay valid and are refilled by the caller between
+   replays; host pointers give TG_ERR_INVALID_ARG.  Replay r (counted from
+   the capture or the last tg_graph_seek) runs RNG step in->step + r with
+   pose_dt = in->pose_dt + r * pose_dt_per_step: the step index lives in
+   device memory and the graph's last node advances it, so a replay needs
+   no host work.  tg_graph_launch enqueues n_steps replays on `stream`;
+   tg_graph_seek resets the replay counter to (step, pose_dt) in stream
+   order.  The captured schedule (tg_set_schedule) is fixed until release.
+   Errors: TG_ERR_STATE (no objects / nothing captured), TG_ERR_INVALID_ARG,
+   TG_ERR_CUDA. */
+tg_status tg_graph_capture(tg_scene* scene, const tg_step_inputs* in, double pose_dt_per_step, tg_stream stream);
+tg_status tg_graph_launch(tg_scene* scene, int32_t n_steps, tg_stream stream);
+tg_status tg_graph_seek(tg_scene* scene, uint32_t step, double pose_dt, double pose_dt_per_step, tg_stream stream);
+tg_status tg_graph_release(tg_scene* scene);
+
+/* Work schedule of the step kernel.  persistent = 0: one CTA per work item
+   (a run of whole links of one env); 1: a grid of the resident CTA count
+   takes items from an atomic counter.  sorted = 1: items run in the order
+   of the object their env holds (a counting sort each step), so concurrent
+   CTAs share object grids in L2.  Results do not depend on the schedule.
+   tg_autotune times every schedule on `steps` steps of the given inputs
+   (after one warm-up step each), keeps the fastest, and restores the noise
+   state it found (the output buffers then hold the last trial's step).
+   Errors: TG_ERR_STATE (a captured graph exists), TG_ERR_INVALID_ARG. */
+typedef struct {
+    int32_t persistent, sorted;
+    double ms_per_step;
+} tg_tune_candidate;
+typedef struct {
+    int32_t n, chosen;
+    tg_tune_candidate cand[8];
+} tg_tune_report;
+tg_status tg_set_schedule(tg_scene* scene, int32_t persistent, int32_t sorted);
+tg_status tg_get_schedule(const tg_scene* scene, int32_t* persistent, int32_t* sorted);
+tg_status tg_autotune(tg_scene* scene, const tg_step_inputs* in, int32_t steps, tg_tune_report* report,
+                      tg_stream stream);
 
 typedef enum {
     TG_CH_CONTACT = 0,        /* uint8 [T]: 0/1 */

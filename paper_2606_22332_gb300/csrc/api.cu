@@ -53,6 +53,16 @@ struct tg_scene {
     float* pad_frame = nullptr;
     float* marker_u = nullptr;
 
+    // schedule (tg_set_schedule / tg_autotune) and step control
+    int persistent = 0;               // step kernel: persistent CTAs on a work counter
+    int sorted = 1;                   // object-sorted item order (several objects)
+    int resident_ctas = 0;            // step kernel CTAs resident on the device at once
+    StepCtl* ctl = nullptr;
+    // captured step (tg_graph_*)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+
     std::string last_error;
     // kernel timing (tg_profile_*)
     bool profiling = false;
@@ -142,6 +152,14 @@ const char* make_params(const tg_params& p, ParamsDev* out) {
     if (p.chi != 0.0 && !(p.xt_sigma > 0.0)) return "crosstalk needs xt_sigma > 0";
     if (p.prox_rays < 0 || p.prox_rays > 16 || !finite(p.prox_range) || !finite(p.prox_cone))
         return "prox_rays must be in 0..16 with finite range and cone";
+    if (p.dr_on) {
+        const double* b[3] = {p.dr_mu, p.dr_k, p.dr_scale};
+        for (int i = 0; i < 3; ++i)
+            if (!finite(b[i][0]) || !finite(b[i][1]) || b[i][0] > b[i][1])
+                return "domain randomisation bounds must be finite with lo <= hi";
+        if (!(p.dr_scale[0] > 0.0)) return "domain randomisation scale must be positive";
+        if (p.dr_k[0] < 0.0) return "domain randomisation k must be non-negative";
+    }
     for (const tg_noise_group* g : {&p.depth, &p.ft, &p.prox})
         if (const char* m = check_group(*g)) return m;
     ParamsDev d{};
@@ -178,6 +196,12 @@ const char* make_params(const tg_params& p, ParamsDev* out) {
         d.prox_az_cos[k] = (float)std::cos(az);
         d.prox_az_sin[k] = (float)std::sin(az);
     }
+    d.dr_on = p.dr_on ? 1 : 0;
+    const double* b[3] = {p.dr_mu, p.dr_k, p.dr_scale};
+    for (int i = 0; i < 3; ++i) {
+        d.dr_lo[i] = (float)b[i][0];
+        d.dr_hi[i] = (float)b[i][1];
+    }
     *out = d;
     return nullptr;
 }
@@ -211,6 +235,10 @@ StepArgs step_args(tg_scene* s) {
     a.err = s->err;
     a.prox_clean = s->prox_clean;
     a.prox_noisy = s->prox_noisy;
+    a.ctl = s->ctl;
+    a.n_items = s->n_items;
+    a.persistent = s->persistent;
+    a.resident_ctas = s->resident_ctas;
     return a;
 }
 
@@ -415,6 +443,11 @@ tg_status tg_create_scene(const tg_scene_desc* d, tg_scene** out) {
     CKC(dalloc(&s->s_mask, E));
     CKC(dalloc(&s->s_contact, T));
     CKC(dalloc(&s->item_order, items.size()));
+    CKC(dalloc(&s->ctl, 1));
+    CKC(cudaMemset(s->ctl, 0, sizeof(StepCtl)));
+    CKC(configure_step_kernels());
+    s->resident_ctas = step_kernel_resident_ctas();
+    if (s->resident_ctas <= 0) return bail(cudaErrorInvalidConfiguration, "step kernel occupancy");
     if (d->sensors & TG_SENSOR_PROX) {
         CKC(dalloc(&s->prox_clean, T));
         CKC(dalloc(&s->prox_noisy, T));
@@ -478,6 +511,9 @@ tg_status tg_create_scene(const tg_scene_desc* d, tg_scene** out) {
 void tg_destroy_scene(tg_scene* s) {
     if (!s) return;
     cudaDeviceSynchronize();
+    if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
+    if (s->graph) cudaGraphDestroy(s->graph);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     free_objects(s);
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : s->ev_pending) cudaEventDestroy(e);
@@ -486,7 +522,7 @@ void tg_destroy_scene(tg_scene* s) {
                     s->ft_noisy, s->link_out, s->link_count, s->err, s->link_rec, s->s_link_pose, s->s_link_vel,
                     s->s_obj_pose, s->s_obj_vel, s->s_env_params, s->s_obj_id, s->s_mask, s->s_contact,
                     s->item_order, s->prox_clean, s->prox_noisy, s->pad_link, s->pad_frame,
-                    s->marker_u};
+                    s->marker_u, s->ctl};
     for (void* p : ptrs) dfree(p);
     delete s;
 }
@@ -597,13 +633,20 @@ tg_status tg_reset_envs(tg_scene* s, const uint8_t* env_mask, uint32_t episode, 
     return TG_OK;
 }
 
-tg_status tg_step_sensors(tg_scene* s, const tg_step_inputs* in, tg_stream stream) {
-    if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
+namespace {
+
+const char* check_inputs(const tg_scene* s, const tg_step_inputs* in) {
     if (!in || !in->link_pose || !in->link_vel || !in->obj_pose || !in->obj_vel || !in->obj_id)
-        return fail(s, TG_ERR_INVALID_ARG, "step inputs: link_pose, link_vel, obj_pose, obj_vel, obj_id are required");
-    if (s->n_objects < 1) return fail(s, TG_ERR_STATE, "tg_upload_objects must come before tg_step_sensors");
-    if (!std::isfinite(in->pose_dt)) return fail(s, TG_ERR_INVALID_ARG, "pose_dt must be finite");
-    cudaStream_t st = (cudaStream_t)stream;
+        return "step inputs: link_pose, link_vel, obj_pose, obj_vel, obj_id are required";
+    if (!std::isfinite(in->pose_dt)) return "pose_dt must be finite";
+    if (s->P.dr_on && in->env_params) return "env_params must be NULL when domain randomisation is on";
+    return nullptr;
+}
+
+// Every launch of one sensor step, in order, on `st`.  graph: the kernels
+// take step and pose_dt from the device step control (and no profiling
+// events are recorded), so the sequence can be captured and replayed.
+tg_status enqueue_step(tg_scene* s, const tg_step_inputs* in, cudaStream_t st, bool graph) {
     const size_t EL = (size_t)s->E * s->L;
     PoseArgs pa{};
     CK(s, stage(in->link_pose, s->s_link_pose, EL * 7, st, &pa.link_pose));
@@ -622,8 +665,18 @@ tg_status tg_step_sensors(tg_scene* s, const tg_step_inputs* in, tg_stream strea
     pa.tau_hi = (float)in->pose_dt;
     pa.tau_lo = (float)(in->pose_dt - (double)pa.tau_hi);
     pa.link_rec = s->link_rec;
+    pa.dr_on = s->P.dr_on;
+    for (int i = 0; i < 3; ++i) {
+        pa.dr_lo[i] = s->P.dr_lo[i];
+        pa.dr_hi[i] = s->P.dr_hi[i];
+    }
+    pa.seed = s->P.seed;
+    pa.env_gid0 = s->env_gid0;
+    pa.step = in->step;
+    pa.ctl = graph ? s->ctl : nullptr;
+    const bool prof = s->profiling && !graph;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-    if (s->profiling) {
+    if (prof) {
         for (int i = 0; i < 3; ++i) {
             if (s->ev_pool.empty()) {
                 CK(s, cudaEventCreate(&ev[i]));
@@ -639,14 +692,15 @@ tg_status tg_step_sensors(tg_scene* s, const tg_step_inputs* in, tg_stream strea
     StepArgs a = step_args(s);
     a.obj_id = oid;
     a.step = in->step;
+    a.step_from_ctl = graph ? 1 : 0;
     a.item_order = nullptr;
-    if (s->n_objects > 1 && s->n_objects <= 12288) {
+    if (s->sorted && s->n_objects > 1 && s->n_objects <= 12288) {
         CK(s, launch_order_items(s->items, s->n_items, oid, s->n_objects, s->item_order, st));
         a.item_order = s->item_order;
     }
-    if (s->profiling) CK(s, cudaEventRecord(ev[1], st));
+    if (prof) CK(s, cudaEventRecord(ev[1], st));
     CK(s, launch_step(a, s->n_items, st));
-    if (s->profiling) CK(s, cudaEventRecord(ev[2], st));
+    if (prof) CK(s, cudaEventRecord(ev[2], st));
     if (s->sensors & TG_SENSOR_PROX) CK(s, launch_prox(a, s->n_items, st));
     if (s->sensors & TG_SENSOR_MARKERS) {
         MarkerArgs m = s->markers;
@@ -655,6 +709,181 @@ tg_status tg_step_sensors(tg_scene* s, const tg_step_inputs* in, tg_stream strea
         m.n_objects = s->n_objects;
         CK(s, launch_markers(m, st));
     }
+    if (graph) CK(s, launch_advance_ctl(s->ctl, st));
+    return TG_OK;
+}
+
+StepCtl make_ctl(uint32_t step, double tau0, double dtau) {
+    StepCtl c{};
+    c.step = step;
+    c.replay = 0;
+    c.tau0_hi = (float)tau0;
+    c.tau0_lo = (float)(tau0 - (double)c.tau0_hi);
+    c.dtau_hi = (float)dtau;
+    c.dtau_lo = (float)(dtau - (double)c.dtau_hi);
+    return c;
+}
+
+void release_graph(tg_scene* s) {
+    if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
+    if (s->graph) cudaGraphDestroy(s->graph);
+    s->graph_exec = nullptr;
+    s->graph = nullptr;
+}
+
+}  // namespace
+
+tg_status tg_step_sensors(tg_scene* s, const tg_step_inputs* in, tg_stream stream) {
+    if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
+    if (const char* m = check_inputs(s, in)) return fail(s, TG_ERR_INVALID_ARG, m);
+    if (s->n_objects < 1) return fail(s, TG_ERR_STATE, "tg_upload_objects must come before tg_step_sensors");
+    return enqueue_step(s, in, (cudaStream_t)stream, false);
+}
+
+tg_status tg_graph_capture(tg_scene* s, const tg_step_inputs* in, double pose_dt_per_step, tg_stream stream) {
+    if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
+    if (const char* m = check_inputs(s, in)) return fail(s, TG_ERR_INVALID_ARG, m);
+    if (!std::isfinite(pose_dt_per_step)) return fail(s, TG_ERR_INVALID_ARG, "pose_dt_per_step must be finite");
+    if (s->n_objects < 1) return fail(s, TG_ERR_STATE, "tg_upload_objects must come before tg_graph_capture");
+    const void* ptrs[] = {in->link_pose, in->link_vel, in->obj_pose, in->obj_vel, in->obj_id, in->env_params};
+    for (const void* p : ptrs)
+        if (p && !is_device_ptr(p))
+            return fail(s, TG_ERR_INVALID_ARG, "a captured step reads its inputs in place: device pointers only");
+    release_graph(s);
+    if (!s->cap_stream) CK(s, cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(s, launch_set_ctl(s->ctl, make_ctl(in->step, in->pose_dt, pose_dt_per_step), st));
+    CK(s, cudaStreamSynchronize(st));
+    CK(s, cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const tg_status r = enqueue_step(s, in, s->cap_stream, true);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(s->cap_stream, &g);
+    if (r != TG_OK) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+    }
+    if (ec != cudaSuccess) return cuda_fail(s, ec, "graph capture");
+    s->graph = g;
+    const cudaError_t ei = cudaGraphInstantiate(&s->graph_exec, g, 0);
+    if (ei != cudaSuccess) {
+        release_graph(s);
+        return cuda_fail(s, ei, "graph instantiate");
+    }
+    return TG_OK;
+}
+
+tg_status tg_graph_launch(tg_scene* s, int32_t n_steps, tg_stream stream) {
+    if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
+    if (!s->graph_exec) return fail(s, TG_ERR_STATE, "no captured step: call tg_graph_capture first");
+    if (n_steps < 0) return fail(s, TG_ERR_INVALID_ARG, "n_steps must be >= 0");
+    for (int32_t i = 0; i < n_steps; ++i) CK(s, cudaGraphLaunch(s->graph_exec, (cudaStream_t)stream));
+    return TG_OK;
+}
+
+tg_status tg_graph_seek(tg_scene* s, uint32_t step, double pose_dt, double pose_dt_per_step, tg_stream stream) {
+    if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
+    if (!std::isfinite(pose_dt) || !std::isfinite(pose_dt_per_step))
+        return fail(s, TG_ERR_INVALID_ARG, "pose_dt and pose_dt_per_step must be finite");
+    CK(s, launch_set_ctl(s->ctl, make_ctl(step, pose_dt, pose_dt_per_step), (cudaStream_t)stream));
+    return TG_OK;
+}
+
+tg_status tg_graph_release(tg_scene* s) {
+    if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
+    CK(s, cudaDeviceSynchronize());
+    release_graph(s);
+    return TG_OK;
+}
+
+tg_status tg_set_schedule(tg_scene* s, int32_t persistent, int32_t sorted) {
+    if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
+    if (s->graph_exec) return fail(s, TG_ERR_STATE, "release the captured step before changing the schedule");
+    s->persistent = persistent != 0;
+    s->sorted = sorted != 0;
+    return TG_OK;
+}
+
+tg_status tg_get_schedule(const tg_scene* s, int32_t* persistent, int32_t* sorted) {
+    if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
+    if (persistent) *persistent = s->persistent;
+    if (sorted) *sorted = s->sorted;
+    return TG_OK;
+}
+
+tg_status tg_autotune(tg_scene* s, const tg_step_inputs* in, int32_t steps, tg_tune_report* report,
+                      tg_stream stream) {
+    if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
+    if (const char* m = check_inputs(s, in)) return fail(s, TG_ERR_INVALID_ARG, m);
+    if (s->n_objects < 1) return fail(s, TG_ERR_STATE, "tg_upload_objects must come before tg_autotune");
+    if (steps < 1 || steps > 1000) return fail(s, TG_ERR_INVALID_ARG, "steps must be in 1..1000");
+    if (s->graph_exec) return fail(s, TG_ERR_STATE, "release the captured step before tuning");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t T = (size_t)s->T, E = (size_t)s->E;
+    // the noise state is put back afterwards: trials are not steps of the run
+    uint8_t* keep = nullptr;
+    const size_t bytes = T + 3 * 8 * T * 4 + E * 4;
+    CK(s, cudaMalloc(&keep, bytes));
+    auto save = [&](bool back) {
+        struct { void* p; size_t n; } part[] = {{s->flags, T}, {s->hyst_prev, 8 * T * 4}, {s->hyst_xi, 8 * T * 4},
+                                                 {s->drift, 8 * T * 4}, {s->episode, E * 4}};
+        size_t off = 0;
+        cudaError_t e = cudaSuccess;
+        for (auto& q : part) {
+            if (e == cudaSuccess)
+                e = back ? cudaMemcpyAsync(q.p, keep + off, q.n, cudaMemcpyDeviceToDevice, st)
+                         : cudaMemcpyAsync(keep + off, q.p, q.n, cudaMemcpyDeviceToDevice, st);
+            off += q.n;
+        }
+        return e;
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    tg_tune_report rep{};
+    const int old_p = s->persistent, old_s = s->sorted;
+    const bool prof = s->profiling;
+    s->profiling = false;
+    cudaError_t err = save(false);
+    if (err == cudaSuccess) err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    tg_status r = TG_OK;
+    const int sort_options = s->n_objects > 1 ? 2 : 1;
+    for (int ps = 0; ps < 2 && err == cudaSuccess && r == TG_OK; ++ps)
+        for (int so = 0; so < sort_options && err == cudaSuccess && r == TG_OK; ++so) {
+            s->persistent = ps;
+            s->sorted = sort_options == 2 ? 1 - so : s->sorted;
+            r = enqueue_step(s, in, st, false);  // warm-up of this variant
+            if (r != TG_OK) break;
+            err = cudaEventRecord(e0, st);
+            for (int k = 0; k < steps && r == TG_OK && err == cudaSuccess; ++k) r = enqueue_step(s, in, st, false);
+            if (r != TG_OK || err != cudaSuccess) break;
+            err = cudaEventRecord(e1, st);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            if (err != cudaSuccess) break;
+            tg_tune_candidate& c = rep.cand[rep.n++];
+            c.persistent = s->persistent;
+            c.sorted = s->sorted;
+            c.ms_per_step = (double)ms / steps;
+        }
+    if (err == cudaSuccess && r == TG_OK) err = save(true);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    s->profiling = prof;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(keep);
+    if (r != TG_OK || err != cudaSuccess || rep.n == 0) {
+        s->persistent = old_p;
+        s->sorted = old_s;
+        if (r != TG_OK) return r;
+        return cuda_fail(s, err == cudaSuccess ? cudaErrorUnknown : err, "autotune");
+    }
+    int best = 0;
+    for (int i = 1; i < rep.n; ++i)
+        if (rep.cand[i].ms_per_step < rep.cand[best].ms_per_step) best = i;
+    rep.chosen = best;
+    s->persistent = rep.cand[best].persistent;
+    s->sorted = rep.cand[best].sorted;
+    if (report) *report = rep;
     return TG_OK;
 }
 

@@ -16,6 +16,20 @@ constexpr int kStepMinBlocks = 2;    // resident CTAs per SM the register budget
 constexpr int kLinkRec = 40;         // floats per (env, link) pose record
 constexpr int kLinkOut = 18;         // floats per (env, link) output record
 
+// Step control in device memory.  Direct steps pass step and pose_dt as
+// kernel arguments; a captured CUDA graph reads them from here instead and
+// its last node advances them, so replays need no host work:
+// replay r of a graph captured at (step0, tau0) runs step0 + r with
+// pose_dt = tau0 + r dtau.  `counter` is the persistent step kernel's work
+// counter, zeroed before every step.
+struct StepCtl {
+    uint32_t step;
+    uint32_t replay;
+    float tau0_hi, tau0_lo, dtau_hi, dtau_lo;
+    uint32_t counter;
+    uint32_t pad;
+};
+
 // A noise group with the host-derived constants the kernel uses.
 struct NoiseDev {
     float gain_lo, gain_span;    // gain = lo + span * u
@@ -37,6 +51,9 @@ struct ParamsDev {
     int prox_rays;
     float prox_range, prox_cos, prox_sin;
     float prox_az_cos[16], prox_az_sin[16];
+    // per-step domain randomisation of (mu, k, scale)
+    int dr_on;
+    float dr_lo[3], dr_hi[3];
 };
 
 // Object table entry (object frame).
@@ -92,6 +109,11 @@ struct StepArgs {
 
     const float* link_rec;            // [E*L][kLinkRec] from the pose kernel
     uint32_t step;
+    StepCtl* ctl;                     // work counter; the step too when step_from_ctl
+    int step_from_ctl;
+    int n_items;
+    int persistent;                   // step kernel: CTAs take items from ctl->counter
+    int resident_ctas;                // persistent grid size (SMs x resident CTAs per SM)
     // state
     uint8_t* flags;
     float* hyst_prev;                 // [8][T]
@@ -141,10 +163,21 @@ struct PoseArgs {
     float def_mu, def_k;
     float tau_hi, tau_lo;             // pose_dt as a float pair
     float* link_rec;
+    // per-step domain randomisation
+    int dr_on;
+    float dr_lo[3], dr_hi[3];
+    uint64_t seed;
+    int64_t env_gid0;
+    uint32_t step;
+    const StepCtl* ctl;               // non-null: step and pose_dt from here
 };
 
 cudaError_t launch_pose(const PoseArgs& a, cudaStream_t s);
 cudaError_t launch_step(const StepArgs& a, int n_items, cudaStream_t s);
+cudaError_t configure_step_kernels();
+cudaError_t launch_set_ctl(StepCtl* ctl, StepCtl value, cudaStream_t s);
+cudaError_t launch_advance_ctl(StepCtl* ctl, cudaStream_t s);
+int step_kernel_resident_ctas();
 cudaError_t launch_order_items(const Item* items, int n_items, const int32_t* obj_id, int n_objects,
                                int32_t* order, cudaStream_t s);
 cudaError_t launch_reset(const StepArgs& a, int n_items, const uint8_t* env_mask, uint32_t episode,

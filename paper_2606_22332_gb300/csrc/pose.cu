@@ -10,8 +10,11 @@
 //                        p_LC = R_L^T (p_C - p_L)
 // M and t are kept as compensated float pairs: they carry the probe position
 // to ~1e-14 relative, which the depth of near-contact taxels needs.
+// The per-env mu, k and scale come from the caller, or, with per-step domain
+// randomisation, from Philox (tag DR) for this env and step.
 #include "df.cuh"
 #include "internal.h"
+#include "rng.cuh"
 
 namespace tg {
 
@@ -92,10 +95,18 @@ __device__ dmat advance_rotation(const float* q0, const float* w, df tau) {
 
 constexpr int kPoseThreads = 128;
 
+// lo + (hi - lo) u with u = (m + 1/2) 2^-24 (m the top 24 bits of x), formed
+// as a float pair and rounded once to binary32: the FP64 value rounded.
+__device__ __forceinline__ float dr_value(float lo, float hi, uint32_t x) {
+    const df span = two_sum(hi, -lo);
+    const df u = df{(float)(x >> 8) * 5.9604644775390625e-08f, 2.98023223876953125e-08f};
+    return df_add(df_from(lo), df_mul(span, u)).hi;
+}
+
 // One thread per (env, link); the object pose of each env the block touches
 // is advanced once, by one thread, into shared memory.
 __global__ void __launch_bounds__(kPoseThreads) pose_kernel(const PoseArgs a) {
-    __shared__ float s_obj[kPoseThreads][24];  // R_C as 9 float pairs, p_C as 3 float pairs
+    __shared__ float s_obj[kPoseThreads][27];  // R_C as 9 float pairs, p_C as 3 float pairs, mu k scale
     const int L = a.max_links;
     const int n = a.n_envs * L;
     const int base = blockIdx.x * kPoseThreads;
@@ -103,7 +114,13 @@ __global__ void __launch_bounds__(kPoseThreads) pose_kernel(const PoseArgs a) {
     const int e0 = base / L;
     const int e_last = min(base + kPoseThreads, n) - 1;
     const int n_env = e_last / L - e0 + 1;
-    const df tau{a.tau_hi, a.tau_lo};
+    df tau{a.tau_hi, a.tau_lo};
+    uint32_t step = a.step;
+    if (a.ctl) {
+        const StepCtl c = *a.ctl;
+        step = c.step;
+        tau = df_add(df{c.tau0_hi, c.tau0_lo}, df_mul_f(df{c.dtau_hi, c.dtau_lo}, (float)c.replay));
+    }
     if ((int)threadIdx.x < n_env) {
         const int e = e0 + threadIdx.x;
         const float* op = a.obj_pose + (size_t)e * 7;
@@ -119,6 +136,20 @@ __global__ void __launch_bounds__(kPoseThreads) pose_kernel(const PoseArgs a) {
             o[18 + 2 * i] = p.hi;
             o[19 + 2 * i] = p.lo;
         }
+        float mu = a.def_mu, k = a.def_k, scale = 1.0f;
+        if (a.dr_on) {
+            const uint4 w = draw(a.seed, (uint64_t)(a.env_gid0 + e), step, TAG_DR);
+            mu = dr_value(a.dr_lo[0], a.dr_hi[0], w.x);
+            k = dr_value(a.dr_lo[1], a.dr_hi[1], w.y);
+            scale = dr_value(a.dr_lo[2], a.dr_hi[2], w.z);
+        } else if (a.env_params) {
+            mu = a.env_params[3 * e];
+            k = a.env_params[3 * e + 1];
+            scale = a.env_params[3 * e + 2];
+        }
+        o[24] = mu;
+        o[25] = k;
+        o[26] = scale;
     }
     __syncthreads();
     if (idx >= n) return;
@@ -127,13 +158,8 @@ __global__ void __launch_bounds__(kPoseThreads) pose_kernel(const PoseArgs a) {
     const float* lp = a.link_pose + (size_t)idx * 7;
     const float* lv = a.link_vel + (size_t)idx * 6;
     const float* ov = a.obj_vel + (size_t)e * 6;
-    float mu = a.def_mu, k = a.def_k, scale = 1.0f;
-    if (a.env_params) {
-        mu = a.env_params[3 * e];
-        k = a.env_params[3 * e + 1];
-        scale = a.env_params[3 * e + 2];
-    }
     const float* o = s_obj[e - e0];
+    const float mu = o[24], k = o[25], scale = o[26];
     dmat RC;
 #pragma unroll
     for (int i = 0; i < 9; ++i) RC.m[i] = df{o[2 * i], o[2 * i + 1]};

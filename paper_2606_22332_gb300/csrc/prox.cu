@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(kProxThreads) prox_kernel(const StepArgs a) {
     const Item it = a.items[a.item_order ? a.item_order[blockIdx.x] : blockIdx.x];
     const int e = it.env, L = a.max_links, lb = it.link_begin, nl = it.link_end - it.link_begin, n = it.n_taxels;
     const ParamsDev& P = a.P;
+    const uint32_t step = a.step_from_ctl ? a.ctl->step : a.step;
     for (int i = threadIdx.x; i < nl * kLinkRec; i += kProxThreads)
         rec_s[i / kLinkRec][i % kLinkRec] = a.link_rec[(size_t)(e * L + lb + i / kLinkRec) * kLinkRec + i % kLinkRec];
     if ((int)threadIdx.x <= nl) {
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(kProxThreads) prox_kernel(const StepArgs a) {
         if (G.gain_on) x *= G.gain_lo + G.gain_span * u24(draw(P.seed, gid, ep, TAG_EPISODE).w);
         if (G.beta != 0.0f) x = hyst_update(G, x, a.hyst_prev + 7 * T + g, a.hyst_xi + 7 * T + g);
         if (G.sigma_rw != 0.0f || G.sigma_white != 0.0f) {
-            const uint4 w = draw(P.seed, gid, a.step, TAG_SCALAR);
+            const uint4 w = draw(P.seed, gid, step, TAG_SCALAR);
             const float2 z = box_muller(w.z, w.w);
             float dr = 0.0f;
             if (G.sigma_rw != 0.0f) {

@@ -40,7 +40,9 @@ __device__ __forceinline__ uint4 draw(uint64_t seed, uint64_t gid, uint32_t word
                          (uint32_t)(seed >> 32));
 }
 
-// (top 24 bits + 1/2) * 2^-24: exact in float, strictly inside (0, 1)
+// (top 24 bits + 1/2) * 2^-24, strictly inside (0, 1): exact in float for
+// words below 2^31; above, m + 1/2 needs 25 bits and rounds (ties to even)
+// by at most 2^-25
 __device__ __forceinline__ float u24(uint32_t x) { return ((float)(x >> 8) + 0.5f) * 5.9604644775390625e-08f; }
 
 // two standard normals from two words: r = sqrt(-2 ln u1), angle 2 pi u2.

@@ -1,9 +1,11 @@
 // step.cu -- the fused per-taxel sensor step (Appendix A) and the episode
 // reset.
 //
-// One CTA per work item: a run of whole links of one env (at most kItemCap
-// taxels, kItemMaxLinks links); items are taken in an object-sorted order so
-// that concurrently running CTAs share one or two SDF grids in L2.  Per-taxel
+// One work item per CTA at a time: a run of whole links of one env (at most
+// kItemCap taxels, kItemMaxLinks links); items are taken in an object-sorted
+// order so that concurrently running CTAs share one or two SDF grids in L2.
+// Either every item gets its own CTA (grid schedule) or a resident grid takes
+// items from an atomic counter (persistent schedule); the autotuner picks.  Per-taxel
 // arrays are SoA in HBM, read and written coalesced with streaming
 // (evict-first) cache operators.
 //   phase A1 per taxel: FP32 object-frame query; taxels clear of the surface
@@ -37,13 +39,13 @@ struct SmemStep {
     uint8_t bits[kItemCap];             // BIT_* flags
     int16_t queue[kItemCap];            // near-contact taxels for phase A2
     int nq;
+    unsigned int slot;                  // persistent schedule: the item being run
 };
 
+// One work item: every phase of the step for its taxels.
 template <int NT>
-__global__ void __launch_bounds__(NT, kStepMinBlocks) step_kernel(const StepArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SmemStep& S = *reinterpret_cast<SmemStep*>(smem_raw);
-    const Item it = a.items[a.item_order ? a.item_order[blockIdx.x] : blockIdx.x];
+__device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int slot, uint32_t step) {
+    const Item it = a.items[a.item_order ? a.item_order[slot] : slot];
     const int e = it.env;
     const int L = a.max_links;
     const int lb = it.link_begin;
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(NT, kStepMinBlocks) step_kernel(const StepArgs
     for (int i = tid; i < n; i += NT) {
         const int64_t g = it.taxel_begin + i;
         const uint8_t bits = S.bits[i];
-        if (bits & BIT_ACTIVE) noise_state(a, S, i, g, ep, bits);
+        if (bits & BIT_ACTIVE) noise_state(a, S, i, g, ep, step, bits);
         else noise_state_filler(a, S, i, g);
     }
     __syncthreads();
@@ -165,8 +167,8 @@ __global__ void __launch_bounds__(NT, kStepMinBlocks) step_kernel(const StepArgs
         while (i >= S.start[l + 1]) ++l;
         const int j = i - S.start[l], cols = S.cols[l];
         const int r = j / cols;
-        noisy_ft(a, S, S.fc, i, it.taxel_begin + i, ep, S.bits[i], S.start[l], r, j - r * cols, S.rows[l], cols,
-                 S.wrap[l] != 0);
+        noisy_ft(a, S, S.fc, i, it.taxel_begin + i, ep, step, S.bits[i], S.start[l], r, j - r * cols, S.rows[l],
+                 cols, S.wrap[l] != 0);
     }
     __syncthreads();
 
@@ -174,6 +176,28 @@ __global__ void __launch_bounds__(NT, kStepMinBlocks) step_kernel(const StepArgs
     for (int t = tid; t < nl * 6; t += NT) {
         const int ll = t % nl;
         link_quantity(a, S, S.fc, (size_t)(e * L + lb + ll), S.start[ll], S.start[ll + 1], 14 + t / nl);
+    }
+}
+
+// Grid schedule: CTA b runs item slot b.  Persistent schedule: a grid sized
+// to the resident CTAs takes item slots from an atomic counter (zeroed
+// before the launch) until none are left.
+template <int NT, bool PERSISTENT>
+__global__ void __launch_bounds__(NT, kStepMinBlocks) step_kernel(const StepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemStep& S = *reinterpret_cast<SmemStep*>(smem_raw);
+    const uint32_t step = a.step_from_ctl ? a.ctl->step : a.step;
+    if (!PERSISTENT) {
+        step_item<NT>(a, S, blockIdx.x, step);
+        return;
+    }
+    for (;;) {
+        if (threadIdx.x == 0) S.slot = atomicAdd(&a.ctl->counter, 1u);
+        __syncthreads();
+        const int slot = (int)S.slot;
+        if (slot >= a.n_items) break;
+        step_item<NT>(a, S, slot, step);
+        __syncthreads();  // shared memory is reused by the next item
     }
 }
 
@@ -205,17 +229,56 @@ __global__ void unpack_contact_kernel(const uint8_t* flags, int64_t n, int noisy
     if (i < n) out[i] = (flags[i] >> (noisy ? 2 : 0)) & 1u;
 }
 
+cudaError_t configure_step_kernels() {
+    const int smem = (int)sizeof(SmemStep);
+    cudaError_t err = cudaFuncSetAttribute(step_kernel<kStepThreads, false>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(step_kernel<kStepThreads, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return err;
+}
+
+int step_kernel_resident_ctas() {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<kStepThreads, true>, kStepThreads,
+                                                      sizeof(SmemStep)) != cudaSuccess)
+        return 0;
+    return sms * per_sm;
+}
+
 cudaError_t launch_step(const StepArgs& a, int n_items, cudaStream_t s) {
     if (n_items == 0) return cudaSuccess;
     const size_t smem = sizeof(SmemStep);
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t err = cudaFuncSetAttribute(step_kernel<kStepThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem);
+    if (a.persistent) {
+        if (!a.ctl || a.n_items != n_items) return cudaErrorInvalidValue;
+        const int ctas = a.resident_ctas;
+        if (ctas <= 0) return cudaErrorInvalidConfiguration;
+        cudaError_t err = cudaMemsetAsync(&a.ctl->counter, 0, sizeof(uint32_t), s);
         if (err != cudaSuccess) return err;
-        configured = true;
+        step_kernel<kStepThreads, true><<<min(ctas, n_items), kStepThreads, smem, s>>>(a);
+    } else {
+        step_kernel<kStepThreads, false><<<n_items, kStepThreads, smem, s>>>(a);
     }
-    step_kernel<kStepThreads><<<n_items, kStepThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+__global__ void set_ctl_kernel(StepCtl* ctl, StepCtl value) { *ctl = value; }
+
+// last node of a captured step: the next replay runs the next step
+__global__ void advance_ctl_kernel(StepCtl* ctl) {
+    ctl->step += 1u;
+    ctl->replay += 1u;
+}
+
+cudaError_t launch_set_ctl(StepCtl* ctl, StepCtl value, cudaStream_t s) {
+    set_ctl_kernel<<<1, 1, 0, s>>>(ctl, value);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance_ctl(StepCtl* ctl, cudaStream_t s) {
+    advance_ctl_kernel<<<1, 1, 0, s>>>(ctl);
     return cudaGetLastError();
 }
 

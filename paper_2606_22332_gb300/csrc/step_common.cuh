@@ -144,7 +144,8 @@ __device__ __forceinline__ CleanReading refine_taxel(const StepArgs& a, const fl
 // Noise state of one active taxel after its clean reading (fc[.][i] and the
 // clean depth in ag[0][i]); the state loads do not depend on the geometry.
 template <class Smem>
-__device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, int64_t g, uint32_t ep, uint8_t bits) {
+__device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, int64_t g, uint32_t ep, uint32_t step,
+                                            uint8_t bits) {
     const ParamsDev& P = a.P;
     const int64_t T = a.n_taxels;
     const float n0 = __ldcs(a.nx + g), n1 = __ldcs(a.ny + g), n2 = __ldcs(a.nz + g);
@@ -177,7 +178,7 @@ __device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, i
         for (int c = 0; c < 6; ++c) S.hx[c][i] = gain_f * S.fc[c][i];
     }
     if (P.depth.sigma_rw != 0.0f || P.depth.sigma_white != 0.0f) {
-        uint4 w = draw(P.seed, gid, a.step, TAG_SCALAR);
+        uint4 w = draw(P.seed, gid, step, TAG_SCALAR);
         float2 z = box_muller(w.x, w.y);
         float dr = 0.0f;
         if (P.depth.sigma_rw != 0.0f) {
@@ -210,7 +211,8 @@ __device__ __forceinline__ void noise_state_filler(const StepArgs& a, Smem& S, i
 // whose first taxel is `base` in the hx arrays; writes ft_noisy and out[.][i].
 template <class Smem, class Out>
 __device__ __forceinline__ void noisy_ft(const StepArgs& a, const Smem& S, Out out, int i, int64_t g, uint32_t ep,
-                                         uint8_t bits, int base, int r, int cc, int rows, int cols, bool wrap) {
+                                         uint32_t step, uint8_t bits, int base, int r, int cc, int rows, int cols,
+                                         bool wrap) {
     const ParamsDev& P = a.P;
     const int64_t T = a.n_taxels;
     if (!(bits & BIT_ACTIVE)) {
@@ -255,13 +257,13 @@ __device__ __forceinline__ void noisy_ft(const StepArgs& a, const Smem& S, Out o
     }
     if (G.sigma_rw != 0.0f || G.sigma_white != 0.0f) {
         float nrm[12];
-        uint4 wa = draw(P.seed, gid, a.step, TAG_FT_A);
-        uint4 wb = draw(P.seed, gid, a.step, TAG_FT_B);
+        uint4 wa = draw(P.seed, gid, step, TAG_FT_A);
+        uint4 wb = draw(P.seed, gid, step, TAG_FT_B);
         float2 p0 = box_muller(wa.x, wa.y), p1 = box_muller(wa.z, wa.w);
         float2 p2 = box_muller(wb.x, wb.y);
         nrm[0] = p0.x; nrm[1] = p0.y; nrm[2] = p1.x; nrm[3] = p1.y; nrm[4] = p2.x; nrm[5] = p2.y;
         if (G.sigma_white != 0.0f) {
-            uint4 wc = draw(P.seed, gid, a.step, TAG_FT_C);
+            uint4 wc = draw(P.seed, gid, step, TAG_FT_C);
             float2 p3 = box_muller(wb.z, wb.w), p4 = box_muller(wc.x, wc.y), p5 = box_muller(wc.z, wc.w);
             nrm[6] = p3.x; nrm[7] = p3.y; nrm[8] = p4.x; nrm[9] = p4.y; nrm[10] = p5.x; nrm[11] = p5.y;
         } else {

@@ -48,7 +48,8 @@ class Params(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("k", "c", "alpha", "k_t", "k_omega", "mu", "eta_on", "eta_off", "dt",
                                           "p_dead", "chi", "xt_sigma")] + [
         ("seed", C.c_uint64), ("depth", NoiseGroup), ("ft", NoiseGroup), ("prox", NoiseGroup),
-        ("prox_rays", C.c_int32), ("prox_range", C.c_double), ("prox_cone", C.c_double)]
+        ("prox_rays", C.c_int32), ("prox_range", C.c_double), ("prox_cone", C.c_double),
+        ("dr_on", C.c_int32), ("dr_mu", C.c_double * 2), ("dr_k", C.c_double * 2), ("dr_scale", C.c_double * 2)]
 
 
 class PadDesc(C.Structure):
@@ -80,6 +81,14 @@ class StepInputs(C.Structure):
                 ("pose_dt", C.c_double), ("step", C.c_uint32)]
 
 
+class TuneCandidate(C.Structure):
+    _fields_ = [("persistent", C.c_int32), ("sorted", C.c_int32), ("ms_per_step", C.c_double)]
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("n", C.c_int32), ("chosen", C.c_int32), ("cand", TuneCandidate * 8)]
+
+
 _vp, _i32, _sz = C.c_void_p, C.c_int32, C.c_size_t
 _lib.tg_create_scene.argtypes = [C.POINTER(SceneDesc), C.POINTER(_vp)]
 _lib.tg_destroy_scene.argtypes = [_vp]
@@ -102,15 +111,24 @@ _lib.tg_profile_read.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_doubl
 _lib.tg_bake_grid.argtypes = [_vp, _i32, _vp, _i32, _vp, _vp, _vp, _i32, _vp, _vp]
 _lib.tg_mesh_sdf.argtypes = [_vp, _i32, _vp, _i32, _vp, C.c_int64, _vp, _vp, _vp]
 _lib.tg_mesh_sdf_noalloc.argtypes = [_vp, _i32, _vp, _i32, _vp, C.c_int64, _vp, _vp, _vp]
+_lib.tg_graph_capture.argtypes = [_vp, C.POINTER(StepInputs), C.c_double, _vp]
+_lib.tg_graph_launch.argtypes = [_vp, _i32, _vp]
+_lib.tg_graph_seek.argtypes = [_vp, C.c_uint32, C.c_double, C.c_double, _vp]
+_lib.tg_graph_release.argtypes = [_vp]
+_lib.tg_set_schedule.argtypes = [_vp, _i32, _i32]
+_lib.tg_get_schedule.argtypes = [_vp, C.POINTER(_i32), C.POINTER(_i32)]
+_lib.tg_autotune.argtypes = [_vp, C.POINTER(StepInputs), _i32, C.POINTER(TuneReport), _vp]
 for _f in ("tg_create_scene", "tg_upload_objects", "tg_reset_envs", "tg_step_sensors", "tg_read_taxels",
            "tg_get_buffer", "tg_sync", "tg_save_state", "tg_load_state", "tg_bake_grid", "tg_mesh_sdf",
-           "tg_profile_enable", "tg_profile_read", "tg_mesh_sdf_noalloc"):
+           "tg_profile_enable", "tg_profile_read", "tg_mesh_sdf_noalloc", "tg_graph_capture", "tg_graph_launch",
+           "tg_graph_seek", "tg_graph_release", "tg_set_schedule", "tg_get_schedule", "tg_autotune"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ["tg_create_scene", "tg_destroy_scene", "tg_max_link_taxels", "tg_upload_objects", "tg_reset_envs",
             "tg_step_sensors", "tg_read_taxels", "tg_channel_bytes", "tg_get_buffer", "tg_sync", "tg_last_error",
             "tg_save_state", "tg_load_state", "tg_bake_grid", "tg_mesh_sdf", "tg_profile_enable", "tg_profile_read",
-            "tg_mesh_sdf_noalloc"]
+            "tg_mesh_sdf_noalloc", "tg_graph_capture", "tg_graph_launch", "tg_graph_seek", "tg_graph_release",
+            "tg_set_schedule", "tg_get_schedule", "tg_autotune"]
 NOALLOC_MAX_FACES = 65536
 
 
@@ -155,6 +173,12 @@ def _fill_params(params: dict) -> Params:
     P.prox_rays = int(params.get("prox_rays", 0))
     P.prox_range = float(params.get("prox_range", 0.05))
     P.prox_cone = float(params.get("prox_cone", np.radians(30.0)))
+    dr = params.get("dr")
+    P.dr_on = 1 if dr else 0
+    if dr:
+        for k in ("mu", "k", "scale"):
+            getattr(P, "dr_" + k)[0] = float(dr[k][0])
+            getattr(P, "dr_" + k)[1] = float(dr[k][1])
     for g in ("depth", "ft", "prox"):
         grp = getattr(P, g)
         for k in NoiseGroup._fields_:
@@ -267,9 +291,7 @@ class Scene:
     def reset(self, episode: int, env_mask=None, stream=None):
         _check(_lib.tg_reset_envs(self.h, _ptr(env_mask), int(episode), _stream(stream)), self.h)
 
-    def step(self, inputs: dict, stream=None):
-        """inputs: link_pose, link_vel, obj_pose, obj_vel, obj_id, optional env_params (numpy = host,
-        torch = host or device), pose_dt (s), step (RNG counter)."""
+    def _inputs(self, inputs: dict):
         I = StepInputs()
         keep = {}
         for k, dt in (("link_pose", np.float32), ("link_vel", np.float32), ("obj_pose", np.float32),
@@ -283,8 +305,49 @@ class Scene:
             setattr(I, k, _ptr(a))
         I.pose_dt = float(inputs.get("pose_dt", 0.0))
         I.step = int(inputs.get("step", 0))
+        return I, keep
+
+    def step(self, inputs: dict, stream=None):
+        """inputs: link_pose, link_vel, obj_pose, obj_vel, obj_id, optional env_params (numpy = host,
+        torch = host or device), pose_dt (s), step (RNG counter)."""
+        I, keep = self._inputs(inputs)
         self._keep_inputs = keep  # host sources must outlive the async copies
         _check(_lib.tg_step_sensors(self.h, C.byref(I), _stream(stream)), self.h)
+
+    def graph_capture(self, inputs: dict, pose_dt_per_step: float, stream=None):
+        """Capture one step into a CUDA graph; inputs must be device tensors that stay in place."""
+        I, keep = self._inputs(inputs)
+        self._graph_inputs = keep
+        _check(_lib.tg_graph_capture(self.h, C.byref(I), float(pose_dt_per_step), _stream(stream)), self.h)
+
+    def graph_launch(self, n_steps: int = 1, stream=None):
+        _check(_lib.tg_graph_launch(self.h, int(n_steps), _stream(stream)), self.h)
+
+    def graph_seek(self, step: int, pose_dt: float, pose_dt_per_step: float, stream=None):
+        _check(_lib.tg_graph_seek(self.h, int(step), float(pose_dt), float(pose_dt_per_step), _stream(stream)),
+               self.h)
+
+    def graph_release(self):
+        _check(_lib.tg_graph_release(self.h), self.h)
+        self._graph_inputs = None
+
+    def set_schedule(self, persistent: bool, sorted: bool = True):
+        _check(_lib.tg_set_schedule(self.h, int(bool(persistent)), int(bool(sorted))), self.h)
+
+    def schedule(self):
+        p, s = _i32(), _i32()
+        _check(_lib.tg_get_schedule(self.h, C.byref(p), C.byref(s)), self.h)
+        return {"persistent": int(p.value), "sorted": int(s.value)}
+
+    def autotune(self, inputs: dict, steps: int = 3, stream=None):
+        """Time every step schedule on these inputs, keep the fastest; returns the report as a dict."""
+        I, keep = self._inputs(inputs)
+        self._keep_inputs = keep
+        R = TuneReport()
+        _check(_lib.tg_autotune(self.h, C.byref(I), int(steps), C.byref(R), _stream(stream)), self.h)
+        cands = [{"persistent": R.cand[i].persistent, "sorted": R.cand[i].sorted,
+                  "ms_per_step": R.cand[i].ms_per_step} for i in range(R.n)]
+        return {"candidates": cands, "chosen": cands[R.chosen]}
 
     def channel_bytes(self, ch: int) -> int:
         return int(_lib.tg_channel_bytes(self.h, ch))

@@ -59,6 +59,7 @@ int main(void) {
          sizeof(tg_step_inputs), sizeof(tg_noise_group));
   printf("%zu %zu %zu\n", offsetof(tg_scene_desc, params), offsetof(tg_scene_desc, sensors),
          offsetof(tg_object_desc, values));
+  printf("%zu %zu %zu\n", sizeof(tg_tune_report), offsetof(tg_tune_report, cand), offsetof(tg_params, dr_scale));
   return 0; }
 '''
     with tempfile.TemporaryDirectory() as d:
@@ -70,7 +71,8 @@ int main(void) {
     sizes = [int(v) for v in out]
     assert sizes[:5] == [ctypes.sizeof(tg.Params), ctypes.sizeof(tg.SceneDesc), ctypes.sizeof(tg.ObjectDesc),
                          ctypes.sizeof(tg.StepInputs), ctypes.sizeof(tg.NoiseGroup)]
-    assert sizes[5:] == [tg.SceneDesc.params.offset, tg.SceneDesc.sensors.offset, tg.ObjectDesc.values.offset]
+    assert sizes[5:8] == [tg.SceneDesc.params.offset, tg.SceneDesc.sensors.offset, tg.ObjectDesc.values.offset]
+    assert sizes[8:] == [ctypes.sizeof(tg.TuneReport), tg.TuneReport.cand.offset, tg.Params.dr_scale.offset]
 
 
 def test_max_link_taxels(libpath):
