@@ -5,9 +5,11 @@ Workload (default ``metric_run``): 20,480 envs x 20 capsule links x 50
 taxels (1,000 per env, 20.48M active taxel queries per step), 64 procedural
 objects (superquadrics and convex hulls, 3k-6k faces) as 96^3 FP16 SDF grids
 baked on the GPU from the exact meshes, the full noise model (dead taxels,
-hysteresis, 3x3 crosstalk, drift).  One step = the pose prologue kernel + the
-fused sensor kernel over every env; a taxel query is one active
-(env, taxel) pair of one step.
+hysteresis, 3x3 crosstalk, drift).  One step = one replay of the step's CUDA
+graph: the pose prologue, the object-sorted work order, the fused sensor
+kernel over every env (schedule picked by the autotuner) and the step-counter
+advance; a taxel query is one active (env, taxel) pair of one step.  A second
+measurement ("full_sensor_set") adds proximity rays and marker pads.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl tg|reference]
 
@@ -55,8 +57,10 @@ def parse():
     ap.add_argument("--envs", type=int, default=20480)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--oracle-envs", type=int, default=400, help="env sample of the CPU oracle legs")
-    ap.add_argument("--oracle-steps", type=int, default=10)
+    ap.add_argument("--no-full-sensors", action="store_true", help="skip the proximity + markers line")
+    ap.add_argument("--oracle-envs", type=int, default=800, help="env sample of the CPU oracle legs")
+    ap.add_argument("--oracle-objects", type=int, default=2, help="objects whose envs form the oracle sample")
+    ap.add_argument("--oracle-steps", type=int, default=300, help="steps of the cpu_baseline leg")
     return ap.parse_args()
 
 
@@ -93,24 +97,30 @@ def workload_config(args, wl):
 # ---------------------------------------------------------------------------
 class OracleSample:
     """Bounded sample of the workload for the CPU oracle: the envs that use the
-    object with the fewest faces (at most `oracle_envs` of them), whose 96^3
-    grid the oracle bakes itself from the exact mesh (untimed)."""
+    `oracle_objects` objects with the fewest faces (at most `oracle_envs` envs),
+    whose 96^3 grids the oracle bakes itself from the exact meshes (untimed)."""
 
     def __init__(self, args, wl):
         sys.path.insert(0, os.path.join(ROOT, "tests"))
         from _scenes import bake_objects_oracle, oracle_scene
 
         counts = np.bincount(wl.obj_id, minlength=len(wl.objects))
-        cand = [k for k in range(len(wl.objects)) if counts[k] > 0]
-        k = min(cand, key=lambda i: len(wl.objects[i].faces))
-        envs = np.flatnonzero(wl.obj_id == k)[: args.oracle_envs]
+        cand = sorted((k for k in range(len(wl.objects)) if counts[k] > 0), key=lambda i: len(wl.objects[i].faces))
+        ks = cand[: args.oracle_objects]
+        envs = np.flatnonzero(np.isin(wl.obj_id, ks))[: args.oracle_envs]
         sub = wl.subset(envs)
         t0 = time.time()
-        baked = bake_objects_oracle([wl.objects[k]])[0]
+        baked = bake_objects_oracle([wl.objects[k] for k in ks])
         self.bake_s = time.time() - t0
-        sub.objects = [baked] * len(wl.objects)  # the subset references object k only
-        self.sub, self.k, self.n_envs = sub, k, len(envs)
-        self.faces = len(wl.objects[k].faces)
+        objs = list(wl.objects)  # the subset references objects ks only
+        for k, b in zip(ks, baked):
+            objs[k] = b
+        for k in range(len(objs)):
+            if k not in ks:
+                objs[k] = baked[0]
+        sub.objects = objs
+        self.sub, self.ks, self.n_envs = sub, ks, len(envs)
+        self.faces = [len(wl.objects[k].faces) for k in ks]
         self.sc = oracle_scene(sub)
         self.st = self.sc.new_state()
         self.sc.reset(self.st, 0)
@@ -126,7 +136,7 @@ class OracleSample:
     def describe(self, steps, secs):
         q = self.sub.n_active * steps
         return (f"{self.n_envs} envs x {self.sub.n_active // max(self.n_envs, 1)} taxels x {steps} steps of the same "
-                f"workload (the envs of object {self.k}, {self.faces} faces; its 96^3 grid baked exactly by the "
+                f"workload (the envs of objects {self.ks}, {self.faces} faces; their 96^3 grids baked exactly by the "
                 f"oracle in {self.bake_s:.1f} s, untimed); {q} queries in {secs:.2f} s")
 
 
@@ -263,7 +273,6 @@ def run_tg(args):
     bake_s = time.time() - t_setup
     scene = tg.Scene(wl.geom(), wl.params, taxel_gid0=rank * T, env_gid0=rank * E)
     scene.upload_objects(objs)
-    del objs
     d_in = {k: torch.as_tensor(getattr(wl, k)).to(dev) for k in ("link_pose", "link_vel", "obj_pose", "obj_vel", "obj_id")}
     stream = torch.cuda.current_stream()
     dt = wl.params["dt"]
@@ -271,9 +280,16 @@ def run_tg(args):
     def step_inputs(t, src):
         return dict(src, pose_dt=t * dt, step=t)
 
+    # schedule picked by the autotuner on the live scene (state restored after)
+    scene.step(step_inputs(0, d_in))
+    tune = scene.autotune(step_inputs(0, d_in), steps=3)
+    sched = scene.schedule()
+    launches_per_step = 3 + (1 if sched["sorted"] and len(wl.objects) > 1 else 0)  # pose, [order], step, advance
+
+    # the step as a CUDA graph: replay r runs step r with pose_dt = r dt
     scene.profile(True)
-    for t in range(args.warmup):
-        scene.step(step_inputs(t, d_in))
+    scene.graph_capture(step_inputs(0, d_in), pose_dt_per_step=dt)
+    scene.graph_launch(args.warmup)
     torch.cuda.synchronize()
     scene.sync()
     scene.profile_read()
@@ -289,8 +305,7 @@ def run_tg(args):
         os.path.join(ROOT, "gpurun_out")) else f"/tmp/tg_clocks_{os.getpid()}.csv")
     with clk:
         ev0.record(stream)
-        for t in range(args.warmup, args.warmup + args.steps):
-            scene.step(step_inputs(t, d_in))
+        scene.graph_launch(args.steps)
         ev1.record(stream)
         torch.cuda.synchronize()
     if pg:
@@ -298,6 +313,8 @@ def run_tg(args):
     ms = ev0.elapsed_time(ev1)
     pose_ms, step_ms, nsteps = scene.profile_read()
     scene.sync()
+    scene.graph_release()
+    scene.profile(False)
     t_max = ms
     if pg:
         tt = torch.tensor([ms], device=dev)
@@ -340,6 +357,41 @@ def run_tg(args):
                        "per-link wrench sums and contact counts (agg_force / agg_bool observations) read back to "
                        "pinned host memory every step; same step indices as the device-timed region"}
 
+    # second line: the same workload with proximity rays and marker pads on
+    full = None
+    if not args.no_full_sensors:
+        wlf = W.add_pads(wl)
+        pf = dict(wl.params, prox_rays=8)
+        sc2 = tg.Scene(wlf.geom(), pf, sensors=tg.TG_SENSOR_PROX | tg.TG_SENSOR_MARKERS, taxel_gid0=rank * T,
+                       env_gid0=rank * E, pads=wlf.pads)
+        sc2.upload_objects(objs)
+        sc2.set_schedule(**sched)
+        sc2.graph_capture(step_inputs(0, d_in), pose_dt_per_step=dt)
+        sc2.graph_launch(args.warmup)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        sc2.graph_launch(args.steps)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fms = f0.elapsed_time(f1)
+        if pg:
+            tt = torch.tensor([fms], device=dev)
+            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+            fms = float(tt.item())
+        prox_share = float((sc2.buffer(tg.CH_PROX) > 0).sum().item()) / max(wl.n_active, 1)
+        sc2.graph_release()
+        sc2.close()
+        full = {"sensors": "headline step + proximity (8 rays, 50 mm range, sphere tracing) + marker dilation "
+                           "(5 pads x 16x16 markers per env, 5x5 Gaussian kernel, sigma 1.5 mm)",
+                "value": n_q * args.steps / (fms / 1e3), "unit": UNIT, "ms_per_step": fms / args.steps,
+                "prox_markers_ms_per_step": (fms - t_max) / args.steps,
+                "taxels_with_proximity_reading": round(prox_share, 4),
+                "gpu_launches": (launches_per_step + 2) * args.steps}
+    del objs
+
     peak, peak_kind = peaks()
     bpq = BYTES_PER_QUERY_BASE + BYTES_NORMAL * pen_share
     step_avg_ms = step_ms / max(nsteps, 1)
@@ -363,8 +415,10 @@ def run_tg(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic", "config": workload_config(args, wl), "clocks": clocks,
-            "e2e": e2e, "gpu_launches": 3 * args.steps, "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "roofline": roofline, "cpu_baseline": cpu,
             "contact_share": round(contact_share, 4), "penetrating_share": round(pen_share, 4),
+            "schedule": {"chosen": sched, "autotune": tune["candidates"], "replay": "CUDA graph per step"},
+            "full_sensor_set": full,
             "setup_s": {"bake": round(bake_s, 2), "total": round(time.time() - t_setup, 1)},
         }
         print(json.dumps(out))

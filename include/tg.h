@@ -284,7 +284,8 @@ tg_status tg_load_state(tg_scene* scene, const void* buf, size_t size);
 /* Kernel timing for measurement.  While enabled, every tg_step_sensors
    records CUDA events on its stream around its two kernels (the pose
    prologue: pose advance and the object-sorted work order; and the fused
-   step).  tg_profile_read waits for the recorded events and returns the
+   step), and so does every graph replay of a step that was captured while
+   timing was enabled (each replay records into events of its own).  tg_profile_read waits for the recorded events and returns the
    summed device time in milliseconds of the prologue kernels and of the
    step kernel, and the number of steps since the previous read, then clears
    them. */

@@ -62,6 +62,8 @@ struct tg_scene {
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
+    cudaGraphNode_t graph_ev_node[3] = {nullptr, nullptr, nullptr};  // timing events of the replay
+    cudaEvent_t graph_ev[3] = {nullptr, nullptr, nullptr};
 
     std::string last_error;
     // kernel timing (tg_profile_*)
@@ -514,6 +516,8 @@ void tg_destroy_scene(tg_scene* s) {
     if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
     if (s->graph) cudaGraphDestroy(s->graph);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    for (cudaEvent_t e : s->graph_ev)
+        if (e) cudaEventDestroy(e);
     free_objects(s);
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : s->ev_pending) cudaEventDestroy(e);
@@ -674,7 +678,12 @@ tg_status enqueue_step(tg_scene* s, const tg_step_inputs* in, cudaStream_t st, b
     pa.env_gid0 = s->env_gid0;
     pa.step = in->step;
     pa.ctl = graph ? s->ctl : nullptr;
-    const bool prof = s->profiling && !graph;
+    // (in a capture the three events become event-record nodes that every
+    // replay re-targets to fresh events, see tg_graph_launch)
+    const bool prof = s->profiling;
+    auto record = [&](cudaEvent_t e) {
+        return graph ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal) : cudaEventRecord(e, st);
+    };
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     if (prof) {
         for (int i = 0; i < 3; ++i) {
@@ -686,7 +695,7 @@ tg_status enqueue_step(tg_scene* s, const tg_step_inputs* in, cudaStream_t st, b
             }
             s->ev_pending.push_back(ev[i]);
         }
-        CK(s, cudaEventRecord(ev[0], st));
+        CK(s, record(ev[0]));
     }
     CK(s, launch_pose(pa, st));
     StepArgs a = step_args(s);
@@ -698,9 +707,9 @@ tg_status enqueue_step(tg_scene* s, const tg_step_inputs* in, cudaStream_t st, b
         CK(s, launch_order_items(s->items, s->n_items, oid, s->n_objects, s->item_order, st));
         a.item_order = s->item_order;
     }
-    if (prof) CK(s, cudaEventRecord(ev[1], st));
+    if (prof) CK(s, record(ev[1]));
     CK(s, launch_step(a, s->n_items, st));
-    if (prof) CK(s, cudaEventRecord(ev[2], st));
+    if (prof) CK(s, record(ev[2]));
     if (s->sensors & TG_SENSOR_PROX) CK(s, launch_prox(a, s->n_items, st));
     if (s->sensors & TG_SENSOR_MARKERS) {
         MarkerArgs m = s->markers;
@@ -729,6 +738,33 @@ void release_graph(tg_scene* s) {
     if (s->graph) cudaGraphDestroy(s->graph);
     s->graph_exec = nullptr;
     s->graph = nullptr;
+    for (int k = 0; k < 3; ++k) {
+        if (s->graph_ev[k]) s->ev_pool.push_back(s->graph_ev[k]);
+        s->graph_ev[k] = nullptr;
+        s->graph_ev_node[k] = nullptr;
+    }
+}
+
+// the event-record nodes of a captured step, in the order of s->graph_ev
+cudaError_t find_event_nodes(tg_scene* s) {
+    size_t n = 0;
+    cudaError_t e = cudaGraphGetNodes(s->graph, nullptr, &n);
+    if (e != cudaSuccess) return e;
+    std::vector<cudaGraphNode_t> nodes(n);
+    e = cudaGraphGetNodes(s->graph, nodes.data(), &n);
+    if (e != cudaSuccess) return e;
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        if ((e = cudaGraphNodeGetType(nd, &t)) != cudaSuccess) return e;
+        if (t != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev = nullptr;
+        if ((e = cudaGraphEventRecordNodeGetEvent(nd, &ev)) != cudaSuccess) return e;
+        for (int k = 0; k < 3; ++k)
+            if (ev == s->graph_ev[k]) s->graph_ev_node[k] = nd;
+    }
+    for (int k = 0; k < 3; ++k)
+        if (!s->graph_ev_node[k]) return cudaErrorInvalidValue;
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -755,15 +791,32 @@ tg_status tg_graph_capture(tg_scene* s, const tg_step_inputs* in, double pose_dt
     CK(s, launch_set_ctl(s->ctl, make_ctl(in->step, in->pose_dt, pose_dt_per_step), st));
     CK(s, cudaStreamSynchronize(st));
     CK(s, cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const size_t pending = s->ev_pending.size();
     const tg_status r = enqueue_step(s, in, s->cap_stream, true);
     cudaGraph_t g = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(s->cap_stream, &g);
+    if (s->ev_pending.size() == pending + 3) {
+        // the capture's timing events belong to the graph, not to a step
+        for (int k = 0; k < 3; ++k) s->graph_ev[k] = s->ev_pending[pending + k];
+        s->ev_pending.resize(pending);
+    }
     if (r != TG_OK) {
         if (g) cudaGraphDestroy(g);
+        release_graph(s);
         return r;
     }
-    if (ec != cudaSuccess) return cuda_fail(s, ec, "graph capture");
+    if (ec != cudaSuccess) {
+        release_graph(s);
+        return cuda_fail(s, ec, "graph capture");
+    }
     s->graph = g;
+    if (s->graph_ev[0]) {
+        const cudaError_t en = find_event_nodes(s);
+        if (en != cudaSuccess) {
+            release_graph(s);
+            return cuda_fail(s, en, "graph timing nodes");
+        }
+    }
     const cudaError_t ei = cudaGraphInstantiate(&s->graph_exec, g, 0);
     if (ei != cudaSuccess) {
         release_graph(s);
@@ -776,7 +829,23 @@ tg_status tg_graph_launch(tg_scene* s, int32_t n_steps, tg_stream stream) {
     if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
     if (!s->graph_exec) return fail(s, TG_ERR_STATE, "no captured step: call tg_graph_capture first");
     if (n_steps < 0) return fail(s, TG_ERR_INVALID_ARG, "n_steps must be >= 0");
-    for (int32_t i = 0; i < n_steps; ++i) CK(s, cudaGraphLaunch(s->graph_exec, (cudaStream_t)stream));
+    for (int32_t i = 0; i < n_steps; ++i) {
+        if (s->profiling && s->graph_ev_node[0]) {
+            // this replay records into its own events (earlier replays keep theirs)
+            for (int k = 0; k < 3; ++k) {
+                cudaEvent_t ev = nullptr;
+                if (s->ev_pool.empty()) {
+                    CK(s, cudaEventCreate(&ev));
+                } else {
+                    ev = s->ev_pool.back();
+                    s->ev_pool.pop_back();
+                }
+                s->ev_pending.push_back(ev);
+                CK(s, cudaGraphExecEventRecordNodeSetEvent(s->graph_exec, s->graph_ev_node[k], ev));
+            }
+        }
+        CK(s, cudaGraphLaunch(s->graph_exec, (cudaStream_t)stream));
+    }
     return TG_OK;
 }
 

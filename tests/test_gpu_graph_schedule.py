@@ -159,3 +159,19 @@ def test_autotune_restores_state_and_keeps_parity(tg):
         o = osc.step(ost, wl.inputs(s))
         compare_step(g, o, ost, wl.params, wl, where=f"after autotune step {s}")
     sc.close()
+
+
+def test_graph_replays_are_timed_one_by_one(tg):
+    wl = _grid_workload(8, 1)
+    sc = tg.Scene.from_workload(wl)
+    sc.upload_objects(wl.objects)
+    sc.profile(True)
+    sc.graph_capture(_device_inputs(wl, 0), pose_dt_per_step=wl.params["dt"])
+    assert sc.profile_read()[2] == 0  # capturing is not a step
+    sc.graph_launch(5)
+    pose_ms, step_ms, n = sc.profile_read()
+    assert n == 5 and pose_ms > 0 and step_ms > 0
+    sc.graph_launch(2)
+    assert sc.profile_read()[2] == 2
+    sc.graph_release()
+    sc.close()
