@@ -19,22 +19,25 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tg_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "tg_oracle_nsdf.c")]
 _LIB_PATH = os.path.join(_HERE, "_tg_oracle.so")
 _lib = None
 _lock = threading.Lock()
 
-OR_SPHERE, OR_BOX, OR_PLANE, OR_MESH, OR_GRID = 0, 1, 2, 3, 4
+OR_SPHERE, OR_BOX, OR_PLANE, OR_MESH, OR_GRID, OR_NEURAL = 0, 1, 2, 3, 4, 5
+NSDF_LEVELS, NSDF_FEATURES, NSDF_TABLE, NSDF_HIDDEN = 16, 2, 1 << 16, 64
+NSDF_IN = NSDF_LEVELS * NSDF_FEATURES
 NCH = 8
 LINK_REC = 18
 
 
 def build(force: bool = False) -> str:
-    """Compile tg_oracle.c into _tg_oracle.so (OpenMP when the compiler has it)."""
+    """Compile the oracle's C sources into _tg_oracle.so (OpenMP when the compiler has it)."""
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= max(
-        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "tg_oracle.h"))
+        [os.path.getmtime(f) for f in _SRCS] + [os.path.getmtime(os.path.join(_HERE, "tg_oracle.h"))]
     ):
         return _LIB_PATH
-    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC", _SRC, "-o", _LIB_PATH + ".tmp"]
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC"] + _SRCS + ["-o", _LIB_PATH + ".tmp"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:] + ["-lm"], check=True, capture_output=True)
     except subprocess.CalledProcessError:
@@ -49,8 +52,13 @@ class ORObject(C.Structure):
         ("n_verts", C.c_int32), ("n_faces", C.c_int32),
         ("verts", C.c_void_p), ("faces", C.c_void_p),
         ("dims", C.c_int32 * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
-        ("fp16", C.c_int32), ("values", C.c_void_p),
+        ("fp16", C.c_int32), ("values", C.c_void_p), ("nsdf", C.c_void_p),
     ]
+
+
+class ORNsdf(C.Structure):
+    _fields_ = [("lo", C.c_double * 3), ("hi", C.c_double * 3), ("table", C.c_void_p), ("w1", C.c_void_p),
+                ("w2", C.c_void_p), ("w3", C.c_void_p)]
 
 
 class ORNoiseGroup(C.Structure):
@@ -141,6 +149,19 @@ def lib():
                                             C.POINTER(C.c_int)]
             L.or_ray_first_root.restype = C.c_double
             L.or_prox_ray_dirs.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_void_p]
+            L.or_bf16_to_double.argtypes = [C.c_uint16]; L.or_bf16_to_double.restype = C.c_double
+            L.or_double_to_bf16.argtypes = [C.c_double]; L.or_double_to_bf16.restype = C.c_uint16
+            L.or_nsdf_resolution.argtypes = [C.c_int32]; L.or_nsdf_resolution.restype = C.c_int32
+            L.or_nsdf_index.argtypes = [C.c_int32, C.c_int64, C.c_int64, C.c_int64]
+            L.or_nsdf_index.restype = C.c_uint32
+            L.or_nsdf_eval_batch.argtypes = [C.POINTER(ORNsdf), C.c_int64, C.c_void_p, C.c_int32, C.c_void_p,
+                                             C.c_void_p]
+            L.or_nsdf_flip_bound_batch.argtypes = [C.POINTER(ORNsdf), C.c_int64, C.c_void_p, C.c_void_p]
+            L.or_nsdf_loss_grad.argtypes = [C.POINTER(ORNsdf), C.c_int64, C.c_void_p, C.c_void_p, C.c_int32,
+                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+            L.or_nsdf_loss_grad.restype = C.c_double
+            L.or_adam_step.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                       C.c_double, C.c_double, C.c_double, C.c_int32]
             L.or_dr_draw.argtypes = [C.POINTER(ORParams), C.c_uint32, C.c_uint32, C.c_void_p]
             L.or_marker_kernel_g.argtypes = [C.c_double, C.c_double]
             L.or_marker_kernel_g.restype = C.c_double
@@ -258,12 +279,91 @@ class Obj:
         nz, ny, nx = values.shape
         return Obj(OR_GRID, dims=(nx, ny, nz), lo=lo, hi=hi, values=values, fp16=fp16)
 
+    @staticmethod
+    def neural(net: "Nsdf", grid_values=None, grid_lo=None, grid_hi=None, fp16=True):
+        """A learned-SDF object; the optional grid is its fallback (proximity rays march it)."""
+        if grid_values is not None:
+            grid_values = np.asarray(grid_values)
+            nz, ny, nx = grid_values.shape
+            o = Obj(OR_NEURAL, dims=(nx, ny, nz), lo=grid_lo, hi=grid_hi, values=grid_values, fp16=fp16)
+        else:
+            o = Obj(OR_NEURAL)
+        o.keep.append(net)
+        o.s.nsdf = C.cast(C.pointer(net.s), C.c_void_p).value
+        return o
+
     def sdf(self, q):
         q = np.ascontiguousarray(np.atleast_2d(q), np.float64)
         n = len(q)
         phi = np.zeros(n); g = np.zeros((n, 3))
         lib().or_sdf_object_batch(C.byref(self.s), _p(q), n, _p(phi), _p(g))
         return phi, g
+
+
+class Nsdf:
+    """Learned SDF parameters for the oracle: box lo/hi (m), table [16][2^16][2]
+    binary16 bits, w1 [64][32], w2 [64][64], w3 [64] bfloat16 bits."""
+
+    def __init__(self, lo, hi, table, w1, w2, w3):
+        self.table = np.ascontiguousarray(table, np.uint16).reshape(NSDF_LEVELS, NSDF_TABLE, NSDF_FEATURES)
+        self.w1 = np.ascontiguousarray(w1, np.uint16).reshape(NSDF_HIDDEN, NSDF_IN)
+        self.w2 = np.ascontiguousarray(w2, np.uint16).reshape(NSDF_HIDDEN, NSDF_HIDDEN)
+        self.w3 = np.ascontiguousarray(w3, np.uint16).reshape(NSDF_HIDDEN)
+        s = ORNsdf()
+        s.lo[:] = [float(v) for v in lo]
+        s.hi[:] = [float(v) for v in hi]
+        s.table, s.w1, s.w2, s.w3 = _p(self.table), _p(self.w1), _p(self.w2), _p(self.w3)
+        self.s = s
+
+    def eval(self, q, round=True, grad=False):
+        """phi (m) and, with grad, the raw gradient d phi / d q (not normalised)."""
+        q = np.ascontiguousarray(np.atleast_2d(q), np.float64)
+        n = len(q)
+        phi = np.zeros(n)
+        g = np.zeros((n, 3)) if grad else None
+        lib().or_nsdf_eval_batch(C.byref(self.s), n, _p(q), 1 if round else 0, _p(phi), _p(g) if grad else None)
+        return (phi, g) if grad else phi
+
+    def flip_bound(self, q):
+        """Per point, the largest output change (mm) one bfloat16 rounding flip can cause."""
+        q = np.ascontiguousarray(np.atleast_2d(q), np.float64)
+        out = np.zeros(len(q))
+        lib().or_nsdf_flip_bound_batch(C.byref(self.s), len(q), _p(q), _p(out))
+        return out
+
+    def loss_grad(self, pts, labels_mm, round=True):
+        """(loss, g_w1, g_w2, g_w3, g_table) of the mean L1 loss, FP64."""
+        pts = np.ascontiguousarray(pts, np.float64)
+        y = np.ascontiguousarray(labels_mm, np.float64)
+        g1 = np.zeros((NSDF_HIDDEN, NSDF_IN)); g2 = np.zeros((NSDF_HIDDEN, NSDF_HIDDEN)); g3 = np.zeros(NSDF_HIDDEN)
+        gt = np.zeros((NSDF_LEVELS, NSDF_TABLE, NSDF_FEATURES))
+        loss = lib().or_nsdf_loss_grad(C.byref(self.s), len(pts), _p(pts), _p(y), 1 if round else 0,
+                                       _p(g1), _p(g2), _p(g3), _p(gt))
+        return loss, g1, g2, g3, gt
+
+
+def bf16_to_double(b):
+    return lib().or_bf16_to_double(int(b))
+
+
+def double_to_bf16(x):
+    return int(lib().or_double_to_bf16(float(x)))
+
+
+def nsdf_resolution(level):
+    return int(lib().or_nsdf_resolution(int(level)))
+
+
+def nsdf_index(level, i, j, k):
+    return int(lib().or_nsdf_index(int(level), int(i), int(j), int(k)))
+
+
+def adam_step(theta, m, v, g, lr, beta1, beta2, eps, t):
+    """In place on float64 arrays."""
+    for a in (theta, m, v, g):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    lib().or_adam_step(theta.size, _p(theta), _p(m), _p(v), _p(g), float(lr), float(beta1), float(beta2),
+                       float(eps), int(t))
 
 
 def ray_first_root(obj: "Obj", q0, d, tmax, scale=1.0):

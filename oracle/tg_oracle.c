@@ -398,6 +398,18 @@ double or_sdf_object(const or_object* o, const double q[3], double g[3]) {
     case OR_PLANE: return or_sdf_plane(q, g);
     case OR_MESH: return or_sdf_mesh(o->verts, o->faces, o->n_faces, q, g);
     case OR_GRID: return or_sdf_grid(o, q, g);
+    case OR_NEURAL: {
+        double gr[3];
+        double phi = or_nsdf_eval(o->nsdf, q, 1, gr);
+        double gn = norm3(gr);
+        if (gn > 0.0) { g[0] = gr[0] / gn; g[1] = gr[1] / gn; g[2] = gr[2] / gn; }
+        else {
+            double qn = norm3(q);
+            if (qn > 0.0) { g[0] = q[0] / qn; g[1] = q[1] / qn; g[2] = q[2] / qn; }
+            else { g[0] = 0.0; g[1] = 0.0; g[2] = 1.0; }
+        }
+        return phi;
+    }
     default: g[0] = g[1] = g[2] = NAN; return NAN;
     }
 }
@@ -665,7 +677,8 @@ double or_ray_first_root(const or_object* o, double scale, const double q0[3], c
         return t <= tmax ? t : NAN;
     }
     case OR_MESH: return mesh_first_root(o, scale, q0, d, tmax, grazing);
-    case OR_GRID: return grid_first_root(o, scale, q0, d, tmax, grazing);
+    case OR_GRID:
+    case OR_NEURAL: return grid_first_root(o, scale, q0, d, tmax, grazing);  /* neural: its fallback grid */
     default: return NAN;
     }
 }

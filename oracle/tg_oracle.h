@@ -24,7 +24,22 @@ extern "C" {
 #endif
 
 /* ---- object kinds -------------------------------------------------------- */
-enum { OR_SPHERE = 0, OR_BOX = 1, OR_PLANE = 2, OR_MESH = 3, OR_GRID = 4 };
+enum { OR_SPHERE = 0, OR_BOX = 1, OR_PLANE = 2, OR_MESH = 3, OR_GRID = 4, OR_NEURAL = 5 };
+
+/* ---- learned SDF (tg_oracle_nsdf.c): hash encoding + bfloat16 MLP -------- */
+#define OR_NSDF_LEVELS 16
+#define OR_NSDF_FEATURES 2
+#define OR_NSDF_TABLE 65536u
+#define OR_NSDF_HIDDEN 64
+#define OR_NSDF_IN (OR_NSDF_LEVELS * OR_NSDF_FEATURES)
+
+typedef struct {
+    double lo[3], hi[3];      /* encoding box, object frame (m) */
+    const uint16_t* table;    /* [16][2^16][2] binary16 bits */
+    const uint16_t* w1;       /* [64][32] bfloat16 bits, row = hidden unit */
+    const uint16_t* w2;       /* [64][64] */
+    const uint16_t* w3;       /* [64] */
+} or_nsdf;
 
 typedef struct {
     int32_t kind;
@@ -36,7 +51,8 @@ typedef struct {
     int32_t dims[3];          /* OR_GRID nodes per axis (x, y, z) */
     double lo[3], hi[3];      /* OR_GRID box corners, object frame */
     int32_t fp16;             /* OR_GRID: 1 = values are binary16 bits */
-    const void* values;       /* OR_GRID values [z][y][x] */
+    const void* values;       /* OR_GRID values [z][y][x]; OR_NEURAL: its fallback grid, marched by proximity rays */
+    const or_nsdf* nsdf;      /* OR_NEURAL */
 } or_object;
 
 /* ---- noise knobs of one sensor group (Appendix A, "Sensor Noise Model") -- */
@@ -166,6 +182,20 @@ double or_ray_first_root(const or_object* o, double scale, const double q0[3], c
 void or_dr_draw(const or_params* P, uint32_t env_gid, uint32_t step, double out[3]);
 void or_prox_ray_dirs(const double n[3], int n_rays, double cone, double dirs[][3]);
 double or_marker_kernel_g(double lambda_d, double r2);
+
+/* learned SDF (round = 1: activations rounded to bfloat16 as on tensor cores) */
+double or_bf16_to_double(uint16_t b);
+uint16_t or_double_to_bf16(double x);
+int32_t or_nsdf_resolution(int32_t level);
+uint32_t or_nsdf_index(int32_t level, int64_t i, int64_t j, int64_t k);
+double or_nsdf_eval(const or_nsdf* n, const double q[3], int32_t round, double grad_raw[3]);
+double or_nsdf_flip_bound(const or_nsdf* n, const double q[3]);
+double or_nsdf_loss_grad(const or_nsdf* n, int64_t B, const double* pts, const double* labels_mm, int32_t round,
+                         double* g_w1, double* g_w2, double* g_w3, double* g_table);
+void or_adam_step(int64_t n, double* theta, double* m, double* v, const double* g, double lr, double beta1,
+                  double beta2, double eps, int32_t t);
+void or_nsdf_eval_batch(const or_nsdf* n, int64_t B, const double* pts, int32_t round, double* phi, double* grad_raw);
+void or_nsdf_flip_bound_batch(const or_nsdf* n, int64_t B, const double* pts, double* out);
 
 /* ---- whole-scene operations ------------------------------------------------- */
 void or_reset(const or_scene* S, const uint8_t* env_mask, uint32_t episode, or_state* st);
