@@ -99,6 +99,9 @@ typedef struct {
        NULL. */
     int32_t dr_on;
     double dr_mu[2], dr_k[2], dr_scale[2];
+    /* largest probe error (mm, at the largest object scale) for which a
+       NEURAL object's network is used instead of its grid (0.2) */
+    double nsdf_max_err_mm;
 } tg_params;
 
 /* sensor mask bits (depth, contact and force/torque are always computed) */
@@ -158,8 +161,61 @@ typedef enum {
     TG_OBJ_BOX = 1,      /* half[3], centred at the origin */
     TG_OBJ_PLANE = 2,    /* half-space z <= 0 */
     TG_OBJ_MESH = 3,     /* closed, outward-oriented triangle mesh: exact distance, winding-number sign */
-    TG_OBJ_GRID = 4      /* sampled SDF: trilinear, node (i,j,k) at lo + (i,j,k)(hi-lo)/(dims-1) */
+    TG_OBJ_GRID = 4,     /* sampled SDF: trilinear, node (i,j,k) at lo + (i,j,k)(hi-lo)/(dims-1) */
+    TG_OBJ_NEURAL = 5    /* learned SDF (tg_nsdf) with a GRID fallback, see tg_upload_objects */
 } tg_object_kind;
+
+/* ---- learned signed distance ("neural SDF", configs 3-4 of the evaluation)
+   A multiresolution hash encoding (16 levels x 2 binary16 features, 2^16
+   entries per level) of the object-frame point over a box, feeding a
+   32 -> 64 -> 64 -> 1 ReLU MLP with bfloat16 weights and no biases; the output
+   is the signed distance in millimetres.  Level l has N_l = floor(16 2^(l/3))
+   cells per axis (16 .. 512); vertex (i,j,k) is entry i + (N+1)(j + (N+1)k)
+   while (N+1)^3 <= 2^16, else (i ^ j 2654435761 ^ k 805459861) mod 2^16.
+   Inference runs the layers on tensor cores (bfloat16 operands, FP32
+   accumulation: the encoding and both hidden activations are rounded to
+   bfloat16).  Outside the box phi = phi(clamp q) + |q - clamp q|.
+   Parameter layout: table [16][2^16][2] binary16 bits; weights 6,208
+   bfloat16 bits = W1 [64][32], then W2 [64][64], then W3 [64] (row = output
+   unit).  A tg_nsdf owns device parameters, FP32 master copies and Adam
+   state; not thread-safe. */
+typedef struct tg_nsdf tg_nsdf;
+#define TG_NSDF_TABLE_ENTRIES (16 * 65536)
+#define TG_NSDF_WEIGHTS 6208
+
+/* New network over the box [lo, hi] (object frame, m), initialised from
+   `seed`: table uniform in +-1e-4, weights uniform in +-sqrt(6 / (fan_in +
+   fan_out)).  Errors: TG_ERR_INVALID_ARG (lo >= hi), TG_ERR_OOM. */
+tg_status tg_nsdf_create(const float lo[3], const float hi[3], uint64_t seed, tg_nsdf** out);
+void tg_nsdf_destroy(tg_nsdf* net);
+/* Set / get the parameters (host or device buffers of the layout above);
+   setting also resets the Adam state and the FP32 masters to the values. */
+tg_status tg_nsdf_set_params(tg_nsdf* net, const uint16_t* table, const uint16_t* weights);
+tg_status tg_nsdf_get_params(tg_nsdf* net, uint16_t* table, uint16_t* weights);
+/* phi (m) at n object-frame points (device [n][3]) into device phi [n];
+   grad (device [n][3] or NULL): the raw gradient d phi / d q of the network
+   (FP32, taken at the clamped point; not normalised).  Asynchronous. */
+tg_status tg_nsdf_eval(tg_nsdf* net, const float* points, int64_t n, float* phi, float* grad, tg_stream stream);
+/* Mean over the n points (device [n][3]) of |out - label_mm| and its
+   gradients, the training forward and backward: FP32 activations on the
+   stored binary16 / bfloat16 parameters, gradients into device g_weights
+   [6208] and g_table [16][2^16][2] (FP32); *loss written on the host after
+   the work completes (the call synchronises `stream`). */
+tg_status tg_nsdf_loss_grad(tg_nsdf* net, const float* points, const float* labels_mm, int64_t n, double* loss,
+                            float* g_weights, float* g_table, tg_stream stream);
+/* `steps` Adam steps (beta1 0.9, beta2 0.99, eps 1e-15) on minibatches of
+   `batch` points drawn uniformly (Philox, `seed`) from the n labelled points
+   (device [n][3] and [n], labels in mm); learning rate lr0 (lr_final /
+   lr0)^(t / steps).  losses (host [steps] or NULL): each step's minibatch
+   loss; the call synchronises `stream` when losses is given. */
+tg_status tg_nsdf_train(tg_nsdf* net, const float* points, const float* labels_mm, int64_t n, int32_t steps,
+                        int32_t batch, double lr0, double lr_final, uint64_t seed, float* losses, tg_stream stream);
+/* Error probe against the exact mesh distance: over n probe points (device
+   [n][3]), the maximum and mean |phi_net - phi_mesh| in mm.  Synchronous. */
+/* message of the last failed tg_nsdf_* call on this thread */
+const char* tg_nsdf_last_error(void);
+tg_status tg_nsdf_probe(tg_nsdf* net, const float* verts, int32_t n_verts, const int32_t* faces, int32_t n_faces,
+                        const float* points, int64_t n, double* max_err_mm, double* mean_err_mm, tg_stream stream);
 
 typedef struct {
     int32_t kind;
@@ -172,13 +228,22 @@ typedef struct {
     float lo[3], hi[3];               /* GRID box, lo < hi */
     int32_t fp16;                     /* GRID: 1 = values are IEEE binary16 */
     const void* values;               /* GRID: host or device [dims z][dims y][dims x] */
+    const tg_nsdf* nsdf;              /* NEURAL: the network (its parameters are copied) */
+    double nsdf_err_mm;               /* NEURAL: probe error (tg_nsdf_probe max); < 0 = not probed */
 } tg_object_desc;
 
 /* Upload (replace) the scene's object table.  Per env, tg_step_inputs.obj_id
    picks one object.  The library copies everything.  A query outside a grid's
-   box reads phi(clamp(q)) + |q - clamp(q)|.  Errors: TG_ERR_INVALID_ARG,
-   TG_ERR_OOM, TG_ERR_CUDA. */
+   box reads phi(clamp(q)) + |q - clamp(q)|.  A NEURAL object carries a
+   network and a GRID (dims, lo, hi, fp16, values): the network answers the
+   contact query when 0 <= nsdf_err_mm * s_max <= params.nsdf_max_err_mm
+   (s_max = dr_scale hi under domain randomisation, else 1), else the grid
+   does; proximity rays always march the grid.  tg_object_info reports the
+   choice.  Errors: TG_ERR_INVALID_ARG, TG_ERR_OOM, TG_ERR_CUDA. */
 tg_status tg_upload_objects(tg_scene* scene, const tg_object_desc* objs, int32_t n);
+/* kind in use for object i (TG_OBJ_NEURAL or, after a fallback, TG_OBJ_GRID)
+   and the probe error it was uploaded with (NaN for other kinds). */
+tg_status tg_object_info(const tg_scene* scene, int32_t i, int32_t* kind_used, double* nsdf_err_mm);
 
 /* Start a new episode for the envs whose env_mask byte is non-zero (host or
    device [E]; NULL = all): dead masks are redrawn from (seed, taxel id,

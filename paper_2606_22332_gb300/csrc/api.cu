@@ -1,6 +1,7 @@
 // api.cu -- host side of the C-ABI declared in include/tg.h: argument
 // validation, scene layout (CSR work items, link lattices), device
 // allocation, staging of host inputs, launches, reads and checkpoints.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -10,6 +11,11 @@
 #include "internal.h"
 
 using namespace tg;
+
+struct ObjInfo {
+    int32_t kind = 0;
+    double err_mm = NAN;
+};
 
 struct tg_scene {
     int E = 0, L = 0;
@@ -53,6 +59,11 @@ struct tg_scene {
     float* pad_frame = nullptr;
     float* marker_u = nullptr;
 
+    // objects as uploaded; learned-SDF query scratch
+    std::vector<ObjInfo> obj_info;
+    bool any_neural = false;
+    float* nq_phi = nullptr;          // [T]
+    float* nq_grad = nullptr;         // [3][T]
     // schedule (tg_set_schedule / tg_autotune) and step control
     int persistent = 0;               // step kernel: persistent CTAs on a work counter
     int sorted = 1;                   // object-sorted item order (several objects)
@@ -241,6 +252,9 @@ StepArgs step_args(tg_scene* s) {
     a.n_items = s->n_items;
     a.persistent = s->persistent;
     a.resident_ctas = s->resident_ctas;
+    a.nq_phi = s->nq_phi;
+    a.nq_grad = s->nq_grad;
+    a.any_neural = s->any_neural ? 1 : 0;
     return a;
 }
 
@@ -526,7 +540,7 @@ void tg_destroy_scene(tg_scene* s) {
                     s->ft_noisy, s->link_out, s->link_count, s->err, s->link_rec, s->s_link_pose, s->s_link_vel,
                     s->s_obj_pose, s->s_obj_vel, s->s_env_params, s->s_obj_id, s->s_mask, s->s_contact,
                     s->item_order, s->prox_clean, s->prox_noisy, s->pad_link, s->pad_frame,
-                    s->marker_u, s->ctl};
+                    s->marker_u, s->ctl, s->nq_phi, s->nq_grad};
     for (void* p : ptrs) dfree(p);
     delete s;
 }
@@ -538,6 +552,47 @@ tg_status tg_upload_objects(tg_scene* s, const tg_object_desc* objs, int32_t n) 
     std::vector<void*> bufs;
     auto cleanup = [&]() {
         for (void* p : bufs) dfree(p);
+    };
+    std::vector<ObjInfo> info(n);
+    for (int i = 0; i < n; ++i) info[i].kind = objs[i].kind;
+    bool any_neural = false;
+    // a grid (or a neural object's fallback grid): cell-major device copy
+    auto load_grid = [&](const tg_object_desc& o, ObjDev& t) -> tg_status {
+        size_t cnt = 1;
+        for (int a = 0; a < 3; ++a) {
+            if (o.dims[a] < 2 || !(o.hi[a] > o.lo[a]) || !std::isfinite(o.lo[a]) || !std::isfinite(o.hi[a]))
+                return fail(s, TG_ERR_INVALID_ARG, "grid needs dims >= 2 and lo < hi on every axis");
+            cnt *= (size_t)o.dims[a];
+            t.dims[a] = o.dims[a];
+            t.lo[a] = o.lo[a];
+            t.hi[a] = o.hi[a];
+            const double h = ((double)o.hi[a] - (double)o.lo[a]) / (double)(o.dims[a] - 1);
+            const double ih = 1.0 / h;
+            t.h[a] = (float)h;
+            t.inv_h_hi[a] = (float)ih;
+            t.inv_h_lo[a] = (float)(ih - (double)t.inv_h_hi[a]);
+        }
+        if (!o.values) return fail(s, TG_ERR_INVALID_ARG, "grid values are NULL");
+        const size_t esz = o.fp16 ? 2 : 4;
+        const size_t bytes = cnt * esz;
+        const size_t ncell = (size_t)(o.dims[0] - 1) * (o.dims[1] - 1) * (o.dims[2] - 1);
+        void *dv = nullptr, *dc = nullptr;
+        cudaError_t e = cudaMalloc(&dv, bytes);
+        if (e != cudaSuccess) return cuda_fail(s, e, "grid alloc");
+        e = cudaMalloc(&dc, ncell * 8 * esz);
+        if (e != cudaSuccess) {
+            cudaFree(dv);
+            return cuda_fail(s, e, "grid cell alloc");
+        }
+        bufs.push_back(dc);
+        e = cudaMemcpy(dv, o.values, bytes, cudaMemcpyDefault);
+        if (e == cudaSuccess) e = launch_build_cells(dv, o.dims, o.fp16 ? 1 : 0, dc, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        cudaFree(dv);  // queries read the cell-major copy only
+        if (e != cudaSuccess) return cuda_fail(s, e, "grid copy");
+        t.fp16 = o.fp16 ? 1 : 0;
+        t.cells = dc;
+        return TG_OK;
     };
     for (int i = 0; i < n; ++i) {
         const tg_object_desc& o = objs[i];
@@ -575,40 +630,38 @@ tg_status tg_upload_objects(tg_scene* s, const tg_object_desc* objs, int32_t n) 
             t.tri_n = dn;
             break;
         }
-        case TG_OBJ_GRID: {
-            size_t cnt = 1;
+        case TG_OBJ_GRID:
+            if (tg_status st = load_grid(o, t)) { cleanup(); return st; }
+            break;
+        case TG_OBJ_NEURAL: {
+            if (!o.nsdf) { cleanup(); return fail(s, TG_ERR_INVALID_ARG, "neural object without a network"); }
+            if (tg_status st = load_grid(o, t)) { cleanup(); return st; }  // the fallback
+            const NsdfNet* net = nsdf_net(o.nsdf);
+            const double smax = s->params.dr_on ? s->params.dr_scale[1] : 1.0;
+            const double err = o.nsdf_err_mm;
+            const bool use = err >= 0.0 && err * smax <= s->params.nsdf_max_err_mm;
+            info[i].kind = use ? TG_OBJ_NEURAL : TG_OBJ_GRID;
+            info[i].err_mm = err;
+            if (!use) { t.kind = TG_OBJ_GRID; break; }
+            uint32_t* tab = nullptr;
+            uint16_t* w = nullptr;
+            cudaError_t e1 = dalloc(&tab, (size_t)TG_NSDF_TABLE_ENTRIES), e2 = dalloc(&w, (size_t)TG_NSDF_WEIGHTS);
+            if (tab) bufs.push_back(tab);
+            if (w) bufs.push_back(w);
+            if (e1 != cudaSuccess || e2 != cudaSuccess) { cleanup(); return cuda_fail(s, e1 != cudaSuccess ? e1 : e2, "network alloc"); }
+            cudaError_t e = cudaDeviceSynchronize();  // the network may still be training on a stream
+            if (e == cudaSuccess) e = cudaMemcpy(tab, net->table, sizeof(uint32_t) * TG_NSDF_TABLE_ENTRIES, cudaMemcpyDeviceToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(w, net->weights, sizeof(uint16_t) * TG_NSDF_WEIGHTS, cudaMemcpyDeviceToDevice);
+            if (e != cudaSuccess) { cleanup(); return cuda_fail(s, e, "network copy"); }
+            const ObjDev nd = nsdf_objdev(*net);
             for (int a = 0; a < 3; ++a) {
-                if (o.dims[a] < 2 || !(o.hi[a] > o.lo[a]) || !std::isfinite(o.lo[a]) || !std::isfinite(o.hi[a])) {
-                    cleanup();
-                    return fail(s, TG_ERR_INVALID_ARG, "grid needs dims >= 2 and lo < hi on every axis");
-                }
-                cnt *= (size_t)o.dims[a];
-                t.dims[a] = o.dims[a];
-                t.lo[a] = o.lo[a];
-                t.hi[a] = o.hi[a];
-                const double h = ((double)o.hi[a] - (double)o.lo[a]) / (double)(o.dims[a] - 1);
-                const double ih = 1.0 / h;
-                t.h[a] = (float)h;
-                t.inv_h_hi[a] = (float)ih;
-                t.inv_h_lo[a] = (float)(ih - (double)t.inv_h_hi[a]);
+                t.nlo[a] = nd.nlo[a];
+                t.nhi[a] = nd.nhi[a];
+                t.ninv_ext[a] = nd.ninv_ext[a];
             }
-            if (!o.values) { cleanup(); return fail(s, TG_ERR_INVALID_ARG, "grid values are NULL"); }
-            const size_t esz = o.fp16 ? 2 : 4;
-            const size_t bytes = cnt * esz;
-            const size_t ncell = (size_t)(o.dims[0] - 1) * (o.dims[1] - 1) * (o.dims[2] - 1);
-            void *dv = nullptr, *dc = nullptr;
-            cudaError_t e = cudaMalloc(&dv, bytes);
-            if (e != cudaSuccess) { cleanup(); return cuda_fail(s, e, "grid alloc"); }
-            e = cudaMalloc(&dc, ncell * 8 * esz);
-            if (e != cudaSuccess) { cudaFree(dv); cleanup(); return cuda_fail(s, e, "grid cell alloc"); }
-            bufs.push_back(dc);
-            e = cudaMemcpy(dv, o.values, bytes, cudaMemcpyDefault);
-            if (e == cudaSuccess) e = launch_build_cells(dv, o.dims, o.fp16 ? 1 : 0, dc, 0);
-            if (e == cudaSuccess) e = cudaDeviceSynchronize();
-            cudaFree(dv);  // queries read the cell-major copy only
-            if (e != cudaSuccess) { cleanup(); return cuda_fail(s, e, "grid copy"); }
-            t.fp16 = o.fp16 ? 1 : 0;
-            t.cells = dc;
+            t.ntable = tab;
+            t.nweights = w;
+            any_neural = true;
             break;
         }
         default:
@@ -621,10 +674,29 @@ tg_status tg_upload_objects(tg_scene* s, const tg_object_desc* objs, int32_t n) 
     if (e != cudaSuccess) { cleanup(); return cuda_fail(s, e, "object table alloc"); }
     cudaMemcpy(dtab, table.data(), sizeof(ObjDev) * n, cudaMemcpyHostToDevice);
     CK(s, cudaDeviceSynchronize());  // old objects may still be read by queued steps
+    if (any_neural && !s->nq_phi) {
+        cudaError_t ea = dalloc(&s->nq_phi, (size_t)std::max<int64_t>(s->T, 1));
+        if (ea == cudaSuccess) ea = dalloc(&s->nq_grad, (size_t)3 * std::max<int64_t>(s->T, 1));
+        if (ea != cudaSuccess) {
+            dfree(dtab);
+            cleanup();
+            return cuda_fail(s, ea, "learned-SDF scratch");
+        }
+    }
     free_objects(s);
     s->objects = dtab;
     s->n_objects = n;
     s->obj_bufs = bufs;
+    s->obj_info = info;
+    s->any_neural = any_neural;
+    return TG_OK;
+}
+
+tg_status tg_object_info(const tg_scene* s, int32_t i, int32_t* kind_used, double* nsdf_err_mm) {
+    if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
+    if (i < 0 || i >= (int32_t)s->obj_info.size()) return TG_ERR_INVALID_ARG;
+    if (kind_used) *kind_used = s->obj_info[i].kind;
+    if (nsdf_err_mm) *nsdf_err_mm = s->obj_info[i].err_mm;
     return TG_OK;
 }
 
@@ -708,6 +780,7 @@ tg_status enqueue_step(tg_scene* s, const tg_step_inputs* in, cudaStream_t st, b
         a.item_order = s->item_order;
     }
     if (prof) CK(s, record(ev[1]));
+    if (s->any_neural) CK(s, launch_nsdf_step_query(a, s->n_items, s->nq_phi, s->nq_grad, st));
     CK(s, launch_step(a, s->n_items, st));
     if (prof) CK(s, record(ev[2]));
     if (s->sensors & TG_SENSOR_PROX) CK(s, launch_prox(a, s->n_items, st));

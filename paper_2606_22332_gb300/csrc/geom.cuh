@@ -368,7 +368,8 @@ __device__ __forceinline__ float sdf_fast(const ObjDev& o, float3 q, float3* g) 
     case TG_OBJ_BOX: return box_fast(o, q, g);
     case TG_OBJ_PLANE: *g = f3(0.f, 0.f, 1.f); return q.z;
     case TG_OBJ_MESH: return mesh_fast(o, q, g);
-    case TG_OBJ_GRID: return grid_fast(o, q, g);
+    case TG_OBJ_GRID:
+    case TG_OBJ_NEURAL: return grid_fast(o, q, g);  // a learned SDF's fallback grid (proximity, markers)
     default: *g = f3(0.f, 0.f, 1.f); return __int_as_float(0x7fc00000);
     }
 }
@@ -383,7 +384,8 @@ __device__ __forceinline__ df sdf_refine(const ObjDev& o, df3 q, float3* g) {
     case TG_OBJ_BOX: return box_refine(o, q, g);
     case TG_OBJ_PLANE: *g = f3(0.f, 0.f, 1.f); return q.z;
     case TG_OBJ_MESH: return mesh_refine(o, q, g);
-    case TG_OBJ_GRID: return grid_refine(o, q, g);
+    case TG_OBJ_GRID:
+    case TG_OBJ_NEURAL: return grid_refine(o, q, g);
     default: *g = f3(0.f, 0.f, 1.f); return df_from(__int_as_float(0x7fc00000));
     }
 }

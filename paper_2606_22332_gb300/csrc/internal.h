@@ -73,6 +73,10 @@ struct ObjDev {
     int n_verts, n_faces;
     const float* tri;                 // [n_faces][9]: a, b, c vertices
     const float* tri_n;               // [n_faces][3]: unit outward normals
+    // learned SDF (kind TG_OBJ_NEURAL; the grid fields hold its fallback grid)
+    float nlo[3], nhi[3], ninv_ext[3];
+    const uint32_t* ntable;           // [16][2^16] binary16 pairs
+    const uint16_t* nweights;         // 6,208 bfloat16: W1 [64][32], W2 [64][64], W3 [64]
 };
 
 // One CTA of the step kernel: a run of whole links of one env.
@@ -131,6 +135,12 @@ struct StepArgs {
     unsigned int* err;                // [0] non-finite count
     float* prox_clean;                // [T] (proximity on)
     float* prox_noisy;                // [T]
+    // learned-SDF objects: phi (scaled) of every taxel of a neural item and
+    // the raw object-frame gradient of its near-contact taxels, from the
+    // neural query kernel that runs before the step kernel
+    const float* nq_phi;              // [T]
+    const float* nq_grad;             // [3][T]
+    int any_neural;
 };
 
 // Elastomer marker pads (one CTA per (env, pad)).
@@ -191,5 +201,34 @@ cudaError_t launch_build_cells(const void* values, const int dims[3], int fp16, 
 cudaError_t launch_prox(const StepArgs& a, int n_items, cudaStream_t s);
 cudaError_t launch_markers(const MarkerArgs& m, cudaStream_t s);
 cudaError_t launch_unpack_contact(const uint8_t* flags, int64_t n, int noisy, uint8_t* out, cudaStream_t s);
+
+// learned SDF (nsdf.cu)
+struct NsdfNet {
+    float lo[3], hi[3];
+    uint32_t* table;                  // [16][2^16] binary16 pairs (inference copy)
+    uint16_t* weights;                // [6208] bfloat16 (inference copy)
+    float* master;                    // [6208 + 2 * 16 * 2^16] FP32 masters: weights, then table
+    float* adam_m;
+    float* adam_v;
+    int32_t adam_t;
+};
+cudaError_t nsdf_alloc(NsdfNet* n);
+void nsdf_free(NsdfNet* n);
+cudaError_t nsdf_init(NsdfNet* n, uint64_t seed, cudaStream_t s);
+cudaError_t nsdf_sync_masters(NsdfNet* n, cudaStream_t s);   // masters <- inference copies, Adam state zeroed
+cudaError_t launch_nsdf_eval(const ObjDev& o, const float* pts, int64_t n, float* phi, float* grad, cudaStream_t s);
+// training forward/backward on points[idx[b]] (idx null: b), gradients accumulated into g_w [6208] and
+// g_table [16][2^16][2]; per-CTA partial sums of |out - label| into loss_part [ceil(n/128)]
+cudaError_t launch_nsdf_train_step(const ObjDev& o, const float* pts, const float* labels, const uint32_t* idx,
+                                   int64_t n, float* g_part, float* g_w, float* g_table, float* loss_part,
+                                   cudaStream_t s);
+cudaError_t launch_nsdf_sample(uint64_t seed, uint32_t step, int64_t n_points, int32_t batch, uint32_t* idx,
+                               cudaStream_t s);
+cudaError_t launch_nsdf_adam(NsdfNet* n, const float* g_w, const float* g_table, float lr, float inv_batch_scale,
+                             cudaStream_t s);
+cudaError_t launch_nsdf_step_query(const StepArgs& a, int n_items, float* phi, float* grad, cudaStream_t s);
+int nsdf_train_ctas(int64_t n);       // partial-gradient rows launch_nsdf_train_step writes
+ObjDev nsdf_objdev(const NsdfNet& n); // a learned-SDF object over the network's own buffers
+const NsdfNet* nsdf_net(const tg_nsdf* h);
 
 }  // namespace tg

@@ -1,0 +1,654 @@
+// nsdf.cu -- the learned signed-distance surrogate on the GPU: inference on
+// tensor cores, the input gradient of near-contact queries, the training
+// forward/backward, and Adam.
+//
+// Inference (tiles of 128 points, 8 warps): each point's 32 encoding values
+// are gathered from the binary16 table and rounded to bfloat16; the two
+// hidden layers run as warp-level bfloat16 MMAs with FP32 accumulation (one
+// warp per 16 points; the accumulator fragments of layer 1 are re-packed in
+// registers as the A operand of layer 2); ReLU outputs are rounded to
+// bfloat16; the output layer is an FP32 dot product of the rounded h2 with
+// W3.  Near-contact points get d phi / d q in FP32 (one warp per point).
+//
+// Training (tiles of 128 points, one thread per point for the per-point
+// vectors): FP32 activations on the stored binary16 / bfloat16 parameters,
+// backward of the mean L1 loss; weight gradients as per-CTA partial sums
+// reduced by a second kernel, table gradients by float2 atomics.
+#include <cmath>
+#include <cstdint>
+#include <cuda_bf16.h>
+
+#include "nsdf.cuh"
+#include "rng.cuh"
+
+namespace tg {
+
+namespace {
+
+constexpr int kRows = 128;
+constexpr int kInferThreads = 256;
+constexpr int kEncStride = 40;   // bfloat16 per row of the encoding tile (32 + 8 padding)
+constexpr int kHidStride = 72;   // bfloat16 per row of a hidden tile (64 + 8 padding)
+constexpr uint32_t kTagNsdfBatch = 48, kTagNsdfInit = 49;
+
+struct SmemInfer {
+    __nv_bfloat16 w1[kNsdfHidden * kEncStride];  // [o][k]
+    __nv_bfloat16 w2[kNsdfHidden * kHidStride];  // [o][i]
+    float w3[kNsdfHidden];
+    __nv_bfloat16 enc[kRows * kEncStride];
+    __nv_bfloat16 h1[kRows * kHidStride];
+    __nv_bfloat16 h2[kRows * kHidStride];
+    float u[kRows][3];
+    float ext[kRows];
+    float out[kRows];
+    float q[kRows][3];
+    int64_t gidx[kRows];   // destination index of each row (-1: padding)
+    float scale[kRows];
+    int16_t queue[kRows];
+    int nq;
+};
+
+__device__ __forceinline__ uint32_t ld_u32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ void load_weights(SmemInfer& S, const uint16_t* w) {
+    const __nv_bfloat16* wb = reinterpret_cast<const __nv_bfloat16*>(w);
+    for (int j = threadIdx.x; j < kNsdfHidden * kNsdfIn; j += blockDim.x)
+        S.w1[(j / kNsdfIn) * kEncStride + j % kNsdfIn] = wb[j];
+    for (int j = threadIdx.x; j < kNsdfHidden * kNsdfHidden; j += blockDim.x)
+        S.w2[(j / kNsdfHidden) * kHidStride + j % kNsdfHidden] = wb[kNsdfHidden * kNsdfIn + j];
+    for (int j = threadIdx.x; j < kNsdfHidden; j += blockDim.x)
+        S.w3[j] = bf16f(w[kNsdfHidden * kNsdfIn + kNsdfHidden * kNsdfHidden + j]);
+}
+
+// Forward of the 128 rows whose u[] is set: S.out[r] (mm); h1, h2 kept.
+__device__ void infer_tile(SmemInfer& S, const uint32_t* table) {
+    const int tid = threadIdx.x;
+    {   // encoding: two threads per row, 8 levels each
+        const int r = tid >> 1, half = tid & 1;
+        float enc[16];
+        nsdf_encode_levels<8>(table, S.u[r], 8 * half, enc);
+#pragma unroll
+        for (int j = 0; j < 16; j += 2)
+            *reinterpret_cast<uint32_t*>(&S.enc[r * kEncStride + 16 * half + j]) = pack_bf16(enc[j], enc[j + 1]);
+    }
+    __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    const int r0 = 16 * warp;
+    float acc[8][4];
+    uint32_t af[4][4];
+    // layer 1: [16 x 32] x [32 x 64]
+#pragma unroll
+    for (int n = 0; n < 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+        const __nv_bfloat16* A = S.enc + (r0 + g) * kEncStride + 16 * ks + 2 * t;
+        const uint32_t a0 = ld_u32(A), a1 = ld_u32(A + 8 * kEncStride), a2 = ld_u32(A + 8),
+                       a3 = ld_u32(A + 8 * kEncStride + 8);
+#pragma unroll
+        for (int n = 0; n < 8; ++n) {
+            const __nv_bfloat16* B = S.w1 + (8 * n + g) * kEncStride + 16 * ks + 2 * t;
+            mma_bf16(acc[n], a0, a1, a2, a3, ld_u32(B), ld_u32(B + 8));
+        }
+    }
+    // ReLU, bfloat16, re-pack as the A operand of layer 2, keep h1
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+        const uint32_t lo = pack_bf16(fmaxf(acc[n][0], 0.f), fmaxf(acc[n][1], 0.f));
+        const uint32_t hi = pack_bf16(fmaxf(acc[n][2], 0.f), fmaxf(acc[n][3], 0.f));
+        af[n >> 1][(n & 1) ? 2 : 0] = lo;
+        af[n >> 1][(n & 1) ? 3 : 1] = hi;
+        *reinterpret_cast<uint32_t*>(&S.h1[(r0 + g) * kHidStride + 8 * n + 2 * t]) = lo;
+        *reinterpret_cast<uint32_t*>(&S.h1[(r0 + g + 8) * kHidStride + 8 * n + 2 * t]) = hi;
+    }
+    // layer 2: [16 x 64] x [64 x 64]
+#pragma unroll
+    for (int n = 0; n < 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+#pragma unroll
+        for (int n = 0; n < 8; ++n) {
+            const __nv_bfloat16* B = S.w2 + (8 * n + g) * kHidStride + 16 * ks + 2 * t;
+            mma_bf16(acc[n], af[ks][0], af[ks][1], af[ks][2], af[ks][3], ld_u32(B), ld_u32(B + 8));
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+        *reinterpret_cast<uint32_t*>(&S.h2[(r0 + g) * kHidStride + 8 * n + 2 * t]) =
+            pack_bf16(fmaxf(acc[n][0], 0.f), fmaxf(acc[n][1], 0.f));
+        *reinterpret_cast<uint32_t*>(&S.h2[(r0 + g + 8) * kHidStride + 8 * n + 2 * t]) =
+            pack_bf16(fmaxf(acc[n][2], 0.f), fmaxf(acc[n][3], 0.f));
+    }
+    __syncwarp();
+    // output layer: FP32 dot of the rounded h2 with W3 (one lane per row, two rows per lane pair)
+    if (lane < 16) {
+        const int r = r0 + lane;
+        float s = 0.f;
+#pragma unroll 8
+        for (int i = 0; i < kNsdfHidden; ++i) s = fmaf(__bfloat162float(S.h2[r * kHidStride + i]), S.w3[i], s);
+        S.out[r] = s;
+    }
+}
+
+// d phi / d q (object frame, raw) of row r, by one warp.
+__device__ float3 row_grad(const SmemInfer& S, const uint32_t* table, const ObjDev& o, int r) {
+    const int lane = threadIdx.x & 31;
+    // g_z2 = [h2 > 0] W3 for units lane, lane + 32
+    const float gz2a = __bfloat162float(S.h2[r * kHidStride + lane]) > 0.f ? S.w3[lane] : 0.f;
+    const float gz2b = __bfloat162float(S.h2[r * kHidStride + lane + 32]) > 0.f ? S.w3[lane + 32] : 0.f;
+    float gh1a = 0.f, gh1b = 0.f;  // units lane, lane + 32
+#pragma unroll 8
+    for (int oo = 0; oo < kNsdfHidden; ++oo) {
+        const float v = __shfl_sync(0xffffffffu, oo < 32 ? gz2a : gz2b, oo & 31);
+        gh1a = fmaf(v, __bfloat162float(S.w2[oo * kHidStride + lane]), gh1a);
+        gh1b = fmaf(v, __bfloat162float(S.w2[oo * kHidStride + lane + 32]), gh1b);
+    }
+    const float gz1a = __bfloat162float(S.h1[r * kHidStride + lane]) > 0.f ? gh1a : 0.f;
+    const float gz1b = __bfloat162float(S.h1[r * kHidStride + lane + 32]) > 0.f ? gh1b : 0.f;
+    float genc = 0.f;  // d out / d enc[lane]
+#pragma unroll 8
+    for (int i = 0; i < kNsdfHidden; ++i) {
+        const float v = __shfl_sync(0xffffffffu, i < 32 ? gz1a : gz1b, i & 31);
+        genc = fmaf(v, __bfloat162float(S.w1[i * kEncStride + lane]), genc);
+    }
+    const float ge0 = __shfl_sync(0xffffffffu, genc, (2 * lane) & 31);
+    const float ge1 = __shfl_sync(0xffffffffu, genc, (2 * lane + 1) & 31);
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    if (lane < kNsdfLevels) {
+        const int l = lane;
+        const NsdfCell c = nsdf_cell(l, S.u[r][0], S.u[r][1], S.u[r][2]);
+        const float N = (float)(c.n1 - 1);
+#pragma unroll
+        for (int corner = 0; corner < 8; ++corner) {
+            const uint32_t dx = corner & 1, dy = (corner >> 1) & 1, dz = corner >> 2;
+            const float tx = dx ? c.fx : 1.f - c.fx, ty = dy ? c.fy : 1.f - c.fy, tz = dz ? c.fz : 1.f - c.fz;
+            const float sx = dx ? 1.f : -1.f, sy = dy ? 1.f : -1.f, sz = dz ? 1.f : -1.f;
+            const float2 f = nsdf_feat(table, l, nsdf_entry(l, c.n1, c.i + dx, c.j + dy, c.k + dz));
+            const float fe = ge0 * f.x + ge1 * f.y;
+            gx = fmaf(sx * ty * tz * N, fe, gx);
+            gy = fmaf(tx * sy * tz * N, fe, gy);
+            gz = fmaf(tx * ty * sz * N, fe, gz);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        gx += __shfl_xor_sync(0xffffffffu, gx, off);
+        gy += __shfl_xor_sync(0xffffffffu, gy, off);
+        gz += __shfl_xor_sync(0xffffffffu, gz, off);
+    }
+    return make_float3(1e-3f * gx * o.ninv_ext[0], 1e-3f * gy * o.ninv_ext[1], 1e-3f * gz * o.ninv_ext[2]);
+}
+
+__device__ __forceinline__ void set_row(SmemInfer& S, const ObjDev& o, int r, float3 q) {
+    S.ext[r] = nsdf_clamp(o, q, S.u[r]);
+}
+
+__global__ void __launch_bounds__(kInferThreads) nsdf_eval_kernel(const ObjDev o, const float* pts, int64_t n,
+                                                                  float* phi, float* grad) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemInfer& S = *reinterpret_cast<SmemInfer*>(smem_raw);
+    load_weights(S, o.nweights);
+    const int64_t n_tiles = (n + kRows - 1) / kRows;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t base = tile * kRows;
+        if (threadIdx.x < kRows) {
+            const int64_t i = base + threadIdx.x;
+            float3 q = make_float3(0.f, 0.f, 0.f);
+            if (i < n) q = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
+            else q = make_float3(o.nlo[0], o.nlo[1], o.nlo[2]);
+            set_row(S, o, threadIdx.x, q);
+        }
+        __syncthreads();
+        infer_tile(S, o.ntable);
+        __syncthreads();
+        if (threadIdx.x < kRows && base + threadIdx.x < n) phi[base + threadIdx.x] = 1e-3f * S.out[threadIdx.x] + S.ext[threadIdx.x];
+        if (grad) {
+            const int warp = threadIdx.x >> 5;
+            for (int r = warp; r < kRows && base + r < n; r += kInferThreads / 32) {
+                const float3 gr = row_grad(S, o.ntable, o, r);
+                if ((threadIdx.x & 31) == 0) {
+                    grad[3 * (base + r)] = gr.x;
+                    grad[3 * (base + r) + 1] = gr.y;
+                    grad[3 * (base + r) + 2] = gr.z;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+constexpr int kQueryLinks = 32;
+
+// Per work item whose env holds a learned-SDF object: phi (scaled) of every
+// taxel, and the raw object-frame gradient of the taxels within 1 um of
+// contact (those the step kernel refines).
+__global__ void __launch_bounds__(kInferThreads) nsdf_step_query_kernel(const StepArgs a, float* phi_out,
+                                                                        float* grad_out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemInfer& S = *reinterpret_cast<SmemInfer*>(smem_raw);
+    __shared__ float rec_s[kQueryLinks][kLinkRec];
+    __shared__ int start_s[kQueryLinks + 1];
+    const Item it = a.items[a.item_order ? a.item_order[blockIdx.x] : blockIdx.x];
+    const int e = it.env, L = a.max_links, lb = it.link_begin, nl = it.link_end - it.link_begin, n = it.n_taxels;
+    const int oid = min(max(a.obj_id[e], 0), a.n_objects - 1);
+    const ObjDev& o = a.objects[oid];
+    if (o.kind != TG_OBJ_NEURAL) return;
+    const int64_t T = a.n_taxels;
+    load_weights(S, o.nweights);
+    for (int i = threadIdx.x; i < nl * kLinkRec; i += kInferThreads)
+        rec_s[i / kLinkRec][i % kLinkRec] = a.link_rec[(size_t)(e * L + lb + i / kLinkRec) * kLinkRec + i % kLinkRec];
+    if ((int)threadIdx.x <= nl) {
+        const int base = a.lattice[e * L + lb].env_offset;
+        start_s[threadIdx.x] = (int)threadIdx.x < nl ? a.lattice[e * L + lb + threadIdx.x].env_offset - base : n;
+    }
+    __syncthreads();
+    for (int base = 0; base < n; base += kRows) {
+        if (threadIdx.x == 0) S.nq = 0;
+        if (threadIdx.x < kRows) {
+            const int i = base + threadIdx.x;
+            float3 q = make_float3(o.nlo[0], o.nlo[1], o.nlo[2]);
+            S.gidx[threadIdx.x] = -1;
+            S.scale[threadIdx.x] = 0.f;
+            if (i < n) {
+                int l = 0;
+                while (i >= start_s[l + 1]) ++l;
+                const float* rec = rec_s[l];
+                const int64_t g = it.taxel_begin + i;
+                const float x0 = a.x[g], x1 = a.y[g], x2 = a.z[g];
+                q = make_float3(fmaf(rec[0], x0, fmaf(rec[1], x1, fmaf(rec[2], x2, rec[18]))),
+                                fmaf(rec[3], x0, fmaf(rec[4], x1, fmaf(rec[5], x2, rec[19]))),
+                                fmaf(rec[6], x0, fmaf(rec[7], x1, fmaf(rec[8], x2, rec[20]))));
+                S.gidx[threadIdx.x] = g;
+                S.scale[threadIdx.x] = rec[38];
+            }
+            set_row(S, o, threadIdx.x, q);
+        }
+        __syncthreads();
+        infer_tile(S, o.ntable);
+        __syncthreads();
+        if (threadIdx.x < kRows) {
+            const int64_t g = S.gidx[threadIdx.x];
+            if (g >= 0) {
+                const float p = S.scale[threadIdx.x] * (1e-3f * S.out[threadIdx.x] + S.ext[threadIdx.x]);
+                phi_out[g] = p;
+                const float R = a.R[g];
+                if (R > 0.0f && p < R + 1e-6f) S.queue[atomicAdd(&S.nq, 1)] = (int16_t)threadIdx.x;
+            }
+        }
+        __syncthreads();
+        const int warp = threadIdx.x >> 5;
+        for (int k = warp; k < S.nq; k += kInferThreads / 32) {
+            const int r = S.queue[k];
+            const float3 gr = row_grad(S, o.ntable, o, r);
+            if ((threadIdx.x & 31) == 0) {
+                const int64_t g = S.gidx[r];
+                grad_out[g] = gr.x;
+                grad_out[T + g] = gr.y;
+                grad_out[2 * T + g] = gr.z;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- training
+constexpr int kTrainThreads = 128;
+
+struct SmemTrain {
+    float w1[kNsdfHidden][kNsdfIn + 1];
+    float w2[kNsdfHidden][kNsdfHidden + 1];
+    float w3[kNsdfHidden];
+    float enc[kRows][kNsdfIn + 1];
+    float h1[kRows][kNsdfHidden + 1];   // h1, later g_z1
+    float h2[kRows][kNsdfHidden + 1];   // h2, later g_z2
+    float gout[kRows];
+    float red[kTrainThreads / 32];
+};
+
+__global__ void __launch_bounds__(kTrainThreads) nsdf_train_kernel(const ObjDev o, const float* pts,
+                                                                   const float* labels, const uint32_t* idx,
+                                                                   int64_t n, float* g_part, float* g_table,
+                                                                   float* loss_part) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemTrain& S = *reinterpret_cast<SmemTrain*>(smem_raw);
+    const int p = threadIdx.x;
+    for (int j = p; j < kNsdfHidden * kNsdfIn; j += kTrainThreads) S.w1[j / kNsdfIn][j % kNsdfIn] = bf16f(o.nweights[j]);
+    for (int j = p; j < kNsdfHidden * kNsdfHidden; j += kTrainThreads)
+        S.w2[j / kNsdfHidden][j % kNsdfHidden] = bf16f(o.nweights[kNsdfHidden * kNsdfIn + j]);
+    if (p < kNsdfHidden) S.w3[p] = bf16f(o.nweights[kNsdfHidden * kNsdfIn + kNsdfHidden * kNsdfHidden + p]);
+    const int64_t b = (int64_t)blockIdx.x * kRows + p;
+    const bool valid = b < n;
+    const int64_t src = valid ? (idx ? (int64_t)idx[b] : b) : 0;
+    float u[3];
+    {
+        const float3 q = make_float3(pts[3 * src], pts[3 * src + 1], pts[3 * src + 2]);
+        nsdf_clamp(o, q, u);
+    }
+    float enc[kNsdfIn];
+    nsdf_encode(o.ntable, u, enc);
+#pragma unroll
+    for (int k = 0; k < kNsdfIn; ++k) S.enc[p][k] = enc[k];
+    __syncthreads();
+    // forward, one row per thread, FP32
+    for (int oo = 0; oo < kNsdfHidden; ++oo) {
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < kNsdfIn; ++k) s = fmaf(S.w1[oo][k], enc[k], s);
+        S.h1[p][oo] = fmaxf(s, 0.f);
+    }
+    float out = 0.f;
+    for (int oo = 0; oo < kNsdfHidden; ++oo) {
+        float s = 0.f;
+#pragma unroll 16
+        for (int i = 0; i < kNsdfHidden; ++i) s = fmaf(S.w2[oo][i], S.h1[p][i], s);
+        s = fmaxf(s, 0.f);
+        S.h2[p][oo] = s;
+        out = fmaf(S.w3[oo], s, out);
+    }
+    const float res = valid ? out - labels[src] : 0.f;
+    const float go = res > 0.f ? 1.f : (res < 0.f ? -1.f : 0.f);
+    S.gout[p] = go;
+    // loss partial
+    float l = fabsf(res);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
+    if ((p & 31) == 0) S.red[p >> 5] = l;
+    __syncthreads();
+    if (p == 0) {
+        float s = 0.f;
+        for (int w = 0; w < kTrainThreads / 32; ++w) s += S.red[w];
+        loss_part[blockIdx.x] = s;
+    }
+    float* gp = g_part + (size_t)blockIdx.x * kNsdfWeights;
+    // dW3[i] = sum_p gout[p] h2[p][i]
+    if (p < kNsdfHidden) {
+        float s = 0.f;
+        for (int r = 0; r < kRows; ++r) s = fmaf(S.gout[r], S.h2[r][p], s);
+        gp[kNsdfHidden * kNsdfIn + kNsdfHidden * kNsdfHidden + p] = s;
+    }
+    __syncthreads();
+    // g_z2 = [h2 > 0] gout W3 (in place, own row)
+    for (int oo = 0; oo < kNsdfHidden; ++oo) S.h2[p][oo] = S.h2[p][oo] > 0.f ? go * S.w3[oo] : 0.f;
+    __syncthreads();
+    {   // dW2[o][i] = sum_p g_z2[p][o] h1[p][i]: thread -> o = p / 2, i in 32 columns
+        const int oo = p >> 1, i0 = (p & 1) * 32;
+        float acc[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+        for (int r = 0; r < kRows; ++r) {
+            const float gz = S.h2[r][oo];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc[j] = fmaf(gz, S.h1[r][i0 + j], acc[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) gp[kNsdfHidden * kNsdfIn + oo * kNsdfHidden + i0 + j] = acc[j];
+    }
+    __syncthreads();
+    // g_z1 = [h1 > 0] W2^T g_z2 (in place, own row)
+    for (int i = 0; i < kNsdfHidden; ++i) {
+        float s = 0.f;
+#pragma unroll 16
+        for (int oo = 0; oo < kNsdfHidden; ++oo) s = fmaf(S.h2[p][oo], S.w2[oo][i], s);
+        S.h1[p][i] = S.h1[p][i] > 0.f ? s : 0.f;
+    }
+    __syncthreads();
+    {   // dW1[o][k] = sum_p g_z1[p][o] enc[p][k]: thread -> o = p / 2, k in 16 columns
+        const int oo = p >> 1, k0 = (p & 1) * 16;
+        float acc[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[j] = 0.f;
+        for (int r = 0; r < kRows; ++r) {
+            const float gz = S.h1[r][oo];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[j] = fmaf(gz, S.enc[r][k0 + j], acc[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) gp[oo * kNsdfIn + k0 + j] = acc[j];
+    }
+    // d loss / d enc for this row, then the table entries it read
+    if (!valid || go == 0.f) return;
+    float genc[kNsdfIn];
+#pragma unroll
+    for (int k = 0; k < kNsdfIn; ++k) genc[k] = 0.f;
+    for (int oo = 0; oo < kNsdfHidden; ++oo) {
+        const float gz = S.h1[p][oo];
+        if (gz == 0.f) continue;
+#pragma unroll
+        for (int k = 0; k < kNsdfIn; ++k) genc[k] = fmaf(gz, S.w1[oo][k], genc[k]);
+    }
+    float2* gt = reinterpret_cast<float2*>(g_table);
+#pragma unroll 1
+    for (int lv = 0; lv < kNsdfLevels; ++lv) {
+        const NsdfCell c = nsdf_cell(lv, u[0], u[1], u[2]);
+#pragma unroll
+        for (int corner = 0; corner < 8; ++corner) {
+            const uint32_t dx = corner & 1, dy = (corner >> 1) & 1, dz = corner >> 2;
+            const float w = (dx ? c.fx : 1.f - c.fx) * (dy ? c.fy : 1.f - c.fy) * (dz ? c.fz : 1.f - c.fz);
+            const uint32_t e = nsdf_entry(lv, c.n1, c.i + dx, c.j + dy, c.k + dz);
+            atomicAdd(gt + (size_t)lv * kNsdfTable + e, make_float2(w * genc[2 * lv], w * genc[2 * lv + 1]));
+        }
+    }
+}
+
+// g_w[j] = scale * sum over CTAs of g_part[cta][j]
+__global__ void nsdf_reduce_kernel(const float* g_part, int n_part, float scale, float* g_w) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= kNsdfWeights) return;
+    float s = 0.f;
+    for (int b = 0; b < n_part; ++b) s += g_part[(size_t)b * kNsdfWeights + j];
+    g_w[j] = s * scale;
+}
+
+__global__ void nsdf_sample_kernel(uint64_t seed, uint32_t step, int64_t n_points, int32_t batch, uint32_t* idx) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    const uint4 w = draw(seed, (uint64_t)b, step, kTagNsdfBatch);
+    idx[b] = (uint32_t)(((uint64_t)w.x * (uint64_t)n_points) >> 32);
+}
+
+__device__ __forceinline__ uint16_t to_bf16_bits(float x) {
+    const __nv_bfloat16 v = __float2bfloat16_rn(x);
+    return *reinterpret_cast<const uint16_t*>(&v);
+}
+
+// Adam over the weights (j < 6208) and the table entries (two features each).
+__global__ void nsdf_adam_kernel(float* master, float* m, float* v, const float* g_w, const float* g_table,
+                                 uint16_t* weights, uint32_t* table, float lr, float c1, float c2, float gscale) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const float b1 = 0.9f, b2 = 0.99f, eps = 1e-15f;
+    if (j < kNsdfWeights) {
+        const float g = g_w[j] * gscale;
+        const float mm = b1 * m[j] + (1.f - b1) * g, vv = b2 * v[j] + (1.f - b2) * g * g;
+        m[j] = mm;
+        v[j] = vv;
+        const float th = master[j] - lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+        master[j] = th;
+        weights[j] = to_bf16_bits(th);
+        return;
+    }
+    const int64_t e = j - kNsdfWeights;
+    if (e >= kNsdfTableEntries) return;
+    float th[2];
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+        const int64_t k = kNsdfWeights + 2 * e + f;
+        const float g = g_table[2 * e + f] * gscale;
+        const float mm = b1 * m[k] + (1.f - b1) * g, vv = b2 * v[k] + (1.f - b2) * g * g;
+        m[k] = mm;
+        v[k] = vv;
+        th[f] = master[k] - lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+        master[k] = th[f];
+    }
+    const __half2 h = __floats2half2_rn(th[0], th[1]);
+    table[e] = *reinterpret_cast<const uint32_t*>(&h);
+}
+
+__global__ void nsdf_init_kernel(uint64_t seed, float* master, float* m, float* v, uint16_t* weights,
+                                 uint32_t* table) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < kNsdfWeights) {
+        const float lim = j < kNsdfHidden * kNsdfIn
+                              ? sqrtf(6.f / (kNsdfIn + kNsdfHidden))
+                              : (j < kNsdfHidden * kNsdfIn + kNsdfHidden * kNsdfHidden ? sqrtf(6.f / (2 * kNsdfHidden))
+                                                                                      : sqrtf(6.f / (kNsdfHidden + 1)));
+        const float th = lim * (2.f * u24(draw(seed, (uint64_t)j, 0u, kTagNsdfInit).x) - 1.f);
+        master[j] = th;
+        m[j] = 0.f;
+        v[j] = 0.f;
+        weights[j] = to_bf16_bits(th);
+        return;
+    }
+    const int64_t e = j - kNsdfWeights;
+    if (e >= kNsdfTableEntries) return;
+    const uint4 w = draw(seed, (uint64_t)j, 0u, kTagNsdfInit);
+    float th[2];
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+        const int64_t k = kNsdfWeights + 2 * e + f;
+        th[f] = 1e-4f * (2.f * u24(f ? w.y : w.x) - 1.f);
+        master[k] = th[f];
+        m[k] = 0.f;
+        v[k] = 0.f;
+    }
+    const __half2 h = __floats2half2_rn(th[0], th[1]);
+    table[e] = *reinterpret_cast<const uint32_t*>(&h);
+}
+
+__global__ void nsdf_sync_masters_kernel(float* master, float* m, float* v, const uint16_t* weights,
+                                         const uint32_t* table) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < kNsdfWeights) {
+        master[j] = bf16f(weights[j]);
+        m[j] = v[j] = 0.f;
+        return;
+    }
+    const int64_t e = j - kNsdfWeights;
+    if (e >= kNsdfTableEntries) return;
+    const uint32_t t = table[e];
+    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&t));
+    master[kNsdfWeights + 2 * e] = f.x;
+    master[kNsdfWeights + 2 * e + 1] = f.y;
+    m[kNsdfWeights + 2 * e] = m[kNsdfWeights + 2 * e + 1] = 0.f;
+    v[kNsdfWeights + 2 * e] = v[kNsdfWeights + 2 * e + 1] = 0.f;
+}
+
+constexpr int64_t kParamCount = kNsdfWeights + 2 * kNsdfTableEntries;
+constexpr int64_t kUpdateCount = kNsdfWeights + kNsdfTableEntries;  // Adam threads
+
+bool g_configured = false;
+
+cudaError_t configure() {
+    if (g_configured) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(nsdf_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(SmemInfer));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(nsdf_step_query_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(SmemInfer));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(nsdf_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SmemTrain));
+    if (e == cudaSuccess) g_configured = true;
+    return e;
+}
+
+}  // namespace
+
+cudaError_t nsdf_alloc(NsdfNet* n) {
+    cudaError_t e = cudaMalloc(&n->table, sizeof(uint32_t) * kNsdfTableEntries);
+    if (e == cudaSuccess) e = cudaMalloc(&n->weights, sizeof(uint16_t) * kNsdfWeights);
+    if (e == cudaSuccess) e = cudaMalloc(&n->master, sizeof(float) * kParamCount);
+    if (e == cudaSuccess) e = cudaMalloc(&n->adam_m, sizeof(float) * kParamCount);
+    if (e == cudaSuccess) e = cudaMalloc(&n->adam_v, sizeof(float) * kParamCount);
+    if (e == cudaSuccess) e = configure();
+    n->adam_t = 0;
+    return e;
+}
+
+void nsdf_free(NsdfNet* n) {
+    cudaFree(n->table);
+    cudaFree(n->weights);
+    cudaFree(n->master);
+    cudaFree(n->adam_m);
+    cudaFree(n->adam_v);
+    n->table = nullptr;
+    n->weights = nullptr;
+    n->master = n->adam_m = n->adam_v = nullptr;
+}
+
+cudaError_t nsdf_init(NsdfNet* n, uint64_t seed, cudaStream_t s) {
+    nsdf_init_kernel<<<(unsigned)((kUpdateCount + 255) / 256), 256, 0, s>>>(seed, n->master, n->adam_m, n->adam_v,
+                                                                           n->weights, n->table);
+    n->adam_t = 0;
+    return cudaGetLastError();
+}
+
+cudaError_t nsdf_sync_masters(NsdfNet* n, cudaStream_t s) {
+    nsdf_sync_masters_kernel<<<(unsigned)((kUpdateCount + 255) / 256), 256, 0, s>>>(n->master, n->adam_m, n->adam_v,
+                                                                                   n->weights, n->table);
+    n->adam_t = 0;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nsdf_eval(const ObjDev& o, const float* pts, int64_t n, float* phi, float* grad, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    cudaError_t e = configure();
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = (n + kRows - 1) / kRows;
+    const unsigned grid = (unsigned)(tiles < 152 * 3 ? tiles : 152 * 3);
+    nsdf_eval_kernel<<<grid, kInferThreads, sizeof(SmemInfer), s>>>(o, pts, n, phi, grad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nsdf_step_query(const StepArgs& a, int n_items, float* phi, float* grad, cudaStream_t s) {
+    if (n_items == 0) return cudaSuccess;
+    cudaError_t e = configure();
+    if (e != cudaSuccess) return e;
+    nsdf_step_query_kernel<<<n_items, kInferThreads, sizeof(SmemInfer), s>>>(a, phi, grad);
+    return cudaGetLastError();
+}
+
+int nsdf_train_ctas(int64_t n) { return (int)((n + kRows - 1) / kRows); }
+
+cudaError_t launch_nsdf_train_step(const ObjDev& o, const float* pts, const float* labels, const uint32_t* idx,
+                                   int64_t n, float* g_part, float* g_w, float* g_table, float* loss_part,
+                                   cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    cudaError_t e = configure();
+    if (e != cudaSuccess) return e;
+    const int ctas = nsdf_train_ctas(n);
+    nsdf_train_kernel<<<ctas, kTrainThreads, sizeof(SmemTrain), s>>>(o, pts, labels, idx, n, g_part, g_table,
+                                                                     loss_part);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    nsdf_reduce_kernel<<<(kNsdfWeights + 255) / 256, 256, 0, s>>>(g_part, ctas, 1.0f, g_w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nsdf_sample(uint64_t seed, uint32_t step, int64_t n_points, int32_t batch, uint32_t* idx,
+                               cudaStream_t s) {
+    nsdf_sample_kernel<<<(batch + 255) / 256, 256, 0, s>>>(seed, step, n_points, batch, idx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nsdf_adam(NsdfNet* n, const float* g_w, const float* g_table, float lr, float gscale,
+                             cudaStream_t s) {
+    n->adam_t += 1;
+    const double c1 = 1.0 - std::pow(0.9, (double)n->adam_t), c2 = 1.0 - std::pow(0.99, (double)n->adam_t);
+    nsdf_adam_kernel<<<(unsigned)((kUpdateCount + 255) / 256), 256, 0, s>>>(
+        n->master, n->adam_m, n->adam_v, g_w, g_table, n->weights, n->table, lr, (float)c1, (float)c2, gscale);
+    return cudaGetLastError();
+}
+
+}  // namespace tg

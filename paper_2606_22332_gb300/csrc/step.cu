@@ -101,8 +101,13 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
         if (has1)
             while (i1 >= S.start[l1 + 1]) ++l1;
         float phi0 = 0.0f, phi1 = 0.0f;
-        if (R0 > 0.0f) phi0 = fast_query(S.rec[l0], obj, x00, x01, x02);
-        if (R1 > 0.0f) phi1 = fast_query(S.rec[l1], obj, x10, x11, x12);
+        if (obj.kind == TG_OBJ_NEURAL) {  // from the learned-SDF query kernel
+            if (R0 > 0.0f) phi0 = a.nq_phi[g0];
+            if (R1 > 0.0f) phi1 = a.nq_phi[g1];
+        } else {
+            if (R0 > 0.0f) phi0 = fast_query(S.rec[l0], obj, x00, x01, x02);
+            if (R1 > 0.0f) phi1 = fast_query(S.rec[l1], obj, x10, x11, x12);
+        }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             if (u == 1 && !has1) break;

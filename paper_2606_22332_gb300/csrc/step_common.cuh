@@ -95,7 +95,14 @@ __device__ __forceinline__ CleanReading refine_taxel(const StepArgs& a, const fl
     }
     float3 go;
     const float scale = rec[38];
-    const df phid = df_mul_f(sdf_refine(obj, df3{qd[0], qd[1], qd[2]}, &go), scale);
+    df phid;
+    if (obj.kind == TG_OBJ_NEURAL) {
+        // the learned SDF has no compensated form: its FP32 phi and gradient
+        phid = df_from(a.nq_phi[g]);
+        go = f3(a.nq_grad[g], a.nq_grad[T + g], a.nq_grad[2 * T + g]);
+    } else {
+        phid = df_mul_f(sdf_refine(obj, df3{qd[0], qd[1], qd[2]}, &go), scale);
+    }
     const df dd = df_add_f(df_neg(phid), R);  // R - phi
     CleanReading out;
     out.d = dd.hi > 0.0f ? dd.hi : 0.0f;

@@ -27,7 +27,8 @@ _lib = C.CDLL(LIB_PATH)
 TG_OK = 0
 STATUS = {0: "TG_OK", 1: "TG_ERR_INVALID_ARG", 2: "TG_ERR_OOM", 3: "TG_ERR_CUDA", 4: "TG_ERR_STATE",
           5: "TG_ERR_TIMEOUT", 6: "TG_ERR_NUMERIC", 7: "TG_ERR_UNSUPPORTED"}
-TG_OBJ_SPHERE, TG_OBJ_BOX, TG_OBJ_PLANE, TG_OBJ_MESH, TG_OBJ_GRID = 0, 1, 2, 3, 4
+TG_OBJ_SPHERE, TG_OBJ_BOX, TG_OBJ_PLANE, TG_OBJ_MESH, TG_OBJ_GRID, TG_OBJ_NEURAL = 0, 1, 2, 3, 4, 5
+NSDF_TABLE_ENTRIES, NSDF_WEIGHTS = 16 * 65536, 6208
 CH_CONTACT, CH_DEPTH, CH_DIST, CH_FORCE_TORQUE, CH_LINK_WRENCH, CH_LINK_COUNT, CH_STATE_FLAGS, CH_PROX, CH_MARKER = range(9)
 TG_SENSOR_DIST, TG_SENSOR_PROX, TG_SENSOR_MARKERS = 0x1, 0x2, 0x4
 LINK_REC = 18
@@ -49,7 +50,8 @@ class Params(C.Structure):
                                           "p_dead", "chi", "xt_sigma")] + [
         ("seed", C.c_uint64), ("depth", NoiseGroup), ("ft", NoiseGroup), ("prox", NoiseGroup),
         ("prox_rays", C.c_int32), ("prox_range", C.c_double), ("prox_cone", C.c_double),
-        ("dr_on", C.c_int32), ("dr_mu", C.c_double * 2), ("dr_k", C.c_double * 2), ("dr_scale", C.c_double * 2)]
+        ("dr_on", C.c_int32), ("dr_mu", C.c_double * 2), ("dr_k", C.c_double * 2), ("dr_scale", C.c_double * 2),
+        ("nsdf_max_err_mm", C.c_double)]
 
 
 class PadDesc(C.Structure):
@@ -72,7 +74,7 @@ class ObjectDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("radius", C.c_float), ("half", C.c_float * 3),
                 ("n_verts", C.c_int32), ("n_faces", C.c_int32), ("verts", C.c_void_p), ("faces", C.c_void_p),
                 ("dims", C.c_int32 * 3), ("lo", C.c_float * 3), ("hi", C.c_float * 3),
-                ("fp16", C.c_int32), ("values", C.c_void_p)]
+                ("fp16", C.c_int32), ("values", C.c_void_p), ("nsdf", C.c_void_p), ("nsdf_err_mm", C.c_double)]
 
 
 class StepInputs(C.Structure):
@@ -118,17 +120,33 @@ _lib.tg_graph_release.argtypes = [_vp]
 _lib.tg_set_schedule.argtypes = [_vp, _i32, _i32]
 _lib.tg_get_schedule.argtypes = [_vp, C.POINTER(_i32), C.POINTER(_i32)]
 _lib.tg_autotune.argtypes = [_vp, C.POINTER(StepInputs), _i32, C.POINTER(TuneReport), _vp]
+_lib.tg_object_info.argtypes = [_vp, _i32, C.POINTER(_i32), C.POINTER(C.c_double)]
+_lib.tg_nsdf_create.argtypes = [_vp, _vp, C.c_uint64, C.POINTER(_vp)]
+_lib.tg_nsdf_destroy.argtypes = [_vp]
+_lib.tg_nsdf_destroy.restype = None
+_lib.tg_nsdf_set_params.argtypes = [_vp, _vp, _vp]
+_lib.tg_nsdf_get_params.argtypes = [_vp, _vp, _vp]
+_lib.tg_nsdf_eval.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp]
+_lib.tg_nsdf_loss_grad.argtypes = [_vp, _vp, _vp, C.c_int64, C.POINTER(C.c_double), _vp, _vp, _vp]
+_lib.tg_nsdf_train.argtypes = [_vp, _vp, _vp, C.c_int64, _i32, _i32, C.c_double, C.c_double, C.c_uint64, _vp, _vp]
+_lib.tg_nsdf_probe.argtypes = [_vp, _vp, _i32, _vp, _i32, _vp, C.c_int64, C.POINTER(C.c_double),
+                               C.POINTER(C.c_double), _vp]
+_lib.tg_nsdf_last_error.restype = C.c_char_p
 for _f in ("tg_create_scene", "tg_upload_objects", "tg_reset_envs", "tg_step_sensors", "tg_read_taxels",
            "tg_get_buffer", "tg_sync", "tg_save_state", "tg_load_state", "tg_bake_grid", "tg_mesh_sdf",
            "tg_profile_enable", "tg_profile_read", "tg_mesh_sdf_noalloc", "tg_graph_capture", "tg_graph_launch",
-           "tg_graph_seek", "tg_graph_release", "tg_set_schedule", "tg_get_schedule", "tg_autotune"):
+           "tg_graph_seek", "tg_graph_release", "tg_set_schedule", "tg_get_schedule", "tg_autotune", "tg_object_info",
+           "tg_nsdf_create", "tg_nsdf_set_params", "tg_nsdf_get_params", "tg_nsdf_eval", "tg_nsdf_loss_grad",
+           "tg_nsdf_train", "tg_nsdf_probe"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ["tg_create_scene", "tg_destroy_scene", "tg_max_link_taxels", "tg_upload_objects", "tg_reset_envs",
             "tg_step_sensors", "tg_read_taxels", "tg_channel_bytes", "tg_get_buffer", "tg_sync", "tg_last_error",
             "tg_save_state", "tg_load_state", "tg_bake_grid", "tg_mesh_sdf", "tg_profile_enable", "tg_profile_read",
             "tg_mesh_sdf_noalloc", "tg_graph_capture", "tg_graph_launch", "tg_graph_seek", "tg_graph_release",
-            "tg_set_schedule", "tg_get_schedule", "tg_autotune"]
+            "tg_set_schedule", "tg_get_schedule", "tg_autotune", "tg_object_info", "tg_nsdf_create",
+            "tg_nsdf_destroy", "tg_nsdf_set_params", "tg_nsdf_get_params", "tg_nsdf_eval", "tg_nsdf_loss_grad",
+            "tg_nsdf_train", "tg_nsdf_probe", "tg_nsdf_last_error"]
 NOALLOC_MAX_FACES = 65536
 
 
@@ -179,6 +197,7 @@ def _fill_params(params: dict) -> Params:
         for k in ("mu", "k", "scale"):
             getattr(P, "dr_" + k)[0] = float(dr[k][0])
             getattr(P, "dr_" + k)[1] = float(dr[k][1])
+    P.nsdf_max_err_mm = float(params.get("nsdf_max_err_mm", 0.2))
     for g in ("depth", "ft", "prox"):
         grp = getattr(P, g)
         for k in NoiseGroup._fields_:
@@ -196,7 +215,7 @@ def object_desc(o, keep: list) -> ObjectDesc:
     """tg_object_desc of a workload ObjectSpec (arrays kept alive in `keep`)."""
     d = ObjectDesc()
     kind = {"sphere": TG_OBJ_SPHERE, "box": TG_OBJ_BOX, "plane": TG_OBJ_PLANE, "mesh": TG_OBJ_MESH,
-            "grid": TG_OBJ_GRID}[o.kind]
+            "grid": TG_OBJ_GRID, "neural": TG_OBJ_NEURAL}[o.kind]
     d.kind = kind
     d.radius = float(o.radius)
     d.half[:] = [float(h) for h in o.half]
@@ -205,7 +224,13 @@ def object_desc(o, keep: list) -> ObjectDesc:
         keep += [V, F]
         d.n_verts, d.n_faces = len(V), len(F)
         d.verts, d.faces = _ptr(V), _ptr(F)
-    if kind == TG_OBJ_GRID:
+    if kind == TG_OBJ_NEURAL:
+        net = o.net if isinstance(o.net, Nsdf) else Nsdf.from_params(o.nsdf_lo, o.nsdf_hi, o.nsdf_table,
+                                                                     o.nsdf_weights)
+        keep.append(net)
+        d.nsdf = net.h
+        d.nsdf_err_mm = float(o.nsdf_err_mm)
+    if kind in (TG_OBJ_GRID, TG_OBJ_NEURAL):
         vals = o.values
         if isinstance(vals, np.ndarray):
             vals = np.ascontiguousarray(vals, np.uint16 if o.fp16 else np.float32)
@@ -331,6 +356,12 @@ class Scene:
         _check(_lib.tg_graph_release(self.h), self.h)
         self._graph_inputs = None
 
+    def object_info(self, i: int):
+        """(kind in use, probe error mm) of uploaded object i."""
+        k, e = _i32(), C.c_double()
+        _check(_lib.tg_object_info(self.h, int(i), C.byref(k), C.byref(e)), self.h)
+        return int(k.value), float(e.value)
+
     def set_schedule(self, persistent: bool, sorted: bool = True):
         _check(_lib.tg_set_schedule(self.h, int(bool(persistent)), int(bool(sorted))), self.h)
 
@@ -421,6 +452,93 @@ def bake_grid(verts, faces, dims, lo, hi, fp16=False, stream=None):
     _check(_lib.tg_bake_grid(_ptr(V), len(V), _ptr(F), len(F), _ptr(d), _ptr(lo), _ptr(hi), int(fp16),
                              out.data_ptr(), _stream(stream)), None)
     return out
+
+
+def _ncheck(status):
+    if status != 0:
+        msg = _lib.tg_nsdf_last_error()
+        raise TGError(status, msg.decode() if msg else "")
+
+
+class Nsdf:
+    """A learned SDF (tg_nsdf): hash-encoding table and bfloat16 MLP on the device."""
+
+    def __init__(self, lo, hi, seed: int = 0):
+        lo = np.ascontiguousarray(lo, np.float32); hi = np.ascontiguousarray(hi, np.float32)
+        self.lo, self.hi = lo, hi
+        h = _vp()
+        _ncheck(_lib.tg_nsdf_create(_ptr(lo), _ptr(hi), int(seed), C.byref(h)))
+        self.h = h.value
+
+    @classmethod
+    def from_params(cls, lo, hi, table, weights):
+        n = cls(lo, hi, 0)
+        n.set_params(table, weights)
+        return n
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.tg_nsdf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, table, weights):
+        t = np.ascontiguousarray(table, np.uint16).reshape(-1)
+        w = np.ascontiguousarray(weights, np.uint16).reshape(-1)
+        assert t.size == 2 * NSDF_TABLE_ENTRIES and w.size == NSDF_WEIGHTS
+        _ncheck(_lib.tg_nsdf_set_params(self.h, _ptr(t), _ptr(w)))
+
+    def params(self):
+        """(table uint16 [16][65536][2] binary16 bits, weights uint16 [6208] bfloat16 bits)"""
+        t = np.zeros((16, 65536, 2), np.uint16)
+        w = np.zeros(NSDF_WEIGHTS, np.uint16)
+        _ncheck(_lib.tg_nsdf_get_params(self.h, _ptr(t), _ptr(w)))
+        return t, w
+
+    def eval(self, points, grad=False, stream=None):
+        import torch
+
+        pts = points.contiguous()
+        n = pts.shape[0]
+        phi = torch.empty(n, dtype=torch.float32, device=pts.device)
+        g = torch.empty((n, 3), dtype=torch.float32, device=pts.device) if grad else None
+        _ncheck(_lib.tg_nsdf_eval(self.h, pts.data_ptr(), n, phi.data_ptr(), g.data_ptr() if grad else None,
+                                  _stream(stream)))
+        return (phi, g) if grad else phi
+
+    def loss_grad(self, points, labels_mm, stream=None):
+        import torch
+
+        pts, lab = points.contiguous(), labels_mm.contiguous()
+        gw = torch.empty(NSDF_WEIGHTS, dtype=torch.float32, device=pts.device)
+        gt = torch.empty((16, 65536, 2), dtype=torch.float32, device=pts.device)
+        loss = C.c_double()
+        _ncheck(_lib.tg_nsdf_loss_grad(self.h, pts.data_ptr(), lab.data_ptr(), pts.shape[0], C.byref(loss),
+                                       gw.data_ptr(), gt.data_ptr(), _stream(stream)))
+        return loss.value, gw, gt
+
+    def train(self, points, labels_mm, steps: int, batch: int = 1 << 14, lr0: float = 1e-2, lr_final: float = 1e-3,
+              seed: int = 0, record_losses: bool = True, stream=None):
+        pts, lab = points.contiguous(), labels_mm.contiguous()
+        losses = np.zeros(max(steps, 1), np.float32) if record_losses else None
+        _ncheck(_lib.tg_nsdf_train(self.h, pts.data_ptr(), lab.data_ptr(), pts.shape[0], int(steps), int(batch),
+                                   float(lr0), float(lr_final), int(seed),
+                                   _ptr(losses) if record_losses else None, _stream(stream)))
+        return losses[:steps] if record_losses else None
+
+    def probe(self, verts, faces, points, stream=None):
+        """(max, mean) |phi_net - phi_mesh| in mm over device probe points."""
+        V = np.ascontiguousarray(verts, np.float32); F = np.ascontiguousarray(faces, np.int32)
+        pts = points.contiguous()
+        mx, mean = C.c_double(), C.c_double()
+        _ncheck(_lib.tg_nsdf_probe(self.h, _ptr(V), len(V), _ptr(F), len(F), pts.data_ptr(), pts.shape[0],
+                                   C.byref(mx), C.byref(mean), _stream(stream)))
+        return mx.value, mean.value
 
 
 def mesh_sdf(verts, faces, points, with_grad=True, stream=None):

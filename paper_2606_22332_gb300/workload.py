@@ -192,7 +192,7 @@ def superquadric_mesh(rng, eps1: float, eps2: float, axes, n_eta: int, n_omega: 
 # ---------------------------------------------------------------------------
 @dataclass
 class ObjectSpec:
-    kind: str                     # 'sphere' | 'box' | 'plane' | 'mesh' | 'grid'
+    kind: str                     # 'sphere' | 'box' | 'plane' | 'mesh' | 'grid' | 'neural'
     radius: float = 0.0
     half: tuple = (0.0, 0.0, 0.0)
     verts: np.ndarray | None = None
@@ -203,6 +203,58 @@ class ObjectSpec:
     fp16: bool = False
     values: np.ndarray | None = None  # [z][y][x] float32 or binary16 bits (uint16), set by a bake
     name: str = ""
+    # learned SDF ('neural'; the grid fields above hold its fallback grid, verts/faces the exact mesh)
+    net: object = None                # a trained network handle, or None to build one from the arrays below
+    nsdf_lo: np.ndarray | None = None
+    nsdf_hi: np.ndarray | None = None
+    nsdf_table: np.ndarray | None = None    # uint16 [16][65536][2] binary16 bits
+    nsdf_weights: np.ndarray | None = None  # uint16 [6208] bfloat16 bits: W1 [64][32], W2 [64][64], W3 [64]
+    nsdf_err_mm: float = -1.0
+
+
+def bf16_bits(x) -> np.ndarray:
+    """float32 values rounded to the nearest bfloat16 (ties to even), as uint16 bits."""
+    b = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    return ((b + 0x7FFF + ((b >> 16) & 1)) >> 16).astype(np.uint16)
+
+
+def random_nsdf_params(rng, table_scale: float = 1.0, out_scale: float = 20.0):
+    """Seeded learned-SDF parameters for parity tests: table entries uniform in
+    +-table_scale (binary16), weights uniform in +-sqrt(6 / (fan_in + fan_out))
+    (bfloat16; W3 scaled by out_scale so outputs span millimetres)."""
+    table = rng.uniform(-table_scale, table_scale, (16, 65536, 2)).astype(np.float16).view(np.uint16)
+    w1 = rng.uniform(-1, 1, (64, 32)) * np.sqrt(6 / 96)
+    w2 = rng.uniform(-1, 1, (64, 64)) * np.sqrt(6 / 128)
+    w3 = rng.uniform(-1, 1, 64) * np.sqrt(6 / 65) * out_scale
+    weights = bf16_bits(np.concatenate([w1.reshape(-1), w2.reshape(-1), w3]))
+    return table, weights
+
+
+def surface_samples(rng, verts: np.ndarray, faces: np.ndarray, n: int):
+    """n points uniform over the mesh surface (area-weighted) and their face normals."""
+    V = verts.astype(np.float64)
+    a, b, c = V[faces[:, 0]], V[faces[:, 1]], V[faces[:, 2]]
+    cr = np.cross(b - a, c - a)
+    area = 0.5 * np.linalg.norm(cr, axis=1)
+    f = rng.choice(len(faces), n, p=area / area.sum())
+    r1, r2 = np.sqrt(rng.uniform(size=n)), rng.uniform(size=n)
+    p = (1 - r1)[:, None] * a[f] + (r1 * (1 - r2))[:, None] * b[f] + (r1 * r2)[:, None] * c[f]
+    nrm = cr[f] / np.linalg.norm(cr[f], axis=1, keepdims=True)
+    return p, nrm
+
+
+def sdf_sample_points(rng, verts: np.ndarray, faces: np.ndarray, lo, hi, n: int, band: float = 5e-3) -> np.ndarray:
+    """Learned-SDF training / probe points (float32 [n][3], object frame): half
+    within `band` of the surface (a surface point moved along its normal by
+    U(-band, band)), half uniform in the box [lo, hi]."""
+    n_near = n // 2
+    p, nrm = surface_samples(rng, verts, faces, n_near)
+    near = p + nrm * rng.uniform(-band, band, (n_near, 1))
+    lo, hi = np.asarray(lo, np.float64), np.asarray(hi, np.float64)
+    near = np.clip(near, lo, hi)
+    uni = lo + (hi - lo) * rng.uniform(size=(n - n_near, 3))
+    pts = np.concatenate([near, uni])
+    return f32(pts[rng.permutation(n)])
 
 
 def grid_box(verts: np.ndarray):

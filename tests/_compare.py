@@ -40,8 +40,19 @@ def gpu_outputs(scene):
     }
 
 
-def compare_step(gpu, ora, ostate, params, wl, active=None, where=""):
-    """Assert the CUDA step matches the oracle step; returns error statistics."""
+def compare_step(gpu, ora, ostate, params, wl, active=None, where="", tol=None, exclude=None):
+    """Assert the CUDA step matches the oracle step; returns error statistics.
+
+    tol overrides the bounds (keys d_abs, f_rel, f_abs, band, agg_d) where the
+    path has a larger stated error, e.g. a learned SDF's bfloat16 roundings;
+    tol["f_outliers"] is the fraction of active taxels whose force / torque
+    may exceed its bound (normals that are discontinuous at the point, as a
+    learned SDF's are at every hash-grid cell face); those taxels are
+    returned in stats["outliers"] and, with the links that hold them, are
+    skipped for the force checks of the taxels in `exclude`."""
+    t = {"d_abs": D_ABS, "f_rel": F_REL, "f_abs": F_ABS, "band": BAND, "agg_d": 0.0, "f_outliers": 0.0}
+    t.update(tol or {})
+    D_ABS_, F_REL_, F_ABS_, BAND_ = t["d_abs"], t["f_rel"], t["f_abs"], t["band"]
     R = wl.R
     act = R > 0 if active is None else active
     n_act = int(act.sum())
@@ -50,7 +61,7 @@ def compare_step(gpu, ora, ostate, params, wl, active=None, where=""):
     assert np.array_equal((gpu["flags"] >> 1) & 1, (ostate["flags"] >> 1) & 1), f"{where}: dead masks differ"
     # contact bits, with the threshold band
     d_or = ora["depth_clean"]
-    band = (np.abs(d_or - params["eta_on"]) < BAND) | (np.abs(d_or - params["eta_off"]) < BAND)
+    band = (np.abs(d_or - params["eta_on"]) < BAND_) | (np.abs(d_or - params["eta_off"]) < BAND_)
     for k in ("contact_clean", "contact_noisy"):
         bad = (gpu[k] != ora[k]) & ~band
         assert not bad.any(), f"{where}: {k} differs at {np.flatnonzero(bad)[:10]}"
@@ -61,25 +72,31 @@ def compare_step(gpu, ora, ostate, params, wl, active=None, where=""):
     for k in ("depth_clean", "depth_noisy"):
         err = np.abs(gpu[k].astype(np.float64) - ora[k])
         stats[k] = float(err.max()) if err.size else 0.0
-        assert stats[k] <= D_ABS, f"{where}: {k} max err {stats[k]:.3e} at {np.argmax(err)}"
+        assert stats[k] <= D_ABS_, f"{where}: {k} max err {stats[k]:.3e} at {np.argmax(err)}"
     if gpu.get("dist") is not None:
         err = np.abs(gpu["dist"].astype(np.float64) - ora["dist"])
         stats["dist"] = float(err.max()) if err.size else 0.0
-        assert stats["dist"] <= D_ABS, f"{where}: dist max err {stats['dist']:.3e}"
+        assert stats["dist"] <= D_ABS_, f"{where}: dist max err {stats['dist']:.3e}"
     # force/torque, per 3-vector
+    skip = np.zeros(len(R), bool) if exclude is None else exclude.copy()
+    bad = np.zeros(len(R), bool)
     for k in ("ft_clean", "ft_noisy"):
         g, o = gpu[k].astype(np.float64), ora[k]
         for part, rows in (("force", slice(0, 3)), ("torque", slice(3, 6))):
             err = np.linalg.norm(g[rows] - o[rows], axis=0)
-            tol = F_REL * np.linalg.norm(o[rows], axis=0) + F_ABS
-            ratio = err / tol
+            tol_ = F_REL_ * np.linalg.norm(o[rows], axis=0) + F_ABS_
+            ratio = np.where(skip, 0.0, err / tol_)
             key = f"{k}_{part}"
             stats[key] = float(ratio.max()) if ratio.size else 0.0
             stats[key + "_abs"] = float(err.max()) if err.size else 0.0
-            if stats[key] > 1.0:
-                i = int(np.argmax(ratio))
-                raise AssertionError(f"{where}: {key} err {err[i]:.3e} > tol {tol[i]:.3e} at taxel {i}: "
-                                     f"gpu {g[rows, i]} oracle {o[rows, i]} depth {d_or[i]:.3e}")
+            bad |= ratio > 1.0
+    stats["outliers"] = bad
+    if bad.sum() > t["f_outliers"] * n_act:
+        k = "ft_clean" if (np.linalg.norm(gpu["ft_clean"].astype(np.float64) - ora["ft_clean"], axis=0)[bad] > 0).any() else "ft_noisy"
+        i = int(np.flatnonzero(bad)[0])
+        raise AssertionError(f"{where}: {int(bad.sum())} taxels outside the force/torque bound, e.g. taxel {i}: "
+                             f"gpu {gpu[k][:, i]} oracle {ora[k][:, i]} depth {d_or[i]:.3e}")
+    skip |= bad
     # per-link sums
     L = wl.max_links
     off = wl.taxel_offsets
@@ -102,15 +119,17 @@ def compare_step(gpu, ora, ostate, params, wl, active=None, where=""):
             sl = slice(t0, t0 + nl)
             t0 += nl
             rec = e * L + l
+            if skip[sl].any():
+                continue
             for part, cols_, srcs in (("c", range(0, 6), absf["c"]), ("n", range(6, 12), absf["n"])):
                 for j, col in enumerate(cols_):
-                    tol = F_REL * srcs[j, sl].sum() + F_ABS * nl
+                    tol = F_REL_ * srcs[j, sl].sum() + F_ABS_ * nl
                     err = abs(ls_g[rec, col] - ls_o[rec, col])
                     worst = max(worst, err / tol)
                     assert err <= tol, f"{where}: link sum env {e} link {l} col {col}: {ls_g[rec, col]} vs {ls_o[rec, col]}"
             for col, dsrc in ((12, "depth_clean"), (15, "depth_noisy")):
                 for j in range(3):
-                    tol = 1e4 * (D_ABS * 0 + 1e-4 * np.abs(ora[dsrc][sl]).sum()) + F_ABS * nl
+                    tol = 1e4 * (t["agg_d"] * nl + max(1e-4, F_REL_) * np.abs(ora[dsrc][sl]).sum()) + F_ABS_ * nl
                     err = abs(ls_g[rec, col + j] - ls_o[rec, col + j])
                     assert err <= tol, f"{where}: agg_force env {e} link {l}: {ls_g[rec, col + j]} vs {ls_o[rec, col + j]}"
     stats["link_sums"] = worst

@@ -7,7 +7,19 @@ import oracle
 from paper_2606_22332_gb300 import workload as W
 
 
-def oracle_objects(objects):
+def oracle_nsdf(lo, hi, table, weights):
+    """The oracle's copy of learned-SDF parameters (weights split W1 | W2 | W3)."""
+    w = np.asarray(weights, np.uint16).reshape(-1)
+    return oracle.Nsdf(lo, hi, table, w[:2048].reshape(64, 32), w[2048:6144].reshape(64, 64), w[6144:])
+
+
+def neural_in_use(o, params):
+    """The upload rule: the network answers when 0 <= err * s_max <= nsdf_max_err_mm."""
+    smax = params["dr"]["scale"][1] if params.get("dr") else 1.0
+    return 0 <= o.nsdf_err_mm and o.nsdf_err_mm * smax <= params.get("nsdf_max_err_mm", 0.2)
+
+
+def oracle_objects(objects, params=None):
     out = []
     for o in objects:
         if o.kind == "sphere":
@@ -18,16 +30,20 @@ def oracle_objects(objects):
             out.append(oracle.Obj.plane())
         elif o.kind == "mesh":
             out.append(oracle.Obj.mesh(o.verts, o.faces))
-        elif o.kind == "grid":
+        elif o.kind == "grid" or (o.kind == "neural" and not neural_in_use(o, params or {})):
             assert o.values is not None, "grid object has no baked values"
             out.append(oracle.Obj.grid(o.values, o.lo, o.hi, fp16=o.fp16))
+        elif o.kind == "neural":
+            assert o.nsdf_table is not None, "the oracle needs the network's parameters"
+            net = oracle_nsdf(o.nsdf_lo, o.nsdf_hi, o.nsdf_table, o.nsdf_weights)
+            out.append(oracle.Obj.neural(net, o.values, o.lo, o.hi, fp16=o.fp16))
         else:
             raise ValueError(o.kind)
     return out
 
 
 def oracle_scene(wl: W.Workload):
-    return oracle.OracleScene(wl.geom(), oracle_objects(wl.objects), wl.params)
+    return oracle.OracleScene(wl.geom(), oracle_objects(wl.objects, wl.params), wl.params)
 
 
 def pad_workload(depths, rows, cols, params=None, wrap=0, pitch=1e-3, obj=None,

@@ -1,0 +1,180 @@
+"""Learned SDF on the GPU against the FP64 oracle, through the C-ABI.
+
+Inference: the GPU rounds the encoding and both hidden activations to
+bfloat16 before each tensor-core product, as the oracle's round = 1 form
+does; the two differ only where an FP32 sum and its FP64 counterpart round
+to different bfloat16 neighbours.  Each point's tolerance is four times the
+oracle's bound on what one such flip can change (plus FP32 accumulation),
+and most points must agree to 1e-4 mm.
+
+Training: the GPU forward/backward is the exact network (FP32 activations)
+on the stored binary16 / bfloat16 parameters; gradients against the
+oracle's round = 0 gradients to 1e-3 relative; one Adam step against the
+oracle's Adam on the same minibatch.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle
+from paper_2606_22332_gb300 import workload as W
+from _compare import compare_step, gpu_outputs
+from _scenes import bake_objects_oracle, oracle_nsdf, oracle_scene
+
+LO = np.array([-0.02, -0.025, -0.018], np.float32)
+HI = np.array([0.022, 0.02, 0.03], np.float32)
+
+
+@pytest.fixture(scope="module")
+def tg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2606_22332_gb300.tg as tg
+    return tg
+
+
+def _points(rng, n_in, n_out):
+    a = LO + (HI - LO) * rng.uniform(0, 1, (n_in, 3))
+    b = LO + (HI - LO) * rng.uniform(-0.5, 1.5, (n_out, 3))
+    return W.f32(np.concatenate([a, b]))
+
+
+def test_inference_matches_oracle(tg):
+    rng = np.random.default_rng(10)
+    table, w = W.random_nsdf_params(rng)
+    net = tg.Nsdf.from_params(LO, HI, table, w)
+    on = oracle_nsdf(LO, HI, table, w)
+    pts = _points(rng, 20000, 4003)                     # ragged against the 128-point tiles
+    phi, g = net.eval(torch.from_numpy(pts).cuda(), grad=True)
+    phi, g = phi.cpu().numpy().astype(np.float64), g.cpu().numpy().astype(np.float64)
+    phi_o, g_o = on.eval(pts.astype(np.float64), round=True, grad=True)
+    bound = on.flip_bound(pts.astype(np.float64))      # mm
+    err = np.abs(phi - phi_o) * 1e3
+    tol = 4 * bound + 1e-5 + 1e-6 * np.abs(phi_o * 1e3)
+    assert np.all(err <= tol), f"worst {err.max():.3e} mm vs tol {tol[np.argmax(err / tol)]:.3e}"
+    assert np.mean(err < 1e-4) > 0.8  # (outputs span tens of mm: about 1 point in 10 sees a flip)
+    gn = np.linalg.norm(g_o, axis=1)
+    gerr = np.linalg.norm(g - g_o, axis=1) / np.maximum(gn, 1e-12)
+    assert np.mean(gerr < 1e-3) > 0.99, np.quantile(gerr, [0.5, 0.99])
+    # outside the box: phi(clamp) + |q - clamp|
+    out = np.any((pts < LO) | (pts > HI), axis=1)
+    assert out.sum() > 1000
+
+
+def test_loss_gradients_match_oracle(tg):
+    rng = np.random.default_rng(11)
+    table, w = W.random_nsdf_params(rng)
+    net = tg.Nsdf.from_params(LO, HI, table, w)
+    on = oracle_nsdf(LO, HI, table, w)
+    pts = _points(rng, 2500, 501)
+    y = on.eval(pts.astype(np.float64), round=False) * 1e3
+    y = y + rng.choice([-1.0, 1.0], len(y)) * rng.uniform(0.5, 2.0, len(y))
+    loss, gw, gt = net.loss_grad(torch.from_numpy(pts).cuda(), torch.from_numpy(y.astype(np.float32)).cuda())
+    loss_o, g1, g2, g3, gt_o = on.loss_grad(pts.astype(np.float64), y.astype(np.float32).astype(np.float64),
+                                            round=False)
+    assert abs(loss - loss_o) <= 1e-5 * loss_o
+    gw_o = np.concatenate([g1.reshape(-1), g2.reshape(-1), g3])
+    gw = gw.cpu().numpy().astype(np.float64)
+    assert np.allclose(gw, gw_o, rtol=1e-3, atol=1e-5 * np.abs(gw_o).max())
+    gt = gt.cpu().numpy().astype(np.float64)
+    assert np.allclose(gt, gt_o, rtol=1e-3, atol=1e-5 * np.abs(gt_o).max())
+    assert np.count_nonzero(gt_o) > 10000
+
+
+def test_one_adam_step_matches_oracle(tg):
+    rng = np.random.default_rng(12)
+    table, w = W.random_nsdf_params(rng)
+    net = tg.Nsdf.from_params(LO, HI, table, w)
+    on = oracle_nsdf(LO, HI, table, w)
+    n, batch, seed = 5000, 1024, 77
+    pts = _points(rng, 4000, 1000)
+    y = (on.eval(pts.astype(np.float64), round=False) * 1e3
+         + rng.choice([-1.0, 1.0], n) * rng.uniform(0.5, 2.0, n)).astype(np.float32)
+    losses = net.train(torch.from_numpy(pts).cuda(), torch.from_numpy(y).cuda(), steps=1, batch=batch, lr0=1e-2,
+                       lr_final=1e-2, seed=seed)
+    # the same minibatch: index (x n) >> 32 of Philox word 0 at counter (b, step 0, tag 48, 0)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    idx = np.array([(int(oracle.philox([b, 0, 48, 0], key)[0]) * n) >> 32 for b in range(batch)])
+    loss_o, g1, g2, g3, gt_o = on.loss_grad(pts[idx].astype(np.float64), y[idx].astype(np.float64), round=False)
+    assert abs(losses[0] - loss_o) <= 1e-5 * loss_o
+    theta = np.concatenate([W.f32((w.astype(np.uint32) << 16).view(np.float32)).astype(np.float64),
+                            table.view(np.float16).astype(np.float64).reshape(-1)])
+    grad = np.concatenate([g1.reshape(-1), g2.reshape(-1), g3, gt_o.reshape(-1)])
+    m, v = np.zeros_like(theta), np.zeros_like(theta)
+    oracle.adam_step(theta, m, v, grad, 1e-2, 0.9, 0.99, 1e-15, 1)
+    t_gpu, w_gpu = net.params()
+    want_w = W.bf16_bits(theta[:6208].astype(np.float32))
+    diff_w = np.abs(want_w.astype(np.int32) - w_gpu.astype(np.int32))
+    assert np.all(diff_w <= 1) and np.mean(diff_w == 0) > 0.999
+    want_t = theta[6208:].astype(np.float16).view(np.uint16)
+    diff_t = np.abs(want_t.astype(np.int32) - t_gpu.reshape(-1).astype(np.int32))
+    assert np.all(diff_t <= 1) and np.mean(diff_t == 0) > 0.999
+    assert np.count_nonzero(t_gpu.reshape(-1) != table.reshape(-1)) > 1000
+
+
+def _neural_workload(rng, out_scale=2.0):
+    """Grid envs of config 1 with object 0 replaced by a seeded network
+    (its fallback grid is the object's own baked grid)."""
+    wl = W.config1(n_envs=14, n_objects=2, n_grid=24, steps=3)
+    wl.objects = bake_objects_oracle(wl.objects)
+    o = wl.objects[0]
+    table, w = W.random_nsdf_params(rng, table_scale=1.0, out_scale=out_scale)
+    wl.objects[0] = W.ObjectSpec(kind="neural", dims=o.dims, lo=o.lo, hi=o.hi, fp16=o.fp16, values=o.values,
+                                 verts=o.verts, faces=o.faces, nsdf_lo=o.lo, nsdf_hi=o.hi, nsdf_table=table,
+                                 nsdf_weights=w, nsdf_err_mm=0.0, name="neural0")
+    wl.obj_id[:] = np.arange(wl.n_envs) % 2
+    return wl
+
+
+def test_scene_step_with_a_neural_object_matches_oracle(tg):
+    rng = np.random.default_rng(13)
+    wl = _neural_workload(rng)
+    on = oracle_nsdf(wl.objects[0].nsdf_lo, wl.objects[0].nsdf_hi, wl.objects[0].nsdf_table,
+                     wl.objects[0].nsdf_weights)
+    # the phi tolerance of this network: four flips at the worst of 20k box points
+    lo, hi = wl.objects[0].nsdf_lo.astype(np.float64), wl.objects[0].nsdf_hi.astype(np.float64)
+    S = on.flip_bound(lo + (hi - lo) * rng.uniform(0, 1, (20000, 3))).max()
+    d_tol = 4 * S * 1e-3 + 2e-7
+    # normals jump at the hash-grid cell faces: a taxel within FP32 rounding of
+    # a face may take either side's (both are the network's gradient there)
+    tol = {"d_abs": max(d_tol, 1e-5), "band": d_tol, "f_rel": 1e-3, "f_abs": 4 * wl.params["k"] * d_tol + 1e-6,
+           "agg_d": d_tol, "f_outliers": 0.005}
+    sc = tg.Scene.from_workload(wl, sensors=tg.TG_SENSOR_DIST)
+    sc.upload_objects(wl.objects)
+    assert sc.object_info(0)[0] == tg.TG_OBJ_NEURAL and sc.object_info(1)[0] == tg.TG_OBJ_GRID
+    osc = oracle_scene(wl)
+    ost = osc.new_state(); osc.reset(ost, 0)
+    pen = 0
+    skip = np.zeros(wl.n_taxels, bool)
+    for s in range(3):
+        inp = wl.inputs(s)
+        sc.step(inp)
+        g = gpu_outputs(sc)
+        sc.sync()
+        o = osc.step(ost, inp)
+        st = compare_step(g, o, ost, wl.params, wl, where=f"neural step {s}", tol=tol, exclude=skip)
+        skip |= st["outliers"]
+        envs = np.repeat(wl.obj_id, np.diff(wl.taxel_offsets)) == 0
+        pen += int((o["depth_clean"][envs] > 0).sum())
+    assert pen > 100, "the network must put taxels in contact for the test to exercise it"
+    sc.close()
+
+
+def test_probe_error_decides_the_fallback(tg):
+    rng = np.random.default_rng(14)
+    wl = _neural_workload(rng)
+    o = wl.objects[0]
+    o.nsdf_err_mm = 5.0          # above 0.2 mm: the grid answers
+    sc = tg.Scene.from_workload(wl, sensors=tg.TG_SENSOR_DIST)
+    sc.upload_objects(wl.objects)
+    kind, err = sc.object_info(0)
+    assert kind == tg.TG_OBJ_GRID and err == 5.0
+    osc = oracle_scene(wl)       # the oracle takes the same rule
+    ost = osc.new_state(); osc.reset(ost, 0)
+    sc.step(wl.inputs(0))
+    g = gpu_outputs(sc)
+    sc.sync()
+    compare_step(g, osc.step(ost, wl.inputs(0)), ost, wl.params, wl, where="fallback")
+    sc.close()
