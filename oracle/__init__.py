@@ -156,6 +156,7 @@ def lib():
             L.or_nsdf_index.restype = C.c_uint32
             L.or_nsdf_eval_batch.argtypes = [C.POINTER(ORNsdf), C.c_int64, C.c_void_p, C.c_int32, C.c_void_p,
                                              C.c_void_p]
+            L.or_nsdf_normal_batch.argtypes = [C.POINTER(ORNsdf), C.c_int64, C.c_void_p, C.c_int32, C.c_void_p]
             L.or_nsdf_flip_bound_batch.argtypes = [C.POINTER(ORNsdf), C.c_int64, C.c_void_p, C.c_void_p]
             L.or_nsdf_loss_grad.argtypes = [C.POINTER(ORNsdf), C.c_int64, C.c_void_p, C.c_void_p, C.c_int32,
                                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -323,6 +324,13 @@ class Nsdf:
         g = np.zeros((n, 3)) if grad else None
         lib().or_nsdf_eval_batch(C.byref(self.s), n, _p(q), 1 if round else 0, _p(phi), _p(g) if grad else None)
         return (phi, g) if grad else phi
+
+    def normal(self, q, round=True):
+        """Contact-normal gradient (tetrahedral central difference, h = 0.25 mm), not normalised."""
+        q = np.ascontiguousarray(np.atleast_2d(q), np.float64)
+        g = np.zeros((len(q), 3))
+        lib().or_nsdf_normal_batch(C.byref(self.s), len(q), _p(q), 1 if round else 0, _p(g))
+        return g
 
     def flip_bound(self, q):
         """Per point, the largest output change (mm) one bfloat16 rounding flip can cause."""

@@ -400,7 +400,8 @@ double or_sdf_object(const or_object* o, const double q[3], double g[3]) {
     case OR_GRID: return or_sdf_grid(o, q, g);
     case OR_NEURAL: {
         double gr[3];
-        double phi = or_nsdf_eval(o->nsdf, q, 1, gr);
+        double phi = or_nsdf_eval(o->nsdf, q, 1, 0);
+        or_nsdf_normal(o->nsdf, q, 1, gr);
         double gn = norm3(gr);
         if (gn > 0.0) { g[0] = gr[0] / gn; g[1] = gr[1] / gn; g[2] = gr[2] / gn; }
         else {

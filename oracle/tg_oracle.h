@@ -190,6 +190,8 @@ int32_t or_nsdf_resolution(int32_t level);
 uint32_t or_nsdf_index(int32_t level, int64_t i, int64_t j, int64_t k);
 double or_nsdf_eval(const or_nsdf* n, const double q[3], int32_t round, double grad_raw[3]);
 double or_nsdf_flip_bound(const or_nsdf* n, const double q[3]);
+void or_nsdf_normal(const or_nsdf* n, const double q[3], int32_t round, double g[3]);
+void or_nsdf_normal_batch(const or_nsdf* n, int64_t B, const double* pts, int32_t round, double* g);
 double or_nsdf_loss_grad(const or_nsdf* n, int64_t B, const double* pts, const double* labels_mm, int32_t round,
                          double* g_w1, double* g_w2, double* g_w3, double* g_table);
 void or_adam_step(int64_t n, double* theta, double* m, double* v, const double* g, double lr, double beta1,

@@ -213,6 +213,25 @@ double or_nsdf_eval(const or_nsdf* n, const double q[3], int32_t round, double g
     return phi;
 }
 
+/* Contact normal of a learned SDF: the gradient by the four-point
+   tetrahedral central difference at h = 0.25 mm (object frame),
+   sum_k v_k phi(q + h v_k) / (4 h) with v_k = (1,-1,-1), (-1,-1,1),
+   (-1,1,-1), (1,1,1) (sum_k v_k v_k^T = 4 I, so the stencil is exact on
+   affine fields).  phi is the full distance, outside extension included.
+   The analytic gradient of a hash-encoded network jumps at every cell face
+   of its finest levels (cells of ~0.1 mm); the stencil averages over a few
+   of them. */
+void or_nsdf_normal(const or_nsdf* n, const double q[3], int32_t round, double g[3]) {
+    static const double v[4][3] = {{1, -1, -1}, {-1, -1, 1}, {-1, 1, -1}, {1, 1, 1}};
+    const double h = 2.5e-4;
+    g[0] = g[1] = g[2] = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        double p[3] = {q[0] + h * v[k][0], q[1] + h * v[k][1], q[2] + h * v[k][2]};
+        const double phi = or_nsdf_eval(n, p, round, 0);
+        for (int a = 0; a < 3; ++a) g[a] += v[k][a] * phi / (4.0 * h);
+    }
+}
+
 /* Largest change of `out` (mm) that one bfloat16 rounding decided the other
    way can cause: an activation moved by one bfloat16 spacing at its value,
    propagated through |W| (the ReLU pattern held fixed). */
@@ -303,6 +322,11 @@ void or_adam_step(int64_t n, double* theta, double* m, double* v, const double* 
 void or_nsdf_eval_batch(const or_nsdf* n, int64_t B, const double* pts, int32_t round, double* phi, double* grad_raw) {
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t b = 0; b < B; ++b) phi[b] = or_nsdf_eval(n, pts + 3 * b, round, grad_raw ? grad_raw + 3 * b : 0);
+}
+
+void or_nsdf_normal_batch(const or_nsdf* n, int64_t B, const double* pts, int32_t round, double* g) {
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t b = 0; b < B; ++b) or_nsdf_normal(n, pts + 3 * b, round, g + 3 * b);
 }
 
 void or_nsdf_flip_bound_batch(const or_nsdf* n, int64_t B, const double* pts, double* out) {

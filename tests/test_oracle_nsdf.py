@@ -258,3 +258,19 @@ def test_adam_constant_gradient_closed_form():
     th = rng.normal(size=n); th0 = th.copy(); z = np.zeros(n)
     oracle.adam_step(th, np.zeros(n), np.zeros(n), z, lr, 0.9, 0.99, eps, 1)
     assert np.array_equal(th, th0)
+
+
+def test_contact_normal_stencil_is_exact_on_affine_fields():
+    rng = np.random.default_rng(9)
+    lo, hi = np.array([-0.01, -0.02, 0.0]), np.array([0.03, 0.02, 0.05])
+    table = np.zeros((NL, TT, 2), np.float16)
+    n1 = oracle.nsdf_resolution(2) + 1
+    i, j, k = np.meshgrid(np.arange(n1), np.arange(n1), np.arange(n1), indexing="ij")
+    table[2, (i + n1 * (j + n1 * k)).reshape(-1), 0] = (1 + i / 64 + j / 128 + k / 256).reshape(-1)
+    net = _feature_probe_net(lo, hi, table.view(np.uint16), 2, 0)
+    N = oracle.nsdf_resolution(2)
+    q = lo + (hi - lo) * rng.uniform(0.05, 0.95, (30, 3))
+    g = net.normal(q, round=False)
+    # phi (m) = 1e-3 (1 + p_x / 64 + p_y / 128 + p_z / 256), p = N (q - lo) / (hi - lo)
+    expect = 1e-3 * N * np.array([1 / 64, 1 / 128, 1 / 256]) / (hi - lo)
+    assert np.allclose(g, expect[None], rtol=1e-9)
