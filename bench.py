@@ -58,6 +58,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-full-sensors", action="store_true", help="skip the proximity + markers line")
+    ap.add_argument("--neural-objects", type=int, default=64, help="objects given a learned SDF (0: skip the line)")
+    ap.add_argument("--neural-points", type=int, default=2_000_000, help="labelled training points per object")
+    ap.add_argument("--neural-steps", type=int, default=3000, help="Adam steps per object")
+    ap.add_argument("--neural-check-envs", type=int, default=256, help="envs compared against the exact mesh")
     ap.add_argument("--oracle-envs", type=int, default=800, help="env sample of the CPU oracle legs")
     ap.add_argument("--oracle-objects", type=int, default=2, help="objects whose envs form the oracle sample")
     ap.add_argument("--oracle-steps", type=int, default=300, help="steps of the cpu_baseline leg")
@@ -222,6 +226,108 @@ class ClockSampler:
                     reasons.add(name)
         return {"sm_mhz": float(np.median([r[0] for r in load])), "sm_max_mhz": float(max(r[1] for r in rows)),
                 "reasons": sorted(reasons), "samples": len(rows), "power_w_max": pmax}
+
+
+def neural_line(args, wl, objs, d_in, dev, sched, stream, step_inputs, t_plain_ms):
+    """Learned SDFs for the first objects of the workload: trained on the GPU
+    (labels from the exact-mesh query), probed against it, then the same
+    workload timed with the networks answering the contact query (fallback
+    to the grid above 0.2 mm), and a subset of envs compared against the grid
+    and the exact mesh."""
+    import torch
+    import paper_2606_22332_gb300.tg as tg
+    from paper_2606_22332_gb300 import workload as W
+
+    dt = wl.params["dt"]
+    n_obj = min(args.neural_objects, len(wl.objects))
+    t0 = time.time()
+    nets, probe_stats = [], []
+    for k in range(n_obj):
+        o = wl.objects[k]
+        rng = np.random.default_rng(1000 + k)
+        P = torch.from_numpy(W.sdf_sample_points(rng, o.verts, o.faces, o.lo, o.hi, args.neural_points)).to(dev)
+        lab, _ = tg.mesh_sdf(o.verts, o.faces, P, with_grad=False)
+        net = tg.Nsdf(o.lo, o.hi, seed=k)
+        net.train(P, lab * 1e3, steps=args.neural_steps, batch=1 << 14, lr0=1e-2, lr_final=3e-4, seed=k,
+                  record_losses=False)
+        probe = torch.from_numpy(W.sdf_sample_points(np.random.default_rng(5000 + k), o.verts, o.faces, o.lo, o.hi,
+                                                     8192)).to(dev)
+        mx, mean = net.probe(o.verts, o.faces, probe)
+        ex, _ = tg.mesh_sdf(o.verts, o.faces, probe, with_grad=False)
+        p99 = float(torch.quantile((net.eval(probe) - ex).abs() * 1e3, 0.99).item())
+        nets.append(net)
+        probe_stats.append((mx, mean, p99))
+        del P, lab
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    nobjs = [W.ObjectSpec(kind="neural", dims=objs[k].dims, lo=objs[k].lo, hi=objs[k].hi, fp16=objs[k].fp16,
+                          values=objs[k].values, net=nets[k], nsdf_err_mm=probe_stats[k][0], name=objs[k].name)
+             for k in range(n_obj)] + list(objs[n_obj:])
+    sc = tg.Scene(wl.geom(), wl.params)
+    sc.upload_objects(nobjs)
+    used = [k for k in range(n_obj) if sc.object_info(k)[0] == tg.TG_OBJ_NEURAL]
+    sc.set_schedule(**sched)
+    sc.profile(True)
+    sc.graph_capture(step_inputs(0, d_in), pose_dt_per_step=dt)
+    sc.graph_launch(args.warmup)
+    torch.cuda.synchronize()
+    sc.profile_read()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sc.graph_launch(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    pose_ms, step_ms, nsteps = sc.profile_read()
+    sc.graph_release()
+    sc.close()
+    q_used = int(np.isin(wl.obj_id, used).sum()) * (wl.n_active // wl.n_envs)
+
+    # accuracy on envs whose object uses its network: network vs 96^3 grid vs exact mesh, one step
+    acc = None
+    envs = np.flatnonzero(np.isin(wl.obj_id, used))[: args.neural_check_envs]
+    if len(envs):
+        sub = wl.subset(envs)
+        inp = sub.inputs(args.warmup)
+        outs = {}
+        for name, ol in (("neural", nobjs), ("grid", objs),
+                         ("mesh", [W.ObjectSpec(kind="mesh", verts=o.verts, faces=o.faces) for o in wl.objects])):
+            s2 = tg.Scene(sub.geom(), sub.params, taxel_gid0=0, env_gid0=0)
+            s2.upload_objects(ol)
+            s2.step(inp)
+            outs[name] = {"flags": s2.read(tg.CH_STATE_FLAGS) & 1, "depth": s2.read(tg.CH_DEPTH).astype(np.float64),
+                          "f": s2.read(tg.CH_FORCE_TORQUE)[:3].astype(np.float64)}
+            s2.sync()
+            s2.close()
+        act = sub.R > 0
+
+        def cmp(a, b):
+            pen = act & ((outs[a]["depth"] > 0) | (outs[b]["depth"] > 0))
+            dd = np.abs(outs[a]["depth"] - outs[b]["depth"])[pen] * 1e3
+            df = np.linalg.norm(outs[a]["f"] - outs[b]["f"], axis=0)[pen]
+            fb = np.linalg.norm(outs[b]["f"], axis=0)[pen]
+            return {"contact_flag_agreement": float(np.mean(outs[a]["flags"][act] == outs[b]["flags"][act])),
+                    "depth_err_mm": {"mean": float(dd.mean()), "p99": float(np.quantile(dd, 0.99)),
+                                     "max": float(dd.max())},
+                    "force_err_N": {"mean": float(df.mean()), "p99": float(np.quantile(df, 0.99))},
+                    "force_rel_err_median": float(np.median(df / np.maximum(fb, 1e-9)))}
+
+        acc = {"envs": int(len(envs)), "neural_vs_exact_mesh": cmp("neural", "mesh"),
+               "grid_vs_exact_mesh": cmp("grid", "mesh"), "neural_vs_grid": cmp("neural", "grid")}
+    pm = np.array(probe_stats)
+    for net in nets:
+        net.close()
+    return {
+        "objects_with_network": n_obj, "objects_using_network": len(used), "envs_using_network": int(np.isin(wl.obj_id, used).sum()),
+        "training": {"points_per_object": args.neural_points, "steps": args.neural_steps, "batch": 1 << 14,
+                     "seconds_total": round(train_s, 1), "labels": "GPU exact-mesh query"},
+        "probe_err_mm": {"max_over_objects": float(pm[:, 0].max()), "median_of_max": float(np.median(pm[:, 0])),
+                         "mean": float(pm[:, 1].mean()), "p99_median": float(np.median(pm[:, 2]))},
+        "value": wl.n_active * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
+        "vs_plain_grid": round(t_plain_ms / ms, 4), "queries_answered_by_network_per_step": q_used,
+        "step_kernels_ms": round((step_ms) / max(nsteps, 1), 4),
+        "accuracy": acc,
+    }
 
 
 def peaks():
@@ -390,6 +496,9 @@ def run_tg(args):
                 "prox_markers_ms_per_step": (fms - t_max) / args.steps,
                 "taxels_with_proximity_reading": round(prox_share, 4),
                 "gpu_launches": (launches_per_step + 2) * args.steps}
+    neural = None
+    if args.neural_objects > 0 and ws == 1:
+        neural = neural_line(args, wl, objs, d_in, dev, sched, stream, step_inputs, t_max)
     del objs
 
     peak, peak_kind = peaks()
@@ -419,6 +528,7 @@ def run_tg(args):
             "contact_share": round(contact_share, 4), "penetrating_share": round(pen_share, 4),
             "schedule": {"chosen": sched, "autotune": tune["candidates"], "replay": "CUDA graph per step"},
             "full_sensor_set": full,
+            "neural_sdf": neural,
             "setup_s": {"bake": round(bake_s, 2), "total": round(time.time() - t_setup, 1)},
         }
         print(json.dumps(out))

@@ -8,7 +8,8 @@
 // warp per 16 points; the accumulator fragments of layer 1 are re-packed in
 // registers as the A operand of layer 2); ReLU outputs are rounded to
 // bfloat16; the output layer is an FP32 dot product of the rounded h2 with
-// W3.  Near-contact points get d phi / d q in FP32 (one warp per point).
+// W3.  tg_nsdf_eval's gradient is the analytic d phi / d q in FP32 (one warp
+// per point); contact normals in a step use a central-difference stencil.
 //
 // Training (tiles of 128 points, one thread per point for the per-point
 // vectors): FP32 activations on the stored binary16 / bfloat16 parameters,
@@ -231,16 +232,24 @@ __global__ void __launch_bounds__(kInferThreads) nsdf_eval_kernel(const ObjDev o
 }
 
 constexpr int kQueryLinks = 32;
+constexpr float kNormalStep = 2.5e-4f;  // stencil half-width h of the contact normal (object frame, m)
 
 // Per work item whose env holds a learned-SDF object: phi (scaled) of every
-// taxel, and the raw object-frame gradient of the taxels within 1 um of
-// contact (those the step kernel refines).
+// taxel; then, for the taxels within 1 um of contact (those the step kernel
+// refines), the contact normal by the tetrahedral central difference
+// sum_k v_k phi(q + h v_k) / (4 h), v_k = (1,-1,-1), (-1,-1,1), (-1,1,-1),
+// (1,1,1): the analytic gradient of the hash encoding jumps at every cell
+// face of its finest levels, the stencil averages over a few cells.  The
+// stencil points go through the same tensor-core tiles, 32 taxels per tile.
 __global__ void __launch_bounds__(kInferThreads) nsdf_step_query_kernel(const StepArgs a, float* phi_out,
                                                                         float* grad_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmemInfer& S = *reinterpret_cast<SmemInfer*>(smem_raw);
     __shared__ float rec_s[kQueryLinks][kLinkRec];
     __shared__ int start_s[kQueryLinks + 1];
+    __shared__ float cq_pt[kItemCap][3];   // object-frame points of the near-contact taxels
+    __shared__ int64_t cq_g[kItemCap];
+    __shared__ int ncq;
     const Item it = a.items[a.item_order ? a.item_order[blockIdx.x] : blockIdx.x];
     const int e = it.env, L = a.max_links, lb = it.link_begin, nl = it.link_end - it.link_begin, n = it.n_taxels;
     const int oid = min(max(a.obj_id[e], 0), a.n_objects - 1);
@@ -254,9 +263,10 @@ __global__ void __launch_bounds__(kInferThreads) nsdf_step_query_kernel(const St
         const int base = a.lattice[e * L + lb].env_offset;
         start_s[threadIdx.x] = (int)threadIdx.x < nl ? a.lattice[e * L + lb + threadIdx.x].env_offset - base : n;
     }
+    if (threadIdx.x == 0) ncq = 0;
     __syncthreads();
+    // pass 1: phi of every taxel
     for (int base = 0; base < n; base += kRows) {
-        if (threadIdx.x == 0) S.nq = 0;
         if (threadIdx.x < kRows) {
             const int i = base + threadIdx.x;
             float3 q = make_float3(o.nlo[0], o.nlo[1], o.nlo[2]);
@@ -274,6 +284,9 @@ __global__ void __launch_bounds__(kInferThreads) nsdf_step_query_kernel(const St
                 S.gidx[threadIdx.x] = g;
                 S.scale[threadIdx.x] = rec[38];
             }
+            S.q[threadIdx.x][0] = q.x;
+            S.q[threadIdx.x][1] = q.y;
+            S.q[threadIdx.x][2] = q.z;
             set_row(S, o, threadIdx.x, q);
         }
         __syncthreads();
@@ -285,19 +298,52 @@ __global__ void __launch_bounds__(kInferThreads) nsdf_step_query_kernel(const St
                 const float p = S.scale[threadIdx.x] * (1e-3f * S.out[threadIdx.x] + S.ext[threadIdx.x]);
                 phi_out[g] = p;
                 const float R = a.R[g];
-                if (R > 0.0f && p < R + 1e-6f) S.queue[atomicAdd(&S.nq, 1)] = (int16_t)threadIdx.x;
+                if (R > 0.0f && p < R + 1e-6f) {
+                    const int k = atomicAdd(&ncq, 1);
+                    cq_g[k] = g;
+                    cq_pt[k][0] = S.q[threadIdx.x][0];
+                    cq_pt[k][1] = S.q[threadIdx.x][1];
+                    cq_pt[k][2] = S.q[threadIdx.x][2];
+                }
             }
         }
         __syncthreads();
-        const int warp = threadIdx.x >> 5;
-        for (int k = warp; k < S.nq; k += kInferThreads / 32) {
-            const int r = S.queue[k];
-            const float3 gr = row_grad(S, o.ntable, o, r);
-            if ((threadIdx.x & 31) == 0) {
-                const int64_t g = S.gidx[r];
-                grad_out[g] = gr.x;
-                grad_out[T + g] = gr.y;
-                grad_out[2 * T + g] = gr.z;
+    }
+    // pass 2: stencil normals, 4 points per near-contact taxel
+    const int nc = ncq;
+    for (int c0 = 0; c0 < nc; c0 += kRows / 4) {
+        if (threadIdx.x < kRows) {
+            const int t = c0 + (threadIdx.x >> 2), k = threadIdx.x & 3;
+            float3 q = make_float3(o.nlo[0], o.nlo[1], o.nlo[2]);
+            if (t < nc) {
+                const float vx = (k == 0 || k == 3) ? 1.f : -1.f;
+                const float vy = (k >= 2) ? 1.f : -1.f;
+                const float vz = (k == 1 || k == 3) ? 1.f : -1.f;
+                q = make_float3(cq_pt[t][0] + kNormalStep * vx, cq_pt[t][1] + kNormalStep * vy,
+                                cq_pt[t][2] + kNormalStep * vz);
+            }
+            set_row(S, o, threadIdx.x, q);
+        }
+        __syncthreads();
+        infer_tile(S, o.ntable);
+        __syncthreads();
+        if (threadIdx.x < kRows / 4) {
+            const int t = c0 + threadIdx.x;
+            if (t < nc) {
+                float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int r = 4 * threadIdx.x + k;
+                    const float ph = 1e-3f * S.out[r] + S.ext[r];
+                    gx += ((k == 0 || k == 3) ? ph : -ph);
+                    gy += ((k >= 2) ? ph : -ph);
+                    gz += ((k == 1 || k == 3) ? ph : -ph);
+                }
+                const float inv = 1.0f / (4.0f * kNormalStep);
+                const int64_t g = cq_g[t];
+                grad_out[g] = gx * inv;
+                grad_out[T + g] = gy * inv;
+                grad_out[2 * T + g] = gz * inv;
             }
         }
         __syncthreads();

@@ -133,14 +133,18 @@ def test_scene_step_with_a_neural_object_matches_oracle(tg):
     wl = _neural_workload(rng)
     on = oracle_nsdf(wl.objects[0].nsdf_lo, wl.objects[0].nsdf_hi, wl.objects[0].nsdf_table,
                      wl.objects[0].nsdf_weights)
-    # the phi tolerance of this network: four flips at the worst of 20k box points
+    # the phi tolerance of this network: four flips at the worst of 20k box points; the contact
+    # normal (a central difference of four phi values over 4 h, h = 0.25 mm) inherits it
     lo, hi = wl.objects[0].nsdf_lo.astype(np.float64), wl.objects[0].nsdf_hi.astype(np.float64)
-    S = on.flip_bound(lo + (hi - lo) * rng.uniform(0, 1, (20000, 3))).max()
+    box = lo + (hi - lo) * rng.uniform(0, 1, (20000, 3))
+    S = on.flip_bound(box).max()
     d_tol = 4 * S * 1e-3 + 2e-7
-    # normals jump at the hash-grid cell faces: a taxel within FP32 rounding of
-    # a face may take either side's (both are the network's gradient there)
-    tol = {"d_abs": max(d_tol, 1e-5), "band": d_tol, "f_rel": 1e-3, "f_abs": 4 * wl.params["k"] * d_tol + 1e-6,
-           "agg_d": d_tol, "f_outliers": 0.005}
+    g_typ = np.median(np.linalg.norm(on.normal(box[:2000]), axis=1))
+    n_rel = 4 * 4 * S * 1e-3 * np.sqrt(3) / (4 * 2.5e-4) / g_typ
+    # normals jump where the stencil straddles a hash-grid cell face or ReLU kink: a taxel whose
+    # stencil points sit within rounding of one may take either side's value (counted, not failed)
+    tol = {"d_abs": max(d_tol, 1e-5), "band": d_tol, "f_rel": max(1e-3, 2 * n_rel),
+           "f_abs": 4 * wl.params["k"] * d_tol + 1e-6, "agg_d": d_tol, "f_outliers": 0.005}
     sc = tg.Scene.from_workload(wl, sensors=tg.TG_SENSOR_DIST)
     sc.upload_objects(wl.objects)
     assert sc.object_info(0)[0] == tg.TG_OBJ_NEURAL and sc.object_info(1)[0] == tg.TG_OBJ_GRID
@@ -178,3 +182,39 @@ def test_probe_error_decides_the_fallback(tg):
     sc.sync()
     compare_step(g, osc.step(ost, wl.inputs(0)), ost, wl.params, wl, where="fallback")
     sc.close()
+
+
+def test_training_fits_a_mesh_and_beats_the_exact_query(tg):
+    """A network trained on the GPU (labels from the GPU exact-mesh query)
+    reaches the 0.2 mm target against the oracle's exact mesh distance on
+    seeded probe points (half within 5 mm of the surface), while answering
+    far faster than the exact query it replaces; the library's probe agrees
+    with this measurement."""
+    rng = np.random.default_rng(15)
+    V, F = W.hull_mesh(rng, 64, 0.04, min_faces=1500)
+    lo, hi = W.grid_box(V)
+    pts = torch.from_numpy(W.sdf_sample_points(rng, V, F, lo, hi, 500_000)).cuda()
+    lab, _ = tg.mesh_sdf(V, F, pts, with_grad=False)
+    net = tg.Nsdf(lo, hi, seed=3)
+    losses = net.train(pts, lab * 1e3, steps=3000, batch=1 << 14, lr0=1e-2, lr_final=3e-4, seed=1)
+    assert losses[-100:].mean() < 0.1 * losses[:10].mean()
+    probe = W.sdf_sample_points(np.random.default_rng(99), V, F, lo, hi, 8192)
+    exact, _ = oracle.Obj.mesh(V, F).sdf(probe.astype(np.float64))
+    phi = net.eval(torch.from_numpy(probe).cuda()).cpu().numpy().astype(np.float64)
+    err = np.abs(phi - exact) * 1e3
+    near = np.abs(exact) < 5e-3
+    print(f"neural error mm: mean {err.mean():.4f} p99 {np.quantile(err, 0.99):.4f} max {err.max():.4f}; "
+          f"within 5 mm: p99 {np.quantile(err[near], 0.99):.4f} max {err[near].max():.4f}")
+    assert np.quantile(err, 0.99) <= 0.2 and err[near].max() <= 0.3
+    mx, mean = net.probe(V, F, torch.from_numpy(probe).cuda())
+    assert abs(mx - err.max()) <= 2e-3 and abs(mean - err.mean()) <= 1e-3
+    # the gain: the same queries at a fraction of the exact query's cost
+    q = torch.from_numpy(W.sdf_sample_points(rng, V, F, lo, hi, 1 << 20)).cuda()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    net.eval(q); tg.mesh_sdf(V, F, q, with_grad=False); torch.cuda.synchronize()
+    ev[0].record(); net.eval(q); ev[1].record()
+    ev[2].record(); tg.mesh_sdf(V, F, q, with_grad=False); ev[3].record()
+    torch.cuda.synchronize()
+    t_net, t_exact = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+    print(f"1M queries: network {t_net:.3f} ms, exact mesh ({len(F)} faces) {t_exact:.3f} ms")
+    assert t_net * 10 < t_exact
