@@ -1091,7 +1091,8 @@ static void env_markers(const or_scene* S, const or_pads* pads, const or_inputs*
             sub3(q, pC, dq);
             matTvec(RC, dq, qh);
             for (int a = 0; a < 3; ++a) qh[a] /= scale;
-            double phi = scale * or_sdf_object(obj, qh, g);
+            /* a learned SDF's markers read its fallback grid, as its proximity rays do */
+            double phi = scale * (obj->kind == OR_NEURAL ? or_sdf_grid(obj, qh, g) : or_sdf_object(obj, qh, g));
             hs[m] = phi < 0.0 ? -phi : 0.0;
             if (h_out) h_out[((size_t)e * P + p) * M + m] = hs[m];
         }
