@@ -3,7 +3,7 @@
 //
 // From each active probe centre, rays leave along the probe normal and on a
 // cone around it; each ray is sphere-traced through the object's signed
-// distance (step max(phi, 10 um), at most 192 steps).  When a sample falls
+// distance (step max(phi, 10 um), at most 192 samples).  When a sample falls
 // inside, the crossing is bracketed by it and the last outside sample and
 // refined by the Illinois variant of regula falsi, so the reported distance
 // is the first surface crossing along the ray.  The reading is the mean over
@@ -26,55 +26,39 @@ __device__ __forceinline__ float ray_field(const ObjDev& obj, float3 q0, float3 
     return scale * sdf_fast(obj, q0 + d * t, &go);
 }
 
-// first crossing on [ta, tb] with f(ta) > 0 >= f(tb), Illinois regula falsi
-__device__ __forceinline__ float refine_root(const ObjDev& obj, float3 q0, float3 d, float scale, float ta, float fa,
-                                             float tb, float fb) {
-    int side = 0;
-    for (int it = 0; it < 24 && tb - ta > 1e-7f; ++it) {
-        const float tc = (fa * tb - fb * ta) / (fa - fb);
-        const float fc = ray_field(obj, q0, d, tc, scale);
-        if (fc > 0.0f) {
-            ta = tc; fa = fc;
-            if (side == -1) fb *= 0.5f;
-            side = -1;
-        } else {
-            tb = tc; fb = fc;
-            if (side == 1) fa *= 0.5f;
-            side = 1;
-        }
+constexpr int kRefineIters = 24;
+
+// The taxel of item-relative index i: its link (last start <= i).
+__device__ __forceinline__ int link_of(const int* start, int nl, int i) {
+    int lo = 0, hi = nl - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= i) lo = mid;
+        else hi = mid - 1;
     }
-    return tb;
+    return lo;
 }
 
-// distance to the first surface crossing along one ray, or -1 (no hit):
-// march by max(phi, 10 um) until a sample falls inside, then refine between
-// the last outside and the first inside sample.  192 steps reach the end of
-// the range even for rays meeting the surface at 3 degrees (the geometric
-// convergence of sphere tracing at incidence theta shrinks phi by
-// (1 - sin theta) per step).
-__device__ __forceinline__ float trace_ray(const ObjDev& obj, float3 q0, float3 d, float scale, float range) {
-    float t = 0.0f;
-    float f = ray_field(obj, q0, d, 0.0f, scale);
-    if (!(f > 0.0f)) return 0.0f;  // the probe centre is inside
-    for (int it = 0; it < kMaxMarch; ++it) {
-        const float tn = t + fmaxf(f, kMinStep);
-        if (tn > range) {
-            // the last stretch up to the range end
-            const float fe = ray_field(obj, q0, d, range, scale);
-            return fe > 0.0f ? -1.0f : refine_root(obj, q0, d, scale, t, f, range, fe);
-        }
-        const float fn = ray_field(obj, q0, d, tn, scale);
-        if (!(fn > 0.0f)) return refine_root(obj, q0, d, scale, t, f, tn, fn);
-        t = tn;
-        f = fn;
-    }
-    return -1.0f;
-}
-
-__global__ void __launch_bounds__(kProxThreads) prox_kernel(const StepArgs a) {
+// Lanes take rays, not taxels: every lane owns one ray at a time and takes
+// the next ray of the item's pool (a warp-aggregated atomic) when its ray
+// ends, so the warp stays full while rays march for very different numbers
+// of steps.  Marching and the Illinois refinement of the first crossing are
+// one state machine with exactly one field evaluation per iteration, so the
+// lanes of a warp stay converged on it:
+//   march:  t' = min(t + max(f, 10 um), range); f' = f(t'); f' <= 0 -> refine
+//           on [t, t'], else if t' = range -> miss, else continue (at most
+//           192 samples)
+//   refine: t_c = (f_a t_b - f_b t_a) / (f_a - f_b), halving the retained
+//           end's value after two moves on the same side (at most 24
+//           samples, or until t_b - t_a <= 1e-7 m); the crossing is t_b.
+// Per-ray distances go to shared memory; each taxel then sums its rays in
+// ray order (deterministic) and runs the noise chain.
+__global__ void __launch_bounds__(kProxThreads, 4) prox_kernel(const StepArgs a) {
+    extern __shared__ float t_s[];  // [n taxels][rays]: crossing distance or -1
     __shared__ float rec_s[kProxItemLinks][kLinkRec];
     __shared__ int start_s[kProxItemLinks + 1];
     __shared__ ObjDev obj_s;
+    __shared__ unsigned int next_ray;
     const Item it = a.items[a.item_order ? a.item_order[blockIdx.x] : blockIdx.x];
     const int e = it.env, L = a.max_links, lb = it.link_begin, nl = it.link_end - it.link_begin, n = it.n_taxels;
     const ParamsDev& P = a.P;
@@ -88,13 +72,112 @@ __global__ void __launch_bounds__(kProxThreads) prox_kernel(const StepArgs a) {
     if (threadIdx.x == 0) {
         int oid = min(max(a.obj_id[e], 0), a.n_objects - 1);
         obj_s = a.objects[oid];
+        next_ray = 0;
+    }
+    __syncthreads();
+    const int nr = P.prox_rays;
+    const unsigned total = (unsigned)(n * nr);
+    const float range = P.prox_range;
+    const unsigned lane = threadIdx.x & 31u;
+    // one ray per lane
+    int rid = -1, mode = 0, cnt = 0, side = 0;  // mode 0 idle, 1 march, 2 refine
+    bool exhausted = false;
+    float ta = 0.f, fa = 0.f, tb = 0.f, fb = 0.f, scale = 1.f;
+    float3 q0 = f3(0.f, 0.f, 0.f), d = f3(0.f, 0.f, 0.f);
+    for (;;) {
+        // refill idle lanes from the pool
+        const bool want = mode == 0 && !exhausted;
+        const unsigned need = __ballot_sync(0xffffffffu, want);
+        if (need) {
+            const int leader = __ffs(need) - 1;
+            unsigned base = 0;
+            if ((int)lane == leader) base = atomicAdd(&next_ray, (unsigned)__popc(need));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (want) {
+                const unsigned r = base + (unsigned)__popc(need & ((1u << lane) - 1u));
+                if (r >= total) {
+                    exhausted = true;
+                } else {
+                    rid = (int)r;
+                    const int i = rid / nr, k = rid - i * nr;
+                    const int64_t g = it.taxel_begin + i;
+                    const float R = a.R[g];
+                    if (!(R > 0.0f)) {
+                        t_s[rid] = -1.0f;  // filler: no rays
+                    } else {
+                        const float* rec = rec_s[link_of(start_s, nl, i)];
+                        const float x0 = a.x[g], x1 = a.y[g], x2 = a.z[g];
+                        const float3 nn = f3(a.nx[g], a.ny[g], a.nz[g]);
+                        q0 = f3(fmaf(rec[0], x0, fmaf(rec[1], x1, fmaf(rec[2], x2, rec[18]))),
+                                fmaf(rec[3], x0, fmaf(rec[4], x1, fmaf(rec[5], x2, rec[19]))),
+                                fmaf(rec[6], x0, fmaf(rec[7], x1, fmaf(rec[8], x2, rec[20]))));
+                        // the fan in the link frame: n, then the cone around n
+                        float3 dl = nn;
+                        if (k > 0) {
+                            float3 u = cross(nn, f3(0.f, 0.f, 1.f));
+                            if (dot(u, u) < 1e-12f) u = cross(nn, f3(1.f, 0.f, 0.f));
+                            u = normalize_or(u, f3(1.f, 0.f, 0.f));
+                            const float3 v = cross(nn, u);
+                            dl = nn * P.prox_cos + (u * P.prox_az_cos[k] + v * P.prox_az_sin[k]) * P.prox_sin;
+                        }
+                        d = f3(rec[0] * dl.x + rec[1] * dl.y + rec[2] * dl.z, rec[3] * dl.x + rec[4] * dl.y + rec[5] * dl.z,
+                               rec[6] * dl.x + rec[7] * dl.y + rec[8] * dl.z);
+                        scale = rec[38];
+                        ta = 0.0f;
+                        fa = -1.0f;  // the first sample is t = 0 (mode 1 with cnt = -1)
+                        cnt = -1;
+                        mode = 1;
+                    }
+                }
+            }
+        }
+        if (!__any_sync(0xffffffffu, mode != 0 || !exhausted)) break;
+        // the one field evaluation of this iteration
+        float tq = 0.0f;
+        bool eval = false;
+        if (mode == 1) {
+            tq = cnt < 0 ? 0.0f : fminf(ta + fmaxf(fa, kMinStep), range);
+            eval = true;
+        } else if (mode == 2) {
+            if (cnt >= kRefineIters || !(tb - ta > 1e-7f)) {
+                t_s[rid] = tb;
+                mode = 0;
+            } else {
+                tq = (fa * tb - fb * ta) / (fa - fb);
+                eval = true;
+            }
+        }
+        float fq = 0.0f;
+        if (eval) fq = ray_field(obj_s, q0, d, tq, scale);
+        if (mode == 1) {
+            if (cnt < 0) {                   // the probe centre
+                if (!(fq > 0.0f)) { t_s[rid] = 0.0f; mode = 0; }
+                else { fa = fq; cnt = 0; }
+            } else if (!(fq > 0.0f)) {       // crossed: refine on [ta, tq]
+                tb = tq; fb = fq; mode = 2; cnt = 0; side = 0;
+            } else if (tq >= range || ++cnt >= kMaxMarch) {
+                t_s[rid] = -1.0f;            // no crossing within the range
+                mode = 0;
+            } else {
+                ta = tq; fa = fq;
+            }
+        } else if (mode == 2 && eval) {
+            if (fq > 0.0f) {
+                ta = tq; fa = fq;
+                if (side == -1) fb *= 0.5f;
+                side = -1;
+            } else {
+                tb = tq; fb = fq;
+                if (side == 1) fa *= 0.5f;
+                side = 1;
+            }
+            ++cnt;
+        }
     }
     __syncthreads();
     const uint32_t ep = a.episode[e];
     const int64_t T = a.n_taxels;
-    int l = 0;
     for (int i = threadIdx.x; i < n; i += kProxThreads) {
-        while (i >= start_s[l + 1]) ++l;
         const int64_t g = it.taxel_begin + i;
         const float R = a.R[g];
         if (!(R > 0.0f)) {
@@ -102,29 +185,12 @@ __global__ void __launch_bounds__(kProxThreads) prox_kernel(const StepArgs a) {
             a.prox_noisy[g] = 0.0f;
             continue;
         }
-        const float* rec = rec_s[l];
-        const float x0 = a.x[g], x1 = a.y[g], x2 = a.z[g];
-        const float3 nl_ = f3(a.nx[g], a.ny[g], a.nz[g]);
-        const float3 q0 = f3(fmaf(rec[0], x0, fmaf(rec[1], x1, fmaf(rec[2], x2, rec[18]))),
-                             fmaf(rec[3], x0, fmaf(rec[4], x1, fmaf(rec[5], x2, rec[19]))),
-                             fmaf(rec[6], x0, fmaf(rec[7], x1, fmaf(rec[8], x2, rec[20]))));
-        // ray fan in the link frame: n, then the cone around n
-        float3 u = cross(nl_, f3(0.f, 0.f, 1.f));
-        if (dot(u, u) < 1e-12f) u = cross(nl_, f3(1.f, 0.f, 0.f));
-        u = normalize_or(u, f3(1.f, 0.f, 0.f));
-        const float3 v = cross(nl_, u);
-        const float scale = rec[38];
         float reading = 0.0f;
-        for (int k = 0; k < P.prox_rays; ++k) {
-            float3 dl = nl_;
-            if (k > 0) dl = nl_ * P.prox_cos + (u * P.prox_az_cos[k] + v * P.prox_az_sin[k]) * P.prox_sin;
-            const float3 dobj = f3(rec[0] * dl.x + rec[1] * dl.y + rec[2] * dl.z,
-                                   rec[3] * dl.x + rec[4] * dl.y + rec[5] * dl.z,
-                                   rec[6] * dl.x + rec[7] * dl.y + rec[8] * dl.z);
-            const float t = trace_ray(obj_s, q0, dobj, scale, P.prox_range);
-            if (t >= 0.0f) reading += 1.0f - t / P.prox_range;
+        for (int k = 0; k < nr; ++k) {
+            const float t = t_s[i * nr + k];
+            if (t >= 0.0f) reading += 1.0f - t / range;
         }
-        reading /= (float)P.prox_rays;
+        reading /= (float)nr;
         a.prox_clean[g] = reading;
         // noise chain of the proximity group
         const NoiseDev& G = P.prox;
@@ -152,8 +218,15 @@ __global__ void __launch_bounds__(kProxThreads) prox_kernel(const StepArgs a) {
 }
 
 cudaError_t launch_prox(const StepArgs& a, int n_items, cudaStream_t s) {
-    if (n_items == 0) return cudaSuccess;
-    prox_kernel<<<n_items, kProxThreads, 0, s>>>(a);
+    if (n_items == 0 || a.P.prox_rays < 1) return cudaSuccess;
+    const size_t smem = sizeof(float) * (size_t)kItemCap * (size_t)a.P.prox_rays;  // <= 64 KB (16 rays)
+    static size_t configured = 0;
+    if (smem > configured) {
+        const cudaError_t err = cudaFuncSetAttribute(prox_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        configured = smem;
+    }
+    prox_kernel<<<n_items, kProxThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
