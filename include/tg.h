@@ -194,7 +194,9 @@ tg_status tg_nsdf_set_params(tg_nsdf* net, const uint16_t* table, const uint16_t
 tg_status tg_nsdf_get_params(tg_nsdf* net, uint16_t* table, uint16_t* weights);
 /* phi (m) at n object-frame points (device [n][3]) into device phi [n];
    grad (device [n][3] or NULL): the raw gradient d phi / d q of the network
-   (FP32, taken at the clamped point; not normalised).  Asynchronous. */
+   (FP32, taken at the clamped point; not normalised).  Asynchronous; a
+   tensor-core wait that timed out (no result written for the rest of that
+   CTA's points) is reported as TG_ERR_TIMEOUT by the next tg_nsdf_probe. */
 tg_status tg_nsdf_eval(tg_nsdf* net, const float* points, int64_t n, float* phi, float* grad, tg_stream stream);
 /* Mean over the n points (device [n][3]) of |out - label_mm| and its
    gradients, the training forward and backward: FP32 activations on the

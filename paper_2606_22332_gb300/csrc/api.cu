@@ -1125,8 +1125,11 @@ tg_status tg_sync(tg_scene* s, tg_stream stream) {
     CK(s, cudaGetLastError());
     unsigned h[4] = {0, 0, 0, 0};
     CK(s, cudaMemcpy(h, s->err, sizeof(h), cudaMemcpyDeviceToHost));
-    if (h[0]) {
+    if (h[0] || h[1]) {
         CK(s, cudaMemset(s->err, 0, sizeof(h)));
+        if (h[1])
+            return fail(s, TG_ERR_TIMEOUT, "a tensor-core MMA of the learned-SDF query did not complete in time (" +
+                                               std::to_string(h[1]) + " work items skipped)");
         return fail(s, TG_ERR_NUMERIC, "non-finite signed distances were seen (" + std::to_string(h[0]) + " taxel queries)");
     }
     return TG_OK;

@@ -132,7 +132,7 @@ struct StepArgs {
     float* ft_noisy;                  // [6][T]
     float* link_out;                  // [E*L][kLinkOut]
     int32_t* link_count;              // [E*L][2]
-    unsigned int* err;                // [0] non-finite count
+    unsigned int* err;                // [0] non-finite count, [1] learned-SDF MMA wait timeouts
     float* prox_clean;                // [T] (proximity on)
     float* prox_noisy;                // [T]
     // learned-SDF objects: phi (scaled) of every taxel of a neural item and
@@ -216,7 +216,9 @@ cudaError_t nsdf_alloc(NsdfNet* n);
 void nsdf_free(NsdfNet* n);
 cudaError_t nsdf_init(NsdfNet* n, uint64_t seed, cudaStream_t s);
 cudaError_t nsdf_sync_masters(NsdfNet* n, cudaStream_t s);   // masters <- inference copies, Adam state zeroed
-cudaError_t launch_nsdf_eval(const ObjDev& o, const float* pts, int64_t n, float* phi, float* grad, cudaStream_t s);
+// err: device word counting CTAs that stopped on an MMA wait timeout
+cudaError_t launch_nsdf_eval(const ObjDev& o, const float* pts, int64_t n, float* phi, float* grad, unsigned* err,
+                             cudaStream_t s);
 // training forward/backward on points[idx[b]] (idx null: b), gradients accumulated into g_w [6208] and
 // g_table [16][2^16][2]; per-CTA partial sums of |out - label| into loss_part [ceil(n/128)]
 cudaError_t launch_nsdf_train_step(const ObjDev& o, const float* pts, const float* labels, const uint32_t* idx,

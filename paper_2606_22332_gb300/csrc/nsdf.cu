@@ -28,17 +28,27 @@ namespace {
 
 constexpr int kRows = 128;
 constexpr int kInferThreads = 256;
-constexpr int kEncStride = 40;   // bfloat16 per row of the encoding tile (32 + 8 padding)
 constexpr int kHidStride = 72;   // bfloat16 per row of a hidden tile (64 + 8 padding)
 constexpr uint32_t kTagNsdfBatch = 48, kTagNsdfInit = 49;
 
-struct SmemInfer {
-    __nv_bfloat16 w1[kNsdfHidden * kEncStride];  // [o][k]
-    __nv_bfloat16 w2[kNsdfHidden * kHidStride];  // [o][i]
+// Operand tiles in the tensor cores' no-swizzle K-major layout: core
+// matrices of 8 rows x 16 bytes (8 bfloat16 along K); element (r, k) of an
+// operand with R rows at byte ((k / 8) (R / 8) + r / 8) 128 + (r % 8) 16 +
+// (k % 8) 2.  Core matrices adjacent along K are (R / 8) 128 bytes apart
+// (the descriptor's leading byte offset), adjacent 8-row groups 128 bytes
+// (its stride byte offset).
+__host__ __device__ constexpr uint32_t core_off(int r, int k, int R) {
+    return (uint32_t)(((k >> 3) * (R >> 3) + (r >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+struct __align__(128) SmemInfer {
+    unsigned char a1[kRows * kNsdfIn * 2];          // encoding tile, 128 x 32 (8 KB)
+    unsigned char a2[kRows * kNsdfHidden * 2];      // h1 tile, 128 x 64 (16 KB)
+    unsigned char w1[kNsdfHidden * kNsdfIn * 2];    // W1 as the B operand, 64 x 32 (4 KB)
+    unsigned char w2[kNsdfHidden * kNsdfHidden * 2];  // W2, 64 x 64 (8 KB)
+    __nv_bfloat16 h2[kRows * kHidStride];           // rounded h2, row-major (analytic gradient)
     float w3[kNsdfHidden];
-    __nv_bfloat16 enc[kRows * kEncStride];
-    __nv_bfloat16 h1[kRows * kHidStride];
-    __nv_bfloat16 h2[kRows * kHidStride];
+    float outp[2][kRows];                           // the two column halves of W3 . h2
     float u[kRows][3];
     float ext[kRows];
     float out[kRows];
@@ -47,101 +57,190 @@ struct SmemInfer {
     float scale[kRows];
     int16_t queue[kRows];
     int nq;
+    uint64_t mbar;         // MMA completion barrier
+    uint32_t tmem;         // TMEM base: columns [0, 64) layer 1, [64, 128) layer 2
+    uint32_t phase;        // completions so far (parity of the next wait)
 };
 
-__device__ __forceinline__ uint32_t ld_u32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+__device__ __forceinline__ float bf16_at(const unsigned char* tile, int r, int k, int R) {
+    return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(tile + core_off(r, k, R)));
+}
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
 __device__ void load_weights(SmemInfer& S, const uint16_t* w) {
-    const __nv_bfloat16* wb = reinterpret_cast<const __nv_bfloat16*>(w);
     for (int j = threadIdx.x; j < kNsdfHidden * kNsdfIn; j += blockDim.x)
-        S.w1[(j / kNsdfIn) * kEncStride + j % kNsdfIn] = wb[j];
+        *reinterpret_cast<uint16_t*>(S.w1 + core_off(j / kNsdfIn, j % kNsdfIn, kNsdfHidden)) = w[j];
     for (int j = threadIdx.x; j < kNsdfHidden * kNsdfHidden; j += blockDim.x)
-        S.w2[(j / kNsdfHidden) * kHidStride + j % kNsdfHidden] = wb[kNsdfHidden * kNsdfIn + j];
+        *reinterpret_cast<uint16_t*>(S.w2 + core_off(j / kNsdfHidden, j % kNsdfHidden, kNsdfHidden)) =
+            w[kNsdfHidden * kNsdfIn + j];
     for (int j = threadIdx.x; j < kNsdfHidden; j += blockDim.x)
         S.w3[j] = bf16f(w[kNsdfHidden * kNsdfIn + kNsdfHidden * kNsdfHidden + j]);
 }
 
-// Forward of the 128 rows whose u[] is set: S.out[r] (mm); h1, h2 kept.
-__device__ void infer_tile(SmemInfer& S, const uint32_t* table) {
+// ---- tcgen05 plumbing (inline PTX) -------------------------------------------
+// shared-memory operand descriptor: start, leading byte offset (K-adjacent
+// core matrices), stride byte offset (row groups), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t lbo, uint32_t sbo) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    return (uint64_t)((a >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor, kind::f16: FP32 accumulator, bfloat16 A and B, both
+// K-major, N = 64, M = 128
+constexpr uint32_t kIdescM128N64 = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(kIdescM128N64), "r"(accumulate));
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+        (uint32_t)__cvta_generic_to_shared(mbar)));
+}
+
+// bounded wait for the barrier phase with the given parity; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(mbar);
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 22) && !done; ++it)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity));
+    return done != 0;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
+}
+
+// TMEM (128 columns) and the MMA barrier for this CTA; warp 0 allocates.
+__device__ void tc_setup(SmemInfer& S) {
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&S.mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        S.phase = 0;
+    }
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+            (uint32_t)__cvta_generic_to_shared(&S.tmem)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+}
+
+__device__ void tc_teardown(SmemInfer& S) {
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(S.tmem));
+}
+
+// Forward of the 128 rows whose u[] is set: S.out[r] (mm); h1 (a2) and h2 kept.
+// Both hidden layers on the tensor cores (M = 128 rows, N = 64, K = 32 / 64 in
+// steps of 16), accumulators in TMEM; 8 warps read them back, warp w the lanes
+// 32 (w % 4) .. + 31 and the column half w / 4.  Returns false (the same in
+// every thread) if an MMA did not complete within the wait limit.
+__device__ bool infer_tile(SmemInfer& S, const uint32_t* table) {
     const int tid = threadIdx.x;
-    {   // encoding: two threads per row, 8 levels each
+    const uint32_t ph = S.phase;  // MMA completions so far: this tile waits for ph and ph + 1
+    {   // encoding: two threads per row, 8 levels each, two 16-byte stores each
         const int r = tid >> 1, half = tid & 1;
         float enc[16];
         nsdf_encode_levels<8>(table, S.u[r], 8 * half, enc);
-#pragma unroll
-        for (int j = 0; j < 16; j += 2)
-            *reinterpret_cast<uint32_t*>(&S.enc[r * kEncStride + 16 * half + j]) = pack_bf16(enc[j], enc[j + 1]);
+        uint4 v0, v1;
+        v0.x = pack_bf16(enc[0], enc[1]);   v0.y = pack_bf16(enc[2], enc[3]);
+        v0.z = pack_bf16(enc[4], enc[5]);   v0.w = pack_bf16(enc[6], enc[7]);
+        v1.x = pack_bf16(enc[8], enc[9]);   v1.y = pack_bf16(enc[10], enc[11]);
+        v1.z = pack_bf16(enc[12], enc[13]); v1.w = pack_bf16(enc[14], enc[15]);
+        *reinterpret_cast<uint4*>(S.a1 + core_off(r, 16 * half, kRows)) = v0;
+        *reinterpret_cast<uint4*>(S.a1 + core_off(r, 16 * half + 8, kRows)) = v1;
     }
+    proxy_fence();
+    tc_fence_before();
     __syncthreads();
-    const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-    const int r0 = 16 * warp;
-    float acc[8][4];
-    uint32_t af[4][4];
-    // layer 1: [16 x 32] x [32 x 64]
+    if (tid == 0) {
+        tc_fence_after();
+        for (int ks = 0; ks < kNsdfIn / 16; ++ks)
+            tc_mma(S.tmem, smem_desc(S.a1 + ks * 2 * (kRows / 8) * 128, (kRows / 8) * 128, 128),
+                   smem_desc(S.w1 + ks * 2 * (kNsdfHidden / 8) * 128, (kNsdfHidden / 8) * 128, 128), ks > 0);
+        tc_commit(&S.mbar);
+    }
+    const int warp = tid >> 5, lane = tid & 31;
+    const int r = 32 * (warp & 3) + lane, c0 = 32 * (warp >> 2);
+    const uint32_t lane_addr = S.tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    bool ok = mbar_wait(&S.mbar, ph & 1u);
+    if (__syncthreads_or(!ok)) return false;
+    tc_fence_after();
+    {   // layer-1 epilogue: ReLU, bfloat16, into the h1 operand tile
+        float z[32];
+        tmem_ld32(lane_addr + c0, z);
 #pragma unroll
-    for (int n = 0; n < 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-#pragma unroll
-    for (int ks = 0; ks < 2; ++ks) {
-        const __nv_bfloat16* A = S.enc + (r0 + g) * kEncStride + 16 * ks + 2 * t;
-        const uint32_t a0 = ld_u32(A), a1 = ld_u32(A + 8 * kEncStride), a2 = ld_u32(A + 8),
-                       a3 = ld_u32(A + 8 * kEncStride + 8);
-#pragma unroll
-        for (int n = 0; n < 8; ++n) {
-            const __nv_bfloat16* B = S.w1 + (8 * n + g) * kEncStride + 16 * ks + 2 * t;
-            mma_bf16(acc[n], a0, a1, a2, a3, ld_u32(B), ld_u32(B + 8));
+        for (int j = 0; j < 4; ++j) {
+            uint4 v;
+            v.x = pack_bf16(fmaxf(z[8 * j], 0.f), fmaxf(z[8 * j + 1], 0.f));
+            v.y = pack_bf16(fmaxf(z[8 * j + 2], 0.f), fmaxf(z[8 * j + 3], 0.f));
+            v.z = pack_bf16(fmaxf(z[8 * j + 4], 0.f), fmaxf(z[8 * j + 5], 0.f));
+            v.w = pack_bf16(fmaxf(z[8 * j + 6], 0.f), fmaxf(z[8 * j + 7], 0.f));
+            *reinterpret_cast<uint4*>(S.a2 + core_off(r, c0 + 8 * j, kRows)) = v;
         }
     }
-    // ReLU, bfloat16, re-pack as the A operand of layer 2, keep h1
-#pragma unroll
-    for (int n = 0; n < 8; ++n) {
-        const uint32_t lo = pack_bf16(fmaxf(acc[n][0], 0.f), fmaxf(acc[n][1], 0.f));
-        const uint32_t hi = pack_bf16(fmaxf(acc[n][2], 0.f), fmaxf(acc[n][3], 0.f));
-        af[n >> 1][(n & 1) ? 2 : 0] = lo;
-        af[n >> 1][(n & 1) ? 3 : 1] = hi;
-        *reinterpret_cast<uint32_t*>(&S.h1[(r0 + g) * kHidStride + 8 * n + 2 * t]) = lo;
-        *reinterpret_cast<uint32_t*>(&S.h1[(r0 + g + 8) * kHidStride + 8 * n + 2 * t]) = hi;
+    proxy_fence();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+        tc_fence_after();
+        for (int ks = 0; ks < kNsdfHidden / 16; ++ks)
+            tc_mma(S.tmem + 64, smem_desc(S.a2 + ks * 2 * (kRows / 8) * 128, (kRows / 8) * 128, 128),
+                   smem_desc(S.w2 + ks * 2 * (kNsdfHidden / 8) * 128, (kNsdfHidden / 8) * 128, 128), ks > 0);
+        tc_commit(&S.mbar);
     }
-    // layer 2: [16 x 64] x [64 x 64]
-#pragma unroll
-    for (int n = 0; n < 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-#pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
-#pragma unroll
-        for (int n = 0; n < 8; ++n) {
-            const __nv_bfloat16* B = S.w2 + (8 * n + g) * kHidStride + 16 * ks + 2 * t;
-            mma_bf16(acc[n], af[ks][0], af[ks][1], af[ks][2], af[ks][3], ld_u32(B), ld_u32(B + 8));
-        }
-    }
-#pragma unroll
-    for (int n = 0; n < 8; ++n) {
-        *reinterpret_cast<uint32_t*>(&S.h2[(r0 + g) * kHidStride + 8 * n + 2 * t]) =
-            pack_bf16(fmaxf(acc[n][0], 0.f), fmaxf(acc[n][1], 0.f));
-        *reinterpret_cast<uint32_t*>(&S.h2[(r0 + g + 8) * kHidStride + 8 * n + 2 * t]) =
-            pack_bf16(fmaxf(acc[n][2], 0.f), fmaxf(acc[n][3], 0.f));
-    }
-    __syncwarp();
-    // output layer: FP32 dot of the rounded h2 with W3 (one lane per row, two rows per lane pair)
-    if (lane < 16) {
-        const int r = r0 + lane;
+    ok = mbar_wait(&S.mbar, (ph + 1u) & 1u);
+    if (__syncthreads_or(!ok)) return false;
+    tc_fence_after();
+    {   // layer-2 epilogue: ReLU, bfloat16, the half dot product with W3; keep h2
+        float z[32];
+        tmem_ld32(lane_addr + 64 + c0, z);
         float s = 0.f;
-#pragma unroll 8
-        for (int i = 0; i < kNsdfHidden; ++i) s = fmaf(__bfloat162float(S.h2[r * kHidStride + i]), S.w3[i], s);
-        S.out[r] = s;
+#pragma unroll
+        for (int j = 0; j < 32; j += 2) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(z[j], 0.f), fmaxf(z[j + 1], 0.f));
+            *reinterpret_cast<__nv_bfloat162*>(&S.h2[r * kHidStride + c0 + j]) = h;
+            s = fmaf(__low2float(h), S.w3[c0 + j], s);
+            s = fmaf(__high2float(h), S.w3[c0 + j + 1], s);
+        }
+        S.outp[warp >> 2][r] = s;
     }
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) S.phase = ph + 2u;  // read again only after the caller's next barrier
+    if (tid < kRows) S.out[tid] = S.outp[0][tid] + S.outp[1][tid];
+    return true;
 }
 
 // d phi / d q (object frame, raw) of row r, by one warp.
@@ -154,16 +253,16 @@ __device__ float3 row_grad(const SmemInfer& S, const uint32_t* table, const ObjD
 #pragma unroll 8
     for (int oo = 0; oo < kNsdfHidden; ++oo) {
         const float v = __shfl_sync(0xffffffffu, oo < 32 ? gz2a : gz2b, oo & 31);
-        gh1a = fmaf(v, __bfloat162float(S.w2[oo * kHidStride + lane]), gh1a);
-        gh1b = fmaf(v, __bfloat162float(S.w2[oo * kHidStride + lane + 32]), gh1b);
+        gh1a = fmaf(v, bf16_at(S.w2, oo, lane, kNsdfHidden), gh1a);
+        gh1b = fmaf(v, bf16_at(S.w2, oo, lane + 32, kNsdfHidden), gh1b);
     }
-    const float gz1a = __bfloat162float(S.h1[r * kHidStride + lane]) > 0.f ? gh1a : 0.f;
-    const float gz1b = __bfloat162float(S.h1[r * kHidStride + lane + 32]) > 0.f ? gh1b : 0.f;
+    const float gz1a = bf16_at(S.a2, r, lane, kRows) > 0.f ? gh1a : 0.f;
+    const float gz1b = bf16_at(S.a2, r, lane + 32, kRows) > 0.f ? gh1b : 0.f;
     float genc = 0.f;  // d out / d enc[lane]
 #pragma unroll 8
     for (int i = 0; i < kNsdfHidden; ++i) {
         const float v = __shfl_sync(0xffffffffu, i < 32 ? gz1a : gz1b, i & 31);
-        genc = fmaf(v, __bfloat162float(S.w1[i * kEncStride + lane]), genc);
+        genc = fmaf(v, bf16_at(S.w1, i, lane, kNsdfHidden), genc);
     }
     const float ge0 = __shfl_sync(0xffffffffu, genc, (2 * lane) & 31);
     const float ge1 = __shfl_sync(0xffffffffu, genc, (2 * lane + 1) & 31);
@@ -198,10 +297,11 @@ __device__ __forceinline__ void set_row(SmemInfer& S, const ObjDev& o, int r, fl
 }
 
 __global__ void __launch_bounds__(kInferThreads) nsdf_eval_kernel(const ObjDev o, const float* pts, int64_t n,
-                                                                  float* phi, float* grad) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+                                                                  float* phi, float* grad, unsigned* err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     SmemInfer& S = *reinterpret_cast<SmemInfer*>(smem_raw);
     load_weights(S, o.nweights);
+    tc_setup(S);
     const int64_t n_tiles = (n + kRows - 1) / kRows;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int64_t base = tile * kRows;
@@ -213,7 +313,10 @@ __global__ void __launch_bounds__(kInferThreads) nsdf_eval_kernel(const ObjDev o
             set_row(S, o, threadIdx.x, q);
         }
         __syncthreads();
-        infer_tile(S, o.ntable);
+        if (!infer_tile(S, o.ntable)) {
+            if (threadIdx.x == 0) atomicAdd(err, 1u);
+            break;
+        }
         __syncthreads();
         if (threadIdx.x < kRows && base + threadIdx.x < n) phi[base + threadIdx.x] = 1e-3f * S.out[threadIdx.x] + S.ext[threadIdx.x];
         if (grad) {
@@ -229,6 +332,7 @@ __global__ void __launch_bounds__(kInferThreads) nsdf_eval_kernel(const ObjDev o
         }
         __syncthreads();
     }
+    tc_teardown(S);
 }
 
 constexpr int kQueryLinks = 32;
@@ -264,7 +368,8 @@ __global__ void __launch_bounds__(kInferThreads) nsdf_step_query_kernel(const St
         start_s[threadIdx.x] = (int)threadIdx.x < nl ? a.lattice[e * L + lb + threadIdx.x].env_offset - base : n;
     }
     if (threadIdx.x == 0) ncq = 0;
-    __syncthreads();
+    tc_setup(S);  // (its barrier also publishes the loads above)
+    bool failed = false;
     // pass 1: phi of every taxel
     for (int base = 0; base < n; base += kRows) {
         if (threadIdx.x < kRows) {
@@ -290,7 +395,10 @@ __global__ void __launch_bounds__(kInferThreads) nsdf_step_query_kernel(const St
             set_row(S, o, threadIdx.x, q);
         }
         __syncthreads();
-        infer_tile(S, o.ntable);
+        if (!infer_tile(S, o.ntable)) {
+            failed = true;
+            break;
+        }
         __syncthreads();
         if (threadIdx.x < kRows) {
             const int64_t g = S.gidx[threadIdx.x];
@@ -310,7 +418,7 @@ __global__ void __launch_bounds__(kInferThreads) nsdf_step_query_kernel(const St
         __syncthreads();
     }
     // pass 2: stencil normals, 4 points per near-contact taxel
-    const int nc = ncq;
+    const int nc = failed ? 0 : ncq;
     for (int c0 = 0; c0 < nc; c0 += kRows / 4) {
         if (threadIdx.x < kRows) {
             const int t = c0 + (threadIdx.x >> 2), k = threadIdx.x & 3;
@@ -325,7 +433,10 @@ __global__ void __launch_bounds__(kInferThreads) nsdf_step_query_kernel(const St
             set_row(S, o, threadIdx.x, q);
         }
         __syncthreads();
-        infer_tile(S, o.ntable);
+        if (!infer_tile(S, o.ntable)) {
+            failed = true;
+            break;
+        }
         __syncthreads();
         if (threadIdx.x < kRows / 4) {
             const int t = c0 + threadIdx.x;
@@ -348,6 +459,8 @@ __global__ void __launch_bounds__(kInferThreads) nsdf_step_query_kernel(const St
         }
         __syncthreads();
     }
+    if (failed && threadIdx.x == 0) atomicAdd(a.err + 1, 1u);
+    tc_teardown(S);
 }
 
 // ---------------------------------------------------------------- training
@@ -647,13 +760,14 @@ cudaError_t nsdf_sync_masters(NsdfNet* n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_nsdf_eval(const ObjDev& o, const float* pts, int64_t n, float* phi, float* grad, cudaStream_t s) {
+cudaError_t launch_nsdf_eval(const ObjDev& o, const float* pts, int64_t n, float* phi, float* grad, unsigned* err,
+                             cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     cudaError_t e = configure();
     if (e != cudaSuccess) return e;
     const int64_t tiles = (n + kRows - 1) / kRows;
     const unsigned grid = (unsigned)(tiles < 152 * 3 ? tiles : 152 * 3);
-    nsdf_eval_kernel<<<grid, kInferThreads, sizeof(SmemInfer), s>>>(o, pts, n, phi, grad);
+    nsdf_eval_kernel<<<grid, kInferThreads, sizeof(SmemInfer), s>>>(o, pts, n, phi, grad, err);
     return cudaGetLastError();
 }
 

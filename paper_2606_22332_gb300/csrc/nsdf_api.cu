@@ -35,6 +35,7 @@ struct tg_nsdf {
     float* loss_part = nullptr; // [ctas]
     uint32_t* idx = nullptr;    // [batch]
     int64_t cap = 0;            // points the scratch holds
+    unsigned* err = nullptr;    // inference CTAs stopped on an MMA wait timeout
 };
 
 namespace tg {
@@ -136,6 +137,8 @@ tg_status tg_nsdf_create(const float lo[3], const float hi[3], uint64_t seed, tg
     cudaError_t e = nsdf_alloc(&h->net);
     if (e == cudaSuccess) e = cudaMalloc(&h->g_w, sizeof(float) * kWeights);
     if (e == cudaSuccess) e = cudaMalloc(&h->g_table, sizeof(float) * 2 * (size_t)kEntries);
+    if (e == cudaSuccess) e = cudaMalloc(&h->err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(h->err, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = nsdf_init(&h->net, seed, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -155,6 +158,7 @@ void tg_nsdf_destroy(tg_nsdf* h) {
     cudaFree(h->g_part);
     cudaFree(h->loss_part);
     cudaFree(h->idx);
+    cudaFree(h->err);
     delete h;
 }
 
@@ -179,7 +183,7 @@ tg_status tg_nsdf_eval(tg_nsdf* h, const float* points, int64_t n, float* phi, f
     if (!h || n < 0 || (n > 0 && (!points || !phi))) return nfail(TG_ERR_INVALID_ARG, "net, points and phi are required");
     if (n > 0 && (!is_dev(points) || !is_dev(phi) || (grad && !is_dev(grad))))
         return nfail(TG_ERR_INVALID_ARG, "points, phi and grad must be device buffers");
-    NCK(launch_nsdf_eval(nsdf_objdev(h->net), points, n, phi, grad, (cudaStream_t)stream));
+    NCK(launch_nsdf_eval(nsdf_objdev(h->net), points, n, phi, grad, h->err, (cudaStream_t)stream));
     return TG_OK;
 }
 
@@ -250,11 +254,17 @@ tg_status tg_nsdf_probe(tg_nsdf* h, const float* verts, int32_t n_verts, const i
     tg_status st = tg_mesh_sdf(verts, n_verts, faces, n_faces, points, n, phi_m, nullptr, stream);
     if (st == TG_OK) st = tg_nsdf_eval(h, points, n, phi_n, nullptr, stream);
     double out[2] = {0.0, 0.0};
+    unsigned timeouts = 0;
     if (st == TG_OK) {
         probe_err_kernel<<<1, 256, 0, s>>>(phi_n, phi_m, n, stats);
         cudaError_t e = cudaMemcpyAsync(out, stats, sizeof(out), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&timeouts, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = ncuda(e, "probe");
+        else if (timeouts) {
+            cudaMemset(h->err, 0, sizeof(unsigned));
+            st = nfail(TG_ERR_TIMEOUT, "a tensor-core MMA of the network's evaluation did not complete in time");
+        }
     }
     cudaFreeAsync(phi_n, s);
     cudaFreeAsync(phi_m, s);
