@@ -178,3 +178,17 @@ def test_mesh_sdf_points_match_oracle(tg):
     assert (np.abs(phi.cpu().numpy() - ophi) <= 6e-8 * np.abs(ophi) + 1e-12).all()
     far = np.abs(ophi) > 1e-6
     assert np.abs(grad.cpu().numpy()[far] - og[far]).max() < 1e-4
+
+
+def test_maximum_sizes(tg):
+    """A link of tg_max_link_taxels() taxels (one whole work item), an env of
+    33 links (split by the 32-link item limit), one-taxel links and a
+    one-taxel env."""
+    rng = np.random.default_rng(21)
+    assert tg.lib().tg_max_link_taxels() == 1024
+    objs = bake_objects_oracle(W.config1_objects(rng, 2, n_grid=24, fp16=True, faces=(1500, 2500)))
+    lat = [[(32, 32, 1024)], [(2, 3, 6)] * 33, [(32, 32, 1024), (1, 1, 1), (4, 5, 20)], [(1, 1, 1)]]
+    wl = W._assemble("maxsize", rng, objs, rng.integers(0, 2, len(lat)), lat, W.default_params(7), steps=3,
+                     max_links=34, arc=W.PAD_ARC, press_frac=(1.0, 1.0), press_depth=(0.5e-3, 2.5e-3))
+    stats = run_both(tg, wl, steps=3)
+    print("maxsize", stats[-1])
