@@ -69,10 +69,9 @@ def parse():
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2606_22332_gb300.dist import rank_env
+
+    return rank_env()
 
 
 def make_workload(args, rank=0):
@@ -377,7 +376,10 @@ def run_tg(args):
         objs.append(W.ObjectSpec(kind="grid", dims=o.dims, lo=o.lo, hi=o.hi, fp16=o.fp16, values=vals, name=o.name))
     torch.cuda.synchronize()
     bake_s = time.time() - t_setup
-    scene = tg.Scene(wl.geom(), wl.params, taxel_gid0=rank * T, env_gid0=rank * E)
+    from paper_2606_22332_gb300.dist import max_over_ranks, shard_ids
+
+    gid0, egid0 = shard_ids(rank, E, T)
+    scene = tg.Scene(wl.geom(), wl.params, taxel_gid0=gid0, env_gid0=egid0)
     scene.upload_objects(objs)
     d_in = {k: torch.as_tensor(getattr(wl, k)).to(dev) for k in ("link_pose", "link_vel", "obj_pose", "obj_vel", "obj_id")}
     stream = torch.cuda.current_stream()
@@ -421,11 +423,7 @@ def run_tg(args):
     scene.sync()
     scene.graph_release()
     scene.profile(False)
-    t_max = ms
-    if pg:
-        tt = torch.tensor([ms], device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(ms, dev)
     n_q = wl.n_active * ws
     value = n_q * args.steps / (t_max / 1e3)
 
@@ -452,11 +450,7 @@ def run_tg(args):
             scene.read(tg.CH_LINK_COUNT, out=out_c)
         e1.record(stream)
         torch.cuda.synchronize()
-        ems = e0.elapsed_time(e1)
-        if pg:
-            tt = torch.tensor([ems], device=dev)
-            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-            ems = float(tt.item())
+        ems = max_over_ranks(e0.elapsed_time(e1), dev)
         e2e = {"value": n_q * k2 / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h),
                "note": "time-0 poses/velocities copied from pinned host memory every step (the C-ABI stages them); "
@@ -468,8 +462,8 @@ def run_tg(args):
     if not args.no_full_sensors:
         wlf = W.add_pads(wl)
         pf = dict(wl.params, prox_rays=8)
-        sc2 = tg.Scene(wlf.geom(), pf, sensors=tg.TG_SENSOR_PROX | tg.TG_SENSOR_MARKERS, taxel_gid0=rank * T,
-                       env_gid0=rank * E, pads=wlf.pads)
+        sc2 = tg.Scene(wlf.geom(), pf, sensors=tg.TG_SENSOR_PROX | tg.TG_SENSOR_MARKERS, taxel_gid0=gid0,
+                       env_gid0=egid0, pads=wlf.pads)
         sc2.upload_objects(objs)
         sc2.set_schedule(**sched)
         sc2.graph_capture(step_inputs(0, d_in), pose_dt_per_step=dt)
@@ -482,11 +476,7 @@ def run_tg(args):
         sc2.graph_launch(args.steps)
         f1.record(stream)
         torch.cuda.synchronize()
-        fms = f0.elapsed_time(f1)
-        if pg:
-            tt = torch.tensor([fms], device=dev)
-            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-            fms = float(tt.item())
+        fms = max_over_ranks(f0.elapsed_time(f1), dev)
         prox_share = float((sc2.buffer(tg.CH_PROX) > 0).sum().item()) / max(wl.n_active, 1)
         sc2.graph_release()
         sc2.close()
