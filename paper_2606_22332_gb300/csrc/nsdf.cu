@@ -28,7 +28,6 @@ namespace {
 
 constexpr int kRows = 128;
 constexpr int kInferThreads = 256;
-constexpr int kHidStride = 72;   // bfloat16 per row of a hidden tile (64 + 8 padding)
 constexpr uint32_t kTagNsdfBatch = 48, kTagNsdfInit = 49;
 
 // Operand tiles in the tensor cores' no-swizzle K-major layout: core
@@ -46,7 +45,7 @@ struct __align__(128) SmemInfer {
     unsigned char a2[kRows * kNsdfHidden * 2];      // h1 tile, 128 x 64 (16 KB)
     unsigned char w1[kNsdfHidden * kNsdfIn * 2];    // W1 as the B operand, 64 x 32 (4 KB)
     unsigned char w2[kNsdfHidden * kNsdfHidden * 2];  // W2, 64 x 64 (8 KB)
-    __nv_bfloat16 h2[kRows * kHidStride];           // rounded h2, row-major (analytic gradient)
+    uint32_t h2pos[2][kRows];                       // h2 > 0 per unit (column halves), for the analytic gradient
     float w3[kNsdfHidden];
     float outp[2][kRows];                           // the two column halves of W3 . h2
     float u[kRows][3];
@@ -60,7 +59,13 @@ struct __align__(128) SmemInfer {
     uint64_t mbar;         // MMA completion barrier
     uint32_t tmem;         // TMEM base: columns [0, 64) layer 1, [64, 128) layer 2
     uint32_t phase;        // completions so far (parity of the next wait)
+    // sized to ~61 KB: 3 CTAs per SM (384 of the 512 TMEM columns) with the
+    // shared-memory carveout leaving ~60 KB of L1 for the table gathers; a
+    // sweep on GB300 (1M queries) gave 0.92 ms at 4 CTAs / 49 KB, 0.48 ms here,
+    // 0.90 ms at 3 CTAs / 73 KB (carveout 228 KB, L1 28 KB), 0.60 ms at 2 CTAs
+    unsigned char pad_l1[16384];
 };
+static_assert(sizeof(SmemInfer) * 4 > 228 * 1024, "at most 3 CTAs per SM (3 x 128 TMEM columns)");
 
 __device__ __forceinline__ float bf16_at(const unsigned char* tile, int r, int k, int R) {
     return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(tile + core_off(r, k, R)));
@@ -227,14 +232,18 @@ __device__ bool infer_tile(SmemInfer& S, const uint32_t* table) {
         float z[32];
         tmem_ld32(lane_addr + 64 + c0, z);
         float s = 0.f;
+        uint32_t pos = 0;
 #pragma unroll
         for (int j = 0; j < 32; j += 2) {
             const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(z[j], 0.f), fmaxf(z[j + 1], 0.f));
-            *reinterpret_cast<__nv_bfloat162*>(&S.h2[r * kHidStride + c0 + j]) = h;
-            s = fmaf(__low2float(h), S.w3[c0 + j], s);
-            s = fmaf(__high2float(h), S.w3[c0 + j + 1], s);
+            const float lo = __low2float(h), hi = __high2float(h);
+            pos |= (lo > 0.f ? 1u : 0u) << j;
+            pos |= (hi > 0.f ? 1u : 0u) << (j + 1);
+            s = fmaf(lo, S.w3[c0 + j], s);
+            s = fmaf(hi, S.w3[c0 + j + 1], s);
         }
         S.outp[warp >> 2][r] = s;
+        S.h2pos[warp >> 2][r] = pos;
     }
     tc_fence_before();
     __syncthreads();
@@ -247,8 +256,8 @@ __device__ bool infer_tile(SmemInfer& S, const uint32_t* table) {
 __device__ float3 row_grad(const SmemInfer& S, const uint32_t* table, const ObjDev& o, int r) {
     const int lane = threadIdx.x & 31;
     // g_z2 = [h2 > 0] W3 for units lane, lane + 32
-    const float gz2a = __bfloat162float(S.h2[r * kHidStride + lane]) > 0.f ? S.w3[lane] : 0.f;
-    const float gz2b = __bfloat162float(S.h2[r * kHidStride + lane + 32]) > 0.f ? S.w3[lane + 32] : 0.f;
+    const float gz2a = ((S.h2pos[0][r] >> lane) & 1u) ? S.w3[lane] : 0.f;
+    const float gz2b = ((S.h2pos[1][r] >> lane) & 1u) ? S.w3[lane + 32] : 0.f;
     float gh1a = 0.f, gh1b = 0.f;  // units lane, lane + 32
 #pragma unroll 8
     for (int oo = 0; oo < kNsdfHidden; ++oo) {
