@@ -800,6 +800,10 @@ static double base_noise(const or_noise_group* g, double z, double white_n, doub
     return y;
 }
 
+/* A learned-SDF object's network answers where its fallback grid puts the
+   probe within this distance (m) of contact (phi_grid <= R + band). */
+#define OR_NEURAL_BAND 1e-3
+
 /* ======================================================================== */
 /* One step of the whole sensor pipeline for every env of the (sub)scene.   */
 /* ======================================================================== */
@@ -861,7 +865,15 @@ static void env_step(const or_scene* S, const or_inputs* in, or_state* st, or_ou
             sub3(q, pC, dq);
             matTvec(RC, dq, qh);
             for (int a = 0; a < 3; ++a) qh[a] /= scale;
-            double phi = scale * or_sdf_object(obj, qh, go);
+            double phi;
+            if (obj->kind == OR_NEURAL) {
+                /* a learned SDF answers within 1 mm of contact as its
+                   fallback grid sees it; farther out the grid answers */
+                phi = scale * or_sdf_grid(obj, qh, go);
+                if (!(phi > R + OR_NEURAL_BAND)) phi = scale * or_sdf_object(obj, qh, go);
+            } else {
+                phi = scale * or_sdf_object(obj, qh, go);
+            }
             matvec(RC, go, m);          /* world normal */
             matTvec(RL, m, mbar);       /* link-frame normal */
             /* Eq. 2 */

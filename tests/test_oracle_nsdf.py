@@ -274,3 +274,32 @@ def test_contact_normal_stencil_is_exact_on_affine_fields():
     # phi (m) = 1e-3 (1 + p_x / 64 + p_y / 128 + p_z / 256), p = N (q - lo) / (hi - lo)
     expect = 1e-3 * N * np.array([1 / 64, 1 / 128, 1 / 256]) / (hi - lo)
     assert np.allclose(g, expect[None], rtol=1e-9)
+
+
+def test_scene_uses_the_network_only_within_1mm_of_contact():
+    """A learned-SDF object: grid phi = z (a plane, exact for trilinear
+    interpolation), network with zero weights (phi_net = 0).  Probes whose
+    grid distance is beyond R + 1 mm read the grid, the others the network."""
+    from paper_2606_22332_gb300 import workload as W
+    from _scenes import oracle_scene, pad_workload, quiet_params
+
+    lo = np.array([-0.02, -0.02, -0.005], np.float32)
+    hi = np.array([0.02, 0.02, 0.02], np.float32)
+    dims = (9, 9, 26)
+    zs = np.linspace(float(lo[2]), float(hi[2]), dims[2])
+    grid = np.broadcast_to(zs[:, None, None], (dims[2], dims[1], dims[0])).astype(np.float32).copy()
+    obj = W.ObjectSpec(kind="neural", dims=dims, lo=lo, hi=hi, fp16=False, values=grid, nsdf_lo=lo, nsdf_hi=hi,
+                       nsdf_table=np.zeros((NL, TT, 2), np.uint16), nsdf_weights=np.zeros(6208, np.uint16),
+                       nsdf_err_mm=0.0)
+    heights_over_R = np.array([[5e-3, 2e-3, 1.2e-3, 0.8e-3, 0.3e-3, -0.5e-3]])   # probe height minus R
+    wl = pad_workload(-heights_over_R, 1, 6, params=quiet_params(), obj=obj)
+    osc = oracle_scene(wl)
+    st = osc.new_state(); osc.reset(st, 0)
+    o = osc.step(st, wl.inputs(0))
+    R = 1e-3
+    far = heights_over_R[0] > 1e-3
+    h = W.f32(wl.z).astype(np.float64) + 0.01                  # probe height above the plane
+    assert np.allclose(o["dist"][far], h[far] - float(np.float32(R)), atol=1e-12)
+    assert np.allclose(o["dist"][~far], -float(np.float32(R)), atol=1e-12)   # phi_net = 0
+    assert np.allclose(o["depth_clean"][~far], float(np.float32(R)), atol=1e-12)
+    assert np.all(o["depth_clean"][far] == 0)
