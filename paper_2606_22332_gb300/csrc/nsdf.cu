@@ -19,6 +19,7 @@
 #include <cstdint>
 #include <cuda_bf16.h>
 
+#include "geom.cuh"
 #include "nsdf.cuh"
 #include "rng.cuh"
 
@@ -346,23 +347,40 @@ __global__ void __launch_bounds__(kInferThreads) nsdf_eval_kernel(const ObjDev o
 
 constexpr int kQueryLinks = 32;
 constexpr float kNormalStep = 2.5e-4f;  // stencil half-width h of the contact normal (object frame, m)
+constexpr float kNeuralBand = 1e-3f;    // the network answers where phi_grid <= R + this (m)
+
+// The object-frame point and scale of taxel i of the item (link records in smem).
+__device__ __forceinline__ float3 taxel_point(const StepArgs& a, const float (*rec_s)[kLinkRec], const int* start_s,
+                                              int64_t g, int i, float* scale) {
+    int l = 0;
+    while (i >= start_s[l + 1]) ++l;
+    const float* rec = rec_s[l];
+    const float x0 = a.x[g], x1 = a.y[g], x2 = a.z[g];
+    *scale = rec[38];
+    return make_float3(fmaf(rec[0], x0, fmaf(rec[1], x1, fmaf(rec[2], x2, rec[18]))),
+                       fmaf(rec[3], x0, fmaf(rec[4], x1, fmaf(rec[5], x2, rec[19]))),
+                       fmaf(rec[6], x0, fmaf(rec[7], x1, fmaf(rec[8], x2, rec[20]))));
+}
 
 // Per work item whose env holds a learned-SDF object: phi (scaled) of every
-// taxel; then, for the taxels within 1 um of contact (those the step kernel
-// refines), the contact normal by the tetrahedral central difference
-// sum_k v_k phi(q + h v_k) / (4 h), v_k = (1,-1,-1), (-1,-1,1), (-1,1,-1),
-// (1,1,1): the analytic gradient of the hash encoding jumps at every cell
-// face of its finest levels, the stencil averages over a few cells.  The
-// stencil points go through the same tensor-core tiles, 32 taxels per tile.
+// taxel -- the fallback grid's where it puts the probe more than 1 mm beyond
+// contact (phi_grid > R + 1 mm), the network's elsewhere -- and, for the
+// taxels within 1 um of contact (those the step kernel refines), the contact
+// normal by the tetrahedral central difference sum_k v_k phi(q + h v_k) / (4 h),
+// v_k = (1,-1,-1), (-1,-1,1), (-1,1,-1), (1,1,1): the analytic gradient of
+// the hash encoding jumps at every cell face of its finest levels, the
+// stencil averages over a few cells.  Network points go through the
+// tensor-core tiles (the near-field taxels, then 32 stencil taxels per tile).
 __global__ void __launch_bounds__(kInferThreads) nsdf_step_query_kernel(const StepArgs a, float* phi_out,
                                                                         float* grad_out) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     SmemInfer& S = *reinterpret_cast<SmemInfer*>(smem_raw);
     __shared__ float rec_s[kQueryLinks][kLinkRec];
     __shared__ int start_s[kQueryLinks + 1];
     __shared__ float cq_pt[kItemCap][3];   // object-frame points of the near-contact taxels
     __shared__ int64_t cq_g[kItemCap];
-    __shared__ int ncq;
+    __shared__ int16_t near_i[kItemCap];   // taxels the network answers
+    __shared__ int ncq, nnear;
     const Item it = a.items[a.item_order ? a.item_order[blockIdx.x] : blockIdx.x];
     const int e = it.env, L = a.max_links, lb = it.link_begin, nl = it.link_end - it.link_begin, n = it.n_taxels;
     const int oid = min(max(a.obj_id[e], 0), a.n_objects - 1);
@@ -376,27 +394,39 @@ __global__ void __launch_bounds__(kInferThreads) nsdf_step_query_kernel(const St
         const int base = a.lattice[e * L + lb].env_offset;
         start_s[threadIdx.x] = (int)threadIdx.x < nl ? a.lattice[e * L + lb + threadIdx.x].env_offset - base : n;
     }
-    if (threadIdx.x == 0) ncq = 0;
+    if (threadIdx.x == 0) {
+        ncq = 0;
+        nnear = 0;
+    }
     tc_setup(S);  // (its barrier also publishes the loads above)
+    // pass 1a: the fallback grid for every taxel; near-field taxels are listed
+    for (int i = threadIdx.x; i < n; i += kInferThreads) {
+        const int64_t g = it.taxel_begin + i;
+        float scale;
+        const float3 q = taxel_point(a, rec_s, start_s, g, i, &scale);
+        float3 go;
+        const float pg = scale * grid_fast(o, q, &go);
+        const float R = a.R[g];
+        if (R > 0.0f && !(pg > R + kNeuralBand)) near_i[atomicAdd(&nnear, 1)] = (int16_t)i;
+        else phi_out[g] = pg;
+    }
+    __syncthreads();
     bool failed = false;
-    // pass 1: phi of every taxel
-    for (int base = 0; base < n; base += kRows) {
+    // pass 1b: the network for the listed taxels
+    const int nn = nnear;
+    for (int base = 0; base < nn; base += kRows) {
         if (threadIdx.x < kRows) {
-            const int i = base + threadIdx.x;
+            const int k = base + threadIdx.x;
             float3 q = make_float3(o.nlo[0], o.nlo[1], o.nlo[2]);
             S.gidx[threadIdx.x] = -1;
             S.scale[threadIdx.x] = 0.f;
-            if (i < n) {
-                int l = 0;
-                while (i >= start_s[l + 1]) ++l;
-                const float* rec = rec_s[l];
+            if (k < nn) {
+                const int i = near_i[k];
                 const int64_t g = it.taxel_begin + i;
-                const float x0 = a.x[g], x1 = a.y[g], x2 = a.z[g];
-                q = make_float3(fmaf(rec[0], x0, fmaf(rec[1], x1, fmaf(rec[2], x2, rec[18]))),
-                                fmaf(rec[3], x0, fmaf(rec[4], x1, fmaf(rec[5], x2, rec[19]))),
-                                fmaf(rec[6], x0, fmaf(rec[7], x1, fmaf(rec[8], x2, rec[20]))));
+                float scale;
+                q = taxel_point(a, rec_s, start_s, g, i, &scale);
                 S.gidx[threadIdx.x] = g;
-                S.scale[threadIdx.x] = rec[38];
+                S.scale[threadIdx.x] = scale;
             }
             S.q[threadIdx.x][0] = q.x;
             S.q[threadIdx.x][1] = q.y;
