@@ -35,6 +35,14 @@ def tg():
     return tg
 
 
+def _device_inputs(wl, step):
+    inp = wl.inputs(step)
+    out = dict(pose_dt=inp["pose_dt"], step=inp["step"])
+    for k in ("link_pose", "link_vel", "obj_pose", "obj_vel", "obj_id"):
+        out[k] = torch.from_numpy(np.ascontiguousarray(inp[k])).cuda()
+    return out
+
+
 def _points(rng, n_in, n_out):
     a = LO + (HI - LO) * rng.uniform(0, 1, (n_in, 3))
     b = LO + (HI - LO) * rng.uniform(-0.5, 1.5, (n_out, 3))
@@ -218,3 +226,51 @@ def test_training_fits_a_mesh_and_beats_the_exact_query(tg):
     t_net, t_exact = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
     print(f"1M queries: network {t_net:.3f} ms, exact mesh ({len(F)} faces) {t_exact:.3f} ms")
     assert t_net * 10 < t_exact
+
+
+def test_mixed_workload_neural_grid_fallback_dr_graph(tg):
+    """The mixed workload's combination at a size the oracle steps in full:
+    uneven envs (200-1000 taxels, 10-20 links), grid objects, learned-SDF
+    objects (one of them over its error budget, so its grid answers),
+    per-step domain randomisation of mu, k and scale, steps replayed from a
+    CUDA graph."""
+    rng = np.random.default_rng(16)
+    objs = bake_objects_oracle(W.config1_objects(rng, 6, n_grid=24, fp16=True, faces=(1500, 2500)))
+    nets = []
+    for k, err in ((0, 0.0), (2, 0.1), (4, 0.0), (5, 0.5)):
+        o = objs[k]
+        table, w = W.random_nsdf_params(rng, table_scale=1.0, out_scale=2.0)
+        objs[k] = W.ObjectSpec(kind="neural", dims=o.dims, lo=o.lo, hi=o.hi, fp16=o.fp16, values=o.values,
+                               verts=o.verts, faces=o.faces, nsdf_lo=o.lo, nsdf_hi=o.hi, nsdf_table=table,
+                               nsdf_weights=w, nsdf_err_mm=err)
+        if err * 1.2 <= 0.2:
+            nets.append(oracle_nsdf(o.lo, o.hi, table, w))
+    lat = W.uneven_lattices(rng, 18)
+    params = dict(W.default_params(44), dr={"mu": (0.4, 1.2), "k": (5e3, 2e4), "scale": (0.8, 1.2)})
+    wl = W._assemble("mixed", rng, objs, rng.integers(0, len(objs), len(lat)), lat, params, steps=4, max_links=20,
+                     arc=W.PAD_ARC, press_frac=(1.0, 1.0), press_depth=(0.5e-3, 2.5e-3))
+    S = 0.0
+    for net in nets:
+        lo, hi = np.array(net.s.lo[:]), np.array(net.s.hi[:])
+        S = max(S, net.flip_bound(lo + (hi - lo) * rng.uniform(0, 1, (5000, 3))).max())
+    d_tol = 4 * S * 1e-3 * 1.2 + 2e-7
+    tol = {"d_abs": max(d_tol, 1e-5), "band": d_tol, "f_rel": 5e-2, "f_abs": 4 * 2e4 * d_tol + 1e-6, "agg_d": d_tol,
+           "f_outliers": 0.005}
+    sc = tg.Scene.from_workload(wl)
+    sc.upload_objects(wl.objects)
+    kinds = [sc.object_info(k)[0] for k in range(len(objs))]
+    assert kinds == [tg.TG_OBJ_NEURAL, tg.TG_OBJ_GRID, tg.TG_OBJ_NEURAL, tg.TG_OBJ_GRID, tg.TG_OBJ_NEURAL,
+                     tg.TG_OBJ_GRID]
+    sc.graph_capture(_device_inputs(wl, 0), pose_dt_per_step=wl.params["dt"])
+    osc = oracle_scene(wl)
+    ost = osc.new_state(); osc.reset(ost, 0)
+    skip = np.zeros(wl.n_taxels, bool)
+    for s in range(4):
+        sc.graph_launch(1)
+        g = gpu_outputs(sc)
+        sc.sync()
+        o = osc.step(ost, wl.inputs(s))
+        st = compare_step(g, o, ost, wl.params, wl, where=f"mixed replay {s}", tol=tol, exclude=skip)
+        skip |= st["outliers"]
+    sc.graph_release()
+    sc.close()
