@@ -152,56 +152,67 @@ __global__ void __launch_bounds__(kPoseThreads) pose_kernel(const PoseArgs a) {
         o[26] = scale;
     }
     __syncthreads();
-    if (idx >= n) return;
-    const int e = idx / L;
-    if (!a.lattice[idx].present) return;
-    const float* lp = a.link_pose + (size_t)idx * 7;
-    const float* lv = a.link_vel + (size_t)idx * 6;
-    const float* ov = a.obj_vel + (size_t)e * 6;
-    const float* o = s_obj[e - e0];
-    const float mu = o[24], k = o[25], scale = o[26];
-    dmat RC;
+    // each thread's record is staged in shared memory; the block's records
+    // (one contiguous range) are then written with coalesced 16-byte stores
+    __shared__ __align__(16) float s_rec[kPoseThreads * kLinkRec];
+    float* rec = s_rec + threadIdx.x * kLinkRec;
+    const bool live = idx < n && a.lattice[idx].present;
+    if (!live) {
+        for (int f = 0; f < kLinkRec; ++f) rec[f] = 0.0f;  // absent links: a zero record
+    } else {
+        const int e = idx / L;
+        const float* lp = a.link_pose + (size_t)idx * 7;
+        const float* lv = a.link_vel + (size_t)idx * 6;
+        const float* ov = a.obj_vel + (size_t)e * 6;
+        const float* o = s_obj[e - e0];
+        const float mu = o[24], k = o[25], scale = o[26];
+        dmat RC;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) RC.m[i] = df{o[2 * i], o[2 * i + 1]};
-    float lq[4] = {lp[3], lp[4], lp[5], lp[6]};
-    float lw[3] = {lv[3], lv[4], lv[5]}, ow[3] = {ov[3], ov[4], ov[5]};
-    dmat RL = advance_rotation(lq, lw, tau);
-    df dp[3];
+        for (int i = 0; i < 9; ++i) RC.m[i] = df{o[2 * i], o[2 * i + 1]};
+        float lq[4] = {lp[3], lp[4], lp[5], lp[6]};
+        float lw[3] = {lv[3], lv[4], lv[5]}, ow[3] = {ov[3], ov[4], ov[5]};
+        dmat RL = advance_rotation(lq, lw, tau);
+        df dp[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const df pL = df_add(df_from(lp[i]), df_mul_f(tau, lv[i]));
-        dp[i] = df_sub(pL, df{o[18 + 2 * i], o[19 + 2 * i]});  // p_L - p_C
+        for (int i = 0; i < 3; ++i) {
+            const df pL = df_add(df_from(lp[i]), df_mul_f(tau, lv[i]));
+            dp[i] = df_sub(pL, df{o[18 + 2 * i], o[19 + 2 * i]});  // p_L - p_C
+        }
+        dmat M = dmatTmul(RC, RL);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            df m = df_div_f(M.m[i], scale);
+            rec[i] = m.hi;
+            rec[9 + i] = m.lo;
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            df t = df_add(df_add(df_mul(RC.m[i], dp[0]), df_mul(RC.m[3 + i], dp[1])), df_mul(RC.m[6 + i], dp[2]));
+            t = df_div_f(t, scale);
+            rec[18 + i] = t.hi;
+            rec[21 + i] = t.lo;
+        }
+        // velocity terms in the link frame (FP32 is enough here)
+        float dv[3] = {ov[0] - lv[0], ov[1] - lv[1], ov[2] - lv[2]};
+        float nd[3] = {-dp[0].hi - dp[0].lo, -dp[1].hi - dp[1].lo, -dp[2].hi - dp[2].lo};  // p_C - p_L
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            float r0 = RL.m[i].hi, r1 = RL.m[3 + i].hi, r2 = RL.m[6 + i].hi;  // column i of R_L
+            rec[24 + i] = r0 * dv[0] + r1 * dv[1] + r2 * dv[2];
+            rec[27 + i] = r0 * ow[0] + r1 * ow[1] + r2 * ow[2];
+            rec[30 + i] = r0 * lw[0] + r1 * lw[1] + r2 * lw[2];
+            rec[33 + i] = r0 * nd[0] + r1 * nd[1] + r2 * nd[2];
+        }
+        rec[36] = k;
+        rec[37] = mu;
+        rec[38] = scale;
+        rec[39] = 0.0f;
     }
-    dmat M = dmatTmul(RC, RL);
-    float* rec = a.link_rec + (size_t)idx * kLinkRec;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        df m = df_div_f(M.m[i], scale);
-        rec[i] = m.hi;
-        rec[9 + i] = m.lo;
-    }
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        df t = df_add(df_add(df_mul(RC.m[i], dp[0]), df_mul(RC.m[3 + i], dp[1])), df_mul(RC.m[6 + i], dp[2]));
-        t = df_div_f(t, scale);
-        rec[18 + i] = t.hi;
-        rec[21 + i] = t.lo;
-    }
-    // velocity terms in the link frame (FP32 is enough here)
-    float dv[3] = {ov[0] - lv[0], ov[1] - lv[1], ov[2] - lv[2]};
-    float nd[3] = {-dp[0].hi - dp[0].lo, -dp[1].hi - dp[1].lo, -dp[2].hi - dp[2].lo};  // p_C - p_L
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        float r0 = RL.m[i].hi, r1 = RL.m[3 + i].hi, r2 = RL.m[6 + i].hi;  // column i of R_L
-        rec[24 + i] = r0 * dv[0] + r1 * dv[1] + r2 * dv[2];
-        rec[27 + i] = r0 * ow[0] + r1 * ow[1] + r2 * ow[2];
-        rec[30 + i] = r0 * lw[0] + r1 * lw[1] + r2 * lw[2];
-        rec[33 + i] = r0 * nd[0] + r1 * nd[1] + r2 * nd[2];
-    }
-    rec[36] = k;
-    rec[37] = mu;
-    rec[38] = scale;
-    rec[39] = 0.0f;
+    __syncthreads();
+    const int n_block = min(kPoseThreads, n - base);  // records of this block
+    float4* dst = reinterpret_cast<float4*>(a.link_rec + (size_t)base * kLinkRec);
+    const float4* src = reinterpret_cast<const float4*>(s_rec);
+    for (int v = threadIdx.x; v < n_block * kLinkRec / 4; v += kPoseThreads) dst[v] = src[v];
 }
 
 cudaError_t launch_pose(const PoseArgs& a, cudaStream_t s) {
