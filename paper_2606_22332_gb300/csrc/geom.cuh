@@ -1,10 +1,11 @@
 // geom.cuh -- signed distance queries in the object frame (Appendix A, Eq. 2:
 // depth from phi_g, contact normal from grad phi_g).
 //
-// Two evaluations per object kind:
-//   sdf_fast    FP32 phi and unit gradient; enough for every taxel whose
-//               probe sphere is clear of the surface (depth = 0 exactly) and
-//               for the surface-distance output.
+// Evaluations per object kind:
+//   sdf_fast    FP32 phi and unit gradient (proximity rays, markers)
+//   sdf_phi_fast  the same FP32 phi without the gradient; enough for every
+//               taxel whose probe sphere is clear of the surface (depth = 0
+//               exactly) and for the surface-distance output.
 //   sdf_refine  phi as a compensated float pair from a compensated query
 //               point, gradient in FP32 at the compensated cell / feature.
 //               Used only for taxels within a guard band of contact, so the
@@ -115,6 +116,31 @@ __device__ __forceinline__ float grid_fast(const ObjDev& o, float3 q, float3* g)
     float3 gr = trilinear_grad(v, fx, fy, fz);
     gr = f3(gr.x * o.inv_h_hi[0], gr.y * o.inv_h_hi[1], gr.z * o.inv_h_hi[2]);
     *g = normalize_or(gr, normalize_or(q, f3(0.f, 0.f, 1.f)));
+    float3 out = f3(q.x - c[0], q.y - c[1], q.z - c[2]);
+    return phi + sqrtf(dot(out, out));
+}
+
+// phi alone, for the pass that only decides whether a taxel is near contact:
+// the same FP32 interpolation as grid_fast without the gradient
+__device__ __forceinline__ float grid_phi_fast(const ObjDev& o, float3 q) {
+    float c[3] = {fminf(fmaxf(q.x, o.lo[0]), o.hi[0]), fminf(fmaxf(q.y, o.lo[1]), o.hi[1]),
+                  fminf(fmaxf(q.z, o.lo[2]), o.hi[2])};
+    int i[3];
+    float f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float u = (c[a] - o.lo[a]) * o.inv_h_hi[a];
+        int ii = (int)floorf(u);
+        ii = min(max(ii, 0), o.dims[a] - 2);
+        i[a] = ii;
+        f[a] = u - (float)ii;
+    }
+    Corners v = grid_corners(o, i[0], i[1], i[2]);
+    float fx = f[0], fy = f[1], fz = f[2];
+    float c00 = v.v000 + fx * (v.v100 - v.v000), c10 = v.v010 + fx * (v.v110 - v.v010);
+    float c01 = v.v001 + fx * (v.v101 - v.v001), c11 = v.v011 + fx * (v.v111 - v.v011);
+    float c0 = c00 + fy * (c10 - c00), c1 = c01 + fy * (c11 - c01);
+    float phi = c0 + fz * (c1 - c0);
     float3 out = f3(q.x - c[0], q.y - c[1], q.z - c[2]);
     return phi + sqrtf(dot(out, out));
 }
@@ -371,6 +397,20 @@ __device__ __forceinline__ float sdf_fast(const ObjDev& o, float3 q, float3* g) 
     case TG_OBJ_GRID:
     case TG_OBJ_NEURAL: return grid_fast(o, q, g);  // a learned SDF's fallback grid (proximity, markers)
     default: *g = f3(0.f, 0.f, 1.f); return __int_as_float(0x7fc00000);
+    }
+}
+
+// FP32 phi without the gradient (equal to sdf_fast's phi)
+__device__ __forceinline__ float sdf_phi_fast(const ObjDev& o, float3 q) {
+    float3 g;
+    switch (o.kind) {
+    case TG_OBJ_SPHERE: return sqrtf(dot(q, q)) - o.radius;
+    case TG_OBJ_BOX: return box_fast(o, q, &g);
+    case TG_OBJ_PLANE: return q.z;
+    case TG_OBJ_MESH: return mesh_fast(o, q, &g);
+    case TG_OBJ_GRID:
+    case TG_OBJ_NEURAL: return grid_phi_fast(o, q);
+    default: return __int_as_float(0x7fc00000);
     }
 }
 

@@ -12,6 +12,8 @@
 //            finish here (depth 0, no contact, no force), the others queue
 //   phase A2 queued near-contact taxels, compacted onto whole warps:
 //            compensated query point and SDF, depth, Schmitt bit, force/torque
+//            (position, radius and flags come from shared memory, where A1
+//            left them)
 //   phase N  per taxel: noise state (gain, hysteresis, depth base noise, dead)
 //            with all state loads independent of the geometry; agg_force terms
 //   phase C1 per (link, quantity): clean sums, agg_force, contact counts
@@ -33,7 +35,7 @@ struct SmemStep {
     int start[kItemMaxLinks + 1];       // first taxel of each link, relative to the item
     int rows[kItemMaxLinks], cols[kItemMaxLinks], wrap[kItemMaxLinks];
     ObjDev obj;
-    float hx[6][kItemCap];              // force/torque after gain + hysteresis
+    float hx[6][kItemCap];              // force/torque after gain + hysteresis (A1-A2: near-taxel inputs)
     float fc[6][kItemCap];              // clean force/torque, later noisy force/torque
     float ag[6][kItemCap];              // clean depth, then agg_force terms d n: clean xyz, noisy xyz
     uint8_t bits[kItemCap];             // BIT_* flags
@@ -117,6 +119,13 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
             if (R > 0.0f && !isfinite(phi)) atomicAdd(a.err, 1u);
             if (R > 0.0f && phi < R + 1e-6f) {
                 S.queue[atomicAdd(&S.nq, 1)] = (int16_t)i;
+                // A2's inputs, kept on chip (hx is not used before phase N)
+                float* st = &S.hx[0][0];
+                st[i] = u ? x10 : x00;
+                st[kItemCap + i] = u ? x11 : x01;
+                st[2 * kItemCap + i] = u ? x12 : x02;
+                st[3 * kItemCap + i] = R;
+                st[4 * kItemCap + i] = __uint_as_float(u ? fl1 : fl0);
                 continue;
             }
             S.bits[i] = clear_taxel(a, g, R, u ? fl1 : fl0, phi);
@@ -138,7 +147,10 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
             if (S.start[mid] <= i) lo = mid;
             else hi = mid - 1;
         }
-        const CleanReading cr = refine_taxel(a, S.rec[lo], obj, it.taxel_begin + i);
+        const float* st = &S.hx[0][0];
+        const CleanReading cr = refine_taxel(a, S.rec[lo], obj, it.taxel_begin + i, st[i], st[kItemCap + i],
+                                             st[2 * kItemCap + i], st[3 * kItemCap + i],
+                                             (uint8_t)__float_as_uint(st[4 * kItemCap + i]));
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             S.fc[c][i] = cr.f[c];

@@ -52,8 +52,7 @@ __device__ __forceinline__ float fast_query(const float* rec, const ObjDev& obj,
     const float3 q = f3(fmaf(rec[0], x0, fmaf(rec[1], x1, fmaf(rec[2], x2, rec[18]))),
                         fmaf(rec[3], x0, fmaf(rec[4], x1, fmaf(rec[5], x2, rec[19]))),
                         fmaf(rec[6], x0, fmaf(rec[7], x1, fmaf(rec[8], x2, rec[20]))));
-    float3 go;
-    return rec[38] * sdf_fast(obj, q, &go);
+    return rec[38] * sdf_phi_fast(obj, q);
 }
 
 // A taxel clear of the surface (or an inactive filler, R = 0): depth 0,
@@ -74,16 +73,16 @@ struct CleanReading {
     uint8_t bits;
 };
 
-// A near-contact taxel: compensated query point and SDF (near-contact depths
-// carry ~1e-14 relative error), depth, Schmitt decision on the compensated
-// depth, force/torque; writes the clean outputs and the new flag byte.
+// A near-contact taxel at link-frame position (x0, x1, x2) with probe radius
+// R and last step's flag byte: compensated query point and SDF (near-contact
+// depths carry ~1e-14 relative error), depth, Schmitt decision on the
+// compensated depth, force/torque; writes the clean outputs and the new flag
+// byte.
 __device__ __forceinline__ CleanReading refine_taxel(const StepArgs& a, const float* rec, const ObjDev& obj,
-                                                     int64_t g) {
+                                                     int64_t g, float x0, float x1, float x2, float R,
+                                                     uint8_t flags) {
     const ParamsDev& P = a.P;
     const int64_t T = a.n_taxels;
-    const float R = a.R[g];
-    const uint8_t flags = a.flags[g];
-    const float x0 = a.x[g], x1 = a.y[g], x2 = a.z[g];
     df qd[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
@@ -149,13 +148,30 @@ __device__ __forceinline__ CleanReading refine_taxel(const StepArgs& a, const fl
 }
 
 // Noise state of one active taxel after its clean reading (fc[.][i] and the
-// clean depth in ag[0][i]); the state loads do not depend on the geometry.
+// clean depth in ag[0][i]).  The state loads do not depend on the geometry,
+// and all of them are issued before the first store: the compiler cannot move
+// a load above a store to a pointer that may alias it, and every such barrier
+// would cost a further round trip to memory.
 template <class Smem>
 __device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, int64_t g, uint32_t ep, uint32_t step,
                                             uint8_t bits) {
     const ParamsDev& P = a.P;
     const int64_t T = a.n_taxels;
+    const bool hyst_d = P.depth.beta != 0.0f, hyst_f = P.ft.beta != 0.0f, walk_d = P.depth.sigma_rw != 0.0f;
     const float n0 = __ldcs(a.nx + g), n1 = __ldcs(a.ny + g), n2 = __ldcs(a.nz + g);
+    float prev_d = 0.0f, xi_d = 0.0f, drift_d = 0.0f, pv[6], xv[6];
+    if (hyst_d) {
+        prev_d = __ldcs(a.hyst_prev + g);
+        xi_d = __ldcs(a.hyst_xi + g);
+    }
+    if (hyst_f) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            pv[c] = __ldcs(a.hyst_prev + (1 + c) * T + g);
+            xv[c] = __ldcs(a.hyst_xi + (1 + c) * T + g);
+        }
+    }
+    if (walk_d) drift_d = __ldcs(a.drift + g);
     const uint64_t gid = (uint64_t)(a.gid0 + g);
     const bool dead = bits & BIT_DEAD;
     const float d = S.ag[0][i];
@@ -164,14 +180,13 @@ __device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, i
     const float gain_d = P.depth.gain_on ? P.depth.gain_lo + P.depth.gain_span * u24(wep.y) : 1.0f;
     const float gain_f = P.ft.gain_on ? P.ft.gain_lo + P.ft.gain_span * u24(wep.z) : 1.0f;
     float xd = gain_d * d;
-    if (P.depth.beta != 0.0f) xd = hyst_update(P.depth, xd, a.hyst_prev + g, a.hyst_xi + g);
-    if (P.ft.beta != 0.0f) {
-        float pv[6], xv[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            pv[c] = __ldcs(a.hyst_prev + (1 + c) * T + g);
-            xv[c] = __ldcs(a.hyst_xi + (1 + c) * T + g);
-        }
+    if (hyst_d) {
+        const float xi = P.depth.decay * xi_d + (xd - prev_d);
+        __stcs(a.hyst_xi + g, xi);
+        __stcs(a.hyst_prev + g, xd);
+        xd = xd + P.depth.beta * xi;
+    }
+    if (hyst_f) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             const float x = gain_f * S.fc[c][i];
@@ -188,8 +203,8 @@ __device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, i
         uint4 w = draw(P.seed, gid, step, TAG_SCALAR);
         float2 z = box_muller(w.x, w.y);
         float dr = 0.0f;
-        if (P.depth.sigma_rw != 0.0f) {
-            dr = __ldcs(a.drift + g) + P.depth.sigma_rw * z.x;
+        if (walk_d) {
+            dr = drift_d + P.depth.sigma_rw * z.x;
             __stcs(a.drift + g, dr);
         }
         xd = xd + P.depth.bias + P.depth.sigma_white * z.y + dr;
