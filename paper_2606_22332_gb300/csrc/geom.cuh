@@ -141,8 +141,12 @@ __device__ __forceinline__ float grid_phi_fast(const ObjDev& o, float3 q) {
     float c01 = v.v001 + fx * (v.v101 - v.v001), c11 = v.v011 + fx * (v.v111 - v.v011);
     float c0 = c00 + fy * (c10 - c00), c1 = c01 + fy * (c11 - c01);
     float phi = c0 + fz * (c1 - c0);
+    // distance to the box for points outside it (0 inside); only points
+    // outside the padded box, far from any surface, get a non-zero term, and
+    // the hardware reciprocal square root is accurate enough there
     float3 out = f3(q.x - c[0], q.y - c[1], q.z - c[2]);
-    return phi + sqrtf(dot(out, out));
+    const float o2 = dot(out, out);
+    return phi + o2 * rsqrtf(fmaxf(o2, 1e-30f));
 }
 
 __device__ __forceinline__ df df_lerp(df a, df b, df f) { return df_add(a, df_mul(f, df_sub(b, a))); }

@@ -42,7 +42,20 @@ struct SmemStep {
     int16_t queue[kItemCap];            // near-contact taxels for phase A2
     int nq;
     unsigned int slot;                  // persistent schedule: the item being run
+    uint32_t episode;                   // the env's episode counter
+    // when every link of the item has the same lattice (rows x cols, wrap)
+    // and holds rows * cols taxels: that taxel count (else 0), the lattice,
+    // and 1/count, 1/cols for the index arithmetic below
+    int uni_len, uni_rows, uni_cols, uni_wrap;
+    float uni_inv_len, uni_inv_cols;
 };
+
+// Link of item taxel i (and, in B, its lattice row and column) for a uniform
+// item: l = floor((i + 1/2) / len) evaluated as (i + 1/2) * fl(1/len) in
+// FP32.  The quotient lies at least 1/(2 len) from an integer while the two
+// roundings move it by at most 2^-23 (i + 1/2) / len; for i < 1024 and
+// len <= 1024 that is below 1.3e-4 < 1/(2 len), so the floor is exact.
+__device__ __forceinline__ int uni_div(int i, float inv) { return (int)(((float)i + 0.5f) * inv); }
 
 // One work item: every phase of the step for its taxels.
 template <int NT>
@@ -55,10 +68,33 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
     const int n = it.n_taxels;
     const int tid = threadIdx.x;
 
-    // ---- prologue: link records, lattice, object
-    for (int i = tid; i < nl * kLinkRec; i += NT) {
-        int l = i / kLinkRec, f = i % kLinkRec;
-        S.rec[l][f] = a.link_rec[(size_t)(e * L + lb + l) * kLinkRec + f];
+    // ---- prologue: link records (the item's links are consecutive: one
+    //      contiguous block of 16-byte vectors), lattice, object
+    static_assert(kLinkRec % 4 == 0 && kItemCap <= 1024, "vector copy of link records; uni_div range");
+    {
+        const float4* src = reinterpret_cast<const float4*>(a.link_rec + (size_t)(e * L + lb) * kLinkRec);
+        float4* dst = reinterpret_cast<float4*>(&S.rec[0][0]);
+        for (int v = tid; v < nl * (kLinkRec / 4); v += NT) dst[v] = src[v];
+    }
+    if (tid < 32) {  // uniform-lattice test over the item's (at most 32) links
+        const bool act = tid < nl;
+        LinkLattice lat{};
+        if (act) lat = a.lattice[e * L + lb + tid];
+        int next = __shfl_down_sync(0xffffffffu, lat.env_offset, 1);
+        if (tid == nl - 1) next = a.lattice[e * L + lb].env_offset + n;
+        const int cnt = act ? next - lat.env_offset : 0;
+        const int r0 = __shfl_sync(0xffffffffu, (int)lat.rows, 0), c0 = __shfl_sync(0xffffffffu, (int)lat.cols, 0);
+        const int w0 = __shfl_sync(0xffffffffu, (int)lat.wrap, 0);
+        const bool same = !act || ((int)lat.rows == r0 && (int)lat.cols == c0 && (int)lat.wrap == w0 && cnt == r0 * c0);
+        const bool uni = __all_sync(0xffffffffu, same) && r0 * c0 > 0;
+        if (tid == 0) {
+            S.uni_len = uni ? r0 * c0 : 0;
+            S.uni_rows = r0;
+            S.uni_cols = c0;
+            S.uni_wrap = w0;
+            S.uni_inv_len = uni ? 1.0f / (float)(r0 * c0) : 0.0f;
+            S.uni_inv_cols = uni ? 1.0f / (float)c0 : 0.0f;
+        }
     }
     if (tid <= nl) {
         // the lattice table holds each link's first taxel relative to the env
@@ -78,10 +114,11 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
         oid = min(max(oid, 0), a.n_objects - 1);
         S.obj = a.objects[oid];
         S.nq = 0;
+        S.episode = a.episode[e];
     }
     __syncthreads();
 
-    const uint32_t ep = a.episode[e];
+    const uint32_t ep = S.episode;
     const ObjDev& obj = S.obj;
 
     // ---- phase A1 (geometry): FP32 query of every taxel; those clear of the
@@ -97,11 +134,16 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
         const float x00 = __ldcs(a.x + g0), x01 = __ldcs(a.y + g0), x02 = __ldcs(a.z + g0);
         const float x10 = __ldcs(a.x + g1), x11 = __ldcs(a.y + g1), x12 = __ldcs(a.z + g1);
         const uint8_t fl0 = __ldcs(a.flags + g0), fl1 = __ldcs(a.flags + g1);
-        while (i0 >= S.start[l + 1]) ++l;
-        const int l0 = l;
-        int l1 = l;
-        if (has1)
-            while (i1 >= S.start[l1 + 1]) ++l1;
+        int l0, l1;
+        if (S.uni_len) {
+            l0 = uni_div(i0, S.uni_inv_len);
+            l1 = has1 ? uni_div(i1, S.uni_inv_len) : l0;
+        } else {
+            while (i0 >= S.start[l + 1]) ++l;
+            l0 = l1 = l;
+            if (has1)
+                while (i1 >= S.start[l1 + 1]) ++l1;
+        }
         float phi0 = 0.0f, phi1 = 0.0f;
         if (obj.kind == TG_OBJ_NEURAL) {  // from the learned-SDF query kernel
             if (R0 > 0.0f) phi0 = a.nq_phi[g0];
@@ -181,6 +223,14 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
     //      (written over the clean values in fc, which C1 has consumed)
     l = 0;
     for (int i = tid; i < n; i += NT) {
+        if (S.uni_len) {
+            const int base = uni_div(i, S.uni_inv_len) * S.uni_len;
+            const int j = i - base;
+            const int r = uni_div(j, S.uni_inv_cols);
+            noisy_ft(a, S, S.fc, i, it.taxel_begin + i, ep, step, S.bits[i], base, r, j - r * S.uni_cols,
+                     S.uni_rows, S.uni_cols, S.uni_wrap != 0);
+            continue;
+        }
         while (i >= S.start[l + 1]) ++l;
         const int j = i - S.start[l], cols = S.cols[l];
         const int r = j / cols;

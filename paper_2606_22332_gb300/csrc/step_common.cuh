@@ -256,20 +256,32 @@ __device__ __forceinline__ void noisy_ft(const StepArgs& a, const Smem& S, Out o
 #pragma unroll
     for (int c = 0; c < 6; ++c) z[c] = S.hx[c][i];
     if (P.chi != 0.0f) {
+        // 3x3 window without branches: a neighbour off the lattice (no wrap)
+        // gets weight 0 and the taxel's own index, so every tap is a plain
+        // shared-memory load
+        const bool vu = r > 0, vd = r + 1 < rows;
+        int cl = cc - 1, cr = cc + 1;
+        bool vl = true, vr = true;
+        if (cl < 0) {
+            if (wrap) cl += cols;
+            else { vl = false; cl = cc; }
+        }
+        if (cr >= cols) {
+            if (wrap) cr -= cols;
+            else { vr = false; cr = cc; }
+        }
+        const int row_off[3] = {vu ? -cols : 0, 0, vd ? cols : 0};
+        const float row_w[3] = {vu ? 1.f : 0.f, 1.f, vd ? 1.f : 0.f};
+        const int col_idx[3] = {cl, cc, cr};
+        const float col_w[3] = {vl ? 1.f : 0.f, 1.f, vr ? 1.f : 0.f};
+        const int row0 = base + r * cols;
         float conv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int di = -1; di <= 1; ++di) {
-            const int rr = r + di;
-            if (rr < 0 || rr >= rows) continue;
+        for (int di = 0; di < 3; ++di) {
 #pragma unroll
-            for (int dj = -1; dj <= 1; ++dj) {
-                int c2 = cc + dj;
-                if (c2 < 0 || c2 >= cols) {
-                    if (!wrap) continue;
-                    c2 += c2 < 0 ? cols : -cols;
-                }
-                const int nb = base + rr * cols + c2;
-                const float w = P.xt_w[(di + 1) * 3 + (dj + 1)];
+            for (int dj = 0; dj < 3; ++dj) {
+                const float w = P.xt_w[di * 3 + dj] * (row_w[di] * col_w[dj]);
+                const int nb = row0 + row_off[di] + col_idx[dj];
 #pragma unroll
                 for (int c = 0; c < 6; ++c) conv[c] = fmaf(w, S.hx[c][nb], conv[c]);
             }
