@@ -36,15 +36,14 @@ sys.path.insert(0, ROOT)
 METRIC = "taxel-queries/s at 20,480 envs×1,000 taxels; neural-SDF vs plain at ≤0.2 mm"
 UNIT = "taxel-queries/s"
 
-# Algorithmic HBM bytes per taxel query of the fused step kernel (itemised in
-# the design doc): taxel position + radius 16, flag byte r/w 2, hysteresis x_{t-1}
-# and xi for 7 channels r/w 112, drift for 6 channels r/w 48, outputs 58
-# (clean/noisy depth, clean/noisy force/torque), per-link pose records and
-# link outputs amortised over 50 taxels 4.8.  Contact taxels additionally read
-# their normal (12 B) for agg_force; counted with the measured contact share.
-BYTES_PER_QUERY_BASE = 16 + 2 + 112 + 48 + 58 + 4.8
-BYTES_NORMAL = 12.0
-SURVEY_BYTES_PER_QUERY = 251.0
+# Algorithmic HBM bytes per taxel query of the fused step kernel: taxel
+# geometry (position, normal, radius) 28 + a link byte, flag byte r/w 2,
+# hysteresis x_{t-1} and xi for 7 channels r/w 112, drift for 6 channels r/w
+# 48, outputs 58 (contact, clean/noisy depth, clean/noisy force/torque),
+# per-env poses and link outputs amortised ~2: 251 B, the per-query figure the
+# roofline is taken against.  The SDF cells a query reads are not counted (the
+# grids are read from L2 where the object-sorted schedule keeps them).
+BYTES_PER_QUERY = 251.0
 
 
 def parse():
@@ -65,6 +64,8 @@ def parse():
     ap.add_argument("--oracle-envs", type=int, default=800, help="env sample of the CPU oracle legs")
     ap.add_argument("--oracle-objects", type=int, default=2, help="objects whose envs form the oracle sample")
     ap.add_argument("--oracle-steps", type=int, default=300, help="steps of the cpu_baseline leg")
+    ap.add_argument("--schedule", choices=["auto", "grid", "grid-sorted", "persistent", "persistent-sorted"],
+                    default="auto", help="step-kernel schedule: picked by the autotuner (auto) or fixed")
     return ap.parse_args()
 
 
@@ -337,16 +338,25 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def traffic_from_profile(kernel_source):
+STEP_KERNEL_SOURCES = ("step.cu", "step_common.cuh", "geom.cuh", "df.cuh", "rng.cuh", "internal.h")
+
+
+def step_kernel_sha():
+    """sha256 (16 hex digits) over the step kernel's source files."""
+    h = hashlib.sha256()
+    for f in STEP_KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2606_22332_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile():
     """dram bytes per launch of the step kernel from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
+    if it was taken on the current kernel sources (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p))
-    sha = hashlib.sha256(open(kernel_source, "rb").read()).hexdigest()[:16]
-    rec = d.get("step_kernel")
-    if not rec or rec.get("source_sha") != sha:
+    rec = json.load(open(p)).get("step_kernel")
+    if not rec or rec.get("source_sha") != step_kernel_sha():
         return None
     return rec.get("dram_bytes_per_launch_full")
 
@@ -390,7 +400,11 @@ def run_tg(args):
 
     # schedule picked by the autotuner on the live scene (state restored after)
     scene.step(step_inputs(0, d_in))
-    tune = scene.autotune(step_inputs(0, d_in), steps=3)
+    if args.schedule == "auto":
+        tune = scene.autotune(step_inputs(0, d_in), steps=3)
+    else:
+        scene.set_schedule(persistent=args.schedule.startswith("persistent"), sorted=args.schedule.endswith("sorted"))
+        tune = {"candidates": "fixed by --schedule"}
     sched = scene.schedule()
     launches_per_step = 3 + (1 if sched["sorted"] and len(wl.objects) > 1 else 0)  # pose, [order], step, advance
 
@@ -492,14 +506,14 @@ def run_tg(args):
     del objs
 
     peak, peak_kind = peaks()
-    bpq = BYTES_PER_QUERY_BASE + BYTES_NORMAL * pen_share
+    bpq = BYTES_PER_QUERY
     step_avg_ms = step_ms / max(nsteps, 1)
     achieved = bpq * wl.n_active / (step_avg_ms / 1e3) / 1e9
-    traffic = traffic_from_profile(os.path.join(ROOT, "paper_2606_22332_gb300", "csrc", "step.cu"))
+    traffic = traffic_from_profile()
     roofline = {
         "bound": "hbm", "kernel": "step_kernel", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
         "frac": round(achieved / peak, 4), "peak_kind": peak_kind, "traffic": traffic,
-        "algorithmic_bytes_per_query": round(bpq, 2), "survey_bytes_per_query": SURVEY_BYTES_PER_QUERY,
+        "algorithmic_bytes_per_query": bpq,
         "step_kernel_ms": round(step_avg_ms, 4), "prologue_kernels_ms": round(pose_ms / max(nsteps, 1), 4),
         "step_kernel_share": round(step_ms / max(step_ms + pose_ms, 1e-9), 4),
     }
