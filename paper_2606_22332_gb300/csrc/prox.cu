@@ -22,11 +22,40 @@ constexpr int kMaxMarch = 192;
 // signed distance in world units along the ray q0 + t d (object frame, d
 // already scaled by 1/s)
 __device__ __forceinline__ float ray_field(const ObjDev& obj, float3 q0, float3 d, float t, float scale) {
-    float3 go;
-    return scale * sdf_fast(obj, q0 + d * t, &go);
+    return scale * sdf_phi_fast(obj, q0 + d * t);
+}
+
+// The part [t0, t1] of [0, range] where the ray q0 + t d is inside a grid
+// object's box (a grid has no surface outside it: the first crossing is
+// searched in the box only); false when the ray misses the box within range.
+// Other object kinds: [0, range].
+__device__ __forceinline__ bool ray_box(const ObjDev& o, float3 q0, float3 d, float range, float* t0, float* t1) {
+    float ta = 0.0f, tb = range;
+    if (o.kind == TG_OBJ_GRID || o.kind == TG_OBJ_NEURAL) {
+        const float q[3] = {q0.x, q0.y, q0.z}, dd[3] = {d.x, d.y, d.z};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (dd[a] == 0.0f) {
+                if (q[a] < o.lo[a] || q[a] > o.hi[a]) return false;
+            } else {
+                float u = (o.lo[a] - q[a]) / dd[a], v = (o.hi[a] - q[a]) / dd[a];
+                if (u > v) { const float w = u; u = v; v = w; }
+                ta = fmaxf(ta, u);
+                tb = fminf(tb, v);
+            }
+        }
+    }
+    *t0 = ta;
+    *t1 = tb;
+    return ta <= tb;
 }
 
 constexpr int kRefineIters = 24;
+// idle lanes refill from the pool once at least this many are idle (or the
+// whole warp is): a refill is ~200 instructions executed by the refilling
+// lanes only, and refilling every iteration left most lanes of each warp
+// masked off through it
+constexpr int kRefillBatch = 16;
 
 // The taxel of item-relative index i: its link (last start <= i).
 __device__ __forceinline__ int link_of(const int* start, int nl, int i) {
@@ -39,42 +68,14 @@ __device__ __forceinline__ int link_of(const int* start, int nl, int i) {
     return lo;
 }
 
-// Lanes take rays, not taxels: every lane owns one ray at a time and takes
-// the next ray of the item's pool (a warp-aggregated atomic) when its ray
-// ends, so the warp stays full while rays march for very different numbers
-// of steps.  Marching and the Illinois refinement of the first crossing are
-// one state machine with exactly one field evaluation per iteration, so the
-// lanes of a warp stay converged on it:
-//   march:  t' = min(t + max(f, 10 um), range); f' = f(t'); f' <= 0 -> refine
-//           on [t, t'], else if t' = range -> miss, else continue (at most
-//           192 samples)
-//   refine: t_c = (f_a t_b - f_b t_a) / (f_a - f_b), halving the retained
-//           end's value after two moves on the same side (at most 24
-//           samples, or until t_b - t_a <= 1e-7 m); the crossing is t_b.
-// Per-ray distances go to shared memory; each taxel then sums its rays in
-// ray order (deterministic) and runs the noise chain.
-__global__ void __launch_bounds__(kProxThreads, 4) prox_kernel(const StepArgs a) {
-    extern __shared__ float t_s[];  // [n taxels][rays]: crossing distance or -1
-    __shared__ float rec_s[kProxItemLinks][kLinkRec];
-    __shared__ int start_s[kProxItemLinks + 1];
-    __shared__ ObjDev obj_s;
-    __shared__ unsigned int next_ray;
-    const Item it = a.items[a.item_order ? a.item_order[blockIdx.x] : blockIdx.x];
-    const int e = it.env, L = a.max_links, lb = it.link_begin, nl = it.link_end - it.link_begin, n = it.n_taxels;
+// The rays of one item (pool, march, refine) into t_s.  Instantiated once for
+// grid objects (the field is the inlined grid interpolation) and once for
+// the other kinds (dispatch per sample), so the grid loop carries no calls.
+template <bool GRID>
+__device__ __forceinline__ void trace_item_rays(const StepArgs& a, const Item& it, int n, int nl,
+                                                const float (*rec_s)[kLinkRec], const int* start_s,
+                                                const ObjDev& obj_s, unsigned int* next_ray, float* t_s) {
     const ParamsDev& P = a.P;
-    const uint32_t step = a.step_from_ctl ? a.ctl->step : a.step;
-    for (int i = threadIdx.x; i < nl * kLinkRec; i += kProxThreads)
-        rec_s[i / kLinkRec][i % kLinkRec] = a.link_rec[(size_t)(e * L + lb + i / kLinkRec) * kLinkRec + i % kLinkRec];
-    if ((int)threadIdx.x <= nl) {
-        const int base = a.lattice[e * L + lb].env_offset;
-        start_s[threadIdx.x] = (int)threadIdx.x < nl ? a.lattice[e * L + lb + threadIdx.x].env_offset - base : n;
-    }
-    if (threadIdx.x == 0) {
-        int oid = min(max(a.obj_id[e], 0), a.n_objects - 1);
-        obj_s = a.objects[oid];
-        next_ray = 0;
-    }
-    __syncthreads();
     const int nr = P.prox_rays;
     const unsigned total = (unsigned)(n * nr);
     const float range = P.prox_range;
@@ -82,16 +83,17 @@ __global__ void __launch_bounds__(kProxThreads, 4) prox_kernel(const StepArgs a)
     // one ray per lane
     int rid = -1, mode = 0, cnt = 0, side = 0;  // mode 0 idle, 1 march, 2 refine
     bool exhausted = false;
-    float ta = 0.f, fa = 0.f, tb = 0.f, fb = 0.f, scale = 1.f;
+    float ta = 0.f, fa = 0.f, tb = 0.f, fb = 0.f, scale = 1.f, tend = 0.f;
     float3 q0 = f3(0.f, 0.f, 0.f), d = f3(0.f, 0.f, 0.f);
     for (;;) {
         // refill idle lanes from the pool
         const bool want = mode == 0 && !exhausted;
         const unsigned need = __ballot_sync(0xffffffffu, want);
-        if (need) {
+        const unsigned busy = __ballot_sync(0xffffffffu, mode != 0);
+        if (need && (__popc(need) >= kRefillBatch || busy == 0u)) {
             const int leader = __ffs(need) - 1;
             unsigned base = 0;
-            if ((int)lane == leader) base = atomicAdd(&next_ray, (unsigned)__popc(need));
+            if ((int)lane == leader) base = atomicAdd(next_ray, (unsigned)__popc(need));
             base = __shfl_sync(0xffffffffu, base, leader);
             if (want) {
                 const unsigned r = base + (unsigned)__popc(need & ((1u << lane) - 1u));
@@ -123,10 +125,16 @@ __global__ void __launch_bounds__(kProxThreads, 4) prox_kernel(const StepArgs a)
                         d = f3(rec[0] * dl.x + rec[1] * dl.y + rec[2] * dl.z, rec[3] * dl.x + rec[4] * dl.y + rec[5] * dl.z,
                                rec[6] * dl.x + rec[7] * dl.y + rec[8] * dl.z);
                         scale = rec[38];
-                        ta = 0.0f;
-                        fa = -1.0f;  // the first sample is t = 0 (mode 1 with cnt = -1)
-                        cnt = -1;
-                        mode = 1;
+                        float t0, t1;
+                        if (!ray_box(obj_s, q0, d, range, &t0, &t1)) {
+                            t_s[rid] = -1.0f;  // misses the object's box within the range
+                        } else {
+                            ta = t0;       // the first sample is the box entry (mode 1 with cnt = -1)
+                            tend = t1;
+                            fa = -1.0f;
+                            cnt = -1;
+                            mode = 1;
+                        }
                     }
                 }
             }
@@ -136,7 +144,7 @@ __global__ void __launch_bounds__(kProxThreads, 4) prox_kernel(const StepArgs a)
         float tq = 0.0f;
         bool eval = false;
         if (mode == 1) {
-            tq = cnt < 0 ? 0.0f : fminf(ta + fmaxf(fa, kMinStep), range);
+            tq = cnt < 0 ? ta : fminf(ta + fmaxf(fa, kMinStep), tend);
             eval = true;
         } else if (mode == 2) {
             if (cnt >= kRefineIters || !(tb - ta > 1e-7f)) {
@@ -147,15 +155,21 @@ __global__ void __launch_bounds__(kProxThreads, 4) prox_kernel(const StepArgs a)
                 eval = true;
             }
         }
+        // the marching and refining lanes evaluate the field together
         float fq = 0.0f;
-        if (eval) fq = ray_field(obj_s, q0, d, tq, scale);
+        __syncwarp();
+        if (eval) {
+            if constexpr (GRID) fq = scale * grid_phi_fast(obj_s, q0 + d * tq);
+            else fq = ray_field(obj_s, q0, d, tq, scale);
+        }
+        __syncwarp();
         if (mode == 1) {
-            if (cnt < 0) {                   // the probe centre
-                if (!(fq > 0.0f)) { t_s[rid] = 0.0f; mode = 0; }
+            if (cnt < 0) {                   // the probe centre, or the box entry
+                if (!(fq > 0.0f)) { t_s[rid] = tq; mode = 0; }
                 else { fa = fq; cnt = 0; }
             } else if (!(fq > 0.0f)) {       // crossed: refine on [ta, tq]
                 tb = tq; fb = fq; mode = 2; cnt = 0; side = 0;
-            } else if (tq >= range || ++cnt >= kMaxMarch) {
+            } else if (tq >= tend || ++cnt >= kMaxMarch) {
                 t_s[rid] = -1.0f;            // no crossing within the range
                 mode = 0;
             } else {
@@ -174,7 +188,52 @@ __global__ void __launch_bounds__(kProxThreads, 4) prox_kernel(const StepArgs a)
             ++cnt;
         }
     }
+}
+
+// Lanes take rays, not taxels: every lane owns one ray at a time and takes
+// the next ray of the item's pool (a warp-aggregated atomic) once its ray has
+// ended and enough lanes of the warp are idle, so the warp stays full while
+// rays march for very different numbers of steps.  Marching and the Illinois refinement of the first crossing are
+// one state machine with exactly one field evaluation per iteration, so the
+// lanes of a warp stay converged on it:
+//   march:  from the entry into the object's box (a grid has no surface
+//           outside it), t' = min(t + max(f, 10 um), t_end) with t_end the
+//           box exit or the range; f' = f(t'); f' <= 0 -> refine on [t, t'],
+//           else if t' = t_end -> miss, else continue (at most 192 samples)
+//   refine: t_c = (f_a t_b - f_b t_a) / (f_a - f_b), halving the retained
+//           end's value after two moves on the same side (at most 24
+//           samples, or until t_b - t_a <= 1e-7 m); the crossing is t_b.
+// Per-ray distances go to shared memory; each taxel then sums its rays in
+// ray order (deterministic) and runs the noise chain.
+__global__ void __launch_bounds__(kProxThreads, 4) prox_kernel(const StepArgs a) {
+    extern __shared__ float t_s[];  // [n taxels][rays]: crossing distance or -1
+    __shared__ float rec_s[kProxItemLinks][kLinkRec];
+    __shared__ int start_s[kProxItemLinks + 1];
+    __shared__ ObjDev obj_s;
+    __shared__ unsigned int next_ray;
+    const Item it = a.items[a.item_order ? a.item_order[blockIdx.x] : blockIdx.x];
+    const int e = it.env, L = a.max_links, lb = it.link_begin, nl = it.link_end - it.link_begin, n = it.n_taxels;
+    const ParamsDev& P = a.P;
+    const uint32_t step = a.step_from_ctl ? a.ctl->step : a.step;
+    for (int i = threadIdx.x; i < nl * kLinkRec; i += kProxThreads)
+        rec_s[i / kLinkRec][i % kLinkRec] = a.link_rec[(size_t)(e * L + lb + i / kLinkRec) * kLinkRec + i % kLinkRec];
+    if ((int)threadIdx.x <= nl) {
+        const int base = a.lattice[e * L + lb].env_offset;
+        start_s[threadIdx.x] = (int)threadIdx.x < nl ? a.lattice[e * L + lb + threadIdx.x].env_offset - base : n;
+    }
+    if (threadIdx.x == 0) {
+        int oid = min(max(a.obj_id[e], 0), a.n_objects - 1);
+        obj_s = a.objects[oid];
+        next_ray = 0;
+    }
     __syncthreads();
+    if (obj_s.kind == TG_OBJ_GRID || obj_s.kind == TG_OBJ_NEURAL)
+        trace_item_rays<true>(a, it, n, nl, rec_s, start_s, obj_s, &next_ray, t_s);
+    else
+        trace_item_rays<false>(a, it, n, nl, rec_s, start_s, obj_s, &next_ray, t_s);
+    __syncthreads();
+    const int nr = P.prox_rays;
+    const float range = P.prox_range;
     const uint32_t ep = a.episode[e];
     const int64_t T = a.n_taxels;
     for (int i = threadIdx.x; i < n; i += kProxThreads) {
