@@ -400,15 +400,51 @@ __global__ void __launch_bounds__(kInferThreads) nsdf_step_query_kernel(const St
     }
     tc_setup(S);  // (its barrier also publishes the loads above)
     // pass 1a: the fallback grid for every taxel; near-field taxels are listed
-    for (int i = threadIdx.x; i < n; i += kInferThreads) {
-        const int64_t g = it.taxel_begin + i;
-        float scale;
-        const float3 q = taxel_point(a, rec_s, start_s, g, i, &scale);
-        float3 go;
-        const float pg = scale * grid_fast(o, q, &go);
-        const float R = a.R[g];
-        if (R > 0.0f && !(pg > R + kNeuralBand)) near_i[atomicAdd(&nnear, 1)] = (int16_t)i;
-        else phi_out[g] = pg;
+    //          (a thread's four taxels at once, so that their loads and
+    //          their grid-cell loads are in flight together)
+    static_assert(kItemCap <= 4 * kInferThreads, "four taxels per thread cover an item");
+    {
+        constexpr int U = 4;
+        float px[U][3], pr[U];
+        int64_t pgid[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = threadIdx.x + u * kInferThreads;
+            pgid[u] = it.taxel_begin + (i < n ? i : 0);
+            pr[u] = 0.0f;
+            if (i < n) {
+                px[u][0] = a.x[pgid[u]];
+                px[u][1] = a.y[pgid[u]];
+                px[u][2] = a.z[pgid[u]];
+                pr[u] = a.R[pgid[u]];
+            }
+        }
+        float pg[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = threadIdx.x + u * kInferThreads;
+            pg[u] = 0.0f;
+            if (i < n) {
+                int lo = 0, hi = nl - 1;  // link of taxel i: last start <= i
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (start_s[mid] <= i) lo = mid;
+                    else hi = mid - 1;
+                }
+                const float* rec = rec_s[lo];
+                const float3 q = make_float3(fmaf(rec[0], px[u][0], fmaf(rec[1], px[u][1], fmaf(rec[2], px[u][2], rec[18]))),
+                                             fmaf(rec[3], px[u][0], fmaf(rec[4], px[u][1], fmaf(rec[5], px[u][2], rec[19]))),
+                                             fmaf(rec[6], px[u][0], fmaf(rec[7], px[u][1], fmaf(rec[8], px[u][2], rec[20]))));
+                pg[u] = rec[38] * grid_phi_fast(o, q);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = threadIdx.x + u * kInferThreads;
+            if (i >= n) break;
+            if (pr[u] > 0.0f && !(pg[u] > pr[u] + kNeuralBand)) near_i[atomicAdd(&nnear, 1)] = (int16_t)i;
+            else phi_out[pgid[u]] = pg[u];
+        }
     }
     __syncthreads();
     bool failed = false;
