@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--neural-points", type=int, default=2_000_000, help="labelled training points per object")
     ap.add_argument("--neural-steps", type=int, default=3000, help="Adam steps per object")
     ap.add_argument("--neural-check-envs", type=int, default=256, help="envs compared against the exact mesh")
+    ap.add_argument("--neural-max-err-mm", type=float, default=0.2,
+                    help="probe error (mm) above which an object falls back to its grid")
     ap.add_argument("--oracle-envs", type=int, default=800, help="env sample of the CPU oracle legs")
     ap.add_argument("--oracle-objects", type=int, default=2, help="objects whose envs form the oracle sample")
     ap.add_argument("--oracle-steps", type=int, default=300, help="steps of the cpu_baseline leg")
@@ -263,7 +265,7 @@ def neural_line(args, wl, objs, d_in, dev, sched, stream, step_inputs, t_plain_m
     nobjs = [W.ObjectSpec(kind="neural", dims=objs[k].dims, lo=objs[k].lo, hi=objs[k].hi, fp16=objs[k].fp16,
                           values=objs[k].values, net=nets[k], nsdf_err_mm=probe_stats[k][0], name=objs[k].name)
              for k in range(n_obj)] + list(objs[n_obj:])
-    sc = tg.Scene(wl.geom(), wl.params)
+    sc = tg.Scene(wl.geom(), dict(wl.params, nsdf_max_err_mm=args.neural_max_err_mm))
     sc.upload_objects(nobjs)
     used = [k for k in range(n_obj) if sc.object_info(k)[0] == tg.TG_OBJ_NEURAL]
     sc.set_schedule(**sched)
@@ -292,7 +294,7 @@ def neural_line(args, wl, objs, d_in, dev, sched, stream, step_inputs, t_plain_m
         outs = {}
         for name, ol in (("neural", nobjs), ("grid", objs),
                          ("mesh", [W.ObjectSpec(kind="mesh", verts=o.verts, faces=o.faces) for o in wl.objects])):
-            s2 = tg.Scene(sub.geom(), sub.params, taxel_gid0=0, env_gid0=0)
+            s2 = tg.Scene(sub.geom(), dict(sub.params, nsdf_max_err_mm=args.neural_max_err_mm), taxel_gid0=0, env_gid0=0)
             s2.upload_objects(ol)
             s2.step(inp)
             outs[name] = {"flags": s2.read(tg.CH_STATE_FLAGS) & 1, "depth": s2.read(tg.CH_DEPTH).astype(np.float64),
@@ -319,6 +321,7 @@ def neural_line(args, wl, objs, d_in, dev, sched, stream, step_inputs, t_plain_m
         net.close()
     return {
         "objects_with_network": n_obj, "objects_using_network": len(used), "envs_using_network": int(np.isin(wl.obj_id, used).sum()),
+        "fallback_above_mm": args.neural_max_err_mm,
         "training": {"points_per_object": args.neural_points, "steps": args.neural_steps, "batch": 1 << 14,
                      "seconds_total": round(train_s, 1), "labels": "GPU exact-mesh query"},
         "probe_err_mm": {"max_over_objects": float(pm[:, 0].max()), "median_of_max": float(np.median(pm[:, 0])),
