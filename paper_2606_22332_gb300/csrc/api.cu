@@ -51,7 +51,7 @@ struct tg_scene {
     int32_t* s_obj_id = nullptr;
     uint8_t* s_mask = nullptr;
     uint8_t* s_contact = nullptr;
-    int32_t* item_order = nullptr;    // per-step object-sorted item order
+    Item* items_sorted = nullptr;     // per-step object-sorted copy of the items
     // proximity and markers
     float *prox_clean = nullptr, *prox_noisy = nullptr;
     MarkerArgs markers{};
@@ -197,6 +197,10 @@ const char* make_params(const tg_params& p, ParamsDev* out) {
         }
     for (int i = 0; i < 9; ++i) d.xt_w[i] = (float)(w[i] / sum);
     d.seed = p.seed;
+    for (uint32_t r = 0; r < 10; ++r) {
+        d.rk[2 * r] = (uint32_t)p.seed + r * 0x9E3779B9u;
+        d.rk[2 * r + 1] = (uint32_t)(p.seed >> 32) + r * 0xBB67AE85u;
+    }
     d.depth = make_group(p.depth, p.dt);
     d.ft = make_group(p.ft, p.dt);
     d.prox = make_group(p.prox, p.dt);
@@ -458,7 +462,7 @@ tg_status tg_create_scene(const tg_scene_desc* d, tg_scene** out) {
     CKC(dalloc(&s->s_obj_id, E));
     CKC(dalloc(&s->s_mask, E));
     CKC(dalloc(&s->s_contact, T));
-    CKC(dalloc(&s->item_order, items.size()));
+    CKC(dalloc(&s->items_sorted, items.size()));
     CKC(dalloc(&s->ctl, 1));
     CKC(cudaMemset(s->ctl, 0, sizeof(StepCtl)));
     CKC(configure_step_kernels());
@@ -539,7 +543,7 @@ void tg_destroy_scene(tg_scene* s) {
                     s->hyst_xi, s->drift, s->episode, s->depth_clean, s->depth_noisy, s->dist, s->ft_clean,
                     s->ft_noisy, s->link_out, s->link_count, s->err, s->link_rec, s->s_link_pose, s->s_link_vel,
                     s->s_obj_pose, s->s_obj_vel, s->s_env_params, s->s_obj_id, s->s_mask, s->s_contact,
-                    s->item_order, s->prox_clean, s->prox_noisy, s->pad_link, s->pad_frame,
+                    s->items_sorted, s->prox_clean, s->prox_noisy, s->pad_link, s->pad_frame,
                     s->marker_u, s->ctl, s->nq_phi, s->nq_grad};
     for (void* p : ptrs) dfree(p);
     delete s;
@@ -774,10 +778,10 @@ tg_status enqueue_step(tg_scene* s, const tg_step_inputs* in, cudaStream_t st, b
     a.obj_id = oid;
     a.step = in->step;
     a.step_from_ctl = graph ? 1 : 0;
-    a.item_order = nullptr;
+    a.items_sorted = nullptr;
     if (s->sorted && s->n_objects > 1 && s->n_objects <= 12288) {
-        CK(s, launch_order_items(s->items, s->n_items, oid, s->n_objects, s->item_order, st));
-        a.item_order = s->item_order;
+        CK(s, launch_order_items(s->items, s->n_items, oid, s->n_objects, s->items_sorted, st));
+        a.items_sorted = s->items_sorted;
     }
     if (prof) CK(s, record(ev[1]));
     if (s->any_neural) CK(s, launch_nsdf_step_query(a, s->n_items, s->nq_phi, s->nq_grad, st));

@@ -46,6 +46,7 @@ struct ParamsDev {
     float chi;
     float xt_w[9];                        // L1-normalised 3x3 Gaussian, row-major
     uint64_t seed;
+    uint32_t rk[20];                  // Philox round keys of the seed: (k0, k1) + r (0x9E3779B9, 0xBB67AE85)
     NoiseDev depth, ft, prox;
     // proximity rays
     int prox_rays;
@@ -109,7 +110,7 @@ struct StepArgs {
     ParamsDev P;
     // per-step inputs (device)
     const int32_t* obj_id;
-    const int32_t* item_order;        // item of each CTA (object-sorted), or null
+    const Item* items_sorted;         // this step's items in object-sorted order, or null (items in env order)
 
     const float* link_rec;            // [E*L][kLinkRec] from the pose kernel
     uint32_t step;
@@ -188,8 +189,8 @@ cudaError_t configure_step_kernels();
 cudaError_t launch_set_ctl(StepCtl* ctl, StepCtl value, cudaStream_t s);
 cudaError_t launch_advance_ctl(StepCtl* ctl, cudaStream_t s);
 int step_kernel_resident_ctas();
-cudaError_t launch_order_items(const Item* items, int n_items, const int32_t* obj_id, int n_objects,
-                               int32_t* order, cudaStream_t s);
+cudaError_t launch_order_items(const Item* items, int n_items, const int32_t* obj_id, int n_objects, Item* sorted,
+                               cudaStream_t s);
 cudaError_t launch_reset(const StepArgs& a, int n_items, const uint8_t* env_mask, uint32_t episode,
                          uint32_t* episode_arr, cudaStream_t s);
 constexpr int kItemMaxLinksHost = 32;   // links per work item (matches the step kernel)

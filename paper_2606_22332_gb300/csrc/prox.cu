@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kProxThreads, 4) prox_kernel(const StepArgs a)
     __shared__ int start_s[kProxItemLinks + 1];
     __shared__ ObjDev obj_s;
     __shared__ unsigned int next_ray;
-    const Item it = a.items[a.item_order ? a.item_order[blockIdx.x] : blockIdx.x];
+    const Item it = a.items_sorted ? a.items_sorted[blockIdx.x] : a.items[blockIdx.x];
     const int e = it.env, L = a.max_links, lb = it.link_begin, nl = it.link_end - it.link_begin, n = it.n_taxels;
     const ParamsDev& P = a.P;
     const uint32_t step = a.step_from_ctl ? a.ctl->step : a.step;

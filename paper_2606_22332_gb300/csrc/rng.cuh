@@ -34,6 +34,24 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// The same generator with the ten round keys precomputed (rk[2r], rk[2r+1] =
+// the key after r bumps): each round XORs a key that is a kernel parameter.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t* rk) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 draw_rk(const uint32_t* rk, uint64_t gid, uint32_t word1, uint32_t tag) {
+    return philox4x32_10_rk(make_uint4((uint32_t)gid, word1, tag, (uint32_t)(gid >> 32)), rk);
+}
+
 // counter (taxel id low, step or episode, tag, taxel id high), key = seed
 __device__ __forceinline__ uint4 draw(uint64_t seed, uint64_t gid, uint32_t word1, uint32_t tag) {
     return philox4x32_10(make_uint4((uint32_t)gid, word1, tag, (uint32_t)(gid >> 32)), (uint32_t)seed,

@@ -60,7 +60,7 @@ __device__ __forceinline__ int uni_div(int i, float inv) { return (int)(((float)
 // One work item: every phase of the step for its taxels.
 template <int NT>
 __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int slot, uint32_t step) {
-    const Item it = a.items[a.item_order ? a.item_order[slot] : slot];
+    const Item it = a.items_sorted ? a.items_sorted[slot] : a.items[slot];
     const int e = it.env;
     const int L = a.max_links;
     const int lb = it.link_begin;
@@ -357,14 +357,36 @@ cudaError_t launch_advance_ctl(StepCtl* ctl, cudaStream_t s) {
 // CTAs launched together then read one or two object grids, which stay in L2
 // while the per-taxel state streams past.  Order within an object is
 // arbitrary; every item's result is independent of it.
-__global__ void order_items_kernel(const Item* items, int n_items, const int32_t* obj_id, int n_objects,
-                                   int32_t* order) {
-    extern __shared__ int cnt[];
+// Counting sort of the items by the object their env holds this step, into
+// a copy of the items (so a CTA reads its item with one load).  One CTA: the
+// items' objects are read once, a thread's items at once (their dependent
+// loads in flight together), and kept in shared memory when they fit
+// (cache != 0); the order within an object is that of the atomics (results do
+// not depend on it: every item is computed the same wherever it runs).
+__global__ void order_items_kernel(const Item* items, int n_items, const int32_t* obj_id, int n_objects, int cache,
+                                   Item* sorted) {
+    extern __shared__ int cnt[];  // [n_objects], then [n_items] uint16 objects when cached
+    uint16_t* oc = reinterpret_cast<uint16_t*>(cnt + n_objects);
     for (int k = threadIdx.x; k < n_objects; k += blockDim.x) cnt[k] = 0;
     __syncthreads();
-    for (int i = threadIdx.x; i < n_items; i += blockDim.x) {
-        const int k = min(max(obj_id[items[i].env], 0), n_objects - 1);
-        atomicAdd(&cnt[k], 1);
+    constexpr int U = 8;
+    for (int i0 = threadIdx.x; i0 < n_items; i0 += U * blockDim.x) {
+        int env[U], obj[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * blockDim.x;
+            env[u] = i < n_items ? items[i].env : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) obj[u] = env[u] >= 0 ? obj_id[env[u]] : 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i >= n_items) break;
+            const int k = min(max(obj[u], 0), n_objects - 1);
+            atomicAdd(&cnt[k], 1);
+            if (cache) oc[i] = (uint16_t)k;
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -377,15 +399,28 @@ __global__ void order_items_kernel(const Item* items, int n_items, const int32_t
     }
     __syncthreads();
     for (int i = threadIdx.x; i < n_items; i += blockDim.x) {
-        const int k = min(max(obj_id[items[i].env], 0), n_objects - 1);
-        order[atomicAdd(&cnt[k], 1)] = i;
+        const Item it = items[i];
+        const int k = cache ? (int)oc[i] : min(max(obj_id[it.env], 0), n_objects - 1);
+        sorted[atomicAdd(&cnt[k], 1)] = it;
     }
 }
 
-cudaError_t launch_order_items(const Item* items, int n_items, const int32_t* obj_id, int n_objects,
-                               int32_t* order, cudaStream_t s) {
+cudaError_t launch_order_items(const Item* items, int n_items, const int32_t* obj_id, int n_objects, Item* sorted,
+                               cudaStream_t s) {
     if (n_items == 0) return cudaSuccess;
-    order_items_kernel<<<1, 1024, (size_t)n_objects * sizeof(int), s>>>(items, n_items, obj_id, n_objects, order);
+    constexpr size_t kCap = 160 * 1024;
+    const size_t base = (size_t)n_objects * sizeof(int);
+    const size_t with_cache = base + (size_t)n_items * sizeof(uint16_t);
+    const int cache = with_cache <= kCap && n_objects <= 65535 ? 1 : 0;
+    const size_t smem = cache ? with_cache : base;
+    static size_t configured = 0;
+    if (smem > 48 * 1024 && smem > configured) {
+        const cudaError_t e = cudaFuncSetAttribute(order_items_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)kCap);
+        if (e != cudaSuccess) return e;
+        configured = kCap;
+    }
+    order_items_kernel<<<1, 1024, smem, s>>>(items, n_items, obj_id, n_objects, cache, sorted);
     return cudaGetLastError();
 }
 

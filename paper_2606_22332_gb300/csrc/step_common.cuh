@@ -176,7 +176,7 @@ __device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, i
     const bool dead = bits & BIT_DEAD;
     const float d = S.ag[0][i];
     uint4 wep = make_uint4(0, 0, 0, 0);
-    if (P.depth.gain_on | P.ft.gain_on) wep = draw(P.seed, gid, ep, TAG_EPISODE);
+    if (P.depth.gain_on | P.ft.gain_on) wep = draw_rk(P.rk, gid, ep, TAG_EPISODE);
     const float gain_d = P.depth.gain_on ? P.depth.gain_lo + P.depth.gain_span * u24(wep.y) : 1.0f;
     const float gain_f = P.ft.gain_on ? P.ft.gain_lo + P.ft.gain_span * u24(wep.z) : 1.0f;
     float xd = gain_d * d;
@@ -200,7 +200,7 @@ __device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, i
         for (int c = 0; c < 6; ++c) S.hx[c][i] = gain_f * S.fc[c][i];
     }
     if (P.depth.sigma_rw != 0.0f || P.depth.sigma_white != 0.0f) {
-        uint4 w = draw(P.seed, gid, step, TAG_SCALAR);
+        uint4 w = draw_rk(P.rk, gid, step, TAG_SCALAR);
         float2 z = box_muller(w.x, w.y);
         float dr = 0.0f;
         if (walk_d) {
@@ -212,7 +212,7 @@ __device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, i
         xd += P.depth.bias;
     }
     xd = quantise(P.depth, xd);
-    if (dead) xd = P.depth.stuck_lo + P.depth.stuck_span * u24(draw(P.seed, gid, ep, TAG_STUCK).x);
+    if (dead) xd = P.depth.stuck_lo + P.depth.stuck_span * u24(draw_rk(P.rk, gid, ep, TAG_STUCK).x);
     __stcs(a.depth_noisy + g, xd);
     S.ag[0][i] = d * n0; S.ag[1][i] = d * n1; S.ag[2][i] = d * n2;
     S.ag[3][i] = xd * n0; S.ag[4][i] = xd * n1; S.ag[5][i] = xd * n2;
@@ -291,13 +291,13 @@ __device__ __forceinline__ void noisy_ft(const StepArgs& a, const Smem& S, Out o
     }
     if (G.sigma_rw != 0.0f || G.sigma_white != 0.0f) {
         float nrm[12];
-        uint4 wa = draw(P.seed, gid, step, TAG_FT_A);
-        uint4 wb = draw(P.seed, gid, step, TAG_FT_B);
+        uint4 wa = draw_rk(P.rk, gid, step, TAG_FT_A);
+        uint4 wb = draw_rk(P.rk, gid, step, TAG_FT_B);
         float2 p0 = box_muller(wa.x, wa.y), p1 = box_muller(wa.z, wa.w);
         float2 p2 = box_muller(wb.x, wb.y);
         nrm[0] = p0.x; nrm[1] = p0.y; nrm[2] = p1.x; nrm[3] = p1.y; nrm[4] = p2.x; nrm[5] = p2.y;
         if (G.sigma_white != 0.0f) {
-            uint4 wc = draw(P.seed, gid, step, TAG_FT_C);
+            uint4 wc = draw_rk(P.rk, gid, step, TAG_FT_C);
             float2 p3 = box_muller(wb.z, wb.w), p4 = box_muller(wc.x, wc.y), p5 = box_muller(wc.z, wc.w);
             nrm[6] = p3.x; nrm[7] = p3.y; nrm[8] = p4.x; nrm[9] = p4.y; nrm[10] = p5.x; nrm[11] = p5.y;
         } else {
@@ -319,7 +319,7 @@ __device__ __forceinline__ void noisy_ft(const StepArgs& a, const Smem& S, Out o
     }
     const bool dead = bits & BIT_DEAD;
     float stuck = 0.0f;
-    if (dead) stuck = G.stuck_lo + G.stuck_span * u24(draw(P.seed, gid, ep, TAG_STUCK).y);
+    if (dead) stuck = G.stuck_lo + G.stuck_span * u24(draw_rk(P.rk, gid, ep, TAG_STUCK).y);
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
         float v = quantise(G, z[c]);
