@@ -175,3 +175,24 @@ def test_graph_replays_are_timed_one_by_one(tg):
     assert sc.profile_read()[2] == 2
     sc.graph_release()
     sc.close()
+
+
+def test_object_sort_beyond_the_cached_item_count_is_bit_identical(tg):
+    """90,000 single-link envs: more items than the ordering kernel keeps in
+    shared memory (2 bytes each within 160 KB), so it re-reads each item's
+    object; the sorted schedule must give the unsorted results bit for bit."""
+    wl = W.config1(n_envs=90000, n_links=1, rows=2, cols=4, n_objects=4, n_grid=24, steps=2)
+    wl.objects = bake_objects_oracle(wl.objects)
+    assert wl.n_envs * 2 + 4 * 4 > 160 * 1024
+    outs = []
+    for sorted_ in (False, True):
+        sc = tg.Scene.from_workload(wl)
+        sc.upload_objects(wl.objects)
+        sc.set_schedule(persistent=False, sorted=sorted_)
+        for s in range(2):
+            sc.step(wl.inputs(s))
+        outs.append(_all_channels(tg, sc))
+        sc.close()
+    assert float((outs[0][1] > 0).mean()) > 0.01  # some taxels penetrate
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
