@@ -75,6 +75,7 @@ class ORParams(C.Structure):
         ("chi", C.c_double), ("xt_sigma", C.c_double),
         ("prox_rays", C.c_int32), ("prox_range", C.c_double), ("prox_cone", C.c_double),
         ("dr_on", C.c_int32), ("dr_mu", C.c_double * 2), ("dr_k", C.c_double * 2), ("dr_scale", C.c_double * 2),
+        ("rho", C.c_double),
     ]
 
 
@@ -437,6 +438,7 @@ def make_params(p: dict) -> ORParams:
     P.prox_rays = int(p.get("prox_rays", 0))
     P.prox_range = float(p.get("prox_range", 0.05))
     P.prox_cone = float(p.get("prox_cone", np.radians(30.0)))
+    P.rho = float(p.get("rho", 0.0))
     dr = p.get("dr")
     P.dr_on = 1 if dr else 0
     if dr:

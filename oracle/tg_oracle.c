@@ -73,6 +73,7 @@ enum {
     TAG_FT_B = 17,    /* normals: drift ty tz, white fx fy */
     TAG_FT_C = 18,    /* normals: white fz tx ty tz */
     TAG_SCALAR = 19,  /* normals: drift depth, white depth, drift prox, white prox */
+    TAG_RADIUS = 20,  /* w0: probe-radius noise */
     TAG_DR = 32       /* per-env domain randomisation */
 };
 
@@ -80,6 +81,18 @@ static void philox_draw(uint64_t seed, uint64_t gid, uint32_t word1, uint32_t ta
     uint32_t ctr[4] = {(uint32_t)gid, word1, tag, (uint32_t)(gid >> 32)};
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     or_philox4x32_10(ctr, key, out);
+}
+
+/* Probe-radius noise offset (Appendix "Sensor Noise Model", probe-level
+   imperfections): eps = rho (2u - 1), u the 24-bit uniform of word w.  It is
+   formed in binary32 -- u as (float)(w >> 8) + 1/2 rounded, times 2^-24;
+   2u - 1 is then exact; one rounding of the product -- so that every
+   implementation forms the same value. */
+static float radius_eps(double rho, uint32_t w) {
+    volatile float u = ((float)(w >> 8) + 0.5f) * 5.9604644775390625e-08f;
+    volatile float s = 2.0f * u - 1.0f;
+    volatile float e = (float)rho * s;
+    return e;
 }
 
 static void philox_normals(uint64_t seed, uint64_t gid, uint32_t step, uint32_t tag, double z[4]) {
@@ -833,7 +846,7 @@ static void env_step(const or_scene* S, const or_inputs* in, or_state* st, or_ou
 
     /* per-taxel scratch in clean order */
     double* hx = (double*)calloc((size_t)n * 6, sizeof(double)); /* x~ of force/torque after hysteresis */
-    double* fclean = (double*)calloc((size_t)n * 6, sizeof(double));
+    double* fclean = (double*)calloc((size_t)n * 6, sizeof(double));  /* force entering the noise chain */
     int* active = (int*)calloc((size_t)n, sizeof(int));
 
     uint32_t episode = st->episode[e];
@@ -883,14 +896,30 @@ static void env_step(const or_scene* S, const or_inputs* in, or_state* st, or_ou
             /* Eq. 3 */
             int prev = st->flags[j] & 1;
             int y = or_schmitt(prev, d, P->eta_on, P->eta_off);
-            st->flags[j] = (uint8_t)((st->flags[j] & ~1u) | (unsigned)y);
             int dead = (st->flags[j] >> 1) & 1;
+            /* the noisy readout's depth: with probe-radius noise, from the
+               perturbed radius, with its own Schmitt state (flag bit 2, the
+               last noisy contact bit); without it, the clean depth */
+            double dn = d;
+            int yn = y && !dead;
+            if (P->rho > 0.0) {
+                uint32_t wr[4];
+                philox_draw(P->seed, gid, in->step, TAG_RADIUS, wr);
+                double Rn = R + (double)radius_eps(P->rho, wr[0]);
+                if (Rn < 0.0) Rn = 0.0;
+                dn = Rn - phi;
+                if (dn < 0.0) dn = 0.0;
+                int ys = or_schmitt((st->flags[j] >> 2) & 1, dn, P->eta_on, P->eta_off);
+                yn = ys && !dead;
+            }
+            st->flags[j] = (uint8_t)((st->flags[j] & 2u) | (unsigned)y | ((unsigned)yn << 2));
             out->contact_clean[j] = (uint8_t)y;
-            out->contact_noisy[j] = (uint8_t)(y && !dead);
+            out->contact_noisy[j] = (uint8_t)yn;
             out->depth_clean[j] = d;
 
             double f[3] = {0, 0, 0}, tau[3] = {0, 0, 0};
-            if (d > 0.0) {
+            double fn[3] = {0, 0, 0}, taun[3] = {0, 0, 0};  /* the force the noise chain starts from */
+            if (d > 0.0 || dn > 0.0) {
                 /* Eqs. 4-6: point velocities and link-frame relative velocity */
                 double rC[3], rL[3], vCq[3], vLq[3], tmp[3], vrel[3];
                 sub3(q, pC, rC); sub3(q, pL, rL);
@@ -902,9 +931,14 @@ static void env_step(const or_scene* S, const or_inputs* in, or_state* st, or_ou
                 matTvec(RL, tmp, vrel);
                 double dw[3];
                 sub3(wC, wL, dw);
-                or_taxel_force(P, k, mu, d, x, mbar, vrel, dot3(dw, m), f, tau);
+                if (d > 0.0) or_taxel_force(P, k, mu, d, x, mbar, vrel, dot3(dw, m), f, tau);
+                if (P->rho > 0.0) {
+                    if (dn > 0.0) or_taxel_force(P, k, mu, dn, x, mbar, vrel, dot3(dw, m), fn, taun);
+                } else {
+                    for (int a = 0; a < 3; ++a) { fn[a] = f[a]; taun[a] = tau[a]; }
+                }
             }
-            for (int a = 0; a < 3; ++a) { fclean[jl * 6 + a] = f[a]; fclean[jl * 6 + 3 + a] = tau[a]; }
+            for (int a = 0; a < 3; ++a) { fclean[jl * 6 + a] = fn[a]; fclean[jl * 6 + 3 + a] = taun[a]; }
             for (int a = 0; a < 3; ++a) { out->ft_clean[(size_t)a * T + j] = f[a]; out->ft_clean[(size_t)(3 + a) * T + j] = tau[a]; }
 
             /* noise: per-probe gains for this episode */
@@ -913,7 +947,7 @@ static void env_step(const or_scene* S, const or_inputs* in, or_state* st, or_ou
             double gain_d = group_gain_on(&P->depth) ? P->depth.gain_lo + (P->depth.gain_hi - P->depth.gain_lo) * or_uniform(we[1]) : 1.0;
             double gain_f = group_gain_on(&P->ft) ? P->ft.gain_lo + (P->ft.gain_hi - P->ft.gain_lo) * or_uniform(we[2]) : 1.0;
             /* depth: gain, hysteresis, base noise, dead */
-            double hd = gain_hysteresis(&P->depth, P->dt, gain_d, d, &st->hyst_prev[j], &st->hyst_xi[j]);
+            double hd = gain_hysteresis(&P->depth, P->dt, gain_d, dn, &st->hyst_prev[j], &st->hyst_xi[j]);
             double zs[4];
             philox_normals(P->seed, gid, in->step, TAG_SCALAR, zs);
             uint32_t wst[4];

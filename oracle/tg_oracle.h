@@ -84,6 +84,10 @@ typedef struct {
        mu, k and the object scale uniform on [lo, hi] (index 0 lo, 1 hi) */
     int32_t dr_on;
     double dr_mu[2], dr_k[2], dr_scale[2];
+    /* probe-radius noise (0 = off): the noisy readout of a taxel sees the
+       radius max(0, R + eps), eps uniform on [-rho, rho], drawn per taxel and
+       step (the clean readout keeps R) */
+    double rho;
 } or_params;
 
 /* elastomer marker pads (ElastomerTaxel dilation, Eqs. 18-21) */
