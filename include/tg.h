@@ -102,6 +102,15 @@ typedef struct {
     /* largest probe error (mm, at the largest object scale) for which a
        NEURAL object's network is used instead of its grid (0.2) */
     double nsdf_max_err_mm;
+    /* probe-radius noise rho (m, 0 = off; at most 5e-4): the noisy readout
+       of a taxel sees the radius max(0, R + eps), eps = rho (2u - 1) with u
+       the 24-bit uniform of word 0 of Philox at counter (global taxel id,
+       step, tag 20, taxel id high), formed in binary32 (Appendix "Sensor Noise
+       Model", probe-level imperfections).  The noisy depth, the force the
+       force/torque noise chain starts from and the noisy contact bit (its
+       own Schmitt state) use that radius; the clean readout keeps R, and the
+       proximity rays do not depend on it. */
+    double probe_radius_noise;
 } tg_params;
 
 /* sensor mask bits (depth, contact and force/torque are always computed) */

@@ -163,6 +163,8 @@ const char* make_params(const tg_params& p, ParamsDev* out) {
     if (p.p_dead < 0.0 || p.p_dead > 1.0) return "p_dead outside [0, 1]";
     if (!(p.alpha > 0.0)) return "alpha must be positive";
     if (p.chi != 0.0 && !(p.xt_sigma > 0.0)) return "crosstalk needs xt_sigma > 0";
+    if (!finite(p.probe_radius_noise) || p.probe_radius_noise < 0.0 || p.probe_radius_noise > 5e-4)
+        return "probe_radius_noise must be in [0, 5e-4] m";
     if (p.prox_rays < 0 || p.prox_rays > 16 || !finite(p.prox_range) || !finite(p.prox_cone))
         return "prox_rays must be in 0..16 with finite range and cone";
     if (p.dr_on) {
@@ -197,6 +199,7 @@ const char* make_params(const tg_params& p, ParamsDev* out) {
         }
     for (int i = 0; i < 9; ++i) d.xt_w[i] = (float)(w[i] / sum);
     d.seed = p.seed;
+    d.rho = (float)p.probe_radius_noise;
     for (uint32_t r = 0; r < 10; ++r) {
         d.rk[2 * r] = (uint32_t)p.seed + r * 0x9E3779B9u;
         d.rk[2 * r + 1] = (uint32_t)(p.seed >> 32) + r * 0xBB67AE85u;

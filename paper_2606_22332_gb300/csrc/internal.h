@@ -47,6 +47,7 @@ struct ParamsDev {
     float xt_w[9];                        // L1-normalised 3x3 Gaussian, row-major
     uint64_t seed;
     uint32_t rk[20];                  // Philox round keys of the seed: (k0, k1) + r (0x9E3779B9, 0xBB67AE85)
+    float rho;                        // probe-radius noise half-width (m), 0 = off
     NoiseDev depth, ft, prox;
     // proximity rays
     int prox_rays;

@@ -481,7 +481,7 @@ __global__ void __launch_bounds__(kInferThreads) nsdf_step_query_kernel(const St
                 const float p = S.scale[threadIdx.x] * (1e-3f * S.out[threadIdx.x] + S.ext[threadIdx.x]);
                 phi_out[g] = p;
                 const float R = a.R[g];
-                if (R > 0.0f && p < R + 1e-6f) {
+                if (R > 0.0f && p < R + 1e-6f + a.P.rho) {  // (the noisy radius reaches R + rho)
                     const int k = atomicAdd(&ncq, 1);
                     cq_g[k] = g;
                     cq_pt[k][0] = S.q[threadIdx.x][0];

@@ -17,6 +17,7 @@ enum : uint32_t {
     TAG_FT_B = 17,    // normals: drift ty tz, white fx fy
     TAG_FT_C = 18,    // normals: white fz tx ty tz
     TAG_SCALAR = 19,  // normals: drift depth, white depth, drift prox, white prox
+    TAG_RADIUS = 20,  // w0: probe-radius noise
     TAG_DR = 32       // per-env domain randomisation
 };
 

@@ -58,7 +58,7 @@ struct SmemStep {
 __device__ __forceinline__ int uni_div(int i, float inv) { return (int)(((float)i + 0.5f) * inv); }
 
 // One work item: every phase of the step for its taxels.
-template <int NT>
+template <int NT, bool RADIUS>
 __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int slot, uint32_t step) {
     const Item it = a.items_sorted ? a.items_sorted[slot] : a.items[slot];
     const int e = it.env;
@@ -163,7 +163,8 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
             const int64_t g = u ? g1 : g0;
             const float R = u ? R1 : R0, phi = u ? phi1 : phi0;
             if (R > 0.0f && !isfinite(phi)) atomicAdd(a.err, 1u);
-            if (R > 0.0f && phi < R + 1e-6f) {
+            // (with probe-radius noise the noisy readout's radius reaches R + rho)
+            if (R > 0.0f && phi < R + 1e-6f + (RADIUS ? a.P.rho : 0.0f)) {
                 S.queue[atomicAdd(&S.nq, 1)] = (int16_t)i;
                 // A2's inputs, kept on chip (hx is not used before phase N)
                 float* st = &S.hx[0][0];
@@ -194,9 +195,9 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
             else hi = mid - 1;
         }
         const float* st = &S.hx[0][0];
-        const CleanReading cr = refine_taxel(a, S.rec[lo], obj, it.taxel_begin + i, st[i], st[kItemCap + i],
+        const CleanReading cr = refine_taxel<RADIUS>(a, S.rec[lo], obj, it.taxel_begin + i, st[i], st[kItemCap + i],
                                              st[2 * kItemCap + i], st[3 * kItemCap + i],
-                                             (uint8_t)__float_as_uint(st[4 * kItemCap + i]));
+                                             (uint8_t)__float_as_uint(st[4 * kItemCap + i]), step);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             S.fc[c][i] = cr.f[c];
@@ -204,6 +205,14 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
         }
         S.ag[0][i] = cr.d;
         S.bits[i] = cr.bits;
+        if constexpr (RADIUS) {  // the noisy chain's depth and force, for phase N (slots free until then)
+            S.ag[1][i] = cr.dn;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                S.hx[c][i] = cr.fn[c];
+                S.hx[3 + c][i] = cr.tqn[c];
+            }
+        }
     }
     __syncthreads();
 
@@ -211,7 +220,7 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
     for (int i = tid; i < n; i += NT) {
         const int64_t g = it.taxel_begin + i;
         const uint8_t bits = S.bits[i];
-        if (bits & BIT_ACTIVE) noise_state(a, S, i, g, ep, step, bits);
+        if (bits & BIT_ACTIVE) noise_state<RADIUS>(a, S, i, g, ep, step, bits);
         else noise_state_filler(a, S, i, g);
     }
     __syncthreads();
@@ -253,13 +262,13 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
 // Grid schedule: CTA b runs item slot b.  Persistent schedule: a grid sized
 // to the resident CTAs takes item slots from an atomic counter (zeroed
 // before the launch) until none are left.
-template <int NT, bool PERSISTENT>
+template <int NT, bool PERSISTENT, bool RADIUS>
 __global__ void __launch_bounds__(NT, kStepMinBlocks) step_kernel(const StepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmemStep& S = *reinterpret_cast<SmemStep*>(smem_raw);
     const uint32_t step = a.step_from_ctl ? a.ctl->step : a.step;
     if (!PERSISTENT) {
-        step_item<NT>(a, S, blockIdx.x, step);
+        step_item<NT, RADIUS>(a, S, blockIdx.x, step);
         return;
     }
     for (;;) {
@@ -267,7 +276,7 @@ __global__ void __launch_bounds__(NT, kStepMinBlocks) step_kernel(const StepArgs
         __syncthreads();
         const int slot = (int)S.slot;
         if (slot >= a.n_items) break;
-        step_item<NT>(a, S, slot, step);
+        step_item<NT, RADIUS>(a, S, slot, step);
         __syncthreads();  // shared memory is reused by the next item
     }
 }
@@ -302,18 +311,22 @@ __global__ void unpack_contact_kernel(const uint8_t* flags, int64_t n, int noisy
 
 cudaError_t configure_step_kernels() {
     const int smem = (int)sizeof(SmemStep);
-    cudaError_t err = cudaFuncSetAttribute(step_kernel<kStepThreads, false>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (err == cudaSuccess)
-        err = cudaFuncSetAttribute(step_kernel<kStepThreads, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    return err;
+    const void* k[4] = {(const void*)step_kernel<kStepThreads, false, false>,
+                        (const void*)step_kernel<kStepThreads, true, false>,
+                        (const void*)step_kernel<kStepThreads, false, true>,
+                        (const void*)step_kernel<kStepThreads, true, true>};
+    for (const void* f : k) {
+        const cudaError_t err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
 }
 
 int step_kernel_resident_ctas() {
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<kStepThreads, true>, kStepThreads,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<kStepThreads, true, false>, kStepThreads,
                                                       sizeof(SmemStep)) != cudaSuccess)
         return 0;
     return sms * per_sm;
@@ -328,9 +341,11 @@ cudaError_t launch_step(const StepArgs& a, int n_items, cudaStream_t s) {
         if (ctas <= 0) return cudaErrorInvalidConfiguration;
         cudaError_t err = cudaMemsetAsync(&a.ctl->counter, 0, sizeof(uint32_t), s);
         if (err != cudaSuccess) return err;
-        step_kernel<kStepThreads, true><<<min(ctas, n_items), kStepThreads, smem, s>>>(a);
+        if (a.P.rho > 0.0f) step_kernel<kStepThreads, true, true><<<min(ctas, n_items), kStepThreads, smem, s>>>(a);
+        else step_kernel<kStepThreads, true, false><<<min(ctas, n_items), kStepThreads, smem, s>>>(a);
     } else {
-        step_kernel<kStepThreads, false><<<n_items, kStepThreads, smem, s>>>(a);
+        if (a.P.rho > 0.0f) step_kernel<kStepThreads, false, true><<<n_items, kStepThreads, smem, s>>>(a);
+        else step_kernel<kStepThreads, false, false><<<n_items, kStepThreads, smem, s>>>(a);
     }
     return cudaGetLastError();
 }

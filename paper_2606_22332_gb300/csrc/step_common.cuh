@@ -70,6 +70,9 @@ __device__ __forceinline__ uint8_t clear_taxel(const StepArgs& a, int64_t g, flo
 struct CleanReading {
     float d;
     float f[3], tq[3];
+    // with probe-radius noise: the depth and force the noisy chain starts from
+    float dn;
+    float fn[3], tqn[3];
     uint8_t bits;
 };
 
@@ -77,10 +80,13 @@ struct CleanReading {
 // R and last step's flag byte: compensated query point and SDF (near-contact
 // depths carry ~1e-14 relative error), depth, Schmitt decision on the
 // compensated depth, force/torque; writes the clean outputs and the new flag
-// byte.
+// byte.  With probe-radius noise the noisy readout's radius max(0, R + eps)
+// gives a second depth, its own Schmitt decision (flag bit 2) and a second
+// force (same normal and velocities).
+template <bool RADIUS>  // probe-radius noise on (rho > 0)
 __device__ __forceinline__ CleanReading refine_taxel(const StepArgs& a, const float* rec, const ObjDev& obj,
                                                      int64_t g, float x0, float x1, float x2, float R,
-                                                     uint8_t flags) {
+                                                     uint8_t flags, uint32_t step) {
     const ParamsDev& P = a.P;
     const int64_t T = a.n_taxels;
     df qd[3];
@@ -105,15 +111,28 @@ __device__ __forceinline__ CleanReading refine_taxel(const StepArgs& a, const fl
     const df dd = df_add_f(df_neg(phid), R);  // R - phi
     CleanReading out;
     out.d = dd.hi > 0.0f ? dd.hi : 0.0f;
+    const df eta_on = df{P.eta_on_hi, P.eta_on_lo}, eta_off = df{P.eta_off_hi, P.eta_off_lo};
     const bool prev = flags & 1u;
-    const bool y = df_gt(dd, df{P.eta_on_hi, P.eta_on_lo}) || (prev && df_gt(dd, df{P.eta_off_hi, P.eta_off_lo}));
+    const bool y = df_gt(dd, eta_on) || (prev && df_gt(dd, eta_off));
     const bool dead = flags & 2u;
-    const bool yn = y && !dead;
+    bool yn = y && !dead;
+    out.dn = out.d;
+    if constexpr (RADIUS) {
+        // eps = rho (2u - 1) in binary32 (2u - 1 is exact); R + eps exact as a pair
+        const float u = u24(draw_rk(P.rk, (uint64_t)(a.gid0 + g), step, TAG_RADIUS).x);
+        const float eps = P.rho * (2.0f * u - 1.0f);
+        df Rn = df_add_f(df_from(R), eps);
+        if (df_lt(Rn, df_from(0.0f))) Rn = df_from(0.0f);
+        const df ddn = df_add(df_neg(phid), Rn);  // R~ - phi
+        out.dn = ddn.hi > 0.0f ? ddn.hi : 0.0f;
+        const bool prevn = flags & 4u;
+        yn = (df_gt(ddn, eta_on) || (prevn && df_gt(ddn, eta_off))) && !dead;
+    }
     __stcs(a.flags + g, (uint8_t)((y ? 1u : 0u) | (flags & 2u) | (yn ? 4u : 0u)));
 #pragma unroll
-    for (int c = 0; c < 3; ++c) { out.f[c] = 0.f; out.tq[c] = 0.f; }
-    const float d = out.d;
-    if (d > 0.0f) {
+    for (int c = 0; c < 3; ++c) { out.f[c] = 0.f; out.tq[c] = 0.f; out.fn[c] = 0.f; out.tqn[c] = 0.f; }
+    const float d = out.d, dn = out.dn;
+    if (d > 0.0f || (RADIUS && dn > 0.0f)) {
         const float3 mb = normalize_or(f3(rec[0] * go.x + rec[3] * go.y + rec[6] * go.z,
                                           rec[1] * go.x + rec[4] * go.y + rec[7] * go.z,
                                           rec[2] * go.x + rec[5] * go.y + rec[8] * go.z),
@@ -122,19 +141,25 @@ __device__ __forceinline__ CleanReading refine_taxel(const StepArgs& a, const fl
         const float3 V = f3(rec[24], rec[25], rec[26]), Wc = f3(rec[27], rec[28], rec[29]);
         const float3 Wl = f3(rec[30], rec[31], rec[32]), pLC = f3(rec[33], rec[34], rec[35]);
         const float3 vrel = V + cross(Wc, xv - pLC) - cross(Wl, xv);
-        const float s = (P.alpha == 1.0f) ? d : powf(d, P.alpha);
         const float kk = rec[36], mu = rec[37];
         const float vns = dot(vrel, mb);
         const float3 vn = mb * vns;
         const float3 vt = vrel - vn;
-        const float3 fn = mb * (kk * s) + vn * (P.c * s);
         const float vtn = sqrtf(dot(vt, vt));
-        float sc = 1.0f;
-        if (mu >= 0.0f && P.k_t * vtn > 0.0f) sc = fminf(1.0f, mu * sqrtf(dot(fn, fn)) / (P.k_t * vtn));
-        const float3 ff = fn - vt * (P.k_t * sc);
-        const float3 tt = cross(xv, ff) - mb * (P.k_omega * dot(Wc - Wl, mb));
-        out.f[0] = ff.x; out.f[1] = ff.y; out.f[2] = ff.z;
-        out.tq[0] = tt.x; out.tq[1] = tt.y; out.tq[2] = tt.z;
+        const float spin = P.k_omega * dot(Wc - Wl, mb);
+        // Eqs. 4-9 with the Coulomb clamp at depth dep
+        auto force = [&](float dep, float* f, float* tq) {
+            const float s = (P.alpha == 1.0f) ? dep : powf(dep, P.alpha);
+            const float3 fnv = mb * (kk * s) + vn * (P.c * s);
+            float sc = 1.0f;
+            if (mu >= 0.0f && P.k_t * vtn > 0.0f) sc = fminf(1.0f, mu * sqrtf(dot(fnv, fnv)) / (P.k_t * vtn));
+            const float3 ff = fnv - vt * (P.k_t * sc);
+            const float3 tt = cross(xv, ff) - mb * spin;
+            f[0] = ff.x; f[1] = ff.y; f[2] = ff.z;
+            tq[0] = tt.x; tq[1] = tt.y; tq[2] = tt.z;
+        };
+        if (d > 0.0f) force(d, out.f, out.tq);
+        if (RADIUS && dn > 0.0f) force(dn, out.fn, out.tqn);
     }
     __stcs(a.depth_clean + g, d);
     if (a.sensors & TG_SENSOR_DIST) __stcs(a.dist + g, -dd.hi);
@@ -143,7 +168,8 @@ __device__ __forceinline__ CleanReading refine_taxel(const StepArgs& a, const fl
         __stcs(a.ft_clean + c * T + g, out.f[c]);
         __stcs(a.ft_clean + (3 + c) * T + g, out.tq[c]);
     }
-    out.bits = (uint8_t)((y ? BIT_CLEAN : 0u) | (yn ? BIT_NOISY : 0u) | (dead ? BIT_DEAD : 0u) | BIT_ACTIVE);
+    out.bits = (uint8_t)((y ? BIT_CLEAN : 0u) | (yn ? BIT_NOISY : 0u) | (dead ? BIT_DEAD : 0u) | BIT_ACTIVE |
+                         (RADIUS ? BIT_NEAR : 0u));
     return out;
 }
 
@@ -152,7 +178,7 @@ __device__ __forceinline__ CleanReading refine_taxel(const StepArgs& a, const fl
 // and all of them are issued before the first store: the compiler cannot move
 // a load above a store to a pointer that may alias it, and every such barrier
 // would cost a further round trip to memory.
-template <class Smem>
+template <bool RADIUS, class Smem>
 __device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, int64_t g, uint32_t ep, uint32_t step,
                                             uint8_t bits) {
     const ParamsDev& P = a.P;
@@ -175,11 +201,23 @@ __device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, i
     const uint64_t gid = (uint64_t)(a.gid0 + g);
     const bool dead = bits & BIT_DEAD;
     const float d = S.ag[0][i];
+    // the depth and force the noisy chain starts from: the clean ones, or with
+    // probe-radius noise those of the perturbed radius (refined taxels; the
+    // others are clear of it)
+    float d_in = d, f_in[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) f_in[c] = S.fc[c][i];
+    if constexpr (RADIUS) {
+        const bool near = bits & BIT_NEAR;
+        d_in = near ? S.ag[1][i] : 0.0f;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) f_in[c] = near ? S.hx[c][i] : 0.0f;
+    }
     uint4 wep = make_uint4(0, 0, 0, 0);
     if (P.depth.gain_on | P.ft.gain_on) wep = draw_rk(P.rk, gid, ep, TAG_EPISODE);
     const float gain_d = P.depth.gain_on ? P.depth.gain_lo + P.depth.gain_span * u24(wep.y) : 1.0f;
     const float gain_f = P.ft.gain_on ? P.ft.gain_lo + P.ft.gain_span * u24(wep.z) : 1.0f;
-    float xd = gain_d * d;
+    float xd = gain_d * d_in;
     if (hyst_d) {
         const float xi = P.depth.decay * xi_d + (xd - prev_d);
         __stcs(a.hyst_xi + g, xi);
@@ -189,7 +227,7 @@ __device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, i
     if (hyst_f) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            const float x = gain_f * S.fc[c][i];
+            const float x = gain_f * f_in[c];
             const float xi = P.ft.decay * xv[c] + (x - pv[c]);
             __stcs(a.hyst_xi + (1 + c) * T + g, xi);
             __stcs(a.hyst_prev + (1 + c) * T + g, x);
@@ -197,7 +235,7 @@ __device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, i
         }
     } else {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) S.hx[c][i] = gain_f * S.fc[c][i];
+        for (int c = 0; c < 6; ++c) S.hx[c][i] = gain_f * f_in[c];
     }
     if (P.depth.sigma_rw != 0.0f || P.depth.sigma_white != 0.0f) {
         uint4 w = draw_rk(P.rk, gid, step, TAG_SCALAR);

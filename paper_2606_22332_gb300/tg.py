@@ -51,7 +51,7 @@ class Params(C.Structure):
         ("seed", C.c_uint64), ("depth", NoiseGroup), ("ft", NoiseGroup), ("prox", NoiseGroup),
         ("prox_rays", C.c_int32), ("prox_range", C.c_double), ("prox_cone", C.c_double),
         ("dr_on", C.c_int32), ("dr_mu", C.c_double * 2), ("dr_k", C.c_double * 2), ("dr_scale", C.c_double * 2),
-        ("nsdf_max_err_mm", C.c_double)]
+        ("nsdf_max_err_mm", C.c_double), ("probe_radius_noise", C.c_double)]
 
 
 class PadDesc(C.Structure):
@@ -198,6 +198,7 @@ def _fill_params(params: dict) -> Params:
             getattr(P, "dr_" + k)[0] = float(dr[k][0])
             getattr(P, "dr_" + k)[1] = float(dr[k][1])
     P.nsdf_max_err_mm = float(params.get("nsdf_max_err_mm", 0.2))
+    P.probe_radius_noise = float(params.get("rho", 0.0))
     for g in ("depth", "ft", "prox"):
         grp = getattr(P, g)
         for k in NoiseGroup._fields_:

@@ -192,3 +192,42 @@ def test_maximum_sizes(tg):
                      max_links=34, arc=W.PAD_ARC, press_frac=(1.0, 1.0), press_depth=(0.5e-3, 2.5e-3))
     stats = run_both(tg, wl, steps=3)
     print("maxsize", stats[-1])
+
+
+@pytest.mark.parametrize("case", ["config0", "grid16", "paper_noisy"])
+def test_probe_radius_noise(tg, case):
+    """Probe-radius noise (rho): the noisy readout's depth, contact bit and
+    force/torque from max(0, R + eps) against the oracle, every query."""
+    if case == "config0":
+        wl = W.config0(seed=31, n_envs=12)
+        wl.params = dict(wl.params, rho=3e-4)
+        sensors = tg.TG_SENSOR_DIST
+    elif case == "grid16":
+        wl = W.config1(n_envs=16, n_objects=3, n_grid=24, steps=4)
+        wl.objects = bake_objects_oracle(wl.objects)
+        wl.params = dict(wl.params, rho=5e-4)
+        sensors = 0
+    else:
+        p = W.default_params(9)
+        p.update(alpha=1.2, k=500.0, c=1.0, mu=None, rho=3e-4, p_dead=0.05)
+        p["noise"]["depth"] = W.noise_group(beta=0.5, tau=0.05, sigma_white=2e-4, quant=1e-4, gain_lo=0.85,
+                                            gain_hi=1.15)
+        p["noise"]["ft"] = W.noise_group(beta=0.5, tau=0.05, sigma_white=5e-3, sigma_rw=1e-4, gain_lo=0.85,
+                                         gain_hi=1.15, stuck_lo=-0.1, stuck_hi=0.1)
+        wl = W.config0(seed=78, n_envs=10)
+        wl.params = p
+        sensors = 0
+    stats = run_both(tg, wl, steps=3, sensors=sensors)
+    print(case, stats[-1])
+
+
+def test_probe_radius_noise_bounds_are_checked(tg):
+    wl = W.config0(seed=32, n_envs=2)
+    for bad in (-1e-6, 6e-4, float("nan")):
+        with pytest.raises(tg.TGError):
+            tg.Scene.from_workload(dict_params(wl, rho=bad))
+
+
+def dict_params(wl, **over):
+    wl.params = dict(wl.params, **over)
+    return wl
