@@ -62,8 +62,12 @@ def compare_step(gpu, ora, ostate, params, wl, active=None, where="", tol=None, 
     # contact bits, with the threshold band
     d_or = ora["depth_clean"]
     band = (np.abs(d_or - params["eta_on"]) < BAND_) | (np.abs(d_or - params["eta_off"]) < BAND_)
-    for k in ("contact_clean", "contact_noisy"):
-        bad = (gpu[k] != ora[k]) & ~band
+    # the noisy bit decides on the noisy readout's depth (with probe-radius noise up to rho from the
+    # clean one): tol["band_noisy"] widens its band where the path's phi carries a stated error
+    bn = t.get("band_noisy", BAND_)
+    band_n = (np.abs(d_or - params["eta_on"]) < bn) | (np.abs(d_or - params["eta_off"]) < bn)
+    for k, b in (("contact_clean", band), ("contact_noisy", band_n)):
+        bad = (gpu[k] != ora[k]) & ~b
         assert not bad.any(), f"{where}: {k} differs at {np.flatnonzero(bad)[:10]}"
     nb = int(((gpu["contact_clean"] != ora["contact_clean"]) & band).sum())
     assert nb <= max(1, 1e-4 * n_act), f"{where}: {nb} banded contact mismatches"

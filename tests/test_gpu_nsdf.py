@@ -136,9 +136,11 @@ def _neural_workload(rng, out_scale=2.0):
     return wl
 
 
-def test_scene_step_with_a_neural_object_matches_oracle(tg):
+@pytest.mark.parametrize("rho", [0.0, 3e-4])
+def test_scene_step_with_a_neural_object_matches_oracle(tg, rho):
     rng = np.random.default_rng(13)
     wl = _neural_workload(rng)
+    wl.params = dict(wl.params, rho=rho)  # probe-radius noise: noisy depths within rho of the clean ones
     on = oracle_nsdf(wl.objects[0].nsdf_lo, wl.objects[0].nsdf_hi, wl.objects[0].nsdf_table,
                      wl.objects[0].nsdf_weights)
     # the phi tolerance of this network: four flips at the worst of 20k box points; the contact
@@ -152,7 +154,8 @@ def test_scene_step_with_a_neural_object_matches_oracle(tg):
     # normals jump where the stencil straddles a hash-grid cell face or ReLU kink: a taxel whose
     # stencil points sit within rounding of one may take either side's value (counted, not failed)
     tol = {"d_abs": max(d_tol, 1e-5), "band": d_tol, "f_rel": max(1e-3, 2 * n_rel),
-           "f_abs": 4 * wl.params["k"] * d_tol + 1e-6, "agg_d": d_tol, "f_outliers": 0.005}
+           "f_abs": 4 * wl.params["k"] * d_tol + 1e-6, "agg_d": d_tol, "f_outliers": 0.005,
+           "band_noisy": d_tol + rho}
     sc = tg.Scene.from_workload(wl, sensors=tg.TG_SENSOR_DIST)
     sc.upload_objects(wl.objects)
     assert sc.object_info(0)[0] == tg.TG_OBJ_NEURAL and sc.object_info(1)[0] == tg.TG_OBJ_GRID
