@@ -86,6 +86,11 @@ class ORPads(C.Structure):
                 ("eps", C.c_double), ("radius", C.c_int32)]
 
 
+class ORPcProx(C.Structure):
+    _fields_ = [("cloud", C.c_void_p), ("cloud_off", C.c_void_p), ("radius", C.c_double), ("k", C.c_double),
+                ("ks", C.c_double), ("density", C.c_double)]
+
+
 class ORScene(C.Structure):
     _fields_ = [
         ("n_envs", C.c_int32), ("max_links", C.c_int32),
@@ -169,6 +174,8 @@ def lib():
             L.or_marker_kernel_g.restype = C.c_double
             L.or_markers.argtypes = [C.POINTER(ORScene), C.POINTER(ORPads), C.POINTER(ORInputs), C.c_void_p,
                                      C.c_void_p, C.c_int32]
+            L.or_pc_prox.argtypes = [C.POINTER(ORScene), C.POINTER(ORPcProx), C.POINTER(ORInputs), C.c_void_p,
+                                     C.c_int32]
             _lib = L
     return _lib
 
@@ -572,3 +579,27 @@ class OracleScene:
         h = np.zeros((E, Pd.pads_per_env, M))
         lib().or_markers(C.byref(self.S), C.byref(Pd), C.byref(I), _p(u), _p(h), int(threads))
         return u, h
+
+    def pc_prox(self, clouds, inputs: dict, radius: float, k: float, ks: float, density: float, threads: int = 0):
+        """Point-cloud ProximityTaxel: link-frame force/torque [6][T] of every taxel
+        from each object's tracked points clouds[o] ([n_o][3], object frame)."""
+        keep = {"cloud": np.ascontiguousarray(np.concatenate([np.asarray(c, np.float32).reshape(-1, 3)
+                                                              for c in clouds]), np.float32),
+                "off": np.ascontiguousarray(np.concatenate([[0], np.cumsum([len(c) for c in clouds])]), np.int64)}
+        Pc = ORPcProx()
+        Pc.cloud, Pc.cloud_off = _p(keep["cloud"]), _p(keep["off"])
+        Pc.radius, Pc.k, Pc.ks, Pc.density = float(radius), float(k), float(ks), float(density)
+        I = ORInputs()
+        for kk, dt in (("link_pose", np.float32), ("link_vel", np.float32), ("obj_pose", np.float32),
+                       ("obj_vel", np.float32), ("obj_id", np.int32)):
+            keep[kk] = np.ascontiguousarray(inputs[kk], dt)
+            setattr(I, kk, _p(keep[kk]))
+        if inputs.get("env_params") is not None:
+            keep["env_params"] = np.ascontiguousarray(inputs["env_params"], np.float32)
+            I.env_params = _p(keep["env_params"])
+        I.pose_dt = float(inputs.get("pose_dt", 0.0))
+        I.step = int(inputs.get("step", 0))
+        T = self.T
+        ft = np.zeros((6, T))
+        lib().or_pc_prox(C.byref(self.S), C.byref(Pc), C.byref(I), _p(ft), int(threads))
+        return ft

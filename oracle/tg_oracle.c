@@ -1173,6 +1173,104 @@ static void env_markers(const or_scene* S, const or_pads* pads, const or_inputs*
     free(hs);
 }
 
+/* Point-cloud ProximityTaxel (Appendix A "ProximityTaxel"): the env's
+   object is tracked by its surface points p_i; taxel j at q_j with normal a_j
+   and sensing radius R collects P_ij = R - |p_i - q_j| from every point inside
+   its sphere, the point's velocity relative to the taxel's with the normal
+   component removed (v_t), and reports in the link frame
+   f = k rho sum P a + ks rho sum P v_t,  tau = k rho sum P (p - q) x a,
+   rho = density / max(N, 1).  Every point is tested (brute force). */
+static void env_pc_prox(const or_scene* S, const or_pcprox* pc, const or_inputs* in, double* ft, int32_t e) {
+    const int32_t L = S->max_links;
+    const int64_t T = S->taxel_offsets[S->n_envs];
+    double scale = in->env_params ? in->env_params[3 * e + 2] : 1.0;
+    if (S->params.dr_on) {
+        double v[3];
+        or_dr_draw(&S->params, (uint32_t)S->env_gid[e], in->step, v);
+        scale = v[2];
+    }
+    int32_t oid = in->obj_id[e];
+    if (oid < 0) oid = 0;
+    if (oid > S->n_objects - 1) oid = S->n_objects - 1;
+    const float* pts = pc->cloud + 3 * pc->cloud_off[oid];
+    const int64_t N = pc->cloud_off[oid + 1] - pc->cloud_off[oid];
+    const double rho = pc->density / (double)(N > 1 ? N : 1);
+    const double R = pc->radius;
+    double pC0[3], qC0[4], vC[3], wC[3], pC[3], RC[9];
+    for (int a = 0; a < 3; ++a) pC0[a] = in->obj_pose[7 * e + a];
+    for (int a = 0; a < 4; ++a) qC0[a] = in->obj_pose[7 * e + 3 + a];
+    for (int a = 0; a < 3; ++a) { vC[a] = in->obj_vel[6 * e + a]; wC[a] = in->obj_vel[6 * e + 3 + a]; }
+    or_advance_pose(pC0, qC0, vC, wC, in->pose_dt, pC, RC);
+    /* world positions and velocities of the tracked points */
+    double* pw = (double*)malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
+    double* vw = (double*)malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
+    for (int64_t i = 0; i < N; ++i) {
+        double ph[3] = {scale * pts[3 * i], scale * pts[3 * i + 1], scale * pts[3 * i + 2]}, r[3], w[3];
+        matvec(RC, ph, r);
+        for (int a = 0; a < 3; ++a) pw[3 * i + a] = pC[a] + r[a];
+        cross3(wC, r, w);
+        for (int a = 0; a < 3; ++a) vw[3 * i + a] = vC[a] + w[a];
+    }
+    int64_t j = S->taxel_offsets[e];
+    for (int32_t l = 0; l < L; ++l) {
+        int32_t nl = S->link_rows[e * L + l] * S->link_cols[e * L + l];
+        if (nl == 0) continue;
+        const float* lp = in->link_pose + ((size_t)e * L + l) * 7;
+        const float* lv = in->link_vel + ((size_t)e * L + l) * 6;
+        double pL0[3], qL0[4], vL[3], wL[3], pL[3], RL[9];
+        for (int a = 0; a < 3; ++a) pL0[a] = lp[a];
+        for (int a = 0; a < 4; ++a) qL0[a] = lp[3 + a];
+        for (int a = 0; a < 3; ++a) { vL[a] = lv[a]; wL[a] = lv[3 + a]; }
+        or_advance_pose(pL0, qL0, vL, wL, in->pose_dt, pL, RL);
+        for (int32_t m_ = 0; m_ < nl; ++m_, ++j) {
+            double fw[3] = {0, 0, 0}, tw[3] = {0, 0, 0};
+            if (S->R[j] > 0.0) {
+                double x[3] = {S->x[j], S->y[j], S->z[j]}, nl_[3] = {S->nx[j], S->ny[j], S->nz[j]};
+                double q[3], a_[3], rq[3], vt_[3], vtax[3];
+                matvec(RL, x, rq);
+                for (int a = 0; a < 3; ++a) q[a] = pL[a] + rq[a];
+                matvec(RL, nl_, a_);
+                cross3(wL, rq, vt_);
+                for (int a = 0; a < 3; ++a) vtax[a] = vL[a] + vt_[a];
+                for (int64_t i = 0; i < N; ++i) {
+                    double dlt[3];
+                    sub3(&pw[3 * i], q, dlt);
+                    double dist = sqrt(dot3(dlt, dlt));
+                    if (!(dist < R)) continue;
+                    double P = R - dist, vr[3], vt[3], c[3];
+                    sub3(&vw[3 * i], vtax, vr);
+                    double vn = dot3(vr, a_);
+                    for (int a = 0; a < 3; ++a) vt[a] = vr[a] - a_[a] * vn;
+                    cross3(dlt, a_, c);
+                    for (int a = 0; a < 3; ++a) {
+                        fw[a] += pc->k * rho * P * a_[a] + pc->ks * rho * P * vt[a];
+                        tw[a] += pc->k * rho * P * c[a];
+                    }
+                }
+            }
+            double fl[3], tl[3];
+            matTvec(RL, fw, fl);
+            matTvec(RL, tw, tl);
+            for (int a = 0; a < 3; ++a) {
+                ft[(size_t)a * T + j] = fl[a];
+                ft[(size_t)(3 + a) * T + j] = tl[a];
+            }
+        }
+    }
+    free(pw);
+    free(vw);
+}
+
+void or_pc_prox(const or_scene* S, const or_pcprox* pc, const or_inputs* in, double* ft, int32_t threads) {
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#else
+    (void)threads;
+#endif
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t e = 0; e < S->n_envs; ++e) env_pc_prox(S, pc, in, ft, e);
+}
+
 void or_markers(const or_scene* S, const or_pads* pads, const or_inputs* in, double* u, double* h_out, int32_t threads) {
 #ifdef _OPENMP
     if (threads > 0) omp_set_num_threads(threads);

@@ -101,6 +101,17 @@ typedef struct {
     int32_t radius;              /* neighbourhood half-width in markers (2 = 5x5) */
 } or_pads;
 
+/* point-cloud ProximityTaxel (Appendix A "ProximityTaxel"): every object
+   carries tracked surface points (object frame, unscaled); a taxel's sensing
+   sphere of radius R collects the points within it */
+typedef struct {
+    const float* cloud;          /* [sum of counts][3] tracked points of every object, object frame */
+    const int64_t* cloud_off;    /* [n_objects + 1]: object o's points are rows cloud_off[o] .. cloud_off[o+1] - 1 */
+    double radius;               /* sensing radius R (m) */
+    double k, ks;                /* normal and shear gains */
+    double density;              /* density scalar: rho_b = density / max(N_b, 1), N_b the env object's points */
+} or_pcprox;
+
 typedef struct {
     int32_t n_envs, max_links;
     const int64_t* taxel_offsets; /* [n_envs+1] CSR of this (sub)scene */
@@ -208,6 +219,9 @@ void or_reset(const or_scene* S, const uint8_t* env_mask, uint32_t episode, or_s
 int or_step(const or_scene* S, const or_inputs* in, or_state* st, or_outputs* out, int32_t threads);
 /* marker displacements u [E][P][rows*cols][3] (pad frame: normal, tangent, normal x tangent) */
 void or_markers(const or_scene* S, const or_pads* pads, const or_inputs* in, double* u, double* h_out, int32_t threads);
+/* point-cloud proximity of every taxel: ft [6][T], link-frame force (rows 0-2)
+   and torque (rows 3-5); inactive taxels read zero */
+void or_pc_prox(const or_scene* S, const or_pcprox* pc, const or_inputs* in, double* ft, int32_t threads);
 
 #ifdef __cplusplus
 }
