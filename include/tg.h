@@ -111,12 +111,23 @@ typedef struct {
        own Schmitt state) use that radius; the clean readout keeps R, and the
        proximity rays do not depend on it. */
     double probe_radius_noise;
+    /* point-cloud ProximityTaxel (TG_SENSOR_PCPROX; Appendix A
+       "ProximityTaxel"): every object's tracked surface points
+       (tg_object_desc.cloud) within pc_radius of a taxel contribute
+       P = pc_radius - |p - q|; the taxel reports, in its link frame,
+       f = pc_k rho sum P a + pc_ks rho sum P v_t and
+       tau = pc_k rho sum P (p - q) x a, with a the taxel normal, v_t the
+       point's velocity relative to the taxel's without its component along
+       a, rho = pc_density / max(N, 1) and N the env object's point count.
+       The object scale scales the points. */
+    double pc_radius, pc_k, pc_ks, pc_density;
 } tg_params;
 
 /* sensor mask bits (depth, contact and force/torque are always computed) */
 #define TG_SENSOR_DIST 0x1u           /* SurfaceDistanceProbe output phi - R */
 #define TG_SENSOR_PROX 0x2u           /* proximity by rays (geometry-aware ProximityTaxel form) */
 #define TG_SENSOR_MARKERS 0x4u        /* ElastomerTaxel marker dilation on planar pads */
+#define TG_SENSOR_PCPROX 0x8u         /* point-cloud ProximityTaxel (objects' tracked surface points) */
 
 /* Elastomer marker pads (ElastomerTaxel, Eqs. 18-21): every env carries
    pads_per_env planar pads of rows x cols markers at `pitch`, each fixed in a
@@ -241,6 +252,9 @@ typedef struct {
     const void* values;               /* GRID: host or device [dims z][dims y][dims x] */
     const tg_nsdf* nsdf;              /* NEURAL: the network (its parameters are copied) */
     double nsdf_err_mm;               /* NEURAL: probe error (tg_nsdf_probe max); < 0 = not probed */
+    const float* cloud;               /* any kind: host or device [n_cloud][3] tracked surface points
+                                         (object frame) for TG_SENSOR_PCPROX, or NULL */
+    int64_t n_cloud;                  /* 0 .. 2^24 */
 } tg_object_desc;
 
 /* Upload (replace) the scene's object table.  Per env, tg_step_inputs.obj_id
@@ -330,7 +344,9 @@ typedef enum {
     TG_CH_LINK_COUNT = 5,     /* int32 [E*L][2]: contact count clean, noisy (agg_bool = count > 2) */
     TG_CH_STATE_FLAGS = 6,    /* uint8 [T]: bit0 clean contact, bit1 dead, bit2 noisy contact */
     TG_CH_PROX = 7,           /* float [T] (needs TG_SENSOR_PROX) */
-    TG_CH_MARKER = 8          /* float [E*P*rows*cols][3] (needs TG_SENSOR_MARKERS); clean only */
+    TG_CH_MARKER = 8,         /* float [E*P*rows*cols][3] (needs TG_SENSOR_MARKERS); clean only */
+    TG_CH_PC_FT = 9           /* float [6][T]: point-cloud proximity force/torque, link frame (needs
+                                 TG_SENSOR_PCPROX); clean only */
 } tg_channel;
 
 /* Copy one output channel (clean or noisy) into dst (host or device),

@@ -54,6 +54,7 @@ struct tg_scene {
     Item* items_sorted = nullptr;     // per-step object-sorted copy of the items
     // proximity and markers
     float *prox_clean = nullptr, *prox_noisy = nullptr;
+    float* pc_ft = nullptr;            // [6][T] point-cloud proximity (sensor on)
     MarkerArgs markers{};
     int32_t* pad_link = nullptr;
     float* pad_frame = nullptr;
@@ -200,6 +201,10 @@ const char* make_params(const tg_params& p, ParamsDev* out) {
     for (int i = 0; i < 9; ++i) d.xt_w[i] = (float)(w[i] / sum);
     d.seed = p.seed;
     d.rho = (float)p.probe_radius_noise;
+    d.pc_radius = (float)p.pc_radius;
+    d.pc_k = (float)p.pc_k;
+    d.pc_ks = (float)p.pc_ks;
+    d.pc_density = (float)p.pc_density;
     for (uint32_t r = 0; r < 10; ++r) {
         d.rk[2 * r] = (uint32_t)p.seed + r * 0x9E3779B9u;
         d.rk[2 * r + 1] = (uint32_t)(p.seed >> 32) + r * 0xBB67AE85u;
@@ -254,6 +259,7 @@ StepArgs step_args(tg_scene* s) {
     a.link_count = s->link_count;
     a.err = s->err;
     a.prox_clean = s->prox_clean;
+    a.pc_ft = s->pc_ft;
     a.prox_noisy = s->prox_noisy;
     a.ctl = s->ctl;
     a.n_items = s->n_items;
@@ -349,6 +355,11 @@ tg_status tg_create_scene(const tg_scene_desc* d, tg_scene** out) {
     if (const char* m = make_params(d->params, &P)) return fail(nullptr, TG_ERR_INVALID_ARG, m);
     if ((d->sensors & TG_SENSOR_PROX) && (d->params.prox_rays < 1 || !(d->params.prox_range > 0.0)))
         return fail(nullptr, TG_ERR_INVALID_ARG, "TG_SENSOR_PROX needs prox_rays in 1..16 and prox_range > 0");
+    if ((d->sensors & TG_SENSOR_PCPROX) &&
+        (!(d->params.pc_radius > 0.0) || d->params.pc_radius > 0.1 || !std::isfinite(d->params.pc_k) ||
+         !std::isfinite(d->params.pc_ks) || !(d->params.pc_density >= 0.0) || !std::isfinite(d->params.pc_density)))
+        return fail(nullptr, TG_ERR_INVALID_ARG,
+                    "TG_SENSOR_PCPROX needs pc_radius in (0, 0.1] m, finite pc_k and pc_ks, pc_density >= 0");
     const tg_pad_desc& pd = d->pads;
     if (d->sensors & TG_SENSOR_MARKERS) {
         if (pd.pads_per_env < 1 || pd.rows < 1 || pd.cols < 1 || pd.rows * pd.cols > kMaxPadMarkers ||
@@ -477,6 +488,10 @@ tg_status tg_create_scene(const tg_scene_desc* d, tg_scene** out) {
         CKC(cudaMemset(s->prox_clean, 0, (size_t)T * sizeof(float)));
         CKC(cudaMemset(s->prox_noisy, 0, (size_t)T * sizeof(float)));
     }
+    if (d->sensors & TG_SENSOR_PCPROX) {
+        CKC(dalloc(&s->pc_ft, (size_t)6 * std::max<int64_t>(T, 1)));
+        CKC(cudaMemset(s->pc_ft, 0, (size_t)6 * std::max<int64_t>(T, 1) * sizeof(float)));
+    }
     if (d->sensors & TG_SENSOR_MARKERS) {
         const size_t EP = (size_t)E * pd.pads_per_env, M = (size_t)pd.rows * pd.cols;
         CKC(dalloc(&s->pad_link, EP));
@@ -547,9 +562,65 @@ void tg_destroy_scene(tg_scene* s) {
                     s->ft_noisy, s->link_out, s->link_count, s->err, s->link_rec, s->s_link_pose, s->s_link_vel,
                     s->s_obj_pose, s->s_obj_vel, s->s_env_params, s->s_obj_id, s->s_mask, s->s_contact,
                     s->items_sorted, s->prox_clean, s->prox_noisy, s->pad_link, s->pad_frame,
-                    s->marker_u, s->ctl, s->nq_phi, s->nq_grad};
+                    s->marker_u, s->ctl, s->nq_phi, s->nq_grad, s->pc_ft};
     for (void* p : ptrs) dfree(p);
     delete s;
+}
+
+// An object's tracked points sorted into a uniform grid of cell size h over
+// their box (counting sort on the host), uploaded as float4 points and cell
+// start offsets; returns an error message or null.
+static const char* load_cloud(const tg_object_desc& o, double h, ObjDev& t, std::vector<void*>& bufs) {
+    const int64_t n = o.n_cloud;
+    std::vector<float> pts((size_t)n * 3);
+    if (cudaMemcpy(pts.data(), o.cloud, pts.size() * sizeof(float), cudaMemcpyDefault) != cudaSuccess)
+        return "cloud copy failed";
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            const double v = pts[3 * i + a];
+            if (!std::isfinite(v)) return "cloud points must be finite";
+            lo[a] = std::min(lo[a], v);
+            hi[a] = std::max(hi[a], v);
+        }
+    int dims[3];
+    size_t cells = 1;
+    for (int a = 0; a < 3; ++a) {
+        dims[a] = (int)std::floor((hi[a] - lo[a]) / h) + 1;
+        cells *= (size_t)dims[a];
+    }
+    if (cells > ((size_t)1 << 22)) return "cloud box over 2^22 cells of pc_radius";
+    const float inv_h = (float)(1.0 / h);
+    auto cell_of = [&](int64_t i) {
+        int c[3];
+        for (int a = 0; a < 3; ++a)
+            c[a] = std::min(std::max((int)std::floor((pts[3 * i + a] - (float)lo[a]) * inv_h), 0), dims[a] - 1);
+        return ((size_t)c[2] * dims[1] + c[1]) * dims[0] + c[0];
+    };
+    std::vector<int32_t> start(cells + 1, 0);
+    for (int64_t i = 0; i < n; ++i) ++start[cell_of(i) + 1];
+    for (size_t c = 0; c < cells; ++c) start[c + 1] += start[c];
+    std::vector<int32_t> fill(start.begin(), start.end() - 1);
+    std::vector<float4> sorted((size_t)n);
+    for (int64_t i = 0; i < n; ++i) sorted[fill[cell_of(i)]++] = make_float4(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2], 0.f);
+    float4* dp = nullptr;
+    int32_t* ds = nullptr;
+    cudaError_t e1 = dalloc(&dp, (size_t)n), e2 = dalloc(&ds, cells + 1);
+    if (dp) bufs.push_back(dp);
+    if (ds) bufs.push_back(ds);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) return "cloud alloc failed";
+    if (cudaMemcpy(dp, sorted.data(), sizeof(float4) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ds, start.data(), sizeof(int32_t) * (cells + 1), cudaMemcpyHostToDevice) != cudaSuccess)
+        return "cloud upload failed";
+    t.pc_pts = dp;
+    t.pc_start = ds;
+    for (int a = 0; a < 3; ++a) {
+        t.pc_dims[a] = dims[a];
+        t.pc_lo[a] = (float)lo[a];
+    }
+    t.pc_inv_h = inv_h;
+    t.pc_n = (int32_t)n;
+    return nullptr;
 }
 
 tg_status tg_upload_objects(tg_scene* s, const tg_object_desc* objs, int32_t n) {
@@ -675,6 +746,16 @@ tg_status tg_upload_objects(tg_scene* s, const tg_object_desc* objs, int32_t n) 
             cleanup();
             return fail(s, TG_ERR_INVALID_ARG, "unknown object kind");
         }
+        if (o.n_cloud < 0 || o.n_cloud > (1 << 24) || (o.n_cloud > 0 && !o.cloud)) {
+            cleanup();
+            return fail(s, TG_ERR_INVALID_ARG, "n_cloud must be in 0..2^24 with a cloud");
+        }
+        if ((s->sensors & TG_SENSOR_PCPROX) && o.n_cloud > 0) {
+            if (const char* m = load_cloud(o, s->params.pc_radius, t, bufs)) {
+                cleanup();
+                return fail(s, TG_ERR_INVALID_ARG, m);
+            }
+        }
     }
     ObjDev* dtab = nullptr;
     cudaError_t e = dalloc(&dtab, (size_t)n);
@@ -791,6 +872,7 @@ tg_status enqueue_step(tg_scene* s, const tg_step_inputs* in, cudaStream_t st, b
     CK(s, launch_step(a, s->n_items, st));
     if (prof) CK(s, record(ev[2]));
     if (s->sensors & TG_SENSOR_PROX) CK(s, launch_prox(a, s->n_items, st));
+    if (s->sensors & TG_SENSOR_PCPROX) CK(s, launch_pc_prox(a, s->n_items, st));
     if (s->sensors & TG_SENSOR_MARKERS) {
         MarkerArgs m = s->markers;
         m.obj_id = oid;
@@ -1079,6 +1161,7 @@ size_t tg_channel_bytes(const tg_scene* s, int32_t ch) {
         return (s->sensors & TG_SENSOR_MARKERS)
                    ? (size_t)s->E * s->markers.pads_per_env * s->markers.rows * s->markers.cols * 12
                    : 0;
+    case TG_CH_PC_FT: return (s->sensors & TG_SENSOR_PCPROX) ? T * 24 : 0;
     default: return 0;
     }
 }
@@ -1096,6 +1179,7 @@ tg_status tg_get_buffer(tg_scene* s, int32_t ch, int32_t noisy, void** ptr, size
     case TG_CH_STATE_FLAGS: p = s->flags; break;
     case TG_CH_PROX: p = (s->sensors & TG_SENSOR_PROX) ? (noisy ? s->prox_noisy : s->prox_clean) : nullptr; break;
     case TG_CH_MARKER: p = (s->sensors & TG_SENSOR_MARKERS) ? s->marker_u : nullptr; break;
+    case TG_CH_PC_FT: p = (s->sensors & TG_SENSOR_PCPROX) ? s->pc_ft : nullptr; break;
     default: break;
     }
     if (!p) return fail(s, TG_ERR_INVALID_ARG, "channel has no device view (or its sensor is off)");

@@ -48,6 +48,7 @@ struct ParamsDev {
     uint64_t seed;
     uint32_t rk[20];                  // Philox round keys of the seed: (k0, k1) + r (0x9E3779B9, 0xBB67AE85)
     float rho;                        // probe-radius noise half-width (m), 0 = off
+    float pc_radius, pc_k, pc_ks, pc_density;  // point-cloud proximity
     NoiseDev depth, ft, prox;
     // proximity rays
     int prox_rays;
@@ -79,6 +80,14 @@ struct ObjDev {
     float nlo[3], nhi[3], ninv_ext[3];
     const uint32_t* ntable;           // [16][2^16] binary16 pairs
     const uint16_t* nweights;         // 6,208 bfloat16: W1 [64][32], W2 [64][64], W3 [64]
+    // tracked surface points (point-cloud proximity), sorted by cell of a
+    // uniform grid of cell size pc_radius over their box (object frame)
+    const float4* pc_pts;             // [n] x, y, z, 0; null: no cloud
+    const int32_t* pc_start;          // [cells + 1] first point of each cell
+    int32_t pc_dims[3];
+    float pc_lo[3];
+    float pc_inv_h;
+    int32_t pc_n;
 };
 
 // One CTA of the step kernel: a run of whole links of one env.
@@ -135,6 +144,7 @@ struct StepArgs {
     float* link_out;                  // [E*L][kLinkOut]
     int32_t* link_count;              // [E*L][2]
     unsigned int* err;                // [0] non-finite count, [1] learned-SDF MMA wait timeouts
+    float* pc_ft;                     // [6][T] point-cloud proximity force/torque (sensor on)
     float* prox_clean;                // [T] (proximity on)
     float* prox_noisy;                // [T]
     // learned-SDF objects: phi (scaled) of every taxel of a neural item and
@@ -201,6 +211,7 @@ cudaError_t launch_mesh_bake(const float* tri, const float* tri_n, int n_faces, 
                              const float lo[3], const float hi[3], int fp16, void* out, cudaStream_t s);
 cudaError_t launch_build_cells(const void* values, const int dims[3], int fp16, void* cells, cudaStream_t s);
 cudaError_t launch_prox(const StepArgs& a, int n_items, cudaStream_t s);
+cudaError_t launch_pc_prox(const StepArgs& a, int n_items, cudaStream_t s);
 cudaError_t launch_markers(const MarkerArgs& m, cudaStream_t s);
 cudaError_t launch_unpack_contact(const uint8_t* flags, int64_t n, int noisy, uint8_t* out, cudaStream_t s);
 

@@ -29,8 +29,9 @@ STATUS = {0: "TG_OK", 1: "TG_ERR_INVALID_ARG", 2: "TG_ERR_OOM", 3: "TG_ERR_CUDA"
           5: "TG_ERR_TIMEOUT", 6: "TG_ERR_NUMERIC", 7: "TG_ERR_UNSUPPORTED"}
 TG_OBJ_SPHERE, TG_OBJ_BOX, TG_OBJ_PLANE, TG_OBJ_MESH, TG_OBJ_GRID, TG_OBJ_NEURAL = 0, 1, 2, 3, 4, 5
 NSDF_TABLE_ENTRIES, NSDF_WEIGHTS = 16 * 65536, 6208
-CH_CONTACT, CH_DEPTH, CH_DIST, CH_FORCE_TORQUE, CH_LINK_WRENCH, CH_LINK_COUNT, CH_STATE_FLAGS, CH_PROX, CH_MARKER = range(9)
-TG_SENSOR_DIST, TG_SENSOR_PROX, TG_SENSOR_MARKERS = 0x1, 0x2, 0x4
+(CH_CONTACT, CH_DEPTH, CH_DIST, CH_FORCE_TORQUE, CH_LINK_WRENCH, CH_LINK_COUNT, CH_STATE_FLAGS, CH_PROX, CH_MARKER,
+ CH_PC_FT) = range(10)
+TG_SENSOR_DIST, TG_SENSOR_PROX, TG_SENSOR_MARKERS, TG_SENSOR_PCPROX = 0x1, 0x2, 0x4, 0x8
 LINK_REC = 18
 
 
@@ -51,7 +52,8 @@ class Params(C.Structure):
         ("seed", C.c_uint64), ("depth", NoiseGroup), ("ft", NoiseGroup), ("prox", NoiseGroup),
         ("prox_rays", C.c_int32), ("prox_range", C.c_double), ("prox_cone", C.c_double),
         ("dr_on", C.c_int32), ("dr_mu", C.c_double * 2), ("dr_k", C.c_double * 2), ("dr_scale", C.c_double * 2),
-        ("nsdf_max_err_mm", C.c_double), ("probe_radius_noise", C.c_double)]
+        ("nsdf_max_err_mm", C.c_double), ("probe_radius_noise", C.c_double),
+        ("pc_radius", C.c_double), ("pc_k", C.c_double), ("pc_ks", C.c_double), ("pc_density", C.c_double)]
 
 
 class PadDesc(C.Structure):
@@ -74,7 +76,8 @@ class ObjectDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("radius", C.c_float), ("half", C.c_float * 3),
                 ("n_verts", C.c_int32), ("n_faces", C.c_int32), ("verts", C.c_void_p), ("faces", C.c_void_p),
                 ("dims", C.c_int32 * 3), ("lo", C.c_float * 3), ("hi", C.c_float * 3),
-                ("fp16", C.c_int32), ("values", C.c_void_p), ("nsdf", C.c_void_p), ("nsdf_err_mm", C.c_double)]
+                ("fp16", C.c_int32), ("values", C.c_void_p), ("nsdf", C.c_void_p), ("nsdf_err_mm", C.c_double),
+                ("cloud", C.c_void_p), ("n_cloud", C.c_int64)]
 
 
 class StepInputs(C.Structure):
@@ -199,6 +202,11 @@ def _fill_params(params: dict) -> Params:
             getattr(P, "dr_" + k)[1] = float(dr[k][1])
     P.nsdf_max_err_mm = float(params.get("nsdf_max_err_mm", 0.2))
     P.probe_radius_noise = float(params.get("rho", 0.0))
+    # point-cloud ProximityTaxel (the paper's experiment values by default)
+    P.pc_radius = float(params.get("pc_radius", 0.01))
+    P.pc_k = float(params.get("pc_k", 300.0))
+    P.pc_ks = float(params.get("pc_ks", 10.0))
+    P.pc_density = float(params.get("pc_density", 100.0))
     for g in ("depth", "ft", "prox"):
         grp = getattr(P, g)
         for k in NoiseGroup._fields_:
@@ -241,6 +249,11 @@ def object_desc(o, keep: list) -> ObjectDesc:
         d.hi[:] = [float(v) for v in o.hi]
         d.fp16 = 1 if o.fp16 else 0
         d.values = _ptr(vals)
+    cloud = getattr(o, "cloud", None)
+    if cloud is not None and len(cloud):
+        c = np.ascontiguousarray(cloud, np.float32).reshape(-1, 3)
+        keep.append(c)
+        d.cloud, d.n_cloud = _ptr(c), len(c)
     return d
 
 
@@ -390,7 +403,7 @@ class Scene:
                 CH_FORCE_TORQUE: ((6, T), np.float32), CH_LINK_WRENCH: ((EL, LINK_REC), np.float32),
                 CH_LINK_COUNT: ((EL, 2), np.int32), CH_STATE_FLAGS: ((T,), np.uint8),
                 CH_PROX: ((T,), np.float32),
-                CH_MARKER: ((self._n_markers(), 3), np.float32)}[ch]
+                CH_MARKER: ((self._n_markers(), 3), np.float32), CH_PC_FT: ((6, T), np.float32)}[ch]
 
     def _n_markers(self):
         p = self.pads

@@ -210,6 +210,8 @@ class ObjectSpec:
     nsdf_table: np.ndarray | None = None    # uint16 [16][65536][2] binary16 bits
     nsdf_weights: np.ndarray | None = None  # uint16 [6208] bfloat16 bits: W1 [64][32], W2 [64][64], W3 [64]
     nsdf_err_mm: float = -1.0
+    # tracked surface points (object frame, [n][3]) for the point-cloud ProximityTaxel
+    cloud: np.ndarray | None = None
 
 
 def bf16_bits(x) -> np.ndarray:
@@ -241,6 +243,35 @@ def surface_samples(rng, verts: np.ndarray, faces: np.ndarray, n: int):
     p = (1 - r1)[:, None] * a[f] + (r1 * (1 - r2))[:, None] * b[f] + (r1 * r2)[:, None] * c[f]
     nrm = cr[f] / np.linalg.norm(cr[f], axis=1, keepdims=True)
     return p, nrm
+
+
+def object_cloud(rng, o: "ObjectSpec", n: int):
+    """n tracked surface points of an object (float32 [n][3], object frame;
+    Appendix A "ProximityTaxel" samples tracked links into a surface point
+    cloud at reset): area-weighted on a mesh, uniform on a sphere or a box;
+    None for a plane (unbounded)."""
+    if o.verts is not None and o.faces is not None:
+        return surface_samples(rng, o.verts, o.faces, n)[0].astype(np.float32)
+    if o.kind == "sphere":
+        v = rng.standard_normal((n, 3))
+        return (o.radius * v / np.linalg.norm(v, axis=1, keepdims=True)).astype(np.float32)
+    if o.kind == "box":
+        h = np.asarray(o.half, np.float64)
+        areas = np.array([h[1] * h[2], h[0] * h[2], h[0] * h[1]] * 2)
+        f = rng.choice(6, n, p=areas / areas.sum())
+        p = rng.uniform(-1, 1, (n, 3)) * h
+        ax = f % 3
+        p[np.arange(n), ax] = np.where(f < 3, 1.0, -1.0) * h[ax]
+        return p.astype(np.float32)
+    return None
+
+
+def add_clouds(wl: "Workload", n: int = 5000, seed: int = 20260099) -> "Workload":
+    """Give every object of the workload n tracked surface points."""
+    rng = np.random.default_rng(seed)
+    for o in wl.objects:
+        o.cloud = object_cloud(rng, o, n)
+    return wl
 
 
 def sdf_sample_points(rng, verts: np.ndarray, faces: np.ndarray, lo, hi, n: int, band: float = 5e-3) -> np.ndarray:
