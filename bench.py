@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-full-sensors", action="store_true", help="skip the proximity + markers line")
+    ap.add_argument("--no-pc-prox", action="store_true", help="skip the point-cloud proximity line")
+    ap.add_argument("--pc-points", type=int, default=5000, help="tracked surface points per object")
     ap.add_argument("--neural-objects", type=int, default=64, help="objects given a learned SDF (0: skip the line)")
     ap.add_argument("--neural-points", type=int, default=2_000_000, help="labelled training points per object")
     ap.add_argument("--neural-steps", type=int, default=3000, help="Adam steps per object")
@@ -503,6 +505,38 @@ def run_tg(args):
                 "prox_markers_ms_per_step": (fms - t_max) / args.steps,
                 "taxels_with_proximity_reading": round(prox_share, 4),
                 "gpu_launches": (launches_per_step + 2) * args.steps}
+    # third line: the point-cloud ProximityTaxel (the paper's experiment settings) on the same workload
+    pcl = None
+    if not args.no_pc_prox:
+        import dataclasses
+        rngc = np.random.default_rng(20260099)
+        objs_c = [dataclasses.replace(objs[k], cloud=W.object_cloud(rngc, wl.objects[k], args.pc_points))
+                  for k in range(len(objs))]
+        pcp = dict(wl.params, pc_radius=0.01, pc_k=300.0, pc_ks=10.0, pc_density=100.0)
+        sc3 = tg.Scene(wl.geom(), pcp, sensors=tg.TG_SENSOR_PCPROX, taxel_gid0=gid0, env_gid0=egid0)
+        sc3.upload_objects(objs_c)
+        sc3.set_schedule(**sched)
+        sc3.graph_capture(step_inputs(0, d_in), pose_dt_per_step=dt)
+        sc3.graph_launch(args.warmup)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        sc3.graph_launch(args.steps)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        cms = max_over_ranks(c0.elapsed_time(c1), dev)
+        pcf = sc3.buffer(tg.CH_PC_FT).reshape(6, -1)
+        pc_share = float((pcf[:3].abs().sum(0) > 0).sum().item()) / max(wl.n_active, 1)
+        sc3.graph_release()
+        sc3.close()
+        pcl = {"sensors": f"headline step + point-cloud ProximityTaxel ({args.pc_points} tracked surface points per "
+                          "object in a uniform cell grid, sensing radius 10 mm, k 300, ks 10, density 100)",
+               "value": n_q * args.steps / (cms / 1e3), "unit": UNIT, "ms_per_step": cms / args.steps,
+               "pc_prox_ms_per_step": (cms - t_max) / args.steps,
+               "taxels_with_reading": round(pc_share, 4),
+               "gpu_launches": (launches_per_step + 1) * args.steps}
     neural = None
     if args.neural_objects > 0 and ws == 1:
         neural = neural_line(args, wl, objs, d_in, dev, sched, stream, step_inputs, t_max)
@@ -535,6 +569,7 @@ def run_tg(args):
             "contact_share": round(contact_share, 4), "penetrating_share": round(pen_share, 4),
             "schedule": {"chosen": sched, "autotune": tune["candidates"], "replay": "CUDA graph per step"},
             "full_sensor_set": full,
+            "point_cloud_proximity": pcl,
             "neural_sdf": neural,
             "setup_s": {"bake": round(bake_s, 2), "total": round(time.time() - t_setup, 1)},
         }

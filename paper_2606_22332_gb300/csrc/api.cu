@@ -589,7 +589,7 @@ static const char* load_cloud(const tg_object_desc& o, double h, ObjDev& t, std:
         dims[a] = (int)std::floor((hi[a] - lo[a]) / h) + 1;
         cells *= (size_t)dims[a];
     }
-    if (cells > ((size_t)1 << 22)) return "cloud box over 2^22 cells of pc_radius";
+    if (cells > ((size_t)1 << 22)) return "cloud box over 2^22 cells of pc_radius / 2";
     const float inv_h = (float)(1.0 / h);
     auto cell_of = [&](int64_t i) {
         int c[3];
@@ -751,7 +751,7 @@ tg_status tg_upload_objects(tg_scene* s, const tg_object_desc* objs, int32_t n) 
             return fail(s, TG_ERR_INVALID_ARG, "n_cloud must be in 0..2^24 with a cloud");
         }
         if ((s->sensors & TG_SENSOR_PCPROX) && o.n_cloud > 0) {
-            if (const char* m = load_cloud(o, s->params.pc_radius, t, bufs)) {
+            if (const char* m = load_cloud(o, 0.5 * s->params.pc_radius, t, bufs)) {
                 cleanup();
                 return fail(s, TG_ERR_INVALID_ARG, m);
             }

@@ -1,13 +1,14 @@
 // pcprox.cu -- the point-cloud ProximityTaxel (Appendix A "ProximityTaxel"):
 // the env's object is tracked by surface points p_i (object frame, sorted
-// into a uniform grid of cell size R at upload); taxel j at q_j with normal
+// into a uniform grid of cell size R/2 at upload); taxel j at q_j with normal
 // a_j collects, from every point within its sensing sphere of radius R,
 // P_ij = R - |p_i - q_j|, the point's velocity relative to the taxel's with
 // the component along a_j removed (v_t), and reports in its link frame
 //   f = k rho sum P a + ks rho sum P v_t,   tau = k rho sum P (p - q) x a,
 // rho = density / max(N, 1), N the object's point count.
-// One CTA per work item, one thread per taxel; a taxel visits the grid cells
-// its sphere overlaps.  Everything is evaluated in the link frame: with the
+// One CTA per work item, one thread per taxel; a taxel visits, row by row of
+// cells, the x range of cells its sphere reaches in that row (rows it misses
+// are skipped), four points' loads in flight at a time.  Everything is evaluated in the link frame: with the
 // link record's M = R_C^T R_L / s and t (object frame scaled by 1/s), the
 // link-frame offset of a point is s^2 M^T (p^ - q^), and the relative
 // velocity of a point at link position x + d is V + W_C x (x + d - p_LC) -
@@ -74,20 +75,33 @@ __global__ void __launch_bounds__(kPcThreads) pc_prox_kernel(const StepArgs a) {
                 c1[ax] = min((int)floorf(hi), obj_s.pc_dims[ax] - 1);
             }
             if (!empty) {
-                for (int cz = c0[2]; cz <= c1[2]; ++cz)
+                const float h = 1.0f / obj_s.pc_inv_h;
+                for (int cz = c0[2]; cz <= c1[2]; ++cz) {
+                    // distance from q to the slab of cell layer cz (0 inside it)
+                    const float z0 = obj_s.pc_lo[2] + cz * h;
+                    const float dzs = fmaxf(fmaxf(z0 - q[2], q[2] - (z0 + h)), 0.0f);
                     for (int cy = c0[1]; cy <= c1[1]; ++cy) {
+                        const float y0 = obj_s.pc_lo[1] + cy * h;
+                        const float dys = fmaxf(fmaxf(y0 - q[1], q[1] - (y0 + h)), 0.0f);
+                        // the sphere's x extent within this row of cells (skip the row if it misses)
+                        const float w2 = rh * rh - dys * dys - dzs * dzs;
+                        if (!(w2 > 0.0f)) continue;
+                        const float w = sqrtf(w2) * 1.0001f;
+                        const int x0 = max((int)floorf((q[0] - w - obj_s.pc_lo[0]) * obj_s.pc_inv_h), c0[0]);
+                        const int x1 = min((int)floorf((q[0] + w - obj_s.pc_lo[0]) * obj_s.pc_inv_h), c1[0]);
+                        if (x1 < x0) continue;
                         const int row = (cz * obj_s.pc_dims[1] + cy) * obj_s.pc_dims[0];
-                        const int p0 = __ldg(obj_s.pc_start + row + c0[0]), p1 = __ldg(obj_s.pc_start + row + c1[0] + 1);
-                        for (int k = p0; k < p1; ++k) {
-                            const float4 p = __ldg(obj_s.pc_pts + k);
+                        const int p0 = __ldg(obj_s.pc_start + row + x0), p1 = __ldg(obj_s.pc_start + row + x1 + 1);
+                        // one point's contribution, if it lies in the sphere
+                        auto add = [&](const float4 p) {
                             const float dx = p.x - q[0], dy = p.y - q[1], dz = p.z - q[2];
-                            if (!(dx * dx + dy * dy + dz * dz < rh * rh)) continue;
+                            if (!(dx * dx + dy * dy + dz * dz < rh * rh)) return;
                             // link-frame offset s^2 M^T (p^ - q^)
                             const float3 d = f3(s2 * (rec[0] * dx + rec[3] * dy + rec[6] * dz),
                                                 s2 * (rec[1] * dx + rec[4] * dy + rec[7] * dz),
                                                 s2 * (rec[2] * dx + rec[5] * dy + rec[8] * dz));
                             const float dist = sqrtf(dot(d, d));
-                            if (!(dist < R)) continue;
+                            if (!(dist < R)) return;
                             const float Pw = R - dist;
                             const float3 vr = V + cross(Wc, x + d - pLC) - vtax;
                             const float3 vt = vr - nn * dot(vr, nn);
@@ -95,8 +109,17 @@ __global__ void __launch_bounds__(kPcThreads) pc_prox_kernel(const StepArgs a) {
                             sp += Pw;
                             sv[0] = fmaf(Pw, vt.x, sv[0]); sv[1] = fmaf(Pw, vt.y, sv[1]); sv[2] = fmaf(Pw, vt.z, sv[2]);
                             st[0] = fmaf(Pw, tq.x, st[0]); st[1] = fmaf(Pw, tq.y, st[1]); st[2] = fmaf(Pw, tq.z, st[2]);
+                        };
+                        // four points' loads in flight at a time (same order of the sums)
+                        int k = p0;
+                        for (; k + 3 < p1; k += 4) {
+                            const float4 pa = __ldg(obj_s.pc_pts + k), pb = __ldg(obj_s.pc_pts + k + 1);
+                            const float4 pc = __ldg(obj_s.pc_pts + k + 2), pd = __ldg(obj_s.pc_pts + k + 3);
+                            add(pa); add(pb); add(pc); add(pd);
                         }
+                        for (; k < p1; ++k) add(__ldg(obj_s.pc_pts + k));
                     }
+                }
             }
         }
         const float kr = P.pc_k * rho, ksr = P.pc_ks * rho;
