@@ -91,6 +91,12 @@ class ORPcProx(C.Structure):
                 ("ks", C.c_double), ("density", C.c_double)]
 
 
+class ORShear(C.Structure):
+    _fields_ = [("cloud", C.c_void_p), ("cloud_off", C.c_void_p), ("s_s", C.c_double), ("lambda_s", C.c_double),
+                ("eta_enter", C.c_double), ("eta_exit", C.c_double), ("thickness", C.c_double),
+                ("n_max", C.c_int64)]
+
+
 class ORScene(C.Structure):
     _fields_ = [
         ("n_envs", C.c_int32), ("max_links", C.c_int32),
@@ -176,6 +182,9 @@ def lib():
                                      C.c_void_p, C.c_int32]
             L.or_pc_prox.argtypes = [C.POINTER(ORScene), C.POINTER(ORPcProx), C.POINTER(ORInputs), C.c_void_p,
                                      C.c_int32]
+            L.or_shear_step.argtypes = [C.POINTER(ORScene), C.POINTER(ORPads), C.POINTER(ORShear),
+                                        C.POINTER(ORInputs), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_int32]
             _lib = L
     return _lib
 
@@ -550,13 +559,10 @@ class OracleScene:
         lib().or_step(C.byref(self.S), C.byref(I), C.byref(s), C.byref(O), int(threads))
         return out
 
-    def markers(self, pads: dict, inputs: dict, threads: int = 0):
-        """Marker displacements u [E][P][rows*cols][3] (pad frame: normal, tangent, bitangent)
-        and marker depths h [E][P][rows*cols].  pads: pads_per_env, rows, cols, pitch, pad_link
-        [E][P], pad_frame [E][P][9], s_d, alpha, lambda_d, c, eps, radius."""
-        E = self.n_envs
-        keep = {"link": np.ascontiguousarray(pads["pad_link"], np.int32),
-                "frame": np.ascontiguousarray(pads["pad_frame"], np.float32)}
+    @staticmethod
+    def _pads(pads: dict, keep: dict) -> ORPads:
+        keep["link"] = np.ascontiguousarray(pads["pad_link"], np.int32)
+        keep["frame"] = np.ascontiguousarray(pads["pad_frame"], np.float32)
         Pd = ORPads()
         Pd.pads_per_env, Pd.rows, Pd.cols = int(pads["pads_per_env"]), int(pads["rows"]), int(pads["cols"])
         Pd.pitch = float(pads["pitch"])
@@ -564,6 +570,63 @@ class OracleScene:
         for k in ("s_d", "alpha", "lambda_d", "c", "eps"):
             setattr(Pd, k, float(pads[k]))
         Pd.radius = int(pads["radius"])
+        return Pd
+
+    @staticmethod
+    def _pose_inputs(inputs: dict, keep: dict) -> ORInputs:
+        I = ORInputs()
+        for k, dt in (("link_pose", np.float32), ("link_vel", np.float32), ("obj_pose", np.float32),
+                      ("obj_vel", np.float32), ("obj_id", np.int32)):
+            keep[k] = np.ascontiguousarray(inputs[k], dt)
+            setattr(I, k, _p(keep[k]))
+        if inputs.get("env_params") is not None:
+            keep["env_params"] = np.ascontiguousarray(inputs["env_params"], np.float32)
+            I.env_params = _p(keep["env_params"])
+        I.pose_dt = float(inputs.get("pose_dt", 0.0))
+        I.step = int(inputs.get("step", 0))
+        return I
+
+    def new_shear_state(self, pads_per_env: int, n_max: int) -> dict:
+        """Shear-anchor state with no anchors: anchors [E][P][n_max][2] (NaN = none), anchor_obj [E][P]."""
+        E = self.n_envs
+        return {"anchors": np.full((E, pads_per_env, n_max, 2), np.nan),
+                "anchor_obj": np.full((E, pads_per_env), -1, np.int32)}
+
+    def shear_step(self, pads: dict, clouds, shear: dict, inputs: dict, state: dict, threads: int = 0):
+        """One step of the ElastomerTaxel shear anchors (Eqs. 19-20): updates
+        `state` in place and returns (u [E][P][rows*cols][3] the shear part of
+        the marker displacements, n_anchored [E][P], margin [E][P]).  clouds[o]:
+        object o's tracked points ([n_o][3], object frame); shear: s_s,
+        lambda_s, eta_enter, eta_exit, thickness."""
+        E = self.n_envs
+        keep = {"cloud": np.ascontiguousarray(np.concatenate([np.asarray(c, np.float32).reshape(-1, 3)
+                                                              for c in clouds]), np.float32),
+                "off": np.ascontiguousarray(np.concatenate([[0], np.cumsum([len(c) for c in clouds])]), np.int64)}
+        Pd = self._pads(pads, keep)
+        an, ao = state["anchors"], state["anchor_obj"]
+        assert an.dtype == np.float64 and an.flags.c_contiguous and ao.dtype == np.int32 and ao.flags.c_contiguous
+        assert an.shape == (E, Pd.pads_per_env, an.shape[2], 2) and an.shape[2] >= max(len(c) for c in clouds)
+        Sh = ORShear()
+        Sh.cloud, Sh.cloud_off = _p(keep["cloud"]), _p(keep["off"])
+        for k in ("s_s", "lambda_s", "eta_enter", "eta_exit", "thickness"):
+            setattr(Sh, k, float(shear[k]))
+        Sh.n_max = an.shape[2]
+        I = self._pose_inputs(inputs, keep)
+        M = Pd.rows * Pd.cols
+        u = np.zeros((E, Pd.pads_per_env, M, 3))
+        na = np.zeros((E, Pd.pads_per_env), np.int32)
+        mg = np.zeros((E, Pd.pads_per_env))
+        lib().or_shear_step(C.byref(self.S), C.byref(Pd), C.byref(Sh), C.byref(I), _p(an), _p(ao), _p(u), _p(na),
+                            _p(mg), int(threads))
+        return u, na, mg
+
+    def markers(self, pads: dict, inputs: dict, threads: int = 0):
+        """Marker displacements u [E][P][rows*cols][3] (pad frame: normal, tangent, bitangent)
+        and marker depths h [E][P][rows*cols].  pads: pads_per_env, rows, cols, pitch, pad_link
+        [E][P], pad_frame [E][P][9], s_d, alpha, lambda_d, c, eps, radius."""
+        E = self.n_envs
+        keep = {}
+        Pd = self._pads(pads, keep)
         I = ORInputs()
         for k, dt in (("link_pose", np.float32), ("link_vel", np.float32), ("obj_pose", np.float32),
                       ("obj_vel", np.float32), ("obj_id", np.int32)):

@@ -1261,6 +1261,120 @@ static void env_pc_prox(const or_scene* S, const or_pcprox* pc, const or_inputs*
     free(vw);
 }
 
+/* ElastomerTaxel shear anchors (Eqs. 19-20).  For every pad: each tracked
+   point of the env object is taken into the sensor frame, z = (z_t, z_b, z_n)
+   in the pad's tangent, bitangent and normal; its elastomer SDF is that of
+   the box under the pad; an unanchored point whose SDF is below -eta_enter
+   anchors at e = (z_t, z_b), an anchored one whose SDF is above +eta_exit
+   lets go.  Every anchored point with penetration h = max(0, -SDF) > 0 then
+   moves marker j (pad position x_j = (a_j, b_j, 0)) by
+   s_s Pi_n(z - e) h exp(-lambda_s |Pi_n(x_j - z)|^2). */
+static void env_shear(const or_scene* S, const or_pads* pads, const or_shear* sh, const or_inputs* in,
+                      double* anchors, int32_t* anchor_obj, double* u, int32_t* n_anchored, double* margin, int32_t e) {
+    const int32_t L = S->max_links, P = pads->pads_per_env, M = pads->rows * pads->cols;
+    double scale = in->env_params ? in->env_params[3 * e + 2] : 1.0;
+    if (S->params.dr_on) {
+        double v[3];
+        or_dr_draw(&S->params, (uint32_t)S->env_gid[e], in->step, v);
+        scale = v[2];
+    }
+    int32_t oid = in->obj_id[e];
+    if (oid < 0) oid = 0;
+    if (oid > S->n_objects - 1) oid = S->n_objects - 1;
+    const float* pts = sh->cloud + 3 * sh->cloud_off[oid];
+    const int64_t N = sh->cloud_off[oid + 1] - sh->cloud_off[oid];
+    double pC0[3], qC0[4], vC[3], wC[3], pC[3], RC[9];
+    for (int a = 0; a < 3; ++a) pC0[a] = in->obj_pose[7 * e + a];
+    for (int a = 0; a < 4; ++a) qC0[a] = in->obj_pose[7 * e + 3 + a];
+    for (int a = 0; a < 3; ++a) { vC[a] = in->obj_vel[6 * e + a]; wC[a] = in->obj_vel[6 * e + 3 + a]; }
+    or_advance_pose(pC0, qC0, vC, wC, in->pose_dt, pC, RC);
+    /* the elastomer box: centre (0, 0, -thickness / 2) in pad coordinates */
+    const double half[3] = {0.5 * pads->rows * pads->pitch, 0.5 * pads->cols * pads->pitch, 0.5 * sh->thickness};
+    double* con = (double*)malloc(sizeof(double) * 4 * (size_t)(N > 0 ? N : 1));
+    for (int32_t p = 0; p < P; ++p) {
+        const size_t ep = (size_t)e * P + p;
+        double* an = anchors + ep * (size_t)sh->n_max * 2;
+        if (anchor_obj[ep] != oid) {
+            for (int64_t i = 0; i < 2 * sh->n_max; ++i) an[i] = NAN;
+            anchor_obj[ep] = oid;
+        }
+        int32_t l = pads->pad_link[ep];
+        const float* fr = pads->pad_frame + ep * 9;
+        double o[3] = {fr[0], fr[1], fr[2]}, n[3] = {fr[3], fr[4], fr[5]}, tu[3] = {fr[6], fr[7], fr[8]}, tv[3];
+        cross3(n, tu, tv);
+        const float* lp = in->link_pose + ((size_t)e * L + l) * 7;
+        const float* lv = in->link_vel + ((size_t)e * L + l) * 6;
+        double pL0[3], qL0[4], vL[3], wL[3], pL[3], RL[9];
+        for (int a = 0; a < 3; ++a) pL0[a] = lp[a];
+        for (int a = 0; a < 4; ++a) qL0[a] = lp[3 + a];
+        for (int a = 0; a < 3; ++a) { vL[a] = lv[a]; wL[a] = lv[3 + a]; }
+        or_advance_pose(pL0, qL0, vL, wL, in->pose_dt, pL, RL);
+        int32_t count = 0;
+        int64_t K = 0;
+        double mg = INFINITY;
+        for (int64_t i = 0; i < N; ++i) {
+            double ph[3] = {scale * pts[3 * i], scale * pts[3 * i + 1], scale * pts[3 * i + 2]}, w[3], d[3], xl[3], r[3];
+            matvec(RC, ph, w);
+            for (int a = 0; a < 3; ++a) w[a] += pC[a];
+            sub3(w, pL, d);
+            matTvec(RL, d, xl);
+            sub3(xl, o, r);
+            const double z[3] = {dot3(r, tu), dot3(r, tv), dot3(r, n)};
+            const double zb[3] = {z[0], z[1], z[2] + half[2]};
+            double g[3];
+            const double sdf = or_sdf_box(half, zb, g);
+            mg = fmin(mg, fmin(fabs(sdf + sh->eta_enter), fabs(sdf - sh->eta_exit)));
+            int anchored = !isnan(an[2 * i]);
+            if (!anchored && sdf < -sh->eta_enter) {
+                an[2 * i] = z[0];
+                an[2 * i + 1] = z[1];
+                anchored = 1;
+            } else if (anchored && sdf > sh->eta_exit) {
+                an[2 * i] = an[2 * i + 1] = NAN;
+                anchored = 0;
+            }
+            count += anchored;
+            const double h = sdf < 0.0 ? -sdf : 0.0;
+            if (anchored && h > 0.0) {
+                con[4 * K] = z[0];
+                con[4 * K + 1] = z[1];
+                con[4 * K + 2] = sh->s_s * (z[0] - an[2 * i]) * h;
+                con[4 * K + 3] = sh->s_s * (z[1] - an[2 * i + 1]) * h;
+                ++K;
+            }
+        }
+        for (int32_t j = 0; j < M; ++j) {
+            int32_t ra = j / pads->cols, cb = j % pads->cols;
+            double sa = (ra - 0.5 * (pads->rows - 1)) * pads->pitch, sb = (cb - 0.5 * (pads->cols - 1)) * pads->pitch;
+            double ut = 0.0, ub = 0.0;
+            for (int64_t k = 0; k < K; ++k) {
+                const double da = sa - con[4 * k], db = sb - con[4 * k + 1];
+                const double gk = exp(-sh->lambda_s * (da * da + db * db));
+                ut += con[4 * k + 2] * gk;
+                ub += con[4 * k + 3] * gk;
+            }
+            double* uo = u + (ep * M + j) * 3;
+            uo[0] = 0.0;
+            uo[1] = ut;
+            uo[2] = ub;
+        }
+        n_anchored[ep] = count;
+        margin[ep] = mg;
+    }
+    free(con);
+}
+
+void or_shear_step(const or_scene* S, const or_pads* pads, const or_shear* sh, const or_inputs* in, double* anchors,
+                   int32_t* anchor_obj, double* u, int32_t* n_anchored, double* margin, int32_t threads) {
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#else
+    (void)threads;
+#endif
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t e = 0; e < S->n_envs; ++e) env_shear(S, pads, sh, in, anchors, anchor_obj, u, n_anchored, margin, e);
+}
+
 void or_pc_prox(const or_scene* S, const or_pcprox* pc, const or_inputs* in, double* ft, int32_t threads) {
 #ifdef _OPENMP
     if (threads > 0) omp_set_num_threads(threads);

@@ -112,6 +112,21 @@ typedef struct {
     double density;              /* density scalar: rho_b = density / max(N_b, 1), N_b the env object's points */
 } or_pcprox;
 
+/* ElastomerTaxel shear anchors (Eqs. 19-20): the env object's tracked
+   surface points, taken into each pad's frame (sensor frame: tangent,
+   bitangent = normal x tangent, normal), anchor when their elastomer SDF
+   falls below -eta_enter and release it above +eta_exit.  The elastomer is
+   the box under the pad: the marker footprint (rows x pitch along the
+   tangent, cols x pitch along the bitangent) and `thickness` deep. */
+typedef struct {
+    const float* cloud;          /* [sum of counts][3] tracked points of every object, object frame */
+    const int64_t* cloud_off;    /* [n_objects + 1] */
+    double s_s, lambda_s;        /* shear scale, Gaussian rate */
+    double eta_enter, eta_exit;  /* anchor set below -eta_enter, cleared above +eta_exit (m) */
+    double thickness;            /* elastomer thickness (m) */
+    int64_t n_max;               /* anchor slots per pad (>= every object's point count) */
+} or_shear;
+
 typedef struct {
     int32_t n_envs, max_links;
     const int64_t* taxel_offsets; /* [n_envs+1] CSR of this (sub)scene */
@@ -222,6 +237,15 @@ void or_markers(const or_scene* S, const or_pads* pads, const or_inputs* in, dou
 /* point-cloud proximity of every taxel: ft [6][T], link-frame force (rows 0-2)
    and torque (rows 3-5); inactive taxels read zero */
 void or_pc_prox(const or_scene* S, const or_pcprox* pc, const or_inputs* in, double* ft, int32_t threads);
+/* one step of the shear anchors of every pad.  State: anchors [E][P][n_max][2]
+   (the anchor's tangent and bitangent coordinates, NaN = none) and
+   anchor_obj [E][P] (the object they were taken on, -1 = none; a different
+   object clears them).  Out: u [E][P][rows*cols][3] the shear displacement
+   of every marker (normal, tangent, bitangent components), n_anchored [E][P],
+   and margin [E][P] the least distance of a point's SDF from -eta_enter or
+   +eta_exit (how far the anchor decisions are from their thresholds). */
+void or_shear_step(const or_scene* S, const or_pads* pads, const or_shear* sh, const or_inputs* in, double* anchors,
+                   int32_t* anchor_obj, double* u, int32_t* n_anchored, double* margin, int32_t threads);
 
 #ifdef __cplusplus
 }
