@@ -8,8 +8,11 @@ baked on the GPU from the exact meshes, the full noise model (dead taxels,
 hysteresis, 3x3 crosstalk, drift).  One step = one replay of the step's CUDA
 graph: the pose prologue, the object-sorted work order, the fused sensor
 kernel over every env (schedule picked by the autotuner) and the step-counter
-advance; a taxel query is one active (env, taxel) pair of one step.  A second
-measurement ("full_sensor_set") adds proximity rays and marker pads.
+advance; a taxel query is one active (env, taxel) pair of one step.  Further
+measurements on the same workload add proximity rays and marker pads
+("full_sensor_set"), the point-cloud ProximityTaxel ("point_cloud_proximity"),
+the elastomer markers with shear anchors ("elastomer_shear") and learned-SDF
+objects ("neural_sdf").
 
   python bench.py [--gpus N --steps K --warmup W] [--impl tg|reference]
 
@@ -59,6 +62,8 @@ def parse():
     ap.add_argument("--no-full-sensors", action="store_true", help="skip the proximity + markers line")
     ap.add_argument("--no-pc-prox", action="store_true", help="skip the point-cloud proximity line")
     ap.add_argument("--pc-points", type=int, default=5000, help="tracked surface points per object")
+    ap.add_argument("--no-shear", action="store_true", help="skip the elastomer shear-anchor line")
+    ap.add_argument("--shear-points", type=int, default=1000, help="tracked points per object for the shear anchors")
     ap.add_argument("--neural-objects", type=int, default=64, help="objects given a learned SDF (0: skip the line)")
     ap.add_argument("--neural-points", type=int, default=2_000_000, help="labelled training points per object")
     ap.add_argument("--neural-steps", type=int, default=3000, help="Adam steps per object")
@@ -537,6 +542,42 @@ def run_tg(args):
                "pc_prox_ms_per_step": (cms - t_max) / args.steps,
                "taxels_with_reading": round(pc_share, 4),
                "gpu_launches": (launches_per_step + 1) * args.steps}
+    # fourth line: elastomer markers with shear anchors (the paper's experiment settings)
+    shear = None
+    if not args.no_shear:
+        import dataclasses
+        rngs = np.random.default_rng(20260098)
+        objs_s = [dataclasses.replace(objs[k], cloud=W.object_cloud(rngs, wl.objects[k], args.shear_points))
+                  for k in range(len(objs))]
+        pads_s = dict(W.add_pads(wl).pads, shear_points=args.shear_points, s_s=100.0, lambda_s=2000.0,
+                      eta_enter=1e-5, eta_exit=1e-4, thickness=2e-3)
+        sc4 = tg.Scene(wl.geom(), wl.params, sensors=tg.TG_SENSOR_MARKERS, taxel_gid0=gid0, env_gid0=egid0,
+                       pads=pads_s)
+        sc4.upload_objects(objs_s)
+        sc4.set_schedule(**sched)
+        sc4.graph_capture(step_inputs(0, d_in), pose_dt_per_step=dt)
+        sc4.graph_launch(args.warmup)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        sc4.graph_launch(args.steps)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        sms = max_over_ranks(s0.elapsed_time(s1), dev)
+        n_anch = int(sc4.buffer(tg.CH_SHEAR_ANCHORS).sum().item())
+        n_pads = wl.n_envs * pads_s["pads_per_env"]
+        sc4.graph_release()
+        sc4.close()
+        shear = {"sensors": f"headline step + elastomer markers (5 pads x 16x16 per env, dilation 5x5) with shear "
+                            f"anchors ({args.shear_points} tracked surface points per object, s_s 100, lambda_s 2000, "
+                            "eta_enter 1e-5 m, eta_exit 1e-4 m, 2 mm elastomer)",
+                 "value": n_q * args.steps / (sms / 1e3), "unit": UNIT, "ms_per_step": sms / args.steps,
+                 "markers_shear_ms_per_step": (sms - t_max) / args.steps,
+                 "anchored_points_per_pad": round(n_anch / max(n_pads, 1), 2),
+                 "anchor_state_bytes": n_pads * args.shear_points * 8,
+                 "gpu_launches": (launches_per_step + 1) * args.steps}
     neural = None
     if args.neural_objects > 0 and ws == 1:
         neural = neural_line(args, wl, objs, d_in, dev, sched, stream, step_inputs, t_max)
@@ -570,6 +611,7 @@ def run_tg(args):
             "schedule": {"chosen": sched, "autotune": tune["candidates"], "replay": "CUDA graph per step"},
             "full_sensor_set": full,
             "point_cloud_proximity": pcl,
+            "elastomer_shear": shear,
             "neural_sdf": neural,
             "setup_s": {"bake": round(bake_s, 2), "total": round(time.time() - t_setup, 1)},
         }

@@ -137,7 +137,19 @@ typedef struct {
    x_j - x_i, g(r) = exp(-lambda_d |r|^2), w_ij = h_i (c g / g_bar +
    (1 - c) rho / rho_bar), rho = 1 / (|r|^2 + eps^2); g_bar and rho_bar are
    the peaks of r g(r) and r rho(r).  Output per marker: (normal, tangent,
-   normal x tangent) components. */
+   normal x tangent) components.
+
+   Shear anchors (Eqs. 19-20), on when shear_points > 0: the env object's
+   tracked surface points (tg_object_desc.cloud) are taken into each pad's
+   frame, z = (z_t, z_b, z_n) along tangent, bitangent = normal x tangent and
+   normal.  The elastomer is the box under the pad (rows x pitch along the
+   tangent, cols x pitch along the bitangent, `thickness` deep); a point
+   whose SDF to it is below -eta_enter anchors at e = (z_t, z_b), an anchored
+   point whose SDF rises above +eta_exit lets go, and every anchored point
+   with penetration h = max(0, -SDF) > 0 adds
+   s_s Pi_n(z - e) h exp(-lambda_s |Pi_n(x_j - z)|^2) to marker j.  The
+   anchors are per (env, pad, point) state; a step on another object than the
+   one they were taken on, or a reset of the env, clears them. */
 typedef struct {
     int32_t pads_per_env;             /* P >= 0 */
     int32_t rows, cols;               /* rows * cols <= 1024 */
@@ -146,6 +158,11 @@ typedef struct {
     const float* pad_frame;           /* host [E][P][9]: origin, unit normal, unit tangent (link frame) */
     double s_d, alpha, lambda_d, c, eps;
     int32_t radius;                   /* neighbourhood half-width in markers, 0..4 */
+    int32_t shear_points;             /* anchor slots per pad, 0 (shear off) .. 65536; every object's
+                                         n_cloud must fit */
+    double s_s, lambda_s;             /* shear scale, Gaussian rate (1/m^2) */
+    double eta_enter, eta_exit;       /* anchor thresholds (m), both >= 0 */
+    double thickness;                 /* elastomer thickness (m), > 0 */
 } tg_pad_desc;
 
 typedef struct {
@@ -345,8 +362,10 @@ typedef enum {
     TG_CH_STATE_FLAGS = 6,    /* uint8 [T]: bit0 clean contact, bit1 dead, bit2 noisy contact */
     TG_CH_PROX = 7,           /* float [T] (needs TG_SENSOR_PROX) */
     TG_CH_MARKER = 8,         /* float [E*P*rows*cols][3] (needs TG_SENSOR_MARKERS); clean only */
-    TG_CH_PC_FT = 9           /* float [6][T]: point-cloud proximity force/torque, link frame (needs
+    TG_CH_PC_FT = 9,          /* float [6][T]: point-cloud proximity force/torque, link frame (needs
                                  TG_SENSOR_PCPROX); clean only */
+    TG_CH_SHEAR_ANCHORS = 10  /* int32 [E*P]: anchored points per pad after the last step (needs
+                                 TG_SENSOR_MARKERS with shear_points > 0) */
 } tg_channel;
 
 /* Copy one output channel (clean or noisy) into dst (host or device),
@@ -366,8 +385,8 @@ tg_status tg_get_buffer(tg_scene* scene, int32_t channel, int32_t noisy, void** 
 tg_status tg_sync(tg_scene* scene, tg_stream stream);
 const char* tg_last_error(const tg_scene* scene);
 
-/* Checkpoint: the per-taxel state (flags, hysteresis, drift) and per-env
-   episode numbers.  With buf == NULL, *size receives the needed size.
+/* Checkpoint: the per-taxel state (flags, hysteresis, drift), per-env
+   episode numbers and, with shear anchors on, the anchors of every pad.  With buf == NULL, *size receives the needed size.
    Philox draws are counter-based, so a restored scene replays bit-exactly.
    Synchronous.  Errors: TG_ERR_INVALID_ARG (size mismatch). */
 tg_status tg_save_state(tg_scene* scene, void* buf, size_t* size);

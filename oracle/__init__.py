@@ -184,7 +184,7 @@ def lib():
                                      C.c_int32]
             L.or_shear_step.argtypes = [C.POINTER(ORScene), C.POINTER(ORPads), C.POINTER(ORShear),
                                         C.POINTER(ORInputs), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                                        C.c_void_p, C.c_int32]
+                                        C.c_void_p, C.c_void_p, C.c_int32]
             _lib = L
     return _lib
 
@@ -592,10 +592,12 @@ class OracleScene:
         return {"anchors": np.full((E, pads_per_env, n_max, 2), np.nan),
                 "anchor_obj": np.full((E, pads_per_env), -1, np.int32)}
 
-    def shear_step(self, pads: dict, clouds, shear: dict, inputs: dict, state: dict, threads: int = 0):
+    def shear_step(self, pads: dict, clouds, shear: dict, inputs: dict, state: dict, threads: int = 0,
+                   drag: bool = False):
         """One step of the ElastomerTaxel shear anchors (Eqs. 19-20): updates
         `state` in place and returns (u [E][P][rows*cols][3] the shear part of
-        the marker displacements, n_anchored [E][P], margin [E][P]).  clouds[o]:
+        the marker displacements, n_anchored [E][P], margin [E][P], and, with
+        drag=True, also drag [E][P] (see or_shear_step)).  clouds[o]:
         object o's tracked points ([n_o][3], object frame); shear: s_s,
         lambda_s, eta_enter, eta_exit, thickness."""
         E = self.n_envs
@@ -616,9 +618,10 @@ class OracleScene:
         u = np.zeros((E, Pd.pads_per_env, M, 3))
         na = np.zeros((E, Pd.pads_per_env), np.int32)
         mg = np.zeros((E, Pd.pads_per_env))
+        dg = np.zeros((E, Pd.pads_per_env))
         lib().or_shear_step(C.byref(self.S), C.byref(Pd), C.byref(Sh), C.byref(I), _p(an), _p(ao), _p(u), _p(na),
-                            _p(mg), int(threads))
-        return u, na, mg
+                            _p(mg), _p(dg), int(threads))
+        return (u, na, mg, dg) if drag else (u, na, mg)
 
     def markers(self, pads: dict, inputs: dict, threads: int = 0):
         """Marker displacements u [E][P][rows*cols][3] (pad frame: normal, tangent, bitangent)

@@ -1270,7 +1270,8 @@ static void env_pc_prox(const or_scene* S, const or_pcprox* pc, const or_inputs*
    moves marker j (pad position x_j = (a_j, b_j, 0)) by
    s_s Pi_n(z - e) h exp(-lambda_s |Pi_n(x_j - z)|^2). */
 static void env_shear(const or_scene* S, const or_pads* pads, const or_shear* sh, const or_inputs* in,
-                      double* anchors, int32_t* anchor_obj, double* u, int32_t* n_anchored, double* margin, int32_t e) {
+                      double* anchors, int32_t* anchor_obj, double* u, int32_t* n_anchored, double* margin,
+                      double* drag, int32_t e) {
     const int32_t L = S->max_links, P = pads->pads_per_env, M = pads->rows * pads->cols;
     double scale = in->env_params ? in->env_params[3 * e + 2] : 1.0;
     if (S->params.dr_on) {
@@ -1311,7 +1312,7 @@ static void env_shear(const or_scene* S, const or_pads* pads, const or_shear* sh
         or_advance_pose(pL0, qL0, vL, wL, in->pose_dt, pL, RL);
         int32_t count = 0;
         int64_t K = 0;
-        double mg = INFINITY;
+        double mg = INFINITY, dg = 0.0;
         for (int64_t i = 0; i < N; ++i) {
             double ph[3] = {scale * pts[3 * i], scale * pts[3 * i + 1], scale * pts[3 * i + 2]}, w[3], d[3], xl[3], r[3];
             matvec(RC, ph, w);
@@ -1323,8 +1324,9 @@ static void env_shear(const or_scene* S, const or_pads* pads, const or_shear* sh
             const double zb[3] = {z[0], z[1], z[2] + half[2]};
             double g[3];
             const double sdf = or_sdf_box(half, zb, g);
-            mg = fmin(mg, fmin(fabs(sdf + sh->eta_enter), fabs(sdf - sh->eta_exit)));
             int anchored = !isnan(an[2 * i]);
+            /* the decision this point faces: entering if free, leaving if anchored */
+            mg = fmin(mg, anchored ? fabs(sdf - sh->eta_exit) : fabs(sdf + sh->eta_enter));
             if (!anchored && sdf < -sh->eta_enter) {
                 an[2 * i] = z[0];
                 an[2 * i + 1] = z[1];
@@ -1335,6 +1337,8 @@ static void env_shear(const or_scene* S, const or_pads* pads, const or_shear* sh
             }
             count += anchored;
             const double h = sdf < 0.0 ? -sdf : 0.0;
+            if (anchored && sdf < 1e-6)
+                dg += sh->s_s * (h + hypot(z[0] - an[2 * i], z[1] - an[2 * i + 1]));
             if (anchored && h > 0.0) {
                 con[4 * K] = z[0];
                 con[4 * K + 1] = z[1];
@@ -1360,19 +1364,22 @@ static void env_shear(const or_scene* S, const or_pads* pads, const or_shear* sh
         }
         n_anchored[ep] = count;
         margin[ep] = mg;
+        drag[ep] = dg;
     }
     free(con);
 }
 
 void or_shear_step(const or_scene* S, const or_pads* pads, const or_shear* sh, const or_inputs* in, double* anchors,
-                   int32_t* anchor_obj, double* u, int32_t* n_anchored, double* margin, int32_t threads) {
+                   int32_t* anchor_obj, double* u, int32_t* n_anchored, double* margin, double* drag,
+                   int32_t threads) {
 #ifdef _OPENMP
     if (threads > 0) omp_set_num_threads(threads);
 #else
     (void)threads;
 #endif
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int32_t e = 0; e < S->n_envs; ++e) env_shear(S, pads, sh, in, anchors, anchor_obj, u, n_anchored, margin, e);
+    for (int32_t e = 0; e < S->n_envs; ++e)
+        env_shear(S, pads, sh, in, anchors, anchor_obj, u, n_anchored, margin, drag, e);
 }
 
 void or_pc_prox(const or_scene* S, const or_pcprox* pc, const or_inputs* in, double* ft, int32_t threads) {

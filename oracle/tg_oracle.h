@@ -242,10 +242,15 @@ void or_pc_prox(const or_scene* S, const or_pcprox* pc, const or_inputs* in, dou
    anchor_obj [E][P] (the object they were taken on, -1 = none; a different
    object clears them).  Out: u [E][P][rows*cols][3] the shear displacement
    of every marker (normal, tangent, bitangent components), n_anchored [E][P],
-   and margin [E][P] the least distance of a point's SDF from -eta_enter or
-   +eta_exit (how far the anchor decisions are from their thresholds). */
+   margin [E][P] the least distance of a point's SDF from the threshold it
+   faces (-eta_enter for a free point, +eta_exit for an anchored one: how far
+   the anchor decisions are from being taken the other way), and
+   drag [E][P] = s_s sum (h + |Pi_n(z - e)|) over the anchored points whose
+   SDF is below 1e-6 m (the scale of the shear's sensitivity to an error in
+   the points' coordinates). */
 void or_shear_step(const or_scene* S, const or_pads* pads, const or_shear* sh, const or_inputs* in, double* anchors,
-                   int32_t* anchor_obj, double* u, int32_t* n_anchored, double* margin, int32_t threads);
+                   int32_t* anchor_obj, double* u, int32_t* n_anchored, double* margin, double* drag,
+                   int32_t threads);
 
 #ifdef __cplusplus
 }

@@ -59,6 +59,9 @@ struct tg_scene {
     int32_t* pad_link = nullptr;
     float* pad_frame = nullptr;
     float* marker_u = nullptr;
+    float2* anchors = nullptr;         // shear anchors [E][P][shear_points]
+    int32_t* anchor_obj = nullptr;     // [E][P]
+    int32_t* n_anchored = nullptr;     // [E][P]
 
     // objects as uploaded; learned-SDF query scratch
     std::vector<ObjInfo> obj_info;
@@ -368,6 +371,13 @@ tg_status tg_create_scene(const tg_scene_desc* d, tg_scene** out) {
             return fail(nullptr, TG_ERR_INVALID_ARG,
                         "TG_SENSOR_MARKERS needs pads_per_env >= 1, rows*cols <= 1024, radius <= 4, pitch, "
                         "lambda_d, eps > 0 and the pad_link / pad_frame arrays");
+        if (pd.shear_points < 0 || pd.shear_points > 65536 ||
+            (pd.shear_points > 0 && (!std::isfinite(pd.s_s) || !(pd.lambda_s >= 0.0) || !std::isfinite(pd.lambda_s) ||
+                                     !(pd.eta_enter >= 0.0) || !(pd.eta_exit >= 0.0) || !std::isfinite(pd.eta_enter) ||
+                                     !std::isfinite(pd.eta_exit) || !(pd.thickness > 0.0) || !std::isfinite(pd.thickness))))
+            return fail(nullptr, TG_ERR_INVALID_ARG,
+                        "shear anchors need shear_points in 0..65536, finite s_s, lambda_s >= 0, eta_enter and "
+                        "eta_exit >= 0, thickness > 0");
         for (int i = 0; i < d->n_envs * pd.pads_per_env; ++i) {
             const int l = pd.pad_link[i];
             const int e = i / pd.pads_per_env;
@@ -514,6 +524,22 @@ tg_status tg_create_scene(const tg_scene_desc* d, tg_scene** out) {
         m.link_rec = s->link_rec;
         m.u = s->marker_u;
         m.err = s->err;
+        if (pd.shear_points > 0) {
+            CKC(dalloc(&s->anchors, EP * (size_t)pd.shear_points));
+            CKC(dalloc(&s->anchor_obj, EP));
+            CKC(dalloc(&s->n_anchored, EP));
+            CKC(cudaMemset(s->anchor_obj, 0xff, EP * sizeof(int32_t)));  // -1: no anchors
+            CKC(cudaMemset(s->n_anchored, 0, EP * sizeof(int32_t)));
+            m.shear_n = pd.shear_points;
+            m.s_s = (float)pd.s_s;
+            m.lambda_s = (float)pd.lambda_s;
+            m.eta_enter = (float)pd.eta_enter;
+            m.eta_exit = (float)pd.eta_exit;
+            m.half_t = (float)(0.5 * pd.thickness);
+            m.anchors = s->anchors;
+            m.anchor_obj = s->anchor_obj;
+            m.n_anchored = s->n_anchored;
+        }
         // per-offset weights: w_norm = s_d g(r), w_tan = s_d (c g / g_bar + (1 - c) rho / rho_bar)
         const double gbar = std::exp(-0.5) / std::sqrt(2.0 * pd.lambda_d), rbar = 1.0 / (2.0 * pd.eps);
         const int W = 2 * pd.radius + 1;
@@ -562,7 +588,8 @@ void tg_destroy_scene(tg_scene* s) {
                     s->ft_noisy, s->link_out, s->link_count, s->err, s->link_rec, s->s_link_pose, s->s_link_vel,
                     s->s_obj_pose, s->s_obj_vel, s->s_env_params, s->s_obj_id, s->s_mask, s->s_contact,
                     s->items_sorted, s->prox_clean, s->prox_noisy, s->pad_link, s->pad_frame,
-                    s->marker_u, s->ctl, s->nq_phi, s->nq_grad, s->pc_ft};
+                    s->marker_u, s->ctl, s->nq_phi, s->nq_grad, s->pc_ft, s->anchors, s->anchor_obj,
+                    s->n_anchored};
     for (void* p : ptrs) dfree(p);
     delete s;
 }
@@ -750,8 +777,14 @@ tg_status tg_upload_objects(tg_scene* s, const tg_object_desc* objs, int32_t n) 
             cleanup();
             return fail(s, TG_ERR_INVALID_ARG, "n_cloud must be in 0..2^24 with a cloud");
         }
-        if ((s->sensors & TG_SENSOR_PCPROX) && o.n_cloud > 0) {
-            if (const char* m = load_cloud(o, 0.5 * s->params.pc_radius, t, bufs)) {
+        if (s->markers.shear_n > 0 && o.n_cloud > s->markers.shear_n) {
+            cleanup();
+            return fail(s, TG_ERR_INVALID_ARG, "an object's n_cloud exceeds the pads' shear_points");
+        }
+        const bool pcprox = s->sensors & TG_SENSOR_PCPROX;
+        if ((pcprox || s->markers.shear_n > 0) && o.n_cloud > 0) {
+            // the cell grid serves the point-cloud proximity; the shear pass reads the points alone
+            if (const char* m = load_cloud(o, pcprox ? 0.5 * s->params.pc_radius : 1e3, t, bufs)) {
                 cleanup();
                 return fail(s, TG_ERR_INVALID_ARG, m);
             }
@@ -794,6 +827,7 @@ tg_status tg_reset_envs(tg_scene* s, const uint8_t* env_mask, uint32_t episode, 
     const uint8_t* m = nullptr;
     if (env_mask) CK(s, stage(env_mask, s->s_mask, (size_t)s->E, st, &m));
     CK(s, launch_reset(step_args(s), s->n_items, m, episode, s->episode, st));
+    if (s->anchor_obj) CK(s, launch_shear_reset(s->anchor_obj, s->E, s->markers.pads_per_env, m, st));
     return TG_OK;
 }
 
@@ -1162,6 +1196,7 @@ size_t tg_channel_bytes(const tg_scene* s, int32_t ch) {
                    ? (size_t)s->E * s->markers.pads_per_env * s->markers.rows * s->markers.cols * 12
                    : 0;
     case TG_CH_PC_FT: return (s->sensors & TG_SENSOR_PCPROX) ? T * 24 : 0;
+    case TG_CH_SHEAR_ANCHORS: return s->n_anchored ? (size_t)s->E * s->markers.pads_per_env * 4 : 0;
     default: return 0;
     }
 }
@@ -1180,6 +1215,7 @@ tg_status tg_get_buffer(tg_scene* s, int32_t ch, int32_t noisy, void** ptr, size
     case TG_CH_PROX: p = (s->sensors & TG_SENSOR_PROX) ? (noisy ? s->prox_noisy : s->prox_clean) : nullptr; break;
     case TG_CH_MARKER: p = (s->sensors & TG_SENSOR_MARKERS) ? s->marker_u : nullptr; break;
     case TG_CH_PC_FT: p = (s->sensors & TG_SENSOR_PCPROX) ? s->pc_ft : nullptr; break;
+    case TG_CH_SHEAR_ANCHORS: p = s->n_anchored; break;
     default: break;
     }
     if (!p) return fail(s, TG_ERR_INVALID_ARG, "channel has no device view (or its sensor is off)");
@@ -1230,41 +1266,56 @@ const char* tg_last_error(const tg_scene* s) { return s ? s->last_error.c_str() 
 
 static const uint64_t kStateMagic = 0x3130455441545354ull;  // "TSTATE01"
 
+// shear anchor slots of the scene (0 when the shear anchors are off)
+static size_t shear_slots(const tg_scene* s) {
+    return s->anchors ? (size_t)s->E * s->markers.pads_per_env * s->markers.shear_n : 0;
+}
+
 tg_status tg_save_state(tg_scene* s, void* buf, size_t* size) {
     if (!s || !size) return fail(s, TG_ERR_INVALID_ARG, "scene or size is NULL");
     const size_t T = (size_t)s->T, E = (size_t)s->E;
-    const size_t need = 32 + T + 3 * 8 * T * 4 + E * 4;
+    const size_t A = shear_slots(s), EP = A ? E * s->markers.pads_per_env : 0;
+    const size_t need = 32 + T + 3 * 8 * T * 4 + E * 4 + A * 8 + EP * 4;
     if (!buf) { *size = need; return TG_OK; }
     if (*size != need) return fail(s, TG_ERR_INVALID_ARG, "state buffer size mismatch");
     CK(s, cudaDeviceSynchronize());
     unsigned char* p = (unsigned char*)buf;
-    uint64_t hdr[4] = {kStateMagic, (uint64_t)T, (uint64_t)E, 0};
+    uint64_t hdr[4] = {kStateMagic, (uint64_t)T, (uint64_t)E, (uint64_t)A};
     memcpy(p, hdr, 32);
     p += 32;
     CK(s, cudaMemcpy(p, s->flags, T, cudaMemcpyDeviceToHost)); p += T;
     CK(s, cudaMemcpy(p, s->hyst_prev, 8 * T * 4, cudaMemcpyDeviceToHost)); p += 8 * T * 4;
     CK(s, cudaMemcpy(p, s->hyst_xi, 8 * T * 4, cudaMemcpyDeviceToHost)); p += 8 * T * 4;
     CK(s, cudaMemcpy(p, s->drift, 8 * T * 4, cudaMemcpyDeviceToHost)); p += 8 * T * 4;
-    CK(s, cudaMemcpy(p, s->episode, E * 4, cudaMemcpyDeviceToHost));
+    CK(s, cudaMemcpy(p, s->episode, E * 4, cudaMemcpyDeviceToHost)); p += E * 4;
+    if (A) {
+        CK(s, cudaMemcpy(p, s->anchors, A * 8, cudaMemcpyDeviceToHost)); p += A * 8;
+        CK(s, cudaMemcpy(p, s->anchor_obj, EP * 4, cudaMemcpyDeviceToHost));
+    }
     return TG_OK;
 }
 
 tg_status tg_load_state(tg_scene* s, const void* buf, size_t size) {
     if (!s || !buf) return fail(s, TG_ERR_INVALID_ARG, "scene or buf is NULL");
     const size_t T = (size_t)s->T, E = (size_t)s->E;
-    const size_t need = 32 + T + 3 * 8 * T * 4 + E * 4;
+    const size_t A = shear_slots(s), EP = A ? E * s->markers.pads_per_env : 0;
+    const size_t need = 32 + T + 3 * 8 * T * 4 + E * 4 + A * 8 + EP * 4;
     if (size != need) return fail(s, TG_ERR_INVALID_ARG, "state buffer size mismatch");
     const unsigned char* p = (const unsigned char*)buf;
     uint64_t hdr[4];
     memcpy(hdr, p, 32);
-    if (hdr[0] != kStateMagic || hdr[1] != T || hdr[2] != E) return fail(s, TG_ERR_INVALID_ARG, "state buffer is not from a scene of this shape");
+    if (hdr[0] != kStateMagic || hdr[1] != T || hdr[2] != E || hdr[3] != A) return fail(s, TG_ERR_INVALID_ARG, "state buffer is not from a scene of this shape");
     p += 32;
     CK(s, cudaDeviceSynchronize());
     CK(s, cudaMemcpy(s->flags, p, T, cudaMemcpyHostToDevice)); p += T;
     CK(s, cudaMemcpy(s->hyst_prev, p, 8 * T * 4, cudaMemcpyHostToDevice)); p += 8 * T * 4;
     CK(s, cudaMemcpy(s->hyst_xi, p, 8 * T * 4, cudaMemcpyHostToDevice)); p += 8 * T * 4;
     CK(s, cudaMemcpy(s->drift, p, 8 * T * 4, cudaMemcpyHostToDevice)); p += 8 * T * 4;
-    CK(s, cudaMemcpy(s->episode, p, E * 4, cudaMemcpyHostToDevice));
+    CK(s, cudaMemcpy(s->episode, p, E * 4, cudaMemcpyHostToDevice)); p += E * 4;
+    if (A) {
+        CK(s, cudaMemcpy(s->anchors, p, A * 8, cudaMemcpyHostToDevice)); p += A * 8;
+        CK(s, cudaMemcpy(s->anchor_obj, p, EP * 4, cudaMemcpyHostToDevice));
+    }
     return TG_OK;
 }
 

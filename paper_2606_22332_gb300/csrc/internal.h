@@ -172,6 +172,12 @@ struct MarkerArgs {
     float w_tan[(2 * kMaxPadRadius + 1) * (2 * kMaxPadRadius + 1)];   // s_d (c g / g_bar + (1 - c) rho / rho_bar)
     float* u;                         // [E][P][rows*cols][3]
     unsigned int* err;
+    // shear anchors (off when shear_n == 0)
+    int shear_n;                      // anchor slots per pad
+    float s_s, lambda_s, eta_enter, eta_exit, half_t;  // half_t: half the elastomer thickness
+    float2* anchors;                  // [E][P][shear_n]: (tangent, bitangent), NaN = none
+    int32_t* anchor_obj;              // [E][P]: object the anchors belong to, -1 = none
+    int32_t* n_anchored;              // [E][P]
 };
 
 struct PoseArgs {
@@ -213,6 +219,9 @@ cudaError_t launch_build_cells(const void* values, const int dims[3], int fp16, 
 cudaError_t launch_prox(const StepArgs& a, int n_items, cudaStream_t s);
 cudaError_t launch_pc_prox(const StepArgs& a, int n_items, cudaStream_t s);
 cudaError_t launch_markers(const MarkerArgs& m, cudaStream_t s);
+// anchor_obj = -1 for the pads of the masked envs (all when mask is null)
+cudaError_t launch_shear_reset(int32_t* anchor_obj, int n_envs, int pads_per_env, const uint8_t* mask,
+                               cudaStream_t s);
 cudaError_t launch_unpack_contact(const uint8_t* flags, int64_t n, int noisy, uint8_t* out, cudaStream_t s);
 
 // learned SDF (nsdf.cu)

@@ -292,25 +292,38 @@ cudaError_t launch_prox(const StepArgs& a, int n_items, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Elastomer markers: h = max(0, -phi) at every marker of the pad, then the
 // dilation sum of Eqs. 20-21 over the neighbourhood, with the per-offset
-// weights computed on the host.
+// weights computed on the host; with shear anchors on, the shear of Eq. 19
+// is added (one chunk of 256 tracked points at a time: anchor update, the
+// contributing points compacted in point order into shared memory, then every
+// marker sums their Gaussian-weighted drags).
 // ---------------------------------------------------------------------------
 constexpr int kMarkerThreads = 256;
 
 __global__ void __launch_bounds__(kMarkerThreads) marker_kernel(const MarkerArgs m) {
     __shared__ float h_s[kMaxPadMarkers];
     __shared__ float ha_s[kMaxPadMarkers];
+    __shared__ float ut_s[kMaxPadMarkers];   // shear, tangent
+    __shared__ float ub_s[kMaxPadMarkers];   // shear, bitangent
+    __shared__ float4 con_s[kMarkerThreads]; // contributing points of a chunk: z_t, z_b, drag_t, drag_b
+    __shared__ int warp_cnt[kMarkerThreads / 32];
+    __shared__ int anchored_s;
     __shared__ float rec[kLinkRec];
     __shared__ ObjDev obj_s;
     const int pad = blockIdx.x;  // e * P + p
     const int e = pad / m.pads_per_env;
     const int l = m.pad_link[pad];
     const int M = m.rows * m.cols;
+    const int oid = min(max(m.obj_id[e], 0), m.n_objects - 1);
     if (threadIdx.x < kLinkRec) rec[threadIdx.x] = m.link_rec[(size_t)(e * m.max_links + l) * kLinkRec + threadIdx.x];
-    if (threadIdx.x == 0) obj_s = m.objects[min(max(m.obj_id[e], 0), m.n_objects - 1)];
+    if (threadIdx.x == 0) {
+        obj_s = m.objects[oid];
+        anchored_s = 0;
+    }
     __syncthreads();
     const float* fr = m.pad_frame + (size_t)pad * 9;
     const float3 o = f3(fr[0], fr[1], fr[2]), nrm = f3(fr[3], fr[4], fr[5]), tu = f3(fr[6], fr[7], fr[8]);
     const float3 tv = cross(nrm, tu);
+    const float half_a = 0.5f * m.rows * m.pitch, half_b = 0.5f * m.cols * m.pitch;
     for (int j = threadIdx.x; j < M; j += kMarkerThreads) {
         const int r = j / m.cols, c = j - r * m.cols;
         const float sa = (r - 0.5f * (m.rows - 1)) * m.pitch, sb = (c - 0.5f * (m.cols - 1)) * m.pitch;
@@ -320,8 +333,91 @@ __global__ void __launch_bounds__(kMarkerThreads) marker_kernel(const MarkerArgs
         const float h = phi < 0.0f ? -phi : 0.0f;
         h_s[j] = h;
         ha_s[j] = h > 0.0f ? powf(h, m.alpha) : 0.0f;
+        ut_s[j] = 0.0f;
+        ub_s[j] = 0.0f;
+    }
+    if (m.shear_n > 0) {
+        float2* an = m.anchors + (size_t)pad * m.shear_n;
+        // anchors taken on another object (or cleared by a reset) read as none and are rewritten
+        const bool fresh = m.anchor_obj[pad] != oid;
+        const int N = obj_s.pc_pts ? min(obj_s.pc_n, m.shear_n) : 0;
+        const float s = rec[38], s2 = s * s;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        int count = 0;
+        for (int c0 = 0; c0 < N; c0 += kMarkerThreads) {
+            const int i = c0 + threadIdx.x;
+            bool contrib = false;
+            float4 cv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < N) {
+                const float4 p = __ldg(obj_s.pc_pts + i);
+                // link frame x = s^2 M^T (p^ - t), then the pad's sensor frame
+                const float dx = p.x - rec[18], dy = p.y - rec[19], dz = p.z - rec[20];
+                const float3 xl = f3(s2 * (rec[0] * dx + rec[3] * dy + rec[6] * dz),
+                                     s2 * (rec[1] * dx + rec[4] * dy + rec[7] * dz),
+                                     s2 * (rec[2] * dx + rec[5] * dy + rec[8] * dz));
+                const float3 r = xl - o;
+                const float za = dot(r, tu), zb = dot(r, tv), zn = dot(r, nrm);
+                // SDF of the elastomer box (centre -half_t along the normal)
+                const float qa = fabsf(za) - half_a, qb = fabsf(zb) - half_b, qc = fabsf(zn + m.half_t) - m.half_t;
+                const float oa = fmaxf(qa, 0.f), ob = fmaxf(qb, 0.f), oc = fmaxf(qc, 0.f);
+                const float sdf = sqrtf(oa * oa + ob * ob + oc * oc) + fminf(fmaxf(qa, fmaxf(qb, qc)), 0.f);
+                float2 ea = fresh ? make_float2(NAN, NAN) : an[i];
+                bool anchored = !isnan(ea.x);
+                bool write = fresh;
+                if (!anchored && sdf < -m.eta_enter) {
+                    ea = make_float2(za, zb);
+                    anchored = write = true;
+                } else if (anchored && sdf > m.eta_exit) {
+                    ea = make_float2(NAN, NAN);
+                    anchored = false;
+                    write = true;
+                }
+                if (write) an[i] = ea;
+                count += anchored;
+                const float h = sdf < 0.0f ? -sdf : 0.0f;
+                if (anchored && h > 0.0f) {
+                    contrib = true;
+                    cv = make_float4(za, zb, m.s_s * (za - ea.x) * h, m.s_s * (zb - ea.y) * h);
+                }
+            }
+            // compaction in point order
+            const unsigned bal = __ballot_sync(0xffffffffu, contrib);
+            if (lane == 0) warp_cnt[warp] = __popc(bal);
+            __syncthreads();
+            int off = 0, K = 0;
+#pragma unroll
+            for (int w = 0; w < kMarkerThreads / 32; ++w) {
+                off += w < warp ? warp_cnt[w] : 0;
+                K += warp_cnt[w];
+            }
+            if (contrib) con_s[off + __popc(bal & ((1u << lane) - 1u))] = cv;
+            __syncthreads();
+            if (K > 0) {
+                for (int j = threadIdx.x; j < M; j += kMarkerThreads) {
+                    const int r = j / m.cols, c = j - r * m.cols;
+                    const float sa = (r - 0.5f * (m.rows - 1)) * m.pitch, sb = (c - 0.5f * (m.cols - 1)) * m.pitch;
+                    float ut = ut_s[j], ub = ub_s[j];
+                    for (int k = 0; k < K; ++k) {
+                        const float4 q = con_s[k];
+                        const float da = sa - q.x, db = sb - q.y;
+                        const float g = expf(-m.lambda_s * (da * da + db * db));
+                        ut = fmaf(q.z, g, ut);
+                        ub = fmaf(q.w, g, ub);
+                    }
+                    ut_s[j] = ut;
+                    ub_s[j] = ub;
+                }
+            }
+            __syncthreads();  // con_s and warp_cnt are reused by the next chunk
+        }
+        count = __reduce_add_sync(0xffffffffu, count);
+        if (lane == 0 && count) atomicAdd(&anchored_s, count);
     }
     __syncthreads();
+    if (m.shear_n > 0 && threadIdx.x == 0) {
+        m.n_anchored[pad] = anchored_s;
+        m.anchor_obj[pad] = oid;
+    }
     const int W = 2 * m.radius + 1;
     for (int j = threadIdx.x; j < M; j += kMarkerThreads) {
         const int r = j / m.cols, c = j - r * m.cols;
@@ -345,8 +441,8 @@ __global__ void __launch_bounds__(kMarkerThreads) marker_kernel(const MarkerArgs
         }
         float* out = m.u + ((size_t)pad * M + j) * 3;
         out[0] = un;
-        out[1] = ut;
-        out[2] = uv;
+        out[1] = ut + ut_s[j];
+        out[2] = uv + ub_s[j];
     }
 }
 
@@ -354,6 +450,19 @@ cudaError_t launch_markers(const MarkerArgs& m, cudaStream_t s) {
     const int n = m.n_envs * m.pads_per_env;
     if (n == 0) return cudaSuccess;
     marker_kernel<<<n, kMarkerThreads, 0, s>>>(m);
+    return cudaGetLastError();
+}
+
+__global__ void shear_reset_kernel(int32_t* anchor_obj, int n_pads, int pads_per_env, const uint8_t* mask) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_pads && (!mask || mask[i / pads_per_env])) anchor_obj[i] = -1;
+}
+
+cudaError_t launch_shear_reset(int32_t* anchor_obj, int n_envs, int pads_per_env, const uint8_t* mask,
+                               cudaStream_t s) {
+    const int n = n_envs * pads_per_env;
+    if (n == 0) return cudaSuccess;
+    shear_reset_kernel<<<(n + 255) / 256, 256, 0, s>>>(anchor_obj, n, pads_per_env, mask);
     return cudaGetLastError();
 }
 

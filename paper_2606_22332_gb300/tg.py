@@ -30,7 +30,7 @@ STATUS = {0: "TG_OK", 1: "TG_ERR_INVALID_ARG", 2: "TG_ERR_OOM", 3: "TG_ERR_CUDA"
 TG_OBJ_SPHERE, TG_OBJ_BOX, TG_OBJ_PLANE, TG_OBJ_MESH, TG_OBJ_GRID, TG_OBJ_NEURAL = 0, 1, 2, 3, 4, 5
 NSDF_TABLE_ENTRIES, NSDF_WEIGHTS = 16 * 65536, 6208
 (CH_CONTACT, CH_DEPTH, CH_DIST, CH_FORCE_TORQUE, CH_LINK_WRENCH, CH_LINK_COUNT, CH_STATE_FLAGS, CH_PROX, CH_MARKER,
- CH_PC_FT) = range(10)
+ CH_PC_FT, CH_SHEAR_ANCHORS) = range(11)
 TG_SENSOR_DIST, TG_SENSOR_PROX, TG_SENSOR_MARKERS, TG_SENSOR_PCPROX = 0x1, 0x2, 0x4, 0x8
 LINK_REC = 18
 
@@ -60,7 +60,9 @@ class PadDesc(C.Structure):
     _fields_ = [("pads_per_env", C.c_int32), ("rows", C.c_int32), ("cols", C.c_int32), ("pitch", C.c_double),
                 ("pad_link", C.c_void_p), ("pad_frame", C.c_void_p),
                 ("s_d", C.c_double), ("alpha", C.c_double), ("lambda_d", C.c_double), ("c", C.c_double),
-                ("eps", C.c_double), ("radius", C.c_int32)]
+                ("eps", C.c_double), ("radius", C.c_int32), ("shear_points", C.c_int32),
+                ("s_s", C.c_double), ("lambda_s", C.c_double), ("eta_enter", C.c_double), ("eta_exit", C.c_double),
+                ("thickness", C.c_double)]
 
 
 class SceneDesc(C.Structure):
@@ -296,6 +298,11 @@ class Scene:
             for k in ("s_d", "alpha", "lambda_d", "c", "eps"):
                 setattr(pd, k, float(pads[k]))
             pd.radius = int(pads["radius"])
+            # shear anchors: on when pads carries shear_points > 0
+            pd.shear_points = int(pads.get("shear_points", 0))
+            for k, dflt in (("s_s", 100.0), ("lambda_s", 2000.0), ("eta_enter", 1e-5), ("eta_exit", 1e-4),
+                            ("thickness", 2e-3)):
+                setattr(pd, k, float(pads.get(k, dflt)))
         h = C.c_void_p()
         _check(_lib.tg_create_scene(C.byref(d), C.byref(h)), None)
         self.h = h
@@ -403,7 +410,12 @@ class Scene:
                 CH_FORCE_TORQUE: ((6, T), np.float32), CH_LINK_WRENCH: ((EL, LINK_REC), np.float32),
                 CH_LINK_COUNT: ((EL, 2), np.int32), CH_STATE_FLAGS: ((T,), np.uint8),
                 CH_PROX: ((T,), np.float32),
-                CH_MARKER: ((self._n_markers(), 3), np.float32), CH_PC_FT: ((6, T), np.float32)}[ch]
+                CH_MARKER: ((self._n_markers(), 3), np.float32), CH_PC_FT: ((6, T), np.float32),
+                CH_SHEAR_ANCHORS: ((self._n_pads(),), np.int32)}[ch]
+
+    def _n_pads(self):
+        p = self.pads
+        return 0 if p is None else self.n_envs * int(p["pads_per_env"])
 
     def _n_markers(self):
         p = self.pads
