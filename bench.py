@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--pc-points", type=int, default=5000, help="tracked surface points per object")
     ap.add_argument("--no-shear", action="store_true", help="skip the elastomer shear-anchor line")
     ap.add_argument("--shear-points", type=int, default=1000, help="tracked points per object for the shear anchors")
+    ap.add_argument("--no-temperature", action="store_true", help="skip the TemperatureGrid line")
     ap.add_argument("--neural-objects", type=int, default=64, help="objects given a learned SDF (0: skip the line)")
     ap.add_argument("--neural-points", type=int, default=2_000_000, help="labelled training points per object")
     ap.add_argument("--neural-steps", type=int, default=3000, help="Adam steps per object")
@@ -371,6 +372,72 @@ def traffic_from_profile():
     return rec.get("dram_bytes_per_launch_full")
 
 
+TEMP_BYTES_PER_CELL = 16.0  # T and T_meas, each read and written once per step
+
+
+def temperature_line(args, dev, stream, pg, peaks_fn):
+    """TemperatureGrid: one 8 x 8 x 16 grid per fingertip link (5 per env) at
+    200 Hz, 20 % of the grids touching a ball each step; cells/s, the step
+    kernel's HBM roofline and the oracle on a sample of grids."""
+    import torch
+
+    from paper_2606_22332_gb300 import tg
+    from paper_2606_22332_gb300 import workload as W
+    from paper_2606_22332_gb300.dist import max_over_ranks
+
+    dims = (8, 8, 16)
+    wl = W.temperature_grids(n_envs=args.envs, links_per_env=5, dims=dims)
+    G, cells = wl["G"], dims[0] * dims[1] * dims[2]
+    rng = np.random.default_rng(20260012)
+    contacts = W.temperature_contacts(rng, G, dims, share=0.2)
+    cd = {k: torch.as_tensor(v, device=dev) for k, v in contacts.items()}
+    grids = tg.TempGrid(dims, wl["voxel"], wl["material"])
+    dt, t_amb = 1.0 / 200.0, 22.0
+    s_ptr = stream.cuda_stream
+    for _ in range(args.warmup):
+        grids.step(dt, t_amb, contacts=cd, stream=s_ptr)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        grids.step(dt, t_amb, contacts=cd, stream=s_ptr)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(t0.elapsed_time(t1), dev) / args.steps
+    tmax = float(grids.buffer().max().item())
+    grids.close()
+    peak, kind = peaks_fn()
+    achieved = TEMP_BYTES_PER_CELL * G * cells / (ms * 1e-3) / 1e9
+    out = {"sensors": f"TemperatureGrid: {G} grids (5 fingertip links x {args.envs} envs) of 8x8x16 cells, "
+                      "2.5 mm voxels, silicone-like skin, 200 Hz, 20 % of the grids touching a ball (1 in 8 hot, 45 C)",
+           "value": G * cells / (ms * 1e-3), "unit": "grid-cells/s", "ms_per_step": ms,
+           "contacts_per_step": int(contacts["offsets"][-1]), "max_cell_temp_c": round(tmax, 3),
+           "gpu_launches": args.steps,
+           "roofline": {"bound": "hbm", "kernel": "temp_step_kernel", "achieved": round(achieved, 1),
+                        "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": kind,
+                        "algorithmic_bytes_per_cell": TEMP_BYTES_PER_CELL}}
+    if not args.no_cpu_baseline and dist_env()[1] == 0:
+        import time
+
+        from oracle import temperature as TO
+
+        n_s = min(G, 256)
+        T0 = np.full(dims, 22.0)
+        tc = time.perf_counter()
+        for g in range(n_s):
+            m = wl["material"][g].astype(np.float64)
+            mat = dict(k=m[0], rho=m[1], cp=m[2], emissivity=m[3], h=m[4], tau=m[5])
+            cs = [(int(contacts["cell"][c]), float(contacts["temp"][c]), float(contacts["k"][c]),
+                   float(contacts["area"][c])) for c in range(contacts["offsets"][g], contacts["offsets"][g + 1])]
+            TO.step(T0, T0, wl["voxel"][g].astype(np.float64), mat, dt, t_amb, contacts=cs)
+        el = time.perf_counter() - tc
+        out["cpu_baseline"] = {"value": n_s * cells / el, "unit": "grid-cells/s", "cores": 1, "kind": "oracle",
+                               "sample": f"{n_s} grids x 1 step of the same workload (numpy FFT, one core)"}
+    return out
+
+
 def run_tg(args):
     import torch
 
@@ -578,6 +645,9 @@ def run_tg(args):
                  "anchored_points_per_pad": round(n_anch / max(n_pads, 1), 2),
                  "anchor_state_bytes": n_pads * args.shear_points * 8,
                  "gpu_launches": (launches_per_step + 1) * args.steps}
+    temp = None
+    if not args.no_temperature:
+        temp = temperature_line(args, dev, stream, pg, peaks)
     neural = None
     if args.neural_objects > 0 and ws == 1:
         neural = neural_line(args, wl, objs, d_in, dev, sched, stream, step_inputs, t_max)
@@ -612,6 +682,7 @@ def run_tg(args):
             "full_sensor_set": full,
             "point_cloud_proximity": pcl,
             "elastomer_shear": shear,
+            "temperature_grid": temp,
             "neural_sdf": neural,
             "setup_s": {"bake": round(bake_s, 2), "total": round(time.time() - t_setup, 1)},
         }

@@ -442,6 +442,84 @@ tg_status tg_mesh_sdf(const float* verts, int32_t n_verts, const int32_t* faces,
 tg_status tg_mesh_sdf_noalloc(const float* verts, int32_t n_verts, const int32_t* faces, int32_t n_faces,
                               const float* points, int64_t n, float* phi, float* grad, tg_stream stream);
 
+
+/* ---- TemperatureGrid (Appendix "TemperatureGrid Sensor Model") -----------
+
+   G grids of nx x ny x nz cells (one per voxelized sensor link; cell (i,j,k)
+   at flat index (i*ny + j)*nz + k, per-grid voxel size (dx, dy, dz)).  One
+   step advances every grid's cell temperatures T (Celsius) by
+   1. implicit spectral diffusion: the grid mirror-padded to twice its size on
+      every axis (zero-flux walls), every Fourier mode divided by
+      1 + alpha dt max(k^2, k2_floor), alpha = k / (rho c_p), cropped back;
+   2. the internal source: T += dt q / (dz rho c_p), q in W/m^2 per cell;
+   3. contact conduction: a contact on cell c with a body at T_other of
+      conductivity k_b over area A adds dt k_eff (T_other - T_c) (A / V)^2 /
+      (rho c_p), k_eff = 2 k k_b / (k + k_b), V the cell volume (the flux
+      k_eff dT / L over L = V / A, times A / V); every contact reads the field
+      after the source and the changes add;
+   4. radiation and convection on every cell of a face of the grid:
+      T -= dt (emissivity sigma (T_K^4 - T_amb,K^4) + h (T - T_amb)) / (rho c_p),
+      T_K = T + 273.15, as the paper prints it;
+   and the measured readout follows with a first-order lag:
+   T_meas += dt / tau (T - T_meas), or T_meas = T when tau <= 0.
+   Buffers are device-resident and library-owned. */
+typedef struct tg_temp tg_temp;
+
+typedef struct {
+    int32_t n_grids;                  /* G >= 1 */
+    int32_t nx, ny, nz;               /* each 4, 8, 16 or 32; nx*ny*(nz+1) <= 12288 */
+    const float* voxel;               /* host [G][3]: dx, dy, dz (m), > 0 */
+    const float* material;            /* host [G][7]: k (W/m/K) >= 0, rho (kg/m^3) > 0, c_p (J/kg/K) > 0,
+                                         emissivity >= 0, h (W/m^2/K) >= 0, tau (s), base temperature (C) */
+    double k2_floor;                  /* floor of k^2 (1/m^2) that regularises the zero mode, >= 0 */
+} tg_temp_desc;
+
+typedef struct {
+    double dt;                        /* step (s), > 0 */
+    double t_amb;                     /* ambient temperature (C) */
+    const float* source;              /* device [G][cells] (W/m^2) or NULL */
+    int32_t n_contacts;               /* C >= 0 */
+    const int32_t* contact_offsets;   /* host or device [G+1]: grid g's contacts are offsets[g] .. offsets[g+1]-1 */
+    const int32_t* contact_cell;      /* host or device [C]: flat cell index */
+    const float* contact_temp;        /* host or device [C]: T_other (C) */
+    const float* contact_k;           /* host or device [C]: k_b (W/m/K), > 0 */
+    const float* contact_area;        /* host or device [C]: A (m^2), > 0 (tg_contact_area) */
+} tg_temp_inputs;
+
+/* Create G grids at their base temperatures (T = T_meas = base).  Errors:
+   TG_ERR_INVALID_ARG (sizes, non-finite or out-of-range values), TG_ERR_OOM,
+   TG_ERR_CUDA.  *out is NULL on failure. */
+tg_status tg_temp_create(const tg_temp_desc* desc, tg_temp** out);
+void tg_temp_destroy(tg_temp* grids);
+/* Back to the base temperature for the masked grids (grid_mask host or
+   device [G], NULL = all), ordered on `stream`. */
+tg_status tg_temp_reset(tg_temp* grids, const uint8_t* grid_mask, tg_stream stream);
+/* Overwrite the fields from host or device [G][cells] arrays (measured NULL:
+   the measured readout takes `field`). */
+tg_status tg_temp_set(tg_temp* grids, const float* field, const float* measured, tg_stream stream);
+/* One step, ordered on `stream`.  Host contact arrays are checked (offsets
+   from 0 to C, non-decreasing; cells in range; k_b, A > 0) and staged, and the
+   call waits for the staging; device arrays are used in place (the kernel
+   clamps offsets and skips cells out of range).  Errors: TG_ERR_INVALID_ARG,
+   TG_ERR_CUDA. */
+tg_status tg_temp_step(tg_temp* grids, const tg_temp_inputs* in, tg_stream stream);
+/* Copy T (measured = 0) or T_meas (measured = 1), [G][cells] float, into dst
+   (host or device); dst_bytes must be 4 G nx ny nz. */
+tg_status tg_temp_read(tg_temp* grids, int32_t measured, float* dst, size_t dst_bytes, tg_stream stream);
+/* Device view of T or T_meas (no copy). */
+tg_status tg_temp_buffer(tg_temp* grids, int32_t measured, float** ptr);
+/* Contact area of n_pairs contact manifolds (Appendix "TemperatureGrid Sensor
+   Model", contact area estimation): points device [n_pairs][max_points][3]
+   with n_points device [n_pairs] valid, depth device [n_pairs] the
+   penetration delta.  The points are projected on their best-fit plane,
+   ordered by polar angle about their centroid, and the shoelace area taken;
+   fewer than three points give a disk of radius delta (pi delta^2); the
+   result is floored at pi (d_w delta)^2.  max_points 1..16.  area: device
+   [n_pairs]. */
+tg_status tg_contact_area(const float* points, const int32_t* n_points, const float* depth, int32_t n_pairs,
+                          int32_t max_points, double d_w, float* area, tg_stream stream);
+const char* tg_temp_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

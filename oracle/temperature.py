@@ -24,8 +24,10 @@ radiation and convection), and the measured readout's first-order lag:
 The contact area of a manifold: its points projected on their mean plane
 (the plane through the centroid normal to the least-variance direction),
 ordered by polar angle about the centroid, shoelace polygon area; fewer than
-three points give pi delta; the conduction update floors the area at
-pi d_w delta.
+three points give a disk of radius delta, pi delta^2; the conduction update
+floors the area at pi (d_w delta)^2.  (The paper prints the disk as "pi
+delta" and the floor as "pi d_w delta", lengths where an area is meant; read
+as the disk of radius delta and of radius d_w delta.)
 """
 from __future__ import annotations
 
@@ -86,10 +88,10 @@ def step(T, T_meas, d, mat: dict, dt: float, t_amb: float, source=None, contacts
 
 
 def contact_area(points, depth: float, d_w: float = 1.0) -> float:
-    """Contact area of one manifold, floored at pi d_w depth."""
+    """Contact area of one manifold, floored at pi (d_w depth)^2."""
     p = np.asarray(points, np.float64).reshape(-1, 3)
     if len(p) < 3:
-        area = np.pi * depth
+        area = np.pi * depth * depth
     else:
         c = p.mean(0)
         _, _, vt = np.linalg.svd(p - c)
@@ -98,4 +100,4 @@ def contact_area(points, depth: float, d_w: float = 1.0) -> float:
         order = np.argsort(np.arctan2(y, x), kind="stable")
         x, y = x[order], y[order]
         area = 0.5 * abs(np.dot(x, np.roll(y, -1)) - np.dot(y, np.roll(x, -1)))
-    return max(area, np.pi * d_w * depth)
+    return max(area, np.pi * (d_w * depth) ** 2)

@@ -82,6 +82,17 @@ class ObjectDesc(C.Structure):
                 ("cloud", C.c_void_p), ("n_cloud", C.c_int64)]
 
 
+class TempDesc(C.Structure):
+    _fields_ = [("n_grids", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("voxel", C.c_void_p), ("material", C.c_void_p), ("k2_floor", C.c_double)]
+
+
+class TempInputs(C.Structure):
+    _fields_ = [("dt", C.c_double), ("t_amb", C.c_double), ("source", C.c_void_p), ("n_contacts", C.c_int32),
+                ("contact_offsets", C.c_void_p), ("contact_cell", C.c_void_p), ("contact_temp", C.c_void_p),
+                ("contact_k", C.c_void_p), ("contact_area", C.c_void_p)]
+
+
 class StepInputs(C.Structure):
     _fields_ = [("link_pose", C.c_void_p), ("link_vel", C.c_void_p), ("obj_pose", C.c_void_p),
                 ("obj_vel", C.c_void_p), ("obj_id", C.c_void_p), ("env_params", C.c_void_p),
@@ -137,12 +148,23 @@ _lib.tg_nsdf_train.argtypes = [_vp, _vp, _vp, C.c_int64, _i32, _i32, C.c_double,
 _lib.tg_nsdf_probe.argtypes = [_vp, _vp, _i32, _vp, _i32, _vp, C.c_int64, C.POINTER(C.c_double),
                                C.POINTER(C.c_double), _vp]
 _lib.tg_nsdf_last_error.restype = C.c_char_p
+_lib.tg_temp_create.argtypes = [C.POINTER(TempDesc), C.POINTER(_vp)]
+_lib.tg_temp_destroy.argtypes = [_vp]
+_lib.tg_temp_destroy.restype = None
+_lib.tg_temp_reset.argtypes = [_vp, _vp, _vp]
+_lib.tg_temp_set.argtypes = [_vp, _vp, _vp, _vp]
+_lib.tg_temp_step.argtypes = [_vp, C.POINTER(TempInputs), _vp]
+_lib.tg_temp_read.argtypes = [_vp, _i32, _vp, _sz, _vp]
+_lib.tg_temp_buffer.argtypes = [_vp, _i32, C.POINTER(_vp)]
+_lib.tg_contact_area.argtypes = [_vp, _vp, _vp, _i32, _i32, C.c_double, _vp, _vp]
+_lib.tg_temp_last_error.restype = C.c_char_p
 for _f in ("tg_create_scene", "tg_upload_objects", "tg_reset_envs", "tg_step_sensors", "tg_read_taxels",
            "tg_get_buffer", "tg_sync", "tg_save_state", "tg_load_state", "tg_bake_grid", "tg_mesh_sdf",
            "tg_profile_enable", "tg_profile_read", "tg_mesh_sdf_noalloc", "tg_graph_capture", "tg_graph_launch",
            "tg_graph_seek", "tg_graph_release", "tg_set_schedule", "tg_get_schedule", "tg_autotune", "tg_object_info",
            "tg_nsdf_create", "tg_nsdf_set_params", "tg_nsdf_get_params", "tg_nsdf_eval", "tg_nsdf_loss_grad",
-           "tg_nsdf_train", "tg_nsdf_probe"):
+           "tg_nsdf_train", "tg_nsdf_probe", "tg_temp_create", "tg_temp_reset", "tg_temp_set", "tg_temp_step",
+           "tg_temp_read", "tg_temp_buffer", "tg_contact_area"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ["tg_create_scene", "tg_destroy_scene", "tg_max_link_taxels", "tg_upload_objects", "tg_reset_envs",
@@ -151,7 +173,9 @@ EXPORTED = ["tg_create_scene", "tg_destroy_scene", "tg_max_link_taxels", "tg_upl
             "tg_mesh_sdf_noalloc", "tg_graph_capture", "tg_graph_launch", "tg_graph_seek", "tg_graph_release",
             "tg_set_schedule", "tg_get_schedule", "tg_autotune", "tg_object_info", "tg_nsdf_create",
             "tg_nsdf_destroy", "tg_nsdf_set_params", "tg_nsdf_get_params", "tg_nsdf_eval", "tg_nsdf_loss_grad",
-            "tg_nsdf_train", "tg_nsdf_probe", "tg_nsdf_last_error"]
+            "tg_nsdf_train", "tg_nsdf_probe", "tg_nsdf_last_error", "tg_temp_create", "tg_temp_destroy",
+            "tg_temp_reset", "tg_temp_set", "tg_temp_step", "tg_temp_read", "tg_temp_buffer", "tg_contact_area",
+            "tg_temp_last_error"]
 NOALLOC_MAX_FACES = 65536
 
 
@@ -589,3 +613,107 @@ def mesh_sdf_noalloc(verts, faces, points, phi, grad=None, stream=None):
     _check(_lib.tg_mesh_sdf_noalloc(verts.data_ptr(), verts.shape[0], faces.data_ptr(), faces.shape[0],
                                     points.data_ptr(), points.shape[0], phi.data_ptr(),
                                     grad.data_ptr() if grad is not None else None, _stream(stream)), None)
+
+
+def _tcheck(status):
+    if status != 0:
+        msg = _lib.tg_temp_last_error()
+        raise TGError(status, msg.decode() if msg else "")
+
+
+class TempGrid:
+    """TemperatureGrid sensors (tg_temp): G grids of nx x ny x nz cells on the device.
+
+    voxel: [G][3] voxel sizes (m); material: [G][7] k, rho, c_p, emissivity, h,
+    tau, base temperature.  Fields are [G][nx][ny][nz] float32."""
+
+    def __init__(self, dims, voxel, material, k2_floor: float = 1e-12):
+        voxel = np.ascontiguousarray(voxel, np.float32).reshape(-1, 3)
+        material = np.ascontiguousarray(material, np.float32).reshape(-1, 7)
+        assert len(voxel) == len(material)
+        self.G, self.dims = len(voxel), tuple(int(n) for n in dims)
+        d = TempDesc()
+        d.n_grids = self.G
+        d.nx, d.ny, d.nz = self.dims
+        d.voxel, d.material, d.k2_floor = _ptr(voxel), _ptr(material), float(k2_floor)
+        h = _vp()
+        _tcheck(_lib.tg_temp_create(C.byref(d), C.byref(h)))
+        self.h = h.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.tg_temp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def cells(self):
+        return self.dims[0] * self.dims[1] * self.dims[2]
+
+    def reset(self, grid_mask=None, stream=None):
+        m = None if grid_mask is None else np.ascontiguousarray(grid_mask, np.uint8)
+        _tcheck(_lib.tg_temp_reset(self.h, _ptr(m) if m is not None else None, _stream(stream)))
+
+    def set(self, field, measured=None, stream=None):
+        f = np.ascontiguousarray(field, np.float32)
+        m = None if measured is None else np.ascontiguousarray(measured, np.float32)
+        assert f.size == self.G * self.cells
+        _tcheck(_lib.tg_temp_set(self.h, _ptr(f), _ptr(m) if m is not None else None, _stream(stream)))
+        self.sync(stream)
+
+    def step(self, dt: float, t_amb: float, source=None, contacts=None, stream=None):
+        """source: device tensor [G][cells] (W/m^2) or None.  contacts: None or a
+        dict of offsets [G+1], cell [C], temp [C], k [C], area [C] (numpy arrays
+        or device tensors)."""
+        inp = TempInputs()
+        inp.dt, inp.t_amb = float(dt), float(t_amb)
+        inp.source = source.data_ptr() if source is not None else None
+        keep = []
+        if contacts is not None and len(contacts["cell"]) > 0:
+            inp.n_contacts = len(contacts["cell"])
+            for key, field, dt_ in (("offsets", "contact_offsets", np.int32), ("cell", "contact_cell", np.int32),
+                                    ("temp", "contact_temp", np.float32), ("k", "contact_k", np.float32),
+                                    ("area", "contact_area", np.float32)):
+                v = contacts[key]
+                if hasattr(v, "data_ptr"):
+                    setattr(inp, field, v.data_ptr())
+                else:
+                    a = np.ascontiguousarray(v, dt_)
+                    keep.append(a)
+                    setattr(inp, field, _ptr(a))
+        _tcheck(_lib.tg_temp_step(self.h, C.byref(inp), _stream(stream)))
+
+    def read(self, measured: bool = False, stream=None):
+        out = np.zeros((self.G,) + self.dims, np.float32)
+        _tcheck(_lib.tg_temp_read(self.h, int(measured), _ptr(out), out.nbytes, _stream(stream)))
+        self.sync(stream)
+        return out
+
+    def buffer(self, measured: bool = False):
+        """Device view of T or T_meas as a torch tensor [G][nx][ny][nz] (no copy)."""
+        import torch
+
+        p = _vp()
+        _tcheck(_lib.tg_temp_buffer(self.h, int(measured), C.byref(p)))
+        return torch.as_tensor(_CudaView(p.value, (self.G,) + self.dims, "<f4"), device="cuda")
+
+    def sync(self, stream=None):
+        import torch
+
+        torch.cuda.synchronize()
+
+
+def contact_area(points, n_points, depth, d_w: float = 1.0, stream=None):
+    """tg_contact_area on device tensors: points [P][M][3], n_points int32 [P], depth [P]; returns area [P]."""
+    import torch
+
+    pts, n, dl = points.contiguous(), n_points.contiguous(), depth.contiguous()
+    area = torch.empty(pts.shape[0], dtype=torch.float32, device=pts.device)
+    _tcheck(_lib.tg_contact_area(pts.data_ptr(), n.data_ptr(), dl.data_ptr(), pts.shape[0], pts.shape[1],
+                                 float(d_w), area.data_ptr(), _stream(stream)))
+    return area

@@ -654,3 +654,51 @@ def config2(seed: int = 20260003, n_envs: int = 20480, n_objects: int = 64, n_gr
     wl = _assemble("config2", rng, objects, env_obj, lattices, params, steps=steps, max_links=20,
                    arc=PAD_ARC, press_frac=(1.0, 1.0), press_depth=(0.5e-3, 2.5e-3))
     return add_pads(wl)
+
+
+# ---------------------------------------------------------------- TemperatureGrid
+TEMP_SILICONE = (0.2, 1100.0, 1500.0, 0.9, 10.0, 0.05, 22.0)   # k, rho, c_p, emissivity, h, tau, base (C)
+TEMP_ALUMINIUM = (200.0, 2700.0, 900.0, 0.1, 10.0, 0.0, 22.0)
+
+
+def temperature_grids(seed: int = 20260011, n_envs: int = 20480, links_per_env: int = 5, dims=(8, 8, 16),
+                      extent=(0.02, 0.02, 0.04), metal_share: float = 0.0) -> dict:
+    """TemperatureGrid sensors, one per fingertip link (n_envs x links_per_env
+    grids of dims cells over a link box of `extent` m, the paper's voxel size
+    extent / dims).  Materials: a silicone-like skin (k 0.2 W/m/K, rho 1100,
+    c_p 1500, emissivity 0.9, h 10, tau 50 ms), each value scaled by
+    U(0.8, 1.2) per grid; a `metal_share` of the grids are aluminium-like
+    (k 200, no lag).  Start at the base temperature 22 C."""
+    rng = np.random.default_rng(seed)
+    G = n_envs * links_per_env
+    voxel = np.tile(np.asarray(extent, np.float32) / np.asarray(dims, np.float32), (G, 1))
+    mat = np.tile(np.asarray(TEMP_SILICONE, np.float32), (G, 1))
+    mat[:, :5] *= rng.uniform(0.8, 1.2, (G, 5)).astype(np.float32)
+    mat[:, 3] = np.minimum(mat[:, 3], 1.0)  # emissivity <= 1
+    metal = rng.random(G) < metal_share
+    mat[metal] = np.asarray(TEMP_ALUMINIUM, np.float32)
+    return dict(G=G, dims=tuple(dims), voxel=voxel, material=mat)
+
+
+def temperature_contacts(rng, G: int, dims, share: float = 0.2, max_per_grid: int = 4, hot_share: float = 0.125,
+                         t_hot: float = 45.0, t_amb: float = 22.0) -> dict:
+    """Per-step contacts of the fingertip grids with the bin's balls: a `share`
+    of the grids touch a ball on 1..max_per_grid cells of one face (the
+    voxels under the contact patch), the ball hot (45 C) with probability
+    `hot_share`, else at ambient; ball conductivity U(0.2, 2) W/m/K; patch
+    areas U(2, 20) mm^2 (the contact manifold's shoelace area).  CSR over grids."""
+    nx, ny, nz = dims
+    touch = rng.random(G) < share
+    counts = np.where(touch, rng.integers(1, max_per_grid + 1, G), 0)
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    C = int(off[-1])
+    g_of = np.repeat(np.arange(G), counts)
+    face = rng.integers(0, 6, G)[g_of]
+    i = rng.integers(0, nx, C); j = rng.integers(0, ny, C); k = rng.integers(0, nz, C)
+    i = np.where(face == 0, 0, np.where(face == 1, nx - 1, i))
+    j = np.where(face == 2, 0, np.where(face == 3, ny - 1, j))
+    k = np.where(face == 4, 0, np.where(face == 5, nz - 1, k))
+    hot = (rng.random(G) < hot_share)[g_of]
+    return dict(offsets=off, cell=((i * ny + j) * nz + k).astype(np.int32),
+                temp=np.where(hot, t_hot, t_amb + rng.uniform(-0.5, 0.5, C)).astype(np.float32),
+                k=rng.uniform(0.2, 2.0, C).astype(np.float32), area=rng.uniform(2e-6, 2e-5, C).astype(np.float32))

@@ -148,5 +148,6 @@ def test_contact_area_of_planar_polygons():
     th = np.linspace(0, 2 * np.pi, 7)[:-1]
     hexa = np.stack([np.cos(th), np.sin(th), np.zeros(6)], 1)[[3, 1, 5, 0, 2, 4]]
     assert np.isclose(TO.contact_area(hexa @ R.T, depth=0.0), 1.5 * np.sqrt(3), rtol=1e-12)
-    assert np.isclose(TO.contact_area(sq[:2], depth=1e-3), np.pi * 1e-3)
-    assert np.isclose(TO.contact_area(sq * 1e-3, depth=1e-3, d_w=1.0), np.pi * 1e-3)  # floored at pi d_w delta
+    assert np.isclose(TO.contact_area(sq[:2], depth=1e-3), np.pi * 1e-6)  # a disk of radius delta
+    assert np.isclose(TO.contact_area(sq * 1e-3, depth=1e-3, d_w=1.0), np.pi * 1e-6)  # 2e-6 floored at pi (d_w delta)^2
+    assert np.isclose(TO.contact_area(sq * 1e-3, depth=1e-3, d_w=0.5), 2e-6)  # above the floor
