@@ -53,20 +53,22 @@ struct TempArgs {
     float* Tm;                // [G][cells]
 };
 
-// dst(p, m, q) = sum_j W(m, j) src(p, j, q), with Wt[j][m] = W(m, j) (n x n),
-// over a [P][n][Q] view with element strides (sp, sj, sq); P, n, Q powers of
-// two (lP, ln, lQ their logs), n >= 4
-__device__ __forceinline__ void temp_contract(const float* __restrict__ src, float* __restrict__ dst,
-                                              const float* __restrict__ Wt, int lP, int ln, int lQ, int sp, int sj,
-                                              int sq) {
-    const int n = 1 << ln, nb = n >> 2, work = 1 << (lP + ln - 2 + lQ);
+// dst(p, m, q) = sum_j W(m, j) src(p, j, q), with Wt[j][m] = W(m, j) (N x N),
+// over a [P][N][Q] view with element strides (sp, sj, sq); P and Q powers of
+// two (lP, lQ their logs); the contraction unrolled over its length N
+template <int N>
+__device__ __forceinline__ void temp_contract_n(const float* __restrict__ src, float* __restrict__ dst,
+                                                const float* __restrict__ Wt, int lP, int lQ, int sp, int sj, int sq) {
+    constexpr int nb = N / 4, lnb = N == 4 ? 0 : N == 8 ? 1 : N == 16 ? 2 : 3;
+    const int work = 1 << (lP + lnb + lQ);
     for (int t = threadIdx.x; t < work; t += kTempThreads) {
         // lanes run over q, then p
         const int q = t & ((1 << lQ) - 1), r = t >> lQ, p = r & ((1 << lP) - 1), mb = r >> lP;
         const float* s = src + p * sp + q * sq;
         const float4* w = reinterpret_cast<const float4*>(Wt) + mb;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int j = 0; j < n; ++j) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
             const float v = s[j * sj];
             const float4 c = w[j * nb];
             acc.x = fmaf(c.x, v, acc.x);
@@ -79,6 +81,17 @@ __device__ __forceinline__ void temp_contract(const float* __restrict__ src, flo
         d[sj] = acc.y;
         d[2 * sj] = acc.z;
         d[3 * sj] = acc.w;
+    }
+}
+
+__device__ __forceinline__ void temp_contract(const float* __restrict__ src, float* __restrict__ dst,
+                                              const float* __restrict__ Wt, int lP, int ln, int lQ, int sp, int sj,
+                                              int sq) {
+    switch (ln) {
+    case 2: temp_contract_n<4>(src, dst, Wt, lP, lQ, sp, sj, sq); break;
+    case 3: temp_contract_n<8>(src, dst, Wt, lP, lQ, sp, sj, sq); break;
+    case 4: temp_contract_n<16>(src, dst, Wt, lP, lQ, sp, sj, sq); break;
+    default: temp_contract_n<32>(src, dst, Wt, lP, lQ, sp, sj, sq); break;
     }
 }
 
