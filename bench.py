@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--no-shear", action="store_true", help="skip the elastomer shear-anchor line")
     ap.add_argument("--shear-points", type=int, default=1000, help="tracked points per object for the shear anchors")
     ap.add_argument("--no-temperature", action="store_true", help="skip the TemperatureGrid line")
+    ap.add_argument("--clocks-csv", default=None,
+                    help="where to keep the nvidia-smi clock samples of the timed region ({rank} is replaced; "
+                         "default: a temporary file)")
     ap.add_argument("--neural-objects", type=int, default=64, help="objects given a learned SDF (0: skip the line)")
     ap.add_argument("--neural-points", type=int, default=2_000_000, help="labelled training points per object")
     ap.add_argument("--neural-steps", type=int, default=3000, help="Adam steps per object")
@@ -500,8 +503,8 @@ def run_tg(args):
         pg.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else f"/tmp/tg_clocks_{os.getpid()}.csv")
+    clk = ClockSampler(args.clocks_csv.replace("{rank}", str(rank)) if args.clocks_csv
+                       else f"/tmp/tg_clocks_{os.getpid()}_rank{rank}.csv")
     with clk:
         ev0.record(stream)
         scene.graph_launch(args.steps)

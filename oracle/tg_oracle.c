@@ -16,7 +16,7 @@
  *   closest point on a triangle by Voronoi regions (Ericson, RTCD 5.1.5),
  *   generalised winding number (Jacobson et al. 2013) with the
  *   Van Oosterom-Strackee (1983) solid angle.
- * The readings where the paper is silent are listed in the design doc.
+ * Where the paper is silent, each function states the reading it takes.
  */
 #include "tg_oracle.h"
 
