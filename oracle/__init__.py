@@ -185,6 +185,9 @@ def lib():
             L.or_shear_step.argtypes = [C.POINTER(ORScene), C.POINTER(ORPads), C.POINTER(ORShear),
                                         C.POINTER(ORInputs), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_void_p, C.c_int32]
+            L.or_raycast_depth.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_void_p,
+                                           C.c_double, C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+            L.or_raycast_depth.restype = C.c_double
             _lib = L
     return _lib
 
@@ -669,3 +672,25 @@ class OracleScene:
         ft = np.zeros((6, T))
         lib().or_pc_prox(C.byref(self.S), C.byref(Pc), C.byref(I), _p(ft), int(threads))
         return ft
+
+
+def raycast_depth(verts, faces, scale: float, q, u, R):
+    """Raycast depth backend at probes q [n][3] (mesh frame) with sensing
+    directions u [n][3] and radii R [n]: (depth [n], normal [n][3], face [n],
+    ray_pen [n]) -- see or_raycast_depth."""
+    V = np.ascontiguousarray(verts, np.float32)
+    F = np.ascontiguousarray(faces, np.int32)
+    q = np.ascontiguousarray(q, np.float64).reshape(-1, 3)
+    u = np.ascontiguousarray(u, np.float64).reshape(-1, 3)
+    R = np.broadcast_to(np.asarray(R, np.float64), (len(q),))
+    n = len(q)
+    depth, normal = np.zeros(n), np.zeros((n, 3))
+    face, ray = np.zeros(n, np.int32), np.zeros(n)
+    L = lib()
+    for i in range(n):
+        nn = np.zeros(3)
+        f, rp = C.c_int32(), C.c_double()
+        depth[i] = L.or_raycast_depth(_p(V), _p(F), len(F), float(scale), _p(np.ascontiguousarray(q[i])),
+                                      _p(np.ascontiguousarray(u[i])), float(R[i]), _p(nn), C.byref(f), C.byref(rp))
+        normal[i], face[i], ray[i] = nn, f.value, rp.value
+    return depth, normal, face, ray

@@ -308,6 +308,60 @@ static void vert(const float* V, int32_t i, double o[3]) {
     o[0] = (double)V[3 * i]; o[1] = (double)V[3 * i + 1]; o[2] = (double)V[3 * i + 2];
 }
 
+/* ray-triangle intersection (Moller and Trumbore 1997): t >= 0 of the hit of
+   o + t d with triangle abc, or -1 */
+static double ray_triangle(const double o[3], const double d[3], const double a[3], const double b[3],
+                           const double c[3]) {
+    double e1[3], e2[3], p[3], s[3], qv[3];
+    sub3(b, a, e1); sub3(c, a, e2);
+    cross3(d, e2, p);
+    double det = dot3(e1, p);
+    if (fabs(det) < 1e-300) return -1.0;
+    double inv = 1.0 / det;
+    sub3(o, a, s);
+    double u = dot3(s, p) * inv;
+    if (u < 0.0 || u > 1.0) return -1.0;
+    cross3(s, e1, qv);
+    double v = dot3(d, qv) * inv;
+    if (v < 0.0 || u + v > 1.0) return -1.0;
+    double t = dot3(e2, qv) * inv;
+    return t >= 0.0 ? t : -1.0;
+}
+
+double or_raycast_depth(const float* V, const int32_t* F, int32_t nf, double scale, const double q[3],
+                        const double u[3], double R, double n_out[3], int32_t* face_out, double* ray_pen) {
+    double best = 0.0, rbest = -INFINITY;
+    int32_t bface = -1;
+    for (int32_t f = 0; f < nf; ++f) {
+        double a[3], b[3], c[3], cp[3];
+        int reg;
+        vert(V, F[3 * f], a); vert(V, F[3 * f + 1], b); vert(V, F[3 * f + 2], c);
+        for (int i = 0; i < 3; ++i) { a[i] *= scale; b[i] *= scale; c[i] *= scale; }
+        double pen = R - or_closest_point_triangle(q, a, b, c, cp, &reg);
+        double t = ray_triangle(q, u, a, b, c);
+        if (t >= 0.0) {
+            if (R - t > rbest) rbest = R - t;
+            if (R - t > pen) pen = R - t;
+        }
+        if (pen > best) {
+            best = pen;
+            bface = f;
+        }
+    }
+    n_out[0] = n_out[1] = n_out[2] = 0.0;
+    if (bface >= 0) {
+        double a[3], b[3], c[3], e1[3], e2[3];
+        vert(V, F[3 * bface], a); vert(V, F[3 * bface + 1], b); vert(V, F[3 * bface + 2], c);
+        sub3(b, a, e1); sub3(c, a, e2);
+        cross3(e1, e2, n_out);
+        double l = norm3(n_out);
+        for (int i = 0; i < 3; ++i) n_out[i] /= l;
+    }
+    if (face_out) *face_out = bface;
+    if (ray_pen) *ray_pen = rbest;
+    return best;
+}
+
 /* generalised winding number: sum of signed solid angles / (4 pi) */
 double or_winding_number(const float* V, const int32_t* F, int32_t nf, const double p[3]) {
     double total = 0.0;

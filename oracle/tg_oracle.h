@@ -194,6 +194,19 @@ double or_closest_point_triangle(const double p[3], const double a[3], const dou
                                  const double c[3], double cp[3], int* region);
 double or_winding_number(const float* V, const int32_t* F, int32_t nf, const double p[3]);
 double or_sdf_mesh(const float* V, const int32_t* F, int32_t nf, const double p[3], double g[3]);
+/* raycast depth backend ("Two contact-depth backends"): a probe at q (the
+   mesh's frame; the mesh is scaled by `scale`) with radius R and sensing
+   direction u (unit, from the probe towards the object) tests every
+   triangle twice: a sphere-triangle closest-point test (penetration
+   R - dist) and a ray-triangle test from q along u (penetration R - t for a
+   hit at t >= 0).  The deepest penetration of either test over all
+   triangles wins; n_out is the unit face normal (winding order) of the
+   triangle that gave it (the first in face order on a tie), face_out its
+   index.  Returns the depth (0 with n_out = 0 and face_out = -1 when nothing
+   penetrates); ray_pen, if not NULL, receives the deepest penetration of the
+   ray test alone (-inf when the ray hits nothing). */
+double or_raycast_depth(const float* V, const int32_t* F, int32_t nf, double scale, const double q[3],
+                        const double u[3], double R, double n_out[3], int32_t* face_out, double* ray_pen);
 double or_sdf_grid(const or_object* o, const double q[3], double g[3]);
 double or_sdf_object(const or_object* o, const double q[3], double g[3]);
 int or_schmitt(int prev, double d, double eta_on, double eta_off);
