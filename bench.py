@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--no-shear", action="store_true", help="skip the elastomer shear-anchor line")
     ap.add_argument("--shear-points", type=int, default=1000, help="tracked points per object for the shear anchors")
     ap.add_argument("--no-temperature", action="store_true", help="skip the TemperatureGrid line")
+    ap.add_argument("--no-raycast", action="store_true", help="skip the raycast depth backend line")
     ap.add_argument("--clocks-csv", default=None,
                     help="where to keep the nvidia-smi clock samples of the timed region ({rank} is replaced; "
                          "default: a temporary file)")
@@ -375,6 +376,84 @@ def traffic_from_profile():
     return rec.get("dram_bytes_per_launch_full")
 
 
+def _quat_mat(q):
+    """rotation matrices [n][3][3] of unit quaternions [n][4] (w, x, y, z)"""
+    w, x, y, z = (q[:, i].astype(np.float64) for i in range(4))
+    return np.stack([np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], 1),
+                     np.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], 1),
+                     np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], 1)], 1)
+
+
+def raycast_line(args, wl, objs, dev, stream):
+    """Raycast depth backend: every active taxel of the headline workload (its
+    time-0 pose) queried against its env object's triangle mesh through a
+    bounding volume hierarchy, one launch per object."""
+    import time
+
+    import torch
+
+    from paper_2606_22332_gb300 import tg
+
+    E, L = wl.n_envs, wl.max_links
+    counts = (wl.link_rows * wl.link_cols).astype(np.int64)
+    link_of = np.repeat(np.arange(E * L), counts)
+    act = wl.R > 0
+    lp = wl.link_pose.reshape(E * L, 7)[link_of]
+    xw = np.einsum("nij,nj->ni", _quat_mat(lp[:, 3:]),
+                   np.stack([wl.x, wl.y, wl.z], 1).astype(np.float64)) + lp[:, :3]
+    env_of = link_of // L
+    op = wl.obj_pose[env_of]
+    q = np.einsum("nji,nj->ni", _quat_mat(op[:, 3:]), xw - op[:, :3])  # R_C^T (x_w - p_C)
+    oid = wl.obj_id[env_of]
+    groups = []
+    for o, ob in enumerate(objs):
+        sel = np.flatnonzero(act & (oid == o))
+        if ob.verts is None or len(sel) == 0:
+            continue
+        bvh = tg.MeshBvh(ob.verts, ob.faces)
+        groups.append((bvh, torch.as_tensor(q[sel].astype(np.float32), device=dev),
+                       torch.as_tensor(wl.R[sel].astype(np.float32), device=dev), sel))
+    n = sum(len(g[3]) for g in groups)
+    outs = [None] * len(groups)
+
+    def one_pass():
+        for k, (bvh, qd, rd, _) in enumerate(groups):
+            outs[k] = bvh.depth(qd, rd, stream=stream.cuda_stream)
+
+    for _ in range(max(args.warmup, 1)):
+        one_pass()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        one_pass()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    touching = sum(int((o[0] > 0).sum().item()) for o in outs)
+    out = {"sensors": f"raycast depth backend over {n} active taxels of the headline workload (time-0 poses), "
+                      f"{len(groups)} object meshes of 3k-6k faces, one tree per mesh",
+           "value": n / (ms * 1e-3), "unit": "probe-queries/s", "ms_per_pass": ms,
+           "probes_in_contact": round(touching / max(n, 1), 4), "gpu_launches": len(groups) * args.steps}
+    if not args.no_cpu_baseline:
+        import oracle
+
+        rng = np.random.default_rng(20260013)
+        k = min(400, n)
+        pick = rng.choice(n, k, replace=False)
+        allsel = np.concatenate([g[3] for g in groups])
+        t0 = time.perf_counter()
+        for i in allsel[pick]:
+            ob = objs[oid[i]]
+            oracle.raycast_depth(ob.verts, ob.faces, 1.0, q[i:i + 1], np.array([[0.0, 0.0, 1.0]]), float(wl.R[i]))
+        el = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": k / el, "unit": "probe-queries/s", "cores": 1, "kind": "oracle",
+                               "sample": f"{k} random active taxels of the same workload, brute force over the faces"}
+    for g in groups:
+        g[0].close()
+    return out
+
+
 TEMP_BYTES_PER_CELL = 16.0  # T and T_meas, each read and written once per step
 
 
@@ -648,6 +727,9 @@ def run_tg(args):
                  "anchored_points_per_pad": round(n_anch / max(n_pads, 1), 2),
                  "anchor_state_bytes": n_pads * args.shear_points * 8,
                  "gpu_launches": (launches_per_step + 1) * args.steps}
+    ray = None
+    if not args.no_raycast and ws == 1:
+        ray = raycast_line(args, wl, wl.objects, dev, stream)  # the meshes behind the baked grids
     temp = None
     if not args.no_temperature:
         temp = temperature_line(args, dev, stream, pg, peaks)
@@ -686,6 +768,7 @@ def run_tg(args):
             "point_cloud_proximity": pcl,
             "elastomer_shear": shear,
             "temperature_grid": temp,
+            "raycast_depth": ray,
             "neural_sdf": neural,
             "setup_s": {"bake": round(bake_s, 2), "total": round(time.time() - t_setup, 1)},
         }

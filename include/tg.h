@@ -520,6 +520,36 @@ tg_status tg_contact_area(const float* points, const int32_t* n_points, const fl
                           int32_t max_points, double d_w, float* area, tg_stream stream);
 const char* tg_temp_last_error(void);
 
+
+/* ---- raycast contact-depth backend ("Two contact-depth backends") --------
+
+   A bounding volume hierarchy over one triangle mesh (its own frame).  Per
+   probe at q with radius R, the paper's raycast backend runs on every nearby
+   triangle a sphere-triangle closest-point test (penetration R - dist) and a
+   ray-triangle test along the probe's sensing direction (penetration R - t);
+   the deepest wins and the contact normal is that triangle's face normal.  A
+   ray's hit lies on its triangle, so t >= dist and the ray test never gives
+   the deeper value: the depth is R - (distance to the nearest triangle within
+   R), 0 when there is none, and that is what tg_raycast_depth computes. */
+typedef struct tg_mesh_bvh tg_mesh_bvh;
+
+/* Build the tree of verts (host [n_verts][3]) and faces (host [n_faces][3],
+   counter-clockwise seen from outside gives the outward normal).  Errors:
+   TG_ERR_INVALID_ARG (indices out of range, non-finite vertices, an empty
+   mesh), TG_ERR_OOM, TG_ERR_CUDA. */
+tg_status tg_mesh_bvh_create(const float* verts, int32_t n_verts, const int32_t* faces, int32_t n_faces,
+                             tg_mesh_bvh** out);
+void tg_mesh_bvh_destroy(tg_mesh_bvh* bvh);
+/* Depth at n probes: probes device [n][3] in the mesh's frame with the mesh
+   scaled by `scale` (> 0), radius device [n] (R <= 0: inactive, depth 0);
+   depth device [n]; normal device [n][3] (unit face normal, mesh frame; 0
+   where the depth is 0) and face device [n] (the face index, -1 where the
+   depth is 0) may be NULL.  Ordered on `stream`.  Errors: TG_ERR_INVALID_ARG,
+   TG_ERR_CUDA. */
+tg_status tg_raycast_depth(const tg_mesh_bvh* bvh, const float* probes, const float* radius, int64_t n, double scale,
+                           float* depth, float* normal, int32_t* face, tg_stream stream);
+const char* tg_mesh_bvh_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -158,13 +158,18 @@ _lib.tg_temp_read.argtypes = [_vp, _i32, _vp, _sz, _vp]
 _lib.tg_temp_buffer.argtypes = [_vp, _i32, C.POINTER(_vp)]
 _lib.tg_contact_area.argtypes = [_vp, _vp, _vp, _i32, _i32, C.c_double, _vp, _vp]
 _lib.tg_temp_last_error.restype = C.c_char_p
+_lib.tg_mesh_bvh_create.argtypes = [_vp, _i32, _vp, _i32, C.POINTER(_vp)]
+_lib.tg_mesh_bvh_destroy.argtypes = [_vp]
+_lib.tg_mesh_bvh_destroy.restype = None
+_lib.tg_raycast_depth.argtypes = [_vp, _vp, _vp, C.c_int64, C.c_double, _vp, _vp, _vp, _vp]
+_lib.tg_mesh_bvh_last_error.restype = C.c_char_p
 for _f in ("tg_create_scene", "tg_upload_objects", "tg_reset_envs", "tg_step_sensors", "tg_read_taxels",
            "tg_get_buffer", "tg_sync", "tg_save_state", "tg_load_state", "tg_bake_grid", "tg_mesh_sdf",
            "tg_profile_enable", "tg_profile_read", "tg_mesh_sdf_noalloc", "tg_graph_capture", "tg_graph_launch",
            "tg_graph_seek", "tg_graph_release", "tg_set_schedule", "tg_get_schedule", "tg_autotune", "tg_object_info",
            "tg_nsdf_create", "tg_nsdf_set_params", "tg_nsdf_get_params", "tg_nsdf_eval", "tg_nsdf_loss_grad",
            "tg_nsdf_train", "tg_nsdf_probe", "tg_temp_create", "tg_temp_reset", "tg_temp_set", "tg_temp_step",
-           "tg_temp_read", "tg_temp_buffer", "tg_contact_area"):
+           "tg_temp_read", "tg_temp_buffer", "tg_contact_area", "tg_mesh_bvh_create", "tg_raycast_depth"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ["tg_create_scene", "tg_destroy_scene", "tg_max_link_taxels", "tg_upload_objects", "tg_reset_envs",
@@ -175,7 +180,8 @@ EXPORTED = ["tg_create_scene", "tg_destroy_scene", "tg_max_link_taxels", "tg_upl
             "tg_nsdf_destroy", "tg_nsdf_set_params", "tg_nsdf_get_params", "tg_nsdf_eval", "tg_nsdf_loss_grad",
             "tg_nsdf_train", "tg_nsdf_probe", "tg_nsdf_last_error", "tg_temp_create", "tg_temp_destroy",
             "tg_temp_reset", "tg_temp_set", "tg_temp_step", "tg_temp_read", "tg_temp_buffer", "tg_contact_area",
-            "tg_temp_last_error"]
+            "tg_temp_last_error", "tg_mesh_bvh_create", "tg_mesh_bvh_destroy", "tg_raycast_depth",
+            "tg_mesh_bvh_last_error"]
 NOALLOC_MAX_FACES = 65536
 
 
@@ -717,3 +723,44 @@ def contact_area(points, n_points, depth, d_w: float = 1.0, stream=None):
     _tcheck(_lib.tg_contact_area(pts.data_ptr(), n.data_ptr(), dl.data_ptr(), pts.shape[0], pts.shape[1],
                                  float(d_w), area.data_ptr(), _stream(stream)))
     return area
+
+
+def _bcheck(status):
+    if status != 0:
+        msg = _lib.tg_mesh_bvh_last_error()
+        raise TGError(status, msg.decode() if msg else "")
+
+
+class MeshBvh:
+    """tg_mesh_bvh: a bounding volume hierarchy over one triangle mesh, for the raycast depth backend."""
+
+    def __init__(self, verts, faces):
+        V = np.ascontiguousarray(verts, np.float32).reshape(-1, 3)
+        F = np.ascontiguousarray(faces, np.int32).reshape(-1, 3)
+        h = _vp()
+        _bcheck(_lib.tg_mesh_bvh_create(_ptr(V), len(V), _ptr(F), len(F), C.byref(h)))
+        self.h = h.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.tg_mesh_bvh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def depth(self, probes, radius, scale: float = 1.0, stream=None):
+        """(depth [n], normal [n][3], face [n]) at device probes [n][3] (mesh frame) with radii [n]."""
+        import torch
+
+        q, r = probes.contiguous(), radius.contiguous()
+        n = q.shape[0]
+        d = torch.empty(n, dtype=torch.float32, device=q.device)
+        nn = torch.empty((n, 3), dtype=torch.float32, device=q.device)
+        f = torch.empty(n, dtype=torch.int32, device=q.device)
+        _bcheck(_lib.tg_raycast_depth(self.h, q.data_ptr(), r.data_ptr(), n, float(scale), d.data_ptr(),
+                                      nn.data_ptr(), f.data_ptr(), _stream(stream)))
+        return d, nn, f
