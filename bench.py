@@ -107,6 +107,9 @@ def workload_config(args, wl):
         "grid": "96^3 fp16",
         "objects": len(wl.objects),
         "l2": "no flush: every step streams ~4.8 GB of taxel state/outputs, far above the 129 MB L2",
+        "placement": "per env a target share f ~ U(0.1, 0.3) of active taxels penetrating at the time-0 poses, "
+                     "all links pressed by one depth of at most 2 mm (no probe deeper than 3 mm); the timed "
+                     "replays run steps 0..K-1 of a fresh episode (warm-up replays first, then reset and rewind)",
     }
 
 
@@ -162,8 +165,8 @@ def oracle_baseline(args, wl):
     o = OracleSample(args, wl)
     secs = sum(o.step_seconds() for _ in range(args.oracle_steps))
     q = o.sub.n_active * args.oracle_steps
-    return {"value": q / secs, "unit": UNIT, "cores": o.threads, "kind": "oracle",
-            "sample": o.describe(args.oracle_steps, secs)}
+    return {"value": q / secs, "unit": UNIT, "cores": o.threads, "per_core": q / secs / o.threads,
+            "kind": "oracle", "sample": o.describe(args.oracle_steps, secs)}
 
 
 def run_reference(args):
@@ -242,6 +245,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows), "power_w_max": pmax}
 
 
+def warm_then_rewind(sc, args, dt, stream=None):
+    """W untimed graph replays (steps 0..W-1), then every env reset to episode
+    0 and the graph rewound to step 0: the timed replays run steps 0..K-1
+    from the time-0 placement, as a fresh episode does."""
+    sc.graph_launch(args.warmup)
+    sc.reset(0)
+    sc.graph_seek(0, 0.0, dt)
+
+
 def neural_line(args, wl, objs, d_in, dev, sched, stream, step_inputs, t_plain_ms):
     """Learned SDFs for the first objects of the workload: trained on the GPU
     (labels from the exact-mesh query), probed against it, then the same
@@ -283,7 +295,7 @@ def neural_line(args, wl, objs, d_in, dev, sched, stream, step_inputs, t_plain_m
     sc.set_schedule(**sched)
     sc.profile(True)
     sc.graph_capture(step_inputs(0, d_in), pose_dt_per_step=dt)
-    sc.graph_launch(args.warmup)
+    warm_then_rewind(sc, args, dt)
     torch.cuda.synchronize()
     sc.profile_read()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -569,14 +581,19 @@ def run_tg(args):
 
     # the step as a CUDA graph: replay r runs step r with pose_dt = r dt
     scene.profile(True)
+    scene.reset(0)
     scene.graph_capture(step_inputs(0, d_in), pose_dt_per_step=dt)
-    scene.graph_launch(args.warmup)
+    scene.graph_launch(1)                       # step 0 from a fresh episode: the shares at the placement
+    torch.cuda.synchronize()
+    act_n = max(wl.n_active, 1)
+    pen_share0 = float((scene.buffer(tg.CH_DEPTH) > 0).sum().item()) / act_n
+    contact_share0 = float((scene.read(tg.CH_STATE_FLAGS) & 1).sum()) / act_n
+    scene.graph_launch(max(args.warmup - 1, 0))
+    scene.reset(0)
+    scene.graph_seek(0, 0.0, dt)
     torch.cuda.synchronize()
     scene.sync()
     scene.profile_read()
-    contact_share = float((scene.read(tg.CH_STATE_FLAGS) & 1).sum()) / max(wl.n_active, 1)
-    depth = scene.buffer(tg.CH_DEPTH)
-    pen_share = float((depth > 0).sum().item()) / max(wl.n_active, 1)
 
     if pg:
         pg.barrier()
@@ -594,6 +611,8 @@ def run_tg(args):
     ms = ev0.elapsed_time(ev1)
     pose_ms, step_ms, nsteps = scene.profile_read()
     scene.sync()
+    pen_share_last = float((scene.buffer(tg.CH_DEPTH) > 0).sum().item()) / act_n
+    contact_share_last = float((scene.read(tg.CH_STATE_FLAGS) & 1).sum()) / act_n
     scene.graph_release()
     scene.profile(False)
     t_max = max_over_ranks(ms, dev)
@@ -601,7 +620,7 @@ def run_tg(args):
     value = n_q * args.steps / (t_max / 1e3)
 
     # e2e: host inputs through the C-ABI (H2D inside), per-link results read back to host
-    e2e = None
+    e2e = e2e_taxel = None
     if not args.no_e2e:
         pinned = {k: torch.as_tensor(getattr(wl, k)).pin_memory() for k in d_in}
         out_w = torch.empty((E * wl.max_links, tg.LINK_REC), dtype=torch.float32).pin_memory()
@@ -609,15 +628,16 @@ def run_tg(args):
         h2d = sum(v.numel() * v.element_size() for v in pinned.values())
         d2h = out_w.numel() * 4 + out_c.numel() * 4
         k2 = args.steps
-        base = args.warmup
-        scene.step(step_inputs(base - 1, pinned))
-        scene.read(tg.CH_LINK_WRENCH, out=out_w)
+        for t in range(args.warmup):
+            scene.step(step_inputs(t, pinned))
+            scene.read(tg.CH_LINK_WRENCH, out=out_w)
+        scene.reset(0)
         torch.cuda.synchronize()
         if pg:
             pg.barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for t in range(base, base + k2):  # the same step indices (same poses) as the device-timed region
+        for t in range(k2):  # the same step indices (same poses) as the device-timed region
             scene.step(step_inputs(t, pinned))
             scene.read(tg.CH_LINK_WRENCH, out=out_w)
             scene.read(tg.CH_LINK_COUNT, out=out_c)
@@ -629,6 +649,29 @@ def run_tg(args):
                "note": "time-0 poses/velocities copied from pinned host memory every step (the C-ABI stages them); "
                        "per-link wrench sums and contact counts (agg_force / agg_bool observations) read back to "
                        "pinned host memory every step; same step indices as the device-timed region"}
+        # the same, reading every taxel's noisy readout back instead (contact bit, depth, force/torque)
+        T_all = wl.n_taxels
+        o_c = torch.empty(T_all, dtype=torch.uint8).pin_memory()
+        o_d = torch.empty(T_all, dtype=torch.float32).pin_memory()
+        o_f = torch.empty((6, T_all), dtype=torch.float32).pin_memory()
+        d2h_t = o_c.numel() + o_d.numel() * 4 + o_f.numel() * 4
+        scene.reset(0)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        e0.record(stream)
+        for t in range(k2):
+            scene.step(step_inputs(t, pinned))
+            scene.read(tg.CH_CONTACT, noisy=True, out=o_c)
+            scene.read(tg.CH_DEPTH, noisy=True, out=o_d)
+            scene.read(tg.CH_FORCE_TORQUE, noisy=True, out=o_f)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems2 = max_over_ranks(e0.elapsed_time(e1), dev)
+        e2e_taxel = {"value": n_q * k2 / (ems2 / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                     "d2h_bytes_per_step": int(d2h_t),
+                     "note": "as e2e, but every taxel's noisy contact bit, depth and force/torque (29 B per "
+                             "taxel) read back to pinned host memory every step instead of the per-link sums"}
 
     # second line: the same workload with proximity rays and marker pads on
     full = None
@@ -640,7 +683,7 @@ def run_tg(args):
         sc2.upload_objects(objs)
         sc2.set_schedule(**sched)
         sc2.graph_capture(step_inputs(0, d_in), pose_dt_per_step=dt)
-        sc2.graph_launch(args.warmup)
+        warm_then_rewind(sc2, args, dt)
         torch.cuda.synchronize()
         if pg:
             pg.barrier()
@@ -671,7 +714,7 @@ def run_tg(args):
         sc3.upload_objects(objs_c)
         sc3.set_schedule(**sched)
         sc3.graph_capture(step_inputs(0, d_in), pose_dt_per_step=dt)
-        sc3.graph_launch(args.warmup)
+        warm_then_rewind(sc3, args, dt)
         torch.cuda.synchronize()
         if pg:
             pg.barrier()
@@ -705,7 +748,7 @@ def run_tg(args):
         sc4.upload_objects(objs_s)
         sc4.set_schedule(**sched)
         sc4.graph_capture(step_inputs(0, d_in), pose_dt_per_step=dt)
-        sc4.graph_launch(args.warmup)
+        warm_then_rewind(sc4, args, dt)
         torch.cuda.synchronize()
         if pg:
             pg.barrier()
@@ -761,8 +804,12 @@ def run_tg(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic", "config": workload_config(args, wl), "clocks": clocks,
-            "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "roofline": roofline, "cpu_baseline": cpu,
-            "contact_share": round(contact_share, 4), "penetrating_share": round(pen_share, 4),
+            "e2e": e2e, "e2e_per_taxel": e2e_taxel, "gpu_launches": launches_per_step * args.steps,
+            "roofline": roofline, "cpu_baseline": cpu,
+            "penetrating_share": {"step_0": round(pen_share0, 4), f"step_{args.steps - 1}": round(pen_share_last, 4),
+                                  "placement": wl.meta.get("placement")},
+            "contact_share": {"step_0": round(contact_share0, 4),
+                              f"step_{args.steps - 1}": round(contact_share_last, 4)},
             "schedule": {"chosen": sched, "autotune": tune["candidates"], "replay": "CUDA graph per step"},
             "full_sensor_set": full,
             "point_cloud_proximity": pcl,

@@ -424,21 +424,31 @@ tg_status tg_mesh_sdf(const float* verts, int32_t n_verts, const int32_t* faces,
 
 /* tg_mesh_sdf without any device allocation.  The paper has no counterpart:
    this entry point exists for callers that cannot call cudaMalloc, such as
-   code being captured into a CUDA graph that must not allocate, or a host
-   application whose allocator owns all device memory.  tg_mesh_sdf copies the
-   mesh into a triangle list it allocates for each call; this variant builds
-   that list on the GPU in a device array inside the library, sized for
-   TG_NOALLOC_MAX_FACES faces (3 MiB, held by every GPU that loads the library
-   until the process exits).
+   an application whose own allocator owns all of the GPU's memory (a
+   framework with a fixed memory budget that forbids allocations from outside
+   it), or code on a path where cudaMalloc's implicit device-wide
+   synchronisation is not acceptable.  tg_mesh_sdf copies the mesh into a
+   triangle list it allocates for each call; this variant builds that list on
+   the GPU in a device array inside the library, sized for
+   TG_NOALLOC_MAX_FACES faces (3 MiB, held by every GPU that loads the
+   library until the process exits).
    verts [n_verts][3], faces [n_faces][3], points [n][3], phi [n] and grad
-   [n][3] (or NULL) must all be device memory; the results are those of
-   tg_mesh_sdf.  Meshes over TG_NOALLOC_MAX_FACES faces, host pointers or bad
-   sizes return TG_ERR_INVALID_ARG and run nothing.  A face index outside
-   [0, n_verts) gives NaN distances instead of an out-of-bounds read.
-   The first call on each device looks up the array's device address once;
-   make that first call before any stream capture.  Every call shares the
-   array: calls whose GPU work overlaps (different streams or host threads)
-   race on it, so the caller must order them.  Asynchronous on `stream`. */
+   [n][3] (or NULL) must all be device memory.  phi is bit-identical to
+   tg_mesh_sdf's; grad too, except where a point's gradient is the normal of
+   the face it is nearest (a face interior, or a point on the surface): this
+   variant normalises the face normal in FP32 on the GPU, tg_mesh_sdf in FP64
+   on the host, so those may differ in the last bits.  Meshes over
+   TG_NOALLOC_MAX_FACES faces, host pointers or bad sizes return
+   TG_ERR_INVALID_ARG and run nothing.  The mesh is not read on the host, so
+   an invalid face cannot be rejected there the way tg_mesh_sdf rejects it:
+   a face index outside [0, n_verts) (never read out of bounds) or a face
+   whose FP32 cross product is zero (zero area) makes every phi and grad
+   value of the call NaN.  The first call on each device looks up the
+   array's device address once; make that first call before any stream
+   capture.  Every call shares the array and clears what must start at zero
+   (the invalid-face counter): calls whose GPU work overlaps (different
+   streams or host threads) race on it, so the caller must order them.
+   Asynchronous on `stream`. */
 tg_status tg_mesh_sdf_noalloc(const float* verts, int32_t n_verts, const int32_t* faces, int32_t n_faces,
                               const float* points, int64_t n, float* phi, float* grad, tg_stream stream);
 

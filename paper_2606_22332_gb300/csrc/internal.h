@@ -200,6 +200,12 @@ struct PoseArgs {
     const StepCtl* ctl;               // non-null: step and pose_dt from here
 };
 
+// Raise a kernel's dynamic shared-memory limit on the current device to at
+// least `bytes`.  The attribute is per device; each (kernel, device) keeps a
+// high-water mark that only grows, so launches sized earlier keep working.
+// Thread-safe.
+cudaError_t raise_smem_limit(const void* func, size_t bytes);
+
 cudaError_t launch_pose(const PoseArgs& a, cudaStream_t s);
 cudaError_t launch_step(const StepArgs& a, int n_items, cudaStream_t s);
 cudaError_t configure_step_kernels();

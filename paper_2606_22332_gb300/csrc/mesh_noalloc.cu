@@ -1,17 +1,21 @@
 // mesh_noalloc.cu -- exact mesh signed distance at points without any device
-// allocation, for callers that cannot call cudaMalloc: code running inside
-// a CUDA-graph capture that must not allocate, inside another framework's
-// memory budget that forbids outside allocations, or on a path where an
-// allocation's implicit synchronisation is not acceptable.
+// allocation, for callers that cannot call cudaMalloc: an application whose
+// own allocator owns all of the GPU's memory (a framework with a fixed
+// memory budget that forbids allocations from outside it), or code on a path
+// where cudaMalloc's implicit device-wide synchronisation is not acceptable
+// (a control loop with a latency budget).
 //
 // tg_mesh_sdf copies the mesh into a triangle list it allocates per call.
 // This variant builds that triangle list on the GPU in a file-scope
 // device array instead, sized for kNoAllocMaxFaces faces (12 floats per face:
-// three vertices and the unit normal; 3 MiB).  Every GPU that loads this
+// three vertices and the unit normal; 3 MiB) plus one 256-byte block whose
+// first word counts the call's invalid faces.  Every GPU that loads this
 // library holds the array until the process exits.  All calls share it:
-// each call overwrites the faces it uses and reads nothing left by an earlier
-// call, but calls whose work overlaps on the GPU (different streams, or
-// different host threads) race on it and must be serialised by the caller.
+// each call clears the counter and overwrites the faces it uses, and reads
+// nothing left by an earlier call, but calls whose work overlaps on the GPU
+// (different streams, or different host threads) race on it and must be
+// serialised by the caller.
+#include <algorithm>
 #include <mutex>
 
 #include "mesh_kernel.cuh"
@@ -21,7 +25,8 @@ namespace tg {
 constexpr int kNoAllocMaxFaces = TG_NOALLOC_MAX_FACES;
 constexpr int kNoAllocMaxDevices = 64;
 
-static __device__ __align__(256) float g_noalloc_tri[(size_t)kNoAllocMaxFaces * 12];
+constexpr size_t kNoAllocFlag = (size_t)kNoAllocMaxFaces * 12;   // float index of the invalid-face counter
+static __device__ __align__(256) float g_noalloc_tri[kNoAllocFlag + 64];
 
 // device address of g_noalloc_tri per device, resolved once per device
 static float* g_noalloc_ptr[kNoAllocMaxDevices];
@@ -44,10 +49,11 @@ static cudaError_t noalloc_scratch(float** out) {
 }
 
 // triangle list (vertices, then unit normals after kNoAllocMaxFaces * 9
-// floats) from the indexed mesh; an out-of-range index yields a NaN triangle
-// instead of an out-of-bounds read.
+// floats) from the indexed mesh.  A face with an index outside [0, nv) (read
+// as a zero vertex, never out of bounds) or with a zero FP32 cross product
+// (zero area) is counted in *bad; the query's results are then set to NaN.
 __global__ void gather_triangles_kernel(const float* verts, int nv, const int32_t* faces, int nf, float* tri,
-                                        float* tri_n) {
+                                        float* tri_n, unsigned int* bad) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nf) return;
     float p[3][3];
@@ -59,17 +65,28 @@ __global__ void gather_triangles_kernel(const float* verts, int nv, const int32_
 #pragma unroll
         for (int a = 0; a < 3; ++a) p[k][a] = (vi >= 0 && vi < nv) ? verts[3 * vi + a] : 0.0f;
     }
-    const float nan = __int_as_float(0x7fc00000);
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) tri[(size_t)f * 9 + 3 * k + a] = ok ? p[k][a] : nan;
+        for (int a = 0; a < 3; ++a) tri[(size_t)f * 9 + 3 * k + a] = p[k][a];
     const float3 u = f3(p[1][0] - p[0][0], p[1][1] - p[0][1], p[1][2] - p[0][2]);
     const float3 w = f3(p[2][0] - p[0][0], p[2][1] - p[0][1], p[2][2] - p[0][2]);
-    const float3 nrm = normalize_or(cross(u, w), f3(0.f, 0.f, 1.f));
+    const float3 cr = cross(u, w);
+    if (!ok || !(dot(cr, cr) > 0.0f)) atomicAdd(bad, 1u);
+    const float3 nrm = normalize_or(cr, f3(0.f, 0.f, 1.f));
     tri_n[(size_t)f * 3] = nrm.x;
     tri_n[(size_t)f * 3 + 1] = nrm.y;
     tri_n[(size_t)f * 3 + 2] = nrm.z;
+}
+
+// every distance (and gradient) NaN when the mesh had an invalid face
+__global__ void poison_kernel(const unsigned int* bad, int64_t n, float* phi, float* grad) {
+    if (*bad == 0u) return;
+    const float nan = __int_as_float(0x7fc00000);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        phi[i] = nan;
+        if (grad) grad[3 * i] = grad[3 * i + 1] = grad[3 * i + 2] = nan;
+    }
 }
 
 static bool on_device(const void* p) {
@@ -95,9 +112,16 @@ extern "C" tg_status tg_mesh_sdf_noalloc(const float* verts, int32_t n_verts, co
     if (noalloc_scratch(&scratch) != cudaSuccess) return TG_ERR_CUDA;
     float* tri = scratch;
     float* tri_n = scratch + (size_t)kNoAllocMaxFaces * 9;
+    unsigned int* bad = reinterpret_cast<unsigned int*>(scratch + kNoAllocFlag);
     cudaStream_t st = (cudaStream_t)stream;
-    gather_triangles_kernel<<<(n_faces + 127) / 128, 128, 0, st>>>(verts, n_verts, faces, n_faces, tri, tri_n);
+    if (cudaMemsetAsync(bad, 0, sizeof(unsigned int), st) != cudaSuccess) return TG_ERR_CUDA;
+    gather_triangles_kernel<<<(n_faces + 127) / 128, 128, 0, st>>>(verts, n_verts, faces, n_faces, tri, tri_n, bad);
     if (cudaGetLastError() != cudaSuccess) return TG_ERR_CUDA;
     if (launch_mesh_sdf_points(tri, tri_n, n_faces, points, n, phi, grad, st) != cudaSuccess) return TG_ERR_CUDA;
+    if (n > 0) {
+        const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+        poison_kernel<<<(unsigned)blocks, 256, 0, st>>>(bad, n, phi, grad);
+        if (cudaGetLastError() != cudaSuccess) return TG_ERR_CUDA;
+    }
     return TG_OK;
 }

@@ -782,18 +782,11 @@ __global__ void nsdf_sync_masters_kernel(float* master, float* m, float* v, cons
 constexpr int64_t kParamCount = kNsdfWeights + 2 * kNsdfTableEntries;
 constexpr int64_t kUpdateCount = kNsdfWeights + kNsdfTableEntries;  // Adam threads
 
-bool g_configured = false;
-
+// shared-memory limits of the three kernels on the current device (per device, once)
 cudaError_t configure() {
-    if (g_configured) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(nsdf_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(SmemInfer));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(nsdf_step_query_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(SmemInfer));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(nsdf_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SmemTrain));
-    if (e == cudaSuccess) g_configured = true;
+    cudaError_t e = raise_smem_limit((const void*)nsdf_eval_kernel, sizeof(SmemInfer));
+    if (e == cudaSuccess) e = raise_smem_limit((const void*)nsdf_step_query_kernel, sizeof(SmemInfer));
+    if (e == cudaSuccess) e = raise_smem_limit((const void*)nsdf_train_kernel, sizeof(SmemTrain));
     return e;
 }
 

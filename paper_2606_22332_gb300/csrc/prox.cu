@@ -279,12 +279,8 @@ __global__ void __launch_bounds__(kProxThreads, 4) prox_kernel(const StepArgs a)
 cudaError_t launch_prox(const StepArgs& a, int n_items, cudaStream_t s) {
     if (n_items == 0 || a.P.prox_rays < 1) return cudaSuccess;
     const size_t smem = sizeof(float) * (size_t)kItemCap * (size_t)a.P.prox_rays;  // <= 64 KB (16 rays)
-    static size_t configured = 0;
-    if (smem > configured) {
-        const cudaError_t err = cudaFuncSetAttribute(prox_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-        configured = smem;
-    }
+    const cudaError_t err = raise_smem_limit((const void*)prox_kernel, smem);
+    if (err != cudaSuccess) return err;
     prox_kernel<<<n_items, kProxThreads, smem, s>>>(a);
     return cudaGetLastError();
 }

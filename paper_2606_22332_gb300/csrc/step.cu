@@ -428,12 +428,9 @@ cudaError_t launch_order_items(const Item* items, int n_items, const int32_t* ob
     const size_t with_cache = base + (size_t)n_items * sizeof(uint16_t);
     const int cache = with_cache <= kCap && n_objects <= 65535 ? 1 : 0;
     const size_t smem = cache ? with_cache : base;
-    static size_t configured = 0;
-    if (smem > 48 * 1024 && smem > configured) {
-        const cudaError_t e = cudaFuncSetAttribute(order_items_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)kCap);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = raise_smem_limit((const void*)order_items_kernel, kCap);
         if (e != cudaSuccess) return e;
-        configured = kCap;
     }
     order_items_kernel<<<1, 1024, smem, s>>>(items, n_items, obj_id, n_objects, cache, sorted);
     return cudaGetLastError();

@@ -409,16 +409,8 @@ tg_status tg_temp_create(const tg_temp_desc* d, tg_temp** out) {
     if ((e = cudaMemcpy(t->dct, dct.data(), sizeof(float) * dct.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
         return undo(e, "upload");
     t->smem = sizeof(float) * (2 * (size_t)d->nx * d->ny * (d->nz + 1) + dct.size());
-    {
-        // the kernel's limit only grows, so that grids created earlier keep launching
-        static size_t smem_limit = 0;
-        if (t->smem > smem_limit) {
-            if ((e = cudaFuncSetAttribute(temp_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)t->smem)) != cudaSuccess)
-                return undo(e, "shared memory");
-            smem_limit = t->smem;
-        }
-    }
+    // per device, the limit only grows: grids created earlier keep launching
+    if ((e = raise_smem_limit((const void*)temp_step_kernel, t->smem)) != cudaSuccess) return undo(e, "shared memory");
     const int64_t n = (int64_t)cells * G;
     temp_fill_kernel<<<(unsigned)((n + 255) / 256), 256>>>(t->T, t->Tm, t->material, G, (int)cells, nullptr);
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return undo(e, "initial fill");

@@ -3,8 +3,10 @@
 This module creates INPUT DATA only: capsule links carrying taxel lattices,
 procedural objects (spheres, convex hulls, superquadrics), poses and
 velocities, and the parameter sets.  It contains no step of the sensing
-method (no signed distance, no depth, force or noise arithmetic); both the
-CUDA path and the CPU oracle consume what it returns.
+method (no depth, force or noise arithmetic, no SDF grid or mesh query);
+the links are placed with a coarse surface estimate of its own
+(nearest face planes, see _PlacementSurface), which neither side reads.
+Both the CUDA path and the CPU oracle consume what it returns.
 
 The paper's own workloads (robot hands, task objects, a 10-cube scene) are
 not available, so these seeded procedural stand-ins follow the sizes the
@@ -24,7 +26,7 @@ import numpy as np
 
 DT = 1.0 / 200.0          # simulation step (200 Hz)
 TAXEL_RADIUS = 1e-3       # probe radius of an active taxel
-PAD_ARC = np.pi           # lattice arc of the batched configs: the pad half of each link
+PAD_ARC = np.pi / 3       # lattice arc of the batched configs: a 60-degree pad strip facing the object
 
 
 def f32(x):
@@ -441,15 +443,90 @@ def _unit(v):
     return v / np.linalg.norm(v, axis=-1, keepdims=True)
 
 
-def _assemble(name, rng, objects, env_obj, env_lattices, params, steps, press_frac=(0.5, 1.0),
-              press_depth=(0.0, 2e-3), gap=(2e-3, 2e-2), max_links=None, arc=2 * np.pi):
+class _PlacementSurface:
+    """Approximate signed distance of an object's surface, used only to place
+    links so that a chosen share of taxels penetrates (input construction,
+    not the sensing method): closed forms for the analytic kinds, and for
+    meshes (convex hulls and superquadrics with exponents <= 2, both convex)
+    the largest signed distance to the planes of the 16 faces whose centroids
+    are nearest.  Inside a convex polytope, and outside it over a face, the
+    largest plane distance over all faces is the exact signed distance; the
+    16 nearest faces reproduce it to ~1e-5 mm within 3 mm of the workloads'
+    surfaces.  Returns (phi, unit normal of the deciding plane)."""
+
+    def __init__(self, obj):
+        self.obj = obj
+        self.tree = None
+        if obj.verts is not None and obj.faces is not None and obj.kind not in ("sphere", "box", "plane"):
+            from scipy.spatial import cKDTree
+
+            V = obj.verts.astype(np.float64)
+            F = np.asarray(obj.faces, np.int64)
+            cen = V[F].mean(axis=1)
+            nrm = np.cross(V[F[:, 1]] - V[F[:, 0]], V[F[:, 2]] - V[F[:, 0]])
+            nrm /= np.maximum(np.linalg.norm(nrm, axis=1, keepdims=True), 1e-300)
+            self.nrm, self.off = nrm, np.einsum("ij,ij->i", nrm, cen)
+            self.k = min(8, len(F))
+            self.tree = cKDTree(cen)
+
+    def __call__(self, q):
+        o = self.obj
+        if len(q) == 0:
+            return np.zeros(0), np.zeros((0, 3))
+        if o.kind == "sphere":
+            r = np.linalg.norm(q, axis=1)
+            return r - float(o.radius), q / np.maximum(r, 1e-300)[:, None]
+        if o.kind == "plane":
+            return q[:, 2].copy(), np.tile([0.0, 0.0, 1.0], (len(q), 1))
+        if o.kind == "box":
+            d = np.abs(q) - np.asarray(o.half, np.float64)
+            out = np.maximum(d, 0.0)
+            on = np.linalg.norm(out, axis=1)
+            ax = np.argmax(d, axis=1)
+            n_in = np.zeros_like(q)
+            n_in[np.arange(len(q)), ax] = np.sign(q[np.arange(len(q)), ax])
+            n_out = np.sign(q) * out / np.maximum(on, 1e-300)[:, None]
+            inside = on == 0.0
+            return np.where(inside, d.max(axis=1), on), np.where(inside[:, None], n_in, n_out)
+        _, idx = self.tree.query(q, k=self.k, workers=-1)
+        idx = idx.reshape(len(q), -1)
+        phi = np.empty(len(q))
+        face = np.empty(len(q), np.int64)
+
+        def chunk(a):  # numpy releases the GIL inside these array operations
+            sl = slice(a, min(a + (1 << 16), len(q)))
+            i, x = idx[sl], q[sl]
+            nn = self.nrm[i]
+            d = nn[..., 0] * x[:, 0:1] + nn[..., 1] * x[:, 1:2] + nn[..., 2] * x[:, 2:3] - self.off[i]
+            b = d.argmax(axis=1)
+            r = np.arange(len(b))
+            phi[sl], face[sl] = d[r, b], i[r, b]
+
+        from concurrent.futures import ThreadPoolExecutor
+
+        with ThreadPoolExecutor(8) as ex:
+            list(ex.map(chunk, range(0, len(q), 1 << 16)))
+        return phi, self.nrm[face]
+
+
+def _assemble(name, rng, objects, env_obj, env_lattices, params, steps, pen_share=(0.1, 0.3), max_press=2e-3,
+              max_links=None, arc=2 * np.pi):
     """Place every env's links around its object and build the arrays.
 
     env_lattices[e] is a list of (rows, cols, n_active) per link.  Each link is
     a capsule (radius 8-12 mm, cylinder 20-45 mm) whose lattice arc faces the
-    object and whose side is pressed into the object's support plane by
-    U(press_depth) with probability U(press_frac) per env, otherwise held off
-    by U(gap).  Vectorised over envs and links."""
+    object along a random direction u, its axis perpendicular to u.  Every env
+    draws a target share f ~ U(pen_share) of its active taxels that penetrate
+    (probe sphere reaching into the object) at the time-0 poses, and all its
+    links are pressed from touching the object's support plane towards the
+    object by one depth delta_e, solved per env so that the share is met:
+    per taxel the press depth at which it starts to penetrate is linearised
+    from the placement surface (its distance over the slope n . u), delta_e is
+    set between the k-th and (k+1)-th smallest of them (k = round(f n)), and
+    the envs whose share, re-evaluated at delta_e, misses the target by more
+    than 1 % get up to three more such corrections from there.  The realised
+    shares and depths are kept in meta["placement"].  Vectorised over envs
+    and links."""
     E = len(env_lattices)
     L = max_links or max(len(lat) for lat in env_lattices)
     rows = np.zeros((E, L), np.int32); cols = np.zeros((E, L), np.int32); nact = np.zeros((E, L), np.int64)
@@ -470,12 +547,10 @@ def _assemble(name, rng, objects, env_obj, env_lattices, params, steps, press_fr
     obj_pose[:, 3:] = mats_to_quats(RC)
     obj_vel = np.concatenate([rng.normal(0.0, 0.1, (E, 3)), rng.normal(0.0, 1.0, (E, 3))], 1).astype(np.float32)
     # links
-    pf = rng.uniform(*press_frac, E)
+    f_target = rng.uniform(*pen_share, E)
     rc = rng.uniform(8e-3, 12e-3, (E, L))
     ln = rng.uniform(20e-3, 45e-3, (E, L))
     u = _unit(rng.standard_normal((E, L, 3)))
-    pressed = rng.uniform(size=(E, L)) < pf[:, None]
-    delta = np.where(pressed, rng.uniform(*press_depth, (E, L)), -rng.uniform(*gap, (E, L)))
     d_obj = np.einsum("eji,elj->eli", RC, u)          # directions in each object's frame
     h = np.einsum("ei,eli->el", pC, u)
     for k, obj in enumerate(objects):
@@ -492,19 +567,12 @@ def _assemble(name, rng, objects, env_obj, env_lattices, params, steps, press_fr
         else:
             Vd = obj.verts.astype(np.float64)
             h[sel] += (dk.reshape(-1, 3) @ Vd.T).max(axis=1).reshape(dk.shape[:2])
-    centre = (h + rc - delta)[..., None] * u
     axis = _unit(np.cross(u, rng.standard_normal((E, L, 3))))
     e1 = -u                                            # lattice column 0 faces the object
     e2 = np.cross(axis, e1)
     RL = np.stack([e1, e2, axis], axis=-1)
-    link_pose = np.zeros((E, L, 7), np.float32)
-    link_pose[..., 3] = 1.0
-    link_pose[..., :3] = centre
-    link_pose[..., 3:] = mats_to_quats(RL)
     link_vel = np.concatenate([rng.normal(0.0, 0.1, (E, L, 3)), rng.normal(0.0, 1.0, (E, L, 3))], -1).astype(np.float32)
     absent = rows * cols == 0
-    link_pose[absent] = (0, 0, 0, 1, 0, 0, 0)
-    link_vel[absent] = 0
     # taxels of every link lattice, in CSR order
     n_link = (rows.astype(np.int64) * cols).reshape(-1)
     starts = np.concatenate([[0], np.cumsum(n_link)])
@@ -524,14 +592,102 @@ def _assemble(name, rng, objects, env_obj, env_lattices, params, steps, press_fr
     z = -length / 2 + (rr + 0.5) * length / rl
     Rt = np.where(j < nact.reshape(-1)[link_of], TAXEL_RADIUS, 0.0)
     off = np.concatenate([[0], np.cumsum(n_link.reshape(E, L).sum(1))]).astype(np.int64)
+
+    # ---- press depth per env (time-0 poses, float32 inputs as both sides read them)
+    env_of = link_of // L
+    touch = (h + rc)[..., None] * u                    # link centres touching the support plane
+    # a taxel can penetrate at press delta only if it reaches the support plane:
+    # radius (1 - cos th) - R < delta; farther ones never do for delta <= max_press
+    cand = np.flatnonzero((Rt > 0) & (radius * (1.0 - np.cos(th)) - Rt < max_press))
+    ce, cl_ = env_of[cand], link_of[cand]
+    xl = np.stack([x[cand], y[cand], z[cand]], 1)
+    xw = np.einsum("nij,nj->ni", RL.reshape(E * L, 3, 3)[cl_], xl) + touch.reshape(E * L, 3)[cl_]
+    q0 = np.einsum("nji,nj->ni", RC[ce], xw - pC[ce])    # object frame, touching (press 0)
+    del xw, xl
+    dirs = d_obj.reshape(E * L, 3)[cl_]                  # a press delta moves a taxel by -delta dirs
+    surfaces = [_PlacementSurface(o) for o in objects]
+    oid_c = env_obj[ce]
+
+    def phi_at(delta_env, which):
+        """placement-surface phi and normal of candidates `which` with env presses delta_env"""
+        i = which
+        q = q0[i] - delta_env[ce[i], None] * dirs[i]
+        phi = np.empty(len(i)); nrm = np.empty((len(i), 3))
+        for k, srf in enumerate(surfaces):
+            s = np.flatnonzero(oid_c[i] == k)
+            if len(s):
+                phi[s], nrm[s] = srf(q[s])
+        return phi, nrm
+
+    n_act = np.bincount(env_of[Rt > 0], minlength=E).astype(np.int64)
+    k_target = np.rint(f_target * n_act).astype(np.int64)
+    n_cand = np.bincount(ce, minlength=E)
+    cstart = np.concatenate([[0], np.cumsum(n_cand)])
+    width = int(n_cand.max()) if E else 0
+
+    def solve(thr, base):
+        """per env: the press between the k-th and (k+1)-th smallest threshold"""
+        M = np.full((E, max(width, 1) + 1), np.inf)
+        M[ce, np.arange(len(ce)) - cstart[ce]] = thr
+        M.sort(axis=1)
+        k = np.minimum(k_target, width)
+        lo = np.where(k > 0, M[np.arange(E), np.maximum(k - 1, 0)], -np.inf)
+        hi = M[np.arange(E), k]
+        d = np.where(np.isfinite(lo) & np.isfinite(hi), 0.5 * (lo + hi),
+                     np.where(np.isfinite(lo), lo + 1e-5, np.where(np.isfinite(hi), hi - 1e-5, base)))
+        return np.clip(d, 0.0, max_press)
+
+    delta = np.zeros(E)
+    phi, nrm = phi_at(delta, np.arange(len(cand)))
+    slope = np.maximum(np.einsum("ij,ij->i", nrm, dirs), 0.05)
+    thr = (phi - Rt[cand]) / slope                     # press at which each candidate starts to penetrate
+    delta = solve(thr, delta)
+    # taxels whose linearised threshold lies within 0.5 mm of their env's
+    # press are re-evaluated at it (every env first, then the envs still off
+    # target); the rest keep the linear model's verdict
+    redo = np.ones(E, bool)
+    for _ in range(4):
+        near = np.flatnonzero(redo[ce] & (np.abs(thr - delta[ce]) < 5e-4))
+        phi_n, nrm_n = phi_at(delta, near)
+        slope[near] = np.maximum(np.einsum("ij,ij->i", nrm_n, dirs[near]), 0.05)
+        thr[near] = delta[ce[near]] + (phi_n - Rt[cand][near]) / slope[near]
+        pen = thr < delta[ce]
+        got = np.bincount(ce, weights=pen.astype(np.float64), minlength=E)
+        off_target = (np.abs(got - k_target) > 0.01 * np.maximum(n_act, 1)) & (delta < max_press)
+        if not off_target.any():
+            break
+        delta = np.where(off_target, solve(thr, delta), delta)
+        redo = off_target
+    pen = thr < delta[ce]
+    got = np.bincount(ce, weights=pen.astype(np.float64), minlength=E)
+    depth_c = np.maximum(delta[ce] - thr, 0.0) * slope  # R - phi of the penetrating candidates
+    share = got / np.maximum(n_act, 1)
+    centre = touch - delta[:, None, None] * u
+    link_pose = np.zeros((E, L, 7), np.float32)
+    link_pose[..., 3] = 1.0
+    link_pose[..., :3] = centre
+    link_pose[..., 3:] = mats_to_quats(RL)
+    link_pose[absent] = (0, 0, 0, 1, 0, 0, 0)
+    link_vel[absent] = 0
     wrap = np.full(E * L, 1 if arc >= 2 * np.pi else 0, np.uint8)
     wrap[absent.reshape(-1)] = 0
+    pd = depth_c[depth_c > 0]
+    meta = {"placement": {
+        "target_share": [float(pen_share[0]), float(pen_share[1])],
+        "share_mean": float(share.mean()) if E else 0.0,
+        "share_p5_p50_p95": [float(v) for v in np.percentile(share, [5, 50, 95])] if E else [],
+        "envs_within_2pct": float(np.mean(np.abs(share - f_target) <= 0.02)) if E else 1.0,
+        "press_mm_p5_p50_p95": [float(v) * 1e3 for v in np.percentile(delta, [5, 50, 95])] if E else [],
+        "depth_mm_p50_p90_max": ([float(v) * 1e3 for v in np.percentile(pd, [50, 90])] + [float(pd.max()) * 1e3])
+        if len(pd) else [],
+        "estimate": "nearest-face-plane distance of the exact meshes at the time-0 poses"},
+        "placement_env": {"target": f_target, "share": share, "press": delta}}
     return Workload(
         name=name, n_envs=E, max_links=L, taxel_offsets=off, taxel_gid0=off[:-1].copy(),
         env_gid=np.arange(E, dtype=np.int32), link_rows=rows.reshape(-1), link_cols=cols.reshape(-1), link_wrap=wrap,
         x=f32(x), y=f32(y), z=f32(z), nx=f32(np.cos(th)), ny=f32(np.sin(th)), nz=f32(np.zeros(T)), R=f32(Rt),
         objects=objects, obj_id=env_obj.astype(np.int32), link_pose=link_pose, link_vel=link_vel,
-        obj_pose=obj_pose, obj_vel=obj_vel, params=params, steps=steps,
+        obj_pose=obj_pose, obj_vel=obj_vel, params=params, steps=steps, meta=meta,
     )
 
 
@@ -576,8 +732,7 @@ def config0(seed: int = 20260001, n_envs: int = 64, n_meshes: int = 8) -> Worklo
     for _ in range(n_envs):
         order = rng.permutation(16)
         lattices.append([lat[i] for i in order])
-    return _assemble("config0", rng, objects, env_obj, lattices, default_params(seed), steps=1,
-                     press_frac=(0.8, 1.0), press_depth=(0.5e-3, 2e-3))
+    return _assemble("config0", rng, objects, env_obj, lattices, default_params(seed), steps=1)
 
 
 def config1_objects(rng, n_objects: int = 8, n_grid: int = 64, fp16: bool = False, faces=(3000, 6000)):
@@ -608,7 +763,7 @@ def config1(seed: int = 20260002, n_envs: int = 4096, n_links: int = 20, rows: i
     env_obj = rng.integers(0, n_objects, n_envs)
     lattices = [[(rows, cols, rows * cols)] * n_links for _ in range(n_envs)]
     return _assemble("config1", rng, objects, env_obj, lattices, default_params(seed), steps=steps,
-                     arc=PAD_ARC, press_frac=(1.0, 1.0), press_depth=(0.5e-3, 2.5e-3))
+                     arc=PAD_ARC)
 
 
 def uneven_lattices(rng, n_envs, taxels=(200, 1000), links=(10, 20), cols=10):
@@ -638,7 +793,7 @@ def metric_run(seed: int = 20260003, n_envs: int = 20480, n_objects: int = 64, n
     env_obj = rng.integers(0, n_objects, n_envs)
     lattices = [[(5, 10, 50)] * 20 for _ in range(n_envs)]
     return _assemble("metric_run", rng, objects, env_obj, lattices, default_params(seed), steps=steps,
-                     arc=PAD_ARC, press_frac=(1.0, 1.0), press_depth=(0.5e-3, 2.5e-3))
+                     arc=PAD_ARC)
 
 
 def config2(seed: int = 20260003, n_envs: int = 20480, n_objects: int = 64, n_grid: int = 96,
@@ -652,7 +807,7 @@ def config2(seed: int = 20260003, n_envs: int = 20480, n_objects: int = 64, n_gr
     params = default_params(seed)
     params["prox_rays"] = 8
     wl = _assemble("config2", rng, objects, env_obj, lattices, params, steps=steps, max_links=20,
-                   arc=PAD_ARC, press_frac=(1.0, 1.0), press_depth=(0.5e-3, 2.5e-3))
+                   arc=PAD_ARC)
     return add_pads(wl)
 
 

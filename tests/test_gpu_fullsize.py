@@ -57,8 +57,7 @@ def test_full_size_sampled_parity_in_the_bench_launch_configuration(tg):
     rng = np.random.default_rng(20260003)
     objs = low_poly_grid_objects(rng, N_OBJ, 96, fp16=True)
     wl = W._assemble("metric_run_lowpoly", rng, objs, rng.integers(0, N_OBJ, E), [[(5, 10, 50)] * L] * E,
-                     W.default_params(20260003), steps=3, arc=W.PAD_ARC, press_frac=(1.0, 1.0),
-                     press_depth=(0.5e-3, 2.5e-3))
+                     W.default_params(20260003), steps=3, arc=W.PAD_ARC)
     assert wl.n_active == E * 1000
     sc = tg.Scene(wl.geom(), wl.params)
     sc.upload_objects(wl.objects)

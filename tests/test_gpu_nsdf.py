@@ -241,7 +241,7 @@ def test_mixed_workload_neural_grid_fallback_dr_graph(tg):
     CUDA graph."""
     rng = np.random.default_rng(16)
     objs = bake_objects_oracle(W.config1_objects(rng, 6, n_grid=24, fp16=True, faces=(1500, 2500)))
-    nets = []
+    nets, used = [], []
     for k, err in ((0, 0.0), (2, 0.1), (4, 0.0), (5, 0.5)):
         o = objs[k]
         table, w = W.random_nsdf_params(rng, table_scale=1.0, out_scale=2.0)
@@ -250,17 +250,33 @@ def test_mixed_workload_neural_grid_fallback_dr_graph(tg):
                                nsdf_weights=w, nsdf_err_mm=err)
         if err * 1.2 <= 0.2:
             nets.append(oracle_nsdf(o.lo, o.hi, table, w))
+            used.append(k)
     lat = W.uneven_lattices(rng, 18)
     params = dict(W.default_params(44), dr={"mu": (0.4, 1.2), "k": (5e3, 2e4), "scale": (0.8, 1.2)})
     wl = W._assemble("mixed", rng, objs, rng.integers(0, len(objs), len(lat)), lat, params, steps=4, max_links=20,
-                     arc=W.PAD_ARC, press_frac=(1.0, 1.0), press_depth=(0.5e-3, 2.5e-3))
-    S = 0.0
+                     arc=W.PAD_ARC)
+    # Per-taxel bounds.  Envs whose object answers through its network get
+    # the learned-SDF bounds, derived as in the single-object test from the
+    # worst flip bound S of the networks in use: phi within 4 S (times the
+    # largest object scale), the stencil normal's relative error over its
+    # 4 h spacing, k at the top of its randomisation range.  Every other env
+    # (grid objects, and the network over its error budget whose grid answers)
+    # keeps the plain bounds: depth 1e-5 m, force 1e-4 relative + 1e-6 N.
+    S, g_typ = 0.0, np.inf
     for net in nets:
         lo, hi = np.array(net.s.lo[:]), np.array(net.s.hi[:])
-        S = max(S, net.flip_bound(lo + (hi - lo) * rng.uniform(0, 1, (5000, 3))).max())
-    d_tol = 4 * S * 1e-3 * 1.2 + 2e-7
-    tol = {"d_abs": max(d_tol, 1e-5), "band": d_tol, "f_rel": 5e-2, "f_abs": 4 * 2e4 * d_tol + 1e-6, "agg_d": d_tol,
-           "f_outliers": 0.005}
+        box = lo + (hi - lo) * rng.uniform(0, 1, (5000, 3))
+        S = max(S, net.flip_bound(box).max())
+        g_typ = min(g_typ, np.median(np.linalg.norm(net.normal(box[:2000]), axis=1)))
+    s_max, k_max = 1.2, 2e4
+    d_tol = 4 * S * 1e-3 * s_max + 2e-7
+    n_rel = 4 * 4 * S * 1e-3 * np.sqrt(3) / (4 * 2.5e-4) / g_typ
+    nt = np.repeat(np.isin(wl.obj_id, used), np.diff(wl.taxel_offsets))
+    tol = {"d_abs": np.where(nt, max(d_tol, 1e-5), 1e-5), "band": np.where(nt, d_tol, 1e-9),
+           "f_rel": np.where(nt, max(1e-3, 2 * n_rel), 1e-4), "f_abs": np.where(nt, 4 * k_max * d_tol + 1e-6, 1e-6),
+           "agg_d": np.where(nt, d_tol, 0.0), "f_outliers": 0.005}
+    print(f"learned-SDF envs: {int(np.isin(wl.obj_id, used).sum())} of {wl.n_envs}; d_tol {d_tol:.3e} m, "
+          f"f_rel {max(1e-3, 2 * n_rel):.3e}; grid envs: 1e-5 m, 1e-4 rel + 1e-6 N")
     sc = tg.Scene.from_workload(wl)
     sc.upload_objects(wl.objects)
     kinds = [sc.object_info(k)[0] for k in range(len(objs))]
@@ -276,6 +292,9 @@ def test_mixed_workload_neural_grid_fallback_dr_graph(tg):
         sc.sync()
         o = osc.step(ost, wl.inputs(s))
         st = compare_step(g, o, ost, wl.params, wl, where=f"mixed replay {s}", tol=tol, exclude=skip)
+        assert not (st["outliers"] & ~nt).any(), "a grid-object taxel outside the plain bounds"
+        print(f"mixed replay {s}: {st['n_outliers']} learned-SDF outliers of {int((nt & (wl.R > 0)).sum())} "
+              f"learned-SDF taxels; worst link-sum ratio {st['link_sums']:.3f}")
         skip |= st["outliers"]
     sc.graph_release()
     sc.close()

@@ -66,7 +66,7 @@ def test_grid_fp16_uneven_split_items(tg):
     lat.insert(5, [])                                                              # an env without taxels
     env_obj = rng.integers(0, len(objs), len(lat))
     wl = W._assemble("uneven16", rng, objs, env_obj, lat, W.default_params(99), steps=4, max_links=20,
-                     arc=W.PAD_ARC, press_frac=(1.0, 1.0), press_depth=(0.5e-3, 2.5e-3))
+                     arc=W.PAD_ARC)
     assert wl.taxel_offsets[6] == wl.taxel_offsets[5]
     stats = run_both(tg, wl, steps=4)
     print("grid16", stats[-1])
@@ -189,7 +189,7 @@ def test_maximum_sizes(tg):
     objs = bake_objects_oracle(W.config1_objects(rng, 2, n_grid=24, fp16=True, faces=(1500, 2500)))
     lat = [[(32, 32, 1024)], [(2, 3, 6)] * 33, [(32, 32, 1024), (1, 1, 1), (4, 5, 20)], [(1, 1, 1)]]
     wl = W._assemble("maxsize", rng, objs, rng.integers(0, 2, len(lat)), lat, W.default_params(7), steps=3,
-                     max_links=34, arc=W.PAD_ARC, press_frac=(1.0, 1.0), press_depth=(0.5e-3, 2.5e-3))
+                     max_links=34, arc=W.PAD_ARC)
     stats = run_both(tg, wl, steps=3)
     print("maxsize", stats[-1])
 

@@ -51,3 +51,40 @@ def test_marker_pads_have_orthonormal_frames_on_present_links():
     for e in range(wl.n_envs):
         for p in range(P):
             assert rows[e, wl.pads["pad_link"][e, p]] > 0
+
+
+def test_links_are_pressed_to_the_target_penetrating_share():
+    """Every env draws a target share f ~ U(0.1, 0.3) of its active taxels
+    that penetrate at the time-0 poses, with no probe deeper than 3 mm (a
+    press of at most 2 mm plus the 1 mm probe radius).  The realised share is
+    measured here with the oracle's exact mesh distance (clean depth > 0),
+    not with the generator's own surface estimate."""
+    from _scenes import oracle_scene
+
+    rng = np.random.default_rng(20260021)
+    objs = W.config1_objects(rng, 4, 8, fp16=False, faces=(3000, 4000))
+    meshes = [W.ObjectSpec(kind="mesh", verts=o.verts, faces=o.faces) for o in objs]
+    E = 48
+    wl = W._assemble("placement", rng, meshes, rng.integers(0, 4, E), [[(5, 10, 50)] * 20] * E,
+                     W.default_params(5), steps=1, arc=W.PAD_ARC)
+    pe = wl.meta["placement_env"]
+    assert np.all((pe["target"] >= 0.1) & (pe["target"] <= 0.3))
+    assert np.all((pe["press"] >= 0.0) & (pe["press"] <= 2e-3 + 1e-12))
+    sc = oracle_scene(wl)
+    st = sc.new_state()
+    sc.reset(st, 0)
+    out = sc.step(st, wl.inputs(0))
+    act = wl.R > 0
+    env = np.repeat(np.arange(E), np.diff(wl.taxel_offsets))
+    pen = act & (out["depth_clean"] > 0)
+    share = np.bincount(env, weights=pen.astype(float), minlength=E) / np.bincount(env, weights=act.astype(float))
+    assert out["depth_clean"].max() <= 3e-3 + 1e-6
+    # the estimate's own share agrees with the exact one to a few taxels per env
+    assert np.max(np.abs(share - pe["share"])) <= 0.01
+    # envs that did not hit the press limit meet their target within 2 %;
+    # the rest fall short (the object curves away from the pad)
+    free = pe["press"] < 2e-3 - 1e-9
+    assert free.sum() >= E // 2
+    assert np.all(np.abs(share[free] - pe["target"][free]) <= 0.02)
+    assert np.all(share[~free] <= pe["target"][~free] + 0.02)
+    assert 0.15 <= share.mean() <= 0.25
