@@ -78,8 +78,10 @@ def parse():
     ap.add_argument("--oracle-envs", type=int, default=800, help="env sample of the CPU oracle legs")
     ap.add_argument("--oracle-objects", type=int, default=2, help="objects whose envs form the oracle sample")
     ap.add_argument("--oracle-steps", type=int, default=300, help="steps of the cpu_baseline leg")
-    ap.add_argument("--schedule", choices=["auto", "grid", "grid-sorted", "persistent", "persistent-sorted"],
-                    default="auto", help="step-kernel schedule: picked by the autotuner (auto) or fixed")
+    ap.add_argument("--schedule", default="auto",
+                    choices=["auto"] + [f"{k}{s}" for k in ("grid", "persistent", "pipe1024", "pipe768", "pipe512")
+                                        for s in ("", "-sorted")],
+                    help="step-kernel schedule: picked by the autotuner (auto) or fixed")
     return ap.parse_args()
 
 
@@ -574,10 +576,12 @@ def run_tg(args):
     if args.schedule == "auto":
         tune = scene.autotune(step_inputs(0, d_in), steps=3)
     else:
-        scene.set_schedule(persistent=args.schedule.startswith("persistent"), sorted=args.schedule.endswith("sorted"))
+        scene.set_schedule(args.schedule.split("-")[0], sorted=args.schedule.endswith("sorted"))
         tune = {"candidates": "fixed by --schedule"}
     sched = scene.schedule()
-    launches_per_step = 3 + (1 if sched["sorted"] and len(wl.objects) > 1 else 0)  # pose, [order], step, advance
+    # pose, [order / order records], step, advance
+    launches_per_step = 3 + (1 if sched["schedule"].startswith("pipe") or (sched["sorted"] and len(wl.objects) > 1)
+                             else 0)
 
     # the step as a CUDA graph: replay r runs step r with pose_dt = r dt
     scene.profile(True)

@@ -330,25 +330,42 @@ tg_status tg_graph_launch(tg_scene* scene, int32_t n_steps, tg_stream stream);
 tg_status tg_graph_seek(tg_scene* scene, uint32_t step, double pose_dt, double pose_dt_per_step, tg_stream stream);
 tg_status tg_graph_release(tg_scene* scene);
 
-/* Work schedule of the step kernel.  persistent = 0: one CTA per work item
-   (a run of whole links of one env); 1: a grid of the resident CTA count
-   takes items from an atomic counter.  sorted = 1: items run in the order
-   of the object their env holds (a counting sort each step), so concurrent
-   CTAs share object grids in L2.  Results do not depend on the schedule.
-   tg_autotune times every schedule on `steps` steps of the given inputs
-   (after one warm-up step each), keeps the fastest, and restores the noise
-   state it found (the output buffers then hold the last trial's step).
+/* Work schedule of the step kernel.  Work items are runs of whole links of
+   one env (at most 1,024 taxels).
+     TG_SCHED_GRID        one 512-thread CTA per work item;
+     TG_SCHED_PERSISTENT  resident 512-thread CTAs take items from an atomic
+                          counter;
+     TG_SCHED_PIPE_1024 / _768 / _512  pipelined: one CTA of that many
+                          threads per SM runs its share of the items in turn,
+                          and bulk copies bring each item's taxel geometry,
+                          link poses and noise state into shared memory while
+                          the item before it computes.
+   sorted = 1: items run in the order of the object their env holds (a
+   counting sort each step), so concurrent CTAs share object grids in L2.
+   Results are bit-identical across schedules.  tg_autotune times every
+   schedule (x sorted / env order when there are several objects) on `steps`
+   steps of the given inputs (after one warm-up step each), keeps the
+   fastest, and restores the noise state it found (the output buffers then
+   hold the last trial's step).
    Errors: TG_ERR_STATE (a captured graph exists), TG_ERR_INVALID_ARG. */
+typedef enum {
+    TG_SCHED_GRID = 0,
+    TG_SCHED_PERSISTENT = 1,
+    TG_SCHED_PIPE_1024 = 2,
+    TG_SCHED_PIPE_768 = 3,
+    TG_SCHED_PIPE_512 = 4,
+    TG_SCHED_COUNT = 5
+} tg_schedule;
 typedef struct {
-    int32_t persistent, sorted;
+    int32_t schedule, sorted;
     double ms_per_step;
 } tg_tune_candidate;
 typedef struct {
     int32_t n, chosen;
-    tg_tune_candidate cand[8];
+    tg_tune_candidate cand[16];
 } tg_tune_report;
-tg_status tg_set_schedule(tg_scene* scene, int32_t persistent, int32_t sorted);
-tg_status tg_get_schedule(const tg_scene* scene, int32_t* persistent, int32_t* sorted);
+tg_status tg_set_schedule(tg_scene* scene, int32_t schedule, int32_t sorted);
+tg_status tg_get_schedule(const tg_scene* scene, int32_t* schedule, int32_t* sorted);
 tg_status tg_autotune(tg_scene* scene, const tg_step_inputs* in, int32_t steps, tg_tune_report* report,
                       tg_stream stream);
 

@@ -89,9 +89,12 @@ struct tg_scene {
     float* nq_phi = nullptr;          // [T]
     float* nq_grad = nullptr;         // [3][T]
     // schedule (tg_set_schedule / tg_autotune) and step control
-    int persistent = 0;               // step kernel: persistent CTAs on a work counter
+    int schedule = TG_SCHED_GRID;     // step kernel schedule (tg_schedule)
     int sorted = 1;                   // object-sorted item order (several objects)
     int resident_ctas = 0;            // step kernel CTAs resident on the device at once
+    int sms = 0;                      // streaming multiprocessors (pipelined schedules: one CTA each)
+    ItemMeta* metas = nullptr;        // [n_items] static item layout (pipelined schedules)
+    SlotRec* slots = nullptr;         // [n_items] this step's order records (pipelined schedules)
     StepCtl* ctl = nullptr;
     // captured step (tg_graph_*)
     cudaStream_t cap_stream = nullptr;
@@ -286,8 +289,11 @@ StepArgs step_args(tg_scene* s) {
     a.prox_noisy = s->prox_noisy;
     a.ctl = s->ctl;
     a.n_items = s->n_items;
-    a.persistent = s->persistent;
+    a.persistent = s->schedule == TG_SCHED_PERSISTENT ? 1 : 0;
     a.resident_ctas = s->resident_ctas;
+    a.metas = s->metas;
+    a.slots = s->slots;
+    a.sms = s->sms;
     a.nq_phi = s->nq_phi;
     a.nq_grad = s->nq_grad;
     a.any_neural = s->any_neural ? 1 : 0;
@@ -474,8 +480,11 @@ tg_status tg_create_scene(const tg_scene_desc* d, tg_scene** out) {
     } while (0)
 
     const size_t EL = (size_t)E * L;
-    CKC(dalloc(&s->x, T)); CKC(dalloc(&s->y, T)); CKC(dalloc(&s->z, T));
-    CKC(dalloc(&s->nx, T)); CKC(dalloc(&s->ny, T)); CKC(dalloc(&s->nz, T)); CKC(dalloc(&s->R, T));
+    // per-taxel arrays the pipelined step kernel bulk-copies carry 16 bytes
+    // of slack: a copy runs to the 16-byte boundary at or past an item's end
+    const size_t Tp = (size_t)T + 16;
+    CKC(dalloc(&s->x, Tp)); CKC(dalloc(&s->y, Tp)); CKC(dalloc(&s->z, Tp));
+    CKC(dalloc(&s->nx, Tp)); CKC(dalloc(&s->ny, Tp)); CKC(dalloc(&s->nz, Tp)); CKC(dalloc(&s->R, Tp));
     const float* src[7] = {d->x, d->y, d->z, d->nx, d->ny, d->nz, d->R};
     float* dst[7] = {s->x, s->y, s->z, s->nx, s->ny, s->nz, s->R};
     for (int i = 0; i < 7; ++i)
@@ -484,10 +493,10 @@ tg_status tg_create_scene(const tg_scene_desc* d, tg_scene** out) {
     if (!items.empty()) CKC(cudaMemcpy(s->items, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice));
     CKC(dalloc(&s->lattice, EL));
     CKC(cudaMemcpy(s->lattice, lat.data(), EL * sizeof(LinkLattice), cudaMemcpyHostToDevice));
-    CKC(dalloc(&s->flags, T));
-    CKC(dalloc(&s->hyst_prev, (size_t)8 * T));
-    CKC(dalloc(&s->hyst_xi, (size_t)8 * T));
-    CKC(dalloc(&s->drift, (size_t)8 * T));
+    CKC(dalloc(&s->flags, Tp));
+    CKC(dalloc(&s->hyst_prev, (size_t)8 * T + 16));
+    CKC(dalloc(&s->hyst_xi, (size_t)8 * T + 16));
+    CKC(dalloc(&s->drift, (size_t)8 * T + 16));
     CKC(dalloc(&s->episode, E));
     CKC(dalloc(&s->depth_clean, T));
     CKC(dalloc(&s->depth_noisy, T));
@@ -507,9 +516,51 @@ tg_status tg_create_scene(const tg_scene_desc* d, tg_scene** out) {
     CKC(dalloc(&s->s_mask, E));
     CKC(dalloc(&s->s_contact, T));
     CKC(dalloc(&s->items_sorted, items.size()));
+    {
+        // static layout of every item for the pipelined schedules
+        std::vector<ItemMeta> metas(items.size());
+        for (size_t q = 0; q < items.size(); ++q) {
+            const Item& it = items[q];
+            ItemMeta& m = metas[q];
+            std::memset(&m, 0, sizeof(m));
+            m.nl = it.link_end - it.link_begin;
+            const LinkLattice* ll = &lat[(size_t)it.env * L + it.link_begin];
+            const int base = ll[0].env_offset;
+            bool uni = true;
+            for (int k = 0; k < m.nl; ++k) {
+                m.start[k] = ll[k].env_offset - base;
+                m.rows[k] = ll[k].rows;
+                m.cols[k] = ll[k].cols;
+                m.wrap[k] = ll[k].wrap;
+                const int cnt = (k + 1 < m.nl ? ll[k + 1].env_offset - base : it.n_taxels) - m.start[k];
+                uni = uni && ll[k].rows == ll[0].rows && ll[k].cols == ll[0].cols && ll[k].wrap == ll[0].wrap &&
+                      cnt == ll[0].rows * ll[0].cols;
+            }
+            m.start[m.nl] = it.n_taxels;
+            const int len = ll[0].rows * ll[0].cols;
+            uni = uni && len > 0;
+            // the same rule and the same FP32 reciprocals as the step kernel's prologue
+            m.uni_len = uni ? len : 0;
+            m.uni_rows = ll[0].rows;
+            m.uni_cols = ll[0].cols;
+            m.uni_wrap = ll[0].wrap;
+            m.uni_inv_len = uni ? 1.0f / (float)len : 0.0f;
+            m.uni_inv_cols = uni ? 1.0f / (float)ll[0].cols : 0.0f;
+        }
+        CKC(dalloc(&s->metas, metas.size()));
+        if (!metas.empty())
+            CKC(cudaMemcpy(s->metas, metas.data(), metas.size() * sizeof(ItemMeta), cudaMemcpyHostToDevice));
+        CKC(dalloc(&s->slots, items.size()));
+    }
     CKC(dalloc(&s->ctl, 1));
     CKC(cudaMemset(s->ctl, 0, sizeof(StepCtl)));
     CKC(configure_step_kernels());
+    CKC(configure_pipe_kernels());
+    {
+        int dev = 0;
+        CKC(cudaGetDevice(&dev));
+        CKC(cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev));
+    }
     s->resident_ctas = step_kernel_resident_ctas();
     if (s->resident_ctas <= 0) return bail(cudaErrorInvalidConfiguration, "step kernel occupancy");
     if (d->sensors & TG_SENSOR_PROX) {
@@ -607,7 +658,7 @@ void tg_destroy_scene(tg_scene* s) {
                     s->hyst_xi, s->drift, s->episode, s->depth_clean, s->depth_noisy, s->dist, s->ft_clean,
                     s->ft_noisy, s->link_out, s->link_count, s->err, s->link_rec, s->s_link_pose, s->s_link_vel,
                     s->s_obj_pose, s->s_obj_vel, s->s_env_params, s->s_obj_id, s->s_mask, s->s_contact,
-                    s->items_sorted, s->prox_clean, s->prox_noisy, s->pad_link, s->pad_frame,
+                    s->items_sorted, s->metas, s->slots, s->prox_clean, s->prox_noisy, s->pad_link, s->pad_frame,
                     s->marker_u, s->ctl, s->nq_phi, s->nq_grad, s->pc_ft, s->anchors, s->anchor_obj,
                     s->n_anchored};
     for (void* p : ptrs) dfree(p);
@@ -917,13 +968,18 @@ tg_status enqueue_step(tg_scene* s, const tg_step_inputs* in, cudaStream_t st, b
     a.step = in->step;
     a.step_from_ctl = graph ? 1 : 0;
     a.items_sorted = nullptr;
-    if (s->sorted && s->n_objects > 1 && s->n_objects <= 12288) {
+    const bool pipe = s->schedule >= TG_SCHED_PIPE_1024;
+    const bool sort = s->sorted && s->n_objects > 1 && s->n_objects <= 12288;
+    if (pipe) {
+        CK(s, launch_slot_records(s->items, s->n_items, oid, s->n_objects, s->episode, sort ? 1 : 0, s->slots, st));
+    } else if (sort) {
         CK(s, launch_order_items(s->items, s->n_items, oid, s->n_objects, s->items_sorted, st));
         a.items_sorted = s->items_sorted;
     }
     if (prof) CK(s, record(ev[1]));
     if (s->any_neural) CK(s, launch_nsdf_step_query(a, s->n_items, s->nq_phi, s->nq_grad, st));
-    CK(s, launch_step(a, s->n_items, st));
+    if (pipe) CK(s, launch_step_pipe(a, s->n_items, kPipeThreads[s->schedule - TG_SCHED_PIPE_1024], st));
+    else CK(s, launch_step(a, s->n_items, st));
     if (prof) CK(s, record(ev[2]));
     if (s->sensors & TG_SENSOR_PROX) CK(s, launch_prox(a, s->n_items, st));
     if (s->sensors & TG_SENSOR_PCPROX) CK(s, launch_pc_prox(a, s->n_items, st));
@@ -1080,17 +1136,18 @@ tg_status tg_graph_release(tg_scene* s) {
     return TG_OK;
 }
 
-tg_status tg_set_schedule(tg_scene* s, int32_t persistent, int32_t sorted) {
+tg_status tg_set_schedule(tg_scene* s, int32_t schedule, int32_t sorted) {
     if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
     if (s->graph_exec) return fail(s, TG_ERR_STATE, "release the captured step before changing the schedule");
-    s->persistent = persistent != 0;
+    if (schedule < 0 || schedule >= TG_SCHED_COUNT) return fail(s, TG_ERR_INVALID_ARG, "unknown schedule");
+    s->schedule = schedule;
     s->sorted = sorted != 0;
     return TG_OK;
 }
 
-tg_status tg_get_schedule(const tg_scene* s, int32_t* persistent, int32_t* sorted) {
+tg_status tg_get_schedule(const tg_scene* s, int32_t* schedule, int32_t* sorted) {
     if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
-    if (persistent) *persistent = s->persistent;
+    if (schedule) *schedule = s->schedule;
     if (sorted) *sorted = s->sorted;
     return TG_OK;
 }
@@ -1123,7 +1180,7 @@ tg_status tg_autotune(tg_scene* s, const tg_step_inputs* in, int32_t steps, tg_t
     };
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     tg_tune_report rep{};
-    const int old_p = s->persistent, old_s = s->sorted;
+    const int old_p = s->schedule, old_s = s->sorted;
     const bool prof = s->profiling;
     s->profiling = false;
     cudaError_t err = save(false);
@@ -1131,9 +1188,9 @@ tg_status tg_autotune(tg_scene* s, const tg_step_inputs* in, int32_t steps, tg_t
     if (err == cudaSuccess) err = cudaEventCreate(&e1);
     tg_status r = TG_OK;
     const int sort_options = s->n_objects > 1 ? 2 : 1;
-    for (int ps = 0; ps < 2 && err == cudaSuccess && r == TG_OK; ++ps)
+    for (int ps = 0; ps < TG_SCHED_COUNT && err == cudaSuccess && r == TG_OK; ++ps)
         for (int so = 0; so < sort_options && err == cudaSuccess && r == TG_OK; ++so) {
-            s->persistent = ps;
+            s->schedule = ps;
             s->sorted = sort_options == 2 ? 1 - so : s->sorted;
             r = enqueue_step(s, in, st, false);  // warm-up of this variant
             if (r != TG_OK) break;
@@ -1146,7 +1203,7 @@ tg_status tg_autotune(tg_scene* s, const tg_step_inputs* in, int32_t steps, tg_t
             if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
             if (err != cudaSuccess) break;
             tg_tune_candidate& c = rep.cand[rep.n++];
-            c.persistent = s->persistent;
+            c.schedule = s->schedule;
             c.sorted = s->sorted;
             c.ms_per_step = (double)ms / steps;
         }
@@ -1157,7 +1214,7 @@ tg_status tg_autotune(tg_scene* s, const tg_step_inputs* in, int32_t steps, tg_t
     if (e1) cudaEventDestroy(e1);
     cudaFree(keep);
     if (r != TG_OK || err != cudaSuccess || rep.n == 0) {
-        s->persistent = old_p;
+        s->schedule = old_p;
         s->sorted = old_s;
         if (r != TG_OK) return r;
         return cuda_fail(s, err == cudaSuccess ? cudaErrorUnknown : err, "autotune");
@@ -1166,7 +1223,7 @@ tg_status tg_autotune(tg_scene* s, const tg_step_inputs* in, int32_t steps, tg_t
     for (int i = 1; i < rep.n; ++i)
         if (rep.cand[i].ms_per_step < rep.cand[best].ms_per_step) best = i;
     rep.chosen = best;
-    s->persistent = rep.cand[best].persistent;
+    s->schedule = rep.cand[best].schedule;
     s->sorted = rep.cand[best].sorted;
     if (report) *report = rep;
     return TG_OK;
@@ -1272,8 +1329,11 @@ tg_status tg_sync(tg_scene* s, tg_stream stream) {
     CK(s, cudaGetLastError());
     unsigned h[4] = {0, 0, 0, 0};
     CK(s, cudaMemcpy(h, s->err, sizeof(h), cudaMemcpyDeviceToHost));
-    if (h[0] || h[1]) {
+    if (h[0] || h[1] || h[2]) {
         CK(s, cudaMemset(s->err, 0, sizeof(h)));
+        if (h[2])
+            return fail(s, TG_ERR_TIMEOUT, "a bulk copy of the pipelined step kernel did not complete in time (" +
+                                               std::to_string(h[2]) + " CTAs stopped)");
         if (h[1])
             return fail(s, TG_ERR_TIMEOUT, "a tensor-core MMA of the learned-SDF query did not complete in time (" +
                                                std::to_string(h[1]) + " work items skipped)");

@@ -15,6 +15,7 @@ constexpr int kStepThreads = 512;    // CTA size of the step kernel
 constexpr int kStepMinBlocks = 2;    // resident CTAs per SM the register budget is set for
 constexpr int kLinkRec = 40;         // floats per (env, link) pose record
 constexpr int kLinkOut = 18;         // floats per (env, link) output record
+constexpr int kItemMaxLinks = 32;    // links per work item
 
 // Step control in device memory.  Direct steps pass step and pose_dt as
 // kernel arguments; a captured CUDA graph reads them from here instead and
@@ -59,8 +60,9 @@ struct ParamsDev {
     float dr_lo[3], dr_hi[3];
 };
 
-// Object table entry (object frame).
-struct ObjDev {
+// Object table entry (object frame); its size is a multiple of 16 bytes so
+// that an entry can be bulk-copied.
+struct alignas(16) ObjDev {
     int kind;
     float radius;
     float half[3];
@@ -89,6 +91,7 @@ struct ObjDev {
     float pc_inv_h;
     int32_t pc_n;
 };
+static_assert(sizeof(ObjDev) % 16 == 0, "bulk-copyable object entries");
 
 // One CTA of the step kernel: a run of whole links of one env.
 struct Item {
@@ -98,6 +101,34 @@ struct Item {
     int32_t n_taxels;
     int32_t pad;
 };
+
+// Static layout of one work item for the pipelined step kernel, built at
+// scene creation: the item's links' first taxels relative to the item, their
+// lattices, and (when every link has the same rows x cols lattice holding
+// rows * cols taxels) that lattice for the index arithmetic.  352 bytes, a
+// multiple of 16 so that it can be bulk-copied.
+struct alignas(16) ItemMeta {
+    int32_t nl;                                  // links
+    int32_t uni_len, uni_rows, uni_cols, uni_wrap;
+    float uni_inv_len, uni_inv_cols;
+    int32_t start[kItemMaxLinks + 1];            // first taxel of each link; start[nl] = taxels
+    uint16_t rows[kItemMaxLinks], cols[kItemMaxLinks];
+    uint8_t wrap[kItemMaxLinks];
+    int32_t pad[8];
+};
+static_assert(sizeof(ItemMeta) == 352, "ItemMeta layout");
+
+// One work item of this step as the pipelined step kernel reads it, in the
+// step's item order (object-sorted or env order): where its taxels are, its
+// env, the object the env holds this step and the env's episode.
+struct alignas(16) SlotRec {
+    int64_t taxel_begin;
+    int32_t n_taxels, env;
+    int32_t item, oid;
+    uint32_t episode;
+    int16_t link_begin, link_end;
+};
+static_assert(sizeof(SlotRec) == 32, "SlotRec layout");
 
 // Per (env, link) lattice: where its taxels start within the item's env.
 struct LinkLattice {
@@ -129,6 +160,10 @@ struct StepArgs {
     int n_items;
     int persistent;                   // step kernel: CTAs take items from ctl->counter
     int resident_ctas;                // persistent grid size (SMs x resident CTAs per SM)
+    // pipelined step kernel
+    const ItemMeta* metas;            // [n_items] static item layout
+    const SlotRec* slots;             // [n_items] this step's items in order
+    int sms;                          // streaming multiprocessors (one CTA each)
     // state
     uint8_t* flags;
     float* hyst_prev;                 // [8][T]
@@ -207,6 +242,14 @@ struct PoseArgs {
 cudaError_t raise_smem_limit(const void* func, size_t bytes);
 
 cudaError_t launch_pose(const PoseArgs& a, cudaStream_t s);
+// pipelined step kernel (step_pipe.cu): threads per CTA 512, 768 or 1024
+constexpr int kPipeShapes = 3;
+constexpr int kPipeThreads[kPipeShapes] = {1024, 768, 512};
+cudaError_t configure_pipe_kernels();
+cudaError_t launch_step_pipe(const StepArgs& a, int n_items, int threads, cudaStream_t s);
+// the step's SlotRec array: items in object-sorted order (sorted != 0) or in env order
+cudaError_t launch_slot_records(const Item* items, int n_items, const int32_t* obj_id, int n_objects,
+                                const uint32_t* episode, int sorted, SlotRec* out, cudaStream_t s);
 cudaError_t launch_step(const StepArgs& a, int n_items, cudaStream_t s);
 cudaError_t configure_step_kernels();
 cudaError_t launch_set_ctl(StepCtl* ctl, StepCtl value, cudaStream_t s);

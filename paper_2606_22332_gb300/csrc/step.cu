@@ -28,8 +28,6 @@
 
 namespace tg {
 
-constexpr int kItemMaxLinks = 32;
-
 struct SmemStep {
     float rec[kItemMaxLinks][kLinkRec];
     int start[kItemMaxLinks + 1];       // first taxel of each link, relative to the item
@@ -49,13 +47,6 @@ struct SmemStep {
     int uni_len, uni_rows, uni_cols, uni_wrap;
     float uni_inv_len, uni_inv_cols;
 };
-
-// Link of item taxel i (and, in B, its lattice row and column) for a uniform
-// item: l = floor((i + 1/2) / len) evaluated as (i + 1/2) * fl(1/len) in
-// FP32.  The quotient lies at least 1/(2 len) from an integer while the two
-// roundings move it by at most 2^-23 (i + 1/2) / len; for i < 1024 and
-// len <= 1024 that is below 1.3e-4 < 1/(2 len), so the floor is exact.
-__device__ __forceinline__ int uni_div(int i, float inv) { return (int)(((float)i + 0.5f) * inv); }
 
 // One work item: every phase of the step for its taxels.
 template <int NT, bool RADIUS>

@@ -47,6 +47,13 @@ __device__ __forceinline__ void acc_add(Acc& a, float x) {
     a.s = t;
 }
 
+// Link of item taxel i (and, in B, its lattice row and column) for a uniform
+// item: l = floor((i + 1/2) / len) evaluated as (i + 1/2) * fl(1/len) in
+// FP32.  The quotient lies at least 1/(2 len) from an integer while the two
+// roundings move it by at most 2^-23 (i + 1/2) / len; for i < 1024 and
+// len <= 1024 that is below 1.3e-4 < 1/(2 len), so the floor is exact.
+__device__ __forceinline__ int uni_div(int i, float inv) { return (int)(((float)i + 0.5f) * inv); }
+
 // FP32 object-frame query point q^ = M x + t and scaled SDF s phi(q^)
 __device__ __forceinline__ float fast_query(const float* rec, const ObjDev& obj, float x0, float x1, float x2) {
     const float3 q = f3(fmaf(rec[0], x0, fmaf(rec[1], x1, fmaf(rec[2], x2, rec[18]))),
@@ -74,21 +81,22 @@ struct CleanReading {
     float dn;
     float fn[3], tqn[3];
     uint8_t bits;
+    uint8_t flags;   // the taxel's new flag byte
+    float dist;      // surface distance phi - R
 };
 
 // A near-contact taxel at link-frame position (x0, x1, x2) with probe radius
 // R and last step's flag byte: compensated query point and SDF (near-contact
 // depths carry ~1e-14 relative error), depth, Schmitt decision on the
-// compensated depth, force/torque; writes the clean outputs and the new flag
-// byte.  With probe-radius noise the noisy readout's radius max(0, R + eps)
-// gives a second depth, its own Schmitt decision (flag bit 2) and a second
-// force (same normal and velocities).
+// compensated depth, force/torque, the new flag byte.  With probe-radius
+// noise the noisy readout's radius max(0, R + eps) gives a second depth, its
+// own Schmitt decision (flag bit 2) and a second force (same normal and
+// velocities).  Pure: the caller stores the results (store_clean).
 template <bool RADIUS>  // probe-radius noise on (rho > 0)
-__device__ __forceinline__ CleanReading refine_taxel(const StepArgs& a, const float* rec, const ObjDev& obj,
-                                                     int64_t g, float x0, float x1, float x2, float R,
-                                                     uint8_t flags, uint32_t step) {
-    const ParamsDev& P = a.P;
-    const int64_t T = a.n_taxels;
+__device__ __forceinline__ CleanReading refine_compute(const ParamsDev& P, const float* nq_phi, const float* nq_grad,
+                                                       int64_t T, int64_t gid0, const float* rec, const ObjDev& obj,
+                                                       int64_t g, float x0, float x1, float x2, float R,
+                                                       uint8_t flags, uint32_t step) {
     df qd[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
@@ -103,14 +111,15 @@ __device__ __forceinline__ CleanReading refine_taxel(const StepArgs& a, const fl
     df phid;
     if (obj.kind == TG_OBJ_NEURAL) {
         // the learned SDF has no compensated form: its FP32 phi and gradient
-        phid = df_from(a.nq_phi[g]);
-        go = f3(a.nq_grad[g], a.nq_grad[T + g], a.nq_grad[2 * T + g]);
+        phid = df_from(nq_phi[g]);
+        go = f3(nq_grad[g], nq_grad[T + g], nq_grad[2 * T + g]);
     } else {
         phid = df_mul_f(sdf_refine(obj, df3{qd[0], qd[1], qd[2]}, &go), scale);
     }
     const df dd = df_add_f(df_neg(phid), R);  // R - phi
     CleanReading out;
     out.d = dd.hi > 0.0f ? dd.hi : 0.0f;
+    out.dist = -dd.hi;
     const df eta_on = df{P.eta_on_hi, P.eta_on_lo}, eta_off = df{P.eta_off_hi, P.eta_off_lo};
     const bool prev = flags & 1u;
     const bool y = df_gt(dd, eta_on) || (prev && df_gt(dd, eta_off));
@@ -119,7 +128,7 @@ __device__ __forceinline__ CleanReading refine_taxel(const StepArgs& a, const fl
     out.dn = out.d;
     if constexpr (RADIUS) {
         // eps = rho (2u - 1) in binary32 (2u - 1 is exact); R + eps exact as a pair
-        const float u = u24(draw_rk(P.rk, (uint64_t)(a.gid0 + g), step, TAG_RADIUS).x);
+        const float u = u24(draw_rk(P.rk, (uint64_t)(gid0 + g), step, TAG_RADIUS).x);
         const float eps = P.rho * (2.0f * u - 1.0f);
         df Rn = df_add_f(df_from(R), eps);
         if (df_lt(Rn, df_from(0.0f))) Rn = df_from(0.0f);
@@ -128,7 +137,7 @@ __device__ __forceinline__ CleanReading refine_taxel(const StepArgs& a, const fl
         const bool prevn = flags & 4u;
         yn = (df_gt(ddn, eta_on) || (prevn && df_gt(ddn, eta_off))) && !dead;
     }
-    __stcs(a.flags + g, (uint8_t)((y ? 1u : 0u) | (flags & 2u) | (yn ? 4u : 0u)));
+    out.flags = (uint8_t)((y ? 1u : 0u) | (flags & 2u) | (yn ? 4u : 0u));
 #pragma unroll
     for (int c = 0; c < 3; ++c) { out.f[c] = 0.f; out.tq[c] = 0.f; out.fn[c] = 0.f; out.tqn[c] = 0.f; }
     const float d = out.d, dn = out.dn;
@@ -161,45 +170,141 @@ __device__ __forceinline__ CleanReading refine_taxel(const StepArgs& a, const fl
         if (d > 0.0f) force(d, out.f, out.tq);
         if (RADIUS && dn > 0.0f) force(dn, out.fn, out.tqn);
     }
-    __stcs(a.depth_clean + g, d);
-    if (a.sensors & TG_SENSOR_DIST) __stcs(a.dist + g, -dd.hi);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        __stcs(a.ft_clean + c * T + g, out.f[c]);
-        __stcs(a.ft_clean + (3 + c) * T + g, out.tq[c]);
-    }
     out.bits = (uint8_t)((y ? BIT_CLEAN : 0u) | (yn ? BIT_NOISY : 0u) | (dead ? BIT_DEAD : 0u) | BIT_ACTIVE |
                          (RADIUS ? BIT_NEAR : 0u));
     return out;
 }
 
+// the clean outputs of a refined taxel
+__device__ __forceinline__ void store_clean(const StepArgs& a, int64_t g, const CleanReading& cr) {
+    const int64_t T = a.n_taxels;
+    __stcs(a.flags + g, cr.flags);
+    __stcs(a.depth_clean + g, cr.d);
+    if (a.sensors & TG_SENSOR_DIST) __stcs(a.dist + g, cr.dist);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        __stcs(a.ft_clean + c * T + g, cr.f[c]);
+        __stcs(a.ft_clean + (3 + c) * T + g, cr.tq[c]);
+    }
+}
+
+template <bool RADIUS>
+__device__ __forceinline__ CleanReading refine_taxel(const StepArgs& a, const float* rec, const ObjDev& obj,
+                                                     int64_t g, float x0, float x1, float x2, float R,
+                                                     uint8_t flags, uint32_t step) {
+    const CleanReading cr = refine_compute<RADIUS>(a.P, a.nq_phi, a.nq_grad, a.n_taxels, a.gid0, rec, obj, g, x0, x1,
+                                                   x2, R, flags, step);
+    store_clean(a, g, cr);
+    return cr;
+}
+
+// The noise state a taxel's step reads (hysteresis x_{t-1} and xi of the
+// depth and six force/torque channels, the depth drift) and what the step
+// leaves of it.
+struct NoiseIn {
+    float prev_d, xi_d, drift_d;
+    float pv[6], xv[6];
+};
+struct NoiseOut {
+    float prev_d, xi_d, drift_d;   // new state (stored where the group has it)
+    float pv[6], xv[6];
+    float xd;                      // noisy depth
+    float hx[6];                   // force/torque after gain and hysteresis (crosstalk input)
+};
+
+// which state a parameter set reads and writes
+__device__ __forceinline__ bool hyst_depth_on(const ParamsDev& P) { return P.depth.beta != 0.0f; }
+__device__ __forceinline__ bool hyst_ft_on(const ParamsDev& P) { return P.ft.beta != 0.0f; }
+__device__ __forceinline__ bool drift_depth_on(const ParamsDev& P) { return P.depth.sigma_rw != 0.0f; }
+__device__ __forceinline__ bool drift_ft_on(const ParamsDev& P) { return P.ft.sigma_rw != 0.0f; }
+
+// Noise state of one active taxel from its clean depth d and the depth and
+// force/torque its noisy chain starts from (d_in, f_in: the clean ones, or
+// those of the perturbed radius): gain, hysteresis (Eqs. 27, 29-30), depth
+// base noise and dead override (Eqs. 25, 28).  Pure.
+__device__ __forceinline__ NoiseOut noise_core(const ParamsDev& P, uint64_t gid, uint32_t ep, uint32_t step,
+                                               uint8_t bits, float d_in, const float* f_in, const NoiseIn& s) {
+    NoiseOut o;
+    const bool hyst_d = hyst_depth_on(P), hyst_f = hyst_ft_on(P), walk_d = drift_depth_on(P);
+    const bool dead = bits & BIT_DEAD;
+    uint4 wep = make_uint4(0, 0, 0, 0);
+    if (P.depth.gain_on | P.ft.gain_on) wep = draw_rk(P.rk, gid, ep, TAG_EPISODE);
+    const float gain_d = P.depth.gain_on ? P.depth.gain_lo + P.depth.gain_span * u24(wep.y) : 1.0f;
+    const float gain_f = P.ft.gain_on ? P.ft.gain_lo + P.ft.gain_span * u24(wep.z) : 1.0f;
+    float xd = gain_d * d_in;
+    o.prev_d = s.prev_d;
+    o.xi_d = s.xi_d;
+    if (hyst_d) {
+        const float xi = P.depth.decay * s.xi_d + (xd - s.prev_d);
+        o.xi_d = xi;
+        o.prev_d = xd;
+        xd = xd + P.depth.beta * xi;
+    }
+    if (hyst_f) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const float x = gain_f * f_in[c];
+            const float xi = P.ft.decay * s.xv[c] + (x - s.pv[c]);
+            o.xv[c] = xi;
+            o.pv[c] = x;
+            o.hx[c] = x + P.ft.beta * xi;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            o.xv[c] = s.xv[c];
+            o.pv[c] = s.pv[c];
+            o.hx[c] = gain_f * f_in[c];
+        }
+    }
+    o.drift_d = s.drift_d;
+    if (P.depth.sigma_rw != 0.0f || P.depth.sigma_white != 0.0f) {
+        uint4 w = draw_rk(P.rk, gid, step, TAG_SCALAR);
+        float2 z = box_muller(w.x, w.y);
+        float dr = 0.0f;
+        if (walk_d) {
+            dr = s.drift_d + P.depth.sigma_rw * z.x;
+            o.drift_d = dr;
+        }
+        xd = xd + P.depth.bias + P.depth.sigma_white * z.y + dr;
+    } else {
+        xd += P.depth.bias;
+    }
+    xd = quantise(P.depth, xd);
+    if (dead) xd = P.depth.stuck_lo + P.depth.stuck_span * u24(draw_rk(P.rk, gid, ep, TAG_STUCK).x);
+    o.xd = xd;
+    return o;
+}
+
 // Noise state of one active taxel after its clean reading (fc[.][i] and the
-// clean depth in ag[0][i]).  The state loads do not depend on the geometry,
-// and all of them are issued before the first store: the compiler cannot move
-// a load above a store to a pointer that may alias it, and every such barrier
-// would cost a further round trip to memory.
+// clean depth in ag[0][i]), from and to the state arrays in HBM.  The state
+// loads do not depend on the geometry, and all of them are issued before
+// the first store: the compiler cannot move a load above a store to a
+// pointer that may alias it, and every such barrier would cost a further
+// round trip to memory.
 template <bool RADIUS, class Smem>
 __device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, int64_t g, uint32_t ep, uint32_t step,
                                             uint8_t bits) {
     const ParamsDev& P = a.P;
     const int64_t T = a.n_taxels;
-    const bool hyst_d = P.depth.beta != 0.0f, hyst_f = P.ft.beta != 0.0f, walk_d = P.depth.sigma_rw != 0.0f;
+    const bool hyst_d = hyst_depth_on(P), hyst_f = hyst_ft_on(P), walk_d = drift_depth_on(P);
     const float n0 = __ldcs(a.nx + g), n1 = __ldcs(a.ny + g), n2 = __ldcs(a.nz + g);
-    float prev_d = 0.0f, xi_d = 0.0f, drift_d = 0.0f, pv[6], xv[6];
+    NoiseIn s;
+    s.prev_d = s.xi_d = s.drift_d = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) s.pv[c] = s.xv[c] = 0.0f;
     if (hyst_d) {
-        prev_d = __ldcs(a.hyst_prev + g);
-        xi_d = __ldcs(a.hyst_xi + g);
+        s.prev_d = __ldcs(a.hyst_prev + g);
+        s.xi_d = __ldcs(a.hyst_xi + g);
     }
     if (hyst_f) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            pv[c] = __ldcs(a.hyst_prev + (1 + c) * T + g);
-            xv[c] = __ldcs(a.hyst_xi + (1 + c) * T + g);
+            s.pv[c] = __ldcs(a.hyst_prev + (1 + c) * T + g);
+            s.xv[c] = __ldcs(a.hyst_xi + (1 + c) * T + g);
         }
     }
-    if (walk_d) drift_d = __ldcs(a.drift + g);
-    const uint64_t gid = (uint64_t)(a.gid0 + g);
-    const bool dead = bits & BIT_DEAD;
+    if (walk_d) s.drift_d = __ldcs(a.drift + g);
     const float d = S.ag[0][i];
     // the depth and force the noisy chain starts from: the clean ones, or with
     // probe-radius noise those of the perturbed radius (refined taxels; the
@@ -213,47 +318,24 @@ __device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, i
 #pragma unroll
         for (int c = 0; c < 6; ++c) f_in[c] = near ? S.hx[c][i] : 0.0f;
     }
-    uint4 wep = make_uint4(0, 0, 0, 0);
-    if (P.depth.gain_on | P.ft.gain_on) wep = draw_rk(P.rk, gid, ep, TAG_EPISODE);
-    const float gain_d = P.depth.gain_on ? P.depth.gain_lo + P.depth.gain_span * u24(wep.y) : 1.0f;
-    const float gain_f = P.ft.gain_on ? P.ft.gain_lo + P.ft.gain_span * u24(wep.z) : 1.0f;
-    float xd = gain_d * d_in;
+    const NoiseOut o = noise_core(P, (uint64_t)(a.gid0 + g), ep, step, bits, d_in, f_in, s);
     if (hyst_d) {
-        const float xi = P.depth.decay * xi_d + (xd - prev_d);
-        __stcs(a.hyst_xi + g, xi);
-        __stcs(a.hyst_prev + g, xd);
-        xd = xd + P.depth.beta * xi;
+        __stcs(a.hyst_xi + g, o.xi_d);
+        __stcs(a.hyst_prev + g, o.prev_d);
     }
     if (hyst_f) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            const float x = gain_f * f_in[c];
-            const float xi = P.ft.decay * xv[c] + (x - pv[c]);
-            __stcs(a.hyst_xi + (1 + c) * T + g, xi);
-            __stcs(a.hyst_prev + (1 + c) * T + g, x);
-            S.hx[c][i] = x + P.ft.beta * xi;
+            __stcs(a.hyst_xi + (1 + c) * T + g, o.xv[c]);
+            __stcs(a.hyst_prev + (1 + c) * T + g, o.pv[c]);
         }
-    } else {
+    }
 #pragma unroll
-        for (int c = 0; c < 6; ++c) S.hx[c][i] = gain_f * f_in[c];
-    }
-    if (P.depth.sigma_rw != 0.0f || P.depth.sigma_white != 0.0f) {
-        uint4 w = draw_rk(P.rk, gid, step, TAG_SCALAR);
-        float2 z = box_muller(w.x, w.y);
-        float dr = 0.0f;
-        if (walk_d) {
-            dr = drift_d + P.depth.sigma_rw * z.x;
-            __stcs(a.drift + g, dr);
-        }
-        xd = xd + P.depth.bias + P.depth.sigma_white * z.y + dr;
-    } else {
-        xd += P.depth.bias;
-    }
-    xd = quantise(P.depth, xd);
-    if (dead) xd = P.depth.stuck_lo + P.depth.stuck_span * u24(draw_rk(P.rk, gid, ep, TAG_STUCK).x);
-    __stcs(a.depth_noisy + g, xd);
+    for (int c = 0; c < 6; ++c) S.hx[c][i] = o.hx[c];
+    if (walk_d) __stcs(a.drift + g, o.drift_d);
+    __stcs(a.depth_noisy + g, o.xd);
     S.ag[0][i] = d * n0; S.ag[1][i] = d * n1; S.ag[2][i] = d * n2;
-    S.ag[3][i] = xd * n0; S.ag[4][i] = xd * n1; S.ag[5][i] = xd * n2;
+    S.ag[3][i] = o.xd * n0; S.ag[4][i] = o.xd * n1; S.ag[5][i] = o.xd * n2;
 }
 
 // Inactive filler: zero noisy depth and staged values.
@@ -264,6 +346,92 @@ __device__ __forceinline__ void noise_state_filler(const StepArgs& a, Smem& S, i
     for (int c = 0; c < 6; ++c) {
         S.hx[c][i] = 0.f;
         S.ag[c][i] = 0.f;
+    }
+}
+
+// 3x3 crosstalk (Eq. 31) of the six force/torque channels at taxel i,
+// lattice (r, cc) of a rows x cols lattice whose first taxel is `base` in
+// hx ([6][kItemCap]): z = (1 - chi) hx_i + chi sum_k w_k hx_k, without
+// branches: a neighbour off the lattice (no wrap) gets weight 0 and the
+// taxel's own index, so every tap is a plain shared-memory load.
+__device__ __forceinline__ void crosstalk(const ParamsDev& P, const float (*hx)[kItemCap], int i, int base, int r,
+                                          int cc, int rows, int cols, bool wrap, float* z) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) z[c] = hx[c][i];
+    if (P.chi == 0.0f) return;
+    const bool vu = r > 0, vd = r + 1 < rows;
+    int cl = cc - 1, cr = cc + 1;
+    bool vl = true, vr = true;
+    if (cl < 0) {
+        if (wrap) cl += cols;
+        else { vl = false; cl = cc; }
+    }
+    if (cr >= cols) {
+        if (wrap) cr -= cols;
+        else { vr = false; cr = cc; }
+    }
+    const int row_off[3] = {vu ? -cols : 0, 0, vd ? cols : 0};
+    const float row_w[3] = {vu ? 1.f : 0.f, 1.f, vd ? 1.f : 0.f};
+    const int col_idx[3] = {cl, cc, cr};
+    const float col_w[3] = {vl ? 1.f : 0.f, 1.f, vr ? 1.f : 0.f};
+    const int row0 = base + r * cols;
+    float conv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int di = 0; di < 3; ++di) {
+#pragma unroll
+        for (int dj = 0; dj < 3; ++dj) {
+            const float w = P.xt_w[di * 3 + dj] * (row_w[di] * col_w[dj]);
+            const int nb = row0 + row_off[di] + col_idx[dj];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) conv[c] = fmaf(w, hx[c][nb], conv[c]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) z[c] = (1.0f - P.chi) * z[c] + P.chi * conv[c];
+}
+
+// Noisy force/torque of an active taxel from its crosstalk output z: drift
+// and white noise, quantisation, dead override (Eqs. 25, 28).  dr holds the
+// drift state on entry and the new drift on return.  Pure.
+__device__ __forceinline__ void noisy_core(const ParamsDev& P, uint64_t gid, uint32_t ep, uint32_t step, uint8_t bits,
+                                           float* z, float* dr) {
+    const NoiseDev& G = P.ft;
+    if (G.sigma_rw != 0.0f || G.sigma_white != 0.0f) {
+        float nrm[12];
+        uint4 wa = draw_rk(P.rk, gid, step, TAG_FT_A);
+        uint4 wb = draw_rk(P.rk, gid, step, TAG_FT_B);
+        float2 p0 = box_muller(wa.x, wa.y), p1 = box_muller(wa.z, wa.w);
+        float2 p2 = box_muller(wb.x, wb.y);
+        nrm[0] = p0.x; nrm[1] = p0.y; nrm[2] = p1.x; nrm[3] = p1.y; nrm[4] = p2.x; nrm[5] = p2.y;
+        if (G.sigma_white != 0.0f) {
+            uint4 wc = draw_rk(P.rk, gid, step, TAG_FT_C);
+            float2 p3 = box_muller(wb.z, wb.w), p4 = box_muller(wc.x, wc.y), p5 = box_muller(wc.z, wc.w);
+            nrm[6] = p3.x; nrm[7] = p3.y; nrm[8] = p4.x; nrm[9] = p4.y; nrm[10] = p5.x; nrm[11] = p5.y;
+        } else {
+#pragma unroll
+            for (int c = 6; c < 12; ++c) nrm[c] = 0.0f;
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            float d = 0.0f;
+            if (G.sigma_rw != 0.0f) {
+                d = dr[c] + G.sigma_rw * nrm[c];
+                dr[c] = d;
+            }
+            z[c] = z[c] + G.bias + G.sigma_white * nrm[6 + c] + d;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) z[c] += G.bias;
+    }
+    const bool dead = bits & BIT_DEAD;
+    float stuck = 0.0f;
+    if (dead) stuck = G.stuck_lo + G.stuck_span * u24(draw_rk(P.rk, gid, ep, TAG_STUCK).y);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        float v = quantise(G, z[c]);
+        if (dead) v = stuck;
+        z[c] = v;
     }
 }
 
@@ -283,87 +451,22 @@ __device__ __forceinline__ void noisy_ft(const StepArgs& a, const Smem& S, Out o
         }
         return;
     }
-    const uint64_t gid = (uint64_t)(a.gid0 + g);
-    const NoiseDev& G = P.ft;
-    float dr_prev[6];
-    if (G.sigma_rw != 0.0f) {
+    float dr[6];
+    if (drift_ft_on(P)) {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) dr_prev[c] = __ldcs(a.drift + (1 + c) * T + g);
+        for (int c = 0; c < 6; ++c) dr[c] = __ldcs(a.drift + (1 + c) * T + g);
     }
     float z[6];
+    crosstalk(P, S.hx, i, base, r, cc, rows, cols, wrap, z);
+    noisy_core(P, (uint64_t)(a.gid0 + g), ep, step, bits, z, dr);
+    if (drift_ft_on(P)) {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) z[c] = S.hx[c][i];
-    if (P.chi != 0.0f) {
-        // 3x3 window without branches: a neighbour off the lattice (no wrap)
-        // gets weight 0 and the taxel's own index, so every tap is a plain
-        // shared-memory load
-        const bool vu = r > 0, vd = r + 1 < rows;
-        int cl = cc - 1, cr = cc + 1;
-        bool vl = true, vr = true;
-        if (cl < 0) {
-            if (wrap) cl += cols;
-            else { vl = false; cl = cc; }
-        }
-        if (cr >= cols) {
-            if (wrap) cr -= cols;
-            else { vr = false; cr = cc; }
-        }
-        const int row_off[3] = {vu ? -cols : 0, 0, vd ? cols : 0};
-        const float row_w[3] = {vu ? 1.f : 0.f, 1.f, vd ? 1.f : 0.f};
-        const int col_idx[3] = {cl, cc, cr};
-        const float col_w[3] = {vl ? 1.f : 0.f, 1.f, vr ? 1.f : 0.f};
-        const int row0 = base + r * cols;
-        float conv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int di = 0; di < 3; ++di) {
-#pragma unroll
-            for (int dj = 0; dj < 3; ++dj) {
-                const float w = P.xt_w[di * 3 + dj] * (row_w[di] * col_w[dj]);
-                const int nb = row0 + row_off[di] + col_idx[dj];
-#pragma unroll
-                for (int c = 0; c < 6; ++c) conv[c] = fmaf(w, S.hx[c][nb], conv[c]);
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < 6; ++c) z[c] = (1.0f - P.chi) * z[c] + P.chi * conv[c];
+        for (int c = 0; c < 6; ++c) __stcs(a.drift + (1 + c) * T + g, dr[c]);
     }
-    if (G.sigma_rw != 0.0f || G.sigma_white != 0.0f) {
-        float nrm[12];
-        uint4 wa = draw_rk(P.rk, gid, step, TAG_FT_A);
-        uint4 wb = draw_rk(P.rk, gid, step, TAG_FT_B);
-        float2 p0 = box_muller(wa.x, wa.y), p1 = box_muller(wa.z, wa.w);
-        float2 p2 = box_muller(wb.x, wb.y);
-        nrm[0] = p0.x; nrm[1] = p0.y; nrm[2] = p1.x; nrm[3] = p1.y; nrm[4] = p2.x; nrm[5] = p2.y;
-        if (G.sigma_white != 0.0f) {
-            uint4 wc = draw_rk(P.rk, gid, step, TAG_FT_C);
-            float2 p3 = box_muller(wb.z, wb.w), p4 = box_muller(wc.x, wc.y), p5 = box_muller(wc.z, wc.w);
-            nrm[6] = p3.x; nrm[7] = p3.y; nrm[8] = p4.x; nrm[9] = p4.y; nrm[10] = p5.x; nrm[11] = p5.y;
-        } else {
-#pragma unroll
-            for (int c = 6; c < 12; ++c) nrm[c] = 0.0f;
-        }
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            float dr = 0.0f;
-            if (G.sigma_rw != 0.0f) {
-                dr = dr_prev[c] + G.sigma_rw * nrm[c];
-                __stcs(a.drift + (1 + c) * T + g, dr);
-            }
-            z[c] = z[c] + G.bias + G.sigma_white * nrm[6 + c] + dr;
-        }
-    } else {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) z[c] += G.bias;
-    }
-    const bool dead = bits & BIT_DEAD;
-    float stuck = 0.0f;
-    if (dead) stuck = G.stuck_lo + G.stuck_span * u24(draw_rk(P.rk, gid, ep, TAG_STUCK).y);
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-        float v = quantise(G, z[c]);
-        if (dead) v = stuck;
-        __stcs(a.ft_noisy + c * T + g, v);
-        out[c][i] = v;
+        __stcs(a.ft_noisy + c * T + g, z[c]);
+        out[c][i] = z[c];
     }
 }
 

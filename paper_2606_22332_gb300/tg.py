@@ -100,11 +100,15 @@ class StepInputs(C.Structure):
 
 
 class TuneCandidate(C.Structure):
-    _fields_ = [("persistent", C.c_int32), ("sorted", C.c_int32), ("ms_per_step", C.c_double)]
+    _fields_ = [("schedule", C.c_int32), ("sorted", C.c_int32), ("ms_per_step", C.c_double)]
 
 
 class TuneReport(C.Structure):
-    _fields_ = [("n", C.c_int32), ("chosen", C.c_int32), ("cand", TuneCandidate * 8)]
+    _fields_ = [("n", C.c_int32), ("chosen", C.c_int32), ("cand", TuneCandidate * 16)]
+
+
+# step-kernel schedules (tg_schedule), by name
+SCHEDULES = ("grid", "persistent", "pipe1024", "pipe768", "pipe512")
 
 
 _vp, _i32, _sz = C.c_void_p, C.c_int32, C.c_size_t
@@ -413,13 +417,15 @@ class Scene:
         _check(_lib.tg_object_info(self.h, int(i), C.byref(k), C.byref(e)), self.h)
         return int(k.value), float(e.value)
 
-    def set_schedule(self, persistent: bool, sorted: bool = True):
-        _check(_lib.tg_set_schedule(self.h, int(bool(persistent)), int(bool(sorted))), self.h)
+    def set_schedule(self, schedule="grid", sorted: bool = True):
+        """schedule: a name of SCHEDULES or its index."""
+        k = SCHEDULES.index(schedule) if isinstance(schedule, str) else int(schedule)
+        _check(_lib.tg_set_schedule(self.h, k, int(bool(sorted))), self.h)
 
     def schedule(self):
         p, s = _i32(), _i32()
         _check(_lib.tg_get_schedule(self.h, C.byref(p), C.byref(s)), self.h)
-        return {"persistent": int(p.value), "sorted": int(s.value)}
+        return {"schedule": SCHEDULES[int(p.value)], "sorted": int(s.value)}
 
     def autotune(self, inputs: dict, steps: int = 3, stream=None):
         """Time every step schedule on these inputs, keep the fastest; returns the report as a dict."""
@@ -427,7 +433,7 @@ class Scene:
         self._keep_inputs = keep
         R = TuneReport()
         _check(_lib.tg_autotune(self.h, C.byref(I), int(steps), C.byref(R), _stream(stream)), self.h)
-        cands = [{"persistent": R.cand[i].persistent, "sorted": R.cand[i].sorted,
+        cands = [{"schedule": SCHEDULES[R.cand[i].schedule], "sorted": R.cand[i].sorted,
                   "ms_per_step": R.cand[i].ms_per_step} for i in range(R.n)]
         return {"candidates": cands, "chosen": cands[R.chosen]}
 

@@ -40,7 +40,7 @@ def gpu_outputs(scene):
     }
 
 
-def compare_step(gpu, ora, ostate, params, wl, active=None, where="", tol=None, exclude=None):
+def compare_step(gpu, ora, ostate, params, wl, active=None, where="", tol=None, exclude=None, ambiguous=None):
     """Assert the CUDA step matches the oracle step; returns error statistics.
 
     tol overrides the bounds (keys d_abs, f_rel, f_abs, band, band_noisy,
@@ -53,9 +53,16 @@ def compare_step(gpu, ora, ostate, params, wl, active=None, where="", tol=None, 
     cell face); those taxels are returned in stats["outliers"], counted in
     stats["n_outliers"], and, like the taxels in `exclude` (earlier
     outliers, whose state carries the difference), enter their links' sums
-    with their own bound widened to the error they show.  No link is skipped."""
+    with their own bound widened to the error they show.  No link is skipped.
+    `ambiguous` marks taxels on a decision boundary of the method where the
+    two sides may legitimately take different branches (a learned SDF's
+    near-field switch, decided in FP32 on the GPU and FP64 here): they are
+    left out of every per-taxel check, counted in stats["ambiguous"], enter
+    their links' sums with the error they show, and the oracle adopts their
+    contact bits."""
     t = {"d_abs": D_ABS, "f_rel": F_REL, "f_abs": F_ABS, "band": BAND, "agg_d": 0.0, "f_outliers": 0.0}
     t.update(tol or {})
+    stats = {}
     R = wl.R
     T = len(R)
 
@@ -64,9 +71,10 @@ def compare_step(gpu, ora, ostate, params, wl, active=None, where="", tol=None, 
 
     D_ABS_, F_REL_, F_ABS_, BAND_ = (per_taxel(t[k]) for k in ("d_abs", "f_rel", "f_abs", "band"))
     AGG_D = per_taxel(t["agg_d"])
+    amb = np.zeros(T, bool) if ambiguous is None else np.asarray(ambiguous, bool)
+    stats["ambiguous"] = int(amb.sum()) if ambiguous is not None else 0
     act = R > 0 if active is None else active
     n_act = int(act.sum())
-    stats = {}
     # dead masks: bit-exact
     assert np.array_equal((gpu["flags"] >> 1) & 1, (ostate["flags"] >> 1) & 1), f"{where}: dead masks differ"
     # contact bits, with the threshold band
@@ -77,24 +85,39 @@ def compare_step(gpu, ora, ostate, params, wl, active=None, where="", tol=None, 
     bn = per_taxel(t.get("band_noisy", t["band"]))
     band_n = (np.abs(d_or - params["eta_on"]) < bn) | (np.abs(d_or - params["eta_off"]) < bn)
     for k, b in (("contact_clean", band), ("contact_noisy", band_n)):
-        bad = (gpu[k] != ora[k]) & ~b
-        assert not bad.any(), f"{where}: {k} differs at {np.flatnonzero(bad)[:10]}"
-    nb = int(((gpu["contact_clean"] != ora["contact_clean"]) & band).sum())
-    assert nb <= max(1, 1e-4 * n_act), f"{where}: {nb} banded contact mismatches"
+        bad = (gpu[k] != ora[k]) & ~b & ~amb
+        if bad.any():
+            i = np.flatnonzero(bad)[:5]
+            raise AssertionError(f"{where}: {k} differs at {i}: gpu {gpu[k][i]} oracle {ora[k][i]} oracle depth "
+                                 f"{d_or[i]} gpu depth {gpu['depth_clean'][i]} band {BAND_[i]} "
+                                 f"oracle flags {ostate['flags'][i]} gpu flags {gpu['flags'][i]}")
+    mis = (gpu["contact_clean"] != ora["contact_clean"]) & band & ~amb
+    nb = int(mis.sum())
+    # the 1e-4 share applies to the plain bound's band; a wider stated band
+    # (a learned SDF's) tolerates its mismatches and counts them
+    nb_plain = int((mis & (BAND_ <= BAND)).sum())
+    assert nb_plain <= max(1, 1e-4 * n_act), f"{where}: {nb_plain} banded contact mismatches"
     stats["banded"] = nb
+    # the oracle adopts the GPU's contact bits where they differ inside the
+    # band, so both sides' Schmitt states stay in step (the next step decides
+    # from the previous bit)
+    for bit, k, b in ((1, "contact_clean", band), (4, "contact_noisy", band_n)):
+        sync = (gpu[k] != ora[k]) & (b | amb)
+        if sync.any():
+            ostate["flags"][sync] = (ostate["flags"][sync] & ~np.uint8(bit)) | (gpu["flags"][sync] & np.uint8(bit))
     # depth
     for k in ("depth_clean", "depth_noisy"):
-        err = np.abs(gpu[k].astype(np.float64) - ora[k])
+        err = np.where(amb, 0.0, np.abs(gpu[k].astype(np.float64) - ora[k]))
         stats[k] = float(err.max()) if err.size else 0.0
         over = err > D_ABS_
         assert not over.any(), f"{where}: {k} err {err[over].max():.3e} > bound at {np.flatnonzero(over)[:5]}"
     if gpu.get("dist") is not None:
-        err = np.abs(gpu["dist"].astype(np.float64) - ora["dist"])
+        err = np.where(amb, 0.0, np.abs(gpu["dist"].astype(np.float64) - ora["dist"]))
         stats["dist"] = float(err.max()) if err.size else 0.0
         over = err > D_ABS_
         assert not over.any(), f"{where}: dist err {err[over].max():.3e} > bound"
     # force/torque, per 3-vector
-    skip = np.zeros(T, bool) if exclude is None else exclude.copy()
+    skip = (np.zeros(T, bool) if exclude is None else exclude.copy()) | amb
     bad = np.zeros(T, bool)
     bound = {}  # per (readout, part): each taxel's share of its link-sum bound
     for k in ("ft_clean", "ft_noisy"):
@@ -141,11 +164,22 @@ def compare_step(gpu, ora, ostate, params, wl, active=None, where="", tol=None, 
                     worst = max(worst, err / tol)
                     assert err <= tol, f"{where}: link sum env {e} link {l} col {col}: {ls_g[rec, col]} vs {ls_o[rec, col]}"
             for col, dsrc in ((12, "depth_clean"), (15, "depth_noisy")):
+                # an ambiguous taxel adds the depth difference it shows
+                d_amb = np.abs(gpu[dsrc][sl].astype(np.float64) - ora[dsrc][sl])[amb[sl]].sum()
                 for j in range(3):
-                    tol = 1e4 * (AGG_D[sl].sum() + (np.maximum(1e-4, F_REL_[sl]) * np.abs(ora[dsrc][sl])).sum()) \
-                        + F_ABS_[sl].sum()
+                    tol = 1e4 * (AGG_D[sl].sum() + (np.maximum(1e-4, F_REL_[sl]) * np.abs(ora[dsrc][sl])).sum()
+                                 + d_amb) + F_ABS_[sl].sum()
                     err = abs(ls_g[rec, col + j] - ls_o[rec, col + j])
                     assert err <= tol, f"{where}: agg_force env {e} link {l}: {ls_g[rec, col + j]} vs {ls_o[rec, col + j]}"
     stats["link_sums"] = worst
-    assert np.array_equal(gpu["link_counts"], ora["link_counts"]) or nb > 0, f"{where}: link contact counts differ"
+    # contact counts: equal on every link without a banded or ambiguous taxel
+    if nb == 0:
+        link_amb = np.zeros(wl.n_envs * L, bool)
+        t0 = 0
+        for rec in range(wl.n_envs * L):
+            nl = int(wl.link_rows[rec] * wl.link_cols[rec])
+            link_amb[rec] = amb[t0:t0 + nl].any()
+            t0 += nl
+        diff = np.any(gpu["link_counts"] != ora["link_counts"], axis=1) & ~link_amb
+        assert not diff.any(), f"{where}: link contact counts differ at links {np.flatnonzero(diff)[:5]}"
     return stats

@@ -46,6 +46,33 @@ def oracle_scene(wl: W.Workload):
     return oracle.OracleScene(wl.geom(), oracle_objects(wl.objects, wl.params), wl.params)
 
 
+def neural_switch_band(wl, used, band=1e-6):
+    """Taxels of the envs whose object answers through its network that lie
+    within `band` of the switch between network and fallback grid (the grid's
+    s phi = R + 1 mm, reading R30): the GPU decides that switch on its FP32
+    grid distance, the oracle on its FP64 one, so there either field may
+    answer.  A grid-only oracle scene (each such object replaced by its
+    fallback grid) gives the grid's distance at every taxel; its state is
+    not used.  Returns a function of the step's inputs."""
+    objs = []
+    for k, o in enumerate(wl.objects):
+        if o.kind == "neural":
+            o = W.ObjectSpec(kind="grid", dims=o.dims, lo=o.lo, hi=o.hi, fp16=o.fp16, values=o.values)
+        objs.append(o)
+    sub = W.Workload(**{f: getattr(wl, f) for f in wl.__dataclass_fields__})
+    sub.objects = objs
+    grid_scene = oracle_scene(sub)
+    st = grid_scene.new_state()
+    grid_scene.reset(st, 0)
+    in_net = np.repeat(np.isin(wl.obj_id, list(used)), np.diff(wl.taxel_offsets)) & (wl.R > 0)
+
+    def at(inputs):
+        out = grid_scene.step(st, inputs)
+        return in_net & (np.abs(out["dist"] - 1e-3) < band)
+
+    return at
+
+
 def pad_workload(depths, rows, cols, params=None, wrap=0, pitch=1e-3, obj=None,
                  link_vel=(0, 0, 0, 0, 0, 0), obj_vel=(0, 0, 0, 0, 0, 0), R=1e-3, link_quat=(1, 0, 0, 0)):
     """One env, one flat pad link over the half-space z <= 0.

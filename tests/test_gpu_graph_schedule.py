@@ -30,6 +30,16 @@ def _grid_workload(n_envs=20, steps=4):
     return wl
 
 
+def _uneven_workload(n_envs=14, steps=3):
+    """Uneven envs (200-1,000 taxels over 10-20 links, lattices padded with
+    fillers) on FP16 grids: items of several lattices, ragged lengths."""
+    rng = np.random.default_rng(31)
+    objs = bake_objects_oracle(W.config1_objects(rng, 3, n_grid=24, fp16=True, faces=(800, 1200)))
+    lat = W.uneven_lattices(rng, n_envs)
+    return W._assemble("uneven", rng, objs, rng.integers(0, 3, n_envs), lat, W.default_params(77), steps=steps,
+                       max_links=20, arc=W.PAD_ARC)
+
+
 def _device_inputs(wl, step):
     inp = wl.inputs(step)
     out = dict(pose_dt=inp["pose_dt"], step=inp["step"])
@@ -77,30 +87,39 @@ def test_env_params_with_domain_randomisation_is_rejected(tg):
     sc.close()
 
 
-@pytest.mark.parametrize("persistent,sorted_", [(0, 1), (1, 1), (1, 0), (0, 0)])
-def test_schedules_give_identical_results(tg, persistent, sorted_):
-    wl = _grid_workload(30, 3)
-    ref = tg.Scene.from_workload(wl)
+SCHEDULES = ("grid", "persistent", "pipe1024", "pipe768", "pipe512")
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES)
+@pytest.mark.parametrize("sorted_", [1, 0])
+@pytest.mark.parametrize("uneven", [0, 1])
+def test_schedules_give_identical_results(tg, schedule, sorted_, uneven):
+    """Every schedule and item order gives the grid schedule's outputs bit for
+    bit, with the surface-distance output on: envs of one lattice (1,000
+    taxels, 20 links) and uneven envs (items of several lattices, fillers)."""
+    wl = _uneven_workload() if uneven else _grid_workload(30, 3)
+    ref = tg.Scene.from_workload(wl, sensors=tg.TG_SENSOR_DIST)
     ref.upload_objects(wl.objects)
-    ref.set_schedule(persistent=False, sorted=True)
-    sc = tg.Scene.from_workload(wl)
+    ref.set_schedule("grid", sorted=True)
+    sc = tg.Scene.from_workload(wl, sensors=tg.TG_SENSOR_DIST)
     sc.upload_objects(wl.objects)
-    sc.set_schedule(persistent=bool(persistent), sorted=bool(sorted_))
-    assert sc.schedule() == {"persistent": persistent, "sorted": sorted_}
+    sc.set_schedule(schedule, sorted=bool(sorted_))
+    assert sc.schedule() == {"schedule": schedule, "sorted": sorted_}
     for s in range(3):
         ref.step(wl.inputs(s))
         sc.step(wl.inputs(s))
         for a, b in zip(_all_channels(tg, ref), _all_channels(tg, sc)):
             assert np.array_equal(a.view(np.uint8), b.view(np.uint8))
+        ref.sync(); sc.sync()
     ref.close(); sc.close()
 
 
-@pytest.mark.parametrize("persistent", [0, 1])
-def test_graph_replay_matches_oracle_and_seek(tg, persistent):
+@pytest.mark.parametrize("schedule", ["grid", "persistent", "pipe1024"])
+def test_graph_replay_matches_oracle_and_seek(tg, schedule):
     wl = _grid_workload(16, 6)
     sc = tg.Scene.from_workload(wl, sensors=tg.TG_SENSOR_DIST)
     sc.upload_objects(wl.objects)
-    sc.set_schedule(persistent=bool(persistent), sorted=True)
+    sc.set_schedule(schedule, sorted=True)
     dev = _device_inputs(wl, 0)
     sc.graph_capture(dev, pose_dt_per_step=wl.params["dt"])
     osc = oracle_scene(wl)
@@ -120,7 +139,7 @@ def test_graph_replay_matches_oracle_and_seek(tg, persistent):
     sc.sync()
     compare_step(g, o, ost, wl.params, wl, where="graph after seek")
     with pytest.raises(tg.TGError):
-        sc.set_schedule(persistent=False)  # fixed while a graph is held
+        sc.set_schedule("grid")  # fixed while a graph is held
     sc.graph_release()
     with pytest.raises(tg.TGError):
         sc.graph_launch(1)
@@ -147,11 +166,12 @@ def test_autotune_restores_state_and_keeps_parity(tg):
         osc.step(ost, wl.inputs(s))
     before = sc.save_state()
     rep = sc.autotune(wl.inputs(2), steps=2)
-    assert len(rep["candidates"]) == 4
+    assert len(rep["candidates"]) == 2 * len(SCHEDULES)
+    assert {c["schedule"] for c in rep["candidates"]} == set(SCHEDULES)
     assert all(c["ms_per_step"] > 0 for c in rep["candidates"])
     assert sc.save_state() == before
     chosen = sc.schedule()
-    assert chosen == {"persistent": rep["chosen"]["persistent"], "sorted": rep["chosen"]["sorted"]}
+    assert chosen == {"schedule": rep["chosen"]["schedule"], "sorted": rep["chosen"]["sorted"]}
     for s in range(2, 5):
         sc.step(wl.inputs(s))
         g = gpu_outputs(sc)
@@ -185,14 +205,15 @@ def test_object_sort_beyond_the_cached_item_count_is_bit_identical(tg):
     wl.objects = bake_objects_oracle(wl.objects)
     assert wl.n_envs * 2 + 4 * 4 > 160 * 1024
     outs = []
-    for sorted_ in (False, True):
+    for schedule, sorted_ in (("grid", False), ("grid", True), ("pipe1024", True)):
         sc = tg.Scene.from_workload(wl)
         sc.upload_objects(wl.objects)
-        sc.set_schedule(persistent=False, sorted=sorted_)
+        sc.set_schedule(schedule, sorted=sorted_)
         for s in range(2):
             sc.step(wl.inputs(s))
         outs.append(_all_channels(tg, sc))
         sc.close()
     assert float((outs[0][1] > 0).mean()) > 0.01  # some taxels penetrate
-    for a, b in zip(*outs):
-        assert np.array_equal(a, b)
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            assert np.array_equal(a, b)

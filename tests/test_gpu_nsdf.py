@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 import oracle
 from paper_2606_22332_gb300 import workload as W
 from _compare import compare_step, gpu_outputs
-from _scenes import bake_objects_oracle, oracle_nsdf, oracle_scene
+from _scenes import bake_objects_oracle, neural_switch_band, oracle_nsdf, oracle_scene
 
 LO = np.array([-0.02, -0.025, -0.018], np.float32)
 HI = np.array([0.022, 0.02, 0.03], np.float32)
@@ -161,16 +161,20 @@ def test_scene_step_with_a_neural_object_matches_oracle(tg, rho):
     assert sc.object_info(0)[0] == tg.TG_OBJ_NEURAL and sc.object_info(1)[0] == tg.TG_OBJ_GRID
     osc = oracle_scene(wl)
     ost = osc.new_state(); osc.reset(ost, 0)
+    switch = neural_switch_band(wl, [0])
     pen = 0
     skip = np.zeros(wl.n_taxels, bool)
+    amb = np.zeros(wl.n_taxels, bool)
     for s in range(3):
         inp = wl.inputs(s)
         sc.step(inp)
         g = gpu_outputs(sc)
         sc.sync()
         o = osc.step(ost, inp)
-        st = compare_step(g, o, ost, wl.params, wl, where=f"neural step {s}", tol=tol, exclude=skip)
+        amb |= switch(inp)  # a taxel that was on the switch keeps its own state from then on
+        st = compare_step(g, o, ost, wl.params, wl, where=f"neural step {s}", tol=tol, exclude=skip, ambiguous=amb)
         skip |= st["outliers"]
+        assert st["ambiguous"] <= 1e-3 * (wl.R > 0).sum()
         envs = np.repeat(wl.obj_id, np.diff(wl.taxel_offsets)) == 0
         pen += int((o["depth_clean"][envs] > 0).sum())
     assert pen > 100, "the network must put taxels in contact for the test to exercise it"
@@ -285,16 +289,21 @@ def test_mixed_workload_neural_grid_fallback_dr_graph(tg):
     sc.graph_capture(_device_inputs(wl, 0), pose_dt_per_step=wl.params["dt"])
     osc = oracle_scene(wl)
     ost = osc.new_state(); osc.reset(ost, 0)
+    switch = neural_switch_band(wl, used)
     skip = np.zeros(wl.n_taxels, bool)
+    amb = np.zeros(wl.n_taxels, bool)
     for s in range(4):
         sc.graph_launch(1)
         g = gpu_outputs(sc)
         sc.sync()
         o = osc.step(ost, wl.inputs(s))
-        st = compare_step(g, o, ost, wl.params, wl, where=f"mixed replay {s}", tol=tol, exclude=skip)
+        amb |= switch(wl.inputs(s))
+        st = compare_step(g, o, ost, wl.params, wl, where=f"mixed replay {s}", tol=tol, exclude=skip, ambiguous=amb)
         assert not (st["outliers"] & ~nt).any(), "a grid-object taxel outside the plain bounds"
-        print(f"mixed replay {s}: {st['n_outliers']} learned-SDF outliers of {int((nt & (wl.R > 0)).sum())} "
-              f"learned-SDF taxels; worst link-sum ratio {st['link_sums']:.3f}")
+        assert st["ambiguous"] <= 1e-3 * (wl.R > 0).sum()
+        print(f"mixed replay {s}: {st['n_outliers']} learned-SDF outliers, {st['ambiguous']} taxels on the network/"
+              f"grid switch, of {int((nt & (wl.R > 0)).sum())} learned-SDF taxels; worst link-sum ratio "
+              f"{st['link_sums']:.3f}")
         skip |= st["outliers"]
     sc.graph_release()
     sc.close()
