@@ -306,8 +306,13 @@ typedef struct {
 } tg_step_inputs;
 
 /* One sensor step for every env: enqueued on `stream`, asynchronous.
-   Errors: TG_ERR_STATE (no objects), TG_ERR_INVALID_ARG (NULL input),
-   TG_ERR_CUDA (launch failure). */
+   Errors: TG_ERR_STATE (no objects), TG_ERR_INVALID_ARG (NULL input, or an
+   obj_id in host memory outside [0, n_objects): nothing runs; object
+   indices in device memory are clamped into that range by the kernels),
+   TG_ERR_CUDA (launch failure).  Non-finite signed distances (from a NaN or
+   infinite pose, say) are counted on the device: those taxels read as clear
+   of the surface, and the next tg_sync returns TG_ERR_NUMERIC with the count
+   and clears it. */
 tg_status tg_step_sensors(tg_scene* scene, const tg_step_inputs* in, tg_stream stream);
 
 /* Step replay through a CUDA graph (one vectorised launch sequence per step,

@@ -1045,6 +1045,13 @@ tg_status tg_step_sensors(tg_scene* s, const tg_step_inputs* in, tg_stream strea
     if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
     if (const char* m = check_inputs(s, in)) return fail(s, TG_ERR_INVALID_ARG, m);
     if (s->n_objects < 1) return fail(s, TG_ERR_STATE, "tg_upload_objects must come before tg_step_sensors");
+    // object indices passed in host memory are checked here, before anything
+    // runs (device-resident indices are clamped by the kernels)
+    if (!is_device_ptr(in->obj_id))
+        for (int e = 0; e < s->E; ++e)
+            if (in->obj_id[e] < 0 || in->obj_id[e] >= s->n_objects)
+                return fail(s, TG_ERR_INVALID_ARG, "obj_id[" + std::to_string(e) + "] = " +
+                                                       std::to_string(in->obj_id[e]) + " is not an uploaded object");
     return enqueue_step(s, in, (cudaStream_t)stream, false);
 }
 

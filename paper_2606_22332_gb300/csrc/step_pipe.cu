@@ -251,6 +251,10 @@ __global__ void __launch_bounds__(NT, 1) step_pipe_kernel(const StepArgs a) {
         S.nc = 0;
         S.abort = 0;
         for (int q = 0; q < 2; ++q) S.lead[q] = Lead{};  // channels a parameter set leaves off read index 0
+    }
+    // no thread may poll a barrier before it is initialised
+    __syncthreads();
+    if (tid == 0) {
         S.slot[0] = a.slots[p0];
         if (p0 + G < n_items) S.slot[1] = a.slots[p0 + G];
         if (p0 + 2 * G < n_items) fetch_slot(a, S, 2, p0 + 2 * G);
@@ -275,8 +279,10 @@ __global__ void __launch_bounds__(NT, 1) step_pipe_kernel(const StepArgs a) {
         const ItemMeta& M = Gb.meta;
         const ObjDev& obj = Gb.obj;
         const Lead& Ld = S.lead[b];
-        const int n = cur.n_taxels;
-        const int nl = M.nl;
+        // (both within their maxima by construction; the clamps keep every
+        // shared-memory index inside its array whatever the records hold)
+        const int n = min(max(cur.n_taxels, 0), kItemCap);
+        const int nl = min(max(M.nl, 1), kItemMaxLinks);
         const uint32_t ep = cur.episode;
         if (tid == 0) {
             wait_slots();  // the records of items k+1 and k+2 are in place

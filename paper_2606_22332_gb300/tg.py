@@ -462,8 +462,9 @@ class Scene:
         shape, dt = self._shape_dtype(ch)
         if out is None:
             out = np.empty(shape, dt)
-        _check(_lib.tg_read_taxels(self.h, ch, int(noisy), _ptr(out), self.channel_bytes(ch), _stream(stream)),
-               self.h)
+        # the destination's own size: the library rejects one that does not match the channel
+        nbytes = out.nbytes if isinstance(out, np.ndarray) else out.numel() * out.element_size()
+        _check(_lib.tg_read_taxels(self.h, ch, int(noisy), _ptr(out), int(nbytes), _stream(stream)), self.h)
         if isinstance(out, np.ndarray):
             self.sync(stream)
         return out
