@@ -28,6 +28,7 @@ OR_SPHERE, OR_BOX, OR_PLANE, OR_MESH, OR_GRID, OR_NEURAL = 0, 1, 2, 3, 4, 5
 NSDF_LEVELS, NSDF_FEATURES, NSDF_TABLE, NSDF_HIDDEN = 16, 2, 1 << 16, 64
 NSDF_IN = NSDF_LEVELS * NSDF_FEATURES
 NCH = 8
+RING_CH = 8   # read-delay ring channels: depth, force/torque (6), noisy contact bit
 LINK_REC = 18
 
 
@@ -75,7 +76,7 @@ class ORParams(C.Structure):
         ("chi", C.c_double), ("xt_sigma", C.c_double),
         ("prox_rays", C.c_int32), ("prox_range", C.c_double), ("prox_cone", C.c_double),
         ("dr_on", C.c_int32), ("dr_mu", C.c_double * 2), ("dr_k", C.c_double * 2), ("dr_scale", C.c_double * 2),
-        ("rho", C.c_double),
+        ("rho", C.c_double), ("delay", C.c_int32), ("jitter", C.c_int32),
     ]
 
 
@@ -118,7 +119,7 @@ class ORInputs(C.Structure):
 
 class ORState(C.Structure):
     _fields_ = [("flags", C.c_void_p), ("hyst_prev", C.c_void_p), ("hyst_xi", C.c_void_p),
-                ("drift", C.c_void_p), ("episode", C.c_void_p)]
+                ("drift", C.c_void_p), ("episode", C.c_void_p), ("ring", C.c_void_p)]
 
 
 class OROutputs(C.Structure):
@@ -176,6 +177,8 @@ def lib():
             L.or_adam_step.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                        C.c_double, C.c_double, C.c_double, C.c_int32]
             L.or_dr_draw.argtypes = [C.POINTER(ORParams), C.c_uint32, C.c_uint32, C.c_void_p]
+            L.or_read_delay.argtypes = [C.POINTER(ORParams), C.c_uint32, C.c_uint32]
+            L.or_read_delay.restype = C.c_int32
             L.or_marker_kernel_g.argtypes = [C.c_double, C.c_double]
             L.or_marker_kernel_g.restype = C.c_double
             L.or_markers.argtypes = [C.POINTER(ORScene), C.POINTER(ORPads), C.POINTER(ORInputs), C.c_void_p,
@@ -421,6 +424,11 @@ def dr_draw(params: dict, env_gid: int, step: int):
     return out
 
 
+def read_delay(params: dict, env_gid: int, step: int) -> int:
+    """The read delay (steps) of one env at one step: delay + jitter draw."""
+    return int(lib().or_read_delay(C.byref(make_params(params)), C.c_uint32(env_gid), C.c_uint32(step)))
+
+
 def schmitt(prev, d, eta_on, eta_off):
     return lib().or_schmitt(int(prev), float(d), float(eta_on), float(eta_off))
 
@@ -458,6 +466,8 @@ def make_params(p: dict) -> ORParams:
     P.prox_range = float(p.get("prox_range", 0.05))
     P.prox_cone = float(p.get("prox_cone", np.radians(30.0)))
     P.rho = float(p.get("rho", 0.0))
+    P.delay = int(p.get("read_delay", 0))
+    P.jitter = int(p.get("read_jitter", 0))
     dr = p.get("dr")
     P.dr_on = 1 if dr else 0
     if dr:
@@ -518,16 +528,19 @@ class OracleScene:
 
     def new_state(self):
         T, E = self.T, self.n_envs
+        K = int(self.params.get("read_delay", 0)) + int(self.params.get("read_jitter", 0)) + 1
         return {
             "flags": np.zeros(T, np.uint8),
             "hyst_prev": np.zeros((NCH, T)), "hyst_xi": np.zeros((NCH, T)), "drift": np.zeros((NCH, T)),
             "episode": np.zeros(E, np.uint32),
+            "ring": np.zeros((K, RING_CH, T)) if K > 1 else None,
         }
 
     def _state(self, st):
         s = ORState()
         for k in ("flags", "hyst_prev", "hyst_xi", "drift", "episode"):
             setattr(s, k, _p(st[k]))
+        s.ring = _p(st.get("ring"))
         return s
 
     def reset(self, st, episode, env_mask=None):

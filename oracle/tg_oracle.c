@@ -74,7 +74,8 @@ enum {
     TAG_FT_C = 18,    /* normals: white fz tx ty tz */
     TAG_SCALAR = 19,  /* normals: drift depth, white depth, drift prox, white prox */
     TAG_RADIUS = 20,  /* w0: probe-radius noise */
-    TAG_DR = 32       /* per-env domain randomisation */
+    TAG_DR = 32,      /* per-env domain randomisation */
+    TAG_JITTER = 33   /* per-env read-delay jitter */
 };
 
 static void philox_draw(uint64_t seed, uint64_t gid, uint32_t word1, uint32_t tag, uint32_t out[4]) {
@@ -839,8 +840,22 @@ void or_reset(const or_scene* S, const uint8_t* env_mask, uint32_t episode, or_s
                 st->hyst_xi[(size_t)ch * T + i] = 0.0;
                 st->drift[(size_t)ch * T + i] = 0.0;
             }
+            if (st->ring) {
+                const int32_t K = S->params.delay + S->params.jitter + 1;
+                for (int32_t k = 0; k < K * OR_RING_CH; ++k) st->ring[(size_t)k * T + i] = 0.0;
+            }
         }
     }
+}
+
+/* The read delay of env e at this step: delay + j, j uniform on {0..jitter}
+   from the top 24 bits of Philox word 0 at (env id, step, TAG_JITTER), as an
+   integer product (exact on every side). */
+int32_t or_read_delay(const or_params* P, uint32_t env_gid, uint32_t step) {
+    if (P->jitter <= 0) return P->delay;
+    uint32_t w[4];
+    philox_draw(P->seed, env_gid, step, TAG_JITTER, w);
+    return P->delay + (int32_t)(((uint64_t)(w[0] >> 8) * (uint64_t)(P->jitter + 1)) >> 24);
 }
 
 /* one noise group applied to one channel value after the clean reading:
@@ -994,6 +1009,21 @@ static void env_step(const or_scene* S, const or_inputs* in, or_state* st, or_ou
             }
             for (int a = 0; a < 3; ++a) { fclean[jl * 6 + a] = fn[a]; fclean[jl * 6 + 3 + a] = taun[a]; }
             for (int a = 0; a < 3; ++a) { out->ft_clean[(size_t)a * T + j] = f[a]; out->ft_clean[(size_t)(3 + a) * T + j] = tau[a]; }
+            if (st->ring) {
+                /* read delay: this step's noisy-chain input goes into the
+                   ring, the chain reads the one from rd steps earlier (the
+                   reset state, 0, before the episode's first steps) */
+                const uint32_t K = (uint32_t)(P->delay + P->jitter + 1);
+                const uint32_t rd = (uint32_t)or_read_delay(P, (uint32_t)S->env_gid[e], in->step);
+                double* w_ = st->ring + (size_t)(in->step % K) * OR_RING_CH * T;
+                const double* r_ = st->ring + (size_t)((in->step % K + K - rd) % K) * OR_RING_CH * T;
+                w_[j] = dn;
+                for (int c = 0; c < 6; ++c) w_[(size_t)(1 + c) * T + j] = fclean[jl * 6 + c];
+                w_[(size_t)7 * T + j] = (double)(P->rho > 0.0 ? ((st->flags[j] >> 2) & 1) : y);
+                dn = r_[j];
+                for (int c = 0; c < 6; ++c) fclean[jl * 6 + c] = r_[(size_t)(1 + c) * T + j];
+                out->contact_noisy[j] = (uint8_t)(r_[(size_t)7 * T + j] != 0.0 && !dead);
+            }
 
             /* noise: per-probe gains for this episode */
             uint32_t we[4];

@@ -88,6 +88,11 @@ typedef struct {
        radius max(0, R + eps), eps uniform on [-rho, rho], drawn per taxel and
        step (the clean readout keeps R) */
     double rho;
+    /* read delay ("Base noise (every sensor)": the noisy readout is formed
+       from y_{t - Delta_read}): the taxel sensor's noisy chain (depth,
+       force/torque, noisy contact bit) reads its input from delay + j steps
+       earlier, j uniform on {0..jitter} per env and step (0, 0 = off) */
+    int32_t delay, jitter;
 } or_params;
 
 /* elastomer marker pads (ElastomerTaxel dilation, Eqs. 18-21) */
@@ -161,7 +166,13 @@ typedef struct {
     double* hyst_xi;    /* [OR_NCH][T] xi_{t-1} */
     double* drift;      /* [OR_NCH][T] d_{t-1} */
     uint32_t* episode;  /* [E] */
+    /* read-delay ring [delay + jitter + 1][OR_RING_CH][T] (NULL when the delay is off):
+       slot step mod (delay + jitter + 1) holds that step's noisy-chain input */
+    double* ring;
 } or_state;
+
+/* channels of the read-delay ring: 0 depth, 1..6 force/torque, 7 the noisy contact bit (0/1) */
+#define OR_RING_CH 8
 
 /* per-link record: F_clean(3) T_clean(3) F_noisy(3) T_noisy(3)
    agg_force_clean(3) agg_force_noisy(3) */
@@ -244,6 +255,7 @@ void or_nsdf_flip_bound_batch(const or_nsdf* n, int64_t B, const double* pts, do
 
 /* ---- whole-scene operations ------------------------------------------------- */
 void or_reset(const or_scene* S, const uint8_t* env_mask, uint32_t episode, or_state* st);
+int32_t or_read_delay(const or_params* P, uint32_t env_gid, uint32_t step);
 int or_step(const or_scene* S, const or_inputs* in, or_state* st, or_outputs* out, int32_t threads);
 /* marker displacements u [E][P][rows*cols][3] (pad frame: normal, tangent, normal x tangent) */
 void or_markers(const or_scene* S, const or_pads* pads, const or_inputs* in, double* u, double* h_out, int32_t threads);
