@@ -517,7 +517,8 @@ void or_bake_grid(const float* V, const int32_t* F, int32_t nf, const int32_t di
 /* The object frame may be scaled: phi_world(t) = s phi(q0 + t d) with d    */
 /* the world-unit ray direction mapped into the object frame (|d| = 1/s).   */
 /* grazing is set when the root is ill-posed: a crossing at a shallow      */
-/* angle (|d phi_world / dt| < 0.05) or a near miss (min phi_world < 2e-5). */
+/* angle (|d phi_world / dt| < 0.05), a near miss (min phi_world < 2e-5),  */
+/* or a skim (the ray leaves again before it is 2e-5 deep).                */
 /* ======================================================================== */
 #define OR_GRAZE_SLOPE 0.05
 #define OR_GRAZE_GAP 2e-5
@@ -732,24 +733,51 @@ static double mesh_first_root(const or_object* o, double scale, const double q0[
     return best;
 }
 
+/* the field a ray is traced through: the object's SDF (a learned SDF's
+   fallback grid), world units */
+static double ray_phi(const or_object* o, double scale, const double q0[3], const double d[3], double t) {
+    double p[3] = {q0[0] + t * d[0], q0[1] + t * d[1], q0[2] + t * d[2]}, g[3];
+    return scale * (o->kind == OR_NEURAL ? or_sdf_grid(o, p, g) : or_sdf_object(o, p, g));
+}
+
+/* A crossing after which the ray leaves the object again before it is
+   OR_GRAZE_GAP deep (it skims the surface) is as ill-posed for a marching
+   scheme as a near miss within OR_GRAZE_GAP: flag it.  Walks inside from the
+   root in steps of max(1 um, |phi| / 2), which cannot pass the exit. */
+static void flag_skim(const or_object* o, double scale, const double q0[3], const double d[3], double t,
+                      double tmax, int* grazing) {
+    double tt = t;
+    for (int m = 0; m < 2000; ++m) {
+        const double phi = ray_phi(o, scale, q0, d, tt);
+        if (m > 0 && phi > 0.0) break;           /* out again */
+        if (-phi >= OR_GRAZE_GAP) return;        /* a hit that goes deep */
+        tt += fmax(1e-6, 0.5 * fabs(phi));
+        if (tt > tmax) break;
+    }
+    *grazing = 1;
+}
+
 double or_ray_first_root(const or_object* o, double scale, const double q0[3], const double d[3], double tmax,
                          int* grazing) {
     double g[3];
     if (or_sdf_object(o, q0, g) <= 0.0) return 0.0;  /* the origin is inside: hit at once */
+    double t;
     switch (o->kind) {
-    case OR_SPHERE: return sphere_first_root(o->radius, scale, q0, d, tmax, grazing);
-    case OR_BOX: return box_first_root(o->half, scale, q0, d, tmax, grazing);
+    case OR_SPHERE: t = sphere_first_root(o->radius, scale, q0, d, tmax, grazing); break;
+    case OR_BOX: t = box_first_root(o->half, scale, q0, d, tmax, grazing); break;
     case OR_PLANE: {
         if (d[2] >= 0.0) return NAN;
-        double t = -q0[2] / d[2];
+        t = -q0[2] / d[2];
         if (fabs(scale * d[2]) < OR_GRAZE_SLOPE) *grazing = 1;
         return t <= tmax ? t : NAN;
     }
-    case OR_MESH: return mesh_first_root(o, scale, q0, d, tmax, grazing);
+    case OR_MESH: t = mesh_first_root(o, scale, q0, d, tmax, grazing); break;
     case OR_GRID:
-    case OR_NEURAL: return grid_first_root(o, scale, q0, d, tmax, grazing);  /* neural: its fallback grid */
+    case OR_NEURAL: t = grid_first_root(o, scale, q0, d, tmax, grazing); break;  /* neural: its fallback grid */
     default: return NAN;
     }
+    if (!isnan(t) && !*grazing) flag_skim(o, scale, q0, d, t, tmax, grazing);
+    return t;
 }
 
 /* ray directions of one probe in the link frame: ray 0 along the normal n,

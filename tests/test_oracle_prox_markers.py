@@ -222,3 +222,20 @@ def test_no_contact_no_displacement():
     wl, pads = _pad_scene(W.ObjectSpec(kind="plane"), 2e-3)
     u, h = oracle_scene(wl).markers(pads, wl.inputs(0))
     assert np.all(h == 0) and np.all(u == 0)
+
+
+def test_a_ray_that_skims_the_surface_is_grazing():
+    """A ray that enters a sphere but leaves it again before it is 20 um deep
+    is flagged like a near miss; one whose chord goes deeper is not.  The
+    sphere is small (r = 1 mm) so that both rays cross at slopes above the
+    shallow-angle limit (0.05), and only the depth decides."""
+    r = 1e-3
+    sph = oracle.Obj.sphere(r)
+    for depth, want in ((10e-6, True), (50e-6, False)):
+        b = r - depth                                  # distance of the ray from the centre
+        q0 = np.array([-5e-3, b, 0.0])
+        t, grazing = oracle.ray_first_root(sph, q0, np.array([1.0, 0.0, 0.0]), 0.05)
+        assert np.isclose(t, 5e-3 - np.sqrt(r * r - b * b))
+        slope = np.sqrt(1.0 - (b / r) ** 2)
+        assert slope > 0.05
+        assert grazing == want
