@@ -121,6 +121,19 @@ typedef struct {
        a, rho = pc_density / max(N, 1) and N the env object's point count.
        The object scale scales the points. */
     double pc_radius, pc_k, pc_ks, pc_density;
+    /* read delay (Appendix "Sensor Noise Model", base noise: the noisy
+       readout is formed from y_{t - Delta_read}, with optional uniform
+       jitter), in steps: the noisy depth, force/torque and contact bit of
+       step t are formed from the noisy chain's input (depth and force/torque
+       before gain, hysteresis and crosstalk, and the contact bit) of step
+       t - read_delay - j, j uniform on {0..read_jitter}, one draw per env and
+       step: Philox at counter (global env id, step, tag 33, 0), j = ((w0 >> 8)
+       (read_jitter + 1)) >> 24.  The noise draws, drift and dead override
+       stay those of step t; before an episode's first read_delay + j steps
+       the reset state (0) is read.  History is kept per step index, mod
+       read_delay + read_jitter + 1 (at most 64 together), in a ring of that
+       many slots x 8 channels per taxel.  0, 0 = off. */
+    int32_t read_delay, read_jitter;
 } tg_params;
 
 /* sensor mask bits (depth, contact and force/torque are always computed) */
@@ -381,7 +394,8 @@ typedef enum {
     TG_CH_FORCE_TORQUE = 3,   /* float [6][T]: fx fy fz tx ty tz, link frame */
     TG_CH_LINK_WRENCH = 4,    /* float [E*L][18]: F_clean T_clean F_noisy T_noisy agg_clean agg_noisy */
     TG_CH_LINK_COUNT = 5,     /* int32 [E*L][2]: contact count clean, noisy (agg_bool = count > 2) */
-    TG_CH_STATE_FLAGS = 6,    /* uint8 [T]: bit0 clean contact, bit1 dead, bit2 noisy contact */
+    TG_CH_STATE_FLAGS = 6,    /* uint8 [T]: bit0 clean contact, bit1 dead, bit2 noisy contact (its Schmitt
+                                 state); with a read delay, bit3 the reported (delayed) noisy contact */
     TG_CH_PROX = 7,           /* float [T] (needs TG_SENSOR_PROX) */
     TG_CH_MARKER = 8,         /* float [E*P*rows*cols][3] (needs TG_SENSOR_MARKERS); clean only */
     TG_CH_PC_FT = 9,          /* float [6][T]: point-cloud proximity force/torque, link frame (needs

@@ -65,6 +65,7 @@ struct tg_scene {
     int32_t* link_count = nullptr;
     unsigned* err = nullptr;
     float* link_rec = nullptr;
+    float* ring = nullptr;            // [ring_k][8][T] read-delay history (read delay on)
     // staging of host inputs
     float *s_link_pose = nullptr, *s_link_vel = nullptr, *s_obj_pose = nullptr, *s_obj_vel = nullptr;
     float* s_env_params = nullptr;
@@ -231,6 +232,11 @@ const char* make_params(const tg_params& p, ParamsDev* out) {
     d.pc_k = (float)p.pc_k;
     d.pc_ks = (float)p.pc_ks;
     d.pc_density = (float)p.pc_density;
+    if (p.read_delay < 0 || p.read_jitter < 0 || p.read_jitter > 255 || p.read_delay + p.read_jitter > 63)
+        return "read_delay >= 0 and read_jitter in 0..255 with read_delay + read_jitter <= 63";
+    d.delay = p.read_delay;
+    d.jitter = p.read_jitter;
+    d.ring_k = p.read_delay + p.read_jitter + 1;
     for (uint32_t r = 0; r < 10; ++r) {
         d.rk[2 * r] = (uint32_t)p.seed + r * 0x9E3779B9u;
         d.rk[2 * r + 1] = (uint32_t)(p.seed >> 32) + r * 0xBB67AE85u;
@@ -276,6 +282,8 @@ StepArgs step_args(tg_scene* s) {
     a.hyst_xi = s->hyst_xi;
     a.drift = s->drift;
     a.episode = s->episode;
+    a.ring = s->ring;
+    a.env_gid0 = s->env_gid0;
     a.depth_clean = s->depth_clean;
     a.depth_noisy = s->depth_noisy;
     a.dist = s->dist;
@@ -498,6 +506,11 @@ tg_status tg_create_scene(const tg_scene_desc* d, tg_scene** out) {
     CKC(dalloc(&s->hyst_xi, (size_t)8 * T + 16));
     CKC(dalloc(&s->drift, (size_t)8 * T + 16));
     CKC(dalloc(&s->episode, E));
+    if (P.ring_k > 1) {
+        const size_t nr = (size_t)P.ring_k * 8 * T + 16;
+        CKC(dalloc(&s->ring, nr));
+        CKC(cudaMemset(s->ring, 0, nr * sizeof(float)));
+    }
     CKC(dalloc(&s->depth_clean, T));
     CKC(dalloc(&s->depth_noisy, T));
     CKC(dalloc(&s->dist, (d->sensors & TG_SENSOR_DIST) ? T : 1));
@@ -659,7 +672,7 @@ void tg_destroy_scene(tg_scene* s) {
                     s->ft_noisy, s->link_out, s->link_count, s->err, s->link_rec, s->s_link_pose, s->s_link_vel,
                     s->s_obj_pose, s->s_obj_vel, s->s_env_params, s->s_obj_id, s->s_mask, s->s_contact,
                     s->items_sorted, s->metas, s->slots, s->prox_clean, s->prox_noisy, s->pad_link, s->pad_frame,
-                    s->marker_u, s->ctl, s->nq_phi, s->nq_grad, s->pc_ft, s->anchors, s->anchor_obj,
+                    s->marker_u, s->ctl, s->nq_phi, s->nq_grad, s->pc_ft, s->anchors, s->anchor_obj, s->ring,
                     s->n_anchored};
     for (void* p : ptrs) dfree(p);
     delete s;
@@ -1170,14 +1183,16 @@ tg_status tg_autotune(tg_scene* s, const tg_step_inputs* in, int32_t steps, tg_t
     const size_t T = (size_t)s->T, E = (size_t)s->E;
     // the noise state is put back afterwards: trials are not steps of the run
     uint8_t* keep = nullptr;
-    const size_t bytes = T + 3 * 8 * T * 4 + E * 4;
+    const size_t RB = s->ring ? (size_t)s->P.ring_k * 8 * T * 4 : 0;
+    const size_t bytes = T + 3 * 8 * T * 4 + E * 4 + RB;
     CK(s, cudaMalloc(&keep, bytes));
     auto save = [&](bool back) {
         struct { void* p; size_t n; } part[] = {{s->flags, T}, {s->hyst_prev, 8 * T * 4}, {s->hyst_xi, 8 * T * 4},
-                                                 {s->drift, 8 * T * 4}, {s->episode, E * 4}};
+                                                 {s->drift, 8 * T * 4}, {s->episode, E * 4}, {s->ring, RB}};
         size_t off = 0;
         cudaError_t e = cudaSuccess;
         for (auto& q : part) {
+            if (q.n == 0) continue;
             if (e == cudaSuccess)
                 e = back ? cudaMemcpyAsync(q.p, keep + off, q.n, cudaMemcpyDeviceToDevice, st)
                          : cudaMemcpyAsync(keep + off, q.p, q.n, cudaMemcpyDeviceToDevice, st);
@@ -1316,9 +1331,9 @@ tg_status tg_read_taxels(tg_scene* s, int32_t ch, int32_t noisy, void* dst, size
     cudaStream_t st = (cudaStream_t)stream;
     if (ch == TG_CH_CONTACT) {
         if (is_device_ptr(dst)) {
-            CK(s, launch_unpack_contact(s->flags, s->T, noisy, (uint8_t*)dst, st));
+            CK(s, launch_unpack_contact(s->flags, s->T, noisy ? (s->P.ring_k > 1 ? 3 : 2) : 0, (uint8_t*)dst, st));
         } else {
-            CK(s, launch_unpack_contact(s->flags, s->T, noisy, s->s_contact, st));
+            CK(s, launch_unpack_contact(s->flags, s->T, noisy ? (s->P.ring_k > 1 ? 3 : 2) : 0, s->s_contact, st));
             CK(s, cudaMemcpyAsync(dst, s->s_contact, need, cudaMemcpyDeviceToHost, st));
         }
         return TG_OK;
@@ -1362,7 +1377,8 @@ tg_status tg_save_state(tg_scene* s, void* buf, size_t* size) {
     if (!s || !size) return fail(s, TG_ERR_INVALID_ARG, "scene or size is NULL");
     const size_t T = (size_t)s->T, E = (size_t)s->E;
     const size_t A = shear_slots(s), EP = A ? E * s->markers.pads_per_env : 0;
-    const size_t need = 32 + T + 3 * 8 * T * 4 + E * 4 + A * 8 + EP * 4;
+    const size_t RB = s->ring ? (size_t)s->P.ring_k * 8 * T * 4 : 0;
+    const size_t need = 32 + T + 3 * 8 * T * 4 + E * 4 + A * 8 + EP * 4 + RB;
     if (!buf) { *size = need; return TG_OK; }
     if (*size != need) return fail(s, TG_ERR_INVALID_ARG, "state buffer size mismatch");
     CK(s, cudaDeviceSynchronize());
@@ -1377,8 +1393,9 @@ tg_status tg_save_state(tg_scene* s, void* buf, size_t* size) {
     CK(s, cudaMemcpy(p, s->episode, E * 4, cudaMemcpyDeviceToHost)); p += E * 4;
     if (A) {
         CK(s, cudaMemcpy(p, s->anchors, A * 8, cudaMemcpyDeviceToHost)); p += A * 8;
-        CK(s, cudaMemcpy(p, s->anchor_obj, EP * 4, cudaMemcpyDeviceToHost));
+        CK(s, cudaMemcpy(p, s->anchor_obj, EP * 4, cudaMemcpyDeviceToHost)); p += EP * 4;
     }
+    if (RB) CK(s, cudaMemcpy(p, s->ring, RB, cudaMemcpyDeviceToHost));
     return TG_OK;
 }
 
@@ -1386,7 +1403,8 @@ tg_status tg_load_state(tg_scene* s, const void* buf, size_t size) {
     if (!s || !buf) return fail(s, TG_ERR_INVALID_ARG, "scene or buf is NULL");
     const size_t T = (size_t)s->T, E = (size_t)s->E;
     const size_t A = shear_slots(s), EP = A ? E * s->markers.pads_per_env : 0;
-    const size_t need = 32 + T + 3 * 8 * T * 4 + E * 4 + A * 8 + EP * 4;
+    const size_t RB = s->ring ? (size_t)s->P.ring_k * 8 * T * 4 : 0;
+    const size_t need = 32 + T + 3 * 8 * T * 4 + E * 4 + A * 8 + EP * 4 + RB;
     if (size != need) return fail(s, TG_ERR_INVALID_ARG, "state buffer size mismatch");
     const unsigned char* p = (const unsigned char*)buf;
     uint64_t hdr[4];
@@ -1401,8 +1419,9 @@ tg_status tg_load_state(tg_scene* s, const void* buf, size_t size) {
     CK(s, cudaMemcpy(s->episode, p, E * 4, cudaMemcpyHostToDevice)); p += E * 4;
     if (A) {
         CK(s, cudaMemcpy(s->anchors, p, A * 8, cudaMemcpyHostToDevice)); p += A * 8;
-        CK(s, cudaMemcpy(s->anchor_obj, p, EP * 4, cudaMemcpyHostToDevice));
+        CK(s, cudaMemcpy(s->anchor_obj, p, EP * 4, cudaMemcpyHostToDevice)); p += EP * 4;
     }
+    if (RB) CK(s, cudaMemcpy(s->ring, p, RB, cudaMemcpyHostToDevice));
     return TG_OK;
 }
 

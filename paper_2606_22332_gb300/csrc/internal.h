@@ -58,6 +58,9 @@ struct ParamsDev {
     // per-step domain randomisation of (mu, k, scale)
     int dr_on;
     float dr_lo[3], dr_hi[3];
+    // read delay of the noisy readout (steps) with uniform jitter; ring_k =
+    // delay + jitter + 1 slots of history (1: off)
+    int delay, jitter, ring_k;
 };
 
 // Object table entry (object frame); its size is a multiple of 16 bytes so
@@ -170,6 +173,8 @@ struct StepArgs {
     float* hyst_xi;                   // [8][T]
     float* drift;                     // [8][T]
     const uint32_t* episode;          // [E]
+    float* ring;                      // [ring_k][8][T] read-delay history (ring_k > 1)
+    int64_t env_gid0;                 // global id of env 0 (per-env draws)
     // outputs
     float* depth_clean;
     float* depth_noisy;
@@ -271,7 +276,8 @@ cudaError_t launch_markers(const MarkerArgs& m, cudaStream_t s);
 // anchor_obj = -1 for the pads of the masked envs (all when mask is null)
 cudaError_t launch_shear_reset(int32_t* anchor_obj, int n_envs, int pads_per_env, const uint8_t* mask,
                                cudaStream_t s);
-cudaError_t launch_unpack_contact(const uint8_t* flags, int64_t n, int noisy, uint8_t* out, cudaStream_t s);
+// contact bit `bit` of every flag byte (0 clean, 2 noisy, 3 reported noisy with a read delay)
+cudaError_t launch_unpack_contact(const uint8_t* flags, int64_t n, int bit, uint8_t* out, cudaStream_t s);
 
 // learned SDF (nsdf.cu)
 struct NsdfNet {

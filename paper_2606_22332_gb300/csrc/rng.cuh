@@ -18,7 +18,8 @@ enum : uint32_t {
     TAG_FT_C = 18,    // normals: white fz tx ty tz
     TAG_SCALAR = 19,  // normals: drift depth, white depth, drift prox, white prox
     TAG_RADIUS = 20,  // w0: probe-radius noise
-    TAG_DR = 32       // per-env domain randomisation
+    TAG_DR = 32,      // per-env domain randomisation
+    TAG_JITTER = 33   // per-env read-delay jitter
 };
 
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {

@@ -41,6 +41,7 @@ struct SmemStep {
     int nq;
     unsigned int slot;                  // persistent schedule: the item being run
     uint32_t episode;                   // the env's episode counter
+    int rdelay;                         // read delay of the env at this step (steps)
     // when every link of the item has the same lattice (rows x cols, wrap)
     // and holds rows * cols taxels: that taxel count (else 0), the lattice,
     // and 1/count, 1/cols for the index arithmetic below
@@ -110,6 +111,7 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
     if (tid == 0) {
         S.nq = 0;
         S.episode = a.episode[e];
+        S.rdelay = a.P.ring_k > 1 ? read_delay(a.P, (uint64_t)(a.env_gid0 + e), step) : 0;
     }
     __syncthreads();
 
@@ -292,12 +294,13 @@ __global__ void reset_kernel(const StepArgs a, const uint8_t* env_mask, uint32_t
             a.hyst_xi[c * T + g] = 0.f;
             a.drift[c * T + g] = 0.f;
         }
+        for (int c = 0; a.P.ring_k > 1 && c < a.P.ring_k * 8; ++c) a.ring[c * T + g] = 0.f;
     }
 }
 
-__global__ void unpack_contact_kernel(const uint8_t* flags, int64_t n, int noisy, uint8_t* out) {
+__global__ void unpack_contact_kernel(const uint8_t* flags, int64_t n, int bit, uint8_t* out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = (flags[i] >> (noisy ? 2 : 0)) & 1u;
+    if (i < n) out[i] = (flags[i] >> bit) & 1u;
 }
 
 cudaError_t configure_step_kernels() {
@@ -467,9 +470,9 @@ cudaError_t launch_build_cells(const void* values, const int dims[3], int fp16, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_unpack_contact(const uint8_t* flags, int64_t n, int noisy, uint8_t* out, cudaStream_t s) {
+cudaError_t launch_unpack_contact(const uint8_t* flags, int64_t n, int bit, uint8_t* out, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    unpack_contact_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(flags, n, noisy, out);
+    unpack_contact_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(flags, n, bit, out);
     return cudaGetLastError();
 }
 

@@ -276,6 +276,50 @@ __device__ __forceinline__ NoiseOut noise_core(const ParamsDev& P, uint64_t gid,
     return o;
 }
 
+// Read delay (Appendix "Sensor Noise Model", base noise: the noisy readout is
+// formed from y_{t - Delta_read}, with optional uniform jitter) of the env
+// with global id env_gid at this step: delay + j, j uniform on {0..jitter}
+// from the top 24 bits of Philox word 0 at (env id, step, TAG_JITTER), as an
+// integer product.
+__device__ __forceinline__ int read_delay(const ParamsDev& P, uint64_t env_gid, uint32_t step) {
+    if (P.jitter <= 0) return P.delay;
+    const uint32_t w = draw_rk(P.rk, env_gid, step, TAG_JITTER).x;
+    return P.delay + (int)(((uint64_t)(w >> 8) * (uint64_t)(P.jitter + 1)) >> 24);
+}
+
+// The read delay's history ([ring_k][8][T]: slot, then channel 0 depth, 1-6
+// force/torque, 7 the noisy contact bit): this step's noisy-chain input goes
+// into slot step mod ring_k, and the input of `rd` steps earlier comes out
+// of its slot into d_in, f_in and the returned bit (with rd = 0, the values
+// just written).
+__device__ __forceinline__ bool ring_step(const ParamsDev& P, float* ring, int64_t T, int64_t g, uint32_t step,
+                                          int rd, float& d_in, float* f_in, bool bit) {
+    const uint32_t K = (uint32_t)P.ring_k;
+    const uint32_t ws = step % K, rs = (ws + K - (uint32_t)rd) % K;
+    float* w = ring + (size_t)ws * 8 * T + g;
+    w[0] = d_in;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) w[(1 + c) * T] = f_in[c];
+    w[7 * T] = bit ? 1.0f : 0.0f;
+    const float* r = ring + (size_t)rs * 8 * T + g;
+    d_in = r[0];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) f_in[c] = r[(1 + c) * T];
+    return r[7 * T] != 0.0f;
+}
+
+// With a read delay: the delayed noisy-chain input replaces (d_in, f_in),
+// the reported noisy contact (the delayed bit, then the dead override) goes
+// into flag bit 3 and replaces BIT_NOISY in the returned bits.
+__device__ __forceinline__ uint8_t delay_readout(const StepArgs& a, int64_t g, uint32_t step, int rd, uint8_t bits,
+                                                 float& d_in, float* f_in) {
+    const bool yn = bits & BIT_NOISY;
+    const bool rep = ring_step(a.P, a.ring, a.n_taxels, g, step, rd, d_in, f_in, yn) && !(bits & BIT_DEAD);
+    __stcs(a.flags + g, (uint8_t)(((bits & BIT_CLEAN) ? 1u : 0u) | ((bits & BIT_DEAD) ? 2u : 0u) | (yn ? 4u : 0u) |
+                                  (rep ? 8u : 0u)));
+    return (uint8_t)((bits & ~BIT_NOISY) | (rep ? BIT_NOISY : 0u));
+}
+
 // Noise state of one active taxel after its clean reading (fc[.][i] and the
 // clean depth in ag[0][i]), from and to the state arrays in HBM.  The state
 // loads do not depend on the geometry, and all of them are issued before
@@ -317,6 +361,10 @@ __device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, i
         d_in = near ? S.ag[1][i] : 0.0f;
 #pragma unroll
         for (int c = 0; c < 6; ++c) f_in[c] = near ? S.hx[c][i] : 0.0f;
+    }
+    if (P.ring_k > 1) {
+        bits = delay_readout(a, g, step, S.rdelay, bits, d_in, f_in);
+        S.bits[i] = bits;
     }
     const NoiseOut o = noise_core(P, (uint64_t)(a.gid0 + g), ep, step, bits, d_in, f_in, s);
     if (hyst_d) {

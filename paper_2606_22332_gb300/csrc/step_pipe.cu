@@ -73,6 +73,7 @@ struct alignas(16) SmemPipe {
     int16_t order[kItemCap];  // A1: near-contact taxels from the front, clear ones from the back
     uint64_t mbar_geo[2], mbar_hy, mbar_dr;
     int nq, nc, abort;
+    int rdelay;             // read delay of the item's env at this step (steps)
 };
 static_assert(sizeof(SmemPipe) <= 227 * 1024, "one CTA per SM");
 static_assert(kStride * 4 % 16 == 0 && kFlagStride % 16 == 0 && sizeof(Geo) % 16 == 0, "bulk copy alignment");
@@ -285,6 +286,7 @@ __global__ void __launch_bounds__(NT, 1) step_pipe_kernel(const StepArgs a) {
         const int nl = min(max(M.nl, 1), kItemMaxLinks);
         const uint32_t ep = cur.episode;
         if (tid == 0) {
+            S.rdelay = P.ring_k > 1 ? read_delay(P, (uint64_t)(a.env_gid0 + cur.env), step) : 0;
             wait_slots();  // the records of items k+1 and k+2 are in place
             // item k+3 into the entry of item k-1, which no thread reads any more
             if (pos + 3 * G < n_items) fetch_slot(a, S, (k + 3) & 3, pos + 3 * G);
@@ -380,6 +382,7 @@ __global__ void __launch_bounds__(NT, 1) step_pipe_kernel(const StepArgs a) {
                     s.pv[c] = hf ? S.hy[1 + c][Ld.hy[1 + c] + i] : 0.0f;
                     s.xv[c] = hf ? S.hy[8 + c][Ld.hy[8 + c] + i] : 0.0f;
                 }
+                if (P.ring_k > 1) bits = delay_readout(a, g, step, S.rdelay, bits, d_in, f_in);
                 const NoiseOut o = noise_core(P, (uint64_t)(a.gid0 + g), ep, step, bits, d_in, f_in, s);
                 if (hd) {
                     __stcs(a.hyst_xi + g, o.xi_d);

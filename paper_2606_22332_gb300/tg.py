@@ -53,7 +53,8 @@ class Params(C.Structure):
         ("prox_rays", C.c_int32), ("prox_range", C.c_double), ("prox_cone", C.c_double),
         ("dr_on", C.c_int32), ("dr_mu", C.c_double * 2), ("dr_k", C.c_double * 2), ("dr_scale", C.c_double * 2),
         ("nsdf_max_err_mm", C.c_double), ("probe_radius_noise", C.c_double),
-        ("pc_radius", C.c_double), ("pc_k", C.c_double), ("pc_ks", C.c_double), ("pc_density", C.c_double)]
+        ("pc_radius", C.c_double), ("pc_k", C.c_double), ("pc_ks", C.c_double), ("pc_density", C.c_double),
+        ("read_delay", C.c_int32), ("read_jitter", C.c_int32)]
 
 
 class PadDesc(C.Structure):
@@ -243,6 +244,8 @@ def _fill_params(params: dict) -> Params:
     P.pc_k = float(params.get("pc_k", 300.0))
     P.pc_ks = float(params.get("pc_ks", 10.0))
     P.pc_density = float(params.get("pc_density", 100.0))
+    P.read_delay = int(params.get("read_delay", 0))
+    P.read_jitter = int(params.get("read_jitter", 0))
     for g in ("depth", "ft", "prox"):
         grp = getattr(P, g)
         for k in NoiseGroup._fields_:
