@@ -477,9 +477,10 @@ tg_status tg_mesh_sdf(const float* verts, int32_t n_verts, const int32_t* faces,
    TG_NOALLOC_MAX_FACES faces, host pointers or bad sizes return
    TG_ERR_INVALID_ARG and run nothing.  The mesh is not read on the host, so
    an invalid face cannot be rejected there the way tg_mesh_sdf rejects it:
-   a face index outside [0, n_verts) (never read out of bounds) or a face
-   whose FP32 cross product is zero (zero area) makes every phi and grad
-   value of the call NaN.  The first call on each device looks up the
+   a face index outside [0, n_verts) (never read out of bounds), a face
+   with two equal indices, or a face whose FP32 cross product (each product
+   rounded on its own) is zero (zero area) makes every phi and grad value of
+   the call NaN.  The first call on each device looks up the
    array's device address once; make that first call before any stream
    capture.  Every call shares the array and clears what must start at zero
    (the invalid-face counter): calls whose GPU work overlaps (different

@@ -50,8 +50,9 @@ static cudaError_t noalloc_scratch(float** out) {
 
 // triangle list (vertices, then unit normals after kNoAllocMaxFaces * 9
 // floats) from the indexed mesh.  A face with an index outside [0, nv) (read
-// as a zero vertex, never out of bounds) or with a zero FP32 cross product
-// (zero area) is counted in *bad; the query's results are then set to NaN.
+// as a zero vertex, never out of bounds), with two equal indices, or with a
+// zero FP32 cross product (zero area) is counted in *bad; the query's
+// results are then set to NaN.
 __global__ void gather_triangles_kernel(const float* verts, int nv, const int32_t* faces, int nf, float* tri,
                                         float* tri_n, unsigned int* bad) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
@@ -71,8 +72,13 @@ __global__ void gather_triangles_kernel(const float* verts, int nv, const int32_
         for (int a = 0; a < 3; ++a) tri[(size_t)f * 9 + 3 * k + a] = p[k][a];
     const float3 u = f3(p[1][0] - p[0][0], p[1][1] - p[0][1], p[1][2] - p[0][2]);
     const float3 w = f3(p[2][0] - p[0][0], p[2][1] - p[0][1], p[2][2] - p[0][2]);
-    const float3 cr = cross(u, w);
-    if (!ok || !(dot(cr, cr) > 0.0f)) atomicAdd(bad, 1u);
+    // each product rounded on its own (no fused multiply-add), so that two
+    // equal edges give exactly zero
+    const float3 cr = f3(__fsub_rn(__fmul_rn(u.y, w.z), __fmul_rn(u.z, w.y)),
+                         __fsub_rn(__fmul_rn(u.z, w.x), __fmul_rn(u.x, w.z)),
+                         __fsub_rn(__fmul_rn(u.x, w.y), __fmul_rn(u.y, w.x)));
+    const int i0 = faces[3 * f], i1 = faces[3 * f + 1], i2 = faces[3 * f + 2];
+    if (!ok || i0 == i1 || i1 == i2 || i0 == i2 || !(dot(cr, cr) > 0.0f)) atomicAdd(bad, 1u);
     const float3 nrm = normalize_or(cr, f3(0.f, 0.f, 1.f));
     tri_n[(size_t)f * 3] = nrm.x;
     tri_n[(size_t)f * 3 + 1] = nrm.y;
