@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--shear-points", type=int, default=1000, help="tracked points per object for the shear anchors")
     ap.add_argument("--no-temperature", action="store_true", help="skip the TemperatureGrid line")
     ap.add_argument("--no-raycast", action="store_true", help="skip the raycast depth backend line")
+    ap.add_argument("--no-config2", action="store_true", help="skip the configuration-2 line")
+    ap.add_argument("--no-read-delay", action="store_true", help="skip the read-delay line")
+    ap.add_argument("--config2-steps", type=int, default=200, help="graph-replayed steps of the configuration-2 line")
     ap.add_argument("--clocks-csv", default=None,
                     help="where to keep the nvidia-smi clock samples of the timed region ({rank} is replaced; "
                          "default: a temporary file)")
@@ -256,17 +259,43 @@ def warm_then_rewind(sc, args, dt, stream=None):
     sc.graph_seek(0, 0.0, dt)
 
 
-def neural_line(args, wl, objs, d_in, dev, sched, stream, step_inputs, t_plain_ms):
-    """Learned SDFs for the first objects of the workload: trained on the GPU
-    (labels from the exact-mesh query), probed against it, then the same
-    workload timed with the networks answering the contact query (fallback
-    to the grid above 0.2 mm), and a subset of envs compared against the grid
+def neural_line(args, dev, stream, step_inputs):
+    """Configuration 3: learned SDFs for 64 procedural meshes of 5k-20k faces
+    (the headline's layout of envs, links and taxels, placed on these
+    objects), each trained on the GPU on 2M points labelled by the exact-mesh
+    query and probed against it; the workload is timed with the plain 96^3
+    FP16 grids and with the networks answering the contact query (fallback to
+    the grid above 0.2 mm), and a subset of envs is compared against the grid
     and the exact mesh."""
     import torch
     import paper_2606_22332_gb300.tg as tg
     from paper_2606_22332_gb300 import workload as W
 
+    wl = W.metric_run(seed=20260004, n_envs=args.envs, faces=(5000, 20000))
+    objs = []
+    for o in wl.objects:
+        vals = tg.bake_grid(o.verts, o.faces, o.dims, o.lo, o.hi, fp16=o.fp16)
+        objs.append(W.ObjectSpec(kind="grid", dims=o.dims, lo=o.lo, hi=o.hi, fp16=o.fp16, values=vals, name=o.name))
+    d_in = {k: torch.as_tensor(getattr(wl, k)).to(dev) for k in ("link_pose", "link_vel", "obj_pose", "obj_vel", "obj_id")}
     dt = wl.params["dt"]
+    # the plain grid path on this workload, in the schedule the autotuner picks for it
+    sc0 = tg.Scene(wl.geom(), wl.params)
+    sc0.upload_objects(objs)
+    sc0.step(step_inputs(0, d_in))
+    sched = sc0.autotune(step_inputs(0, d_in), steps=3)["chosen"]
+    sched = {"schedule": sched["schedule"], "sorted": bool(sched["sorted"])}
+    sc0.set_schedule(**sched)
+    sc0.graph_capture(step_inputs(0, d_in), pose_dt_per_step=dt)
+    warm_then_rewind(sc0, args, dt)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    sc0.graph_launch(args.steps)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    t_plain_ms = p0.elapsed_time(p1)
+    sc0.graph_release()
+    sc0.close()
     n_obj = min(args.neural_objects, len(wl.objects))
     t0 = time.time()
     nets, probe_stats = [], []
@@ -353,10 +382,116 @@ def neural_line(args, wl, objs, d_in, dev, sched, stream, step_inputs, t_plain_m
         "probe_err_mm": {"max_over_objects": float(pm[:, 0].max()), "median_of_max": float(np.median(pm[:, 0])),
                          "mean": float(pm[:, 1].mean()), "p99_median": float(np.median(pm[:, 2]))},
         "value": wl.n_active * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
-        "vs_plain_grid": round(t_plain_ms / ms, 4), "queries_answered_by_network_per_step": q_used,
+        "vs_plain_grid": round(t_plain_ms / ms, 4), "plain_grid_ms_per_step": t_plain_ms / args.steps,
+        "workload": f"configuration 3: {wl.n_envs} envs x {wl.max_links} links x 50 taxels on 64 meshes of "
+                    f"{min(len(o.faces) for o in wl.objects)}-{max(len(o.faces) for o in wl.objects)} faces "
+                    "(superquadrics and subdivided hulls), schedule " + f"{sched}",
+        "queries_answered_by_network_per_step": q_used,
         "step_kernels_ms": round((step_ms) / max(nsteps, 1), 4),
         "accuracy": acc,
     }
+
+
+READ_DELAY_RING_BYTES = 64.0  # per query: this step's noisy-chain input written (8 x 4 B), a delayed one read
+
+
+def read_delay_line(args, wl, objs, dev, stream, sched, peaks_fn):
+    """The headline workload with a read delay of 2 steps and a jitter of 1
+    (Sensor Noise Model, base noise): the same graph-replayed step with each
+    taxel's delayed-readout ring (8 channels x 4 slots) in HBM."""
+    import torch
+
+    import paper_2606_22332_gb300.tg as tg
+
+    dt = wl.params["dt"]
+    sc = tg.Scene(wl.geom(), dict(wl.params, read_delay=2, read_jitter=1))
+    sc.upload_objects(objs)
+    d_in = {k: torch.as_tensor(getattr(wl, k)).to(dev) for k in ("link_pose", "link_vel", "obj_pose", "obj_vel", "obj_id")}
+    sc.set_schedule(**sched)
+    sc.profile(True)
+    sc.graph_capture(dict(d_in, pose_dt=0.0, step=0), pose_dt_per_step=dt)
+    warm_then_rewind(sc, args, dt)
+    torch.cuda.synchronize()
+    sc.profile_read()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sc.graph_launch(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    pose_ms, step_ms, n = sc.profile_read()
+    sc.graph_release()
+    sc.close()
+    bpq = BYTES_PER_QUERY + READ_DELAY_RING_BYTES
+    step_avg = step_ms / max(n, 1)
+    achieved = bpq * wl.n_active / (step_avg * 1e-3) / 1e9
+    peak, kind = peaks_fn()
+    return {"sensors": "headline step with a read delay of 2 steps and a jitter of 1 step on the noisy readout",
+            "value": wl.n_active * args.steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "step_kernel_ms": round(step_avg, 4),
+            "step_kernel_roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                                     "frac": round(achieved / peak, 4), "peak_kind": kind,
+                                     "algorithmic_bytes_per_query": bpq},
+            "ring_bytes": 4 * 8 * 4 * wl.n_taxels, "gpu_launches": 4 * args.steps}
+
+
+def config2_line(args, dev, stream, pg, peaks_fn):
+    """Configuration 2 as stated: 20,480 envs with T_e ~ U{200..1000}
+    taxels over L_e ~ U{10..20} links, 64 objects as 96^3 FP16 grids baked
+    from the exact meshes, proximity (8 rays, 50 mm) and elastomer markers
+    (5 pads x 16 x 16) on, the full noise model, 200 graph-replayed steps of
+    a fresh episode (schedule picked by the autotuner for this workload)."""
+    import torch
+
+    import paper_2606_22332_gb300.tg as tg
+    from paper_2606_22332_gb300 import workload as W
+    from paper_2606_22332_gb300.dist import max_over_ranks
+
+    wl = W.config2(n_envs=args.envs)
+    objs = []
+    for o in wl.objects:
+        vals = tg.bake_grid(o.verts, o.faces, o.dims, o.lo, o.hi, fp16=o.fp16)
+        objs.append(W.ObjectSpec(kind="grid", dims=o.dims, lo=o.lo, hi=o.hi, fp16=o.fp16, values=vals, name=o.name))
+    sc = tg.Scene(wl.geom(), wl.params, sensors=tg.TG_SENSOR_PROX | tg.TG_SENSOR_MARKERS, pads=wl.pads)
+    sc.upload_objects(objs)
+    d_in = {k: torch.as_tensor(getattr(wl, k)).to(dev) for k in ("link_pose", "link_vel", "obj_pose", "obj_vel", "obj_id")}
+    dt = wl.params["dt"]
+    sc.step(dict(d_in, pose_dt=0.0, step=0))
+    tune = sc.autotune(dict(d_in, pose_dt=0.0, step=0), steps=3)
+    sc.profile(True)
+    sc.graph_capture(dict(d_in, pose_dt=0.0, step=0), pose_dt_per_step=dt)
+    warm_then_rewind(sc, args, dt)
+    torch.cuda.synchronize()
+    sc.profile_read()
+    steps = args.config2_steps
+    if pg:
+        pg.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sc.graph_launch(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), dev)
+    pose_ms, step_ms, n = sc.profile_read()
+    pen = float((sc.buffer(tg.CH_DEPTH) > 0).sum().item()) / max(wl.n_active, 1)
+    sc.graph_release()
+    sc.close()
+    n_q = wl.n_active
+    step_avg = step_ms / max(n, 1)
+    achieved = BYTES_PER_QUERY * n_q / (step_avg * 1e-3) / 1e9
+    peak, kind = peaks_fn()
+    return {"sensors": "configuration 2: uneven envs (200-1,000 taxels over 10-20 links), 64 objects as 96^3 FP16 "
+                       "grids, proximity (8 rays, 50 mm) and markers (5 pads x 16x16), full noise model",
+            "envs": wl.n_envs, "active_taxels": n_q, "steps": steps, "value": n_q * steps / (ms * 1e-3),
+            "unit": UNIT, "ms_per_step": ms / steps, "step_kernel_ms": round(step_avg, 4),
+            "step_kernel_roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                                     "frac": round(achieved / peak, 4), "peak_kind": kind,
+                                     "algorithmic_bytes_per_query": BYTES_PER_QUERY},
+            "penetrating_share_last_step": round(pen, 4), "placement": wl.meta.get("placement"),
+            "schedule": {"chosen": tune["chosen"], "candidates": tune["candidates"]},
+            # pose, [order], step, proximity, markers, step-counter advance
+            "gpu_launches": steps * (5 + (1 if tune["chosen"]["schedule"].startswith("pipe") or tune["chosen"]["sorted"]
+                                          else 0))}
 
 
 def peaks():
@@ -774,6 +909,12 @@ def run_tg(args):
                  "anchored_points_per_pad": round(n_anch / max(n_pads, 1), 2),
                  "anchor_state_bytes": n_pads * args.shear_points * 8,
                  "gpu_launches": (launches_per_step + 1) * args.steps}
+    delay = None
+    if not args.no_read_delay:
+        delay = read_delay_line(args, wl, objs, dev, stream, sched, peaks)
+    cfg2 = None
+    if not args.no_config2:
+        cfg2 = config2_line(args, dev, stream, pg, peaks)
     ray = None
     if not args.no_raycast and ws == 1:
         ray = raycast_line(args, wl, wl.objects, dev, stream)  # the meshes behind the baked grids
@@ -782,7 +923,7 @@ def run_tg(args):
         temp = temperature_line(args, dev, stream, pg, peaks)
     neural = None
     if args.neural_objects > 0 and ws == 1:
-        neural = neural_line(args, wl, objs, d_in, dev, sched, stream, step_inputs, t_max)
+        neural = neural_line(args, dev, stream, step_inputs)
     del objs
 
     peak, peak_kind = peaks()
@@ -816,6 +957,8 @@ def run_tg(args):
                               f"step_{args.steps - 1}": round(contact_share_last, 4)},
             "schedule": {"chosen": sched, "autotune": tune["candidates"], "replay": "CUDA graph per step"},
             "full_sensor_set": full,
+            "config2": cfg2,
+            "read_delay": delay,
             "point_cloud_proximity": pcl,
             "elastomer_shear": shear,
             "temperature_grid": temp,
