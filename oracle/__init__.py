@@ -76,7 +76,7 @@ class ORParams(C.Structure):
         ("chi", C.c_double), ("xt_sigma", C.c_double),
         ("prox_rays", C.c_int32), ("prox_range", C.c_double), ("prox_cone", C.c_double),
         ("dr_on", C.c_int32), ("dr_mu", C.c_double * 2), ("dr_k", C.c_double * 2), ("dr_scale", C.c_double * 2),
-        ("rho", C.c_double), ("delay", C.c_int32), ("jitter", C.c_int32),
+        ("rho", C.c_double), ("delay", C.c_int32), ("jitter", C.c_int32), ("depth_backend", C.c_int32),
     ]
 
 
@@ -127,7 +127,7 @@ class OROutputs(C.Structure):
                 ("prox_clean", C.c_void_p), ("prox_noisy", C.c_void_p), ("prox_grazing", C.c_void_p),
                 ("depth_clean", C.c_void_p), ("depth_noisy", C.c_void_p), ("dist", C.c_void_p),
                 ("ft_clean", C.c_void_p), ("ft_noisy", C.c_void_p),
-                ("link_sums", C.c_void_p), ("link_counts", C.c_void_p)]
+                ("link_sums", C.c_void_p), ("link_counts", C.c_void_p), ("depth_tie", C.c_void_p)]
 
 
 def lib():
@@ -468,6 +468,7 @@ def make_params(p: dict) -> ORParams:
     P.rho = float(p.get("rho", 0.0))
     P.delay = int(p.get("read_delay", 0))
     P.jitter = int(p.get("read_jitter", 0))
+    P.depth_backend = {"sdf": 0, "raycast": 1}[p.get("depth_backend", "sdf")]
     dr = p.get("dr")
     P.dr_on = 1 if dr else 0
     if dr:
@@ -567,6 +568,7 @@ class OracleScene:
             "depth_clean": np.zeros(T), "depth_noisy": np.zeros(T), "dist": np.zeros(T),
             "ft_clean": np.zeros((6, T)), "ft_noisy": np.zeros((6, T)),
             "link_sums": np.zeros((E * L, LINK_REC)), "link_counts": np.zeros((E * L, 2), np.int32),
+            "depth_tie": np.zeros(T, np.uint8),
         }
         O = OROutputs()
         for k in out:

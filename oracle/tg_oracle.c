@@ -363,6 +363,26 @@ double or_raycast_depth(const float* V, const int32_t* F, int32_t nf, double sca
     return best;
 }
 
+/* 1 when a triangle other than `face` whose normal is not parallel to n
+   penetrates within 1e-12 m of `pen` (an edge or a vertex shared by
+   non-coplanar faces is the deepest feature: either face's normal is the
+   backend's answer) */
+static int raycast_tie(const float* V, const int32_t* F, int32_t nf, double scale, const double q[3], double R,
+                       double pen, int32_t face, const double n[3]) {
+    for (int32_t f = 0; f < nf; ++f) {
+        if (f == face) continue;
+        double a[3], b[3], c[3], cp[3], e1[3], e2[3], m[3];
+        int reg;
+        vert(V, F[3 * f], a); vert(V, F[3 * f + 1], b); vert(V, F[3 * f + 2], c);
+        for (int i = 0; i < 3; ++i) { a[i] *= scale; b[i] *= scale; c[i] *= scale; }
+        if (R - or_closest_point_triangle(q, a, b, c, cp, &reg) < pen - 1e-12) continue;
+        sub3(b, a, e1); sub3(c, a, e2);
+        cross3(e1, e2, m);
+        if (fabs(dot3(m, n)) < (1.0 - 1e-9) * norm3(m)) return 1;
+    }
+    return 0;
+}
+
 /* generalised winding number: sum of signed solid angles / (4 pi) */
 double or_winding_number(const float* V, const int32_t* F, int32_t nf, const double p[3]) {
     double total = 0.0;
@@ -981,6 +1001,21 @@ static void env_step(const or_scene* S, const or_inputs* in, or_state* st, or_ou
                    fallback grid sees it; farther out the grid answers */
                 phi = scale * or_sdf_grid(obj, qh, go);
                 if (!(phi > R + OR_NEURAL_BAND)) phi = scale * or_sdf_object(obj, qh, go);
+            } else if (obj->kind == OR_MESH && P->depth_backend == 1) {
+                /* raycast backend: the deepest penetration over the
+                   triangles within R (object frame, world units), with that
+                   triangle's normal; phi = R - depth (R when none is near) */
+                double qo[3], nl_[3] = {S->nx[j], S->ny[j], S->nz[j]}, uw[3], uo[3], rpen;
+                int32_t face;
+                for (int a = 0; a < 3; ++a) qo[a] = qh[a] * scale;
+                matvec(RL, nl_, uw);
+                matTvec(RC, uw, uo);
+                const double pen = or_raycast_depth(obj->verts, obj->faces, obj->n_faces, scale, qo, uo, R, go, &face,
+                                                    &rpen);
+                phi = R - pen;
+                if (out->depth_tie)
+                    out->depth_tie[j] = (uint8_t)(face >= 0 && raycast_tie(obj->verts, obj->faces, obj->n_faces, scale,
+                                                                           qo, R, pen, face, go));
             } else {
                 phi = scale * or_sdf_object(obj, qh, go);
             }

@@ -93,6 +93,10 @@ typedef struct {
        force/torque, noisy contact bit) reads its input from delay + j steps
        earlier, j uniform on {0..jitter} per env and step (0, 0 = off) */
     int32_t delay, jitter;
+    /* contact-depth backend of mesh objects ("Two contact-depth backends"):
+       0 the signed distance (sdf), 1 raycast: depth = the deepest penetration
+       over the triangles within R of the probe, normal = that triangle's */
+    int32_t depth_backend;
 } or_params;
 
 /* elastomer marker pads (ElastomerTaxel dilation, Eqs. 18-21) */
@@ -187,6 +191,9 @@ typedef struct {
     double* ft_clean; double* ft_noisy;               /* [6][T] */
     double* link_sums;                                /* [E*L][OR_LINK_REC] */
     int32_t* link_counts;                             /* [E*L][2] clean, noisy */
+    uint8_t* depth_tie;                               /* [T] raycast backend: another triangle with a
+                                                         different normal is as deep (within 1e-12 m),
+                                                         so the normal is either's (NULL: not reported) */
 } or_outputs;
 
 /* ---- primitives (exported for the pins) ------------------------------------ */
