@@ -134,6 +134,15 @@ typedef struct {
        read_delay + read_jitter + 1 (at most 64 together), in a ring of that
        many slots x 8 channels per taxel.  0, 0 = off. */
     int32_t read_delay, read_jitter;
+    /* contact-depth backend of mesh objects (Appendix A, "Probe geometry and
+       contact-depth query", two contact-depth backends): 0 the signed
+       distance (sdf); 1 raycast: a taxel's depth is R minus the distance from
+       its probe centre to the nearest triangle within R (0 when none is; a
+       probe centre more than R inside the mesh is clear), its contact normal
+       that triangle's normal, found through a bounding volume hierarchy
+       built at tg_upload_objects.  Other object kinds keep their signed
+       distance.  Not combined with probe_radius_noise. */
+    int32_t depth_backend;
 } tg_params;
 
 /* sensor mask bits (depth, contact and force/torque are always computed) */

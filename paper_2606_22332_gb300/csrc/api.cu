@@ -89,6 +89,8 @@ struct tg_scene {
     bool any_neural = false;
     float* nq_phi = nullptr;          // [T]
     float* nq_grad = nullptr;         // [3][T]
+    float* nq_phi_lo = nullptr;       // [T] (raycast backend)
+    bool any_raycast = false;         // a mesh object answered by the raycast backend
     // schedule (tg_set_schedule / tg_autotune) and step control
     int schedule = TG_SCHED_GRID;     // step kernel schedule (tg_schedule)
     int sorted = 1;                   // object-sorted item order (several objects)
@@ -237,6 +239,10 @@ const char* make_params(const tg_params& p, ParamsDev* out) {
     d.delay = p.read_delay;
     d.jitter = p.read_jitter;
     d.ring_k = p.read_delay + p.read_jitter + 1;
+    if (p.depth_backend != 0 && p.depth_backend != 1) return "depth_backend must be 0 (sdf) or 1 (raycast)";
+    if (p.depth_backend == 1 && p.probe_radius_noise > 0.0)
+        return "probe-radius noise is not supported with the raycast depth backend";
+    d.depth_backend = p.depth_backend;
     for (uint32_t r = 0; r < 10; ++r) {
         d.rk[2 * r] = (uint32_t)p.seed + r * 0x9E3779B9u;
         d.rk[2 * r + 1] = (uint32_t)(p.seed >> 32) + r * 0xBB67AE85u;
@@ -304,6 +310,7 @@ StepArgs step_args(tg_scene* s) {
     a.sms = s->sms;
     a.nq_phi = s->nq_phi;
     a.nq_grad = s->nq_grad;
+    a.nq_phi_lo = s->nq_phi_lo;
     a.any_neural = s->any_neural ? 1 : 0;
     return a;
 }
@@ -672,7 +679,8 @@ void tg_destroy_scene(tg_scene* s) {
                     s->ft_noisy, s->link_out, s->link_count, s->err, s->link_rec, s->s_link_pose, s->s_link_vel,
                     s->s_obj_pose, s->s_obj_vel, s->s_env_params, s->s_obj_id, s->s_mask, s->s_contact,
                     s->items_sorted, s->metas, s->slots, s->prox_clean, s->prox_noisy, s->pad_link, s->pad_frame,
-                    s->marker_u, s->ctl, s->nq_phi, s->nq_grad, s->pc_ft, s->anchors, s->anchor_obj, s->ring,
+                    s->marker_u, s->ctl, s->nq_phi, s->nq_grad, s->nq_phi_lo, s->pc_ft, s->anchors, s->anchor_obj,
+                    s->ring,
                     s->n_anchored};
     for (void* p : ptrs) dfree(p);
     delete s;
@@ -744,7 +752,7 @@ tg_status tg_upload_objects(tg_scene* s, const tg_object_desc* objs, int32_t n) 
     };
     std::vector<ObjInfo> info(n);
     for (int i = 0; i < n; ++i) info[i].kind = objs[i].kind;
-    bool any_neural = false;
+    bool any_neural = false, any_raycast = false;
     // a grid (or a neural object's fallback grid): cell-major device copy
     auto load_grid = [&](const tg_object_desc& o, ObjDev& t) -> tg_status {
         size_t cnt = 1;
@@ -817,6 +825,19 @@ tg_status tg_upload_objects(tg_scene* s, const tg_object_desc* objs, int32_t n) 
             t.n_faces = o.n_faces;
             t.tri = dt;
             t.tri_n = dn;
+            if (s->P.depth_backend == 1) {
+                std::vector<float> hv;
+                std::vector<int32_t> hf;
+                if (!host_copy(o.verts, (size_t)o.n_verts * 3, &hv) || !host_copy(o.faces, (size_t)o.n_faces * 3, &hf)) {
+                    cleanup();
+                    return fail(s, TG_ERR_INVALID_ARG, "mesh copy failed");
+                }
+                if (const char* m = upload_mesh_bvh(hv.data(), o.n_verts, hf.data(), o.n_faces, &t, &bufs)) {
+                    cleanup();
+                    return fail(s, TG_ERR_INVALID_ARG, m);
+                }
+                any_raycast = true;
+            }
             break;
         }
         case TG_OBJ_GRID:
@@ -879,13 +900,21 @@ tg_status tg_upload_objects(tg_scene* s, const tg_object_desc* objs, int32_t n) 
     if (e != cudaSuccess) { cleanup(); return cuda_fail(s, e, "object table alloc"); }
     cudaMemcpy(dtab, table.data(), sizeof(ObjDev) * n, cudaMemcpyHostToDevice);
     CK(s, cudaDeviceSynchronize());  // old objects may still be read by queued steps
-    if (any_neural && !s->nq_phi) {
+    if ((any_neural || any_raycast) && !s->nq_phi) {
         cudaError_t ea = dalloc(&s->nq_phi, (size_t)std::max<int64_t>(s->T, 1));
         if (ea == cudaSuccess) ea = dalloc(&s->nq_grad, (size_t)3 * std::max<int64_t>(s->T, 1));
         if (ea != cudaSuccess) {
             dfree(dtab);
             cleanup();
-            return cuda_fail(s, ea, "learned-SDF scratch");
+            return cuda_fail(s, ea, "query scratch");
+        }
+    }
+    if (any_raycast && !s->nq_phi_lo) {
+        cudaError_t ea = dalloc(&s->nq_phi_lo, (size_t)std::max<int64_t>(s->T, 1));
+        if (ea != cudaSuccess) {
+            dfree(dtab);
+            cleanup();
+            return cuda_fail(s, ea, "query scratch");
         }
     }
     free_objects(s);
@@ -894,6 +923,7 @@ tg_status tg_upload_objects(tg_scene* s, const tg_object_desc* objs, int32_t n) 
     s->obj_bufs = bufs;
     s->obj_info = info;
     s->any_neural = any_neural;
+    s->any_raycast = any_raycast;
     return TG_OK;
 }
 
@@ -991,6 +1021,7 @@ tg_status enqueue_step(tg_scene* s, const tg_step_inputs* in, cudaStream_t st, b
     }
     if (prof) CK(s, record(ev[1]));
     if (s->any_neural) CK(s, launch_nsdf_step_query(a, s->n_items, s->nq_phi, s->nq_grad, st));
+    if (s->any_raycast) CK(s, launch_raycast_step_query(a, s->n_items, s->nq_phi, s->nq_phi_lo, s->nq_grad, st));
     if (pipe) CK(s, launch_step_pipe(a, s->n_items, kPipeThreads[s->schedule - TG_SCHED_PIPE_1024], st));
     else CK(s, launch_step(a, s->n_items, st));
     if (prof) CK(s, record(ev[2]));

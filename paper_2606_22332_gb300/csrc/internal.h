@@ -2,6 +2,7 @@
 // shared by the translation units of libtg.so.  Not part of the C-ABI.
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -61,6 +62,8 @@ struct ParamsDev {
     // read delay of the noisy readout (steps) with uniform jitter; ring_k =
     // delay + jitter + 1 slots of history (1: off)
     int delay, jitter, ring_k;
+    // contact-depth backend of mesh objects: 0 signed distance, 1 raycast
+    int depth_backend;
 };
 
 // Object table entry (object frame); its size is a multiple of 16 bytes so
@@ -81,6 +84,12 @@ struct alignas(16) ObjDev {
     int n_verts, n_faces;
     const float* tri;                 // [n_faces][9]: a, b, c vertices
     const float* tri_n;               // [n_faces][3]: unit outward normals
+    // raycast contact-depth backend (scenes that select it): the mesh's
+    // bounding volume hierarchy (BvhNode / BvhTri of bvh.cuh) and each
+    // reordered triangle's original face index
+    const void* bvh_nodes;
+    const void* bvh_tris;
+    const int32_t* bvh_face;
     // learned SDF (kind TG_OBJ_NEURAL; the grid fields hold its fallback grid)
     float nlo[3], nhi[3], ninv_ext[3];
     const uint32_t* ntable;           // [16][2^16] binary16 pairs
@@ -192,6 +201,7 @@ struct StepArgs {
     // neural query kernel that runs before the step kernel
     const float* nq_phi;              // [T]
     const float* nq_grad;             // [3][T]
+    const float* nq_phi_lo;           // [T] low part of phi (raycast meshes: phi = hi + lo)
     int any_neural;
 };
 
@@ -306,6 +316,13 @@ cudaError_t launch_nsdf_sample(uint64_t seed, uint32_t step, int64_t n_points, i
 cudaError_t launch_nsdf_adam(NsdfNet* n, const float* g_w, const float* g_table, float lr, float inv_batch_scale,
                              cudaStream_t s);
 cudaError_t launch_nsdf_step_query(const StepArgs& a, int n_items, float* phi, float* grad, cudaStream_t s);
+// raycast backend in the step: phi = s * (distance to the nearest triangle within reach) as a float pair and
+// that triangle's normal, for every taxel of an env whose object is a mesh (raycast.cu)
+cudaError_t launch_raycast_step_query(const StepArgs& a, int n_items, float* phi_hi, float* phi_lo, float* normal,
+                                      cudaStream_t s);
+// host BVH upload for a mesh object (raycast.cu); returns an error message or null
+const char* upload_mesh_bvh(const float* verts, int nv, const int32_t* faces, int nf, ObjDev* t,
+                            std::vector<void*>* bufs);
 int nsdf_train_ctas(int64_t n);       // partial-gradient rows launch_nsdf_train_step writes
 ObjDev nsdf_objdev(const NsdfNet& n); // a learned-SDF object over the network's own buffers
 const NsdfNet* nsdf_net(const tg_nsdf* h);

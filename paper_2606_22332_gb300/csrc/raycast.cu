@@ -19,130 +19,10 @@
 #include <string>
 #include <vector>
 
-#include "internal.h"
+#include "bvh.cuh"
+#include "step_common.cuh"
 
 namespace tg {
-
-struct BvhNode {
-    float lo[3];
-    int32_t first;   // leaf: first triangle; inner node: left child (the right child is first + 1)
-    float hi[3];
-    int32_t count;   // leaf: triangles (> 0); inner node: 0
-};
-
-struct BvhTri {
-    float4 a, b, c;  // vertices (w unused)
-    float4 n;        // unit face normal in winding order (w unused)
-};
-
-constexpr int kBvhLeaf = 4;
-constexpr int kBvhStack = 64;
-
-__host__ __device__ inline float bvh_box_d2(const BvhNode& nd, float px, float py, float pz) {
-    const float dx = fmaxf(fmaxf(nd.lo[0] - px, px - nd.hi[0]), 0.0f);
-    const float dy = fmaxf(fmaxf(nd.lo[1] - py, py - nd.hi[1]), 0.0f);
-    const float dz = fmaxf(fmaxf(nd.lo[2] - pz, pz - nd.hi[2]), 0.0f);
-    return dx * dx + dy * dy + dz * dz;
-}
-
-// squared distance from p to triangle abc (Voronoi regions of the vertices,
-// edges and face; vertices taken relative to p)
-__host__ __device__ inline float bvh_tri_d2(const BvhTri& t, float px, float py, float pz) {
-    const float ax = t.a.x - px, ay = t.a.y - py, az = t.a.z - pz;
-    const float bx = t.b.x - px, by = t.b.y - py, bz = t.b.z - pz;
-    const float cx = t.c.x - px, cy = t.c.y - py, cz = t.c.z - pz;
-    const float abx = bx - ax, aby = by - ay, abz = bz - az;
-    const float acx = cx - ax, acy = cy - ay, acz = cz - az;
-    // ap = p - a = -a (p is the origin)
-    const float d1 = -(abx * ax + aby * ay + abz * az), d2 = -(acx * ax + acy * ay + acz * az);
-    float qx, qy, qz;  // closest point relative to p
-    if (d1 <= 0.0f && d2 <= 0.0f) {
-        qx = ax; qy = ay; qz = az;
-    } else {
-        const float d3 = -(abx * bx + aby * by + abz * bz), d4 = -(acx * bx + acy * by + acz * bz);
-        if (d3 >= 0.0f && d4 <= d3) {
-            qx = bx; qy = by; qz = bz;
-        } else {
-            const float vc = d1 * d4 - d3 * d2;
-            const float d5 = -(abx * cx + aby * cy + abz * cz), d6 = -(acx * cx + acy * cy + acz * cz);
-            const float vb = d5 * d2 - d1 * d6;
-            const float va = d3 * d6 - d5 * d4;
-            if (vc <= 0.0f && d1 >= 0.0f && d3 <= 0.0f) {
-                const float v = d1 / (d1 - d3);
-                qx = ax + v * abx; qy = ay + v * aby; qz = az + v * abz;
-            } else if (d6 >= 0.0f && d5 <= d6) {
-                qx = cx; qy = cy; qz = cz;
-            } else if (vb <= 0.0f && d2 >= 0.0f && d6 <= 0.0f) {
-                const float w = d2 / (d2 - d6);
-                qx = ax + w * acx; qy = ay + w * acy; qz = az + w * acz;
-            } else if (va <= 0.0f && (d4 - d3) >= 0.0f && (d5 - d6) >= 0.0f) {
-                const float w = (d4 - d3) / ((d4 - d3) + (d5 - d6));
-                qx = bx + w * (cx - bx); qy = by + w * (cy - by); qz = bz + w * (cz - bz);
-            } else {
-                const float den = 1.0f / (va + vb + vc);
-                const float v = vb * den, w = vc * den;
-                qx = ax + abx * v + acx * w; qy = ay + aby * v + acy * w; qz = az + abz * v + acz * w;
-            }
-        }
-    }
-    return qx * qx + qy * qy + qz * qz;
-}
-
-// nearest triangle to p with squared distance below r2 (-1 if none); *best_d2 its squared distance
-__host__ __device__ inline int bvh_nearest(const BvhNode* nodes, const BvhTri* tris, float px, float py, float pz,
-                                           float r2, float* best_d2) {
-    float best = r2;
-    int bi = -1;
-    int stack[kBvhStack];
-    float stack_d[kBvhStack];
-    int sp = 0;
-    if (!(bvh_box_d2(nodes[0], px, py, pz) < best)) {
-        *best_d2 = best;
-        return -1;
-    }
-    int node = 0;
-    for (;;) {
-        const BvhNode& nd = nodes[node];
-        bool descend = false;
-        if (nd.count > 0) {
-            for (int k = nd.first; k < nd.first + nd.count; ++k) {
-                const float d2 = bvh_tri_d2(tris[k], px, py, pz);
-                if (d2 < best) {
-                    best = d2;
-                    bi = k;
-                }
-            }
-        } else {
-            const int l = nd.first, r = nd.first + 1;
-            const float dl = bvh_box_d2(nodes[l], px, py, pz), dr = bvh_box_d2(nodes[r], px, py, pz);
-            const int nearc = dl <= dr ? l : r, farc = dl <= dr ? r : l;
-            const float dn = fminf(dl, dr), df = fmaxf(dl, dr);
-            if (dn < best) {
-                if (df < best && sp < kBvhStack) {
-                    stack[sp] = farc;
-                    stack_d[sp] = df;
-                    ++sp;
-                }
-                node = nearc;
-                descend = true;
-            }
-        }
-        if (descend) continue;
-        // next pending subtree still closer than the best triangle
-        bool found = false;
-        while (sp > 0) {
-            --sp;
-            if (stack_d[sp] < best) {
-                node = stack[sp];
-                found = true;
-                break;
-            }
-        }
-        if (!found) break;
-    }
-    *best_d2 = best;
-    return bi;
-}
 
 __global__ void raycast_depth_kernel(const BvhNode* __restrict__ nodes, const BvhTri* __restrict__ tris,
                                      const int32_t* __restrict__ face_id, const float* __restrict__ probes,
@@ -176,90 +56,130 @@ __global__ void raycast_depth_kernel(const BvhNode* __restrict__ nodes, const Bv
     if (face) face[i] = f;
 }
 
-// host tree build; returns an error message or null
-inline const char* bvh_build(const float* V, int nv, const int32_t* F, int nf, std::vector<BvhNode>& nodes,
-                             std::vector<BvhTri>& tris, std::vector<int32_t>& face_id) {
-    if (nf < 1 || nv < 3) return "the mesh needs at least one triangle";
-    std::vector<float> cen((size_t)3 * nf);
-    std::vector<BvhTri> all((size_t)nf);
-    for (int f = 0; f < nf; ++f) {
-        float p[3][3];
-        for (int k = 0; k < 3; ++k) {
-            const int v = F[3 * f + k];
-            if (v < 0 || v >= nv) return "face index out of range";
-            for (int a = 0; a < 3; ++a) {
-                p[k][a] = V[3 * v + a];
-                if (!std::isfinite(p[k][a])) return "vertices must be finite";
-            }
-        }
-        const double e1[3] = {(double)p[1][0] - p[0][0], (double)p[1][1] - p[0][1], (double)p[1][2] - p[0][2]};
-        const double e2[3] = {(double)p[2][0] - p[0][0], (double)p[2][1] - p[0][1], (double)p[2][2] - p[0][2]};
-        double nn[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-        const double l = std::sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
-        for (int a = 0; a < 3; ++a) nn[a] = l > 0.0 ? nn[a] / l : 0.0;
-        all[f].a = make_float4(p[0][0], p[0][1], p[0][2], 0.f);
-        all[f].b = make_float4(p[1][0], p[1][1], p[1][2], 0.f);
-        all[f].c = make_float4(p[2][0], p[2][1], p[2][2], 0.f);
-        all[f].n = make_float4((float)nn[0], (float)nn[1], (float)nn[2], 0.f);
-        for (int a = 0; a < 3; ++a) cen[3 * f + a] = (p[0][a] + p[1][a] + p[2][a]) / 3.0f;
+// Raycast backend inside the sensor step ("Two contact-depth backends"):
+// for every taxel of an env whose object is a mesh, the distance from the
+// probe centre to the nearest triangle within reach, with that triangle's
+// normal (object frame).  The FP32 walk finds the nearest triangle within
+// (R + 1 um) / s; every triangle within a guard of its distance is then
+// re-evaluated in compensated arithmetic from the compensated probe centre,
+// and the nearest wins (equal distances: the lowest original face index).
+// The step kernel reads phi = s * distance as a float pair (depth R - phi)
+// the way it reads a learned SDF's answer; a taxel with no triangle within
+// reach gets phi = R + 1 m (clear).  One CTA per work item, in env order;
+// items of other objects return at once.
+constexpr int kRayStepThreads = 256;
+
+__global__ void __launch_bounds__(kRayStepThreads)
+    raycast_step_query_kernel(const StepArgs a, float* phi_hi, float* phi_lo, float* nrm) {
+    __shared__ float rec_s[kItemMaxLinks][kLinkRec];
+    __shared__ int start_s[kItemMaxLinks + 1];
+    const Item it = a.items[blockIdx.x];
+    const int e = it.env, L = a.max_links, lb = it.link_begin, nl = it.link_end - it.link_begin, n = it.n_taxels;
+    const ObjDev* op = a.objects + min(max(a.obj_id[e], 0), a.n_objects - 1);
+    if (op->kind != TG_OBJ_MESH || !op->bvh_nodes) return;  // the same for the whole CTA
+    const BvhNode* nodes = static_cast<const BvhNode*>(op->bvh_nodes);
+    const BvhTri* tris = static_cast<const BvhTri*>(op->bvh_tris);
+    const int32_t* face = op->bvh_face;
+    for (int v = threadIdx.x; v < nl * kLinkRec; v += blockDim.x)
+        (&rec_s[0][0])[v] = a.link_rec[(size_t)(e * L + lb) * kLinkRec + v];
+    if ((int)threadIdx.x <= nl) {
+        const int base = a.lattice[e * L + lb].env_offset;
+        start_s[threadIdx.x] = (int)threadIdx.x < nl ? a.lattice[e * L + lb + threadIdx.x].env_offset - base : n;
     }
-    std::vector<int32_t> idx((size_t)nf);
-    for (int f = 0; f < nf; ++f) idx[f] = f;
-    nodes.clear();
-    nodes.reserve((size_t)2 * nf);
-    nodes.push_back(BvhNode{});
-    struct Job { int node, begin, end, depth; };
-    std::vector<Job> jobs{{0, 0, nf, 0}};
-    while (!jobs.empty()) {
-        const Job j = jobs.back();
-        jobs.pop_back();
-        if (j.depth > kBvhStack - 4) return "the tree is too deep";
-        BvhNode nd{};
-        float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
-        for (int a = 0; a < 3; ++a) {
-            nd.lo[a] = INFINITY;
-            nd.hi[a] = -INFINITY;
+    __syncthreads();
+    const int64_t T = a.n_taxels;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int64_t g = it.taxel_begin + i;
+        const float R = a.R[g];
+        if (!(R > 0.0f)) continue;
+        int lo = 0, hi = nl - 1;  // link of taxel i: last start <= i
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (start_s[mid] <= i) lo = mid;
+            else hi = mid - 1;
         }
-        for (int k = j.begin; k < j.end; ++k) {
-            const BvhTri& t = all[idx[k]];
-            const float xs[3][3] = {{t.a.x, t.a.y, t.a.z}, {t.b.x, t.b.y, t.b.z}, {t.c.x, t.c.y, t.c.z}};
-            for (int v = 0; v < 3; ++v)
-                for (int a = 0; a < 3; ++a) {
-                    nd.lo[a] = std::min(nd.lo[a], xs[v][a]);
-                    nd.hi[a] = std::max(nd.hi[a], xs[v][a]);
-                }
-            for (int a = 0; a < 3; ++a) {
-                clo[a] = std::min(clo[a], cen[3 * idx[k] + a]);
-                chi[a] = std::max(chi[a], cen[3 * idx[k] + a]);
-            }
-        }
-        if (j.end - j.begin <= kBvhLeaf) {
-            nd.first = j.begin;
-            nd.count = j.end - j.begin;
-            nodes[j.node] = nd;
+        const float* rec = rec_s[lo];
+        const float x0 = a.x[g], x1 = a.y[g], x2 = a.z[g];
+        const float qx = fmaf(rec[0], x0, fmaf(rec[1], x1, fmaf(rec[2], x2, rec[18])));
+        const float qy = fmaf(rec[3], x0, fmaf(rec[4], x1, fmaf(rec[5], x2, rec[19])));
+        const float qz = fmaf(rec[6], x0, fmaf(rec[7], x1, fmaf(rec[8], x2, rec[20])));
+        const float s = rec[38];
+        const float reach = (R + 1e-6f) / s;
+        float best;
+        const int k = bvh_nearest(nodes, tris, qx, qy, qz, reach * reach, &best);
+        if (k < 0) {
+            phi_hi[g] = R + 1.0f;
+            phi_lo[g] = 0.0f;
+            nrm[g] = nrm[T + g] = nrm[2 * T + g] = 0.0f;
             continue;
         }
-        int axis = 0;
-        for (int a = 1; a < 3; ++a)
-            if (chi[a] - clo[a] > chi[axis] - clo[axis]) axis = a;
-        const int mid = (j.begin + j.end) / 2;
-        std::nth_element(idx.begin() + j.begin, idx.begin() + mid, idx.begin() + j.end,
-                         [&](int x, int y) { return cen[3 * x + axis] < cen[3 * y + axis]; });
-        const int left = (int)nodes.size();
-        nodes.push_back(BvhNode{});
-        nodes.push_back(BvhNode{});
-        nd.first = left;
-        nd.count = 0;
-        nodes[j.node] = nd;
-        jobs.push_back({left + 1, mid, j.end, j.depth + 1});
-        jobs.push_back({left, j.begin, mid, j.depth + 1});
+        // the compensated probe centre, as the step's refinement forms it
+        df qd[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            df acc = df{rec[18 + r], rec[21 + r]};
+            acc = df_add(acc, df_mul_f(df{rec[3 * r], rec[9 + 3 * r]}, x0));
+            acc = df_add(acc, df_mul_f(df{rec[3 * r + 1], rec[9 + 3 * r + 1]}, x1));
+            acc = df_add(acc, df_mul_f(df{rec[3 * r + 2], rec[9 + 3 * r + 2]}, x2));
+            qd[r] = acc;
+        }
+        const V3<dfn> pd{dfn{qd[0]}, dfn{qd[1]}, dfn{qd[2]}};
+        const float lim = sqrtf(best) + 1e-6f / s;
+        df bd = df_from(INFINITY);
+        int bk = k, bf = 0x7fffffff;
+        bvh_within(nodes, tris, qx, qy, qz, lim * lim, [&](int kk) {
+            const BvhTri& t = tris[kk];
+            const V3<dfn> A{mk(t.a.x), mk(t.a.y), mk(t.a.z)}, B{mk(t.b.x), mk(t.b.y), mk(t.b.z)},
+                C{mk(t.c.x), mk(t.c.y), mk(t.c.z)};
+            V3<dfn> cp;
+            int reg;
+            const dfn d2 = closest_point_tri<dfn>(pd, A, B, C, &cp, &reg);
+            const int fid = face[kk];
+            if (df_lt(d2.v, bd) || (!df_lt(bd, d2.v) && fid < bf)) {
+                bd = d2.v;
+                bk = kk;
+                bf = fid;
+            }
+        });
+        const df phi = df_mul_f(df_sqrt(bd), s);
+        phi_hi[g] = phi.hi;
+        phi_lo[g] = phi.lo;
+        const float4 fn = tris[bk].n;
+        nrm[g] = fn.x;
+        nrm[T + g] = fn.y;
+        nrm[2 * T + g] = fn.z;
     }
-    tris.resize((size_t)nf);
-    face_id.resize((size_t)nf);
-    for (int k = 0; k < nf; ++k) {
-        tris[k] = all[idx[k]];
-        face_id[k] = idx[k];
-    }
+}
+
+cudaError_t launch_raycast_step_query(const StepArgs& a, int n_items, float* phi_hi, float* phi_lo, float* normal,
+                                      cudaStream_t s) {
+    if (n_items == 0) return cudaSuccess;
+    raycast_step_query_kernel<<<n_items, kRayStepThreads, 0, s>>>(a, phi_hi, phi_lo, normal);
+    return cudaGetLastError();
+}
+
+const char* upload_mesh_bvh(const float* verts, int nv, const int32_t* faces, int nf, ObjDev* t,
+                            std::vector<void*>* bufs) {
+    std::vector<BvhNode> nodes;
+    std::vector<BvhTri> tris;
+    std::vector<int32_t> fid;
+    if (const char* m = bvh_build(verts, nv, faces, nf, nodes, tris, fid)) return m;
+    BvhNode* dn = nullptr;
+    BvhTri* dt = nullptr;
+    int32_t* df_ = nullptr;
+    cudaError_t e = cudaMalloc(&dn, sizeof(BvhNode) * nodes.size());
+    if (dn) bufs->push_back(dn);
+    if (e == cudaSuccess) e = cudaMalloc(&dt, sizeof(BvhTri) * tris.size());
+    if (dt) bufs->push_back(dt);
+    if (e == cudaSuccess) e = cudaMalloc(&df_, sizeof(int32_t) * fid.size());
+    if (df_) bufs->push_back(df_);
+    if (e == cudaSuccess) e = cudaMemcpy(dn, nodes.data(), sizeof(BvhNode) * nodes.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dt, tris.data(), sizeof(BvhTri) * tris.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(df_, fid.data(), sizeof(int32_t) * fid.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return "mesh tree upload failed";
+    t->bvh_nodes = dn;
+    t->bvh_tris = dt;
+    t->bvh_face = df_;
     return nullptr;
 }
 

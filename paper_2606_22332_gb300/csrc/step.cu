@@ -142,7 +142,7 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
                 while (i1 >= S.start[l1 + 1]) ++l1;
         }
         float phi0 = 0.0f, phi1 = 0.0f;
-        if (obj.kind == TG_OBJ_NEURAL) {  // from the learned-SDF query kernel
+        if (phi_precomputed(obj, a.P)) {  // from the learned-SDF or raycast query kernel
             if (R0 > 0.0f) phi0 = a.nq_phi[g0];
             if (R1 > 0.0f) phi1 = a.nq_phi[g1];
         } else {
@@ -168,7 +168,7 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
                 st[4 * kItemCap + i] = __uint_as_float(u ? fl1 : fl0);
                 continue;
             }
-            S.bits[i] = clear_taxel(a, g, R, u ? fl1 : fl0, phi);
+            S.bits[i] = clear_taxel(a, g, R, u ? fl1 : fl0, raycast_obj(obj, a.P) ? R : phi);
 #pragma unroll
             for (int c = 0; c < 6; ++c) S.fc[c][i] = 0.f;
             S.ag[0][i] = 0.f;

@@ -54,6 +54,17 @@ __device__ __forceinline__ void acc_add(Acc& a, float x) {
 // len <= 1024 that is below 1.3e-4 < 1/(2 len), so the floor is exact.
 __device__ __forceinline__ int uni_div(int i, float inv) { return (int)(((float)i + 0.5f) * inv); }
 
+// Objects whose phi comes from a query kernel run ahead of the step kernel:
+// a learned SDF, and a mesh answered by the raycast backend (its phi is a
+// float pair, hi in nq_phi and lo in nq_phi_lo; a phi above R + 1 um marks a
+// probe with no triangle within reach, whose surface-distance output is 0).
+__device__ __forceinline__ bool phi_precomputed(const ObjDev& o, const ParamsDev& P) {
+    return o.kind == TG_OBJ_NEURAL || (o.kind == TG_OBJ_MESH && P.depth_backend != 0);
+}
+__device__ __forceinline__ bool raycast_obj(const ObjDev& o, const ParamsDev& P) {
+    return o.kind == TG_OBJ_MESH && P.depth_backend != 0;
+}
+
 // FP32 object-frame query point q^ = M x + t and scaled SDF s phi(q^)
 __device__ __forceinline__ float fast_query(const float* rec, const ObjDev& obj, float x0, float x1, float x2) {
     const float3 q = f3(fmaf(rec[0], x0, fmaf(rec[1], x1, fmaf(rec[2], x2, rec[18]))),
@@ -93,8 +104,9 @@ struct CleanReading {
 // own Schmitt decision (flag bit 2) and a second force (same normal and
 // velocities).  Pure: the caller stores the results (store_clean).
 template <bool RADIUS>  // probe-radius noise on (rho > 0)
-__device__ __forceinline__ CleanReading refine_compute(const ParamsDev& P, const float* nq_phi, const float* nq_grad,
-                                                       int64_t T, int64_t gid0, const float* rec, const ObjDev& obj,
+__device__ __forceinline__ CleanReading refine_compute(const ParamsDev& P, const float* nq_phi, const float* nq_phi_lo,
+                                                       const float* nq_grad, int64_t T, int64_t gid0,
+                                                       const float* rec, const ObjDev& obj,
                                                        int64_t g, float x0, float x1, float x2, float R,
                                                        uint8_t flags, uint32_t step) {
     df qd[3];
@@ -109,9 +121,10 @@ __device__ __forceinline__ CleanReading refine_compute(const ParamsDev& P, const
     float3 go;
     const float scale = rec[38];
     df phid;
-    if (obj.kind == TG_OBJ_NEURAL) {
-        // the learned SDF has no compensated form: its FP32 phi and gradient
-        phid = df_from(nq_phi[g]);
+    if (phi_precomputed(obj, P)) {
+        // a learned SDF has no compensated form (its FP32 phi and gradient);
+        // the raycast backend's phi is a compensated pair (its face normal)
+        phid = raycast_obj(obj, P) ? df{nq_phi[g], nq_phi_lo[g]} : df_from(nq_phi[g]);
         go = f3(nq_grad[g], nq_grad[T + g], nq_grad[2 * T + g]);
     } else {
         phid = df_mul_f(sdf_refine(obj, df3{qd[0], qd[1], qd[2]}, &go), scale);
@@ -192,8 +205,8 @@ template <bool RADIUS>
 __device__ __forceinline__ CleanReading refine_taxel(const StepArgs& a, const float* rec, const ObjDev& obj,
                                                      int64_t g, float x0, float x1, float x2, float R,
                                                      uint8_t flags, uint32_t step) {
-    const CleanReading cr = refine_compute<RADIUS>(a.P, a.nq_phi, a.nq_grad, a.n_taxels, a.gid0, rec, obj, g, x0, x1,
-                                                   x2, R, flags, step);
+    const CleanReading cr = refine_compute<RADIUS>(a.P, a.nq_phi, a.nq_phi_lo, a.nq_grad, a.n_taxels, a.gid0, rec,
+                                                   obj, g, x0, x1, x2, R, flags, step);
     store_clean(a, g, cr);
     return cr;
 }

@@ -309,13 +309,13 @@ __global__ void __launch_bounds__(NT, 1) step_pipe_kernel(const StepArgs a) {
                 const uint8_t fl = Gb.flags[Ld.geo[kGeoCh] + i];
                 float phi = 0.0f;
                 if (R > 0.0f) {
-                    if (obj.kind == TG_OBJ_NEURAL) phi = a.nq_phi[g];
+                    if (phi_precomputed(obj, P)) phi = a.nq_phi[g];
                     else phi = fast_query(Gb.rec[link_of(M, i)], obj, x0, x1, x2);
                     if (!isfinite(phi)) atomicAdd(a.err, 1u);
                 }
                 near = R > 0.0f && phi < R + 1e-6f + (RADIUS ? P.rho : 0.0f);
                 if (!near) {
-                    S.bits[i] = clear_taxel(a, g, R, fl, phi);
+                    S.bits[i] = clear_taxel(a, g, R, fl, raycast_obj(obj, P) ? R : phi);
 #pragma unroll
                     for (int c = 0; c < 6; ++c) S.fc[c][i] = 0.f;
                     S.dd[0][i] = 0.f;
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(NT, 1) step_pipe_kernel(const StepArgs a) {
                 const float x0 = Gb.ch[0][Ld.geo[0] + i], x1 = Gb.ch[1][Ld.geo[1] + i], x2 = Gb.ch[2][Ld.geo[2] + i];
                 const float R = Gb.ch[3][Ld.geo[3] + i];
                 const uint8_t fl = Gb.flags[Ld.geo[kGeoCh] + i];
-                const CleanReading cr = refine_compute<RADIUS>(P, a.nq_phi, a.nq_grad, T, a.gid0,
+                const CleanReading cr = refine_compute<RADIUS>(P, a.nq_phi, a.nq_phi_lo, a.nq_grad, T, a.gid0,
                                                                Gb.rec[link_of(M, i)], obj, g, x0, x1, x2, R, fl, step);
                 store_clean(a, g, cr);
 #pragma unroll

@@ -54,7 +54,7 @@ class Params(C.Structure):
         ("dr_on", C.c_int32), ("dr_mu", C.c_double * 2), ("dr_k", C.c_double * 2), ("dr_scale", C.c_double * 2),
         ("nsdf_max_err_mm", C.c_double), ("probe_radius_noise", C.c_double),
         ("pc_radius", C.c_double), ("pc_k", C.c_double), ("pc_ks", C.c_double), ("pc_density", C.c_double),
-        ("read_delay", C.c_int32), ("read_jitter", C.c_int32)]
+        ("read_delay", C.c_int32), ("read_jitter", C.c_int32), ("depth_backend", C.c_int32)]
 
 
 class PadDesc(C.Structure):
@@ -246,6 +246,7 @@ def _fill_params(params: dict) -> Params:
     P.pc_density = float(params.get("pc_density", 100.0))
     P.read_delay = int(params.get("read_delay", 0))
     P.read_jitter = int(params.get("read_jitter", 0))
+    P.depth_backend = {"sdf": 0, "raycast": 1}[params.get("depth_backend", "sdf")]
     for g in ("depth", "ft", "prox"):
         grp = getattr(P, g)
         for k in NoiseGroup._fields_:

@@ -3,7 +3,7 @@
 // own query (host-compiled, no GPU call) and compares every nearest distance
 // with brute force over all triangles.  Prints "ok <checks>" or the first
 // mismatch.
-#include "raycast.cu"
+#include "bvh.cuh"
 
 #include <cstdio>
 #include <random>
