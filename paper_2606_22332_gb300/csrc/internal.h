@@ -111,7 +111,7 @@ struct Item {
     int16_t link_begin, link_end;     // [begin, end) over the env's link slots
     int64_t taxel_begin;              // global index of the first taxel
     int32_t n_taxels;
-    int32_t pad;
+    int32_t pad;                      // in the per-step sorted copy: the env's object index
 };
 
 // Static layout of one work item for the pipelined step kernel, built at

@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(kInferThreads) nsdf_step_query_kernel(const St
     __shared__ int ncq, nnear;
     const Item it = a.items_sorted ? a.items_sorted[blockIdx.x] : a.items[blockIdx.x];
     const int e = it.env, L = a.max_links, lb = it.link_begin, nl = it.link_end - it.link_begin, n = it.n_taxels;
-    const int oid = min(max(a.obj_id[e], 0), a.n_objects - 1);
+    const int oid = min(max(a.items_sorted ? it.pad : a.obj_id[e], 0), a.n_objects - 1);
     const ObjDev& o = a.objects[oid];
     if (o.kind != TG_OBJ_NEURAL) return;
     const int64_t T = a.n_taxels;

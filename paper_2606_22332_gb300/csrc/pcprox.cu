@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kPcThreads, 4) pc_prox_kernel(const StepArgs a
         const int base = a.lattice[e * L + lb].env_offset;
         start_s[threadIdx.x] = (int)threadIdx.x < nl ? a.lattice[e * L + lb + threadIdx.x].env_offset - base : n;
     }
-    if (threadIdx.x == 0) obj_s = a.objects[min(max(a.obj_id[e], 0), a.n_objects - 1)];
+    if (threadIdx.x == 0) obj_s = a.objects[min(max(a.items_sorted ? it.pad : a.obj_id[e], 0), a.n_objects - 1)];
     __syncthreads();
     const int64_t T = a.n_taxels;
     const float R = P.pc_radius;

@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kProxThreads, 4) prox_kernel(const StepArgs a)
         start_s[threadIdx.x] = (int)threadIdx.x < nl ? a.lattice[e * L + lb + threadIdx.x].env_offset - base : n;
     }
     if (threadIdx.x == 0) {
-        int oid = min(max(a.obj_id[e], 0), a.n_objects - 1);
+        int oid = min(max(a.items_sorted ? it.pad : a.obj_id[e], 0), a.n_objects - 1);
         obj_s = a.objects[oid];
         next_ray = 0;
     }

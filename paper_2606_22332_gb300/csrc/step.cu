@@ -49,6 +49,33 @@ struct SmemStep {
     float uni_inv_len, uni_inv_cols;
 };
 
+// L2 prefetch of the SDF grid of the object whose run of items begins two
+// waves of resident CTAs after `slot` in the object-sorted order.  Each env
+// queries cells no other env touches, so without it every query's cell is a
+// random HBM sector whose latency the geometry phase waits for; with it the
+// grid streams into L2 (evict-last) once per object and step, ahead of the
+// CTAs that read it.  A hint only: results do not depend on it.
+constexpr uint32_t kGridPrefetchChunk = 64 * 1024;
+
+__device__ __forceinline__ void prefetch_grid_ahead(const StepArgs& a, int slot) {
+    const int t = slot + 2 * a.resident_ctas;  // one wave ahead measured 1 % slower, half a wave 3 %
+    if (t <= 0 || t >= a.n_items) return;
+    const int k = a.items_sorted[t].pad;
+    if (k == a.items_sorted[t - 1].pad) return;
+    const ObjDev& o = a.objects[min(max(k, 0), a.n_objects - 1)];
+    if ((o.kind != TG_OBJ_GRID && o.kind != TG_OBJ_NEURAL) || !o.cells) return;
+    const uint64_t bytes = (uint64_t)(o.dims[0] - 1) * (uint64_t)(o.dims[1] - 1) * (uint64_t)(o.dims[2] - 1) *
+                           (o.fp16 ? 16u : 32u);
+    const char* base = static_cast<const char*>(o.cells);
+    const uint64_t pol = l2_evict_last_policy();
+    for (uint64_t off = 0; off < bytes; off += kGridPrefetchChunk) {
+        const uint32_t len = (uint32_t)min((uint64_t)kGridPrefetchChunk, bytes - off);  // a multiple of 16
+        asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(base + off), "r"(len),
+                     "l"(pol)
+                     : "memory");
+    }
+}
+
 // One work item: every phase of the step for its taxels.
 template <int NT, bool RADIUS>
 __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int slot, uint32_t step) {
@@ -104,7 +131,9 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
     // the object descriptor, 8 bytes per thread of warp 1
     static_assert(sizeof(ObjDev) % 8 == 0 && sizeof(ObjDev) / 8 <= 32 && NT >= 64, "object copy by one warp");
     if (tid >= 32 && tid < 32 + (int)(sizeof(ObjDev) / 8)) {
-        int oid = a.obj_id[e];
+        // the sorted copy of the items carries the object (one load fewer
+        // on the prologue's dependent chain)
+        int oid = a.items_sorted ? it.pad : a.obj_id[e];
         oid = min(max(oid, 0), a.n_objects - 1);
         reinterpret_cast<uint2*>(&S.obj)[tid - 32] = reinterpret_cast<const uint2*>(a.objects + oid)[tid - 32];
     }
@@ -223,6 +252,9 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
         const int ll = t % nl;
         link_quantity(a, S, S.fc, (size_t)(e * L + lb + ll), S.start[ll], S.start[ll + 1], t / nl);
     }
+    // (the last thread has no link quantity here)
+    static_assert(kItemMaxLinks * 14 < NT, "a thread free in phase C1");
+    if (a.items_sorted && tid == NT - 1) prefetch_grid_ahead(a, slot);
     __syncthreads();
 
     // ---- phase B: crosstalk, base noise, dead override -> noisy force/torque
@@ -408,8 +440,9 @@ __global__ void order_items_kernel(const Item* items, int n_items, const int32_t
     }
     __syncthreads();
     for (int i = threadIdx.x; i < n_items; i += blockDim.x) {
-        const Item it = items[i];
+        Item it = items[i];
         const int k = cache ? (int)oc[i] : min(max(obj_id[it.env], 0), n_objects - 1);
+        it.pad = k;  // the env's object this step
         sorted[atomicAdd(&cnt[k], 1)] = it;
     }
 }
