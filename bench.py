@@ -72,6 +72,12 @@ def parse():
     ap.add_argument("--clocks-csv", default=None,
                     help="where to keep the nvidia-smi clock samples of the timed region ({rank} is replaced; "
                          "default: a temporary file)")
+    ap.add_argument("--no-config4", action="store_true", help="skip the configuration-4 line")
+    ap.add_argument("--config4-objects", type=int, default=256, help="distinct objects of the configuration-4 line")
+    ap.add_argument("--config4-steps", type=int, default=500, help="graph-replayed steps of the configuration-4 line")
+    ap.add_argument("--config4-points", type=int, default=1_000_000, help="labelled training points per object")
+    ap.add_argument("--config4-train-steps", type=int, default=2000, help="Adam steps per object")
+    ap.add_argument("--config4-streams", type=int, default=8, help="networks trained at once, one stream each")
     ap.add_argument("--neural-objects", type=int, default=64, help="objects given a learned SDF (0: skip the line)")
     ap.add_argument("--neural-points", type=int, default=2_000_000, help="labelled training points per object")
     ap.add_argument("--neural-steps", type=int, default=3000, help="Adam steps per object")
@@ -259,6 +265,170 @@ def warm_then_rewind(sc, args, dt, stream=None):
     sc.graph_seek(0, 0.0, dt)
 
 
+def accuracy_vs_mesh(args, wl, envs, nobjs, objs):
+    """One step of the envs `envs` with the learned SDFs, the plain grids and
+    the exact meshes: contact-flag agreement, depth and force errors of each
+    pair (None without envs)."""
+    import paper_2606_22332_gb300.tg as tg
+    from paper_2606_22332_gb300 import workload as W
+
+    if not len(envs):
+        return None
+    sub = wl.subset(envs)
+    inp = sub.inputs(args.warmup)
+    outs = {}
+    for name, ol in (("neural", nobjs), ("grid", objs),
+                     ("mesh", [W.ObjectSpec(kind="mesh", verts=o.verts, faces=o.faces) for o in wl.objects])):
+        s2 = tg.Scene(sub.geom(), dict(sub.params, nsdf_max_err_mm=args.neural_max_err_mm), taxel_gid0=0, env_gid0=0)
+        s2.upload_objects(ol)
+        s2.step(inp)
+        outs[name] = {"flags": s2.read(tg.CH_STATE_FLAGS) & 1, "depth": s2.read(tg.CH_DEPTH).astype(np.float64),
+                      "f": s2.read(tg.CH_FORCE_TORQUE)[:3].astype(np.float64)}
+        s2.sync()
+        s2.close()
+    act = sub.R > 0
+
+    def cmp(a, b):
+        pen = act & ((outs[a]["depth"] > 0) | (outs[b]["depth"] > 0))
+        dd = np.abs(outs[a]["depth"] - outs[b]["depth"])[pen] * 1e3
+        df = np.linalg.norm(outs[a]["f"] - outs[b]["f"], axis=0)[pen]
+        fb = np.linalg.norm(outs[b]["f"], axis=0)[pen]
+        return {"contact_flag_agreement": float(np.mean(outs[a]["flags"][act] == outs[b]["flags"][act])),
+                "depth_err_mm": {"mean": float(dd.mean()), "p99": float(np.quantile(dd, 0.99)),
+                                 "max": float(dd.max())},
+                "force_err_N": {"mean": float(df.mean()), "p99": float(np.quantile(df, 0.99))},
+                "force_rel_err_median": float(np.median(df / np.maximum(fb, 1e-9)))}
+
+    return {"envs": int(len(envs)), "neural_vs_exact_mesh": cmp("neural", "mesh"),
+            "grid_vs_exact_mesh": cmp("grid", "mesh"), "neural_vs_grid": cmp("neural", "grid")}
+
+
+def train_networks(args, objects, dev, n_points, n_steps, n_streams, seed0):
+    """One learned SDF per object, trained on the GPU (labels: the exact-mesh
+    query on n_points sampled points, half within 5 mm of the surface), up
+    to n_streams networks at once on their own streams; each probed on 8,192
+    fresh points.  Returns the networks and (max, mean, p99) probe errors in mm."""
+    import torch
+    import paper_2606_22332_gb300.tg as tg
+    from paper_2606_22332_gb300 import workload as W
+
+    nets, stats = [None] * len(objects), [None] * len(objects)
+    streams = [torch.cuda.Stream(device=dev) for _ in range(max(1, n_streams))]
+    for g0 in range(0, len(objects), len(streams)):
+        group = list(range(g0, min(g0 + len(streams), len(objects))))
+        keep = []
+        for k, st in zip(group, streams):
+            o = objects[k]
+            rng = np.random.default_rng(seed0 + k)
+            with torch.cuda.stream(st):
+                P = torch.from_numpy(W.sdf_sample_points(rng, o.verts, o.faces, o.lo, o.hi, n_points)).to(dev)
+                lab, _ = tg.mesh_sdf(o.verts, o.faces, P, with_grad=False, stream=st.cuda_stream)
+                net = tg.Nsdf(o.lo, o.hi, seed=k)
+                net.train(P, lab * 1e3, steps=n_steps, batch=1 << 14, lr0=1e-2, lr_final=3e-4, seed=k,
+                          record_losses=False, stream=st.cuda_stream)
+            nets[k] = net
+            keep.append((P, lab))
+        torch.cuda.synchronize()
+        del keep
+        for k in group:
+            o = objects[k]
+            probe = torch.from_numpy(W.sdf_sample_points(np.random.default_rng(seed0 + 50000 + k), o.verts, o.faces,
+                                                         o.lo, o.hi, 8192)).to(dev)
+            mx, mean = nets[k].probe(o.verts, o.faces, probe)
+            ex, _ = tg.mesh_sdf(o.verts, o.faces, probe, with_grad=False)
+            p99 = float(torch.quantile((nets[k].eval(probe) - ex).abs() * 1e3, 0.99).item())
+            stats[k] = (mx, mean, p99)
+    return nets, stats
+
+
+def config4_line(args, dev, stream):
+    """Configuration 4: 20,480 envs with T_e ~ U{200..1000} taxels over
+    L_e ~ U{10..20} links, 256 distinct objects, one learned SDF per object
+    (trained here on the GPU) answering the near-field contact query with
+    fallback to the object's 96^3 FP16 grid where its error probe exceeds
+    0.2 mm, per-step domain randomisation of mu, k and the object scale,
+    500 graph-replayed steps; the same workload with the plain grids timed
+    alongside, and a subset of envs compared against the exact meshes."""
+    import torch
+    import paper_2606_22332_gb300.tg as tg
+    from paper_2606_22332_gb300 import workload as W
+
+    t_setup = time.time()
+    wl = W.config4(n_envs=args.envs, n_objects=args.config4_objects)
+    objs = []
+    for o in wl.objects:
+        vals = tg.bake_grid(o.verts, o.faces, o.dims, o.lo, o.hi, fp16=o.fp16)
+        objs.append(W.ObjectSpec(kind="grid", dims=o.dims, lo=o.lo, hi=o.hi, fp16=o.fp16, values=vals, name=o.name))
+    d_in = {k: torch.as_tensor(getattr(wl, k)).to(dev) for k in ("link_pose", "link_vel", "obj_pose", "obj_vel", "obj_id")}
+    dt = wl.params["dt"]
+    steps = args.config4_steps
+
+    def timed(objects, params, sched=None):
+        sc = tg.Scene(wl.geom(), params)
+        sc.upload_objects(objects)
+        tune = None
+        if sched is None:
+            sc.step(dict(d_in, pose_dt=0.0, step=0))
+            tune = sc.autotune(dict(d_in, pose_dt=0.0, step=0), steps=3)
+            sched = {"schedule": tune["chosen"]["schedule"], "sorted": bool(tune["chosen"]["sorted"])}
+        sc.set_schedule(**sched)
+        sc.profile(True)
+        sc.graph_capture(dict(d_in, pose_dt=0.0, step=0), pose_dt_per_step=dt)
+        warm_then_rewind(sc, args, dt)
+        torch.cuda.synchronize()
+        sc.profile_read()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sc.graph_launch(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        _, step_ms, n = sc.profile_read()
+        used = [k for k in range(len(objects)) if sc.object_info(k)[0] == tg.TG_OBJ_NEURAL]
+        sc.graph_release()
+        sc.close()
+        return ms, step_ms / max(n, 1), sched, tune, used
+
+    ms_plain, step_plain, sched, tune, _ = timed(objs, wl.params)
+    t0 = time.time()
+    nets, stats = train_networks(args, wl.objects, dev, args.config4_points, args.config4_train_steps,
+                                 args.config4_streams, seed0=7000)
+    train_s = time.time() - t0
+    nobjs = [W.ObjectSpec(kind="neural", dims=objs[k].dims, lo=objs[k].lo, hi=objs[k].hi, fp16=objs[k].fp16,
+                          values=objs[k].values, net=nets[k], nsdf_err_mm=stats[k][0], name=objs[k].name)
+             for k in range(len(objs))]
+    ms_net, step_net, _, _, used = timed(nobjs, dict(wl.params, nsdf_max_err_mm=args.neural_max_err_mm), sched)
+    envs = np.flatnonzero(np.isin(wl.obj_id, used))[: args.neural_check_envs]
+    acc = accuracy_vs_mesh(args, wl, envs, nobjs, objs)
+    for net in nets:
+        net.close()
+    pm = np.array(stats)
+    n_q = wl.n_active
+    faces = [len(o.faces) for o in wl.objects]
+    return {
+        "workload": f"configuration 4: {wl.n_envs} envs, uneven 200-1,000 taxels over 10-20 links "
+                    f"({n_q} active taxels), {len(wl.objects)} distinct objects of {min(faces)}-{max(faces)} faces, "
+                    "per-step domain randomisation (mu U(0.4, 1.2), k U(5e3, 2e4) N/m, scale U(0.8, 1.2)), "
+                    f"{steps} graph-replayed steps, schedule {sched}",
+        "value": n_q * steps / (ms_net * 1e-3), "unit": UNIT, "ms_per_step": ms_net / steps,
+        "step_kernels_ms": round(step_net, 4),
+        "plain_grid": {"value": n_q * steps / (ms_plain * 1e-3), "ms_per_step": ms_plain / steps,
+                       "step_kernels_ms": round(step_plain, 4)},
+        "vs_plain_grid": round(ms_plain / ms_net, 4),
+        "objects_using_network": len(used), "fallback_above_mm": args.neural_max_err_mm,
+        "envs_using_network": int(np.isin(wl.obj_id, used).sum()),
+        "training": {"points_per_object": args.config4_points, "steps": args.config4_train_steps,
+                     "batch": 1 << 14, "networks_at_once": args.config4_streams, "seconds_total": round(train_s, 1),
+                     "labels": "GPU exact-mesh query"},
+        "probe_err_mm": {"max_over_objects": float(pm[:, 0].max()), "median_of_max": float(np.median(pm[:, 0])),
+                         "mean": float(pm[:, 1].mean()), "p99_median": float(np.median(pm[:, 2]))},
+        "accuracy": acc,
+        "autotune": tune["candidates"] if tune else None,
+        "gpu_launches": steps * (5 + (1 if sched["schedule"].startswith("pipe") or sched["sorted"] else 0)),
+        "setup_s": round(time.time() - t_setup, 1),
+    }
+
+
 def neural_line(args, dev, stream, step_inputs):
     """Configuration 3: learned SDFs for 64 procedural meshes of 5k-20k faces
     (the headline's layout of envs, links and taxels, placed on these
@@ -341,36 +511,8 @@ def neural_line(args, dev, stream, step_inputs):
     q_used = int(np.isin(wl.obj_id, used).sum()) * (wl.n_active // wl.n_envs)
 
     # accuracy on envs whose object uses its network: network vs 96^3 grid vs exact mesh, one step
-    acc = None
     envs = np.flatnonzero(np.isin(wl.obj_id, used))[: args.neural_check_envs]
-    if len(envs):
-        sub = wl.subset(envs)
-        inp = sub.inputs(args.warmup)
-        outs = {}
-        for name, ol in (("neural", nobjs), ("grid", objs),
-                         ("mesh", [W.ObjectSpec(kind="mesh", verts=o.verts, faces=o.faces) for o in wl.objects])):
-            s2 = tg.Scene(sub.geom(), dict(sub.params, nsdf_max_err_mm=args.neural_max_err_mm), taxel_gid0=0, env_gid0=0)
-            s2.upload_objects(ol)
-            s2.step(inp)
-            outs[name] = {"flags": s2.read(tg.CH_STATE_FLAGS) & 1, "depth": s2.read(tg.CH_DEPTH).astype(np.float64),
-                          "f": s2.read(tg.CH_FORCE_TORQUE)[:3].astype(np.float64)}
-            s2.sync()
-            s2.close()
-        act = sub.R > 0
-
-        def cmp(a, b):
-            pen = act & ((outs[a]["depth"] > 0) | (outs[b]["depth"] > 0))
-            dd = np.abs(outs[a]["depth"] - outs[b]["depth"])[pen] * 1e3
-            df = np.linalg.norm(outs[a]["f"] - outs[b]["f"], axis=0)[pen]
-            fb = np.linalg.norm(outs[b]["f"], axis=0)[pen]
-            return {"contact_flag_agreement": float(np.mean(outs[a]["flags"][act] == outs[b]["flags"][act])),
-                    "depth_err_mm": {"mean": float(dd.mean()), "p99": float(np.quantile(dd, 0.99)),
-                                     "max": float(dd.max())},
-                    "force_err_N": {"mean": float(df.mean()), "p99": float(np.quantile(df, 0.99))},
-                    "force_rel_err_median": float(np.median(df / np.maximum(fb, 1e-9)))}
-
-        acc = {"envs": int(len(envs)), "neural_vs_exact_mesh": cmp("neural", "mesh"),
-               "grid_vs_exact_mesh": cmp("grid", "mesh"), "neural_vs_grid": cmp("neural", "grid")}
+    acc = accuracy_vs_mesh(args, wl, envs, nobjs, objs)
     pm = np.array(probe_stats)
     for net in nets:
         net.close()
@@ -488,10 +630,21 @@ def config2_line(args, dev, stream, pg, peaks_fn):
                                      "frac": round(achieved / peak, 4), "peak_kind": kind,
                                      "algorithmic_bytes_per_query": BYTES_PER_QUERY},
             "penetrating_share_last_step": round(pen, 4), "placement": wl.meta.get("placement"),
-            "schedule": {"chosen": tune["chosen"], "candidates": tune["candidates"]},
+            "schedule": {"chosen": tune["chosen"], "candidates": tune["candidates"],
+                         "sensor_kernel_threads": tune["sensor_chosen"],
+                         "sensor_candidates": tune["sensor_candidates"]},
             # pose, [order], step, proximity, markers, step-counter advance
             "gpu_launches": steps * (5 + (1 if tune["chosen"]["schedule"].startswith("pipe") or tune["chosen"]["sorted"]
                                           else 0))}
+
+
+def tune_sensor_shapes(sc, inputs, sched):
+    """The autotuner's launch shapes for the scene's sensor kernels, on the
+    step schedule `sched` (kept); returns {kernel: threads} and the trials."""
+    sc.step(inputs)
+    tune = sc.autotune(inputs, steps=2)
+    sc.set_schedule(**sched)
+    return tune["sensor_chosen"], tune["sensor_candidates"]
 
 
 def peaks():
@@ -864,7 +1017,7 @@ def run_tg(args):
         sc2 = tg.Scene(wlf.geom(), pf, sensors=tg.TG_SENSOR_PROX | tg.TG_SENSOR_MARKERS, taxel_gid0=gid0,
                        env_gid0=egid0, pads=wlf.pads)
         sc2.upload_objects(objs)
-        sc2.set_schedule(**sched)
+        shapes2, _ = tune_sensor_shapes(sc2, step_inputs(0, d_in), sched)
         sc2.graph_capture(step_inputs(0, d_in), pose_dt_per_step=dt)
         warm_then_rewind(sc2, args, dt)
         torch.cuda.synchronize()
@@ -884,6 +1037,7 @@ def run_tg(args):
                 "value": n_q * args.steps / (fms / 1e3), "unit": UNIT, "ms_per_step": fms / args.steps,
                 "prox_markers_ms_per_step": (fms - t_max) / args.steps,
                 "taxels_with_proximity_reading": round(prox_share, 4),
+                "sensor_kernel_threads": shapes2,
                 "gpu_launches": (launches_per_step + 2) * args.steps}
     # third line: the point-cloud ProximityTaxel (the paper's experiment settings) on the same workload
     pcl = None
@@ -895,7 +1049,7 @@ def run_tg(args):
         pcp = dict(wl.params, pc_radius=0.01, pc_k=300.0, pc_ks=10.0, pc_density=100.0)
         sc3 = tg.Scene(wl.geom(), pcp, sensors=tg.TG_SENSOR_PCPROX, taxel_gid0=gid0, env_gid0=egid0)
         sc3.upload_objects(objs_c)
-        sc3.set_schedule(**sched)
+        shapes3, _ = tune_sensor_shapes(sc3, step_inputs(0, d_in), sched)
         sc3.graph_capture(step_inputs(0, d_in), pose_dt_per_step=dt)
         warm_then_rewind(sc3, args, dt)
         torch.cuda.synchronize()
@@ -916,6 +1070,7 @@ def run_tg(args):
                "value": n_q * args.steps / (cms / 1e3), "unit": UNIT, "ms_per_step": cms / args.steps,
                "pc_prox_ms_per_step": (cms - t_max) / args.steps,
                "taxels_with_reading": round(pc_share, 4),
+               "sensor_kernel_threads": shapes3,
                "gpu_launches": (launches_per_step + 1) * args.steps}
     # fourth line: elastomer markers with shear anchors (the paper's experiment settings)
     shear = None
@@ -929,7 +1084,7 @@ def run_tg(args):
         sc4 = tg.Scene(wl.geom(), wl.params, sensors=tg.TG_SENSOR_MARKERS, taxel_gid0=gid0, env_gid0=egid0,
                        pads=pads_s)
         sc4.upload_objects(objs_s)
-        sc4.set_schedule(**sched)
+        shapes4, _ = tune_sensor_shapes(sc4, step_inputs(0, d_in), sched)
         sc4.graph_capture(step_inputs(0, d_in), pose_dt_per_step=dt)
         warm_then_rewind(sc4, args, dt)
         torch.cuda.synchronize()
@@ -951,6 +1106,7 @@ def run_tg(args):
                  "value": n_q * args.steps / (sms / 1e3), "unit": UNIT, "ms_per_step": sms / args.steps,
                  "markers_shear_ms_per_step": (sms - t_max) / args.steps,
                  "anchored_points_per_pad": round(n_anch / max(n_pads, 1), 2),
+                 "sensor_kernel_threads": shapes4,
                  "anchor_state_bytes": n_pads * args.shear_points * 8,
                  "gpu_launches": (launches_per_step + 1) * args.steps}
     delay = None
@@ -969,6 +1125,9 @@ def run_tg(args):
     neural = None
     if args.neural_objects > 0 and ws == 1:
         neural = neural_line(args, dev, stream, step_inputs)
+    cfg4 = None
+    if not args.no_config4 and ws == 1:
+        cfg4 = config4_line(args, dev, stream)
     del objs
 
     peak, peak_kind = peaks()
@@ -1010,6 +1169,7 @@ def run_tg(args):
             "raycast_depth": ray,
             "raycast_step": ray_step,
             "neural_sdf": neural,
+            "config4": cfg4,
             "setup_s": {"bake": round(bake_s, 2), "total": round(time.time() - t_setup, 1)},
         }
         print(json.dumps(out))

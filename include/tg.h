@@ -369,11 +369,19 @@ tg_status tg_graph_release(tg_scene* scene);
                           the item before it computes.
    sorted = 1: items run in the order of the object their env holds (a
    counting sort each step), so concurrent CTAs share object grids in L2.
-   Results are bit-identical across schedules.  tg_autotune times every
-   schedule (x sorted / env order when there are several objects) on `steps`
-   steps of the given inputs (after one warm-up step each), keeps the
-   fastest, and restores the noise state it found (the output buffers then
-   hold the last trial's step).
+   Results are bit-identical across schedules.
+
+   Launch shapes of the sensor kernels (proximity rays, point-cloud
+   proximity, elastomer markers): 128, 256 or 512 threads per CTA (default
+   256), set by tg_set_sensor_threads.  Results are bit-identical across
+   shapes.
+
+   tg_autotune times every schedule (x sorted / env order when there are
+   several objects) on `steps` steps of the given inputs (after one warm-up
+   step each) and keeps the fastest; then, on that schedule, each sensor
+   kernel the scene runs at each of its shapes, keeping the fastest.  It
+   restores the noise state and the shear anchors it found (the output
+   buffers then hold the last trial's step).
    Errors: TG_ERR_STATE (a captured graph exists), TG_ERR_INVALID_ARG. */
 typedef enum {
     TG_SCHED_GRID = 0,
@@ -383,16 +391,28 @@ typedef enum {
     TG_SCHED_PIPE_512 = 4,
     TG_SCHED_COUNT = 5
 } tg_schedule;
+typedef enum {
+    TG_KERNEL_PROX = 0,      /* proximity rays (TG_SENSOR_PROX) */
+    TG_KERNEL_PCPROX = 1,    /* point-cloud proximity (TG_SENSOR_PCPROX) */
+    TG_KERNEL_MARKERS = 2,   /* elastomer markers (TG_SENSOR_MARKERS) */
+    TG_SENSOR_KERNEL_COUNT = 3
+} tg_sensor_kernel;
 typedef struct {
-    int32_t schedule, sorted;
-    double ms_per_step;
+    int32_t schedule, sorted;  /* the step kernel's schedule of this trial */
+    double ms_per_step;        /* whole step, CUDA events */
+    int32_t kernel;            /* -1: a step-kernel schedule was timed; else the
+                                  tg_sensor_kernel whose launch shape was timed */
+    int32_t threads;           /* threads per CTA of that kernel */
 } tg_tune_candidate;
 typedef struct {
-    int32_t n, chosen;
-    tg_tune_candidate cand[16];
+    int32_t n, chosen;                 /* chosen: candidate of the step schedule kept */
+    int32_t sensor_chosen[3];          /* per tg_sensor_kernel: candidate kept, -1 if not tuned */
+    tg_tune_candidate cand[32];
 } tg_tune_report;
 tg_status tg_set_schedule(tg_scene* scene, int32_t schedule, int32_t sorted);
 tg_status tg_get_schedule(const tg_scene* scene, int32_t* schedule, int32_t* sorted);
+tg_status tg_set_sensor_threads(tg_scene* scene, int32_t kernel, int32_t threads);
+tg_status tg_get_sensor_threads(const tg_scene* scene, int32_t kernel, int32_t* threads);
 tg_status tg_autotune(tg_scene* scene, const tg_step_inputs* in, int32_t steps, tg_tune_report* report,
                       tg_stream stream);
 

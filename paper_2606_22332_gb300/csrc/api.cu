@@ -94,6 +94,9 @@ struct tg_scene {
     // schedule (tg_set_schedule / tg_autotune) and step control
     int schedule = TG_SCHED_GRID;     // step kernel schedule (tg_schedule)
     int sorted = 1;                   // object-sorted item order (several objects)
+    // threads per CTA of the sensor kernels (tg_sensor_kernel order: proximity,
+    // point-cloud proximity, markers)
+    int sensor_threads[3] = {256, 256, 256};
     int resident_ctas = 0;            // step kernel CTAs resident on the device at once
     int sms = 0;                      // streaming multiprocessors (pipelined schedules: one CTA each)
     ItemMeta* metas = nullptr;        // [n_items] static item layout (pipelined schedules)
@@ -1025,14 +1028,14 @@ tg_status enqueue_step(tg_scene* s, const tg_step_inputs* in, cudaStream_t st, b
     if (pipe) CK(s, launch_step_pipe(a, s->n_items, kPipeThreads[s->schedule - TG_SCHED_PIPE_1024], st));
     else CK(s, launch_step(a, s->n_items, st));
     if (prof) CK(s, record(ev[2]));
-    if (s->sensors & TG_SENSOR_PROX) CK(s, launch_prox(a, s->n_items, st));
-    if (s->sensors & TG_SENSOR_PCPROX) CK(s, launch_pc_prox(a, s->n_items, st));
+    if (s->sensors & TG_SENSOR_PROX) CK(s, launch_prox(a, s->n_items, s->sensor_threads[0], st));
+    if (s->sensors & TG_SENSOR_PCPROX) CK(s, launch_pc_prox(a, s->n_items, s->sensor_threads[1], st));
     if (s->sensors & TG_SENSOR_MARKERS) {
         MarkerArgs m = s->markers;
         m.obj_id = oid;
         m.objects = s->objects;
         m.n_objects = s->n_objects;
-        CK(s, launch_markers(m, st));
+        CK(s, launch_markers(m, s->sensor_threads[2], st));
     }
     if (graph) CK(s, launch_advance_ctl(s->ctl, st));
     return TG_OK;
@@ -1203,6 +1206,35 @@ tg_status tg_get_schedule(const tg_scene* s, int32_t* schedule, int32_t* sorted)
     return TG_OK;
 }
 
+namespace {
+bool sensor_threads_ok(int32_t t) { return t == 128 || t == 256 || t == 512; }
+// the sensor kernels a scene runs (tg_sensor_kernel order)
+bool sensor_kernel_on(const tg_scene* s, int k) {
+    if (k == 0) return (s->sensors & TG_SENSOR_PROX) && s->P.prox_rays > 0;
+    if (k == 1) return (s->sensors & TG_SENSOR_PCPROX) != 0;
+    return (s->sensors & TG_SENSOR_MARKERS) != 0;
+}
+int step_threads(int schedule) {
+    return schedule >= TG_SCHED_PIPE_1024 ? kPipeThreads[schedule - TG_SCHED_PIPE_1024] : kStepThreads;
+}
+}  // namespace
+
+tg_status tg_set_sensor_threads(tg_scene* s, int32_t kernel, int32_t threads) {
+    if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
+    if (s->graph_exec) return fail(s, TG_ERR_STATE, "release the captured step before changing a launch shape");
+    if (kernel < 0 || kernel >= TG_SENSOR_KERNEL_COUNT) return fail(s, TG_ERR_INVALID_ARG, "unknown sensor kernel");
+    if (!sensor_threads_ok(threads)) return fail(s, TG_ERR_INVALID_ARG, "threads must be 128, 256 or 512");
+    s->sensor_threads[kernel] = threads;
+    return TG_OK;
+}
+
+tg_status tg_get_sensor_threads(const tg_scene* s, int32_t kernel, int32_t* threads) {
+    if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
+    if (kernel < 0 || kernel >= TG_SENSOR_KERNEL_COUNT) return fail(nullptr, TG_ERR_INVALID_ARG, "unknown sensor kernel");
+    if (threads) *threads = s->sensor_threads[kernel];
+    return TG_OK;
+}
+
 tg_status tg_autotune(tg_scene* s, const tg_step_inputs* in, int32_t steps, tg_tune_report* report,
                       tg_stream stream) {
     if (!s) return fail(nullptr, TG_ERR_INVALID_ARG, "scene is NULL");
@@ -1215,11 +1247,15 @@ tg_status tg_autotune(tg_scene* s, const tg_step_inputs* in, int32_t steps, tg_t
     // the noise state is put back afterwards: trials are not steps of the run
     uint8_t* keep = nullptr;
     const size_t RB = s->ring ? (size_t)s->P.ring_k * 8 * T * 4 : 0;
-    const size_t bytes = T + 3 * 8 * T * 4 + E * 4 + RB;
+    // the shear anchors are state of the markers' trials too
+    const size_t EP = s->anchors ? (size_t)s->E * s->markers.pads_per_env : 0;
+    const size_t AB = EP * (size_t)s->markers.shear_n * 8;
+    const size_t bytes = T + 3 * 8 * T * 4 + E * 4 + RB + AB + 2 * EP * 4;
     CK(s, cudaMalloc(&keep, bytes));
     auto save = [&](bool back) {
         struct { void* p; size_t n; } part[] = {{s->flags, T}, {s->hyst_prev, 8 * T * 4}, {s->hyst_xi, 8 * T * 4},
-                                                 {s->drift, 8 * T * 4}, {s->episode, E * 4}, {s->ring, RB}};
+                                                 {s->drift, 8 * T * 4}, {s->episode, E * 4}, {s->ring, RB},
+                                                 {s->anchors, AB}, {s->anchor_obj, EP * 4}, {s->n_anchored, EP * 4}};
         size_t off = 0;
         cudaError_t e = cudaSuccess;
         for (auto& q : part) {
@@ -1233,6 +1269,7 @@ tg_status tg_autotune(tg_scene* s, const tg_step_inputs* in, int32_t steps, tg_t
     };
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     tg_tune_report rep{};
+    for (int k = 0; k < TG_SENSOR_KERNEL_COUNT; ++k) rep.sensor_chosen[k] = -1;
     const int old_p = s->schedule, old_s = s->sorted;
     const bool prof = s->profiling;
     s->profiling = false;
@@ -1240,44 +1277,72 @@ tg_status tg_autotune(tg_scene* s, const tg_step_inputs* in, int32_t steps, tg_t
     if (err == cudaSuccess) err = cudaEventCreate(&e0);
     if (err == cudaSuccess) err = cudaEventCreate(&e1);
     tg_status r = TG_OK;
+    const int old_threads[3] = {s->sensor_threads[0], s->sensor_threads[1], s->sensor_threads[2]};
+    // one variant: a warm-up step, then `steps` timed steps; false on failure
+    auto time_variant = [&](int kernel, int threads) {
+        r = enqueue_step(s, in, st, false);
+        if (r != TG_OK) return false;
+        err = cudaEventRecord(e0, st);
+        for (int k = 0; k < steps && r == TG_OK && err == cudaSuccess; ++k) r = enqueue_step(s, in, st, false);
+        if (r != TG_OK || err != cudaSuccess) return false;
+        err = cudaEventRecord(e1, st);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err != cudaSuccess || rep.n >= (int)(sizeof(rep.cand) / sizeof(rep.cand[0]))) return false;
+        tg_tune_candidate& c = rep.cand[rep.n++];
+        c.schedule = s->schedule;
+        c.sorted = s->sorted;
+        c.ms_per_step = (double)ms / steps;
+        c.kernel = kernel;
+        c.threads = threads;
+        return true;
+    };
+    // the step kernel's schedules first
     const int sort_options = s->n_objects > 1 ? 2 : 1;
-    for (int ps = 0; ps < TG_SCHED_COUNT && err == cudaSuccess && r == TG_OK; ++ps)
-        for (int so = 0; so < sort_options && err == cudaSuccess && r == TG_OK; ++so) {
+    bool ok = err == cudaSuccess;
+    for (int ps = 0; ps < TG_SCHED_COUNT && ok; ++ps)
+        for (int so = 0; so < sort_options && ok; ++so) {
             s->schedule = ps;
             s->sorted = sort_options == 2 ? 1 - so : s->sorted;
-            r = enqueue_step(s, in, st, false);  // warm-up of this variant
-            if (r != TG_OK) break;
-            err = cudaEventRecord(e0, st);
-            for (int k = 0; k < steps && r == TG_OK && err == cudaSuccess; ++k) r = enqueue_step(s, in, st, false);
-            if (r != TG_OK || err != cudaSuccess) break;
-            err = cudaEventRecord(e1, st);
-            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-            if (err != cudaSuccess) break;
-            tg_tune_candidate& c = rep.cand[rep.n++];
-            c.schedule = s->schedule;
-            c.sorted = s->sorted;
-            c.ms_per_step = (double)ms / steps;
+            ok = time_variant(-1, step_threads(ps));
         }
-    if (err == cudaSuccess && r == TG_OK) err = save(true);
+    int best = 0;
+    if (ok) {
+        for (int i = 1; i < rep.n; ++i)
+            if (rep.cand[i].ms_per_step < rep.cand[best].ms_per_step) best = i;
+        s->schedule = rep.cand[best].schedule;
+        s->sorted = rep.cand[best].sorted;
+    }
+    // then each sensor kernel's launch shape, on the chosen schedule
+    for (int k = 0; k < TG_SENSOR_KERNEL_COUNT && ok; ++k) {
+        if (!sensor_kernel_on(s, k)) continue;
+        const int first = rep.n;
+        for (int t : {128, 256, 512}) {
+            s->sensor_threads[k] = t;
+            if (!(ok = time_variant(k, t))) break;
+        }
+        if (!ok) break;
+        int kb = first;
+        for (int i = first + 1; i < rep.n; ++i)
+            if (rep.cand[i].ms_per_step < rep.cand[kb].ms_per_step) kb = i;
+        s->sensor_threads[k] = rep.cand[kb].threads;
+        rep.sensor_chosen[k] = kb;
+    }
+    if (ok) err = save(true);
     if (err == cudaSuccess) err = cudaStreamSynchronize(st);
     s->profiling = prof;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(keep);
-    if (r != TG_OK || err != cudaSuccess || rep.n == 0) {
+    if (!ok || r != TG_OK || err != cudaSuccess || rep.n == 0) {
         s->schedule = old_p;
         s->sorted = old_s;
+        for (int k = 0; k < 3; ++k) s->sensor_threads[k] = old_threads[k];
         if (r != TG_OK) return r;
         return cuda_fail(s, err == cudaSuccess ? cudaErrorUnknown : err, "autotune");
     }
-    int best = 0;
-    for (int i = 1; i < rep.n; ++i)
-        if (rep.cand[i].ms_per_step < rep.cand[best].ms_per_step) best = i;
     rep.chosen = best;
-    s->schedule = rep.cand[best].schedule;
-    s->sorted = rep.cand[best].sorted;
     if (report) *report = rep;
     return TG_OK;
 }

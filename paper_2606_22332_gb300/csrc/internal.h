@@ -280,9 +280,10 @@ cudaError_t launch_mesh_sdf_points(const float* tri, const float* tri_n, int n_f
 cudaError_t launch_mesh_bake(const float* tri, const float* tri_n, int n_faces, const int dims[3],
                              const float lo[3], const float hi[3], int fp16, void* out, cudaStream_t s);
 cudaError_t launch_build_cells(const void* values, const int dims[3], int fp16, void* cells, cudaStream_t s);
-cudaError_t launch_prox(const StepArgs& a, int n_items, cudaStream_t s);
-cudaError_t launch_pc_prox(const StepArgs& a, int n_items, cudaStream_t s);
-cudaError_t launch_markers(const MarkerArgs& m, cudaStream_t s);
+// sensor kernels: `threads` per CTA is 128, 256 or 512 (the autotuner's shapes)
+cudaError_t launch_prox(const StepArgs& a, int n_items, int threads, cudaStream_t s);
+cudaError_t launch_pc_prox(const StepArgs& a, int n_items, int threads, cudaStream_t s);
+cudaError_t launch_markers(const MarkerArgs& m, int threads, cudaStream_t s);
 // anchor_obj = -1 for the pads of the masked envs (all when mask is null)
 cudaError_t launch_shear_reset(int32_t* anchor_obj, int n_envs, int pads_per_env, const uint8_t* mask,
                                cudaStream_t s);

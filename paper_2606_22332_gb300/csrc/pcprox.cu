@@ -33,8 +33,6 @@
 
 namespace tg {
 
-constexpr int kPcThreads = 256;
-constexpr int kPcWarps = kPcThreads / 32;
 constexpr int kPcItemLinks = 32;
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -48,7 +46,9 @@ __device__ __forceinline__ int pc_link_of(const int* start, int nl, int i) {
     return lo;
 }
 
-__global__ void __launch_bounds__(kPcThreads, 4) pc_prox_kernel(const StepArgs a) {
+template <int NT>  // threads per CTA (128, 256 or 512: a launch shape the autotuner picks)
+__global__ void __launch_bounds__(NT, 1024 / NT) pc_prox_kernel(const StepArgs a) {
+    constexpr int kPcWarps = NT / 32;
     __shared__ float rec_s[kPcItemLinks][kLinkRec];
     __shared__ int start_s[kPcItemLinks + 1];
     __shared__ ObjDev obj_s;
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kPcThreads, 4) pc_prox_kernel(const StepArgs a
     const Item it = a.items_sorted ? a.items_sorted[blockIdx.x] : a.items[blockIdx.x];
     const int e = it.env, L = a.max_links, lb = it.link_begin, nl = it.link_end - it.link_begin, n = it.n_taxels;
     const ParamsDev& P = a.P;
-    for (int i = threadIdx.x; i < nl * kLinkRec; i += kPcThreads)
+    for (int i = threadIdx.x; i < nl * kLinkRec; i += NT)
         rec_s[i / kLinkRec][i % kLinkRec] = a.link_rec[(size_t)(e * L + lb + i / kLinkRec) * kLinkRec + i % kLinkRec];
     if ((int)threadIdx.x <= nl) {
         const int base = a.lattice[e * L + lb].env_offset;
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kPcThreads, 4) pc_prox_kernel(const StepArgs a
     int* row_first = row_first_s[warp];
     int* row_base = row_base_s[warp];
     const unsigned lanes_upto = (2u << lane) - 1u;  // bits 0..lane
-    for (int b = warp * 32; b < n; b += kPcThreads) {
+    for (int b = warp * 32; b < n; b += NT) {
         // this lane's taxel of the batch: set-up
         {
             const int i = b + lane;
@@ -247,9 +247,14 @@ __global__ void __launch_bounds__(kPcThreads, 4) pc_prox_kernel(const StepArgs a
     }
 }
 
-cudaError_t launch_pc_prox(const StepArgs& a, int n_items, cudaStream_t s) {
+cudaError_t launch_pc_prox(const StepArgs& a, int n_items, int threads, cudaStream_t s) {
     if (n_items == 0) return cudaSuccess;
-    pc_prox_kernel<<<n_items, kPcThreads, 0, s>>>(a);
+    switch (threads) {
+    case 128: pc_prox_kernel<128><<<n_items, 128, 0, s>>>(a); break;
+    case 256: pc_prox_kernel<256><<<n_items, 256, 0, s>>>(a); break;
+    case 512: pc_prox_kernel<512><<<n_items, 512, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

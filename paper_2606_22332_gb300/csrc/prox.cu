@@ -14,7 +14,6 @@
 
 namespace tg {
 
-constexpr int kProxThreads = 256;
 constexpr int kProxItemLinks = 32;
 constexpr float kMinStep = 1e-5f;
 constexpr int kMaxMarch = 192;
@@ -205,7 +204,8 @@ __device__ __forceinline__ void trace_item_rays(const StepArgs& a, const Item& i
 //           samples, or until t_b - t_a <= 1e-7 m); the crossing is t_b.
 // Per-ray distances go to shared memory; each taxel then sums its rays in
 // ray order (deterministic) and runs the noise chain.
-__global__ void __launch_bounds__(kProxThreads, 4) prox_kernel(const StepArgs a) {
+template <int NT>  // threads per CTA (128, 256 or 512: a launch shape the autotuner picks)
+__global__ void __launch_bounds__(NT, 1024 / NT) prox_kernel(const StepArgs a) {
     extern __shared__ float t_s[];  // [n taxels][rays]: crossing distance or -1
     __shared__ float rec_s[kProxItemLinks][kLinkRec];
     __shared__ int start_s[kProxItemLinks + 1];
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(kProxThreads, 4) prox_kernel(const StepArgs a)
     const int e = it.env, L = a.max_links, lb = it.link_begin, nl = it.link_end - it.link_begin, n = it.n_taxels;
     const ParamsDev& P = a.P;
     const uint32_t step = a.step_from_ctl ? a.ctl->step : a.step;
-    for (int i = threadIdx.x; i < nl * kLinkRec; i += kProxThreads)
+    for (int i = threadIdx.x; i < nl * kLinkRec; i += NT)
         rec_s[i / kLinkRec][i % kLinkRec] = a.link_rec[(size_t)(e * L + lb + i / kLinkRec) * kLinkRec + i % kLinkRec];
     if ((int)threadIdx.x <= nl) {
         const int base = a.lattice[e * L + lb].env_offset;
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kProxThreads, 4) prox_kernel(const StepArgs a)
     const float range = P.prox_range;
     const uint32_t ep = a.episode[e];
     const int64_t T = a.n_taxels;
-    for (int i = threadIdx.x; i < n; i += kProxThreads) {
+    for (int i = threadIdx.x; i < n; i += NT) {
         const int64_t g = it.taxel_begin + i;
         const float R = a.R[g];
         if (!(R > 0.0f)) {
@@ -276,13 +276,23 @@ __global__ void __launch_bounds__(kProxThreads, 4) prox_kernel(const StepArgs a)
     }
 }
 
-cudaError_t launch_prox(const StepArgs& a, int n_items, cudaStream_t s) {
+template <int NT>
+cudaError_t launch_prox_nt(const StepArgs& a, int n_items, size_t smem, cudaStream_t s) {
+    const cudaError_t err = raise_smem_limit((const void*)prox_kernel<NT>, smem);
+    if (err != cudaSuccess) return err;
+    prox_kernel<NT><<<n_items, NT, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prox(const StepArgs& a, int n_items, int threads, cudaStream_t s) {
     if (n_items == 0 || a.P.prox_rays < 1) return cudaSuccess;
     const size_t smem = sizeof(float) * (size_t)kItemCap * (size_t)a.P.prox_rays;  // <= 64 KB (16 rays)
-    const cudaError_t err = raise_smem_limit((const void*)prox_kernel, smem);
-    if (err != cudaSuccess) return err;
-    prox_kernel<<<n_items, kProxThreads, smem, s>>>(a);
-    return cudaGetLastError();
+    switch (threads) {
+    case 128: return launch_prox_nt<128>(a, n_items, smem, s);
+    case 256: return launch_prox_nt<256>(a, n_items, smem, s);
+    case 512: return launch_prox_nt<512>(a, n_items, smem, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -293,15 +303,14 @@ cudaError_t launch_prox(const StepArgs& a, int n_items, cudaStream_t s) {
 // contributing points compacted in point order into shared memory, then every
 // marker sums their Gaussian-weighted drags).
 // ---------------------------------------------------------------------------
-constexpr int kMarkerThreads = 256;
-
-__global__ void __launch_bounds__(kMarkerThreads) marker_kernel(const MarkerArgs m) {
+template <int NT>  // threads per CTA (128, 256 or 512: a launch shape the autotuner picks)
+__global__ void __launch_bounds__(NT) marker_kernel(const MarkerArgs m) {
     __shared__ float h_s[kMaxPadMarkers];
     __shared__ float ha_s[kMaxPadMarkers];
     __shared__ float ut_s[kMaxPadMarkers];   // shear, tangent
     __shared__ float ub_s[kMaxPadMarkers];   // shear, bitangent
-    __shared__ float4 con_s[kMarkerThreads]; // contributing points of a chunk: z_t, z_b, drag_t, drag_b
-    __shared__ int warp_cnt[kMarkerThreads / 32];
+    __shared__ float4 con_s[NT]; // contributing points of a chunk: z_t, z_b, drag_t, drag_b
+    __shared__ int warp_cnt[NT / 32];
     __shared__ int anchored_s;
     __shared__ float rec[kLinkRec];
     __shared__ ObjDev obj_s;
@@ -320,7 +329,7 @@ __global__ void __launch_bounds__(kMarkerThreads) marker_kernel(const MarkerArgs
     const float3 o = f3(fr[0], fr[1], fr[2]), nrm = f3(fr[3], fr[4], fr[5]), tu = f3(fr[6], fr[7], fr[8]);
     const float3 tv = cross(nrm, tu);
     const float half_a = 0.5f * m.rows * m.pitch, half_b = 0.5f * m.cols * m.pitch;
-    for (int j = threadIdx.x; j < M; j += kMarkerThreads) {
+    for (int j = threadIdx.x; j < M; j += NT) {
         const int r = j / m.cols, c = j - r * m.cols;
         const float sa = (r - 0.5f * (m.rows - 1)) * m.pitch, sb = (c - 0.5f * (m.cols - 1)) * m.pitch;
         const float3 x = o + tu * sa + tv * sb;
@@ -340,7 +349,7 @@ __global__ void __launch_bounds__(kMarkerThreads) marker_kernel(const MarkerArgs
         const float s = rec[38], s2 = s * s;
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         int count = 0;
-        for (int c0 = 0; c0 < N; c0 += kMarkerThreads) {
+        for (int c0 = 0; c0 < N; c0 += NT) {
             const int i = c0 + threadIdx.x;
             bool contrib = false;
             float4 cv = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -382,14 +391,14 @@ __global__ void __launch_bounds__(kMarkerThreads) marker_kernel(const MarkerArgs
             __syncthreads();
             int off = 0, K = 0;
 #pragma unroll
-            for (int w = 0; w < kMarkerThreads / 32; ++w) {
+            for (int w = 0; w < NT / 32; ++w) {
                 off += w < warp ? warp_cnt[w] : 0;
                 K += warp_cnt[w];
             }
             if (contrib) con_s[off + __popc(bal & ((1u << lane) - 1u))] = cv;
             __syncthreads();
             if (K > 0) {
-                for (int j = threadIdx.x; j < M; j += kMarkerThreads) {
+                for (int j = threadIdx.x; j < M; j += NT) {
                     const int r = j / m.cols, c = j - r * m.cols;
                     const float sa = (r - 0.5f * (m.rows - 1)) * m.pitch, sb = (c - 0.5f * (m.cols - 1)) * m.pitch;
                     float ut = ut_s[j], ub = ub_s[j];
@@ -415,7 +424,7 @@ __global__ void __launch_bounds__(kMarkerThreads) marker_kernel(const MarkerArgs
         m.anchor_obj[pad] = oid;
     }
     const int W = 2 * m.radius + 1;
-    for (int j = threadIdx.x; j < M; j += kMarkerThreads) {
+    for (int j = threadIdx.x; j < M; j += NT) {
         const int r = j / m.cols, c = j - r * m.cols;
         float un = 0.f, ut = 0.f, uv = 0.f;
         for (int di = -m.radius; di <= m.radius; ++di) {
@@ -442,10 +451,15 @@ __global__ void __launch_bounds__(kMarkerThreads) marker_kernel(const MarkerArgs
     }
 }
 
-cudaError_t launch_markers(const MarkerArgs& m, cudaStream_t s) {
+cudaError_t launch_markers(const MarkerArgs& m, int threads, cudaStream_t s) {
     const int n = m.n_envs * m.pads_per_env;
     if (n == 0) return cudaSuccess;
-    marker_kernel<<<n, kMarkerThreads, 0, s>>>(m);
+    switch (threads) {
+    case 128: marker_kernel<128><<<n, 128, 0, s>>>(m); break;
+    case 256: marker_kernel<256><<<n, 256, 0, s>>>(m); break;
+    case 512: marker_kernel<512><<<n, 512, 0, s>>>(m); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

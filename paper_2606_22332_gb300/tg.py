@@ -101,15 +101,20 @@ class StepInputs(C.Structure):
 
 
 class TuneCandidate(C.Structure):
-    _fields_ = [("schedule", C.c_int32), ("sorted", C.c_int32), ("ms_per_step", C.c_double)]
+    _fields_ = [("schedule", C.c_int32), ("sorted", C.c_int32), ("ms_per_step", C.c_double),
+                ("kernel", C.c_int32), ("threads", C.c_int32)]
 
 
 class TuneReport(C.Structure):
-    _fields_ = [("n", C.c_int32), ("chosen", C.c_int32), ("cand", TuneCandidate * 16)]
+    _fields_ = [("n", C.c_int32), ("chosen", C.c_int32), ("sensor_chosen", C.c_int32 * 3),
+                ("cand", TuneCandidate * 32)]
 
 
 # step-kernel schedules (tg_schedule), by name
 SCHEDULES = ("grid", "persistent", "pipe1024", "pipe768", "pipe512")
+# sensor kernels with a tuned launch shape (tg_sensor_kernel), by name
+SENSOR_KERNELS = ("prox", "pc_prox", "markers")
+SENSOR_THREADS = (128, 256, 512)
 
 
 _vp, _i32, _sz = C.c_void_p, C.c_int32, C.c_size_t
@@ -140,6 +145,8 @@ _lib.tg_graph_seek.argtypes = [_vp, C.c_uint32, C.c_double, C.c_double, _vp]
 _lib.tg_graph_release.argtypes = [_vp]
 _lib.tg_set_schedule.argtypes = [_vp, _i32, _i32]
 _lib.tg_get_schedule.argtypes = [_vp, C.POINTER(_i32), C.POINTER(_i32)]
+_lib.tg_set_sensor_threads.argtypes = [_vp, _i32, _i32]
+_lib.tg_get_sensor_threads.argtypes = [_vp, _i32, C.POINTER(_i32)]
 _lib.tg_autotune.argtypes = [_vp, C.POINTER(StepInputs), _i32, C.POINTER(TuneReport), _vp]
 _lib.tg_object_info.argtypes = [_vp, _i32, C.POINTER(_i32), C.POINTER(C.c_double)]
 _lib.tg_nsdf_create.argtypes = [_vp, _vp, C.c_uint64, C.POINTER(_vp)]
@@ -172,7 +179,8 @@ for _f in ("tg_create_scene", "tg_upload_objects", "tg_reset_envs", "tg_step_sen
            "tg_get_buffer", "tg_sync", "tg_save_state", "tg_load_state", "tg_bake_grid", "tg_mesh_sdf",
            "tg_profile_enable", "tg_profile_read", "tg_mesh_sdf_noalloc", "tg_graph_capture", "tg_graph_launch",
            "tg_graph_seek", "tg_graph_release", "tg_set_schedule", "tg_get_schedule", "tg_autotune", "tg_object_info",
-           "tg_nsdf_create", "tg_nsdf_set_params", "tg_nsdf_get_params", "tg_nsdf_eval", "tg_nsdf_loss_grad",
+           "tg_set_sensor_threads", "tg_get_sensor_threads", "tg_nsdf_create", "tg_nsdf_set_params",
+           "tg_nsdf_get_params", "tg_nsdf_eval", "tg_nsdf_loss_grad",
            "tg_nsdf_train", "tg_nsdf_probe", "tg_temp_create", "tg_temp_reset", "tg_temp_set", "tg_temp_step",
            "tg_temp_read", "tg_temp_buffer", "tg_contact_area", "tg_mesh_bvh_create", "tg_raycast_depth"):
     getattr(_lib, _f).restype = C.c_int
@@ -181,7 +189,8 @@ EXPORTED = ["tg_create_scene", "tg_destroy_scene", "tg_max_link_taxels", "tg_upl
             "tg_step_sensors", "tg_read_taxels", "tg_channel_bytes", "tg_get_buffer", "tg_sync", "tg_last_error",
             "tg_save_state", "tg_load_state", "tg_bake_grid", "tg_mesh_sdf", "tg_profile_enable", "tg_profile_read",
             "tg_mesh_sdf_noalloc", "tg_graph_capture", "tg_graph_launch", "tg_graph_seek", "tg_graph_release",
-            "tg_set_schedule", "tg_get_schedule", "tg_autotune", "tg_object_info", "tg_nsdf_create",
+            "tg_set_schedule", "tg_get_schedule", "tg_set_sensor_threads", "tg_get_sensor_threads", "tg_autotune",
+            "tg_object_info", "tg_nsdf_create",
             "tg_nsdf_destroy", "tg_nsdf_set_params", "tg_nsdf_get_params", "tg_nsdf_eval", "tg_nsdf_loss_grad",
             "tg_nsdf_train", "tg_nsdf_probe", "tg_nsdf_last_error", "tg_temp_create", "tg_temp_destroy",
             "tg_temp_reset", "tg_temp_set", "tg_temp_step", "tg_temp_read", "tg_temp_buffer", "tg_contact_area",
@@ -431,15 +440,41 @@ class Scene:
         _check(_lib.tg_get_schedule(self.h, C.byref(p), C.byref(s)), self.h)
         return {"schedule": SCHEDULES[int(p.value)], "sorted": int(s.value)}
 
+    def set_sensor_threads(self, kernel, threads: int):
+        """Threads per CTA (128, 256 or 512) of a sensor kernel (a name of SENSOR_KERNELS or its index)."""
+        k = SENSOR_KERNELS.index(kernel) if isinstance(kernel, str) else int(kernel)
+        _check(_lib.tg_set_sensor_threads(self.h, k, int(threads)), self.h)
+
+    def sensor_threads(self):
+        out = {}
+        for k, name in enumerate(SENSOR_KERNELS):
+            t = _i32()
+            _check(_lib.tg_get_sensor_threads(self.h, k, C.byref(t)), self.h)
+            out[name] = int(t.value)
+        return out
+
     def autotune(self, inputs: dict, steps: int = 3, stream=None):
-        """Time every step schedule on these inputs, keep the fastest; returns the report as a dict."""
+        """Time every step schedule on these inputs and keep the fastest, then
+        every launch shape of each sensor kernel the scene runs; returns the
+        report as a dict (step candidates under "candidates", the sensor
+        kernels' under "sensor_candidates")."""
         I, keep = self._inputs(inputs)
         self._keep_inputs = keep
         R = TuneReport()
         _check(_lib.tg_autotune(self.h, C.byref(I), int(steps), C.byref(R), _stream(stream)), self.h)
-        cands = [{"schedule": SCHEDULES[R.cand[i].schedule], "sorted": R.cand[i].sorted,
-                  "ms_per_step": R.cand[i].ms_per_step} for i in range(R.n)]
-        return {"candidates": cands, "chosen": cands[R.chosen]}
+        step_c, sensor_c = [], []
+        for i in range(R.n):
+            c = R.cand[i]
+            if c.kernel < 0:
+                step_c.append({"schedule": SCHEDULES[c.schedule], "sorted": c.sorted, "threads": c.threads,
+                               "ms_per_step": c.ms_per_step})
+            else:
+                sensor_c.append({"kernel": SENSOR_KERNELS[c.kernel], "threads": c.threads,
+                                 "ms_per_step": c.ms_per_step})
+        chosen_sensor = {SENSOR_KERNELS[k]: R.cand[R.sensor_chosen[k]].threads
+                         for k in range(3) if R.sensor_chosen[k] >= 0}
+        return {"candidates": step_c, "chosen": step_c[R.chosen], "sensor_candidates": sensor_c,
+                "sensor_chosen": chosen_sensor}
 
     def channel_bytes(self, ch: int) -> int:
         return int(_lib.tg_channel_bytes(self.h, ch))

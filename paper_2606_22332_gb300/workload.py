@@ -811,6 +811,24 @@ def config2(seed: int = 20260003, n_envs: int = 20480, n_objects: int = 64, n_gr
     return add_pads(wl)
 
 
+CONFIG4_DR = {"mu": (0.4, 1.2), "k": (5e3, 2e4), "scale": (0.8, 1.2)}
+
+
+def config4(seed: int = 20260005, n_envs: int = 20480, n_objects: int = 256, n_grid: int = 96,
+            steps: int = 500, faces=(3000, 6000)) -> Workload:
+    """Mixed workload with learned parts: uneven T_e ~ U{200..1000} over
+    L_e ~ U{10..20} links, 256 objects (96^3 FP16 grid specs; the caller
+    trains a network per object), per-step domain randomisation of mu, k and
+    the object scale (CONFIG4_DR)."""
+    rng = np.random.default_rng(seed)
+    objects = config1_objects(rng, n_objects, n_grid, fp16=True, faces=faces)
+    env_obj = rng.integers(0, n_objects, n_envs)
+    lattices = uneven_lattices(rng, n_envs)
+    params = default_params(seed)
+    params["dr"] = dict(CONFIG4_DR)
+    return _assemble("config4", rng, objects, env_obj, lattices, params, steps=steps, max_links=20, arc=PAD_ARC)
+
+
 # ---------------------------------------------------------------- TemperatureGrid
 TEMP_SILICONE = (0.2, 1100.0, 1500.0, 0.9, 10.0, 0.05, 22.0)   # k, rho, c_p, emissivity, h, tau, base (C)
 TEMP_ALUMINIUM = (200.0, 2700.0, 900.0, 0.1, 10.0, 0.0, 22.0)
