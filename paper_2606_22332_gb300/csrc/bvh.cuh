@@ -243,90 +243,4 @@ __host__ __device__ inline void bvh_within(const BvhNode* nodes, const BvhTri* t
     }
 }
 
-#ifdef __CUDACC__
-// Warp-coherent forms of the two walks, for probes that lie close together
-// (the taxels of a link): the 32 lanes walk one tree path together, a node
-// visited when any lane's query still reaches it, each lane keeping its own
-// best triangle.  Every lane of the warp calls them (a lane with nothing to
-// find passes r2 = 0); the node, the stack and every branch on them are the
-// same in all lanes, so the lanes never diverge on the walk itself, only on
-// a leaf's triangle updates.  The minimum over a set of FP32 distances does
-// not depend on the order the set is visited in, so the nearest distance is
-// that of the per-lane walk; among triangles at exactly that distance either
-// may be returned.
-constexpr unsigned kBvhWarp = 0xffffffffu;
-
-__device__ __forceinline__ int bvh_nearest_warp(const BvhNode* nodes, const BvhTri* tris, float px, float py,
-                                                float pz, float r2, float* best_d2) {
-    float best = r2;
-    int bi = -1;
-    int stack[kBvhStack];
-    int sp = 0;
-    int node = 0;
-    if (!__any_sync(kBvhWarp, bvh_box_d2(nodes[0], px, py, pz) < best)) {
-        *best_d2 = best;
-        return -1;
-    }
-    for (;;) {
-        const BvhNode nd = nodes[node];
-        int next = -1;
-        if (nd.count > 0) {
-            for (int k = nd.first; k < nd.first + nd.count; ++k) {
-                const float d2 = bvh_tri_d2(tris[k], px, py, pz);
-                if (d2 < best) {
-                    best = d2;
-                    bi = k;
-                }
-            }
-        } else {
-            const int l = nd.first;
-            const float dl = bvh_box_d2(nodes[l], px, py, pz), dr = bvh_box_d2(nodes[l + 1], px, py, pz);
-            const bool want_l = dl < best, want_r = dr < best;
-            const unsigned any = __ballot_sync(kBvhWarp, want_l || want_r);
-            if (any) {
-                const bool wl = __any_sync(kBvhWarp, want_l), wr = __any_sync(kBvhWarp, want_r);
-                if (wl && wr) {
-                    // first the child nearer for most of the lanes that want one
-                    const int left_votes = __popc(__ballot_sync(kBvhWarp, (want_l || want_r) && dl <= dr));
-                    const bool left_first = 2 * left_votes >= __popc(any);
-                    next = left_first ? l : l + 1;
-                    if (sp < kBvhStack) stack[sp++] = left_first ? l + 1 : l;  // depth < kBvhStack (build)
-                } else {
-                    next = wl ? l : l + 1;
-                }
-            }
-        }
-        // the next pending subtree that some lane's best triangle still reaches
-        while (next < 0 && sp > 0) {
-            const int c = stack[--sp];
-            if (__any_sync(kBvhWarp, bvh_box_d2(nodes[c], px, py, pz) < best)) next = c;
-        }
-        if (next < 0) break;
-        node = next;
-    }
-    *best_d2 = best;
-    return bi;
-}
-
-template <class Visit>
-__device__ __forceinline__ void bvh_within_warp(const BvhNode* nodes, const BvhTri* tris, float px, float py, float pz,
-                                                float r2, Visit visit) {
-    int stack[kBvhStack];
-    int sp = 0;
-    if (!__any_sync(kBvhWarp, bvh_box_d2(nodes[0], px, py, pz) < r2)) return;
-    stack[sp++] = 0;
-    while (sp > 0) {
-        const BvhNode nd = nodes[stack[--sp]];
-        if (nd.count > 0) {
-            for (int k = nd.first; k < nd.first + nd.count; ++k)
-                if (bvh_tri_d2(tris[k], px, py, pz) < r2) visit(k);
-        } else {
-            for (int c = 0; c < 2; ++c)
-                if (__any_sync(kBvhWarp, bvh_box_d2(nodes[nd.first + c], px, py, pz) < r2) && sp < kBvhStack)
-                    stack[sp++] = nd.first + c;
-        }
-    }
-}
-#endif
-
 }  // namespace tg

@@ -24,9 +24,6 @@
 
 namespace tg {
 
-// One probe per thread, each walking the tree on its own (the probes of
-// the stand-alone query come in any order; the warp-coherent walk measured
-// slower here).
 __global__ void raycast_depth_kernel(const BvhNode* __restrict__ nodes, const BvhTri* __restrict__ tris,
                                      const int32_t* __restrict__ face_id, const float* __restrict__ probes,
                                      const float* __restrict__ radius, int64_t n, float scale, float* depth,
@@ -91,14 +88,10 @@ __global__ void __launch_bounds__(kRayStepThreads)
     }
     __syncthreads();
     const int64_t T = a.n_taxels;
-    // a warp takes 32 consecutive taxels (one link region) per round, every
-    // lane through both walks
-    const int lane = threadIdx.x & 31;
-    for (int b = threadIdx.x - lane; b < n; b += blockDim.x) {
-        const int i = b + lane;
-        const bool valid = i < n;
-        const int64_t g = it.taxel_begin + (valid ? i : 0);
-        const float R = valid ? a.R[g] : 0.0f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int64_t g = it.taxel_begin + i;
+        const float R = a.R[g];
+        if (!(R > 0.0f)) continue;
         int lo = 0, hi = nl - 1;  // link of taxel i: last start <= i
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -111,9 +104,15 @@ __global__ void __launch_bounds__(kRayStepThreads)
         const float qy = fmaf(rec[3], x0, fmaf(rec[4], x1, fmaf(rec[5], x2, rec[19])));
         const float qz = fmaf(rec[6], x0, fmaf(rec[7], x1, fmaf(rec[8], x2, rec[20])));
         const float s = rec[38];
-        const float reach = R > 0.0f ? (R + 1e-6f) / s : 0.0f;
+        const float reach = (R + 1e-6f) / s;
         float best;
-        const int k = bvh_nearest_warp(nodes, tris, qx, qy, qz, reach * reach, &best);
+        const int k = bvh_nearest(nodes, tris, qx, qy, qz, reach * reach, &best);
+        if (k < 0) {
+            phi_hi[g] = R + 1.0f;
+            phi_lo[g] = 0.0f;
+            nrm[g] = nrm[T + g] = nrm[2 * T + g] = 0.0f;
+            continue;
+        }
         // the compensated probe centre, as the step's refinement forms it
         df qd[3];
 #pragma unroll
@@ -125,10 +124,10 @@ __global__ void __launch_bounds__(kRayStepThreads)
             qd[r] = acc;
         }
         const V3<dfn> pd{dfn{qd[0]}, dfn{qd[1]}, dfn{qd[2]}};
-        const float lim = k >= 0 ? sqrtf(best) + 1e-6f / s : 0.0f;
+        const float lim = sqrtf(best) + 1e-6f / s;
         df bd = df_from(INFINITY);
         int bk = k, bf = 0x7fffffff;
-        bvh_within_warp(nodes, tris, qx, qy, qz, lim * lim, [&](int kk) {
+        bvh_within(nodes, tris, qx, qy, qz, lim * lim, [&](int kk) {
             const BvhTri& t = tris[kk];
             const V3<dfn> A{mk(t.a.x), mk(t.a.y), mk(t.a.z)}, B{mk(t.b.x), mk(t.b.y), mk(t.b.z)},
                 C{mk(t.c.x), mk(t.c.y), mk(t.c.z)};
@@ -142,13 +141,6 @@ __global__ void __launch_bounds__(kRayStepThreads)
                 bf = fid;
             }
         });
-        if (!valid || !(R > 0.0f)) continue;
-        if (k < 0) {
-            phi_hi[g] = R + 1.0f;
-            phi_lo[g] = 0.0f;
-            nrm[g] = nrm[T + g] = nrm[2 * T + g] = 0.0f;
-            continue;
-        }
         const df phi = df_mul_f(df_sqrt(bd), s);
         phi_hi[g] = phi.hi;
         phi_lo[g] = phi.lo;
