@@ -76,7 +76,7 @@ def parse():
     ap.add_argument("--config4-objects", type=int, default=256, help="distinct objects of the configuration-4 line")
     ap.add_argument("--config4-steps", type=int, default=500, help="graph-replayed steps of the configuration-4 line")
     ap.add_argument("--config4-points", type=int, default=1_000_000, help="labelled training points per object")
-    ap.add_argument("--config4-train-steps", type=int, default=2000, help="Adam steps per object")
+    ap.add_argument("--config4-train-steps", type=int, default=3000, help="Adam steps per object")
     ap.add_argument("--config4-streams", type=int, default=8, help="networks trained at once, one stream each")
     ap.add_argument("--neural-objects", type=int, default=64, help="objects given a learned SDF (0: skip the line)")
     ap.add_argument("--neural-points", type=int, default=2_000_000, help="labelled training points per object")
@@ -312,24 +312,31 @@ def train_networks(args, objects, dev, n_points, n_steps, n_streams, seed0):
     import paper_2606_22332_gb300.tg as tg
     from paper_2606_22332_gb300 import workload as W
 
+    from concurrent.futures import ThreadPoolExecutor
+
     nets, stats = [None] * len(objects), [None] * len(objects)
     streams = [torch.cuda.Stream(device=dev) for _ in range(max(1, n_streams))]
+    # the training loop is bound by its launches on the host: each network's
+    # loop runs in its own host thread (the library call releases the
+    # interpreter lock) on its own stream
+    pool = ThreadPoolExecutor(max_workers=len(streams))
     for g0 in range(0, len(objects), len(streams)):
         group = list(range(g0, min(g0 + len(streams), len(objects))))
-        keep = []
+        jobs = []
         for k, st in zip(group, streams):
             o = objects[k]
             rng = np.random.default_rng(seed0 + k)
             with torch.cuda.stream(st):
                 P = torch.from_numpy(W.sdf_sample_points(rng, o.verts, o.faces, o.lo, o.hi, n_points)).to(dev)
                 lab, _ = tg.mesh_sdf(o.verts, o.faces, P, with_grad=False, stream=st.cuda_stream)
-                net = tg.Nsdf(o.lo, o.hi, seed=k)
-                net.train(P, lab * 1e3, steps=n_steps, batch=1 << 14, lr0=1e-2, lr_final=3e-4, seed=k,
-                          record_losses=False, stream=st.cuda_stream)
-            nets[k] = net
-            keep.append((P, lab))
+                lab_mm = lab * 1e3
+            nets[k] = tg.Nsdf(o.lo, o.hi, seed=k)
+            jobs.append((pool.submit(nets[k].train, P, lab_mm, steps=n_steps, batch=1 << 14, lr0=1e-2,
+                                     lr_final=3e-4, seed=k, record_losses=False, stream=st.cuda_stream), P, lab_mm))
+        for j, _, _ in jobs:
+            j.result()
         torch.cuda.synchronize()
-        del keep
+        del jobs
         for k in group:
             o = objects[k]
             probe = torch.from_numpy(W.sdf_sample_points(np.random.default_rng(seed0 + 50000 + k), o.verts, o.faces,

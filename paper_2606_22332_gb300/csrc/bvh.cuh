@@ -8,6 +8,7 @@
 #pragma once
 #include <algorithm>
 #include <cmath>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -28,6 +29,7 @@ struct BvhTri {
 
 constexpr int kBvhLeaf = 4;
 constexpr int kBvhStack = 64;
+constexpr int kBvhLbCells = 32;  // cells per axis of the distance lower-bound grid
 
 __host__ __device__ inline float bvh_box_d2(const BvhNode& nd, float px, float py, float pz) {
     const float dx = fmaxf(fmaxf(nd.lo[0] - px, px - nd.hi[0]), 0.0f);
@@ -241,6 +243,41 @@ __host__ __device__ inline void bvh_within(const BvhNode* nodes, const BvhTri* t
                 if (bvh_box_d2(nodes[nd.first + c], px, py, pz) < r2 && sp < kBvhStack) stack[sp++] = nd.first + c;
         }
     }
+}
+
+// Lower bound on the distance from any point of each cell of a
+// kBvhLbCells^3 grid over the box [lo, hi] to the mesh: the FP32 distance
+// from the cell centre to the nearest triangle, less the cell's half
+// diagonal and a relative margin of 1e-6 of the box (covering the FP32
+// distance's rounding), floored at 0.  For a point p outside the box, the
+// cell of its projection onto the box bounds the distance of p too (the
+// projection onto a convex set holding the mesh moves no point farther from
+// it).  Cells are filled by `threads` host threads.
+inline void bvh_lower_bounds(const std::vector<BvhNode>& nodes, const std::vector<BvhTri>& tris, const float lo[3],
+                             const float hi[3], float* out, int threads) {
+    const int n = kBvhLbCells;
+    double h[3], ext2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        h[a] = ((double)hi[a] - (double)lo[a]) / n;
+        ext2 += ((double)hi[a] - lo[a]) * ((double)hi[a] - lo[a]);
+    }
+    const double half_diag = 0.5 * std::sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+    const double margin = 1e-6 * std::sqrt(ext2);
+    auto work = [&](int t) {
+        for (int c = t; c < n * n * n; c += threads) {
+            const int i = c % n, j = (c / n) % n, k = c / (n * n);
+            const float px = (float)(lo[0] + (i + 0.5) * h[0]), py = (float)(lo[1] + (j + 0.5) * h[1]),
+                        pz = (float)(lo[2] + (k + 0.5) * h[2]);
+            float best;
+            bvh_nearest(nodes.data(), tris.data(), px, py, pz, INFINITY, &best);
+            const double lb = std::sqrt((double)best) - half_diag - margin;
+            out[c] = lb > 0.0 ? std::nextafter((float)lb, 0.0f) : 0.0f;
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < threads; ++t) pool.emplace_back(work, t);
+    work(0);
+    for (auto& th : pool) th.join();
 }
 
 }  // namespace tg

@@ -90,6 +90,11 @@ struct alignas(16) ObjDev {
     const void* bvh_nodes;
     const void* bvh_tris;
     const int32_t* bvh_face;
+    // and a coarse grid over the mesh's box of lower bounds on the distance
+    // from any point of a cell to the mesh ([kBvhLbCells^3], cell-major x
+    // fastest), to pass over probes no triangle can reach
+    const float* bvh_lb;
+    float bvh_lb_lo[3], bvh_lb_inv_h[3];
     // learned SDF (kind TG_OBJ_NEURAL; the grid fields hold its fallback grid)
     float nlo[3], nhi[3], ninv_ext[3];
     const uint32_t* ntable;           // [16][2^16] binary16 pairs

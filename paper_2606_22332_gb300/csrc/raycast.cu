@@ -69,6 +69,17 @@ __global__ void raycast_depth_kernel(const BvhNode* __restrict__ nodes, const Bv
 // items of other objects return at once.
 constexpr int kRayStepThreads = 256;
 
+// link of item taxel i: the last link start <= i
+__device__ __forceinline__ int link_in(const int* start, int nl, int i) {
+    int lo = 0, hi = nl - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 __global__ void __launch_bounds__(kRayStepThreads)
     raycast_step_query_kernel(const StepArgs a, float* phi_hi, float* phi_lo, float* nrm) {
     __shared__ float rec_s[kItemMaxLinks][kLinkRec];
@@ -88,17 +99,45 @@ __global__ void __launch_bounds__(kRayStepThreads)
     }
     __syncthreads();
     const int64_t T = a.n_taxels;
+    // pass 1: taxels whose lower-bound cell is out of reach are clear (no
+    // triangle within R); the others are listed for the tree walk, so that
+    // the walks run on whole warps
+    __shared__ int16_t queue_s[kItemCap];
+    __shared__ int nq_s;
+    if (threadIdx.x == 0) nq_s = 0;
+    __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int64_t g = it.taxel_begin + i;
         const float R = a.R[g];
         if (!(R > 0.0f)) continue;
-        int lo = 0, hi = nl - 1;  // link of taxel i: last start <= i
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (start_s[mid] <= i) lo = mid;
-            else hi = mid - 1;
+        const float* rec = rec_s[link_in(start_s, nl, i)];
+        const float x0 = a.x[g], x1 = a.y[g], x2 = a.z[g];
+        const float q[3] = {fmaf(rec[0], x0, fmaf(rec[1], x1, fmaf(rec[2], x2, rec[18]))),
+                            fmaf(rec[3], x0, fmaf(rec[4], x1, fmaf(rec[5], x2, rec[19]))),
+                            fmaf(rec[6], x0, fmaf(rec[7], x1, fmaf(rec[8], x2, rec[20])))};
+        const float reach = (R + 1e-6f) / rec[38];
+        int c[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            const float u = (q[ax] - op->bvh_lb_lo[ax]) * op->bvh_lb_inv_h[ax];  // NaN -> cell 0
+            c[ax] = min(max((int)floorf(fminf(fmaxf(u, 0.0f), (float)kBvhLbCells)), 0), kBvhLbCells - 1);
         }
-        const float* rec = rec_s[lo];
+        if (op->bvh_lb[(c[2] * kBvhLbCells + c[1]) * kBvhLbCells + c[0]] >= reach) {
+            phi_hi[g] = R + 1.0f;
+            phi_lo[g] = 0.0f;
+            nrm[g] = nrm[T + g] = nrm[2 * T + g] = 0.0f;
+        } else {
+            queue_s[atomicAdd(&nq_s, 1)] = (int16_t)i;
+        }
+    }
+    __syncthreads();
+    // pass 2: the listed taxels, one per thread
+    const int nq = nq_s;
+    for (int k = threadIdx.x; k < nq; k += blockDim.x) {
+        const int i = queue_s[k];
+        const int64_t g = it.taxel_begin + i;
+        const float R = a.R[g];
+        const float* rec = rec_s[link_in(start_s, nl, i)];
         const float x0 = a.x[g], x1 = a.y[g], x2 = a.z[g];
         const float qx = fmaf(rec[0], x0, fmaf(rec[1], x1, fmaf(rec[2], x2, rec[18])));
         const float qy = fmaf(rec[3], x0, fmaf(rec[4], x1, fmaf(rec[5], x2, rec[19])));
@@ -106,8 +145,8 @@ __global__ void __launch_bounds__(kRayStepThreads)
         const float s = rec[38];
         const float reach = (R + 1e-6f) / s;
         float best;
-        const int k = bvh_nearest(nodes, tris, qx, qy, qz, reach * reach, &best);
-        if (k < 0) {
+        const int k0 = bvh_nearest(nodes, tris, qx, qy, qz, reach * reach, &best);
+        if (k0 < 0) {
             phi_hi[g] = R + 1.0f;
             phi_lo[g] = 0.0f;
             nrm[g] = nrm[T + g] = nrm[2 * T + g] = 0.0f;
@@ -126,7 +165,7 @@ __global__ void __launch_bounds__(kRayStepThreads)
         const V3<dfn> pd{dfn{qd[0]}, dfn{qd[1]}, dfn{qd[2]}};
         const float lim = sqrtf(best) + 1e-6f / s;
         df bd = df_from(INFINITY);
-        int bk = k, bf = 0x7fffffff;
+        int bk = k0, bf = 0x7fffffff;
         bvh_within(nodes, tris, qx, qy, qz, lim * lim, [&](int kk) {
             const BvhTri& t = tris[kk];
             const V3<dfn> A{mk(t.a.x), mk(t.a.y), mk(t.a.z)}, B{mk(t.b.x), mk(t.b.y), mk(t.b.z)},
@@ -164,6 +203,16 @@ const char* upload_mesh_bvh(const float* verts, int nv, const int32_t* faces, in
     std::vector<BvhTri> tris;
     std::vector<int32_t> fid;
     if (const char* m = bvh_build(verts, nv, faces, nf, nodes, tris, fid)) return m;
+    // the lower-bound grid over the mesh's box (a flat axis gets a 1 nm extent)
+    float lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = nodes[0].lo[a];
+        hi[a] = std::max(nodes[0].hi[a], lo[a] + 1e-9f);
+    }
+    std::vector<float> lbg((size_t)kBvhLbCells * kBvhLbCells * kBvhLbCells);
+    bvh_lower_bounds(nodes, tris, lo, hi, lbg.data(),
+                     (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency())));
+    float* dl = nullptr;
     BvhNode* dn = nullptr;
     BvhTri* dt = nullptr;
     int32_t* df_ = nullptr;
@@ -176,10 +225,18 @@ const char* upload_mesh_bvh(const float* verts, int nv, const int32_t* faces, in
     if (e == cudaSuccess) e = cudaMemcpy(dn, nodes.data(), sizeof(BvhNode) * nodes.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(dt, tris.data(), sizeof(BvhTri) * tris.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(df_, fid.data(), sizeof(int32_t) * fid.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&dl, sizeof(float) * lbg.size());
+    if (dl) bufs->push_back(dl);
+    if (e == cudaSuccess) e = cudaMemcpy(dl, lbg.data(), sizeof(float) * lbg.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return "mesh tree upload failed";
     t->bvh_nodes = dn;
     t->bvh_tris = dt;
     t->bvh_face = df_;
+    t->bvh_lb = dl;
+    for (int a = 0; a < 3; ++a) {
+        t->bvh_lb_lo[a] = lo[a];
+        t->bvh_lb_inv_h[a] = (float)kBvhLbCells / (hi[a] - lo[a]);
+    }
     return nullptr;
 }
 

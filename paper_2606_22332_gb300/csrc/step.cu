@@ -128,14 +128,14 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
             S.start[nl] = n;
         }
     }
-    // the object descriptor, 8 bytes per thread of warp 1
-    static_assert(sizeof(ObjDev) % 8 == 0 && sizeof(ObjDev) / 8 <= 32 && NT >= 64, "object copy by one warp");
-    if (tid >= 32 && tid < 32 + (int)(sizeof(ObjDev) / 8)) {
+    // the object descriptor, 16 bytes per thread of warp 1
+    static_assert(sizeof(ObjDev) % 16 == 0 && sizeof(ObjDev) / 16 <= 32 && NT >= 64, "object copy by one warp");
+    if (tid >= 32 && tid < 32 + (int)(sizeof(ObjDev) / 16)) {
         // the sorted copy of the items carries the object (one load fewer
         // on the prologue's dependent chain)
         int oid = a.items_sorted ? it.pad : a.obj_id[e];
         oid = min(max(oid, 0), a.n_objects - 1);
-        reinterpret_cast<uint2*>(&S.obj)[tid - 32] = reinterpret_cast<const uint2*>(a.objects + oid)[tid - 32];
+        reinterpret_cast<uint4*>(&S.obj)[tid - 32] = reinterpret_cast<const uint4*>(a.objects + oid)[tid - 32];
     }
     if (tid == 0) {
         S.nq = 0;
