@@ -115,6 +115,14 @@ __global__ void __launch_bounds__(kRayStepThreads)
         const float q[3] = {fmaf(rec[0], x0, fmaf(rec[1], x1, fmaf(rec[2], x2, rec[18]))),
                             fmaf(rec[3], x0, fmaf(rec[4], x1, fmaf(rec[5], x2, rec[19]))),
                             fmaf(rec[6], x0, fmaf(rec[7], x1, fmaf(rec[8], x2, rec[20])))};
+        if (!(isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]))) {
+            // a non-finite pose: phi is NaN, which the step kernel counts
+            // (TG_ERR_NUMERIC) and reads as clear
+            phi_hi[g] = __int_as_float(0x7fc00000);
+            phi_lo[g] = 0.0f;
+            nrm[g] = nrm[T + g] = nrm[2 * T + g] = 0.0f;
+            continue;
+        }
         const float reach = (R + 1e-6f) / rec[38];
         int c[3];
 #pragma unroll

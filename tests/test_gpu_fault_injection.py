@@ -74,6 +74,30 @@ def test_nan_pose_is_reported_then_a_clean_step_recovers(tg, schedule):
     sc.close()
 
 
+def test_nan_pose_is_reported_with_the_raycast_backend(tg):
+    """The raycast backend's pre-pass hands a NaN distance to the step for a
+    probe with a non-finite pose, so the count reaches tg_sync as with the
+    signed-distance backend."""
+    wl = W.config0(seed=41, n_envs=6)
+    wl.params = dict(wl.params, depth_backend="raycast")
+    e = int(np.flatnonzero([wl.objects[k].kind == "mesh" for k in wl.obj_id])[0])
+    sc = tg.Scene.from_workload(wl)
+    sc.upload_objects(wl.objects)
+    bad = wl.inputs(0)
+    bad["link_pose"] = wl.link_pose.copy()
+    bad["link_pose"][e, 2, 1] = np.nan
+    sc.step(bad)
+    with pytest.raises(tg.TGError) as err:
+        sc.sync()
+    L = wl.max_links
+    n_link = int(wl.link_rows[e * L + 2] * wl.link_cols[e * L + 2])
+    n_act = int((wl.R[int(wl.taxel_offsets[e]) + sum(int(wl.link_rows[e * L + k] * wl.link_cols[e * L + k])
+                                                      for k in range(2)):][:n_link] > 0).sum())
+    assert err.value.status == TG_ERR_NUMERIC and f"({n_act} taxel queries)" in str(err.value)
+    assert np.isfinite(sc.read(tg.CH_FORCE_TORQUE)).all()
+    sc.close()
+
+
 def test_object_index_out_of_range_is_rejected_on_the_host(tg):
     wl = _workload()
     sc = tg.Scene.from_workload(wl)
