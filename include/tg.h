@@ -328,6 +328,12 @@ typedef struct {
 } tg_step_inputs;
 
 /* One sensor step for every env: enqueued on `stream`, asynchronous.
+   Inputs in host memory are copied to the device on the scene's own copy
+   stream, into one of two staging sets used in turn, so that a step's
+   copies overlap the kernels of the step before it; `stream` waits for
+   them.  As with any asynchronous copy, the host buffers must not change
+   until `stream` has passed this step (pinned buffers make the copies
+   asynchronous; pageable ones are copied before the call returns).
    Errors: TG_ERR_STATE (no objects), TG_ERR_INVALID_ARG (NULL input, or an
    obj_id in host memory outside [0, n_objects): nothing runs; object
    indices in device memory are clamped into that range by the kernels),

@@ -66,10 +66,16 @@ struct tg_scene {
     unsigned* err = nullptr;
     float* link_rec = nullptr;
     float* ring = nullptr;            // [ring_k][8][T] read-delay history (read delay on)
-    // staging of host inputs
-    float *s_link_pose = nullptr, *s_link_vel = nullptr, *s_obj_pose = nullptr, *s_obj_vel = nullptr;
-    float* s_env_params = nullptr;
-    int32_t* s_obj_id = nullptr;
+    // staging of host inputs: two sets, filled in turn on the copy stream so
+    // that a step's host-to-device copies overlap the previous step's kernels
+    // (set k is refilled once the kernels of the step that read it are done)
+    float *s_link_pose[2] = {}, *s_link_vel[2] = {}, *s_obj_pose[2] = {}, *s_obj_vel[2] = {};
+    float* s_env_params[2] = {};
+    int32_t* s_obj_id[2] = {};
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t staged_ev[2] = {nullptr, nullptr}, used_ev[2] = {nullptr, nullptr};
+    bool used_rec[2] = {false, false};
+    int next_set = 0;
     uint8_t* s_mask = nullptr;
     uint8_t* s_contact = nullptr;
     Item* items_sorted = nullptr;     // per-step object-sorted copy of the items
@@ -530,12 +536,17 @@ tg_status tg_create_scene(const tg_scene_desc* d, tg_scene** out) {
     CKC(dalloc(&s->link_count, EL * 2));
     CKC(dalloc(&s->err, 4));
     CKC(dalloc(&s->link_rec, EL * kLinkRec));
-    CKC(dalloc(&s->s_link_pose, EL * 7));
-    CKC(dalloc(&s->s_link_vel, EL * 6));
-    CKC(dalloc(&s->s_obj_pose, (size_t)E * 7));
-    CKC(dalloc(&s->s_obj_vel, (size_t)E * 6));
-    CKC(dalloc(&s->s_env_params, (size_t)E * 3));
-    CKC(dalloc(&s->s_obj_id, E));
+    for (int k = 0; k < 2; ++k) {
+        CKC(dalloc(&s->s_link_pose[k], EL * 7));
+        CKC(dalloc(&s->s_link_vel[k], EL * 6));
+        CKC(dalloc(&s->s_obj_pose[k], (size_t)E * 7));
+        CKC(dalloc(&s->s_obj_vel[k], (size_t)E * 6));
+        CKC(dalloc(&s->s_env_params[k], (size_t)E * 3));
+        CKC(dalloc(&s->s_obj_id[k], E));
+        CKC(cudaEventCreateWithFlags(&s->staged_ev[k], cudaEventDisableTiming));
+        CKC(cudaEventCreateWithFlags(&s->used_ev[k], cudaEventDisableTiming));
+    }
+    CKC(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking));
     CKC(dalloc(&s->s_mask, E));
     CKC(dalloc(&s->s_contact, T));
     CKC(dalloc(&s->items_sorted, items.size()));
@@ -672,6 +683,14 @@ void tg_destroy_scene(tg_scene* s) {
     if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
     if (s->graph) cudaGraphDestroy(s->graph);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+    for (int k = 0; k < 2; ++k) {
+        if (s->staged_ev[k]) cudaEventDestroy(s->staged_ev[k]);
+        if (s->used_ev[k]) cudaEventDestroy(s->used_ev[k]);
+        for (void* p : {(void*)s->s_link_pose[k], (void*)s->s_link_vel[k], (void*)s->s_obj_pose[k],
+                        (void*)s->s_obj_vel[k], (void*)s->s_env_params[k], (void*)s->s_obj_id[k]})
+            dfree(p);
+    }
     for (cudaEvent_t e : s->graph_ev)
         if (e) cudaEventDestroy(e);
     free_objects(s);
@@ -679,8 +698,7 @@ void tg_destroy_scene(tg_scene* s) {
     for (cudaEvent_t e : s->ev_pending) cudaEventDestroy(e);
     void* ptrs[] = {s->x, s->y, s->z, s->nx, s->ny, s->nz, s->R, s->items, s->lattice, s->flags, s->hyst_prev,
                     s->hyst_xi, s->drift, s->episode, s->depth_clean, s->depth_noisy, s->dist, s->ft_clean,
-                    s->ft_noisy, s->link_out, s->link_count, s->err, s->link_rec, s->s_link_pose, s->s_link_vel,
-                    s->s_obj_pose, s->s_obj_vel, s->s_env_params, s->s_obj_id, s->s_mask, s->s_contact,
+                    s->ft_noisy, s->link_out, s->link_count, s->err, s->link_rec, s->s_mask, s->s_contact,
                     s->items_sorted, s->metas, s->slots, s->prox_clean, s->prox_noisy, s->pad_link, s->pad_frame,
                     s->marker_u, s->ctl, s->nq_phi, s->nq_grad, s->nq_phi_lo, s->pc_ft, s->anchors, s->anchor_obj,
                     s->ring,
@@ -964,14 +982,30 @@ const char* check_inputs(const tg_scene* s, const tg_step_inputs* in) {
 tg_status enqueue_step(tg_scene* s, const tg_step_inputs* in, cudaStream_t st, bool graph) {
     const size_t EL = (size_t)s->E * s->L;
     PoseArgs pa{};
-    CK(s, stage(in->link_pose, s->s_link_pose, EL * 7, st, &pa.link_pose));
-    CK(s, stage(in->link_vel, s->s_link_vel, EL * 6, st, &pa.link_vel));
-    CK(s, stage(in->obj_pose, s->s_obj_pose, (size_t)s->E * 7, st, &pa.obj_pose));
-    CK(s, stage(in->obj_vel, s->s_obj_vel, (size_t)s->E * 6, st, &pa.obj_vel));
+    // host inputs: outside a capture, copied on the copy stream into the
+    // staging set the step before last used, then `st` waits for them
+    const bool host_in = !(is_device_ptr(in->link_pose) && is_device_ptr(in->link_vel) &&
+                           is_device_ptr(in->obj_pose) && is_device_ptr(in->obj_vel) &&
+                           is_device_ptr(in->obj_id) && (!in->env_params || is_device_ptr(in->env_params)));
+    const bool async_copy = host_in && !graph;
+    const int b = async_copy ? s->next_set : 0;
+    cudaStream_t cs = async_copy ? s->copy_stream : st;
+    if (async_copy) {
+        s->next_set ^= 1;
+        if (s->used_rec[b]) CK(s, cudaStreamWaitEvent(cs, s->used_ev[b], 0));
+    }
+    CK(s, stage(in->link_pose, s->s_link_pose[b], EL * 7, cs, &pa.link_pose));
+    CK(s, stage(in->link_vel, s->s_link_vel[b], EL * 6, cs, &pa.link_vel));
+    CK(s, stage(in->obj_pose, s->s_obj_pose[b], (size_t)s->E * 7, cs, &pa.obj_pose));
+    CK(s, stage(in->obj_vel, s->s_obj_vel[b], (size_t)s->E * 6, cs, &pa.obj_vel));
     pa.env_params = nullptr;
-    if (in->env_params) CK(s, stage(in->env_params, s->s_env_params, (size_t)s->E * 3, st, &pa.env_params));
+    if (in->env_params) CK(s, stage(in->env_params, s->s_env_params[b], (size_t)s->E * 3, cs, &pa.env_params));
     const int32_t* oid = nullptr;
-    CK(s, stage(in->obj_id, s->s_obj_id, (size_t)s->E, st, &oid));
+    CK(s, stage(in->obj_id, s->s_obj_id[b], (size_t)s->E, cs, &oid));
+    if (async_copy) {
+        CK(s, cudaEventRecord(s->staged_ev[b], cs));
+        CK(s, cudaStreamWaitEvent(st, s->staged_ev[b], 0));
+    }
     pa.n_envs = s->E;
     pa.max_links = s->L;
     pa.lattice = s->lattice;
@@ -1038,6 +1072,10 @@ tg_status enqueue_step(tg_scene* s, const tg_step_inputs* in, cudaStream_t st, b
         CK(s, launch_markers(m, s->sensor_threads[2], st));
     }
     if (graph) CK(s, launch_advance_ctl(s->ctl, st));
+    if (async_copy) {  // the step's kernels are the last readers of staging set b
+        CK(s, cudaEventRecord(s->used_ev[b], st));
+        s->used_rec[b] = true;
+    }
     return TG_OK;
 }
 
