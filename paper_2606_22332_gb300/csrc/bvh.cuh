@@ -29,7 +29,7 @@ struct BvhTri {
 
 constexpr int kBvhLeaf = 4;
 constexpr int kBvhStack = 64;
-constexpr int kBvhLbCells = 32;  // cells per axis of the distance lower-bound grid
+constexpr int kBvhLbCells = 64;  // cells per axis of the distance lower-bound grid
 
 __host__ __device__ inline float bvh_box_d2(const BvhNode& nd, float px, float py, float pz) {
     const float dx = fmaxf(fmaxf(nd.lo[0] - px, px - nd.hi[0]), 0.0f);
@@ -244,6 +244,23 @@ __host__ __device__ inline void bvh_within(const BvhNode* nodes, const BvhTri* t
         }
     }
 }
+
+#ifdef __CUDACC__
+// The lower bound (from the grid below) on the distance from p to the mesh:
+// the cell of p's projection onto the grid's box.  A NaN coordinate lands in
+// cell 0 (the caller handles non-finite points first).
+__device__ __forceinline__ float bvh_lower_bound(const float* lb, const float lo[3], const float inv_h[3], float px,
+                                                 float py, float pz) {
+    const float p[3] = {px, py, pz};
+    int c[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const float u = (p[ax] - lo[ax]) * inv_h[ax];
+        c[ax] = min(max((int)floorf(fminf(fmaxf(u, 0.0f), (float)kBvhLbCells)), 0), kBvhLbCells - 1);
+    }
+    return lb[(c[2] * kBvhLbCells + c[1]) * kBvhLbCells + c[0]];
+}
+#endif
 
 // Lower bound on the distance from any point of each cell of a
 // kBvhLbCells^3 grid over the box [lo, hi] to the mesh: the FP32 distance

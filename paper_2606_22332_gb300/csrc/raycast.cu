@@ -24,10 +24,15 @@
 
 namespace tg {
 
+struct LowerBoundGrid {
+    const float* lb;
+    float lo[3], inv_h[3];
+};
+
 __global__ void raycast_depth_kernel(const BvhNode* __restrict__ nodes, const BvhTri* __restrict__ tris,
-                                     const int32_t* __restrict__ face_id, const float* __restrict__ probes,
-                                     const float* __restrict__ radius, int64_t n, float scale, float* depth,
-                                     float* normal, int32_t* face) {
+                                     const int32_t* __restrict__ face_id, const LowerBoundGrid lbg,
+                                     const float* __restrict__ probes, const float* __restrict__ radius, int64_t n,
+                                     float scale, float* depth, float* normal, int32_t* face) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float inv = 1.0f / scale;
@@ -35,7 +40,10 @@ __global__ void raycast_depth_kernel(const BvhNode* __restrict__ nodes, const Bv
     const float R = radius[i], r = R * inv;
     float d = 0.0f, nx = 0.0f, ny = 0.0f, nz = 0.0f;
     int f = -1;
-    if (r > 0.0f) {
+    // probes no triangle can reach skip the walk (a non-finite probe walks and finds none)
+    const bool reachable = !(isfinite(px) && isfinite(py) && isfinite(pz)) ||
+                           bvh_lower_bound(lbg.lb, lbg.lo, lbg.inv_h, px, py, pz) < r;
+    if (r > 0.0f && reachable) {
         float best;
         const int k = bvh_nearest(nodes, tris, px, py, pz, r * r, &best);
         if (k >= 0) {
@@ -124,13 +132,7 @@ __global__ void __launch_bounds__(kRayStepThreads)
             continue;
         }
         const float reach = (R + 1e-6f) / rec[38];
-        int c[3];
-#pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-            const float u = (q[ax] - op->bvh_lb_lo[ax]) * op->bvh_lb_inv_h[ax];  // NaN -> cell 0
-            c[ax] = min(max((int)floorf(fminf(fmaxf(u, 0.0f), (float)kBvhLbCells)), 0), kBvhLbCells - 1);
-        }
-        if (op->bvh_lb[(c[2] * kBvhLbCells + c[1]) * kBvhLbCells + c[0]] >= reach) {
+        if (bvh_lower_bound(op->bvh_lb, op->bvh_lb_lo, op->bvh_lb_inv_h, q[0], q[1], q[2]) >= reach) {
             phi_hi[g] = R + 1.0f;
             phi_lo[g] = 0.0f;
             nrm[g] = nrm[T + g] = nrm[2 * T + g] = 0.0f;
@@ -276,6 +278,8 @@ struct tg_mesh_bvh {
     BvhNode* nodes = nullptr;
     BvhTri* tris = nullptr;
     int32_t* face_id = nullptr;
+    float* lb = nullptr;  // the distance lower-bound grid
+    float lb_lo[3] = {0, 0, 0}, lb_inv_h[3] = {0, 0, 0};
     int32_t n_nodes = 0, n_tris = 0;
 };
 
@@ -294,7 +298,18 @@ tg_status tg_mesh_bvh_create(const float* verts, int32_t n_verts, const int32_t*
     tg_mesh_bvh* b = new tg_mesh_bvh();
     b->n_nodes = (int32_t)nodes.size();
     b->n_tris = n_faces;
+    float hi[3];
+    for (int a = 0; a < 3; ++a) {
+        b->lb_lo[a] = nodes[0].lo[a];
+        hi[a] = std::max(nodes[0].hi[a], b->lb_lo[a] + 1e-9f);
+        b->lb_inv_h[a] = (float)kBvhLbCells / (hi[a] - b->lb_lo[a]);
+    }
+    std::vector<float> lbg((size_t)kBvhLbCells * kBvhLbCells * kBvhLbCells);
+    bvh_lower_bounds(nodes, tris, b->lb_lo, hi, lbg.data(),
+                     (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency())));
     cudaError_t e = cudaMalloc(&b->nodes, sizeof(BvhNode) * nodes.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->lb, sizeof(float) * lbg.size());
+    if (e == cudaSuccess) e = cudaMemcpy(b->lb, lbg.data(), sizeof(float) * lbg.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&b->tris, sizeof(BvhTri) * tris.size());
     if (e == cudaSuccess) e = cudaMalloc(&b->face_id, sizeof(int32_t) * fid.size());
     if (e == cudaSuccess) e = cudaMemcpy(b->nodes, nodes.data(), sizeof(BvhNode) * nodes.size(), cudaMemcpyHostToDevice);
@@ -315,6 +330,7 @@ void tg_mesh_bvh_destroy(tg_mesh_bvh* b) {
     if (b->nodes) cudaFree(b->nodes);
     if (b->tris) cudaFree(b->tris);
     if (b->face_id) cudaFree(b->face_id);
+    if (b->lb) cudaFree(b->lb);
     delete b;
 }
 
@@ -327,8 +343,9 @@ tg_status tg_raycast_depth(const tg_mesh_bvh* b, const float* probes, const floa
         (normal && !b_is_dev(normal)) || (face && !b_is_dev(face)))
         return bfail(TG_ERR_INVALID_ARG, "probes, radius, depth (and normal, face) must be device buffers");
     const unsigned blocks = (unsigned)((n + 127) / 128);
-    raycast_depth_kernel<<<blocks, 128, 0, (cudaStream_t)stream>>>(b->nodes, b->tris, b->face_id, probes, radius, n,
-                                                                   (float)scale, depth, normal, face);
+    LowerBoundGrid lbg{b->lb, {b->lb_lo[0], b->lb_lo[1], b->lb_lo[2]}, {b->lb_inv_h[0], b->lb_inv_h[1], b->lb_inv_h[2]}};
+    raycast_depth_kernel<<<blocks, 128, 0, (cudaStream_t)stream>>>(b->nodes, b->tris, b->face_id, lbg, probes, radius,
+                                                                   n, (float)scale, depth, normal, face);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bfail(TG_ERR_CUDA, std::string("raycast launch: ") + cudaGetErrorString(e));
     return TG_OK;
