@@ -252,6 +252,7 @@ const char* make_params(const tg_params& p, ParamsDev* out) {
     if (p.depth_backend == 1 && p.probe_radius_noise > 0.0)
         return "probe-radius noise is not supported with the raycast depth backend";
     d.depth_backend = p.depth_backend;
+    d.prev_out = (p.probe_radius_noise == 0.0 && d.ring_k == 1) ? 1 : 0;
     for (uint32_t r = 0; r < 10; ++r) {
         d.rk[2 * r] = (uint32_t)p.seed + r * 0x9E3779B9u;
         d.rk[2 * r + 1] = (uint32_t)(p.seed >> 32) + r * 0xBB67AE85u;
@@ -1288,11 +1289,14 @@ tg_status tg_autotune(tg_scene* s, const tg_step_inputs* in, int32_t steps, tg_t
     // the shear anchors are state of the markers' trials too
     const size_t EP = s->anchors ? (size_t)s->E * s->markers.pads_per_env : 0;
     const size_t AB = EP * (size_t)s->markers.shear_n * 8;
-    const size_t bytes = T + 3 * 8 * T * 4 + E * 4 + RB + AB + 2 * EP * 4;
+    // (and the clean depth and force/torque outputs, which with prev_out are
+    // the hysteresis x_{t-1})
+    const size_t bytes = T + 3 * 8 * T * 4 + 7 * T * 4 + E * 4 + RB + AB + 2 * EP * 4;
     CK(s, cudaMalloc(&keep, bytes));
     auto save = [&](bool back) {
         struct { void* p; size_t n; } part[] = {{s->flags, T}, {s->hyst_prev, 8 * T * 4}, {s->hyst_xi, 8 * T * 4},
-                                                 {s->drift, 8 * T * 4}, {s->episode, E * 4}, {s->ring, RB},
+                                                 {s->drift, 8 * T * 4}, {s->depth_clean, T * 4},
+                                                 {s->ft_clean, 6 * T * 4}, {s->episode, E * 4}, {s->ring, RB},
                                                  {s->anchors, AB}, {s->anchor_obj, EP * 4}, {s->n_anchored, EP * 4}};
         size_t off = 0;
         cudaError_t e = cudaSuccess;
@@ -1507,6 +1511,14 @@ static size_t shear_slots(const tg_scene* s) {
     return s->anchors ? (size_t)s->E * s->markers.pads_per_env * s->markers.shear_n : 0;
 }
 
+// where channel c of the hysteresis x_{t-1} lives: hyst_prev, or with
+// prev_out (channels 0-6) the clean depth and force/torque outputs
+static float* prev_channel(tg_scene* s, int c) {
+    const size_t T = (size_t)s->T;
+    if (s->P.prev_out && c < 7) return c == 0 ? s->depth_clean : s->ft_clean + (size_t)(c - 1) * T;
+    return s->hyst_prev + (size_t)c * T;
+}
+
 tg_status tg_save_state(tg_scene* s, void* buf, size_t* size) {
     if (!s || !size) return fail(s, TG_ERR_INVALID_ARG, "scene or size is NULL");
     const size_t T = (size_t)s->T, E = (size_t)s->E;
@@ -1521,7 +1533,10 @@ tg_status tg_save_state(tg_scene* s, void* buf, size_t* size) {
     memcpy(p, hdr, 32);
     p += 32;
     CK(s, cudaMemcpy(p, s->flags, T, cudaMemcpyDeviceToHost)); p += T;
-    CK(s, cudaMemcpy(p, s->hyst_prev, 8 * T * 4, cudaMemcpyDeviceToHost)); p += 8 * T * 4;
+    // hysteresis x_{t-1} per channel; with prev_out channels 0-6 are the
+    // clean depth and force/torque outputs
+    for (int c = 0; c < 8; ++c, p += T * 4)
+        CK(s, cudaMemcpy(p, prev_channel(s, c), T * 4, cudaMemcpyDeviceToHost));
     CK(s, cudaMemcpy(p, s->hyst_xi, 8 * T * 4, cudaMemcpyDeviceToHost)); p += 8 * T * 4;
     CK(s, cudaMemcpy(p, s->drift, 8 * T * 4, cudaMemcpyDeviceToHost)); p += 8 * T * 4;
     CK(s, cudaMemcpy(p, s->episode, E * 4, cudaMemcpyDeviceToHost)); p += E * 4;
@@ -1547,7 +1562,8 @@ tg_status tg_load_state(tg_scene* s, const void* buf, size_t size) {
     p += 32;
     CK(s, cudaDeviceSynchronize());
     CK(s, cudaMemcpy(s->flags, p, T, cudaMemcpyHostToDevice)); p += T;
-    CK(s, cudaMemcpy(s->hyst_prev, p, 8 * T * 4, cudaMemcpyHostToDevice)); p += 8 * T * 4;
+    for (int c = 0; c < 8; ++c, p += T * 4)
+        CK(s, cudaMemcpy(prev_channel(s, c), p, T * 4, cudaMemcpyHostToDevice));
     CK(s, cudaMemcpy(s->hyst_xi, p, 8 * T * 4, cudaMemcpyHostToDevice)); p += 8 * T * 4;
     CK(s, cudaMemcpy(s->drift, p, 8 * T * 4, cudaMemcpyHostToDevice)); p += 8 * T * 4;
     CK(s, cudaMemcpy(s->episode, p, E * 4, cudaMemcpyHostToDevice)); p += E * 4;

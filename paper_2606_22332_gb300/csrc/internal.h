@@ -64,6 +64,12 @@ struct ParamsDev {
     int delay, jitter, ring_k;
     // contact-depth backend of mesh objects: 0 signed distance, 1 raycast
     int depth_backend;
+    // 1 when the noisy chain starts from the clean readings (no probe-radius
+    // noise, no read delay): the hysteresis x_{t-1} of the depth and
+    // force/torque channels, gain times last step's noisy-chain input, is
+    // then gain times last step's clean output, read back from the output
+    // arrays instead of being kept in hyst_prev (channels 0-6 unused)
+    int prev_out;
 };
 
 // Object table entry (object frame); its size is a multiple of 16 bytes so

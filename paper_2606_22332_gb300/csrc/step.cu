@@ -307,7 +307,9 @@ __global__ void __launch_bounds__(NT, kStepMinBlocks) step_kernel(const StepArgs
 }
 
 // Reset of the envs whose mask byte is set: dead mask drawn from
-// (seed, taxel id, episode), hysteresis / drift / Schmitt state zeroed.
+// (seed, taxel id, episode), hysteresis / drift / Schmitt state zeroed, and
+// the clean depth and force/torque outputs zeroed (with prev_out they are
+// the hysteresis x_{t-1}).
 __global__ void reset_kernel(const StepArgs a, const uint8_t* env_mask, uint32_t episode, uint32_t* episode_arr) {
     const Item it = a.items[blockIdx.x];
     const int e = it.env;
@@ -326,6 +328,8 @@ __global__ void reset_kernel(const StepArgs a, const uint8_t* env_mask, uint32_t
             a.hyst_xi[c * T + g] = 0.f;
             a.drift[c * T + g] = 0.f;
         }
+        a.depth_clean[g] = 0.f;
+        for (int c = 0; c < 6; ++c) a.ft_clean[c * T + g] = 0.f;
         for (int c = 0; a.P.ring_k > 1 && c < a.P.ring_k * 8; ++c) a.ring[c * T + g] = 0.f;
     }
 }

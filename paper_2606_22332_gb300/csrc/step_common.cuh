@@ -74,14 +74,13 @@ __device__ __forceinline__ float fast_query(const float* rec, const ObjDev& obj,
 }
 
 // A taxel clear of the surface (or an inactive filler, R = 0): depth 0,
-// contact off, zero force.  Returns its shared-memory bits.
+// contact off, zero force.  Stores its flag byte and surface distance (the
+// zero clean depth and force/torque are stored with the noise state, after
+// last step's values have been read there) and returns its shared-memory
+// bits.
 __device__ __forceinline__ uint8_t clear_taxel(const StepArgs& a, int64_t g, float R, uint8_t flags, float phi) {
-    const int64_t T = a.n_taxels;
     __stcs(a.flags + g, (uint8_t)(flags & 2u));
-    __stcs(a.depth_clean + g, 0.f);
     if (a.sensors & TG_SENSOR_DIST) __stcs(a.dist + g, R > 0.0f ? phi - R : 0.0f);
-#pragma unroll
-    for (int c = 0; c < 6; ++c) __stcs(a.ft_clean + c * T + g, 0.f);
     return (uint8_t)(((flags & 2u) ? BIT_DEAD : 0u) | (R > 0.0f ? BIT_ACTIVE : 0u));
 }
 
@@ -188,17 +187,21 @@ __device__ __forceinline__ CleanReading refine_compute(const ParamsDev& P, const
     return out;
 }
 
-// the clean outputs of a refined taxel
+// the flag byte and surface distance of a refined taxel (its clean depth and
+// force/torque are stored with the noise state, see clear_taxel)
 __device__ __forceinline__ void store_clean(const StepArgs& a, int64_t g, const CleanReading& cr) {
-    const int64_t T = a.n_taxels;
     __stcs(a.flags + g, cr.flags);
-    __stcs(a.depth_clean + g, cr.d);
     if (a.sensors & TG_SENSOR_DIST) __stcs(a.dist + g, cr.dist);
+}
+
+// The clean depth and force/torque outputs of taxel g, stored in the noise
+// state phase: with prev_out the previous values there are the hysteresis
+// state, read by that phase first.
+__device__ __forceinline__ void store_clean_out(const StepArgs& a, int64_t g, float d, const float* f) {
+    const int64_t T = a.n_taxels;
+    __stcs(a.depth_clean + g, d);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        __stcs(a.ft_clean + c * T + g, cr.f[c]);
-        __stcs(a.ft_clean + (3 + c) * T + g, cr.tq[c]);
-    }
+    for (int c = 0; c < 6; ++c) __stcs(a.ft_clean + c * T + g, f[c]);
 }
 
 template <bool RADIUS>
@@ -213,7 +216,8 @@ __device__ __forceinline__ CleanReading refine_taxel(const StepArgs& a, const fl
 
 // The noise state a taxel's step reads (hysteresis x_{t-1} and xi of the
 // depth and six force/torque channels, the depth drift) and what the step
-// leaves of it.
+// leaves of it.  With prev_out, prev_d and pv hold last step's clean depth
+// and force/torque, which the gain turns into x_{t-1}.
 struct NoiseIn {
     float prev_d, xi_d, drift_d;
     float pv[6], xv[6];
@@ -245,10 +249,12 @@ __device__ __forceinline__ NoiseOut noise_core(const ParamsDev& P, uint64_t gid,
     const float gain_d = P.depth.gain_on ? P.depth.gain_lo + P.depth.gain_span * u24(wep.y) : 1.0f;
     const float gain_f = P.ft.gain_on ? P.ft.gain_lo + P.ft.gain_span * u24(wep.z) : 1.0f;
     float xd = gain_d * d_in;
-    o.prev_d = s.prev_d;
+    // x_{t-1} = gain * last step's input: the same product as stored then
+    const float prev_d = P.prev_out ? gain_d * s.prev_d : s.prev_d;
+    o.prev_d = prev_d;
     o.xi_d = s.xi_d;
     if (hyst_d) {
-        const float xi = P.depth.decay * s.xi_d + (xd - s.prev_d);
+        const float xi = P.depth.decay * s.xi_d + (xd - prev_d);
         o.xi_d = xi;
         o.prev_d = xd;
         xd = xd + P.depth.beta * xi;
@@ -257,7 +263,8 @@ __device__ __forceinline__ NoiseOut noise_core(const ParamsDev& P, uint64_t gid,
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             const float x = gain_f * f_in[c];
-            const float xi = P.ft.decay * s.xv[c] + (x - s.pv[c]);
+            const float pv = P.prev_out ? gain_f * s.pv[c] : s.pv[c];
+            const float xi = P.ft.decay * s.xv[c] + (x - pv);
             o.xv[c] = xi;
             o.pv[c] = x;
             o.hx[c] = x + P.ft.beta * xi;
@@ -334,7 +341,9 @@ __device__ __forceinline__ uint8_t delay_readout(const StepArgs& a, int64_t g, u
 }
 
 // Noise state of one active taxel after its clean reading (fc[.][i] and the
-// clean depth in ag[0][i]), from and to the state arrays in HBM.  The state
+// clean depth in ag[0][i]), from and to the state arrays in HBM; stores the
+// clean depth and force/torque outputs (with prev_out, after reading last
+// step's values there as x_{t-1}).  The state
 // loads do not depend on the geometry, and all of them are issued before
 // the first store: the compiler cannot move a load above a store to a
 // pointer that may alias it, and every such barrier would cost a further
@@ -350,14 +359,17 @@ __device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, i
     s.prev_d = s.xi_d = s.drift_d = 0.0f;
 #pragma unroll
     for (int c = 0; c < 6; ++c) s.pv[c] = s.xv[c] = 0.0f;
+    // x_{t-1}: kept in hyst_prev, or with prev_out last step's clean output
+    const float* prev_d_src = P.prev_out ? a.depth_clean : a.hyst_prev;
+    const float* prev_f_src = P.prev_out ? a.ft_clean : a.hyst_prev + T;
     if (hyst_d) {
-        s.prev_d = __ldcs(a.hyst_prev + g);
+        s.prev_d = __ldcs(prev_d_src + g);
         s.xi_d = __ldcs(a.hyst_xi + g);
     }
     if (hyst_f) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            s.pv[c] = __ldcs(a.hyst_prev + (1 + c) * T + g);
+            s.pv[c] = __ldcs(prev_f_src + c * T + g);
             s.xv[c] = __ldcs(a.hyst_xi + (1 + c) * T + g);
         }
     }
@@ -380,15 +392,21 @@ __device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, i
         S.bits[i] = bits;
     }
     const NoiseOut o = noise_core(P, (uint64_t)(a.gid0 + g), ep, step, bits, d_in, f_in, s);
+    {
+        float fc[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) fc[c] = S.fc[c][i];
+        store_clean_out(a, g, d, fc);
+    }
     if (hyst_d) {
         __stcs(a.hyst_xi + g, o.xi_d);
-        __stcs(a.hyst_prev + g, o.prev_d);
+        if (!P.prev_out) __stcs(a.hyst_prev + g, o.prev_d);
     }
     if (hyst_f) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             __stcs(a.hyst_xi + (1 + c) * T + g, o.xv[c]);
-            __stcs(a.hyst_prev + (1 + c) * T + g, o.pv[c]);
+            if (!P.prev_out) __stcs(a.hyst_prev + (1 + c) * T + g, o.pv[c]);
         }
     }
 #pragma unroll
@@ -399,9 +417,12 @@ __device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, i
     S.ag[3][i] = o.xd * n0; S.ag[4][i] = o.xd * n1; S.ag[5][i] = o.xd * n2;
 }
 
-// Inactive filler: zero noisy depth and staged values.
+// Inactive filler: zero clean and noisy depth, clean force/torque and
+// staged values.
 template <class Smem>
 __device__ __forceinline__ void noise_state_filler(const StepArgs& a, Smem& S, int i, int64_t g) {
+    const float zero[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    store_clean_out(a, g, 0.f, zero);
     __stcs(a.depth_noisy + g, 0.f);
 #pragma unroll
     for (int c = 0; c < 6; ++c) {

@@ -150,7 +150,12 @@ __device__ void issue_hy(const StepArgs& a, SmemPipe& S, int buf, const SlotRec&
     const bool hd = hyst_depth_on(P), hf = hyst_ft_on(P), wd = drift_depth_on(P);
     for (int c = 0; c < 7; ++c) {
         if (c == 0 ? !hd : !hf) continue;
-        L.hy[c] = stage(S.hy[c], a.hyst_prev, c * T + r.taxel_begin, r.n_taxels, 4, &S.mbar_hy, tx);
+        // x_{t-1}: hyst_prev, or with prev_out last step's clean output
+        if (P.prev_out)
+            L.hy[c] = stage(S.hy[c], c == 0 ? a.depth_clean : a.ft_clean, (c == 0 ? 0 : (c - 1) * T) + r.taxel_begin,
+                            r.n_taxels, 4, &S.mbar_hy, tx);
+        else
+            L.hy[c] = stage(S.hy[c], a.hyst_prev, c * T + r.taxel_begin, r.n_taxels, 4, &S.mbar_hy, tx);
         L.hy[7 + c] = stage(S.hy[7 + c], a.hyst_xi, c * T + r.taxel_begin, r.n_taxels, 4, &S.mbar_hy, tx);
     }
     if (wd) L.hy[14] = stage(S.hy[14], a.drift, r.taxel_begin, r.n_taxels, 4, &S.mbar_hy, tx);
@@ -386,13 +391,13 @@ __global__ void __launch_bounds__(NT, 1) step_pipe_kernel(const StepArgs a) {
                 const NoiseOut o = noise_core(P, (uint64_t)(a.gid0 + g), ep, step, bits, d_in, f_in, s);
                 if (hd) {
                     __stcs(a.hyst_xi + g, o.xi_d);
-                    __stcs(a.hyst_prev + g, o.prev_d);
+                    if (!P.prev_out) __stcs(a.hyst_prev + g, o.prev_d);
                 }
                 if (hf) {
 #pragma unroll
                     for (int c = 0; c < 6; ++c) {
                         __stcs(a.hyst_xi + (1 + c) * T + g, o.xv[c]);
-                        __stcs(a.hyst_prev + (1 + c) * T + g, o.pv[c]);
+                        if (!P.prev_out) __stcs(a.hyst_prev + (1 + c) * T + g, o.pv[c]);
                     }
                 }
                 if (wd) __stcs(a.drift + g, o.drift_d);
@@ -407,6 +412,12 @@ __global__ void __launch_bounds__(NT, 1) step_pipe_kernel(const StepArgs a) {
                 S.dd[1][i] = 0.f;
             }
             S.bits[i] = bits;
+            {  // clean outputs, after the staged copy of last step's (prev_out) has landed
+                float fc[6];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) fc[c] = S.fc[c][i];
+                store_clean_out(a, g, S.dd[0][i], fc);
+            }
         }
         ok = mbar_wait(&S.mbar_dr, (uint32_t)(k & 1));
         if (!ok && atomicExch(&S.abort, 1) == 0) atomicAdd(a.err + 2, 1u);
