@@ -365,9 +365,14 @@ tg_status tg_graph_release(tg_scene* scene);
 
 /* Work schedule of the step kernel.  Work items are runs of whole links of
    one env (at most 1,024 taxels).
-     TG_SCHED_GRID        one 512-thread CTA per work item;
+     TG_SCHED_GRID        one 512-thread CTA per work item, two resident
+                          per SM;
      TG_SCHED_PERSISTENT  resident 512-thread CTAs take items from an atomic
                           counter;
+     TG_SCHED_GRID_384 / TG_SCHED_PERSISTENT_384  the same with 384-thread
+                          CTAs, three resident per SM (each thread takes
+                          more of the item's taxels; a third item in flight
+                          per SM covers more of each item's waits);
      TG_SCHED_PIPE_1024 / _768 / _512  pipelined: one CTA of that many
                           threads per SM runs its share of the items in turn,
                           and bulk copies bring each item's taxel geometry,
@@ -395,7 +400,9 @@ typedef enum {
     TG_SCHED_PIPE_1024 = 2,
     TG_SCHED_PIPE_768 = 3,
     TG_SCHED_PIPE_512 = 4,
-    TG_SCHED_COUNT = 5
+    TG_SCHED_GRID_384 = 5,
+    TG_SCHED_PERSISTENT_384 = 6,
+    TG_SCHED_COUNT = 7
 } tg_schedule;
 typedef enum {
     TG_KERNEL_PROX = 0,      /* proximity rays (TG_SENSOR_PROX) */

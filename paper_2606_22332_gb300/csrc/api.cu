@@ -97,13 +97,14 @@ struct tg_scene {
     float* nq_grad = nullptr;         // [3][T]
     float* nq_phi_lo = nullptr;       // [T] (raycast backend)
     bool any_raycast = false;         // a mesh object answered by the raycast backend
+    bool all_grid = false;            // every object is a plain SDF grid
     // schedule (tg_set_schedule / tg_autotune) and step control
     int schedule = TG_SCHED_GRID;     // step kernel schedule (tg_schedule)
     int sorted = 1;                   // object-sorted item order (several objects)
     // threads per CTA of the sensor kernels (tg_sensor_kernel order: proximity,
     // point-cloud proximity, markers)
     int sensor_threads[3] = {256, 256, 256};
-    int resident_ctas = 0;            // step kernel CTAs resident on the device at once
+    int resident_ctas[kStepShapes] = {0, 0};  // step kernel CTAs resident on the device at once, per shape
     int sms = 0;                      // streaming multiprocessors (pipelined schedules: one CTA each)
     ItemMeta* metas = nullptr;        // [n_items] static item layout (pipelined schedules)
     SlotRec* slots = nullptr;         // [n_items] this step's order records (pipelined schedules)
@@ -279,6 +280,11 @@ const char* make_params(const tg_params& p, ParamsDev* out) {
     return nullptr;
 }
 
+// the step kernel of a schedule: pipelined, persistent, and its CTA shape
+bool sched_pipe(int sc) { return sc >= TG_SCHED_PIPE_1024 && sc <= TG_SCHED_PIPE_512; }
+bool sched_persistent(int sc) { return sc == TG_SCHED_PERSISTENT || sc == TG_SCHED_PERSISTENT_384; }
+int sched_shape(int sc) { return (sc == TG_SCHED_GRID_384 || sc == TG_SCHED_PERSISTENT_384) ? 1 : 0; }
+
 StepArgs step_args(tg_scene* s) {
     StepArgs a{};
     a.x = s->x; a.y = s->y; a.z = s->z; a.nx = s->nx; a.ny = s->ny; a.nz = s->nz; a.R = s->R;
@@ -313,8 +319,9 @@ StepArgs step_args(tg_scene* s) {
     a.prox_noisy = s->prox_noisy;
     a.ctl = s->ctl;
     a.n_items = s->n_items;
-    a.persistent = s->schedule == TG_SCHED_PERSISTENT ? 1 : 0;
-    a.resident_ctas = s->resident_ctas;
+    a.persistent = sched_persistent(s->schedule) ? 1 : 0;
+    a.shape = sched_shape(s->schedule);
+    a.resident_ctas = s->resident_ctas[a.shape];
     a.metas = s->metas;
     a.slots = s->slots;
     a.sms = s->sms;
@@ -322,6 +329,7 @@ StepArgs step_args(tg_scene* s) {
     a.nq_grad = s->nq_grad;
     a.nq_phi_lo = s->nq_phi_lo;
     a.any_neural = s->any_neural ? 1 : 0;
+    a.all_grid = s->all_grid ? 1 : 0;
     return a;
 }
 
@@ -596,8 +604,10 @@ tg_status tg_create_scene(const tg_scene_desc* d, tg_scene** out) {
         CKC(cudaGetDevice(&dev));
         CKC(cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev));
     }
-    s->resident_ctas = step_kernel_resident_ctas();
-    if (s->resident_ctas <= 0) return bail(cudaErrorInvalidConfiguration, "step kernel occupancy");
+    for (int k = 0; k < kStepShapes; ++k) {
+        s->resident_ctas[k] = step_kernel_resident_ctas(k);
+        if (s->resident_ctas[k] <= 0) return bail(cudaErrorInvalidConfiguration, "step kernel occupancy");
+    }
     if (d->sensors & TG_SENSOR_PROX) {
         CKC(dalloc(&s->prox_clean, T));
         CKC(dalloc(&s->prox_noisy, T));
@@ -946,6 +956,8 @@ tg_status tg_upload_objects(tg_scene* s, const tg_object_desc* objs, int32_t n) 
     s->obj_info = info;
     s->any_neural = any_neural;
     s->any_raycast = any_raycast;
+    s->all_grid = n > 0;
+    for (int i = 0; i < n; ++i) s->all_grid = s->all_grid && objs[i].kind == TG_OBJ_GRID;
     return TG_OK;
 }
 
@@ -1049,7 +1061,7 @@ tg_status enqueue_step(tg_scene* s, const tg_step_inputs* in, cudaStream_t st, b
     a.step = in->step;
     a.step_from_ctl = graph ? 1 : 0;
     a.items_sorted = nullptr;
-    const bool pipe = s->schedule >= TG_SCHED_PIPE_1024;
+    const bool pipe = sched_pipe(s->schedule);
     const bool sort = s->sorted && s->n_objects > 1 && s->n_objects <= 12288;
     if (pipe) {
         CK(s, launch_slot_records(s->items, s->n_items, oid, s->n_objects, s->episode, sort ? 1 : 0, s->slots, st));
@@ -1254,7 +1266,7 @@ bool sensor_kernel_on(const tg_scene* s, int k) {
     return (s->sensors & TG_SENSOR_MARKERS) != 0;
 }
 int step_threads(int schedule) {
-    return schedule >= TG_SCHED_PIPE_1024 ? kPipeThreads[schedule - TG_SCHED_PIPE_1024] : kStepThreads;
+    return sched_pipe(schedule) ? kPipeThreads[schedule - TG_SCHED_PIPE_1024] : kStepShapeThreads[sched_shape(schedule)];
 }
 }  // namespace
 

@@ -12,8 +12,12 @@ namespace tg {
 
 constexpr int kMaxLinks = 255;       // u8 link ids
 constexpr int kItemCap = 1024;       // max taxels per work item (one CTA)
-constexpr int kStepThreads = 512;    // CTA size of the step kernel
-constexpr int kStepMinBlocks = 2;    // resident CTAs per SM the register budget is set for
+// CTA shapes of the step kernel: threads per CTA and the resident CTAs per
+// SM its register budget is set for (512 x 2, or 384 x 3 at 56 registers;
+// one item's shared memory, ~75 KB, lets three CTAs share an SM)
+constexpr int kStepShapes = 2;
+constexpr int kStepShapeThreads[kStepShapes] = {512, 384};
+constexpr int kStepShapeBlocks[kStepShapes] = {2, 3};
 constexpr int kLinkRec = 40;         // floats per (env, link) pose record
 constexpr int kLinkOut = 18;         // floats per (env, link) output record
 constexpr int kItemMaxLinks = 32;    // links per work item
@@ -182,6 +186,7 @@ struct StepArgs {
     int step_from_ctl;
     int n_items;
     int persistent;                   // step kernel: CTAs take items from ctl->counter
+    int shape;                        // step kernel CTA shape (kStepShapeThreads index)
     int resident_ctas;                // persistent grid size (SMs x resident CTAs per SM)
     // pipelined step kernel
     const ItemMeta* metas;            // [n_items] static item layout
@@ -214,6 +219,7 @@ struct StepArgs {
     const float* nq_grad;             // [3][T]
     const float* nq_phi_lo;           // [T] low part of phi (raycast meshes: phi = hi + lo)
     int any_neural;
+    int all_grid;                     // every object is a plain SDF grid (the step kernel's grid-only form)
 };
 
 // Elastomer marker pads (one CTA per (env, pad)).
@@ -280,7 +286,7 @@ cudaError_t launch_step(const StepArgs& a, int n_items, cudaStream_t s);
 cudaError_t configure_step_kernels();
 cudaError_t launch_set_ctl(StepCtl* ctl, StepCtl value, cudaStream_t s);
 cudaError_t launch_advance_ctl(StepCtl* ctl, cudaStream_t s);
-int step_kernel_resident_ctas();
+int step_kernel_resident_ctas(int shape);
 cudaError_t launch_order_items(const Item* items, int n_items, const int32_t* obj_id, int n_objects, Item* sorted,
                                cudaStream_t s);
 cudaError_t launch_reset(const StepArgs& a, int n_items, const uint8_t* env_mask, uint32_t episode,

@@ -35,9 +35,12 @@ struct SmemStep {
     ObjDev obj;
     float hx[6][kItemCap];              // force/torque after gain + hysteresis (A1-A2: near-taxel inputs)
     float fc[6][kItemCap];              // clean force/torque, later noisy force/torque
-    float ag[6][kItemCap];              // clean depth, then agg_force terms d n: clean xyz, noisy xyz
+    // 0 clean depth, 1 noisy depth (with probe-radius noise, until phase N,
+    // the perturbed radius's depth), 2-4 probe normal (from phase N; in A1-A2
+    // rows 2-3 hold the near-contact queue); agg_force terms d n are formed
+    // in the link sums
+    float dn[5][kItemCap];
     uint8_t bits[kItemCap];             // BIT_* flags
-    int16_t queue[kItemCap];            // near-contact taxels for phase A2
     int nq;
     unsigned int slot;                  // persistent schedule: the item being run
     uint32_t episode;                   // the env's episode counter
@@ -48,6 +51,10 @@ struct SmemStep {
     int uni_len, uni_rows, uni_cols, uni_wrap;
     float uni_inv_len, uni_inv_cols;
 };
+
+// three items' shared memory (and the 1 KB the SM reserves per CTA) fit in
+// the SM's 228 KB, for the 384 x 3 shape
+static_assert(3 * (sizeof(SmemStep) + 1024) <= 228 * 1024, "three step-kernel CTAs per SM");
 
 // L2 prefetch of the SDF grid of the object whose run of items begins two
 // waves of resident CTAs after `slot` in the object-sorted order.  Each env
@@ -76,8 +83,10 @@ __device__ __forceinline__ void prefetch_grid_ahead(const StepArgs& a, int slot)
     }
 }
 
-// One work item: every phase of the step for its taxels.
-template <int NT, bool RADIUS>
+// One work item: every phase of the step for its taxels.  GRID: the form
+// for scenes whose objects are all plain SDF grids (no kind dispatch, no
+// query kernel ahead of this one).
+template <int NT, bool RADIUS, bool GRID>
 __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int slot, uint32_t step) {
     const Item it = a.items_sorted ? a.items_sorted[slot] : a.items[slot];
     const int e = it.env;
@@ -146,6 +155,9 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
 
     const uint32_t ep = S.episode;
     const ObjDev& obj = S.obj;
+    // near-contact taxels for phase A2 (rows 2-3 of dn are free until phase N)
+    int16_t* queue = reinterpret_cast<int16_t*>(&S.dn[2][0]);
+    static_assert(2 * kItemCap * sizeof(float) >= kItemCap * sizeof(int16_t), "queue fits");
 
     // ---- phase A1 (geometry): FP32 query of every taxel; those clear of the
     //      surface finish here, those within 1 um of contact are queued.  A
@@ -171,12 +183,12 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
                 while (i1 >= S.start[l1 + 1]) ++l1;
         }
         float phi0 = 0.0f, phi1 = 0.0f;
-        if (phi_precomputed(obj, a.P)) {  // from the learned-SDF or raycast query kernel
+        if (!GRID && phi_precomputed(obj, a.P)) {  // from the learned-SDF or raycast query kernel
             if (R0 > 0.0f) phi0 = a.nq_phi[g0];
             if (R1 > 0.0f) phi1 = a.nq_phi[g1];
         } else {
-            if (R0 > 0.0f) phi0 = fast_query(S.rec[l0], obj, x00, x01, x02);
-            if (R1 > 0.0f) phi1 = fast_query(S.rec[l1], obj, x10, x11, x12);
+            if (R0 > 0.0f) phi0 = fast_query<GRID>(S.rec[l0], obj, x00, x01, x02);
+            if (R1 > 0.0f) phi1 = fast_query<GRID>(S.rec[l1], obj, x10, x11, x12);
         }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
@@ -187,7 +199,7 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
             if (R > 0.0f && !isfinite(phi)) atomicAdd(a.err, 1u);
             // (with probe-radius noise the noisy readout's radius reaches R + rho)
             if (R > 0.0f && phi < R + 1e-6f + (RADIUS ? a.P.rho : 0.0f)) {
-                S.queue[atomicAdd(&S.nq, 1)] = (int16_t)i;
+                queue[atomicAdd(&S.nq, 1)] = (int16_t)i;
                 // A2's inputs, kept on chip (hx is not used before phase N)
                 float* st = &S.hx[0][0];
                 st[i] = u ? x10 : x00;
@@ -197,10 +209,10 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
                 st[4 * kItemCap + i] = __uint_as_float(u ? fl1 : fl0);
                 continue;
             }
-            S.bits[i] = clear_taxel(a, g, R, u ? fl1 : fl0, raycast_obj(obj, a.P) ? R : phi);
+            S.bits[i] = clear_taxel(a, g, R, u ? fl1 : fl0, !GRID && raycast_obj(obj, a.P) ? R : phi);
 #pragma unroll
             for (int c = 0; c < 6; ++c) S.fc[c][i] = 0.f;
-            S.ag[0][i] = 0.f;
+            S.dn[0][i] = 0.f;
         }
         l = l1;
     }
@@ -209,7 +221,7 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
     // ---- phase A2: near-contact taxels, compacted onto whole warps
     const int nq = S.nq;
     for (int k = tid; k < nq; k += NT) {
-        const int i = S.queue[k];
+        const int i = queue[k];
         int lo = 0, hi = nl - 1;  // link of taxel i: last start <= i
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -217,7 +229,7 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
             else hi = mid - 1;
         }
         const float* st = &S.hx[0][0];
-        const CleanReading cr = refine_taxel<RADIUS>(a, S.rec[lo], obj, it.taxel_begin + i, st[i], st[kItemCap + i],
+        const CleanReading cr = refine_taxel<RADIUS, GRID>(a, S.rec[lo], obj, it.taxel_begin + i, st[i], st[kItemCap + i],
                                              st[2 * kItemCap + i], st[3 * kItemCap + i],
                                              (uint8_t)__float_as_uint(st[4 * kItemCap + i]), step);
 #pragma unroll
@@ -225,10 +237,10 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
             S.fc[c][i] = cr.f[c];
             S.fc[3 + c][i] = cr.tq[c];
         }
-        S.ag[0][i] = cr.d;
+        S.dn[0][i] = cr.d;
         S.bits[i] = cr.bits;
         if constexpr (RADIUS) {  // the noisy chain's depth and force, for phase N (slots free until then)
-            S.ag[1][i] = cr.dn;
+            S.dn[1][i] = cr.dn;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 S.hx[c][i] = cr.fn[c];
@@ -252,8 +264,7 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
         const int ll = t % nl;
         link_quantity(a, S, S.fc, (size_t)(e * L + lb + ll), S.start[ll], S.start[ll + 1], t / nl);
     }
-    // (the last thread has no link quantity here)
-    static_assert(kItemMaxLinks * 14 < NT, "a thread free in phase C1");
+    // (the last thread, after its link quantities if it has any)
     if (a.items_sorted && tid == NT - 1) prefetch_grid_ahead(a, slot);
     __syncthreads();
 
@@ -287,13 +298,13 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
 // Grid schedule: CTA b runs item slot b.  Persistent schedule: a grid sized
 // to the resident CTAs takes item slots from an atomic counter (zeroed
 // before the launch) until none are left.
-template <int NT, bool PERSISTENT, bool RADIUS>
-__global__ void __launch_bounds__(NT, kStepMinBlocks) step_kernel(const StepArgs a) {
+template <int NT, int MINB, bool PERSISTENT, bool RADIUS, bool GRID>
+__global__ void __launch_bounds__(NT, MINB) step_kernel(const StepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmemStep& S = *reinterpret_cast<SmemStep*>(smem_raw);
     const uint32_t step = a.step_from_ctl ? a.ctl->step : a.step;
     if (!PERSISTENT) {
-        step_item<NT, RADIUS>(a, S, blockIdx.x, step);
+        step_item<NT, RADIUS, GRID>(a, S, blockIdx.x, step);
         return;
     }
     for (;;) {
@@ -301,7 +312,7 @@ __global__ void __launch_bounds__(NT, kStepMinBlocks) step_kernel(const StepArgs
         __syncthreads();
         const int slot = (int)S.slot;
         if (slot >= a.n_items) break;
-        step_item<NT, RADIUS>(a, S, slot, step);
+        step_item<NT, RADIUS, GRID>(a, S, slot, step);
         __syncthreads();  // shared memory is reused by the next item
     }
 }
@@ -339,44 +350,81 @@ __global__ void unpack_contact_kernel(const uint8_t* flags, int64_t n, int bit, 
     if (i < n) out[i] = (flags[i] >> bit) & 1u;
 }
 
+// Every form of the step kernel for one CTA shape: PERSISTENT x RADIUS x GRID.
+template <int NT, int MINB>
+struct StepForms {
+    static const void* fn(int k) {
+        const void* f[8] = {(const void*)step_kernel<NT, MINB, false, false, false>,
+                            (const void*)step_kernel<NT, MINB, true, false, false>,
+                            (const void*)step_kernel<NT, MINB, false, true, false>,
+                            (const void*)step_kernel<NT, MINB, true, true, false>,
+                            (const void*)step_kernel<NT, MINB, false, false, true>,
+                            (const void*)step_kernel<NT, MINB, true, false, true>,
+                            (const void*)step_kernel<NT, MINB, false, true, true>,
+                            (const void*)step_kernel<NT, MINB, true, true, true>};
+        return f[k];
+    }
+    static void launch(const StepArgs& a, int blocks, bool persistent, size_t smem, cudaStream_t s) {
+        const bool r = a.P.rho > 0.0f, g = a.all_grid != 0;
+#define TG_STEP_LAUNCH(P, R, G) step_kernel<NT, MINB, P, R, G><<<blocks, NT, smem, s>>>(a)
+        if (persistent) {
+            if (r) { if (g) TG_STEP_LAUNCH(true, true, true); else TG_STEP_LAUNCH(true, true, false); }
+            else { if (g) TG_STEP_LAUNCH(true, false, true); else TG_STEP_LAUNCH(true, false, false); }
+        } else {
+            if (r) { if (g) TG_STEP_LAUNCH(false, true, true); else TG_STEP_LAUNCH(false, true, false); }
+            else { if (g) TG_STEP_LAUNCH(false, false, true); else TG_STEP_LAUNCH(false, false, false); }
+        }
+#undef TG_STEP_LAUNCH
+    }
+};
+static_assert(kStepShapeThreads[0] == 512 && kStepShapeBlocks[0] == 2 && kStepShapeThreads[1] == 384 &&
+                  kStepShapeBlocks[1] == 3, "step kernel shapes");
+using StepForms0 = StepForms<512, 2>;
+using StepForms1 = StepForms<384, 3>;
+
 cudaError_t configure_step_kernels() {
     const int smem = (int)sizeof(SmemStep);
-    const void* k[4] = {(const void*)step_kernel<kStepThreads, false, false>,
-                        (const void*)step_kernel<kStepThreads, true, false>,
-                        (const void*)step_kernel<kStepThreads, false, true>,
-                        (const void*)step_kernel<kStepThreads, true, true>};
-    for (const void* f : k) {
-        const cudaError_t err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (err != cudaSuccess) return err;
-    }
+    for (int k = 0; k < 8; ++k)
+        for (int shape = 0; shape < kStepShapes; ++shape) {
+            const void* f = shape == 0 ? StepForms0::fn(k) : StepForms1::fn(k);
+            cudaError_t err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            // 384 x 3: the whole carveout, so that three items' shared memory
+            // fits on an SM (512 x 2 keeps the rest of the SM's 256 KB as L1)
+            if (err == cudaSuccess && shape == 1)
+                err = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                           (int)cudaSharedmemCarveoutMaxShared);
+            if (err != cudaSuccess) return err;
+        }
     return cudaSuccess;
 }
 
-int step_kernel_resident_ctas() {
+int step_kernel_resident_ctas(int shape) {
     int dev = 0, sms = 0, per_sm = 0;
+    if (shape < 0 || shape >= kStepShapes) return 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<kStepThreads, true, false>, kStepThreads,
-                                                      sizeof(SmemStep)) != cudaSuccess)
+    const void* f = shape == 0 ? StepForms0::fn(1) : StepForms1::fn(1);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kStepShapeThreads[shape], sizeof(SmemStep)) !=
+        cudaSuccess)
         return 0;
     return sms * per_sm;
 }
 
 cudaError_t launch_step(const StepArgs& a, int n_items, cudaStream_t s) {
     if (n_items == 0) return cudaSuccess;
+    if (a.shape < 0 || a.shape >= kStepShapes) return cudaErrorInvalidValue;
     const size_t smem = sizeof(SmemStep);
+    int blocks = n_items;
     if (a.persistent) {
         if (!a.ctl || a.n_items != n_items) return cudaErrorInvalidValue;
         const int ctas = a.resident_ctas;
         if (ctas <= 0) return cudaErrorInvalidConfiguration;
         cudaError_t err = cudaMemsetAsync(&a.ctl->counter, 0, sizeof(uint32_t), s);
         if (err != cudaSuccess) return err;
-        if (a.P.rho > 0.0f) step_kernel<kStepThreads, true, true><<<min(ctas, n_items), kStepThreads, smem, s>>>(a);
-        else step_kernel<kStepThreads, true, false><<<min(ctas, n_items), kStepThreads, smem, s>>>(a);
-    } else {
-        if (a.P.rho > 0.0f) step_kernel<kStepThreads, false, true><<<n_items, kStepThreads, smem, s>>>(a);
-        else step_kernel<kStepThreads, false, false><<<n_items, kStepThreads, smem, s>>>(a);
+        blocks = min(ctas, n_items);
     }
+    if (a.shape == 0) StepForms0::launch(a, blocks, a.persistent != 0, smem, s);
+    else StepForms1::launch(a, blocks, a.persistent != 0, smem, s);
     return cudaGetLastError();
 }
 

@@ -10,8 +10,9 @@
 //                   dead override (Eqs. 25, 28), agg_force terms (Eq. 32)
 //   noisy_ft        3x3 crosstalk (Eq. 31), drift / white noise,
 //                   quantisation, dead override of the force/torque channels
-// Smem is any shared-memory layout with the per-taxel arrays fc, hx, ag
-// ([6][capacity] floats) and bits.
+// Smem is any shared-memory layout with the per-taxel arrays fc, hx
+// ([6][capacity] floats), dn ([5][capacity]: clean depth, noisy depth,
+// probe normal) and bits.
 #pragma once
 #include <cstdint>
 
@@ -65,12 +66,15 @@ __device__ __forceinline__ bool raycast_obj(const ObjDev& o, const ParamsDev& P)
     return o.kind == TG_OBJ_MESH && P.depth_backend != 0;
 }
 
-// FP32 object-frame query point q^ = M x + t and scaled SDF s phi(q^)
+// FP32 object-frame query point q^ = M x + t and scaled SDF s phi(q^).
+// GRID: the object is known to be a plain SDF grid (a kernel form compiled
+// for scenes whose objects are all grids: no dispatch on the kind).
+template <bool GRID = false>
 __device__ __forceinline__ float fast_query(const float* rec, const ObjDev& obj, float x0, float x1, float x2) {
     const float3 q = f3(fmaf(rec[0], x0, fmaf(rec[1], x1, fmaf(rec[2], x2, rec[18]))),
                         fmaf(rec[3], x0, fmaf(rec[4], x1, fmaf(rec[5], x2, rec[19]))),
                         fmaf(rec[6], x0, fmaf(rec[7], x1, fmaf(rec[8], x2, rec[20]))));
-    return rec[38] * sdf_phi_fast(obj, q);
+    return rec[38] * (GRID ? grid_phi_fast(obj, q) : sdf_phi_fast(obj, q));
 }
 
 // A taxel clear of the surface (or an inactive filler, R = 0): depth 0,
@@ -102,7 +106,7 @@ struct CleanReading {
 // noise the noisy readout's radius max(0, R + eps) gives a second depth, its
 // own Schmitt decision (flag bit 2) and a second force (same normal and
 // velocities).  Pure: the caller stores the results (store_clean).
-template <bool RADIUS>  // probe-radius noise on (rho > 0)
+template <bool RADIUS, bool GRID = false>  // probe-radius noise on (rho > 0); GRID as in fast_query
 __device__ __forceinline__ CleanReading refine_compute(const ParamsDev& P, const float* nq_phi, const float* nq_phi_lo,
                                                        const float* nq_grad, int64_t T, int64_t gid0,
                                                        const float* rec, const ObjDev& obj,
@@ -120,13 +124,14 @@ __device__ __forceinline__ CleanReading refine_compute(const ParamsDev& P, const
     float3 go;
     const float scale = rec[38];
     df phid;
-    if (phi_precomputed(obj, P)) {
+    if (!GRID && phi_precomputed(obj, P)) {
         // a learned SDF has no compensated form (its FP32 phi and gradient);
         // the raycast backend's phi is a compensated pair (its face normal)
         phid = raycast_obj(obj, P) ? df{nq_phi[g], nq_phi_lo[g]} : df_from(nq_phi[g]);
         go = f3(nq_grad[g], nq_grad[T + g], nq_grad[2 * T + g]);
     } else {
-        phid = df_mul_f(sdf_refine(obj, df3{qd[0], qd[1], qd[2]}, &go), scale);
+        const df3 qq{qd[0], qd[1], qd[2]};
+        phid = df_mul_f(GRID ? grid_refine(obj, qq, &go) : sdf_refine(obj, qq, &go), scale);
     }
     const df dd = df_add_f(df_neg(phid), R);  // R - phi
     CleanReading out;
@@ -204,11 +209,11 @@ __device__ __forceinline__ void store_clean_out(const StepArgs& a, int64_t g, fl
     for (int c = 0; c < 6; ++c) __stcs(a.ft_clean + c * T + g, f[c]);
 }
 
-template <bool RADIUS>
+template <bool RADIUS, bool GRID = false>
 __device__ __forceinline__ CleanReading refine_taxel(const StepArgs& a, const float* rec, const ObjDev& obj,
                                                      int64_t g, float x0, float x1, float x2, float R,
                                                      uint8_t flags, uint32_t step) {
-    const CleanReading cr = refine_compute<RADIUS>(a.P, a.nq_phi, a.nq_phi_lo, a.nq_grad, a.n_taxels, a.gid0, rec,
+    const CleanReading cr = refine_compute<RADIUS, GRID>(a.P, a.nq_phi, a.nq_phi_lo, a.nq_grad, a.n_taxels, a.gid0, rec,
                                                    obj, g, x0, x1, x2, R, flags, step);
     store_clean(a, g, cr);
     return cr;
@@ -374,7 +379,7 @@ __device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, i
         }
     }
     if (walk_d) s.drift_d = __ldcs(a.drift + g);
-    const float d = S.ag[0][i];
+    const float d = S.dn[0][i];
     // the depth and force the noisy chain starts from: the clean ones, or with
     // probe-radius noise those of the perturbed radius (refined taxels; the
     // others are clear of it)
@@ -383,7 +388,7 @@ __device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, i
     for (int c = 0; c < 6; ++c) f_in[c] = S.fc[c][i];
     if constexpr (RADIUS) {
         const bool near = bits & BIT_NEAR;
-        d_in = near ? S.ag[1][i] : 0.0f;
+        d_in = near ? S.dn[1][i] : 0.0f;
 #pragma unroll
         for (int c = 0; c < 6; ++c) f_in[c] = near ? S.hx[c][i] : 0.0f;
     }
@@ -413,8 +418,8 @@ __device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, i
     for (int c = 0; c < 6; ++c) S.hx[c][i] = o.hx[c];
     if (walk_d) __stcs(a.drift + g, o.drift_d);
     __stcs(a.depth_noisy + g, o.xd);
-    S.ag[0][i] = d * n0; S.ag[1][i] = d * n1; S.ag[2][i] = d * n2;
-    S.ag[3][i] = o.xd * n0; S.ag[4][i] = o.xd * n1; S.ag[5][i] = o.xd * n2;
+    S.dn[1][i] = o.xd;
+    S.dn[2][i] = n0; S.dn[3][i] = n1; S.dn[4][i] = n2;
 }
 
 // Inactive filler: zero clean and noisy depth, clean force/torque and
@@ -425,10 +430,9 @@ __device__ __forceinline__ void noise_state_filler(const StepArgs& a, Smem& S, i
     store_clean_out(a, g, 0.f, zero);
     __stcs(a.depth_noisy + g, 0.f);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        S.hx[c][i] = 0.f;
-        S.ag[c][i] = 0.f;
-    }
+    for (int c = 0; c < 6; ++c) S.hx[c][i] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) S.dn[c][i] = 0.f;
 }
 
 // 3x3 crosstalk (Eq. 31) of the six force/torque channels at taxel i,
@@ -567,15 +571,23 @@ __device__ __forceinline__ void link_quantity(const StepArgs& a, const Smem& S, 
         a.link_count[rec * 2 + bit] = cnt;
         return;
     }
-    const float* src;
+    Acc acc{0.f, 0.f};
     int col;
     float scale = 1.0f;
-    if (qn < 6) { src = S.fc[qn]; col = qn; }
-    else if (qn < 9) { src = S.ag[2 - (qn - 6)]; col = 12 + (qn - 6); scale = 1e4f; }
-    else if (qn < 12) { src = S.ag[5 - (qn - 9)]; col = 15 + (qn - 9); scale = 1e4f; }
-    else { src = noisy[qn - 14]; col = 6 + (qn - 14); }
-    Acc acc{0.f, 0.f};
-    for (int i = s0; i < s1; ++i) acc_add(acc, src[i]);
+    if (qn < 6 || qn >= 14) {
+        const float* src = qn < 6 ? S.fc[qn] : noisy[qn - 14];
+        col = qn < 6 ? qn : 6 + (qn - 14);
+        for (int i = s0; i < s1; ++i) acc_add(acc, src[i]);
+    } else {
+        // agg_force terms d n (clean or noisy depth), each a single rounded product
+        const bool nz = qn >= 9;
+        const int axis = nz ? 2 - (qn - 9) : 2 - (qn - 6);  // ZYX
+        const float* d = S.dn[nz ? 1 : 0];
+        const float* nv = S.dn[2 + axis];
+        col = nz ? 15 + (qn - 9) : 12 + (qn - 6);
+        scale = 1e4f;
+        for (int i = s0; i < s1; ++i) acc_add(acc, __fmul_rn(d[i], nv[i]));
+    }
     a.link_out[rec * kLinkOut + col] = scale * (acc.s + acc.c);
 }
 

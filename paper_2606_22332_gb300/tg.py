@@ -111,7 +111,7 @@ class TuneReport(C.Structure):
 
 
 # step-kernel schedules (tg_schedule), by name
-SCHEDULES = ("grid", "persistent", "pipe1024", "pipe768", "pipe512")
+SCHEDULES = ("grid", "persistent", "pipe1024", "pipe768", "pipe512", "grid384", "persistent384")
 # sensor kernels with a tuned launch shape (tg_sensor_kernel), by name
 SENSOR_KERNELS = ("prox", "pc_prox", "markers")
 SENSOR_THREADS = (128, 256, 512)

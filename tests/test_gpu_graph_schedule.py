@@ -87,7 +87,7 @@ def test_env_params_with_domain_randomisation_is_rejected(tg):
     sc.close()
 
 
-SCHEDULES = ("grid", "persistent", "pipe1024", "pipe768", "pipe512")
+SCHEDULES = ("grid", "persistent", "pipe1024", "pipe768", "pipe512", "grid384", "persistent384")
 
 
 @pytest.mark.parametrize("schedule", SCHEDULES)
@@ -114,7 +114,7 @@ def test_schedules_give_identical_results(tg, schedule, sorted_, uneven):
     ref.close(); sc.close()
 
 
-@pytest.mark.parametrize("schedule", ["grid", "persistent", "pipe1024"])
+@pytest.mark.parametrize("schedule", ["grid", "persistent", "pipe1024", "grid384"])
 def test_graph_replay_matches_oracle_and_seek(tg, schedule):
     wl = _grid_workload(16, 6)
     sc = tg.Scene.from_workload(wl, sensors=tg.TG_SENSOR_DIST)

@@ -84,7 +84,7 @@ def test_sensor_launch_shapes_give_identical_results(tg, wl, reference, kernel, 
 
 def test_autotune_times_every_sensor_shape(tg, wl, reference):
     out, rep, shape = _outputs(tg, wl, tune=True)
-    assert len(rep["candidates"]) == 10
+    assert len(rep["candidates"]) == 2 * len(tg.SCHEDULES)
     got = {(c["kernel"], c["threads"]) for c in rep["sensor_candidates"]}
     assert got == {(k, t) for k in ("prox", "pc_prox", "markers") for t in (128, 256, 512)}
     assert all(c["ms_per_step"] > 0 for c in rep["sensor_candidates"])
