@@ -88,7 +88,8 @@ def parse():
     ap.add_argument("--oracle-objects", type=int, default=2, help="objects whose envs form the oracle sample")
     ap.add_argument("--oracle-steps", type=int, default=300, help="steps of the cpu_baseline leg")
     ap.add_argument("--schedule", default="auto",
-                    choices=["auto"] + [f"{k}{s}" for k in ("grid", "persistent", "pipe1024", "pipe768", "pipe512")
+                    choices=["auto"] + [f"{k}{s}" for k in ("grid", "persistent", "pipe1024", "pipe768", "pipe512",
+                                                            "grid384", "persistent384")
                                         for s in ("", "-sorted")],
                     help="step-kernel schedule: picked by the autotuner (auto) or fixed")
     return ap.parse_args()

@@ -254,7 +254,8 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
     for (int i = tid; i < n; i += NT) {
         const int64_t g = it.taxel_begin + i;
         const uint8_t bits = S.bits[i];
-        if (bits & BIT_ACTIVE) noise_state<RADIUS>(a, S, i, g, ep, step, bits);
+        if (bits & BIT_ACTIVE)
+            noise_state<RADIUS>(a, S, i, g, ep, step, bits, __ldcs(a.nx + g), __ldcs(a.ny + g), __ldcs(a.nz + g));
         else noise_state_filler(a, S, i, g);
     }
     __syncthreads();

@@ -55,6 +55,18 @@ __device__ __forceinline__ void acc_add(Acc& a, float x) {
 // len <= 1024 that is below 1.3e-4 < 1/(2 len), so the floor is exact.
 __device__ __forceinline__ int uni_div(int i, float inv) { return (int)(((float)i + 0.5f) * inv); }
 
+// link of item taxel i from the item's static layout
+__device__ __forceinline__ int meta_link_of(const ItemMeta& M, int i) {
+    if (M.uni_len) return uni_div(i, M.uni_inv_len);
+    int lo = 0, hi = M.nl - 1;  // last start <= i
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (M.start[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Objects whose phi comes from a query kernel run ahead of the step kernel:
 // a learned SDF, and a mesh answered by the raycast backend (its phi is a
 // float pair, hi in nq_phi and lo in nq_phi_lo; a phi above R + 1 um marks a
@@ -353,13 +365,13 @@ __device__ __forceinline__ uint8_t delay_readout(const StepArgs& a, int64_t g, u
 // the first store: the compiler cannot move a load above a store to a
 // pointer that may alias it, and every such barrier would cost a further
 // round trip to memory.
-template <bool RADIUS, class Smem>
-__device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, int64_t g, uint32_t ep, uint32_t step,
-                                            uint8_t bits) {
+// (n0, n1, n2) is the taxel's probe normal, loaded by the caller (from HBM
+// or from a staged copy in shared memory).
+// The noise state taxel g's step reads (loads only; noise_apply uses it).
+__device__ __forceinline__ NoiseIn noise_load(const StepArgs& a, int64_t g) {
     const ParamsDev& P = a.P;
     const int64_t T = a.n_taxels;
     const bool hyst_d = hyst_depth_on(P), hyst_f = hyst_ft_on(P), walk_d = drift_depth_on(P);
-    const float n0 = __ldcs(a.nx + g), n1 = __ldcs(a.ny + g), n2 = __ldcs(a.nz + g);
     NoiseIn s;
     s.prev_d = s.xi_d = s.drift_d = 0.0f;
 #pragma unroll
@@ -379,6 +391,17 @@ __device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, i
         }
     }
     if (walk_d) s.drift_d = __ldcs(a.drift + g);
+    return s;
+}
+
+// noise_state from state already loaded (noise_load), so that a thread can
+// have several taxels' loads in flight before the first of them is used
+template <bool RADIUS, class Smem>
+__device__ __forceinline__ void noise_apply(const StepArgs& a, Smem& S, int i, int64_t g, uint32_t ep, uint32_t step,
+                                            uint8_t bits, float n0, float n1, float n2, const NoiseIn& s) {
+    const ParamsDev& P = a.P;
+    const int64_t T = a.n_taxels;
+    const bool hyst_d = hyst_depth_on(P), hyst_f = hyst_ft_on(P), walk_d = drift_depth_on(P);
     const float d = S.dn[0][i];
     // the depth and force the noisy chain starts from: the clean ones, or with
     // probe-radius noise those of the perturbed radius (refined taxels; the
@@ -420,6 +443,13 @@ __device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, i
     __stcs(a.depth_noisy + g, o.xd);
     S.dn[1][i] = o.xd;
     S.dn[2][i] = n0; S.dn[3][i] = n1; S.dn[4][i] = n2;
+}
+
+template <bool RADIUS, class Smem>
+__device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, int64_t g, uint32_t ep, uint32_t step,
+                                            uint8_t bits, float n0, float n1, float n2) {
+    const NoiseIn s = noise_load(a, g);
+    noise_apply<RADIUS>(a, S, i, g, ep, step, bits, n0, n1, n2, s);
 }
 
 // Inactive filler: zero clean and noisy depth, clean force/torque and
@@ -521,6 +551,34 @@ __device__ __forceinline__ void noisy_core(const ParamsDev& P, uint64_t gid, uin
     }
 }
 
+// the force/torque drift state of taxel g (zeros when the drift is off)
+__device__ __forceinline__ void noisy_drift_load(const StepArgs& a, int64_t g, float* dr) {
+    const int64_t T = a.n_taxels;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) dr[c] = drift_ft_on(a.P) ? __ldcs(a.drift + (1 + c) * T + g) : 0.0f;
+}
+
+// noisy_ft of an active taxel from its drift state already loaded
+template <class Smem, class Out>
+__device__ __forceinline__ void noisy_ft_apply(const StepArgs& a, const Smem& S, Out out, int i, int64_t g,
+                                               uint32_t ep, uint32_t step, uint8_t bits, int base, int r, int cc,
+                                               int rows, int cols, bool wrap, float* dr) {
+    const ParamsDev& P = a.P;
+    const int64_t T = a.n_taxels;
+    float z[6];
+    crosstalk(P, S.hx, i, base, r, cc, rows, cols, wrap, z);
+    noisy_core(P, (uint64_t)(a.gid0 + g), ep, step, bits, z, dr);
+    if (drift_ft_on(P)) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) __stcs(a.drift + (1 + c) * T + g, dr[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        __stcs(a.ft_noisy + c * T + g, z[c]);
+        out[c][i] = z[c];
+    }
+}
+
 // Noisy force/torque of taxel i at lattice (r, cc) of a rows x cols lattice
 // whose first taxel is `base` in the hx arrays; writes ft_noisy and out[.][i].
 template <class Smem, class Out>
@@ -538,22 +596,8 @@ __device__ __forceinline__ void noisy_ft(const StepArgs& a, const Smem& S, Out o
         return;
     }
     float dr[6];
-    if (drift_ft_on(P)) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) dr[c] = __ldcs(a.drift + (1 + c) * T + g);
-    }
-    float z[6];
-    crosstalk(P, S.hx, i, base, r, cc, rows, cols, wrap, z);
-    noisy_core(P, (uint64_t)(a.gid0 + g), ep, step, bits, z, dr);
-    if (drift_ft_on(P)) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) __stcs(a.drift + (1 + c) * T + g, dr[c]);
-    }
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        __stcs(a.ft_noisy + c * T + g, z[c]);
-        out[c][i] = z[c];
-    }
+    noisy_drift_load(a, g, dr);
+    noisy_ft_apply(a, S, out, i, g, ep, step, bits, base, r, cc, rows, cols, wrap, dr);
 }
 
 // One per-link quantity, summed over taxels [s0, s1) in lattice order with

@@ -34,6 +34,7 @@
 // for its other copies in flight and stops.
 #include <cstdint>
 
+#include "bulk.cuh"
 #include "step_common.cuh"
 
 namespace tg {
@@ -77,48 +78,6 @@ struct alignas(16) SmemPipe {
 };
 static_assert(sizeof(SmemPipe) <= 227 * 1024, "one CTA per SM");
 static_assert(kStride * 4 % 16 == 0 && kFlagStride % 16 == 0 && sizeof(Geo) % 16 == 0, "bulk copy alignment");
-
-__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 :: "r"(saddr(dst)), "l"(src), "r"(bytes), "r"(saddr(mbar)) : "memory");
-}
-
-// the barrier's phase completes once `bytes` have landed (the arrival is this thread's)
-__device__ __forceinline__ void mbar_expect(uint64_t* mbar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(saddr(mbar)), "r"(bytes) : "memory");
-}
-
-// bounded wait for the phase of the given parity; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
-    const uint32_t a = saddr(mbar);
-    uint32_t done = 0;
-    for (int it = 0; it < (1 << 22) && !done; ++it)
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-    return done != 0;
-}
-
-__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// Bulk copy of n elements of esz bytes starting at element `first` of
-// `base`, from the 16-byte boundary at or below it to the one at or above
-// its end (the buffers in HBM carry at least 16 bytes of slack past their
-// end).  Adds the bytes to tx; returns the lead-in in elements.
-__device__ __forceinline__ int stage(void* dst, const void* base, int64_t first, int n, int esz, uint64_t* mbar,
-                                     uint32_t& tx) {
-    const uintptr_t a = (uintptr_t)base + (uintptr_t)first * (uintptr_t)esz;
-    const uintptr_t a0 = a & ~(uintptr_t)15;
-    const uintptr_t a1 = (a + (uintptr_t)n * (uintptr_t)esz + 15) & ~(uintptr_t)15;
-    const uint32_t bytes = (uint32_t)(a1 - a0);
-    if (bytes) bulk_load(dst, reinterpret_cast<const void*>(a0), bytes, mbar);
-    tx += bytes;
-    return (int)((a - a0) / (uintptr_t)esz);
-}
 
 // geometry, flags, link records, item layout and object of the item in `r`
 __device__ void issue_geo(const StepArgs& a, SmemPipe& S, int buf, const SlotRec& r) {
@@ -176,25 +135,12 @@ __device__ void issue_dr(const StepArgs& a, SmemPipe& S, int buf, const SlotRec&
 
 // order record of position p into S.slot[ring] (cp.async: the issuing thread waits for it)
 __device__ __forceinline__ void fetch_slot(const StepArgs& a, SmemPipe& S, int ring, int p) {
-    const SlotRec* src = a.slots + p;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(saddr(&S.slot[ring])), "l"(src) : "memory");
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(saddr(reinterpret_cast<char*>(&S.slot[ring]) + 16)),
-                 "l"(reinterpret_cast<const char*>(src) + 16) : "memory");
-    asm volatile("cp.async.commit_group;" ::: "memory");
+    static_assert(sizeof(SlotRec) == 32, "one 32-byte record");
+    cp_async32(&S.slot[ring], a.slots + p);
 }
-__device__ __forceinline__ void wait_slots() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void wait_slots() { cp_async_wait(); }
 
-// link of item taxel i
-__device__ __forceinline__ int link_of(const ItemMeta& M, int i) {
-    if (M.uni_len) return uni_div(i, M.uni_inv_len);
-    int lo = 0, hi = M.nl - 1;  // last start <= i
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (M.start[mid] <= i) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
+__device__ __forceinline__ int link_of(const ItemMeta& M, int i) { return meta_link_of(M, i); }
 
 // One per-link quantity over taxels [s0, s1) in lattice order, as
 // link_quantity in step_common.cuh (same sources, same compensated sums);
