@@ -42,6 +42,17 @@ __device__ __forceinline__ df df_add(df x, df y) {
     return fast_two_sum(s.hi, s.lo);
 }
 
+// x + y with a single TwoSum, on the high parts.  Its error is at most
+// ~2^-23 (|x.lo| + |y.lo|) + 2^-46 |x + y|: the accurate df_add's bound as
+// a relative one, except where the high parts cancel, where it stays this
+// absolute bound.  For query points and interpolated distances of a few
+// centimetres, needed to ~1e-12 m, that is ~1e-15 m.
+__device__ __forceinline__ df df_add_abs(df x, df y) {
+    df s = two_sum(x.hi, y.hi);
+    s.lo += x.lo + y.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+
 __device__ __forceinline__ df df_neg(df x) { return df{-x.hi, -x.lo}; }
 __device__ __forceinline__ df df_sub(df x, df y) { return df_add(x, df_neg(y)); }
 __device__ __forceinline__ df df_add_f(df x, float b) {

@@ -149,38 +149,61 @@ __device__ __forceinline__ float grid_phi_fast(const ObjDev& o, float3 q) {
     return phi + o2 * rsqrtf(fmaxf(o2, 1e-30f));
 }
 
-__device__ __forceinline__ df df_lerp(df a, df b, df f) { return df_add(a, df_mul(f, df_sub(b, a))); }
+// a + f (b - a) for corner values a, b (floats) at a compensated fraction f:
+// b - a as an exact pair, then one compensated product and sum
+__device__ __forceinline__ df df_lerp_ff(float a, float b, df f) {
+    return df_add_f(df_mul(f, two_sum(b, -a)), a);
+}
+// the same between compensated values (sums with the absolute bound of
+// df_add_abs: the values are distances of a few centimetres at most)
+__device__ __forceinline__ df df_lerp_abs(df a, df b, df f) {
+    return df_add_abs(a, df_mul(f, df_add_abs(b, df_neg(a))));
+}
 
+// Compensated phi at a compensated query point (near-contact taxels): the
+// cell and in-cell fractions from the compensated point, the trilinear
+// interpolant of the stored corner values with compensated products and
+// sums (~1e-15 m absolute), the FP32 gradient of the interpolant.  Points
+// outside the box add their compensated distance to it.
 __device__ __forceinline__ df grid_refine(const ObjDev& o, df3 q, float3* g) {
     df qa[3] = {q.x, q.y, q.z};
+    bool inside = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) inside = inside && !df_lt(qa[a], df_from(o.lo[a])) && !df_gt(qa[a], df_from(o.hi[a]));
+    df out2 = df_from(0.0f);
+    if (!inside) {  // (no near-contact probe of a padded box lies here)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            df ca = qa[a];
+            if (df_lt(ca, df_from(o.lo[a]))) ca = df_from(o.lo[a]);
+            if (df_gt(ca, df_from(o.hi[a]))) ca = df_from(o.hi[a]);
+            const df d = df_sub(qa[a], ca);
+            out2 = df_add(out2, df_mul(d, d));
+            qa[a] = ca;
+        }
+    }
     int i[3];
     df f[3];
-    df out2 = df_from(0.0f);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        df ca = qa[a];
-        if (df_lt(ca, df_from(o.lo[a]))) ca = df_from(o.lo[a]);
-        if (df_gt(ca, df_from(o.hi[a]))) ca = df_from(o.hi[a]);
-        df d = df_sub(qa[a], ca);
-        out2 = df_add(out2, df_mul(d, d));
-        df u = df_mul(df_sub(ca, df_from(o.lo[a])), df{o.inv_h_hi[a], o.inv_h_lo[a]});
+        const df u = df_mul(df_add_f(qa[a], -o.lo[a]), df{o.inv_h_hi[a], o.inv_h_lo[a]});
         int ii = df_floor_int(u);
         ii = min(max(ii, 0), o.dims[a] - 2);
         i[a] = ii;
         f[a] = df_add_f(u, -(float)ii);
     }
-    Corners v = grid_corners(o, i[0], i[1], i[2]);
-    df c00 = df_lerp(df_from(v.v000), df_from(v.v100), f[0]);
-    df c10 = df_lerp(df_from(v.v010), df_from(v.v110), f[0]);
-    df c01 = df_lerp(df_from(v.v001), df_from(v.v101), f[0]);
-    df c11 = df_lerp(df_from(v.v011), df_from(v.v111), f[0]);
-    df c0 = df_lerp(c00, c10, f[1]);
-    df c1 = df_lerp(c01, c11, f[1]);
-    df phi = df_lerp(c0, c1, f[2]);
+    const Corners v = grid_corners(o, i[0], i[1], i[2]);
+    const df c00 = df_lerp_ff(v.v000, v.v100, f[0]);
+    const df c10 = df_lerp_ff(v.v010, v.v110, f[0]);
+    const df c01 = df_lerp_ff(v.v001, v.v101, f[0]);
+    const df c11 = df_lerp_ff(v.v011, v.v111, f[0]);
+    const df c0 = df_lerp_abs(c00, c10, f[1]);
+    const df c1 = df_lerp_abs(c01, c11, f[1]);
+    const df phi = df_lerp_abs(c0, c1, f[2]);
     float3 gr = trilinear_grad(v, f[0].hi, f[1].hi, f[2].hi);
     gr = f3(gr.x * o.inv_h_hi[0], gr.y * o.inv_h_hi[1], gr.z * o.inv_h_hi[2]);
     *g = normalize_or(gr, normalize_or(f3(q.x.hi, q.y.hi, q.z.hi), f3(0.f, 0.f, 1.f)));
-    return df_add(phi, df_sqrt(out2));
+    return inside ? phi : df_add(phi, df_sqrt(out2));
 }
 
 // ------------------------------------------------------------------ analytic

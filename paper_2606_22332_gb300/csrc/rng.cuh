@@ -68,9 +68,15 @@ __device__ __forceinline__ float u24(uint32_t x) { return ((float)(x >> 8) + 0.5
 // two standard normals from two words: r = sqrt(-2 ln u1), angle 2 pi u2.
 // The angle is evaluated as pi (2 u2 - 1) + pi, inside [-pi, pi) where the
 // hardware sine/cosine is accurate to ~4e-7 absolute; cos and sin of the
-// shifted angle change sign.
+// shifted angle change sign.  The root is the hardware approximation (a
+// relative error of a few 2^-24, within the normals' ~1e-6 agreement).
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
-    const float r = sqrtf(-2.0f * logf(u24(a)));
+    const float r = sqrt_approx(-2.0f * logf(u24(a)));
     float s, c;
     __sincosf(3.14159265358979323846f * (2.0f * u24(b) - 1.0f), &s, &c);
     return make_float2(-r * c, -r * s);

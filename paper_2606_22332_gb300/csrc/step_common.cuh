@@ -37,16 +37,19 @@ __device__ __forceinline__ float quantise(const NoiseDev& g, float y) {
     return g.quant > 0.0f ? g.quant * rintf(y / g.quant) : y;
 }
 
-// compensated accumulation (Neumaier)
+// compensated accumulation (Kahan): the sum's error stays within ~2 eps
+// sum |x| whatever the order of magnitudes, at four additions a term
 struct Acc {
     float s, c;
 };
 __device__ __forceinline__ void acc_add(Acc& a, float x) {
-    float t = a.s + x;
-    if (fabsf(a.s) >= fabsf(x)) a.c += (a.s - t) + x;
-    else a.c += (x - t) + a.s;
+    const float y = x - a.c;
+    const float t = a.s + y;
+    a.c = (t - a.s) - y;
     a.s = t;
 }
+// the sum, with the last term's lost part put back
+__device__ __forceinline__ float acc_value(const Acc& a) { return a.s - a.c; }
 
 // Link of item taxel i (and, in B, its lattice row and column) for a uniform
 // item: l = floor((i + 1/2) / len) evaluated as (i + 1/2) * fl(1/len) in
@@ -124,13 +127,15 @@ __device__ __forceinline__ CleanReading refine_compute(const ParamsDev& P, const
                                                        const float* rec, const ObjDev& obj,
                                                        int64_t g, float x0, float x1, float x2, float R,
                                                        uint8_t flags, uint32_t step) {
+    // compensated query point (sums with df_add_abs's absolute bound, ~1e-15 m
+    // for coordinates of a few centimetres)
     df qd[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
         df acc = df{rec[18 + r], rec[21 + r]};
-        acc = df_add(acc, df_mul_f(df{rec[3 * r], rec[9 + 3 * r]}, x0));
-        acc = df_add(acc, df_mul_f(df{rec[3 * r + 1], rec[9 + 3 * r + 1]}, x1));
-        acc = df_add(acc, df_mul_f(df{rec[3 * r + 2], rec[9 + 3 * r + 2]}, x2));
+        acc = df_add_abs(acc, df_mul_f(df{rec[3 * r], rec[9 + 3 * r]}, x0));
+        acc = df_add_abs(acc, df_mul_f(df{rec[3 * r + 1], rec[9 + 3 * r + 1]}, x1));
+        acc = df_add_abs(acc, df_mul_f(df{rec[3 * r + 2], rec[9 + 3 * r + 2]}, x2));
         qd[r] = acc;
     }
     float3 go;
@@ -632,7 +637,7 @@ __device__ __forceinline__ void link_quantity(const StepArgs& a, const Smem& S, 
         scale = 1e4f;
         for (int i = s0; i < s1; ++i) acc_add(acc, __fmul_rn(d[i], nv[i]));
     }
-    a.link_out[rec * kLinkOut + col] = scale * (acc.s + acc.c);
+    a.link_out[rec * kLinkOut + col] = scale * acc_value(acc);
 }
 
 }  // namespace tg

@@ -172,7 +172,7 @@ __device__ __forceinline__ void pipe_link_quantity(const StepArgs& a, const Smem
 #pragma unroll 4
         for (int i = s0; i < s1; ++i) acc_add(acc, __fmul_rn(d[i], n[i]));
     }
-    a.link_out[rec * kLinkOut + col] = scale * (acc.s + acc.c);
+    a.link_out[rec * kLinkOut + col] = scale * acc_value(acc);
 }
 
 template <int NT, bool RADIUS>
