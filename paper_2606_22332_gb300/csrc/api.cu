@@ -411,6 +411,7 @@ tg_status tg_create_scene(const tg_scene_desc* d, tg_scene** out) {
         if (d->taxel_offsets[e + 1] < d->taxel_offsets[e])
             return fail(nullptr, TG_ERR_INVALID_ARG, "taxel_offsets must be non-decreasing");
     const int64_t T = d->taxel_offsets[E];
+    if (T >= kMaxSceneTaxels - 64) return fail(nullptr, TG_ERR_INVALID_ARG, "a scene holds fewer than 2^31 taxels");
     if (T > 0 && (!d->x || !d->y || !d->z || !d->nx || !d->ny || !d->nz || !d->R))
         return fail(nullptr, TG_ERR_INVALID_ARG, "taxel geometry pointers are required");
     ParamsDev P;

@@ -10,6 +10,12 @@
 
 namespace tg {
 
+// Index of a taxel in the scene's per-taxel arrays.  A scene holds fewer
+// than 2^31 taxels, so the step kernels index with 32 bits: an address is
+// then one wide multiply-add on the array's (uniform) base.
+using tidx = uint32_t;
+constexpr int64_t kMaxSceneTaxels = (int64_t)1 << 31;
+
 constexpr int kMaxLinks = 255;       // u8 link ids
 constexpr int kItemCap = 1024;       // max taxels per work item (one CTA)
 // CTA shapes of the step kernel: threads per CTA and the resident CTAs per

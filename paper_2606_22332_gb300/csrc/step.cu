@@ -167,7 +167,7 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
     for (int i0 = tid; i0 < n; i0 += 2 * NT) {
         const int i1 = i0 + NT;
         const bool has1 = i1 < n;
-        const int64_t g0 = it.taxel_begin + i0, g1 = it.taxel_begin + (has1 ? i1 : i0);
+        const tidx g0 = (tidx)(it.taxel_begin + i0), g1 = (tidx)(it.taxel_begin + (has1 ? i1 : i0));
         const float R0 = __ldcs(a.R + g0), R1 = has1 ? __ldcs(a.R + g1) : 0.0f;
         const float x00 = __ldcs(a.x + g0), x01 = __ldcs(a.y + g0), x02 = __ldcs(a.z + g0);
         const float x10 = __ldcs(a.x + g1), x11 = __ldcs(a.y + g1), x12 = __ldcs(a.z + g1);
@@ -194,7 +194,7 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
         for (int u = 0; u < 2; ++u) {
             if (u == 1 && !has1) break;
             const int i = u ? i1 : i0;
-            const int64_t g = u ? g1 : g0;
+            const tidx g = u ? g1 : g0;
             const float R = u ? R1 : R0, phi = u ? phi1 : phi0;
             if (R > 0.0f && !isfinite(phi)) atomicAdd(a.err, 1u);
             // (with probe-radius noise the noisy readout's radius reaches R + rho)
@@ -229,7 +229,7 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
             else hi = mid - 1;
         }
         const float* st = &S.hx[0][0];
-        const CleanReading cr = refine_taxel<RADIUS, GRID>(a, S.rec[lo], obj, it.taxel_begin + i, st[i], st[kItemCap + i],
+        const CleanReading cr = refine_taxel<RADIUS, GRID>(a, S.rec[lo], obj, (tidx)(it.taxel_begin + i), st[i], st[kItemCap + i],
                                              st[2 * kItemCap + i], st[3 * kItemCap + i],
                                              (uint8_t)__float_as_uint(st[4 * kItemCap + i]), step);
 #pragma unroll
@@ -252,7 +252,7 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
 
     // ---- phase N: noise state of every taxel (independent state loads)
     for (int i = tid; i < n; i += NT) {
-        const int64_t g = it.taxel_begin + i;
+        const tidx g = (tidx)(it.taxel_begin + i);
         const uint8_t bits = S.bits[i];
         if (bits & BIT_ACTIVE)
             noise_state<RADIUS>(a, S, i, g, ep, step, bits, __ldcs(a.nx + g), __ldcs(a.ny + g), __ldcs(a.nz + g));
@@ -277,14 +277,14 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
             const int base = uni_div(i, S.uni_inv_len) * S.uni_len;
             const int j = i - base;
             const int r = uni_div(j, S.uni_inv_cols);
-            noisy_ft(a, S, S.fc, i, it.taxel_begin + i, ep, step, S.bits[i], base, r, j - r * S.uni_cols,
+            noisy_ft(a, S, S.fc, i, (tidx)(it.taxel_begin + i), ep, step, S.bits[i], base, r, j - r * S.uni_cols,
                      S.uni_rows, S.uni_cols, S.uni_wrap != 0);
             continue;
         }
         while (i >= S.start[l + 1]) ++l;
         const int j = i - S.start[l], cols = S.cols[l];
         const int r = j / cols;
-        noisy_ft(a, S, S.fc, i, it.taxel_begin + i, ep, step, S.bits[i], S.start[l], r, j - r * cols, S.rows[l],
+        noisy_ft(a, S, S.fc, i, (tidx)(it.taxel_begin + i), ep, step, S.bits[i], S.start[l], r, j - r * cols, S.rows[l],
                  cols, S.wrap[l] != 0);
     }
     __syncthreads();
@@ -329,7 +329,7 @@ __global__ void reset_kernel(const StepArgs a, const uint8_t* env_mask, uint32_t
     if (threadIdx.x == 0) episode_arr[e] = episode;
     const int64_t T = a.n_taxels;
     for (int i = threadIdx.x; i < it.n_taxels; i += blockDim.x) {
-        const int64_t g = it.taxel_begin + i;
+        const tidx g = (tidx)(it.taxel_begin + i);
         const uint64_t gid = (uint64_t)(a.gid0 + g);
         const bool active = a.R[g] > 0.0f;
         bool dead = false;

@@ -97,7 +97,7 @@ __device__ __forceinline__ float fast_query(const float* rec, const ObjDev& obj,
 // zero clean depth and force/torque are stored with the noise state, after
 // last step's values have been read there) and returns its shared-memory
 // bits.
-__device__ __forceinline__ uint8_t clear_taxel(const StepArgs& a, int64_t g, float R, uint8_t flags, float phi) {
+__device__ __forceinline__ uint8_t clear_taxel(const StepArgs& a, tidx g, float R, uint8_t flags, float phi) {
     __stcs(a.flags + g, (uint8_t)(flags & 2u));
     if (a.sensors & TG_SENSOR_DIST) __stcs(a.dist + g, R > 0.0f ? phi - R : 0.0f);
     return (uint8_t)(((flags & 2u) ? BIT_DEAD : 0u) | (R > 0.0f ? BIT_ACTIVE : 0u));
@@ -125,7 +125,7 @@ template <bool RADIUS, bool GRID = false>  // probe-radius noise on (rho > 0); G
 __device__ __forceinline__ CleanReading refine_compute(const ParamsDev& P, const float* nq_phi, const float* nq_phi_lo,
                                                        const float* nq_grad, int64_t T, int64_t gid0,
                                                        const float* rec, const ObjDev& obj,
-                                                       int64_t g, float x0, float x1, float x2, float R,
+                                                       tidx g, float x0, float x1, float x2, float R,
                                                        uint8_t flags, uint32_t step) {
     // compensated query point (sums with df_add_abs's absolute bound, ~1e-15 m
     // for coordinates of a few centimetres)
@@ -211,7 +211,7 @@ __device__ __forceinline__ CleanReading refine_compute(const ParamsDev& P, const
 
 // the flag byte and surface distance of a refined taxel (its clean depth and
 // force/torque are stored with the noise state, see clear_taxel)
-__device__ __forceinline__ void store_clean(const StepArgs& a, int64_t g, const CleanReading& cr) {
+__device__ __forceinline__ void store_clean(const StepArgs& a, tidx g, const CleanReading& cr) {
     __stcs(a.flags + g, cr.flags);
     if (a.sensors & TG_SENSOR_DIST) __stcs(a.dist + g, cr.dist);
 }
@@ -219,7 +219,7 @@ __device__ __forceinline__ void store_clean(const StepArgs& a, int64_t g, const 
 // The clean depth and force/torque outputs of taxel g, stored in the noise
 // state phase: with prev_out the previous values there are the hysteresis
 // state, read by that phase first.
-__device__ __forceinline__ void store_clean_out(const StepArgs& a, int64_t g, float d, const float* f) {
+__device__ __forceinline__ void store_clean_out(const StepArgs& a, tidx g, float d, const float* f) {
     const int64_t T = a.n_taxels;
     __stcs(a.depth_clean + g, d);
 #pragma unroll
@@ -228,7 +228,7 @@ __device__ __forceinline__ void store_clean_out(const StepArgs& a, int64_t g, fl
 
 template <bool RADIUS, bool GRID = false>
 __device__ __forceinline__ CleanReading refine_taxel(const StepArgs& a, const float* rec, const ObjDev& obj,
-                                                     int64_t g, float x0, float x1, float x2, float R,
+                                                     tidx g, float x0, float x1, float x2, float R,
                                                      uint8_t flags, uint32_t step) {
     const CleanReading cr = refine_compute<RADIUS, GRID>(a.P, a.nq_phi, a.nq_phi_lo, a.nq_grad, a.n_taxels, a.gid0, rec,
                                                    obj, g, x0, x1, x2, R, flags, step);
@@ -334,7 +334,7 @@ __device__ __forceinline__ int read_delay(const ParamsDev& P, uint64_t env_gid, 
 // into slot step mod ring_k, and the input of `rd` steps earlier comes out
 // of its slot into d_in, f_in and the returned bit (with rd = 0, the values
 // just written).
-__device__ __forceinline__ bool ring_step(const ParamsDev& P, float* ring, int64_t T, int64_t g, uint32_t step,
+__device__ __forceinline__ bool ring_step(const ParamsDev& P, float* ring, int64_t T, tidx g, uint32_t step,
                                           int rd, float& d_in, float* f_in, bool bit) {
     const uint32_t K = (uint32_t)P.ring_k;
     const uint32_t ws = step % K, rs = (ws + K - (uint32_t)rd) % K;
@@ -353,7 +353,7 @@ __device__ __forceinline__ bool ring_step(const ParamsDev& P, float* ring, int64
 // With a read delay: the delayed noisy-chain input replaces (d_in, f_in),
 // the reported noisy contact (the delayed bit, then the dead override) goes
 // into flag bit 3 and replaces BIT_NOISY in the returned bits.
-__device__ __forceinline__ uint8_t delay_readout(const StepArgs& a, int64_t g, uint32_t step, int rd, uint8_t bits,
+__device__ __forceinline__ uint8_t delay_readout(const StepArgs& a, tidx g, uint32_t step, int rd, uint8_t bits,
                                                  float& d_in, float* f_in) {
     const bool yn = bits & BIT_NOISY;
     const bool rep = ring_step(a.P, a.ring, a.n_taxels, g, step, rd, d_in, f_in, yn) && !(bits & BIT_DEAD);
@@ -373,7 +373,7 @@ __device__ __forceinline__ uint8_t delay_readout(const StepArgs& a, int64_t g, u
 // (n0, n1, n2) is the taxel's probe normal, loaded by the caller (from HBM
 // or from a staged copy in shared memory).
 // The noise state taxel g's step reads (loads only; noise_apply uses it).
-__device__ __forceinline__ NoiseIn noise_load(const StepArgs& a, int64_t g) {
+__device__ __forceinline__ NoiseIn noise_load(const StepArgs& a, tidx g) {
     const ParamsDev& P = a.P;
     const int64_t T = a.n_taxels;
     const bool hyst_d = hyst_depth_on(P), hyst_f = hyst_ft_on(P), walk_d = drift_depth_on(P);
@@ -402,7 +402,7 @@ __device__ __forceinline__ NoiseIn noise_load(const StepArgs& a, int64_t g) {
 // noise_state from state already loaded (noise_load), so that a thread can
 // have several taxels' loads in flight before the first of them is used
 template <bool RADIUS, class Smem>
-__device__ __forceinline__ void noise_apply(const StepArgs& a, Smem& S, int i, int64_t g, uint32_t ep, uint32_t step,
+__device__ __forceinline__ void noise_apply(const StepArgs& a, Smem& S, int i, tidx g, uint32_t ep, uint32_t step,
                                             uint8_t bits, float n0, float n1, float n2, const NoiseIn& s) {
     const ParamsDev& P = a.P;
     const int64_t T = a.n_taxels;
@@ -451,7 +451,7 @@ __device__ __forceinline__ void noise_apply(const StepArgs& a, Smem& S, int i, i
 }
 
 template <bool RADIUS, class Smem>
-__device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, int64_t g, uint32_t ep, uint32_t step,
+__device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, tidx g, uint32_t ep, uint32_t step,
                                             uint8_t bits, float n0, float n1, float n2) {
     const NoiseIn s = noise_load(a, g);
     noise_apply<RADIUS>(a, S, i, g, ep, step, bits, n0, n1, n2, s);
@@ -460,7 +460,7 @@ __device__ __forceinline__ void noise_state(const StepArgs& a, Smem& S, int i, i
 // Inactive filler: zero clean and noisy depth, clean force/torque and
 // staged values.
 template <class Smem>
-__device__ __forceinline__ void noise_state_filler(const StepArgs& a, Smem& S, int i, int64_t g) {
+__device__ __forceinline__ void noise_state_filler(const StepArgs& a, Smem& S, int i, tidx g) {
     const float zero[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     store_clean_out(a, g, 0.f, zero);
     __stcs(a.depth_noisy + g, 0.f);
@@ -557,7 +557,7 @@ __device__ __forceinline__ void noisy_core(const ParamsDev& P, uint64_t gid, uin
 }
 
 // the force/torque drift state of taxel g (zeros when the drift is off)
-__device__ __forceinline__ void noisy_drift_load(const StepArgs& a, int64_t g, float* dr) {
+__device__ __forceinline__ void noisy_drift_load(const StepArgs& a, tidx g, float* dr) {
     const int64_t T = a.n_taxels;
 #pragma unroll
     for (int c = 0; c < 6; ++c) dr[c] = drift_ft_on(a.P) ? __ldcs(a.drift + (1 + c) * T + g) : 0.0f;
@@ -565,7 +565,7 @@ __device__ __forceinline__ void noisy_drift_load(const StepArgs& a, int64_t g, f
 
 // noisy_ft of an active taxel from its drift state already loaded
 template <class Smem, class Out>
-__device__ __forceinline__ void noisy_ft_apply(const StepArgs& a, const Smem& S, Out out, int i, int64_t g,
+__device__ __forceinline__ void noisy_ft_apply(const StepArgs& a, const Smem& S, Out out, int i, tidx g,
                                                uint32_t ep, uint32_t step, uint8_t bits, int base, int r, int cc,
                                                int rows, int cols, bool wrap, float* dr) {
     const ParamsDev& P = a.P;
@@ -587,7 +587,7 @@ __device__ __forceinline__ void noisy_ft_apply(const StepArgs& a, const Smem& S,
 // Noisy force/torque of taxel i at lattice (r, cc) of a rows x cols lattice
 // whose first taxel is `base` in the hx arrays; writes ft_noisy and out[.][i].
 template <class Smem, class Out>
-__device__ __forceinline__ void noisy_ft(const StepArgs& a, const Smem& S, Out out, int i, int64_t g, uint32_t ep,
+__device__ __forceinline__ void noisy_ft(const StepArgs& a, const Smem& S, Out out, int i, tidx g, uint32_t ep,
                                          uint32_t step, uint8_t bits, int base, int r, int cc, int rows, int cols,
                                          bool wrap) {
     const ParamsDev& P = a.P;

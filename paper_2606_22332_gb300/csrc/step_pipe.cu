@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(NT, 1) step_pipe_kernel(const StepArgs a) {
             const bool act = i < n;
             bool near = false;
             if (act) {
-                const int64_t g = cur.taxel_begin + i;
+                const tidx g = (tidx)(cur.taxel_begin + i);
                 const float x0 = Gb.ch[0][Ld.geo[0] + i], x1 = Gb.ch[1][Ld.geo[1] + i], x2 = Gb.ch[2][Ld.geo[2] + i];
                 const float R = Gb.ch[3][Ld.geo[3] + i];
                 const uint8_t fl = Gb.flags[Ld.geo[kGeoCh] + i];
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(NT, 1) step_pipe_kernel(const StepArgs a) {
         const int nq = S.nq;
         for (int j = tid; j < n; j += NT) {
             const int i = S.order[j];
-            const int64_t g = cur.taxel_begin + i;
+            const tidx g = (tidx)(cur.taxel_begin + i);
             uint8_t bits;
             float d_in = 0.0f, f_in[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (j < nq) {
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(NT, 1) step_pipe_kernel(const StepArgs a) {
         for (int u = 0; u < kPer; ++u) {
             const int i = tid + u * NT;
             if (i >= n) break;
-            const int64_t g = cur.taxel_begin + i;
+            const tidx g = (tidx)(cur.taxel_begin + i);
             const uint8_t bits = S.bits[i];
             if (!(bits & BIT_ACTIVE)) {
 #pragma unroll
