@@ -33,8 +33,20 @@ __device__ __forceinline__ float hyst_update(const NoiseDev& g, float x, float* 
     return x + g.beta * xi;
 }
 
+// q rint(y / q); the step (q = 0: off) is a parameter of the scene, so the
+// division sits behind a branch every thread takes alike
 __device__ __forceinline__ float quantise(const NoiseDev& g, float y) {
-    return g.quant > 0.0f ? g.quant * rintf(y / g.quant) : y;
+    if (g.quant > 0.0f) y = g.quant * rintf(y / g.quant);
+    return y;
+}
+
+// the stuck readout of a dead taxel, lo + span u (one draw; none when the
+// span is 0, as when dead taxels read a constant)
+__device__ __forceinline__ float stuck_value(const ParamsDev& P, const NoiseDev& g, uint64_t gid, uint32_t ep,
+                                             int word) {
+    if (g.stuck_span == 0.0f) return g.stuck_lo;
+    const uint4 w = draw_rk(P.rk, gid, ep, TAG_STUCK);
+    return g.stuck_lo + g.stuck_span * u24(word == 0 ? w.x : (word == 1 ? w.y : w.z));
 }
 
 // compensated accumulation (Kahan): the sum's error stays within ~2 eps
@@ -50,6 +62,38 @@ __device__ __forceinline__ void acc_add(Acc& a, float x) {
 }
 // the sum, with the last term's lost part put back
 __device__ __forceinline__ float acc_value(const Acc& a) { return a.s - a.c; }
+
+// Compensated sum of a link's terms src[s0..s1) (deterministic): Kahan
+// accumulators over the even and the odd positions, two independent
+// dependency chains side by side, then combined.
+__device__ __forceinline__ float link_sum(const float* src, int s0, int s1) {
+    Acc e{0.f, 0.f}, o{0.f, 0.f};
+    int i = s0;
+#pragma unroll 4
+    for (; i + 1 < s1; i += 2) {
+        acc_add(e, src[i]);
+        acc_add(o, src[i + 1]);
+    }
+    if (i < s1) acc_add(e, src[i]);
+    acc_add(e, o.s);
+    acc_add(e, -o.c);
+    return acc_value(e);
+}
+
+// the same for the terms d[i] n[i], each product rounded on its own
+__device__ __forceinline__ float link_sum_prod(const float* d, const float* n, int s0, int s1) {
+    Acc e{0.f, 0.f}, o{0.f, 0.f};
+    int i = s0;
+#pragma unroll 4
+    for (; i + 1 < s1; i += 2) {
+        acc_add(e, __fmul_rn(d[i], n[i]));
+        acc_add(o, __fmul_rn(d[i + 1], n[i + 1]));
+    }
+    if (i < s1) acc_add(e, __fmul_rn(d[i], n[i]));
+    acc_add(e, o.s);
+    acc_add(e, -o.c);
+    return acc_value(e);
+}
 
 // Link of item taxel i (and, in B, its lattice row and column) for a uniform
 // item: l = floor((i + 1/2) / len) evaluated as (i + 1/2) * fl(1/len) in
@@ -192,7 +236,8 @@ __device__ __forceinline__ CleanReading refine_compute(const ParamsDev& P, const
         const float spin = P.k_omega * dot(Wc - Wl, mb);
         // Eqs. 4-9 with the Coulomb clamp at depth dep
         auto force = [&](float dep, float* f, float* tq) {
-            const float s = (P.alpha == 1.0f) ? dep : powf(dep, P.alpha);
+            float s = dep;
+            if (P.alpha != 1.0f) s = powf(dep, P.alpha);
             const float3 fnv = mb * (kk * s) + vn * (P.c * s);
             float sc = 1.0f;
             if (mu >= 0.0f && P.k_t * vtn > 0.0f) sc = fminf(1.0f, mu * sqrtf(dot(fnv, fnv)) / (P.k_t * vtn));
@@ -313,7 +358,7 @@ __device__ __forceinline__ NoiseOut noise_core(const ParamsDev& P, uint64_t gid,
         xd += P.depth.bias;
     }
     xd = quantise(P.depth, xd);
-    if (dead) xd = P.depth.stuck_lo + P.depth.stuck_span * u24(draw_rk(P.rk, gid, ep, TAG_STUCK).x);
+    if (dead) xd = stuck_value(P, P.depth, gid, ep, 0);
     o.xd = xd;
     return o;
 }
@@ -545,14 +590,14 @@ __device__ __forceinline__ void noisy_core(const ParamsDev& P, uint64_t gid, uin
 #pragma unroll
         for (int c = 0; c < 6; ++c) z[c] += G.bias;
     }
-    const bool dead = bits & BIT_DEAD;
-    float stuck = 0.0f;
-    if (dead) stuck = G.stuck_lo + G.stuck_span * u24(draw_rk(P.rk, gid, ep, TAG_STUCK).y);
+    if (G.quant > 0.0f) {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        float v = quantise(G, z[c]);
-        if (dead) v = stuck;
-        z[c] = v;
+        for (int c = 0; c < 6; ++c) z[c] = G.quant * rintf(z[c] / G.quant);
+    }
+    if (bits & BIT_DEAD) {
+        const float stuck = stuck_value(P, G, gid, ep, 1);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) z[c] = stuck;
     }
 }
 
@@ -605,8 +650,8 @@ __device__ __forceinline__ void noisy_ft(const StepArgs& a, const Smem& S, Out o
     noisy_ft_apply(a, S, out, i, g, ep, step, bits, base, r, cc, rows, cols, wrap, dr);
 }
 
-// One per-link quantity, summed over taxels [s0, s1) in lattice order with
-// compensated accumulation (deterministic).  Quantities: 0-5 clean
+// One per-link quantity, summed over taxels [s0, s1) with compensated
+// accumulation (link_sum: deterministic).  Quantities: 0-5 clean
 // force/torque (out cols 0-5), 6-8 clean agg_force in ZYX order (cols 12-14,
 // scaled 1e4), 9-11 noisy agg_force (cols 15-17), 12 clean count, 13 noisy
 // count, 14-19 noisy force/torque (cols 6-11, read from `noisy`).
@@ -620,13 +665,13 @@ __device__ __forceinline__ void link_quantity(const StepArgs& a, const Smem& S, 
         a.link_count[rec * 2 + bit] = cnt;
         return;
     }
-    Acc acc{0.f, 0.f};
+    float sum;
     int col;
     float scale = 1.0f;
     if (qn < 6 || qn >= 14) {
         const float* src = qn < 6 ? S.fc[qn] : noisy[qn - 14];
         col = qn < 6 ? qn : 6 + (qn - 14);
-        for (int i = s0; i < s1; ++i) acc_add(acc, src[i]);
+        sum = link_sum(src, s0, s1);
     } else {
         // agg_force terms d n (clean or noisy depth), each a single rounded product
         const bool nz = qn >= 9;
@@ -635,9 +680,9 @@ __device__ __forceinline__ void link_quantity(const StepArgs& a, const Smem& S, 
         const float* nv = S.dn[2 + axis];
         col = nz ? 15 + (qn - 9) : 12 + (qn - 6);
         scale = 1e4f;
-        for (int i = s0; i < s1; ++i) acc_add(acc, __fmul_rn(d[i], nv[i]));
+        sum = link_sum_prod(d, nv, s0, s1);
     }
-    a.link_out[rec * kLinkOut + col] = scale * acc_value(acc);
+    a.link_out[rec * kLinkOut + col] = scale * sum;
 }
 
 }  // namespace tg

@@ -154,14 +154,13 @@ __device__ __forceinline__ void pipe_link_quantity(const StepArgs& a, const Smem
         a.link_count[rec * 2 + bit] = cnt;
         return;
     }
-    Acc acc{0.f, 0.f};
+    float sum;
     int col;
     float scale = 1.0f;
     if (qn < 6 || qn >= 14) {
         const float* src = qn < 6 ? S.fc[qn] : S.hx[qn - 14];
         col = qn < 6 ? qn : 6 + (qn - 14);
-#pragma unroll 4
-        for (int i = s0; i < s1; ++i) acc_add(acc, src[i]);
+        sum = link_sum(src, s0, s1);
     } else {
         const bool noisy = qn >= 9;
         const int axis = noisy ? 2 - (qn - 9) : 2 - (qn - 6);  // ZYX
@@ -169,10 +168,9 @@ __device__ __forceinline__ void pipe_link_quantity(const StepArgs& a, const Smem
         const float* n = G.ch[4 + axis] + L.geo[4 + axis];
         col = noisy ? 15 + (qn - 9) : 12 + (qn - 6);
         scale = 1e4f;
-#pragma unroll 4
-        for (int i = s0; i < s1; ++i) acc_add(acc, __fmul_rn(d[i], n[i]));
+        sum = link_sum_prod(d, n, s0, s1);
     }
-    a.link_out[rec * kLinkOut + col] = scale * acc_value(acc);
+    a.link_out[rec * kLinkOut + col] = scale * sum;
 }
 
 template <int NT, bool RADIUS>
