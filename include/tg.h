@@ -311,8 +311,9 @@ tg_status tg_object_info(const tg_scene* scene, int32_t i, int32_t* kind_used, d
 
 /* Start a new episode for the envs whose env_mask byte is non-zero (host or
    device [E]; NULL = all): dead masks are redrawn from (seed, taxel id,
-   episode), hysteresis, drift and Schmitt state are zeroed.  Ordered on
-   `stream`. */
+   episode), hysteresis, drift and Schmitt state are zeroed, and so are the
+   envs' clean depth and force/torque outputs (they read zero until the
+   envs' next step).  Ordered on `stream`. */
 tg_status tg_reset_envs(tg_scene* scene, const uint8_t* env_mask, uint32_t episode, tg_stream stream);
 
 /* Per-step inputs (host or device pointers, caller-owned). */
@@ -454,7 +455,11 @@ tg_status tg_read_taxels(tg_scene* scene, int32_t channel, int32_t noisy, void* 
 size_t tg_channel_bytes(const tg_scene* scene, int32_t channel);
 
 /* Device view of a library-owned output buffer (no copy).  CONTACT has no
-   view: read it, or decode TG_CH_STATE_FLAGS.  Errors: TG_ERR_INVALID_ARG. */
+   view: read it, or decode TG_CH_STATE_FLAGS.  Views are read-only: without
+   probe-radius noise or a read delay the next step reads last step's clean
+   depth and force/torque back as the hysteresis state (gain times the
+   clean reading is x_{t-1} of Eqs. 29-30), so writing into them changes the
+   next step's noisy readout.  Errors: TG_ERR_INVALID_ARG. */
 tg_status tg_get_buffer(tg_scene* scene, int32_t channel, int32_t noisy, void** dev_ptr, size_t* bytes);
 
 /* Wait for the scene's work on `stream` and report device-side errors
