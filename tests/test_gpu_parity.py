@@ -138,7 +138,15 @@ def test_reset_subset_of_envs(tg):
     osc = oracle_scene(wl); ost = osc.new_state(); osc.reset(ost, 0)
     mask = np.zeros(10, np.uint8); mask[[1, 4, 7]] = 1
     sc.step(wl.inputs(0)); osc.step(ost, wl.inputs(0))
+    before = gpu_outputs(sc)
     sc.reset(5, env_mask=mask); osc.reset(ost, 5, env_mask=mask)
+    # a reset env's clean depth and force/torque read zero until its next
+    # step (they carry the hysteresis x_{t-1}); the other envs keep theirs
+    after = gpu_outputs(sc); sc.sync()
+    in_reset = np.repeat(mask.astype(bool), np.diff(wl.taxel_offsets))
+    for k in ("depth_clean", "ft_clean"):
+        assert not after[k][..., in_reset].any(), k
+        assert np.array_equal(after[k][..., ~in_reset], before[k][..., ~in_reset]), k
     for s in (1, 2):
         sc.step(wl.inputs(s))
         g = gpu_outputs(sc); sc.sync()
