@@ -304,17 +304,17 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(const StepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmemStep& S = *reinterpret_cast<SmemStep*>(smem_raw);
     const uint32_t step = a.step_from_ctl ? a.ctl->step : a.step;
-    if (!PERSISTENT) {
+    if constexpr (!PERSISTENT) {
         step_item<NT, RADIUS, GRID>(a, S, blockIdx.x, step);
-        return;
-    }
-    for (;;) {
-        if (threadIdx.x == 0) S.slot = atomicAdd(&a.ctl->counter, 1u);
-        __syncthreads();
-        const int slot = (int)S.slot;
-        if (slot >= a.n_items) break;
-        step_item<NT, RADIUS, GRID>(a, S, slot, step);
-        __syncthreads();  // shared memory is reused by the next item
+    } else {
+        for (;;) {
+            if (threadIdx.x == 0) S.slot = atomicAdd(&a.ctl->counter, 1u);
+            __syncthreads();
+            const int slot = (int)S.slot;
+            if (slot >= a.n_items) break;
+            step_item<NT, RADIUS, GRID>(a, S, slot, step);
+            __syncthreads();  // shared memory is reused by the next item
+        }
     }
 }
 

@@ -635,7 +635,6 @@ template <class Smem, class Out>
 __device__ __forceinline__ void noisy_ft(const StepArgs& a, const Smem& S, Out out, int i, tidx g, uint32_t ep,
                                          uint32_t step, uint8_t bits, int base, int r, int cc, int rows, int cols,
                                          bool wrap) {
-    const ParamsDev& P = a.P;
     const int64_t T = a.n_taxels;
     if (!(bits & BIT_ACTIVE)) {
 #pragma unroll
