@@ -15,12 +15,14 @@
 //            (position, radius and flags come from shared memory, where A1
 //            left them)
 //   phase N  per taxel: noise state (gain, hysteresis, depth base noise, dead)
-//            with all state loads independent of the geometry; agg_force terms
-//   phase C1 per (link, quantity): clean sums, agg_force, contact counts
+//            with all state loads independent of the geometry; alongside it,
+//            per (link, quantity), the clean force/torque sums and clean
+//            contact counts (their inputs are final after A2)
 //   phase B  per taxel: 3x3 crosstalk from shared memory, drift/white noise,
-//            quantisation, dead override -> noisy force/torque
-//   phase C2 per (link, quantity): noisy sums
-// Link sums are sequential compensated (Neumaier) sums in lattice order, so
+//            quantisation, dead override -> noisy force/torque; alongside it
+//            the agg_force sums and noisy contact counts (final after N)
+//   phase C2 per (link, quantity): noisy force/torque sums
+// Link sums are compensated (Kahan) sums in a fixed order (link_sum), so
 // results are deterministic run to run.
 #include <cstdint>
 
@@ -250,28 +252,54 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
     }
     __syncthreads();
 
-    // ---- phase N: noise state of every taxel (independent state loads)
-    for (int i = tid; i < n; i += NT) {
-        const tidx g = (tidx)(it.taxel_begin + i);
-        const uint8_t bits = S.bits[i];
-        if (bits & BIT_ACTIVE)
-            noise_state<RADIUS>(a, S, i, g, ep, step, bits, __ldcs(a.nx + g), __ldcs(a.ny + g), __ldcs(a.nz + g));
-        else noise_state_filler(a, S, i, g);
+    // ---- phase N: noise state of every taxel (independent state loads);
+    //      the clean force/torque sums and clean counts (final after A2) run
+    //      here too, while a thread's first taxel's state loads are in flight
+    {
+        const int ntask = nl * 7;
+        int i = tid;
+        NoiseIn s0{};
+        float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+        uint8_t b0 = 0;
+        tidx g0 = 0;
+        if (i < n) {
+            g0 = (tidx)(it.taxel_begin + i);
+            b0 = S.bits[i];
+            if (b0 & BIT_ACTIVE) {
+                s0 = noise_load(a, g0);
+                m0 = __ldcs(a.nx + g0); m1 = __ldcs(a.ny + g0); m2 = __ldcs(a.nz + g0);
+            }
+        }
+        for (int t = tid; t < ntask; t += NT) {
+            const int ll = t % nl, q = t / nl;
+            link_quantity(a, S, S.fc, (size_t)(e * L + lb + ll), S.start[ll], S.start[ll + 1], q < 6 ? q : 12);
+        }
+        if (i < n) {
+            if (b0 & BIT_ACTIVE) noise_apply<RADIUS>(a, S, i, g0, ep, step, b0, m0, m1, m2, s0);
+            else noise_state_filler(a, S, i, g0);
+        }
+        for (i = tid + NT; i < n; i += NT) {
+            const tidx g = (tidx)(it.taxel_begin + i);
+            const uint8_t bits = S.bits[i];
+            if (bits & BIT_ACTIVE)
+                noise_state<RADIUS>(a, S, i, g, ep, step, bits, __ldcs(a.nx + g), __ldcs(a.ny + g), __ldcs(a.nz + g));
+            else noise_state_filler(a, S, i, g);
+        }
     }
-    __syncthreads();
-
-    // ---- phase C1: clean link sums, agg_force (clean and noisy), contact counts
-    for (int t = tid; t < nl * 14; t += NT) {
-        const int ll = t % nl;
-        link_quantity(a, S, S.fc, (size_t)(e * L + lb + ll), S.start[ll], S.start[ll + 1], t / nl);
-    }
-    // (the last thread, after its link quantities if it has any)
-    if (a.items_sorted && tid == NT - 1) prefetch_grid_ahead(a, slot);
     __syncthreads();
 
     // ---- phase B: crosstalk, base noise, dead override -> noisy force/torque
-    //      (written over the clean values in fc, which C1 has consumed)
+    //      (written over the clean values in fc, summed in phase N); the
+    //      agg_force sums and noisy counts (final after N) run here too
     l = 0;
+    {
+        const int ntask = nl * 7;
+        for (int t = tid; t < ntask; t += NT) {
+            const int ll = t % nl, q = t / nl;
+            link_quantity(a, S, S.fc, (size_t)(e * L + lb + ll), S.start[ll], S.start[ll + 1], q < 6 ? 6 + q : 13);
+        }
+        if (a.items_sorted && tid == NT - 1) prefetch_grid_ahead(a, slot);
+    }
     for (int i = tid; i < n; i += NT) {
         if (S.uni_len) {
             const int base = uni_div(i, S.uni_inv_len) * S.uni_len;
