@@ -21,7 +21,7 @@
 //   phase B  per taxel: 3x3 crosstalk from shared memory, drift/white noise,
 //            quantisation, dead override -> noisy force/torque; alongside it
 //            the agg_force sums and noisy contact counts (final after N)
-//   phase C2 per (link, quantity): noisy force/torque sums
+//   phase C2 per (link, quantity, half): noisy force/torque sums
 // Link sums are compensated (Kahan) sums in a fixed order (link_sum), so
 // results are deterministic run to run.
 #include <cstdint>
@@ -317,10 +317,19 @@ __device__ __forceinline__ void step_item(const StepArgs& a, SmemStep& S, int sl
     }
     __syncthreads();
 
-    // ---- phase C2: noisy force/torque link sums
-    for (int t = tid; t < nl * 6; t += NT) {
-        const int ll = t % nl;
-        link_quantity(a, S, S.fc, (size_t)(e * L + lb + ll), S.start[ll], S.start[ll + 1], 14 + t / nl);
+    // ---- phase C2: noisy force/torque link sums, two threads (adjacent
+    //      lanes) per (link, quantity), a half of the link each, joined
+    //      through a shuffle as link_sum_halves joins them
+    static_assert(kItemMaxLinks * 12 <= NT, "one pass of C2");
+    if (tid < nl * 12) {
+        const int task = tid >> 1, half = tid & 1;
+        const int ll = task % nl, q = task / nl;
+        const int s0 = S.start[ll], s1 = S.start[ll + 1], mid = link_mid(s0, s1);
+        const Acc h = link_acc(S.fc[q], half ? mid : s0, half ? s1 : mid);
+        // (pairs are whole: nl * 12 is even, and a pair's lanes are adjacent)
+        const unsigned m = __activemask();
+        const float os = __shfl_down_sync(m, h.s, 1), oc = __shfl_down_sync(m, h.c, 1);
+        if (!half) a.link_out[(size_t)(e * L + lb + ll) * kLinkOut + 6 + q] = acc_join(h, Acc{os, oc});
     }
 }
 

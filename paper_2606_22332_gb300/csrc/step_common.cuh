@@ -66,7 +66,7 @@ __device__ __forceinline__ float acc_value(const Acc& a) { return a.s - a.c; }
 // Compensated sum of a link's terms src[s0..s1) (deterministic): Kahan
 // accumulators over the even and the odd positions, two independent
 // dependency chains side by side, then combined.
-__device__ __forceinline__ float link_sum(const float* src, int s0, int s1) {
+__device__ __forceinline__ Acc link_acc(const float* src, int s0, int s1) {
     Acc e{0.f, 0.f}, o{0.f, 0.f};
     int i = s0;
 #pragma unroll 4
@@ -77,7 +77,24 @@ __device__ __forceinline__ float link_sum(const float* src, int s0, int s1) {
     if (i < s1) acc_add(e, src[i]);
     acc_add(e, o.s);
     acc_add(e, -o.c);
+    return e;
+}
+__device__ __forceinline__ float link_sum(const float* src, int s0, int s1) { return acc_value(link_acc(src, s0, s1)); }
+
+// the sum of two partial sums, the first then the second
+__device__ __forceinline__ float acc_join(Acc e, const Acc& o) {
+    acc_add(e, o.s);
+    acc_add(e, -o.c);
     return acc_value(e);
+}
+// the midpoint at which link_sum_halves splits [s0, s1)
+__device__ __forceinline__ int link_mid(int s0, int s1) { return s0 + (s1 - s0) / 2; }
+// link_sum over the two halves of [s0, s1) apart, then joined: the form of
+// the noisy force/torque sums, which the grid and persistent schedules run
+// on two threads (a half each, joined through a shuffle)
+__device__ __forceinline__ float link_sum_halves(const float* src, int s0, int s1) {
+    const int m = link_mid(s0, s1);
+    return acc_join(link_acc(src, s0, m), link_acc(src, m, s1));
 }
 
 // the same for the terms d[i] n[i], each product rounded on its own
@@ -650,7 +667,8 @@ __device__ __forceinline__ void noisy_ft(const StepArgs& a, const Smem& S, Out o
 }
 
 // One per-link quantity, summed over taxels [s0, s1) with compensated
-// accumulation (link_sum: deterministic).  Quantities: 0-5 clean
+// accumulation (link_sum, or link_sum_halves for the noisy force/torque:
+// deterministic).  Quantities: 0-5 clean
 // force/torque (out cols 0-5), 6-8 clean agg_force in ZYX order (cols 12-14,
 // scaled 1e4), 9-11 noisy agg_force (cols 15-17), 12 clean count, 13 noisy
 // count, 14-19 noisy force/torque (cols 6-11, read from `noisy`).
@@ -667,10 +685,12 @@ __device__ __forceinline__ void link_quantity(const StepArgs& a, const Smem& S, 
     float sum;
     int col;
     float scale = 1.0f;
-    if (qn < 6 || qn >= 14) {
-        const float* src = qn < 6 ? S.fc[qn] : noisy[qn - 14];
-        col = qn < 6 ? qn : 6 + (qn - 14);
-        sum = link_sum(src, s0, s1);
+    if (qn < 6) {
+        col = qn;
+        sum = link_sum(S.fc[qn], s0, s1);
+    } else if (qn >= 14) {
+        col = 6 + (qn - 14);
+        sum = link_sum_halves(noisy[qn - 14], s0, s1);
     } else {
         // agg_force terms d n (clean or noisy depth), each a single rounded product
         const bool nz = qn >= 9;

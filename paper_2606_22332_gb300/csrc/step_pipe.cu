@@ -157,10 +157,12 @@ __device__ __forceinline__ void pipe_link_quantity(const StepArgs& a, const Smem
     float sum;
     int col;
     float scale = 1.0f;
-    if (qn < 6 || qn >= 14) {
-        const float* src = qn < 6 ? S.fc[qn] : S.hx[qn - 14];
-        col = qn < 6 ? qn : 6 + (qn - 14);
-        sum = link_sum(src, s0, s1);
+    if (qn < 6) {
+        col = qn;
+        sum = link_sum(S.fc[qn], s0, s1);
+    } else if (qn >= 14) {
+        col = 6 + (qn - 14);
+        sum = link_sum_halves(S.hx[qn - 14], s0, s1);
     } else {
         const bool noisy = qn >= 9;
         const int axis = noisy ? 2 - (qn - 9) : 2 - (qn - 6);  // ZYX
