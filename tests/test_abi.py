@@ -79,3 +79,19 @@ def test_max_link_taxels(libpath):
     import paper_2606_22332_gb300.tg as tg
 
     assert tg.lib().tg_max_link_taxels() >= 1000
+
+
+def test_binding_names_every_schedule():
+    """tg.SCHEDULES names the header's tg_schedule values in order (the
+    autotuner's report and tg_set_schedule index them)."""
+    import paper_2606_22332_gb300.tg as tg
+
+    src = open(os.path.join(ROOT, "include", "tg.h")).read()
+    body = re.search(r"typedef enum \{([^}]*)\} tg_schedule;", src, flags=re.S).group(1)
+    vals = dict((k, int(v)) for k, v in re.findall(r"(TG_SCHED_[A-Z_0-9]+)\s*=\s*(\d+)", body))
+    assert vals["TG_SCHED_COUNT"] == len(tg.SCHEDULES)
+    expect = {"grid": "TG_SCHED_GRID", "persistent": "TG_SCHED_PERSISTENT", "pipe1024": "TG_SCHED_PIPE_1024",
+              "pipe768": "TG_SCHED_PIPE_768", "pipe512": "TG_SCHED_PIPE_512", "grid384": "TG_SCHED_GRID_384",
+              "persistent384": "TG_SCHED_PERSISTENT_384"}
+    for i, name in enumerate(tg.SCHEDULES):
+        assert vals[expect[name]] == i, name
