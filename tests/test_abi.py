@@ -81,7 +81,7 @@ def test_max_link_taxels(libpath):
     assert tg.lib().tg_max_link_taxels() >= 1000
 
 
-def test_binding_names_every_schedule():
+def test_binding_names_every_schedule(libpath):
     """tg.SCHEDULES names the header's tg_schedule values in order (the
     autotuner's report and tg_set_schedule index them)."""
     import paper_2606_22332_gb300.tg as tg
