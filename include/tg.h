@@ -471,7 +471,11 @@ const char* tg_last_error(const tg_scene* scene);
 /* Checkpoint: the per-taxel state (flags, hysteresis, drift), per-env
    episode numbers and, with shear anchors on, the anchors of every pad.  With buf == NULL, *size receives the needed size.
    Philox draws are counter-based, so a restored scene replays bit-exactly.
-   Synchronous.  Errors: TG_ERR_INVALID_ARG (size mismatch). */
+   A checkpoint restores a scene of the same shape and noise-chain form
+   (with or without probe-radius noise or a read delay: without them the
+   hysteresis x_{t-1} of the depth and force/torque channels is stored as the
+   clean outputs it derives from); any other buffer is refused.
+   Synchronous.  Errors: TG_ERR_INVALID_ARG (size or shape mismatch). */
 tg_status tg_save_state(tg_scene* scene, void* buf, size_t* size);
 tg_status tg_load_state(tg_scene* scene, const void* buf, size_t size);
 

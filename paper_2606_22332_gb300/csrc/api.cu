@@ -1518,6 +1518,11 @@ tg_status tg_sync(tg_scene* s, tg_stream stream) {
 const char* tg_last_error(const tg_scene* s) { return s ? s->last_error.c_str() : g_create_error.c_str(); }
 
 static const uint64_t kStateMagic = 0x3130455441545354ull;  // "TSTATE01"
+// with prev_out the hysteresis x_{t-1} of channels 0-6 is stored as the clean
+// outputs (not gain times them): such checkpoints carry their own tag, so
+// that one of the other form is refused rather than misread
+static const uint64_t kStateMagicOut = 0x3230455441545354ull;  // "TSTATE02"
+static uint64_t state_magic(const tg_scene* s) { return s->P.prev_out ? kStateMagicOut : kStateMagic; }
 
 // shear anchor slots of the scene (0 when the shear anchors are off)
 static size_t shear_slots(const tg_scene* s) {
@@ -1542,7 +1547,7 @@ tg_status tg_save_state(tg_scene* s, void* buf, size_t* size) {
     if (*size != need) return fail(s, TG_ERR_INVALID_ARG, "state buffer size mismatch");
     CK(s, cudaDeviceSynchronize());
     unsigned char* p = (unsigned char*)buf;
-    uint64_t hdr[4] = {kStateMagic, (uint64_t)T, (uint64_t)E, (uint64_t)A};
+    uint64_t hdr[4] = {state_magic(s), (uint64_t)T, (uint64_t)E, (uint64_t)A};
     memcpy(p, hdr, 32);
     p += 32;
     CK(s, cudaMemcpy(p, s->flags, T, cudaMemcpyDeviceToHost)); p += T;
@@ -1571,7 +1576,7 @@ tg_status tg_load_state(tg_scene* s, const void* buf, size_t size) {
     const unsigned char* p = (const unsigned char*)buf;
     uint64_t hdr[4];
     memcpy(hdr, p, 32);
-    if (hdr[0] != kStateMagic || hdr[1] != T || hdr[2] != E || hdr[3] != A) return fail(s, TG_ERR_INVALID_ARG, "state buffer is not from a scene of this shape");
+    if (hdr[0] != state_magic(s) || hdr[1] != T || hdr[2] != E || hdr[3] != A) return fail(s, TG_ERR_INVALID_ARG, "state buffer is not from a scene of this shape");
     p += 32;
     CK(s, cudaDeviceSynchronize());
     CK(s, cudaMemcpy(s->flags, p, T, cudaMemcpyHostToDevice)); p += T;
