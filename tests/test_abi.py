@@ -95,3 +95,22 @@ def test_binding_names_every_schedule(libpath):
               "persistent384": "TG_SCHED_PERSISTENT_384"}
     for i, name in enumerate(tg.SCHEDULES):
         assert vals[expect[name]] == i, name
+
+
+def test_create_scene_rejects_too_many_taxels_on_the_host(libpath):
+    """A scene indexes its per-taxel arrays with 32 bits: tg_create_scene
+    refuses 2^31 taxels or more before it touches the GPU."""
+    import numpy as np
+
+    import paper_2606_22332_gb300.tg as tg
+
+    offs = np.array([0, 1 << 31], np.int64)
+    rows = np.ones(1, np.int32)
+    cols = np.ones(1, np.int32)
+    d = tg.SceneDesc()
+    d.n_envs, d.max_links = 1, 1
+    d.taxel_offsets, d.link_rows, d.link_cols = offs.ctypes.data, rows.ctypes.data, cols.ctypes.data
+    h = ctypes.c_void_p()
+    st = tg.lib().tg_create_scene(ctypes.byref(d), ctypes.byref(h))
+    assert st == 1 and not h.value  # TG_ERR_INVALID_ARG, no scene
+    assert b"2^31" in tg.lib().tg_last_error(None)
