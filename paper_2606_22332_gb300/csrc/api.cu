@@ -74,6 +74,10 @@ struct tg_scene {
     int32_t* s_obj_id[2] = {};
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t staged_ev[2] = {nullptr, nullptr}, used_ev[2] = {nullptr, nullptr};
+    // the work-item order kernel runs on aux_stream beside the pose kernel
+    // (it reads only the step's object ids): fork_ev / join_ev bracket it
+    cudaStream_t aux_stream = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     bool used_rec[2] = {false, false};
     int next_set = 0;
     uint8_t* s_mask = nullptr;
@@ -557,6 +561,9 @@ tg_status tg_create_scene(const tg_scene_desc* d, tg_scene** out) {
         CKC(cudaEventCreateWithFlags(&s->used_ev[k], cudaEventDisableTiming));
     }
     CKC(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking));
+    CKC(cudaStreamCreateWithFlags(&s->aux_stream, cudaStreamNonBlocking));
+    CKC(cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming));
+    CKC(cudaEventCreateWithFlags(&s->join_ev, cudaEventDisableTiming));
     CKC(dalloc(&s->s_mask, E));
     CKC(dalloc(&s->s_contact, T));
     CKC(dalloc(&s->items_sorted, items.size()));
@@ -696,6 +703,9 @@ void tg_destroy_scene(tg_scene* s) {
     if (s->graph) cudaGraphDestroy(s->graph);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+    if (s->aux_stream) cudaStreamDestroy(s->aux_stream);
+    if (s->fork_ev) cudaEventDestroy(s->fork_ev);
+    if (s->join_ev) cudaEventDestroy(s->join_ev);
     for (int k = 0; k < 2; ++k) {
         if (s->staged_ev[k]) cudaEventDestroy(s->staged_ev[k]);
         if (s->used_ev[k]) cudaEventDestroy(s->used_ev[k]);
@@ -1056,7 +1066,6 @@ tg_status enqueue_step(tg_scene* s, const tg_step_inputs* in, cudaStream_t st, b
         }
         CK(s, record(ev[0]));
     }
-    CK(s, launch_pose(pa, st));
     StepArgs a = step_args(s);
     a.obj_id = oid;
     a.step = in->step;
@@ -1064,11 +1073,26 @@ tg_status enqueue_step(tg_scene* s, const tg_step_inputs* in, cudaStream_t st, b
     a.items_sorted = nullptr;
     const bool pipe = sched_pipe(s->schedule);
     const bool sort = s->sorted && s->n_objects > 1 && s->n_objects <= 12288;
+    // The order of the work items depends on the step's object ids only, so
+    // its kernel (one CTA) runs on the auxiliary stream beside the pose
+    // kernel and `st` waits for it before the first kernel that reads it.
+    // (Under capture the event pair becomes a fork and a join of the graph.)
+    const bool order = pipe || sort;
+    if (order) {
+        CK(s, cudaEventRecord(s->fork_ev, st));
+        CK(s, cudaStreamWaitEvent(s->aux_stream, s->fork_ev, 0));
+    }
+    CK(s, launch_pose(pa, st));
     if (pipe) {
-        CK(s, launch_slot_records(s->items, s->n_items, oid, s->n_objects, s->episode, sort ? 1 : 0, s->slots, st));
+        CK(s, launch_slot_records(s->items, s->n_items, oid, s->n_objects, s->episode, sort ? 1 : 0, s->slots,
+                                  s->aux_stream));
     } else if (sort) {
-        CK(s, launch_order_items(s->items, s->n_items, oid, s->n_objects, s->items_sorted, st));
+        CK(s, launch_order_items(s->items, s->n_items, oid, s->n_objects, s->items_sorted, s->aux_stream));
         a.items_sorted = s->items_sorted;
+    }
+    if (order) {
+        CK(s, cudaEventRecord(s->join_ev, s->aux_stream));
+        CK(s, cudaStreamWaitEvent(st, s->join_ev, 0));
     }
     if (prof) CK(s, record(ev[1]));
     if (s->any_neural) CK(s, launch_nsdf_step_query(a, s->n_items, s->nq_phi, s->nq_grad, st));
